@@ -1,0 +1,94 @@
+"""Canonical instantiation keys and the expected dispatch choice -- TEST INFRASTRUCTURE.
+
+A restatement, written from the documented key format, of what the library
+must produce for a specialization request.  The paper's runtime looks an
+instantiation up by {mangled template name, non-type template values, type
+strings} (Sec. 4, Algorithm 1, first step); our key is the byte image of the
+same information for a fixed set of kernel templates:
+
+  offset size field
+  0      u16  kernel id (1 update chain, 2 LTimes, 3 grouped update chain)
+  2      u8   dtype (0 f64, 1 f32, 2 bf16 operands / f32 state)
+  3      u8   layout_a (chain: 0 row-major, 1 column-major; LTimes: in order 0..5)
+  4      u8   layout_b (LTimes: out order 0..5; else 0)
+  5      u8   reserved, 0
+  6      u16  n (chain matrix size; else 0)
+  8      u16  m (LTimes moments; else 0)
+  10     u16  d (LTimes directions; else 0)
+  12     u32x4 tile parameters after default resolution
+  28     u32  flags that select code (GENERIC, NO_AOT, INJECT_COMPILE_ERROR)
+
+All little-endian.  Fields that a kernel does not use are zeroed, so requests
+differing only there share an instantiation.
+
+Default tile resolution (tile all zero, no cost model):
+  update chain / grouped, f64 or f32:  n <= 4 -> (2 = instance per thread, 128, 0, 0)
+                                       else   -> (1 = row per thread, ipb, 0, 0)
+                                       with ipb = max(1, 256 // n)
+  update chain, bf16:                  (3 = tensor-core warp tile, 1, 0, 0)
+  LTimes: (TG, TZ, threads, (R << 8) | S) =
+      f64: (1, 64, 256, (1 << 8) | 9)    f32: (1, 128, 96, (4 << 8) | 12)
+Expected variant: GENERIC flag -> generic; else update chain f64/f32 with
+n in {4, 8, 16, 32}, default tile, AoT set enabled and no NO_AOT flag -> aot;
+else jit.
+"""
+from __future__ import annotations
+
+import struct
+
+K_UPDATE_CHAIN = 1
+K_LTIMES = 2
+K_UPDATE_CHAIN_GROUPED = 3
+
+F64, F32, BF16 = 0, 1, 2
+
+FLAG_GENERIC = 1
+FLAG_NO_AOT = 2
+FLAG_INJECT_COMPILE_ERROR = 0x100
+KEY_FLAGS = FLAG_GENERIC | FLAG_NO_AOT | FLAG_INJECT_COMPILE_ERROR
+
+AOT_SIZES = (4, 8, 16, 32)
+
+VARIANT_GENERIC, VARIANT_AOT, VARIANT_JIT = 0, 1, 2
+
+
+def default_tile(kernel: int, dtype: int, n: int) -> tuple:
+    if kernel in (K_UPDATE_CHAIN, K_UPDATE_CHAIN_GROUPED):
+        if dtype == BF16:
+            return (3, 1, 0, 0)
+        if n <= 4:
+            return (2, 128, 0, 0)
+        return (1, max(1, 256 // n), 0, 0)
+    if kernel == K_LTIMES:
+        if dtype == F64:
+            return (1, 64, 256, (1 << 8) | 9)
+        return (1, 128, 96, (4 << 8) | 12)
+    raise ValueError("unknown kernel")
+
+
+def canonical_key(kernel: int, dtype: int, n=0, layout_a=0, layout_b=0, m=0, d=0,
+                  tile=(0, 0, 0, 0), flags=0) -> bytes:
+    tile = tuple(tile)
+    if kernel in (K_UPDATE_CHAIN, K_UPDATE_CHAIN_GROUPED):
+        m = d = layout_b = 0
+        if kernel == K_UPDATE_CHAIN_GROUPED:
+            layout_a = 0
+    elif kernel == K_LTIMES:
+        n = 0
+    if flags & FLAG_GENERIC:
+        tile = (0, 0, 0, 0)            # the generic kernel has no tile template
+    elif all(t == 0 for t in tile):
+        tile = default_tile(kernel, dtype, n)
+    return struct.pack("<HBBBBHHH4II", kernel, dtype, layout_a, layout_b, 0, n, m, d,
+                       *tile, flags & KEY_FLAGS)
+
+
+def expected_variant(kernel: int, dtype: int, n: int, tile=(0, 0, 0, 0), flags=0,
+                     enable_aot_set=True) -> int:
+    if flags & FLAG_GENERIC:
+        return VARIANT_GENERIC
+    if (kernel == K_UPDATE_CHAIN and dtype in (F64, F32) and n in AOT_SIZES
+            and enable_aot_set and not (flags & (FLAG_NO_AOT | FLAG_INJECT_COMPILE_ERROR))
+            and tuple(tile) in ((0, 0, 0, 0), default_tile(kernel, dtype, n))):
+        return VARIANT_AOT
+    return VARIANT_JIT
