@@ -1,0 +1,213 @@
+/*
+ * cj.h -- C ABI of libcj: runtime template specialization of numeric CUDA
+ * kernels for sm_103a (B300).
+ *
+ * The operation (ClangJIT, Finkel, Poliakoff and Richards, 2019): a function
+ * template whose non-type template arguments (matrix size N, storage order)
+ * and type arguments (dtype) become known only while the program runs is
+ * instantiated and compiled at run time, cached in a program-global table
+ * keyed on those arguments, and called through the result (Sec. 4,
+ * Algorithm 1).  Compilation reads only data embedded in the running binary,
+ * never the file system (Sec. 1 design requirement; Sec. 4 in-memory file
+ * system).  Explicit specializations compiled ahead of time are used instead
+ * of JIT compiling the same instantiation (Sec. 2).  Unlike the paper's
+ * attribute, every call here has an error path and a fallback (Sec. 6,
+ * critique of the attribute design): while an instantiation is compiling, or
+ * if its compilation failed, launches run a generic runtime-N kernel.
+ *
+ * Kernels (all on the caller's stream, inputs and outputs in device memory
+ * owned by the caller):
+ *   CJ_K_UPDATE_CHAIN  -- per instance b: X_0 = I, X_{k+1} = X_k + c X_k A_b,
+ *                         c = 1/(N T), k = 0..T-1, output X_T.  The paper's
+ *                         Eigen benchmark loop (Sec. 5, Listings eigen1/eigen2)
+ *                         in a stable form, batched over instances.
+ *   CJ_K_LTIMES        -- out[m][g][z] = sum_d L[m][d] in[d][g][z], storage
+ *                         orders of in and out chosen at run time (Kripke
+ *                         LTimes, Sec. 5.2, Listings kripold/kripnew).
+ *   CJ_K_UPDATE_CHAIN_GROUPED -- the update chain over a work list of
+ *                         instances of one size N but different step counts,
+ *                         pulled by a persistent kernel (batch amortization of
+ *                         the instantiation lookup, Sec. 5.1).
+ *
+ * Thread safety: every function may be called from any host thread.
+ * cj_specialize serialises on one mutex; cj_launch takes no lock.
+ * Status: every function returns cj_status; cj_last_error() gives a
+ * thread-local message (the NVRTC log after a compile failure).
+ */
+#ifndef CJ_H
+#define CJ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CJ_OK = 0,
+    CJ_ERR_INVALID_ARG = 1,      /* bad argument; nothing was launched or changed */
+    CJ_ERR_NOT_INITIALIZED = 2,  /* cj_init has not succeeded */
+    CJ_ERR_NO_DEVICE = 3,        /* no CUDA device / driver (or compile-only mode on launch) */
+    CJ_ERR_UNSUPPORTED_ARCH = 4, /* device is not compute capability 10.3 */
+    CJ_ERR_COMPILE = 5,          /* NVRTC or module load failed; see cj_last_error */
+    CJ_ERR_CUDA = 6,             /* a CUDA driver/runtime call failed */
+    CJ_ERR_OOM = 7,              /* host or device allocation failed */
+    CJ_ERR_TIMEOUT = 8,          /* cj_specialize_wait: still compiling */
+    CJ_ERR_PENDING = 9           /* reserved */
+} cj_status;
+
+typedef enum {
+    CJ_K_UPDATE_CHAIN = 1,
+    CJ_K_LTIMES = 2,
+    CJ_K_UPDATE_CHAIN_GROUPED = 3
+} cj_kernel_id;
+
+typedef enum {
+    CJ_F64 = 0,
+    CJ_F32 = 1,
+    CJ_BF16 = 2    /* bf16 tensor-core operands, fp32 accumulate, fp32 state; N >= 16 */
+} cj_dtype;
+
+/* Request flags (cj_template_args.flags). */
+#define CJ_FLAG_GENERIC 0x1u      /* use the generic runtime-N kernel, never compile */
+#define CJ_FLAG_NO_AOT 0x2u       /* JIT compile even where an AoT specialization exists */
+#define CJ_FLAG_INJECT_COMPILE_ERROR 0x100u  /* test hook: submit a template that fails to compile */
+
+/* Config flags (cj_config.flags). */
+#define CJ_CFG_COMPILE_ONLY 0x1u  /* no device: compile to CUBIN, never load or launch */
+
+typedef struct {
+    uint32_t sync;             /* 1: cj_specialize blocks until the instantiation is compiled */
+    uint32_t compile_threads;  /* background compile threads (0 -> 1) */
+    uint32_t use_cost_model;   /* 1: tile = 0 requests consult the loaded cost model */
+    uint32_t enable_aot_set;   /* 1: N in {4,8,16,32} (f64/f32 update chain) use AoT kernels */
+    uint32_t debug_bounds;     /* reserved */
+    uint32_t flags;            /* CJ_CFG_* */
+} cj_config;
+
+/*
+ * Runtime template arguments.  Unused fields must be 0 (they are ignored and
+ * zeroed in the key).
+ *   UPDATE_CHAIN:  dtype, n (1..64), layout_a (0 row-major, 1 column-major
+ *                  storage of each A_b and X_b), tile.
+ *   LTIMES:        dtype (f64/f32), layout_a = storage order of in, layout_b =
+ *                  storage order of out, m (1..64), d (1..128), tile.
+ *                  Storage orders list (x, g, z) slowest to fastest, x = d for
+ *                  in and m for out: 0 XGZ, 1 XZG, 2 GXZ, 3 GZX, 4 ZXG, 5 ZGX.
+ *   UPDATE_CHAIN_GROUPED: dtype, n (1..64), tile (row-major only).
+ * tile = {0,0,0,0} means "choose": the cost model if enabled and loaded,
+ * else the default rule below.  Meaning of tile fields:
+ *   update chain: {mapping, instances per block, 0, 0}; mapping 1 = one thread
+ *     per row of X (A staged in shared memory), 2 = one thread per instance
+ *     (X and A in registers, n <= 8), 3 = bf16 tensor-core warp tile.
+ *     Default: n <= 4 -> {2, 128}; else {1, max(1, 256 / n)}; bf16 -> {3, 1}.
+ *   LTimes: {TG, TZ, threads, (R << 8) | S}: a block stages a TG x TZ box of
+ *     (g, z) columns with all d in shared memory; each thread accumulates R
+ *     columns x S moments.  Default: columns CT = 64 (f64) or 128 (f32);
+ *     call orders 1 and 4 "g-fast" (g is the fastest axis) and 0 and 2
+ *     "z-fast"; TG = 1 if neither in nor out is g-fast, 8 if one is g-fast
+ *     and the other z-fast, 32 otherwise; TZ = CT / TG;
+ *     f64: threads 256, R 1, S 9; f32: threads 96, R 4, S 12.
+ */
+typedef struct {
+    int32_t dtype, n, layout_a, layout_b, m, d;
+    int32_t tile[4];
+    uint32_t flags;
+} cj_template_args;
+
+/* An instantiation.  Owned by the library, valid until cj_shutdown. */
+typedef struct cj_handle_s *cj_handle;
+
+typedef struct {
+    uint64_t requests, cache_hits, compiles_ok, compiles_failed, aot_hits;
+    uint64_t launches_generic, launches_aot, launches_jit;
+    double compile_ms_p50, compile_ms_p95, lookup_ns_p50;
+} cj_stats_t;
+
+/* Initialise the library for `device` (idempotent for the same device).
+ * Checks that the device is compute capability 10.3, loads the generic and
+ * AoT kernels, and warms NVRTC so that later compiles touch no file.
+ * cfg may be NULL (async, 1 thread, AoT set on, cost model off). */
+cj_status cj_init(const cj_config *cfg, int device);
+
+/* Look up or create the instantiation of kernel k for the runtime template
+ * arguments a; *out receives its handle.  Cache hit: no compile.  Miss: the
+ * handle is created, serves launches with the generic kernel at once, and an
+ * NVRTC compile is queued (sync mode: performed before returning).  Returns
+ * CJ_ERR_INVALID_ARG for out-of-range arguments (n <= 0 or n > 64, layout out
+ * of range, bf16 with n < 16, null pointers), CJ_ERR_COMPILE in sync mode if
+ * compilation failed (the handle is still valid and runs the generic kernel). */
+cj_status cj_specialize(cj_kernel_id k, const cj_template_args *a, cj_handle *out);
+
+/* Wait up to timeout_ms (negative: forever) for h's compile.  CJ_OK: the
+ * specialized kernel is in use.  CJ_ERR_TIMEOUT: still compiling.
+ * CJ_ERR_COMPILE: compilation failed; launches keep using the generic kernel. */
+cj_status cj_specialize_wait(cj_handle h, int timeout_ms);
+
+/*
+ * Launch h on `cuda_stream` (a cudaStream_t; NULL = legacy default stream).
+ * args follows cuLaunchKernel's kernelParams convention: args[i] points at
+ * the i-th argument value.
+ *   UPDATE_CHAIN: {const T** A, T** X, const int32_t* T_steps}; A and X are
+ *     batch * n * n elements, instance b at offset b * n * n, each stored in
+ *     layout_a order; T_steps >= 1; batch >= 0 instances.
+ *   LTIMES: {const T** L, const T** in, T** out, const int64_t* G,
+ *     const int64_t* Z}; L is [m][d] row-major, in is d*G*Z elements in
+ *     order layout_a, out is m*G*Z in order layout_b; batch is ignored.
+ *   UPDATE_CHAIN_GROUPED: {const int64_t** worklist, const T** A_pool,
+ *     T** X_pool, int32_t** counter}; batch = work items.  Item i is three
+ *     int64 {element offset of A_i and X_i in the pools, T_i, reserved}; items
+ *     should be sorted by T descending.  counter is one int32 in device memory
+ *     that must be 0 at launch (the kernel increments it once per chunk of
+ *     items it hands out and once more per block).
+ * T is double for CJ_F64, float for CJ_F32 and CJ_BF16 (fp32 state).
+ * Never blocks on compilation.  Returns CJ_ERR_INVALID_ARG without launching
+ * for null args or negative batch; CJ_ERR_CUDA if the launch failed. */
+cj_status cj_launch(cj_handle h, void *const *args, int64_t batch, void *cuda_stream);
+
+/* Counters since cj_init; compile times are NVRTC + module load wall time. */
+cj_status cj_stats(cj_stats_t *out);
+
+/* Canonical key (64 hex chars + NUL, needs cap >= 65) and the variant that
+ * launches use right now: 0 generic, 1 AoT, 2 JIT. Either output may be NULL. */
+cj_status cj_handle_info(cj_handle h, char *key_hex, size_t cap, int *variant);
+
+/* Per-thread register count and static shared memory of the kernel that h
+ * launches now (cuFuncGetAttribute), for the register comparison of Sec. 5. */
+cj_status cj_handle_regs(cj_handle h, int *regs_per_thread, int *static_smem);
+
+/*
+ * Grouped plan for an uneven batch (many instances of different N and T in
+ * one launch; the lookup cost is paid once per distinct N, Sec. 5.1).
+ * Instance k has size n[k] (1..64) and steps[k] (>= 1); its A and X occupy
+ * n[k]^2 row-major elements of the pools, at the exclusive prefix sum of
+ * n[j]^2 over j < k.  The plan groups instances by n, requests one
+ * UPDATE_CHAIN_GROUPED instantiation per group (tile 0 = default), orders
+ * each group's items by T descending, and keeps work lists and counters in
+ * device memory it owns.  dtype: CJ_F64 or CJ_F32.
+ */
+typedef struct cj_group_plan_s *cj_group_plan;
+cj_status cj_group_plan_create(int32_t dtype, int64_t count, const int32_t *n, const int32_t *steps,
+                               cj_group_plan *out);
+/* Launch every group on `cuda_stream`: groups run concurrently on forked
+ * streams joined back into cuda_stream.  use_graph = 1: the first call
+ * captures the whole launch into a CUDA graph and later calls replay it
+ * (re-captured when a group's instantiation changed, e.g. from generic to
+ * JIT).  Pools are caller-owned device memory. */
+cj_status cj_group_plan_launch(cj_group_plan p, const void *A_pool, void *X_pool, void *cuda_stream,
+                               int use_graph);
+/* Groups in the plan and pool elements it expects. */
+cj_status cj_group_plan_info(cj_group_plan p, int32_t *n_groups, int64_t *pool_elems);
+cj_status cj_group_plan_destroy(cj_group_plan p);
+
+/* Thread-local description of the last error on this thread ("" if none). */
+const char *cj_last_error(void);
+
+/* Wait for queued compiles, unload modules, free every handle and plan. */
+cj_status cj_shutdown(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CJ_H */

@@ -26,8 +26,10 @@ Default tile resolution (tile all zero, no cost model):
                                        else   -> (1 = row per thread, ipb, 0, 0)
                                        with ipb = max(1, 256 // n)
   update chain, bf16:                  (3 = tensor-core warp tile, 1, 0, 0)
-  LTimes: (TG, TZ, threads, (R << 8) | S) =
-      f64: (1, 64, 256, (1 << 8) | 9)    f32: (1, 128, 96, (4 << 8) | 12)
+  LTimes: (TG, TZ, threads, (R << 8) | S) with CT = 64 (f64) or 128 (f32)
+      columns; orders 1, 4 are g-fast and 0, 2 z-fast; TG = 1 if neither in
+      nor out is g-fast, 8 if one is g-fast and the other z-fast, else 32;
+      TZ = CT / TG; f64: threads 256, R 1, S 9; f32: threads 96, R 4, S 12.
 Expected variant: GENERIC flag -> generic; else update chain f64/f32 with
 n in {4, 8, 16, 32}, default tile, AoT set enabled and no NO_AOT flag -> aot;
 else jit.
@@ -52,7 +54,11 @@ AOT_SIZES = (4, 8, 16, 32)
 VARIANT_GENERIC, VARIANT_AOT, VARIANT_JIT = 0, 1, 2
 
 
-def default_tile(kernel: int, dtype: int, n: int) -> tuple:
+G_FAST = (1, 4)
+Z_FAST = (0, 2)
+
+
+def default_tile(kernel: int, dtype: int, n: int, layout_a: int = 0, layout_b: int = 0) -> tuple:
     if kernel in (K_UPDATE_CHAIN, K_UPDATE_CHAIN_GROUPED):
         if dtype == BF16:
             return (3, 1, 0, 0)
@@ -60,9 +66,17 @@ def default_tile(kernel: int, dtype: int, n: int) -> tuple:
             return (2, 128, 0, 0)
         return (1, max(1, 256 // n), 0, 0)
     if kernel == K_LTIMES:
+        ct = 64 if dtype == F64 else 128
+        gin, gout = layout_a in G_FAST, layout_b in G_FAST
+        if not gin and not gout:
+            tg = 1
+        elif (gin and layout_b in Z_FAST) or (gout and layout_a in Z_FAST):
+            tg = 8
+        else:
+            tg = 32
         if dtype == F64:
-            return (1, 64, 256, (1 << 8) | 9)
-        return (1, 128, 96, (4 << 8) | 12)
+            return (tg, ct // tg, 256, (1 << 8) | 9)
+        return (tg, ct // tg, 96, (4 << 8) | 12)
     raise ValueError("unknown kernel")
 
 
@@ -78,7 +92,7 @@ def canonical_key(kernel: int, dtype: int, n=0, layout_a=0, layout_b=0, m=0, d=0
     if flags & FLAG_GENERIC:
         tile = (0, 0, 0, 0)            # the generic kernel has no tile template
     elif all(t == 0 for t in tile):
-        tile = default_tile(kernel, dtype, n)
+        tile = default_tile(kernel, dtype, n, layout_a, layout_b)
     return struct.pack("<HBBBBHHH4II", kernel, dtype, layout_a, layout_b, 0, n, m, d,
                        *tile, flags & KEY_FLAGS)
 

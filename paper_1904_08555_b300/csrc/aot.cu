@@ -1,0 +1,37 @@
+// aot.cu -- kernels compiled ahead of time by nvcc for sm_103a: the generic
+// runtime-N kernels (the stand-ins while a specialization compiles, and the
+// fallback if it fails) and the explicit specializations n in {4, 8, 16, 32}
+// of the update chain.  Explicit specializations are used instead of JIT
+// compiling the same instantiation (Sec. 2).
+#include "cj_internal.h"
+#include "kernels/ltimes.cuh"
+#include "kernels/update_chain.cuh"
+
+using namespace cjint;
+
+#define CJ_AOT_CHAIN(T, DT, N, L)                                                                 \
+    {K_CHAIN, DT, N, L, {chain_default_map(N, DT), chain_default_ipb(N, DT), 0, 0},              \
+     (const void *)&cj::update_chain<T, N, L, chain_default_map(N, DT), chain_default_ipb(N, DT)>}
+
+#define CJ_AOT_CHAIN_SIZES(T, DT, L) \
+    CJ_AOT_CHAIN(T, DT, 4, L), CJ_AOT_CHAIN(T, DT, 8, L), CJ_AOT_CHAIN(T, DT, 16, L), CJ_AOT_CHAIN(T, DT, 32, L)
+
+static const AotKernel kAotTable[] = {
+    CJ_AOT_CHAIN_SIZES(double, D_F64, 0), CJ_AOT_CHAIN_SIZES(double, D_F64, 1),
+    CJ_AOT_CHAIN_SIZES(float, D_F32, 0),  CJ_AOT_CHAIN_SIZES(float, D_F32, 1),
+};
+
+static const GenericKernels kGeneric = {
+    {(const void *)&cj::update_chain_generic<double>, (const void *)&cj::update_chain_generic<float>},
+    {(const void *)&cj::ltimes_generic<double>, (const void *)&cj::ltimes_generic<float>},
+    {(const void *)&cj::update_chain_grouped_generic<double>,
+     (const void *)&cj::update_chain_grouped_generic<float>},
+};
+
+namespace cjint {
+const AotKernel *aot_table(int *count) {
+    *count = (int)(sizeof(kAotTable) / sizeof(kAotTable[0]));
+    return kAotTable;
+}
+const GenericKernels &generic_kernels() { return kGeneric; }
+}  // namespace cjint

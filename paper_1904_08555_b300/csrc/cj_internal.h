@@ -1,0 +1,36 @@
+// cj_internal.h -- declarations shared by the host library (cj.cpp) and the
+// ahead-of-time kernel unit (aot.cu).  Not part of the public ABI.
+#ifndef CJ_INTERNAL_H
+#define CJ_INTERNAL_H
+
+namespace cjint {
+
+enum { K_CHAIN = 1, K_LTIMES = 2, K_GROUPED = 3 };
+enum { D_F64 = 0, D_F32 = 1, D_BF16 = 2 };
+
+// Default tile rule of the update chain kernels (documented in cj.h).
+constexpr int chain_default_map(int n, int dtype) { return dtype == D_BF16 ? 3 : (n <= 4 ? 2 : 1); }
+constexpr int chain_default_ipb(int n, int dtype) {
+    return dtype == D_BF16 ? 1 : (n <= 4 ? 128 : (256 / n > 1 ? 256 / n : 1));
+}
+
+struct AotKernel {
+    int kernel, dtype, n, layout;
+    int tile[4];
+    const void *fn;   // host stub of the __global__ function
+};
+
+// Explicit specializations compiled by nvcc (update chain, f64/f32,
+// n in {4, 8, 16, 32}, layouts 0 and 1, default tile).
+const AotKernel *aot_table(int *count);
+
+// Generic kernels, indexed by dtype (0 f64, 1 f32).
+struct GenericKernels {
+    const void *chain[2];
+    const void *ltimes[2];
+    const void *grouped[2];
+};
+const GenericKernels &generic_kernels();
+
+}  // namespace cjint
+#endif

@@ -1,0 +1,68 @@
+// geometry.h -- shared-memory pitches and block shapes.  Used by the kernels
+// (compiled by nvcc ahead of time and by NVRTC at run time) and by the host
+// launch code, so that both sides agree on every byte offset.  No includes.
+#ifndef CJ_GEOMETRY_H
+#define CJ_GEOMETRY_H
+
+#if defined(__CUDACC__) || defined(__CUDACC_RTC__)
+#define CJ_HD __host__ __device__
+#else
+#define CJ_HD
+#endif
+
+namespace cjg {
+
+// Update chain, one thread per row (mapping 1): pitch in elements of one
+// instance's A in shared memory.  At least nn, a whole number of 16-byte
+// units, and an odd number of them so consecutive instances start in
+// different bank groups (their threads read different addresses at once).
+CJ_HD constexpr int row_pitch(int nn, int esize) {
+    return ((((nn * esize + 15) / 16) | 1) * 16) / esize;
+}
+
+// Update chain, one thread per instance (mapping 2): each thread reads its
+// own instance, so the pitch is odd (in elements) to spread 32 threads over
+// 32 banks.
+CJ_HD constexpr int inst_pitch(int nn) { return nn | 1; }
+
+// Threads per block of the update chain kernels.
+CJ_HD constexpr int chain_threads(int n, int mapping, int ipb) {
+    return mapping == 2 ? ipb : ((ipb * n + 31) / 32) * 32;
+}
+
+// Rows of X kept in shared memory (instead of registers) above this size.
+CJ_HD constexpr int chain_reg_rows_max(int esize) { return esize == 8 ? 32 : 48; }
+
+// Per-thread pitch of X rows kept in shared memory (odd: conflict-free).
+CJ_HD constexpr int xrow_pitch(int n) { return n | 1; }
+
+// Bytes of dynamic shared memory of the specialized update chain kernel.
+CJ_HD constexpr long chain_smem(int n, int mapping, int ipb, int esize) {
+    return mapping == 2
+        ? (long)ipb * inst_pitch(n * n) * esize
+        : (long)ipb * row_pitch(n * n, esize) * esize +
+              (n > chain_reg_rows_max(esize)
+                   ? (long)chain_threads(n, 1, ipb) * xrow_pitch(n) * esize
+                   : 0L);
+}
+
+// Generic update chain: A pitch uses row_pitch; each thread keeps its row of
+// X and of the product in shared memory with pitch xrow_pitch(n).
+CJ_HD constexpr long chain_generic_smem(int n, int ipb, int threads, int esize) {
+    return (long)ipb * row_pitch(n * n, esize) * esize + 2L * threads * xrow_pitch(n) * esize;
+}
+
+// LTimes: L is kept transposed, [d][m] with m padded to a 16-byte multiple.
+CJ_HD constexpr int lt_mpitch(int m, int esize) { return ((m * esize + 15) / 16) * 16 / esize; }
+// Column tile pitch: CT plus 16 bytes.
+CJ_HD constexpr int lt_cpitch(int ct, int esize) { return ct + 16 / esize; }
+CJ_HD constexpr long lt_smem(int m, int d, int ct, int esize) {
+    return ((long)d * lt_mpitch(m, esize) + (long)(m > d ? m : d) * lt_cpitch(ct, esize)) * esize;
+}
+CJ_HD constexpr long lt_generic_smem(int m, int d, int cols, int esize) {
+    return ((long)m * d + (long)d * cols) * esize;
+}
+
+}  // namespace cjg
+
+#endif

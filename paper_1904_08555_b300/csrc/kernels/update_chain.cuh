@@ -1,0 +1,359 @@
+// update_chain.cuh -- batched small-matrix update chain (the Eigen benchmark
+// loop of Sec. 5, Listings eigen1/eigen2, in the stable form
+// X_{k+1} = X_k + c X_k A_b with X_0 = I and c = 1/(N T)).
+//
+// Compiled two ways from this one source: by nvcc ahead of time (the generic
+// runtime-N kernels and the {4, 8, 16, 32} explicit specializations) and by
+// NVRTC at run time for any other (T, N, layout, tile) a caller asks for.
+// No includes besides geometry.h, which NVRTC receives from memory.
+//
+// Row independence: row i of X evolves on its own, x_i <- x_i + c x_i A, so
+// one thread can own one row with no communication during the T steps; the
+// N threads of an instance read A from shared memory (a broadcast).
+#ifndef CJ_UPDATE_CHAIN_CUH
+#define CJ_UPDATE_CHAIN_CUH
+#include "geometry.h"
+
+namespace cj {
+
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// A is invariant across the T steps.  For small N the compiler may keep all
+// N*N entries in registers; above that it would hoist them anyway and spill,
+// so the base offset is made opaque once per step, which keeps the reads
+// inside the step (broadcast shared-memory loads).
+template <class T, int N>
+struct a_in_regs { static constexpr bool value = sizeof(T) == 8 ? N * N <= 64 : N * N <= 100; };
+
+template <class T>
+__device__ __forceinline__ const T* opaque_base(const T* base, int off) {
+    asm volatile("" : "+r"(off));
+    return base + off;
+}
+
+// Stage `ninst` consecutive instances (contiguous in global memory) into
+// shared memory as logical row-major matrices with pitch P.  Layout 1 stores
+// each instance column-major; it is transposed here so that the compute loop
+// is the same for both layouts.
+template <class T, int LAYOUT>
+__device__ __forceinline__ void chain_stage_in(T* sA, const T* __restrict__ gA, int ninst, int n,
+                                               int P, int tid, int nthreads) {
+    const int nn = n * n;
+    for (int e = tid; e < ninst * nn; e += nthreads) {
+        const int inst = e / nn;
+        const int r = e - inst * nn;
+        const int row = r / n, col = r - row * n;
+        const int l = LAYOUT == 0 ? row : col;
+        const int j = LAYOUT == 0 ? col : row;
+        sA[inst * P + l * n + j] = gA[e];
+    }
+}
+
+// Copy staged results (already in physical order, pitch P) to global memory.
+template <class T>
+__device__ __forceinline__ void chain_stage_out(T* __restrict__ gX, const T* sA, int ninst, int nn,
+                                                int P, int tid, int nthreads) {
+    for (int e = tid; e < ninst * nn; e += nthreads) {
+        const int inst = e / nn;
+        gX[e] = sA[inst * P + (e - inst * nn)];
+    }
+}
+
+// One thread, row i of one instance (A at sA + aoff, logical row-major):
+// T steps with the row of X in registers.
+template <class T, int N>
+__device__ __forceinline__ void row_chain_regs(const T* sA, int aoff, int i, int steps, T cc, T (&x)[N]) {
+#pragma unroll
+    for (int j = 0; j < N; ++j) x[j] = (j == i) ? T(1) : T(0);
+    for (int k = 0; k < steps; ++k) {
+        const T* a = a_in_regs<T, N>::value ? sA + aoff : opaque_base(sA, aoff);
+        T p[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) p[j] = T(0);
+#pragma unroll
+        for (int l = 0; l < N; ++l) {
+            const T xl = x[l];
+#pragma unroll
+            for (int j = 0; j < N; ++j) p[j] = fmaT(xl, a[l * N + j], p[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) x[j] = fmaT(cc, p[j], x[j]);
+    }
+}
+
+// Same for large N: the row of X lives in the thread's own shared-memory row
+// xs (read once per N fused multiply-adds); the product row in registers.
+template <class T, int N>
+__device__ __forceinline__ void row_chain_smem(const T* a, T* xs, int i, int steps, T cc) {
+    for (int j = 0; j < N; ++j) xs[j] = (j == i) ? T(1) : T(0);
+    for (int k = 0; k < steps; ++k) {
+        T p[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) p[j] = T(0);
+#pragma unroll 2
+        for (int l = 0; l < N; ++l) {
+            const T xl = xs[l];
+#pragma unroll
+            for (int j = 0; j < N; ++j) p[j] = fmaT(xl, a[l * N + j], p[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) xs[j] = fmaT(cc, p[j], xs[j]);
+    }
+}
+
+// One thread, a whole small instance: X and A in registers.
+template <class T, int N>
+__device__ __forceinline__ void inst_chain_regs(const T* sa, int steps, T cc, T (&x)[N][N]) {
+    T a[N][N];
+#pragma unroll
+    for (int l = 0; l < N; ++l)
+#pragma unroll
+        for (int j = 0; j < N; ++j) a[l][j] = sa[l * N + j];
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+        for (int j = 0; j < N; ++j) x[i][j] = (i == j) ? T(1) : T(0);
+    for (int k = 0; k < steps; ++k) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            T p[N];
+#pragma unroll
+            for (int j = 0; j < N; ++j) p[j] = T(0);
+#pragma unroll
+            for (int l = 0; l < N; ++l)
+#pragma unroll
+                for (int j = 0; j < N; ++j) p[j] = fmaT(x[i][l], a[l][j], p[j]);
+#pragma unroll
+            for (int j = 0; j < N; ++j) x[i][j] = fmaT(cc, p[j], x[i][j]);
+        }
+    }
+}
+
+// Run the chain for the `ninst` instances staged at sA (pitch per geometry.h)
+// and leave each X_T in place of its A, in storage order LAYOUT.
+// steps_of(inst) and c_of(inst) give the per-instance T and c.
+template <class T, int N, int LAYOUT, int MAP, int IPB, class StepsOf, class COf>
+__device__ __forceinline__ void chain_block(T* sA, int ninst, int tid, StepsOf steps_of, COf c_of) {
+    constexpr int NN = N * N;
+    if constexpr (MAP == 2) {
+        constexpr int P = cjg::inst_pitch(NN);
+        const bool active = tid < ninst;
+        T x[N][N];
+        if (active) inst_chain_regs<T, N>(sA + tid * P, steps_of(tid), c_of(tid), x);
+        __syncthreads();
+        if (active) {
+#pragma unroll
+            for (int i = 0; i < N; ++i)
+#pragma unroll
+                for (int j = 0; j < N; ++j) sA[tid * P + (LAYOUT == 0 ? i * N + j : j * N + i)] = x[i][j];
+        }
+    } else {
+        constexpr int P = cjg::row_pitch(NN, (int)sizeof(T));
+        constexpr bool XREG = N <= cjg::chain_reg_rows_max((int)sizeof(T));
+        const int inst = tid / N;
+        const int i = tid - inst * N;
+        const bool active = inst < ninst;
+        if constexpr (XREG) {
+            T x[N];
+            if (active) row_chain_regs<T, N>(sA, inst * P, i, steps_of(inst), c_of(inst), x);
+            __syncthreads();
+            if (active) {
+#pragma unroll
+                for (int j = 0; j < N; ++j) sA[inst * P + (LAYOUT == 0 ? i * N + j : j * N + i)] = x[j];
+            }
+        } else {
+            constexpr int XP = cjg::xrow_pitch(N);
+            T* xs = sA + IPB * P + tid * XP;
+            if (active) row_chain_smem<T, N>(sA + inst * P, xs, i, steps_of(inst), c_of(inst));
+            __syncthreads();
+            if (active)
+                for (int j = 0; j < N; ++j) sA[inst * P + (LAYOUT == 0 ? i * N + j : j * N + i)] = xs[j];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Specialized kernel.  MAP 1: one thread per row of X, A in shared memory.
+// MAP 2: one thread per instance, X and A in registers (small N).
+// ---------------------------------------------------------------------------
+template <class T, int N, int LAYOUT, int MAP, int IPB>
+__global__ void __launch_bounds__(cjg::chain_threads(N, MAP, IPB))
+update_chain(const T* __restrict__ A, T* __restrict__ X, long long batch, int steps, double c) {
+    constexpr int NN = N * N;
+    constexpr int NT = cjg::chain_threads(N, MAP, IPB);
+    constexpr int P = MAP == 2 ? cjg::inst_pitch(NN) : cjg::row_pitch(NN, (int)sizeof(T));
+    extern __shared__ __align__(16) unsigned char cj_smem[];
+    T* sA = reinterpret_cast<T*>(cj_smem);
+    const long long b0 = (long long)blockIdx.x * IPB;
+    if (b0 >= batch) return;
+    const int ninst = (batch - b0) < IPB ? (int)(batch - b0) : IPB;
+    const T cc = (T)c;
+    const int tid = threadIdx.x;
+    chain_stage_in<T, LAYOUT>(sA, A + b0 * NN, ninst, N, P, tid, NT);
+    __syncthreads();
+    chain_block<T, N, LAYOUT, MAP, IPB>(
+        sA, ninst, tid, [&](int) { return steps; }, [&](int) { return cc; });
+    __syncthreads();
+    chain_stage_out<T>(X + b0 * NN, sA, ninst, NN, P, tid, NT);
+}
+
+// ---------------------------------------------------------------------------
+// Generic runtime-N kernel (the analog of Eigen's Dynamic-size matrices): the
+// same one-thread-per-row mapping, but N, the layout and the instances per
+// block are run-time values, so the thread's row of X and of the product live
+// in shared memory and every loop has run-time bounds.  Supports 1 <= n <= 64.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ void generic_row_chain(const T* a, T* xs, T* ps, int n, int i, int steps, T cc) {
+    for (int j = 0; j < n; ++j) xs[j] = (j == i) ? T(1) : T(0);
+    for (int k = 0; k < steps; ++k) {
+        for (int j = 0; j < n; ++j) {
+            T s = T(0);
+            for (int l = 0; l < n; ++l) s = fmaT(xs[l], a[l * n + j], s);
+            ps[j] = s;
+        }
+        for (int j = 0; j < n; ++j) xs[j] = fmaT(cc, ps[j], xs[j]);
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256)
+update_chain_generic(const T* __restrict__ A, T* __restrict__ X, long long batch, int steps,
+                     double c, int n, int layout, int ipb) {
+    extern __shared__ __align__(16) unsigned char cj_smem[];
+    T* sA = reinterpret_cast<T*>(cj_smem);
+    const int nn = n * n;
+    const int P = cjg::row_pitch(nn, (int)sizeof(T));
+    const int XP = cjg::xrow_pitch(n);
+    const int nthreads = blockDim.x;
+    const int tid = threadIdx.x;
+    T* xs = sA + ipb * P + tid * XP;
+    T* ps = sA + ipb * P + nthreads * XP + tid * XP;
+    const long long b0 = (long long)blockIdx.x * ipb;
+    if (b0 >= batch) return;
+    const int ninst = (batch - b0) < ipb ? (int)(batch - b0) : ipb;
+    if (layout == 0) chain_stage_in<T, 0>(sA, A + b0 * nn, ninst, n, P, tid, nthreads);
+    else             chain_stage_in<T, 1>(sA, A + b0 * nn, ninst, n, P, tid, nthreads);
+    __syncthreads();
+    const int inst = tid / n;
+    const int i = tid - inst * n;
+    const bool active = inst < ninst;
+    if (active) generic_row_chain<T>(sA + inst * P, xs, ps, n, i, steps, (T)c);
+    __syncthreads();
+    if (active)
+        for (int j = 0; j < n; ++j) sA[inst * P + (layout == 0 ? i * n + j : j * n + i)] = xs[j];
+    __syncthreads();
+    chain_stage_out<T>(X + b0 * nn, sA, ninst, nn, P, tid, nthreads);
+}
+
+// ---------------------------------------------------------------------------
+// Grouped persistent kernel: instances of one size N with different step
+// counts, listed in a work list (sorted by T descending by the host).  Each
+// block repeatedly takes the next chunk of IPB consecutive items from a
+// device counter (atomicAdd) until the list is exhausted.  Row-major only.
+// Item: {element offset of A and X in the pools, T, reserved} as int64.
+// c = 1/(N T) is formed per instance in double, as the host would.
+// ---------------------------------------------------------------------------
+template <class T, int N, int MAP, int IPB>
+__global__ void __launch_bounds__(cjg::chain_threads(N, MAP, IPB))
+update_chain_grouped(const long long* __restrict__ items, const T* __restrict__ A_pool,
+                     T* __restrict__ X_pool, int* __restrict__ counter, long long n_items) {
+    constexpr int NN = N * N;
+    constexpr int NT = cjg::chain_threads(N, MAP, IPB);
+    constexpr int P = MAP == 2 ? cjg::inst_pitch(NN) : cjg::row_pitch(NN, (int)sizeof(T));
+    extern __shared__ __align__(16) unsigned char cj_smem[];
+    T* sA = reinterpret_cast<T*>(cj_smem);
+    __shared__ long long s_off[IPB];
+    __shared__ int s_steps[IPB];
+    __shared__ int s_chunk;
+    const int tid = threadIdx.x;
+    const long long n_chunks = (n_items + IPB - 1) / IPB;
+    for (;;) {
+        if (tid == 0) s_chunk = atomicAdd(counter, 1);
+        __syncthreads();
+        const long long chunk = s_chunk;
+        if (chunk >= n_chunks) break;
+        const long long it0 = chunk * IPB;
+        const int ninst = (n_items - it0) < IPB ? (int)(n_items - it0) : IPB;
+        for (int q = tid; q < ninst; q += NT) {
+            s_off[q] = items[3 * (it0 + q)];
+            s_steps[q] = (int)items[3 * (it0 + q) + 1];
+        }
+        __syncthreads();
+        for (int e = tid; e < ninst * NN; e += NT) {
+            const int inst = e / NN;
+            sA[inst * P + (e - inst * NN)] = A_pool[s_off[inst] + (e - inst * NN)];
+        }
+        __syncthreads();
+        chain_block<T, N, 0, MAP, IPB>(
+            sA, ninst, tid, [&](int q) { return s_steps[q]; },
+            [&](int q) { return (T)(1.0 / ((double)N * (double)s_steps[q])); });
+        __syncthreads();
+        for (int e = tid; e < ninst * NN; e += NT) {
+            const int inst = e / NN;
+            X_pool[s_off[inst] + (e - inst * NN)] = sA[inst * P + (e - inst * NN)];
+        }
+        __syncthreads();
+    }
+}
+
+// Generic grouped kernel: the stand-in for update_chain_grouped while its
+// specialization compiles.  Run-time n and instances per chunk (ipb <= 256);
+// rows of X and of the product in shared memory.
+template <class T>
+__global__ void __launch_bounds__(256)
+update_chain_grouped_generic(const long long* __restrict__ items, const T* __restrict__ A_pool,
+                             T* __restrict__ X_pool, int* __restrict__ counter, long long n_items,
+                             int n, int ipb) {
+    extern __shared__ __align__(16) unsigned char cj_smem[];
+    __shared__ long long s_off[256];
+    __shared__ int s_steps[256];
+    __shared__ int s_chunk;
+    T* sA = reinterpret_cast<T*>(cj_smem);
+    const int nn = n * n;
+    const int P = cjg::row_pitch(nn, (int)sizeof(T));
+    const int XP = cjg::xrow_pitch(n);
+    const int nthreads = blockDim.x;
+    const int tid = threadIdx.x;
+    T* xs = sA + ipb * P + tid * XP;
+    T* ps = sA + ipb * P + nthreads * XP + tid * XP;
+    const long long n_chunks = (n_items + ipb - 1) / ipb;
+    for (;;) {
+        if (tid == 0) s_chunk = atomicAdd(counter, 1);
+        __syncthreads();
+        const long long chunk = s_chunk;
+        if (chunk >= n_chunks) break;
+        const long long it0 = chunk * ipb;
+        const int ninst = (n_items - it0) < ipb ? (int)(n_items - it0) : ipb;
+        for (int q = tid; q < ninst; q += nthreads) {
+            s_off[q] = items[3 * (it0 + q)];
+            s_steps[q] = (int)items[3 * (it0 + q) + 1];
+        }
+        __syncthreads();
+        for (int e = tid; e < ninst * nn; e += nthreads) {
+            const int inst = e / nn;
+            sA[inst * P + (e - inst * nn)] = A_pool[s_off[inst] + (e - inst * nn)];
+        }
+        __syncthreads();
+        const int inst = tid / n;
+        const int i = tid - inst * n;
+        const bool active = inst < ninst;
+        if (active) {
+            const int steps = s_steps[inst];
+            generic_row_chain<T>(sA + inst * P, xs, ps, n, i, steps, (T)(1.0 / ((double)n * (double)steps)));
+        }
+        __syncthreads();
+        if (active)
+            for (int j = 0; j < n; ++j) sA[inst * P + i * n + j] = xs[j];
+        __syncthreads();
+        for (int e = tid; e < ninst * nn; e += nthreads) {
+            const int inst2 = e / nn;
+            X_pool[s_off[inst2] + (e - inst2 * nn)] = sA[inst2 * P + (e - inst2 * nn)];
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace cj
+#endif
