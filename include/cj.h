@@ -101,7 +101,8 @@ typedef struct {
  *   update chain: {mapping, instances per block, 0, 0}; mapping 1 = one thread
  *     per row of X (A staged in shared memory), 2 = one thread per instance
  *     (X and A in registers, n <= 8), 3 = bf16 tensor-core warp tile.
- *     Default: n <= 4 -> {2, 128}; else {1, max(1, 256 / n)}; bf16 -> {3, 1}.
+ *     Default: n <= 4 -> {2, 128}; n <= 32 -> {1, max(1, 256 / n)};
+ *     else {1, max(1, 128 / n)}; bf16 -> {3, 1}.
  *   LTimes: {TG, TZ, threads, (R << 8) | S}: a block stages a TG x TZ box of
  *     (g, z) columns with all d in shared memory; each thread accumulates R
  *     columns x S moments.  Default: columns CT = 64 (f64) or 128 (f32);

@@ -24,7 +24,8 @@ differing only there share an instantiation.
 Default tile resolution (tile all zero, no cost model):
   update chain / grouped, f64 or f32:  n <= 4 -> (2 = instance per thread, 128, 0, 0)
                                        else   -> (1 = row per thread, ipb, 0, 0)
-                                       with ipb = max(1, 256 // n)
+                                       with ipb = max(1, 256 // n) for n <= 32,
+                                       max(1, 128 // n) above
   update chain, bf16:                  (3 = tensor-core warp tile, 1, 0, 0)
   LTimes: (TG, TZ, threads, (R << 8) | S) with CT = 64 (f64) or 128 (f32)
       columns; orders 1, 4 are g-fast and 0, 2 z-fast; TG = 1 if neither in
@@ -64,7 +65,7 @@ def default_tile(kernel: int, dtype: int, n: int, layout_a: int = 0, layout_b: i
             return (3, 1, 0, 0)
         if n <= 4:
             return (2, 128, 0, 0)
-        return (1, max(1, 256 // n), 0, 0)
+        return (1, max(1, (256 if n <= 32 else 128) // n), 0, 0)
     if kernel == K_LTIMES:
         ct = 64 if dtype == F64 else 128
         gin, gout = layout_a in G_FAST, layout_b in G_FAST

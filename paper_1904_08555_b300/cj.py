@@ -1,0 +1,226 @@
+"""ctypes binding of libcj (include/cj.h): argument marshalling only.
+
+Every step of the path runs in libcj's kernels.  If the shared library is
+missing it is built from source (nvcc / g++); if that fails the import fails:
+there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+CJ_OK, CJ_ERR_INVALID_ARG, CJ_ERR_NOT_INITIALIZED, CJ_ERR_NO_DEVICE = 0, 1, 2, 3
+CJ_ERR_UNSUPPORTED_ARCH, CJ_ERR_COMPILE, CJ_ERR_CUDA, CJ_ERR_OOM = 4, 5, 6, 7
+CJ_ERR_TIMEOUT, CJ_ERR_PENDING = 8, 9
+
+K_UPDATE_CHAIN, K_LTIMES, K_UPDATE_CHAIN_GROUPED = 1, 2, 3
+F64, F32, BF16 = 0, 1, 2
+FLAG_GENERIC, FLAG_NO_AOT, FLAG_INJECT_COMPILE_ERROR = 0x1, 0x2, 0x100
+CFG_COMPILE_ONLY = 0x1
+VARIANT_NAMES = ("generic", "aot", "jit")
+
+EXPORTS = ("cj_init", "cj_specialize", "cj_specialize_wait", "cj_launch", "cj_stats", "cj_handle_info",
+           "cj_handle_regs", "cj_group_plan_create", "cj_group_plan_launch", "cj_group_plan_info",
+           "cj_group_plan_destroy", "cj_last_error", "cj_shutdown")
+
+
+class CJError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: status {status}: {msg}")
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("sync", ctypes.c_uint32), ("compile_threads", ctypes.c_uint32),
+                ("use_cost_model", ctypes.c_uint32), ("enable_aot_set", ctypes.c_uint32),
+                ("debug_bounds", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+
+
+class TemplateArgs(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int32), ("n", ctypes.c_int32), ("layout_a", ctypes.c_int32),
+                ("layout_b", ctypes.c_int32), ("m", ctypes.c_int32), ("d", ctypes.c_int32),
+                ("tile", ctypes.c_int32 * 4), ("flags", ctypes.c_uint32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("requests", "cache_hits", "compiles_ok", "compiles_failed",
+                                               "aot_hits", "launches_generic", "launches_aot", "launches_jit")] + \
+               [(n, ctypes.c_double) for n in ("compile_ms_p50", "compile_ms_p95", "lookup_ns_p50")]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libcj.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        L.cj_init.argtypes = [ctypes.POINTER(Config), ctypes.c_int]
+        L.cj_specialize.argtypes = [ctypes.c_int, ctypes.POINTER(TemplateArgs), ctypes.POINTER(P)]
+        L.cj_specialize_wait.argtypes = [P, ctypes.c_int]
+        L.cj_launch.argtypes = [P, ctypes.POINTER(P), i64, P]
+        L.cj_stats.argtypes = [ctypes.POINTER(Stats)]
+        L.cj_handle_info.argtypes = [P, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int)]
+        L.cj_handle_regs.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        L.cj_group_plan_create.argtypes = [i32, i64, P, P, ctypes.POINTER(P)]
+        L.cj_group_plan_launch.argtypes = [P, P, P, P, ctypes.c_int]
+        L.cj_group_plan_info.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i64)]
+        L.cj_group_plan_destroy.argtypes = [P]
+        L.cj_last_error.restype = ctypes.c_char_p
+        L.cj_shutdown.argtypes = []
+        for name in EXPORTS:
+            if name != "cj_last_error":
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return load().cj_last_error().decode(errors="replace")
+
+
+def _check(rc: int, where: str, ok=(CJ_OK,)):
+    if rc not in ok:
+        raise CJError(rc, where, last_error())
+    return rc
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream, *tensors) -> int:
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    for t in tensors:
+        if hasattr(t, "is_cuda") and t.is_cuda:
+            import torch
+            return torch.cuda.current_stream(t.device).cuda_stream
+    return 0
+
+
+def init(sync=False, compile_threads=1, use_cost_model=False, enable_aot_set=True,
+         compile_only=False, device=0) -> None:
+    cfg = Config(int(sync), compile_threads, int(use_cost_model), int(enable_aot_set), 0,
+                 CFG_COMPILE_ONLY if compile_only else 0)
+    _check(load().cj_init(ctypes.byref(cfg), device), "cj_init")
+
+
+def shutdown() -> None:
+    _check(load().cj_shutdown(), "cj_shutdown")
+
+
+class Handle:
+    """An instantiation returned by cj_specialize (owned by the library)."""
+
+    def __init__(self, ptr: int, kernel: int, args: TemplateArgs):
+        self.ptr = ptr
+        self.kernel = kernel
+        self.dtype = args.dtype
+        self.n = args.n
+
+    def info(self):
+        buf = ctypes.create_string_buffer(65)
+        var = ctypes.c_int(-1)
+        _check(load().cj_handle_info(self.ptr, buf, 65, ctypes.byref(var)), "cj_handle_info")
+        return buf.value.decode(), var.value
+
+    @property
+    def key_hex(self) -> str:
+        return self.info()[0]
+
+    @property
+    def variant(self) -> str:
+        return VARIANT_NAMES[self.info()[1]]
+
+    def regs(self):
+        r, s = ctypes.c_int(0), ctypes.c_int(0)
+        _check(load().cj_handle_regs(self.ptr, ctypes.byref(r), ctypes.byref(s)), "cj_handle_regs")
+        return r.value, s.value
+
+    def wait(self, timeout_ms: int = -1) -> int:
+        return load().cj_specialize_wait(self.ptr, timeout_ms)
+
+    def __eq__(self, other):
+        return isinstance(other, Handle) and other.ptr == self.ptr
+
+    def __hash__(self):
+        return hash(self.ptr)
+
+
+def specialize(kernel: int, dtype: int, n=0, layout_a=0, layout_b=0, m=0, d=0, tile=(0, 0, 0, 0),
+               flags=0, allow_compile_error=False) -> Handle:
+    a = TemplateArgs(dtype, n, layout_a, layout_b, m, d, (ctypes.c_int32 * 4)(*tile), flags)
+    out = ctypes.c_void_p()
+    ok = (CJ_OK, CJ_ERR_COMPILE) if allow_compile_error else (CJ_OK,)
+    _check(load().cj_specialize(kernel, ctypes.byref(a), ctypes.byref(out)), "cj_specialize", ok)
+    return Handle(out.value, kernel, a)
+
+
+def _launch(h: Handle, vals, batch: int, stream: int) -> None:
+    arr = (ctypes.c_void_p * len(vals))(*[ctypes.cast(ctypes.pointer(v), ctypes.c_void_p) for v in vals])
+    _check(load().cj_launch(h.ptr, arr, batch, stream), "cj_launch")
+
+
+def launch_update_chain(h: Handle, A, X, steps: int, batch: int | None = None, stream=None) -> None:
+    """X_T for every instance: A, X hold batch*n*n elements (tensors or device pointers)."""
+    if batch is None:
+        batch = A.numel() // (h.n * h.n)
+    vals = [ctypes.c_void_p(_ptr(A)), ctypes.c_void_p(_ptr(X)), ctypes.c_int32(steps)]
+    _launch(h, vals, batch, _stream(stream, A, X))
+
+
+def launch_ltimes(h: Handle, L, x, out, G: int, Z: int, stream=None) -> None:
+    vals = [ctypes.c_void_p(_ptr(L)), ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(out)),
+            ctypes.c_int64(G), ctypes.c_int64(Z)]
+    _launch(h, vals, Z, _stream(stream, L, x, out))
+
+
+def launch_grouped(h: Handle, items, A_pool, X_pool, counter, n_items: int, stream=None) -> None:
+    vals = [ctypes.c_void_p(_ptr(items)), ctypes.c_void_p(_ptr(A_pool)), ctypes.c_void_p(_ptr(X_pool)),
+            ctypes.c_void_p(_ptr(counter))]
+    _launch(h, vals, n_items, _stream(stream, A_pool, X_pool))
+
+
+def stats() -> dict:
+    s = Stats()
+    _check(load().cj_stats(ctypes.byref(s)), "cj_stats")
+    return {name: getattr(s, name) for name, _ in Stats._fields_}
+
+
+class GroupPlan:
+    """cj_group_plan_*: uneven batch grouped by n, launched as one (graph) launch."""
+
+    def __init__(self, dtype: int, n, steps):
+        import numpy as np
+        n = np.ascontiguousarray(n, dtype=np.int32)
+        steps = np.ascontiguousarray(steps, dtype=np.int32)
+        out = ctypes.c_void_p()
+        _check(load().cj_group_plan_create(dtype, len(n), n.ctypes.data, steps.ctypes.data, ctypes.byref(out)),
+               "cj_group_plan_create")
+        self.ptr = out.value
+        g, e = ctypes.c_int32(0), ctypes.c_int64(0)
+        _check(load().cj_group_plan_info(self.ptr, ctypes.byref(g), ctypes.byref(e)), "cj_group_plan_info")
+        self.n_groups, self.pool_elems = g.value, e.value
+
+    def launch(self, A_pool, X_pool, stream=None, use_graph=True) -> None:
+        _check(load().cj_group_plan_launch(self.ptr, _ptr(A_pool), _ptr(X_pool), _stream(stream, A_pool, X_pool),
+                                           int(use_graph)), "cj_group_plan_launch")
+
+    def destroy(self) -> None:
+        if self.ptr:
+            load().cj_group_plan_destroy(self.ptr)
+            self.ptr = None

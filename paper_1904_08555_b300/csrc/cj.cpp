@@ -1,0 +1,991 @@
+// cj.cpp -- host side of libcj: the C ABI of include/cj.h, the program-global
+// instantiation cache, the NVRTC specializer with its background compile
+// threads, the generic / AoT / JIT dispatch and the grouped-plan scheduler.
+//
+// The runtime follows the paper's Algorithm 1 (Sec. 4) in its CUDA form:
+// look the instantiation up in a global cache guarded by a mutex; on a miss,
+// instantiate the template from source embedded in this binary (never from a
+// file), compile it for the device's architecture and keep the result in the
+// cache.  On B300 the device compiler is NVRTC producing sm_103a CUBIN, which
+// is loaded with cuLibraryLoadData (the paper built PTX and a fatbin by hand,
+// Sec. 4.1).  Unlike the paper, a miss does not block the caller: launches
+// use the generic runtime-N kernel until the specialization is ready.
+#include "cj.h"
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <nvrtc.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "cj_internal.h"
+#include "kernels/geometry.h"
+
+// Kernel template sources, embedded at build time (generated from kernels/).
+#include "generated/embedded_sources.inc"
+
+#define CJ_API extern "C" __attribute__((visibility("default")))
+
+namespace {
+
+using clk = std::chrono::steady_clock;
+
+thread_local std::string t_err;
+
+cj_status fail(cj_status s, const char *fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return s;
+}
+
+// ---------------------------------------------------------------------------
+// Driver API entry points, fetched through the runtime so that the library
+// loads on machines without a driver (compile-only use, CPU tests).
+// ---------------------------------------------------------------------------
+struct Driver {
+    CUresult (*LibraryLoadData)(CUlibrary *, const void *, CUjit_option *, void **, unsigned int,
+                                CUlibraryOption *, void **, unsigned int) = nullptr;
+    CUresult (*LibraryGetKernel)(CUkernel *, CUlibrary, const char *) = nullptr;
+    CUresult (*LibraryUnload)(CUlibrary) = nullptr;
+    CUresult (*KernelGetFunction)(CUfunction *, CUkernel) = nullptr;
+    CUresult (*FuncSetAttribute)(CUfunction, CUfunction_attribute, int) = nullptr;
+    CUresult (*FuncGetAttribute)(int *, CUfunction_attribute, CUfunction) = nullptr;
+    CUresult (*LaunchKernel)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned,
+                             unsigned, CUstream, void **, void **) = nullptr;
+    CUresult (*OccupancyMaxActiveBlocksPerMultiprocessor)(int *, CUfunction, int, size_t) = nullptr;
+    CUresult (*GetErrorString)(CUresult, const char **) = nullptr;
+} drv;
+
+template <class F>
+bool entry(const char *name, F &fp) {
+    cudaDriverEntryPointQueryResult q;
+    void *p = nullptr;
+    if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p)
+        return false;
+    fp = reinterpret_cast<F>(p);
+    return true;
+}
+
+bool load_driver() {
+    return entry("cuLibraryLoadData", drv.LibraryLoadData) && entry("cuLibraryGetKernel", drv.LibraryGetKernel) &&
+           entry("cuLibraryUnload", drv.LibraryUnload) && entry("cuKernelGetFunction", drv.KernelGetFunction) &&
+           entry("cuFuncSetAttribute", drv.FuncSetAttribute) && entry("cuFuncGetAttribute", drv.FuncGetAttribute) &&
+           entry("cuLaunchKernel", drv.LaunchKernel) &&
+           entry("cuOccupancyMaxActiveBlocksPerMultiprocessor", drv.OccupancyMaxActiveBlocksPerMultiprocessor) &&
+           entry("cuGetErrorString", drv.GetErrorString);
+}
+
+const char *cu_str(CUresult r) {
+    const char *s = nullptr;
+    if (drv.GetErrorString) drv.GetErrorString(r, &s);
+    return s ? s : "unknown CUDA driver error";
+}
+
+// ---------------------------------------------------------------------------
+// Handles
+// ---------------------------------------------------------------------------
+enum { ST_PENDING = 0, ST_READY = 1, ST_FAILED = 2, ST_GENERIC_ONLY = 3 };
+enum { V_GENERIC = 0, V_AOT = 1, V_JIT = 2 };
+constexpr uint32_t kKeyFlags = CJ_FLAG_GENERIC | CJ_FLAG_NO_AOT | CJ_FLAG_INJECT_COMPILE_ERROR;
+
+// Everything a launch needs; immutable once published through Handle::impl.
+struct Impl {
+    CUfunction fn = nullptr;
+    int variant = V_GENERIC;
+    int threads = 0;
+    size_t smem = 0;
+    int ipb = 0;            // update chain / grouped: instances per block or chunk
+    int blocks_per_sm = 1;  // persistent kernels (LTimes specialized, grouped)
+};
+
+}  // namespace
+
+struct cj_handle_s {
+    int kernel = 0;
+    cj_template_args a{};   // normalised request, tile resolved
+    unsigned char key[32]{};
+    std::atomic<const Impl *> impl{nullptr};
+    Impl generic, spec;
+    std::atomic<int> state{ST_PENDING};
+    std::mutex mu;
+    std::condition_variable cv;
+    CUlibrary lib = nullptr;
+    std::string name_expr, error;
+    double compile_ms = 0;
+};
+
+struct cj_group_plan_s;
+
+namespace {
+
+struct State {
+    bool inited = false;
+    int device = -1;
+    bool compile_only = false;
+    cj_config cfg{};
+    int num_sms = 0;
+    int smem_optin = 0;
+    std::mutex mu;  // cache, queue, plans
+    std::unordered_map<std::string, cj_handle_s *> cache;
+    std::deque<cj_handle_s *> queue;
+    std::condition_variable qcv;
+    bool stop = false;
+    int busy = 0;
+    std::condition_variable idle_cv;
+    std::vector<std::thread> workers;
+    CUfunction gen_chain[2]{}, gen_lt[2]{}, gen_grp[2]{};
+    struct Aot {
+        cjint::AotKernel k;
+        CUfunction fn;
+    };
+    std::vector<Aot> aot;
+    std::vector<cj_group_plan_s *> plans;
+    // statistics
+    std::atomic<uint64_t> requests{0}, hits{0}, ok{0}, failed{0}, aot_hits{0};
+    std::atomic<uint64_t> l_gen{0}, l_aot{0}, l_jit{0};
+    std::mutex smu;
+    std::vector<double> compile_ms;
+    std::vector<double> lookup_ns;
+    size_t lookup_pos = 0;
+    // A process that exits without cj_shutdown still stops its compile
+    // threads here (no CUDA calls: the runtime may already be gone).
+    ~State() {
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            stop = true;
+            queue.clear();
+        }
+        qcv.notify_all();
+        for (auto &t : workers)
+            if (t.joinable()) t.join();
+    }
+} G;
+
+std::mutex g_init_mu;
+
+int esize(int dtype) { return dtype == CJ_F64 ? 8 : 4; }
+int dt_index(int dtype) { return dtype == CJ_F64 ? 0 : 1; }
+const char *ctype(int dtype) { return dtype == CJ_F64 ? "double" : "float"; }
+
+// ---------------------------------------------------------------------------
+// Requests: validation, normalisation, default tiles, canonical key
+// ---------------------------------------------------------------------------
+bool g_fast(int lay) { return lay == 1 || lay == 4; }
+bool z_fast(int lay) { return lay == 0 || lay == 2; }
+
+void default_tile(int k, cj_template_args &a) {
+    if (k == CJ_K_UPDATE_CHAIN || k == CJ_K_UPDATE_CHAIN_GROUPED) {
+        a.tile[0] = cjint::chain_default_map(a.n, a.dtype);
+        a.tile[1] = cjint::chain_default_ipb(a.n, a.dtype);
+        a.tile[2] = a.tile[3] = 0;
+        return;
+    }
+    const int ct = a.dtype == CJ_F64 ? 64 : 128;
+    const bool gi = g_fast(a.layout_a), go = g_fast(a.layout_b);
+    int tg;
+    if (!gi && !go) tg = 1;
+    else if ((gi && z_fast(a.layout_b)) || (go && z_fast(a.layout_a))) tg = 8;
+    else tg = 32;
+    a.tile[0] = tg;
+    a.tile[1] = ct / tg;
+    if (a.dtype == CJ_F64) {
+        a.tile[2] = 256;
+        a.tile[3] = (1 << 8) | 9;
+    } else {
+        a.tile[2] = 96;
+        a.tile[3] = (4 << 8) | 12;
+    }
+}
+
+cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_args &a) {
+    a = in;
+    if (k != CJ_K_UPDATE_CHAIN && k != CJ_K_LTIMES && k != CJ_K_UPDATE_CHAIN_GROUPED)
+        return fail(CJ_ERR_INVALID_ARG, "unknown kernel id %d", k);
+    if (a.dtype < 0 || a.dtype > 2) return fail(CJ_ERR_INVALID_ARG, "dtype %d out of range", a.dtype);
+    if (a.flags & ~kKeyFlags) return fail(CJ_ERR_INVALID_ARG, "unknown flag bits 0x%x", a.flags & ~kKeyFlags);
+    if (k == CJ_K_LTIMES) {
+        if (a.dtype == CJ_BF16) return fail(CJ_ERR_INVALID_ARG, "LTimes supports f64 and f32 only");
+        if (a.layout_a < 0 || a.layout_a > 5 || a.layout_b < 0 || a.layout_b > 5)
+            return fail(CJ_ERR_INVALID_ARG, "LTimes storage orders must be 0..5");
+        if (a.m < 1 || a.m > 64 || a.d < 1 || a.d > 128)
+            return fail(CJ_ERR_INVALID_ARG, "LTimes needs 1 <= m <= 64 and 1 <= d <= 128");
+        a.n = 0;
+    } else {
+        if (a.n < 1 || a.n > 64) return fail(CJ_ERR_INVALID_ARG, "n = %d outside 1..64", a.n);
+        if (k == CJ_K_UPDATE_CHAIN_GROUPED) a.layout_a = 0;
+        if (a.layout_a != 0 && a.layout_a != 1) return fail(CJ_ERR_INVALID_ARG, "layout %d must be 0 or 1", a.layout_a);
+        if (a.dtype == CJ_BF16)
+            return fail(CJ_ERR_INVALID_ARG, "the bf16 tensor-core update chain is not available in this build");
+        a.m = a.d = a.layout_b = 0;
+    }
+    if (a.flags & CJ_FLAG_GENERIC) {
+        for (int &t : a.tile) t = 0;
+        return CJ_OK;
+    }
+    if (a.tile[0] == 0 && a.tile[1] == 0 && a.tile[2] == 0 && a.tile[3] == 0) default_tile(k, a);
+    // explicit tiles: check the kernel can be instantiated and launched
+    if (k != CJ_K_LTIMES) {
+        const int map = a.tile[0], ipb = a.tile[1];
+        if (map != 1 && map != 2) return fail(CJ_ERR_INVALID_ARG, "update chain mapping %d must be 1 or 2", map);
+        if (map == 2 && a.n > 8) return fail(CJ_ERR_INVALID_ARG, "mapping 2 needs n <= 8");
+        if (ipb < 1 || cjg::chain_threads(a.n, map, ipb) > 1024 || a.tile[2] || a.tile[3])
+            return fail(CJ_ERR_INVALID_ARG, "bad instances-per-block %d for n = %d", ipb, a.n);
+        if (k == CJ_K_UPDATE_CHAIN_GROUPED && ipb > 256) return fail(CJ_ERR_INVALID_ARG, "grouped ipb must be <= 256");
+        if (cjg::chain_smem(a.n, map, ipb, esize(a.dtype)) > 220 * 1024)
+            return fail(CJ_ERR_INVALID_ARG, "tile needs too much shared memory");
+    } else {
+        const int tg = a.tile[0], tz = a.tile[1], nt = a.tile[2], r = a.tile[3] >> 8, s = a.tile[3] & 0xff;
+        if (tg < 1 || tz < 1 || r < 1 || s < 1 || nt < 32 || nt > 1024 || (tg * tz) % r || a.m % s ||
+            (tg * tz / r) * (a.m / s) != nt)
+            return fail(CJ_ERR_INVALID_ARG, "LTimes tile {%d,%d,%d,%d} does not cover its block", a.tile[0],
+                        a.tile[1], a.tile[2], a.tile[3]);
+        if (cjg::lt_smem(a.m, a.d, tg * tz, esize(a.dtype)) > 220 * 1024)
+            return fail(CJ_ERR_INVALID_ARG, "LTimes tile needs too much shared memory");
+    }
+    return CJ_OK;
+}
+
+void put16(unsigned char *p, uint32_t v) { p[0] = v & 0xff; p[1] = (v >> 8) & 0xff; }
+void put32(unsigned char *p, uint32_t v) { for (int i = 0; i < 4; ++i) p[i] = (v >> (8 * i)) & 0xff; }
+
+void make_key(int k, const cj_template_args &a, unsigned char *key) {
+    memset(key, 0, 32);
+    put16(key + 0, (uint32_t)k);
+    key[2] = (unsigned char)a.dtype;
+    key[3] = (unsigned char)a.layout_a;
+    key[4] = (unsigned char)a.layout_b;
+    put16(key + 6, (uint32_t)a.n);
+    put16(key + 8, (uint32_t)a.m);
+    put16(key + 10, (uint32_t)a.d);
+    for (int i = 0; i < 4; ++i) put32(key + 12 + 4 * i, (uint32_t)a.tile[i]);
+    put32(key + 28, a.flags & kKeyFlags);
+}
+
+// ---------------------------------------------------------------------------
+// Launch geometry
+// ---------------------------------------------------------------------------
+int occupancy(CUfunction f, int threads, size_t smem) {
+    int nb = 1;
+    if (f && drv.OccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, threads, smem) != CUDA_SUCCESS) nb = 1;
+    return nb < 1 ? 1 : nb;
+}
+
+void generic_impl(cj_handle_s *h) {
+    Impl &g = h->generic;
+    const cj_template_args &a = h->a;
+    const int di = dt_index(a.dtype), es = esize(a.dtype);
+    g.variant = V_GENERIC;
+    if (h->kernel == CJ_K_LTIMES) {
+        g.fn = G.gen_lt[di];
+        g.threads = a.dtype == CJ_F64 ? 64 : 128;
+        g.smem = (size_t)cjg::lt_generic_smem(a.m, a.d, g.threads, es);
+    } else {
+        g.fn = h->kernel == CJ_K_UPDATE_CHAIN ? G.gen_chain[di] : G.gen_grp[di];
+        g.ipb = std::max(1, 128 / a.n);
+        g.threads = ((g.ipb * a.n + 31) / 32) * 32;
+        g.smem = (size_t)cjg::chain_generic_smem(a.n, g.ipb, g.threads, es);
+        if (h->kernel == CJ_K_UPDATE_CHAIN_GROUPED) g.blocks_per_sm = occupancy(g.fn, g.threads, g.smem);
+    }
+}
+
+void spec_geometry(const cj_handle_s *h, Impl &s) {
+    const cj_template_args &a = h->a;
+    const int es = esize(a.dtype);
+    if (h->kernel == CJ_K_LTIMES) {
+        s.threads = a.tile[2];
+        s.smem = (size_t)cjg::lt_smem(a.m, a.d, a.tile[0] * a.tile[1], es);
+    } else {
+        s.ipb = a.tile[1];
+        s.threads = cjg::chain_threads(a.n, a.tile[0], a.tile[1]);
+        s.smem = (size_t)cjg::chain_smem(a.n, a.tile[0], a.tile[1], es);
+    }
+}
+
+std::string name_expression(const cj_handle_s *h) {
+    const cj_template_args &a = h->a;
+    char buf[256];
+    if (h->kernel == CJ_K_UPDATE_CHAIN)
+        snprintf(buf, sizeof buf, "cj::update_chain<%s, %d, %d, %d, %d>", ctype(a.dtype), a.n, a.layout_a,
+                 a.tile[0], a.tile[1]);
+    else if (h->kernel == CJ_K_UPDATE_CHAIN_GROUPED)
+        snprintf(buf, sizeof buf, "cj::update_chain_grouped<%s, %d, %d, %d>", ctype(a.dtype), a.n, a.tile[0],
+                 a.tile[1]);
+    else
+        snprintf(buf, sizeof buf, "cj::ltimes<%s, %d, %d, %d, %d, %d, %d, %d, %d, %d>", ctype(a.dtype), a.m, a.d,
+                 a.layout_a, a.layout_b, a.tile[0], a.tile[1], a.tile[2], a.tile[3] >> 8, a.tile[3] & 0xff);
+    return buf;
+}
+
+// ---------------------------------------------------------------------------
+// NVRTC specializer: in-memory sources and headers only.
+// ---------------------------------------------------------------------------
+const char *kNvrtcOpts[] = {"-arch=sm_103a", "-std=c++17", "-lineinfo"};
+constexpr int kNumNvrtcOpts = 3;
+
+struct CompileOut {
+    nvrtcResult rc = NVRTC_SUCCESS;
+    std::string log, lowered;
+    std::vector<char> cubin;
+};
+
+CompileOut nvrtc_compile(const std::string &src, const char *name_expr) {
+    CompileOut out;
+    const char *hdr_src[3] = {cj_emb_geometry_h, cj_emb_update_chain_cuh, cj_emb_ltimes_cuh};
+    const char *hdr_name[3] = {"geometry.h", "update_chain.cuh", "ltimes.cuh"};
+    nvrtcProgram prog;
+    out.rc = nvrtcCreateProgram(&prog, src.c_str(), "cj_instantiation.cu", 3, hdr_src, hdr_name);
+    if (out.rc != NVRTC_SUCCESS) return out;
+    if (name_expr) nvrtcAddNameExpression(prog, name_expr);
+    out.rc = nvrtcCompileProgram(prog, kNumNvrtcOpts, kNvrtcOpts);
+    size_t ls = 0;
+    nvrtcGetProgramLogSize(prog, &ls);
+    if (ls > 1) {
+        out.log.resize(ls);
+        nvrtcGetProgramLog(prog, &out.log[0]);
+    }
+    if (out.rc == NVRTC_SUCCESS) {
+        if (name_expr) {
+            const char *low = nullptr;
+            out.rc = nvrtcGetLoweredName(prog, name_expr, &low);
+            if (out.rc == NVRTC_SUCCESS && low) out.lowered = low;
+        }
+        size_t cs = 0;
+        if (out.rc == NVRTC_SUCCESS) out.rc = nvrtcGetCUBINSize(prog, &cs);
+        if (out.rc == NVRTC_SUCCESS) {
+            out.cubin.resize(cs);
+            out.rc = nvrtcGetCUBIN(prog, out.cubin.data());
+        }
+    }
+    nvrtcDestroyProgram(&prog);
+    return out;
+}
+
+void record_compile_ms(double ms) {
+    std::lock_guard<std::mutex> lk(G.smu);
+    G.compile_ms.push_back(ms);
+}
+
+void finish(cj_handle_s *h, int state) {
+    {
+        std::lock_guard<std::mutex> lk(h->mu);
+        h->state.store(state, std::memory_order_release);
+    }
+    h->cv.notify_all();
+}
+
+cj_status compile_handle(cj_handle_s *h) {
+    const auto t0 = clk::now();
+    std::string src = h->kernel == CJ_K_LTIMES ? "#include \"ltimes.cuh\"\n" : "#include \"update_chain.cuh\"\n";
+    if (h->a.flags & CJ_FLAG_INJECT_COMPILE_ERROR)
+        src += "namespace cj { __device__ int injected_failure = this_identifier_does_not_exist; }\n";
+    CompileOut c = nvrtc_compile(src, h->name_expr.c_str());
+    if (c.rc != NVRTC_SUCCESS) {
+        h->error = std::string("NVRTC: ") + nvrtcGetErrorString(c.rc) + "\n" + c.log;
+        t_err = h->error;
+        G.failed++;
+        finish(h, ST_FAILED);
+        return CJ_ERR_COMPILE;
+    }
+    Impl &s = h->spec;
+    spec_geometry(h, s);
+    s.variant = V_JIT;
+    if (!G.compile_only) {
+        cudaSetDevice(G.device);
+        CUkernel kern = nullptr;
+        CUresult r = drv.LibraryLoadData(&h->lib, c.cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+        if (r == CUDA_SUCCESS) r = drv.LibraryGetKernel(&kern, h->lib, c.lowered.c_str());
+        if (r == CUDA_SUCCESS) r = drv.KernelGetFunction(&s.fn, kern);
+        if (r == CUDA_SUCCESS && s.smem > 48 * 1024)
+            r = drv.FuncSetAttribute(s.fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)s.smem);
+        if (r != CUDA_SUCCESS) {
+            h->error = std::string("module load: ") + cu_str(r);
+            t_err = h->error;
+            G.failed++;
+            finish(h, ST_FAILED);
+            return CJ_ERR_COMPILE;
+        }
+        s.blocks_per_sm = occupancy(s.fn, s.threads, s.smem);
+        h->impl.store(&h->spec, std::memory_order_release);
+    }
+    h->compile_ms = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+    record_compile_ms(h->compile_ms);
+    G.ok++;
+    finish(h, ST_READY);
+    return CJ_OK;
+}
+
+void worker_loop() {
+    if (!G.compile_only) cudaSetDevice(G.device);
+    for (;;) {
+        cj_handle_s *h;
+        {
+            std::unique_lock<std::mutex> lk(G.mu);
+            G.qcv.wait(lk, [] { return G.stop || !G.queue.empty(); });
+            if (G.queue.empty()) return;
+            h = G.queue.front();
+            G.queue.pop_front();
+            G.busy++;
+        }
+        compile_handle(h);
+        {
+            std::lock_guard<std::mutex> lk(G.mu);
+            G.busy--;
+        }
+        G.idle_cv.notify_all();
+    }
+}
+
+// The explicit specialization for h's arguments, if one was compiled AoT.
+const State::Aot *find_aot(const cj_handle_s *h) {
+    for (const auto &e : G.aot)
+        if (e.k.kernel == h->kernel && e.k.dtype == h->a.dtype && e.k.n == h->a.n && e.k.layout == h->a.layout_a &&
+            e.k.tile[0] == h->a.tile[0] && e.k.tile[1] == h->a.tile[1])
+            return &e;
+    return nullptr;
+}
+
+double percentile(std::vector<double> v, double p) {
+    if (v.empty()) return 0.0;
+    std::sort(v.begin(), v.end());
+    const double pos = p * (double)(v.size() - 1);
+    const size_t lo = (size_t)pos;
+    const size_t hi = std::min(lo + 1, v.size() - 1);
+    return v[lo] + (v[hi] - v[lo]) * (pos - (double)lo);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Grouped plan
+// ---------------------------------------------------------------------------
+struct cj_group_plan_s {
+    int dtype = 0;
+    int64_t count = 0, pool_elems = 0;
+    struct Group {
+        int n = 0;
+        cj_handle h = nullptr;
+        int64_t n_items = 0, first_item = 0;
+        double cost = 0;
+    };
+    std::vector<Group> groups;
+    long long *d_items = nullptr;
+    int *d_counters = nullptr;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const void *g_A = nullptr;
+    void *g_X = nullptr;
+    cudaStream_t g_stream = nullptr;
+    std::vector<const void *> g_impls;
+};
+
+namespace {
+
+void plan_free(cj_group_plan_s *p) {
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    for (auto s : p->streams) cudaStreamDestroy(s);
+    for (auto e : p->join) cudaEventDestroy(e);
+    if (p->fork) cudaEventDestroy(p->fork);
+    if (p->d_items) cudaFree(p->d_items);
+    if (p->d_counters) cudaFree(p->d_counters);
+    delete p;
+}
+
+cj_status plan_record(cj_group_plan_s *p, const void *A, void *X, cudaStream_t st) {
+    if (cudaMemsetAsync(p->d_counters, 0, sizeof(int) * p->groups.size(), st) != cudaSuccess ||
+        cudaEventRecord(p->fork, st) != cudaSuccess)
+        return fail(CJ_ERR_CUDA, "grouped plan: memset/event record failed");
+    for (size_t g = 0; g < p->groups.size(); ++g) {
+        cudaStream_t s = p->streams[g % p->streams.size()];
+        if (g < p->streams.size() && cudaStreamWaitEvent(s, p->fork, 0) != cudaSuccess)
+            return fail(CJ_ERR_CUDA, "grouped plan: stream wait failed");
+        const auto &gr = p->groups[g];
+        void *items = p->d_items + 3 * gr.first_item;
+        void *counter = p->d_counters + g;
+        const void *a = A;
+        void *x = X;
+        void *args[4] = {&items, &a, &x, &counter};
+        cj_status rc = cj_launch(gr.h, args, gr.n_items, s);
+        if (rc != CJ_OK) return rc;
+    }
+    for (size_t i = 0; i < p->streams.size() && i < p->groups.size(); ++i) {
+        if (cudaEventRecord(p->join[i], p->streams[i]) != cudaSuccess ||
+            cudaStreamWaitEvent(st, p->join[i], 0) != cudaSuccess)
+            return fail(CJ_ERR_CUDA, "grouped plan: join failed");
+    }
+    return CJ_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+CJ_API cj_status cj_init(const cj_config *cfg, int device) {
+    std::lock_guard<std::mutex> ilk(g_init_mu);
+    if (G.inited) {
+        if (device != G.device) return fail(CJ_ERR_INVALID_ARG, "already initialised for device %d", G.device);
+        return CJ_OK;
+    }
+    cj_config c{};
+    c.compile_threads = 1;
+    c.enable_aot_set = 1;
+    if (cfg) c = *cfg;
+    if (c.compile_threads == 0) c.compile_threads = 1;
+    if (c.compile_threads > 16) return fail(CJ_ERR_INVALID_ARG, "compile_threads must be <= 16");
+    G.cfg = c;
+    G.compile_only = (c.flags & CJ_CFG_COMPILE_ONLY) != 0;
+    G.device = device;
+    if (!G.compile_only) {
+        int ndev = 0;
+        if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+            cudaGetLastError();
+            return fail(CJ_ERR_NO_DEVICE, "no CUDA device or driver");
+        }
+        if (device < 0 || device >= ndev) return fail(CJ_ERR_INVALID_ARG, "device %d out of range", device);
+        int maj = 0, min = 0;
+        cudaSetDevice(device);
+        cudaDeviceGetAttribute(&maj, cudaDevAttrComputeCapabilityMajor, device);
+        cudaDeviceGetAttribute(&min, cudaDevAttrComputeCapabilityMinor, device);
+        if (maj != 10 || min != 3)
+            return fail(CJ_ERR_UNSUPPORTED_ARCH, "device is sm_%d%d; this library targets sm_103a", maj, min);
+        if (cudaFree(nullptr) != cudaSuccess) return fail(CJ_ERR_CUDA, "could not create the device context");
+        if (!load_driver()) return fail(CJ_ERR_NO_DEVICE, "driver entry points unavailable");
+        cudaDeviceGetAttribute(&G.num_sms, cudaDevAttrMultiProcessorCount, device);
+        cudaDeviceGetAttribute(&G.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+        auto prep = [](const void *sym, CUfunction *out) -> bool {
+            cudaFunction_t f = nullptr;
+            if (cudaGetFuncBySymbol(&f, sym) != cudaSuccess) return false;
+            *out = reinterpret_cast<CUfunction>(f);
+            int stat = 0;
+            drv.FuncGetAttribute(&stat, CU_FUNC_ATTRIBUTE_SHARED_SIZE_BYTES, *out);
+            return drv.FuncSetAttribute(*out, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES,
+                                        G.smem_optin - stat) == CUDA_SUCCESS;
+        };
+        const auto &gk = cjint::generic_kernels();
+        for (int d = 0; d < 2; ++d)
+            if (!prep(gk.chain[d], &G.gen_chain[d]) || !prep(gk.ltimes[d], &G.gen_lt[d]) ||
+                !prep(gk.grouped[d], &G.gen_grp[d]))
+                return fail(CJ_ERR_CUDA, "could not load the generic kernels");
+        int na = 0;
+        const cjint::AotKernel *tab = cjint::aot_table(&na);
+        G.aot.clear();
+        for (int i = 0; i < na; ++i) {
+            CUfunction f = nullptr;
+            if (!prep(tab[i].fn, &f)) return fail(CJ_ERR_CUDA, "could not load AoT kernel %d", i);
+            G.aot.push_back({tab[i], f});
+        }
+    } else {
+        int na = 0;
+        const cjint::AotKernel *tab = cjint::aot_table(&na);
+        G.aot.clear();
+        for (int i = 0; i < na; ++i) G.aot.push_back({tab[i], nullptr});
+    }
+    // Warm NVRTC here so that later compiles do no first-use work.
+    CompileOut w = nvrtc_compile("#include \"update_chain.cuh\"\n__global__ void cj_warm() {}\n", nullptr);
+    if (w.rc != NVRTC_SUCCESS) return fail(CJ_ERR_COMPILE, "NVRTC warm-up failed: %s", w.log.c_str());
+    G.stop = false;
+    G.requests = G.hits = G.ok = G.failed = G.aot_hits = 0;
+    G.l_gen = G.l_aot = G.l_jit = 0;
+    {
+        std::lock_guard<std::mutex> lk(G.smu);
+        G.compile_ms.clear();
+        G.lookup_ns.clear();
+        G.lookup_pos = 0;
+    }
+    for (uint32_t i = 0; i < c.compile_threads; ++i) G.workers.emplace_back(worker_loop);
+    G.inited = true;
+    t_err.clear();
+    return CJ_OK;
+}
+
+CJ_API cj_status cj_specialize(cj_kernel_id k, const cj_template_args *req, cj_handle *out) {
+    if (!G.inited) return fail(CJ_ERR_NOT_INITIALIZED, "cj_init has not been called");
+    if (!req || !out) return fail(CJ_ERR_INVALID_ARG, "null argument");
+    const auto t0 = clk::now();
+    cj_template_args a;
+    cj_status rc = validate_and_normalise((int)k, *req, a);
+    if (rc != CJ_OK) return rc;
+    unsigned char key[32];
+    make_key((int)k, a, key);
+    const std::string ks(reinterpret_cast<char *>(key), 32);
+    cj_handle_s *h = nullptr;
+    bool created = false;
+    {
+        std::lock_guard<std::mutex> lk(G.mu);
+        G.requests++;
+        auto it = G.cache.find(ks);
+        if (it != G.cache.end()) {
+            h = it->second;
+            G.hits++;
+        } else {
+            h = new cj_handle_s();
+            h->kernel = (int)k;
+            h->a = a;
+            memcpy(h->key, key, 32);
+            generic_impl(h);
+            h->impl.store(&h->generic, std::memory_order_release);
+            created = true;
+            if (a.flags & CJ_FLAG_GENERIC) {
+                h->state = ST_GENERIC_ONLY;
+            } else {
+                const State::Aot *hit = nullptr;
+                if (G.cfg.enable_aot_set && (int)k == CJ_K_UPDATE_CHAIN && !(a.flags & CJ_FLAG_NO_AOT) &&
+                    !(a.flags & CJ_FLAG_INJECT_COMPILE_ERROR))
+                    hit = find_aot(h);
+                if (hit) {
+                    h->spec.fn = hit->fn;
+                    spec_geometry(h, h->spec);
+                    h->spec.variant = V_AOT;
+                    h->impl.store(&h->spec, std::memory_order_release);
+                    h->state = ST_READY;
+                    G.aot_hits++;
+                } else {
+                    h->name_expr = name_expression(h);
+                    h->state = ST_PENDING;
+                    if (!G.cfg.sync) {
+                        G.queue.push_back(h);
+                        G.qcv.notify_one();
+                    }
+                }
+            }
+            G.cache.emplace(ks, h);
+        }
+    }
+    *out = h;
+    if (!created) {
+        const double ns = std::chrono::duration<double, std::nano>(clk::now() - t0).count();
+        std::lock_guard<std::mutex> lk(G.smu);
+        if (G.lookup_ns.size() < 4096) G.lookup_ns.push_back(ns);
+        else G.lookup_ns[G.lookup_pos++ % 4096] = ns;
+    }
+    if (G.cfg.sync) {
+        if (created && h->state.load() == ST_PENDING) return compile_handle(h);
+        std::unique_lock<std::mutex> lk(h->mu);
+        h->cv.wait(lk, [h] { return h->state.load() != ST_PENDING; });
+        if (h->state.load() == ST_FAILED) return fail(CJ_ERR_COMPILE, "%s", h->error.c_str());
+    }
+    return CJ_OK;
+}
+
+CJ_API cj_status cj_specialize_wait(cj_handle h, int timeout_ms) {
+    if (!G.inited) return fail(CJ_ERR_NOT_INITIALIZED, "cj_init has not been called");
+    if (!h) return fail(CJ_ERR_INVALID_ARG, "null handle");
+    std::unique_lock<std::mutex> lk(h->mu);
+    auto done = [h] { return h->state.load() != ST_PENDING; };
+    if (timeout_ms < 0) h->cv.wait(lk, done);
+    else if (!h->cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), done))
+        return fail(CJ_ERR_TIMEOUT, "instantiation still compiling");
+    if (h->state.load() == ST_FAILED) return fail(CJ_ERR_COMPILE, "%s", h->error.c_str());
+    return CJ_OK;
+}
+
+CJ_API cj_status cj_launch(cj_handle h, void *const *args, int64_t batch, void *cuda_stream) {
+    if (!G.inited) return fail(CJ_ERR_NOT_INITIALIZED, "cj_init has not been called");
+    if (!h || !args || batch < 0) return fail(CJ_ERR_INVALID_ARG, "null handle/args or negative batch");
+    for (int i = 0; i < (h->kernel == CJ_K_LTIMES ? 5 : h->kernel == CJ_K_UPDATE_CHAIN ? 3 : 4); ++i)
+        if (!args[i]) return fail(CJ_ERR_INVALID_ARG, "argument %d is null", i);
+    if (G.compile_only) return fail(CJ_ERR_NO_DEVICE, "library initialised in compile-only mode");
+    const Impl *im = h->impl.load(std::memory_order_acquire);
+    const cj_template_args &a = h->a;
+    CUstream st = reinterpret_cast<CUstream>(cuda_stream);
+    CUresult r = CUDA_SUCCESS;
+    if (h->kernel == CJ_K_UPDATE_CHAIN) {
+        void *A = *reinterpret_cast<void *const *>(args[0]);
+        void *X = *reinterpret_cast<void *const *>(args[1]);
+        int steps = *reinterpret_cast<const int32_t *>(args[2]);
+        if (!A || !X || steps < 1) return fail(CJ_ERR_INVALID_ARG, "null A/X or T < 1");
+        if (batch == 0) return CJ_OK;
+        long long b = batch;
+        double c = 1.0 / ((double)a.n * (double)steps);
+        const unsigned grid = (unsigned)((batch + im->ipb - 1) / im->ipb);
+        if (im->variant == V_GENERIC) {
+            int n = a.n, lay = a.layout_a, ipb = im->ipb;
+            void *p[] = {&A, &X, &b, &steps, &c, &n, &lay, &ipb};
+            r = drv.LaunchKernel(im->fn, grid, 1, 1, im->threads, 1, 1, (unsigned)im->smem, st, p, nullptr);
+        } else {
+            void *p[] = {&A, &X, &b, &steps, &c};
+            r = drv.LaunchKernel(im->fn, grid, 1, 1, im->threads, 1, 1, (unsigned)im->smem, st, p, nullptr);
+        }
+    } else if (h->kernel == CJ_K_LTIMES) {
+        void *L = *reinterpret_cast<void *const *>(args[0]);
+        void *in = *reinterpret_cast<void *const *>(args[1]);
+        void *out = *reinterpret_cast<void *const *>(args[2]);
+        long long Gx = *reinterpret_cast<const int64_t *>(args[3]);
+        long long Zx = *reinterpret_cast<const int64_t *>(args[4]);
+        if (!L || !in || !out || Gx < 0 || Zx < 0) return fail(CJ_ERR_INVALID_ARG, "null tensor or negative G/Z");
+        if (Gx == 0 || Zx == 0) return CJ_OK;
+        if (im->variant == V_GENERIC) {
+            int M = a.m, D = a.d;
+            auto strides = [&](int lay, long long ex, long long *s) {
+                // s[axis] for axis 0 = x, 1 = g, 2 = z
+                const long long e[3] = {ex, Gx, Zx};
+                static const int order[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+                const int *o = order[lay];
+                s[o[2]] = 1;
+                s[o[1]] = e[o[2]];
+                s[o[0]] = e[o[2]] * e[o[1]];
+            };
+            long long si[3], so[3];
+            strides(a.layout_a, D, si);
+            strides(a.layout_b, M, so);
+            const long long cols = Gx * Zx;
+            const unsigned grid = (unsigned)((cols + im->threads - 1) / im->threads);
+            void *p[] = {&L, &in, &out, &Gx, &Zx, &M, &D, &si[0], &si[1], &si[2], &so[0], &so[1], &so[2]};
+            r = drv.LaunchKernel(im->fn, grid, 1, 1, im->threads, 1, 1, (unsigned)im->smem, st, p, nullptr);
+        } else {
+            const long long ntiles = ((Gx + a.tile[0] - 1) / a.tile[0]) * ((Zx + a.tile[1] - 1) / a.tile[1]);
+            const long long cap = (long long)G.num_sms * im->blocks_per_sm;
+            const unsigned grid = (unsigned)std::min(ntiles, cap);
+            void *p[] = {&L, &in, &out, &Gx, &Zx};
+            r = drv.LaunchKernel(im->fn, grid, 1, 1, im->threads, 1, 1, (unsigned)im->smem, st, p, nullptr);
+        }
+    } else {
+        void *items = *reinterpret_cast<void *const *>(args[0]);
+        void *A = *reinterpret_cast<void *const *>(args[1]);
+        void *X = *reinterpret_cast<void *const *>(args[2]);
+        void *counter = *reinterpret_cast<void *const *>(args[3]);
+        if (!items || !A || !X || !counter) return fail(CJ_ERR_INVALID_ARG, "null worklist/pool/counter");
+        if (batch == 0) return CJ_OK;
+        long long ni = batch;
+        const long long chunks = (batch + im->ipb - 1) / im->ipb;
+        const unsigned grid = (unsigned)std::min(chunks, (long long)G.num_sms * im->blocks_per_sm);
+        if (im->variant == V_GENERIC) {
+            int n = a.n, ipb = im->ipb;
+            void *p[] = {&items, &A, &X, &counter, &ni, &n, &ipb};
+            r = drv.LaunchKernel(im->fn, grid, 1, 1, im->threads, 1, 1, (unsigned)im->smem, st, p, nullptr);
+        } else {
+            void *p[] = {&items, &A, &X, &counter, &ni};
+            r = drv.LaunchKernel(im->fn, grid, 1, 1, im->threads, 1, 1, (unsigned)im->smem, st, p, nullptr);
+        }
+    }
+    if (r != CUDA_SUCCESS) return fail(CJ_ERR_CUDA, "launch failed: %s", cu_str(r));
+    (im->variant == V_GENERIC ? G.l_gen : im->variant == V_AOT ? G.l_aot : G.l_jit)++;
+    return CJ_OK;
+}
+
+CJ_API cj_status cj_stats(cj_stats_t *out) {
+    if (!G.inited) return fail(CJ_ERR_NOT_INITIALIZED, "cj_init has not been called");
+    if (!out) return fail(CJ_ERR_INVALID_ARG, "null output");
+    out->requests = G.requests;
+    out->cache_hits = G.hits;
+    out->compiles_ok = G.ok;
+    out->compiles_failed = G.failed;
+    out->aot_hits = G.aot_hits;
+    out->launches_generic = G.l_gen;
+    out->launches_aot = G.l_aot;
+    out->launches_jit = G.l_jit;
+    std::lock_guard<std::mutex> lk(G.smu);
+    out->compile_ms_p50 = percentile(G.compile_ms, 0.5);
+    out->compile_ms_p95 = percentile(G.compile_ms, 0.95);
+    out->lookup_ns_p50 = percentile(G.lookup_ns, 0.5);
+    return CJ_OK;
+}
+
+CJ_API cj_status cj_handle_info(cj_handle h, char *key_hex, size_t cap, int *variant) {
+    if (!h) return fail(CJ_ERR_INVALID_ARG, "null handle");
+    if (key_hex) {
+        if (cap < 65) return fail(CJ_ERR_INVALID_ARG, "key buffer needs 65 bytes");
+        for (int i = 0; i < 32; ++i) snprintf(key_hex + 2 * i, 3, "%02x", h->key[i]);
+    }
+    if (variant) {
+        const Impl *im = h->impl.load(std::memory_order_acquire);
+        if (G.compile_only) {
+            const int s = h->state.load();
+            *variant = h->spec.variant == V_AOT ? V_AOT : (s == ST_READY ? V_JIT : V_GENERIC);
+        } else {
+            *variant = im->variant;
+        }
+    }
+    return CJ_OK;
+}
+
+CJ_API cj_status cj_handle_regs(cj_handle h, int *regs, int *static_smem) {
+    if (!h) return fail(CJ_ERR_INVALID_ARG, "null handle");
+    if (G.compile_only) return fail(CJ_ERR_NO_DEVICE, "compile-only mode");
+    const Impl *im = h->impl.load(std::memory_order_acquire);
+    if (regs && drv.FuncGetAttribute(regs, CU_FUNC_ATTRIBUTE_NUM_REGS, im->fn) != CUDA_SUCCESS)
+        return fail(CJ_ERR_CUDA, "cuFuncGetAttribute failed");
+    if (static_smem && drv.FuncGetAttribute(static_smem, CU_FUNC_ATTRIBUTE_SHARED_SIZE_BYTES, im->fn) != CUDA_SUCCESS)
+        return fail(CJ_ERR_CUDA, "cuFuncGetAttribute failed");
+    return CJ_OK;
+}
+
+CJ_API cj_status cj_group_plan_create(int32_t dtype, int64_t count, const int32_t *n, const int32_t *steps,
+                                      cj_group_plan *out) {
+    if (!G.inited) return fail(CJ_ERR_NOT_INITIALIZED, "cj_init has not been called");
+    if (G.compile_only) return fail(CJ_ERR_NO_DEVICE, "compile-only mode");
+    if (!out || count < 0 || (count > 0 && (!n || !steps)))
+        return fail(CJ_ERR_INVALID_ARG, "null output or inputs");
+    if (dtype != CJ_F64 && dtype != CJ_F32) return fail(CJ_ERR_INVALID_ARG, "grouped plans support f64 and f32");
+    for (int64_t k = 0; k < count; ++k)
+        if (n[k] < 1 || n[k] > 64 || steps[k] < 1) return fail(CJ_ERR_INVALID_ARG, "instance %lld out of range", (long long)k);
+    auto *p = new cj_group_plan_s();
+    p->dtype = dtype;
+    p->count = count;
+    std::vector<int64_t> off(count);
+    int64_t acc = 0;
+    for (int64_t k = 0; k < count; ++k) {
+        off[k] = acc;
+        acc += (int64_t)n[k] * n[k];
+    }
+    p->pool_elems = acc;
+    // group by n; items ordered by T descending (ties by index)
+    std::vector<std::vector<int64_t>> by_n(65);
+    for (int64_t k = 0; k < count; ++k) by_n[n[k]].push_back(k);
+    std::vector<long long> items;
+    for (int nn = 1; nn <= 64; ++nn) {
+        auto &v = by_n[nn];
+        if (v.empty()) continue;
+        std::stable_sort(v.begin(), v.end(), [&](int64_t x, int64_t y) { return steps[x] > steps[y]; });
+        cj_group_plan_s::Group g;
+        g.n = nn;
+        g.first_item = (int64_t)items.size() / 3;
+        g.n_items = (int64_t)v.size();
+        for (int64_t k : v) {
+            items.push_back(off[k]);
+            items.push_back(steps[k]);
+            items.push_back(0);
+            g.cost += (double)steps[k] * nn * nn * nn;
+        }
+        p->groups.push_back(g);
+    }
+    // the most expensive groups are launched first
+    std::stable_sort(p->groups.begin(), p->groups.end(),
+                     [](const cj_group_plan_s::Group &x, const cj_group_plan_s::Group &y) { return x.cost > y.cost; });
+    for (auto &g : p->groups) {
+        cj_template_args a{};
+        a.dtype = dtype;
+        a.n = g.n;
+        cj_status rc = cj_specialize(CJ_K_UPDATE_CHAIN_GROUPED, &a, &g.h);
+        if (rc != CJ_OK && rc != CJ_ERR_COMPILE) {
+            plan_free(p);
+            return rc;
+        }
+    }
+    const size_t ng = std::max<size_t>(1, p->groups.size());
+    if (cudaMalloc(&p->d_counters, sizeof(int) * ng) != cudaSuccess ||
+        (!items.empty() && cudaMalloc(&p->d_items, sizeof(long long) * items.size()) != cudaSuccess)) {
+        plan_free(p);
+        return fail(CJ_ERR_OOM, "grouped plan: device allocation failed");
+    }
+    if (!items.empty() &&
+        cudaMemcpy(p->d_items, items.data(), sizeof(long long) * items.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        plan_free(p);
+        return fail(CJ_ERR_CUDA, "grouped plan: work list upload failed");
+    }
+    const size_t ns = std::min<size_t>(8, ng);
+    p->streams.resize(ns);
+    p->join.resize(ns);
+    for (size_t i = 0; i < ns; ++i) {
+        cudaStreamCreateWithFlags(&p->streams[i], cudaStreamNonBlocking);
+        cudaEventCreateWithFlags(&p->join[i], cudaEventDisableTiming);
+    }
+    cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
+    {
+        std::lock_guard<std::mutex> lk(G.mu);
+        G.plans.push_back(p);
+    }
+    *out = p;
+    return CJ_OK;
+}
+
+CJ_API cj_status cj_group_plan_launch(cj_group_plan p, const void *A_pool, void *X_pool, void *cuda_stream,
+                                      int use_graph) {
+    if (!G.inited) return fail(CJ_ERR_NOT_INITIALIZED, "cj_init has not been called");
+    if (!p || (p->pool_elems > 0 && (!A_pool || !X_pool))) return fail(CJ_ERR_INVALID_ARG, "null plan or pool");
+    if (p->groups.empty()) return CJ_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    if (!use_graph) return plan_record(p, A_pool, X_pool, st);
+    std::vector<const void *> impls;
+    for (auto &g : p->groups) impls.push_back(g.h->impl.load(std::memory_order_acquire));
+    if (!p->exec || p->g_A != A_pool || p->g_X != X_pool || p->g_stream != st || p->g_impls != impls) {
+        if (p->exec) cudaGraphExecDestroy(p->exec);
+        if (p->graph) cudaGraphDestroy(p->graph);
+        p->exec = nullptr;
+        p->graph = nullptr;
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return fail(CJ_ERR_CUDA, "stream capture could not start (legacy default stream cannot be captured)");
+        cj_status rc = plan_record(p, A_pool, X_pool, st);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(st, &g);
+        if (rc != CJ_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess || cudaGraphInstantiate(&p->exec, g, 0) != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return fail(CJ_ERR_CUDA, "graph capture/instantiate failed");
+        }
+        p->graph = g;
+        p->g_A = A_pool;
+        p->g_X = X_pool;
+        p->g_stream = st;
+        p->g_impls = impls;
+    }
+    if (cudaGraphLaunch(p->exec, st) != cudaSuccess) return fail(CJ_ERR_CUDA, "graph launch failed");
+    return CJ_OK;
+}
+
+CJ_API cj_status cj_group_plan_info(cj_group_plan p, int32_t *n_groups, int64_t *pool_elems) {
+    if (!p) return fail(CJ_ERR_INVALID_ARG, "null plan");
+    if (n_groups) *n_groups = (int32_t)p->groups.size();
+    if (pool_elems) *pool_elems = p->pool_elems;
+    return CJ_OK;
+}
+
+CJ_API cj_status cj_group_plan_destroy(cj_group_plan p) {
+    if (!p) return fail(CJ_ERR_INVALID_ARG, "null plan");
+    {
+        std::lock_guard<std::mutex> lk(G.mu);
+        G.plans.erase(std::remove(G.plans.begin(), G.plans.end(), p), G.plans.end());
+    }
+    plan_free(p);
+    return CJ_OK;
+}
+
+CJ_API const char *cj_last_error(void) { return t_err.c_str(); }
+
+CJ_API cj_status cj_shutdown(void) {
+    std::lock_guard<std::mutex> ilk(g_init_mu);
+    if (!G.inited) return CJ_OK;
+    {
+        std::lock_guard<std::mutex> lk(G.mu);
+        G.stop = true;
+    }
+    G.qcv.notify_all();
+    for (auto &t : G.workers) t.join();
+    G.workers.clear();
+    if (!G.compile_only) cudaDeviceSynchronize();
+    for (auto *p : G.plans) plan_free(p);
+    G.plans.clear();
+    for (auto &kv : G.cache) {
+        cj_handle_s *h = kv.second;
+        if (h->lib) drv.LibraryUnload(h->lib);
+        delete h;
+    }
+    G.cache.clear();
+    G.queue.clear();
+    G.inited = false;
+    return CJ_OK;
+}

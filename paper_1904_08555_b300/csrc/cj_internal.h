@@ -11,7 +11,7 @@ enum { D_F64 = 0, D_F32 = 1, D_BF16 = 2 };
 // Default tile rule of the update chain kernels (documented in cj.h).
 constexpr int chain_default_map(int n, int dtype) { return dtype == D_BF16 ? 3 : (n <= 4 ? 2 : 1); }
 constexpr int chain_default_ipb(int n, int dtype) {
-    return dtype == D_BF16 ? 1 : (n <= 4 ? 128 : (256 / n > 1 ? 256 / n : 1));
+    return dtype == D_BF16 ? 1 : n <= 4 ? 128 : n <= 32 ? 256 / n : (128 / n > 1 ? 128 / n : 1);
 }
 
 struct AotKernel {
