@@ -105,11 +105,13 @@ typedef struct {
  *     else {1, max(1, 128 / n)}; bf16 -> {3, 1}.
  *   LTimes: {TG, TZ, threads, (R << 8) | S}: a block stages a TG x TZ box of
  *     (g, z) columns with all d in shared memory; each thread accumulates R
- *     columns x S moments.  Default: columns CT = 64 (f64) or 128 (f32);
+ *     columns x S moments (the last moment group may be partial), so
+ *     threads = (TG * TZ / R) * ceil(m / S).  Default: columns CT = 64 (f64)
+ *     or 128 (f32);
  *     call orders 1 and 4 "g-fast" (g is the fastest axis) and 0 and 2
  *     "z-fast"; TG = 1 if neither in nor out is g-fast, 8 if one is g-fast
  *     and the other z-fast, 32 otherwise; TZ = CT / TG;
- *     f64: threads 256, R 1, S 9; f32: threads 96, R 4, S 12.
+ *     f64: R 1, S 9; f32: R 4, S 12 (m = 36: 256 and 96 threads).
  */
 typedef struct {
     int32_t dtype, n, layout_a, layout_b, m, d;

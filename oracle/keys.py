@@ -30,7 +30,7 @@ Default tile resolution (tile all zero, no cost model):
   LTimes: (TG, TZ, threads, (R << 8) | S) with CT = 64 (f64) or 128 (f32)
       columns; orders 1, 4 are g-fast and 0, 2 z-fast; TG = 1 if neither in
       nor out is g-fast, 8 if one is g-fast and the other z-fast, else 32;
-      TZ = CT / TG; f64: threads 256, R 1, S 9; f32: threads 96, R 4, S 12.
+      TZ = CT / TG; f64: R 1, S 9; f32: R 4, S 12; threads = (CT / R) * ceil(m / S).
 Expected variant: GENERIC flag -> generic; else update chain f64/f32 with
 n in {4, 8, 16, 32}, default tile, AoT set enabled and no NO_AOT flag -> aot;
 else jit.
@@ -59,7 +59,7 @@ G_FAST = (1, 4)
 Z_FAST = (0, 2)
 
 
-def default_tile(kernel: int, dtype: int, n: int, layout_a: int = 0, layout_b: int = 0) -> tuple:
+def default_tile(kernel: int, dtype: int, n: int, layout_a: int = 0, layout_b: int = 0, m: int = 36) -> tuple:
     if kernel in (K_UPDATE_CHAIN, K_UPDATE_CHAIN_GROUPED):
         if dtype == BF16:
             return (3, 1, 0, 0)
@@ -75,9 +75,8 @@ def default_tile(kernel: int, dtype: int, n: int, layout_a: int = 0, layout_b: i
             tg = 8
         else:
             tg = 32
-        if dtype == F64:
-            return (tg, ct // tg, 256, (1 << 8) | 9)
-        return (tg, ct // tg, 96, (4 << 8) | 12)
+        r, s = (1, 9) if dtype == F64 else (4, 12)
+        return (tg, ct // tg, (ct // r) * (-(-m // s)), (r << 8) | s)
     raise ValueError("unknown kernel")
 
 
@@ -93,7 +92,7 @@ def canonical_key(kernel: int, dtype: int, n=0, layout_a=0, layout_b=0, m=0, d=0
     if flags & FLAG_GENERIC:
         tile = (0, 0, 0, 0)            # the generic kernel has no tile template
     elif all(t == 0 for t in tile):
-        tile = default_tile(kernel, dtype, n, layout_a, layout_b)
+        tile = default_tile(kernel, dtype, n, layout_a, layout_b, m)
     return struct.pack("<HBBBBHHH4II", kernel, dtype, layout_a, layout_b, 0, n, m, d,
                        *tile, flags & KEY_FLAGS)
 

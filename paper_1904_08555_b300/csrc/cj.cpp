@@ -205,13 +205,10 @@ void default_tile(int k, cj_template_args &a) {
     else tg = 32;
     a.tile[0] = tg;
     a.tile[1] = ct / tg;
-    if (a.dtype == CJ_F64) {
-        a.tile[2] = 256;
-        a.tile[3] = (1 << 8) | 9;
-    } else {
-        a.tile[2] = 96;
-        a.tile[3] = (4 << 8) | 12;
-    }
+    // f64: R 1, S 9; f32: R 4, S 12; threads = (CT / R) * ceil(m / S)
+    const int r = a.dtype == CJ_F64 ? 1 : 4, s = a.dtype == CJ_F64 ? 9 : 12;
+    a.tile[2] = (ct / r) * ((a.m + s - 1) / s);
+    a.tile[3] = (r << 8) | s;
 }
 
 cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_args &a) {
@@ -252,11 +249,11 @@ cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_
             return fail(CJ_ERR_INVALID_ARG, "tile needs too much shared memory");
     } else {
         const int tg = a.tile[0], tz = a.tile[1], nt = a.tile[2], r = a.tile[3] >> 8, s = a.tile[3] & 0xff;
-        if (tg < 1 || tz < 1 || r < 1 || s < 1 || nt < 32 || nt > 1024 || (tg * tz) % r || a.m % s ||
-            (tg * tz / r) * (a.m / s) != nt)
+        if (tg < 1 || tz < 1 || r < 1 || s < 1 || nt < 32 || nt > 1024 || (tg * tz) % r ||
+            (tg * tz / r) * ((a.m + s - 1) / s) != nt)
             return fail(CJ_ERR_INVALID_ARG, "LTimes tile {%d,%d,%d,%d} does not cover its block", a.tile[0],
                         a.tile[1], a.tile[2], a.tile[3]);
-        if (cjg::lt_smem(a.m, a.d, tg * tz, esize(a.dtype)) > 220 * 1024)
+        if (cjg::lt_smem(a.m, s, a.d, tg * tz, esize(a.dtype)) > 220 * 1024)
             return fail(CJ_ERR_INVALID_ARG, "LTimes tile needs too much shared memory");
     }
     return CJ_OK;
@@ -310,7 +307,7 @@ void spec_geometry(const cj_handle_s *h, Impl &s) {
     const int es = esize(a.dtype);
     if (h->kernel == CJ_K_LTIMES) {
         s.threads = a.tile[2];
-        s.smem = (size_t)cjg::lt_smem(a.m, a.d, a.tile[0] * a.tile[1], es);
+        s.smem = (size_t)cjg::lt_smem(a.m, a.tile[3] & 0xff, a.d, a.tile[0] * a.tile[1], es);
     } else {
         s.ipb = a.tile[1];
         s.threads = cjg::chain_threads(a.n, a.tile[0], a.tile[1]);

@@ -52,12 +52,14 @@ CJ_HD constexpr long chain_generic_smem(int n, int ipb, int threads, int esize) 
     return (long)ipb * row_pitch(n * n, esize) * esize + 2L * threads * xrow_pitch(n) * esize;
 }
 
-// LTimes: L is kept transposed, [d][m] with m padded to a 16-byte multiple.
-CJ_HD constexpr int lt_mpitch(int m, int esize) { return ((m * esize + 15) / 16) * 16 / esize; }
+// LTimes: L is kept transposed, [d][m] with m padded to whole moment groups
+// of S and to a 16-byte multiple.
+CJ_HD constexpr int lt_mpitch(int mpad, int esize) { return ((mpad * esize + 15) / 16) * 16 / esize; }
 // Column tile pitch: CT plus 16 bytes.
 CJ_HD constexpr int lt_cpitch(int ct, int esize) { return ct + 16 / esize; }
-CJ_HD constexpr long lt_smem(int m, int d, int ct, int esize) {
-    return ((long)d * lt_mpitch(m, esize) + (long)(m > d ? m : d) * lt_cpitch(ct, esize)) * esize;
+CJ_HD constexpr long lt_smem(int m, int s, int d, int ct, int esize) {
+    return ((long)d * lt_mpitch((m + s - 1) / s * s, esize) + (long)(m > d ? m : d) * lt_cpitch(ct, esize)) *
+           esize;
 }
 CJ_HD constexpr long lt_generic_smem(int m, int d, int cols, int esize) {
     return ((long)m * d + (long)d * cols) * esize;

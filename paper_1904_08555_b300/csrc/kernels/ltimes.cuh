@@ -74,17 +74,18 @@ template <class T, int M, int D, int LIN, int LOUT, int TG, int TZ, int NT, int 
 __global__ void __launch_bounds__(NT)
 ltimes(const T* __restrict__ L, const T* __restrict__ in, T* __restrict__ out, long long G, long long Z) {
     constexpr int CT = TG * TZ;
-    constexpr int MP = cjg::lt_mpitch(M, (int)sizeof(T));
+    constexpr int MG = (M + S - 1) / S;   // moment groups (the last may be partial)
+    constexpr int MP = cjg::lt_mpitch(MG * S, (int)sizeof(T));
     constexpr int CP = cjg::lt_cpitch(CT, (int)sizeof(T));
     constexpr int QG = CT / R;   // column groups
-    static_assert(CT % R == 0 && M % S == 0 && QG * (M / S) == NT, "tile does not cover the block");
+    static_assert(CT % R == 0 && QG * MG == NT, "tile does not cover the block");
     extern __shared__ __align__(16) unsigned char cj_smem[];
     T* sL = reinterpret_cast<T*>(cj_smem);   // [D][MP], L transposed
     T* sX = sL + D * MP;                      // [D][CP] in tile, then [M][CP] out tile
     const int tid = threadIdx.x;
-    for (int e = tid; e < M * D; e += NT) {
+    for (int e = tid; e < MP * D; e += NT) {
         const int m = e / D, d = e - m * D;
-        sL[d * MP + m] = L[e];
+        sL[d * MP + m] = m < M ? L[e] : T(0);
     }
     const long long ntg = (G + TG - 1) / TG, ntz = (Z + TZ - 1) / TZ;
     const long long ntiles = ntg * ntz;
@@ -115,8 +116,9 @@ ltimes(const T* __restrict__ L, const T* __restrict__ in, T* __restrict__ out, l
         __syncthreads();
 #pragma unroll
         for (int s = 0; s < S; ++s)
+            if (M % S == 0 || m0 + s < M)
 #pragma unroll
-            for (int r = 0; r < R; ++r) sX[(m0 + s) * CP + q0 + r] = acc[r][s];
+                for (int r = 0; r < R; ++r) sX[(m0 + s) * CP + q0 + r] = acc[r][s];
         __syncthreads();
         lt_box<T, LOUT, M, TG, TZ, CP, NT, false>(out, sX, G, Z, g0, z0, tid);
     }

@@ -28,7 +28,7 @@ REQUESTS = [
     (K.K_LTIMES, K.F64, 7, 3, 5, 36, 96, (0, 0, 0, 0), 0),               # n ignored
     (K.K_LTIMES, K.F32, 0, 5, 1, 36, 96, (0, 0, 0, 0), 0),
     (K.K_LTIMES, K.F64, 0, 2, 4, 36, 96, (0, 0, 0, 0), K.FLAG_GENERIC),
-    (K.K_LTIMES, K.F32, 0, 1, 1, 36, 96, (32, 4, 128, (2 << 8) | 12), 0),
+    (K.K_LTIMES, K.F32, 0, 1, 1, 36, 96, (32, 4, 192, (2 << 8) | 12), 0),
     (K.K_UPDATE_CHAIN_GROUPED, K.F64, 20, 0, 0, 0, 0, (0, 0, 0, 0), 0),
     (K.K_UPDATE_CHAIN_GROUPED, K.F32, 3, 1, 0, 0, 0, (0, 0, 0, 0), 0),  # layout forced 0
     (K.K_UPDATE_CHAIN, K.F64, 8, 0, 0, 0, 0, (0, 0, 0, 0), K.FLAG_INJECT_COMPILE_ERROR),

@@ -1,0 +1,196 @@
+"""C-ABI checks that need no GPU: exports, keys, dispatch, errors, the
+background compile thread and the no-file-system rule (Sec. 1, Sec. 4).
+
+libcj is initialised in compile-only mode: NVRTC compiles to sm_103a CUBIN
+on the host, nothing is loaded or launched."""
+import os
+import re
+import subprocess
+import sys
+import textwrap
+
+import pytest
+
+from conftest import ROOT
+from paper_1904_08555_b300 import cj
+
+
+def header_functions():
+    with open(os.path.join(ROOT, "include", "cj.h")) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^(?:cj_status|const char \*)\s*(cj_\w+)\(", text, re.M)))
+
+
+def exported_symbols():
+    out = subprocess.run(["nm", "-D", "--defined-only", cj.lib_path()], capture_output=True, text=True).stdout
+    return sorted(l.split()[-1] for l in out.splitlines() if l.split()[-1].startswith("cj_"))
+
+
+def test_library_exports_exactly_the_header():
+    cj.load()
+    assert header_functions() == exported_symbols()
+    assert set(header_functions()) == set(cj.EXPORTS)
+
+
+@pytest.fixture
+def compile_only_sync():
+    cj.init(compile_only=True, sync=True)
+    yield
+    cj.shutdown()
+
+
+def golden_requests():
+    rows = []
+    with open(os.path.join(ROOT, "tests", "golden", "keys.txt")) as f:
+        for line in f:
+            if line.startswith("#"):
+                continue
+            v = line.split()
+            rows.append(([int(x) for x in v[:12]], v[12], int(v[13])))
+    return rows
+
+
+def test_golden_keys_and_dispatch(compile_only_sync):
+    for (k, dt, n, la, lb, m, d, t0, t1, t2, t3, fl), key, var in golden_requests():
+        if dt == cj.BF16:
+            continue   # the bf16 kernel has its own tests
+        h = cj.specialize(k, dt, n, la, lb, m, d, (t0, t1, t2, t3), fl, allow_compile_error=True)
+        got_key, got_var = h.info()
+        assert got_key == key, (k, dt, n, la, lb, fl)
+        expect = var
+        if fl & cj.FLAG_INJECT_COMPILE_ERROR:
+            expect = 0      # failed compiles keep the generic kernel
+        assert got_var == expect, (k, dt, n, la, lb, fl)
+
+
+def test_cache_returns_same_handle(compile_only_sync):
+    a = cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=5)
+    b = cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=5)
+    c = cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=5, m=7, d=3)     # unused fields ignored
+    assert a == b == c
+    s = cj.stats()
+    assert s["requests"] == 3 and s["cache_hits"] == 2 and s["compiles_ok"] == 1
+
+
+def test_aot_sizes_are_not_compiled(compile_only_sync):
+    for n in (4, 8, 16, 32):
+        for dt in (cj.F64, cj.F32):
+            assert cj.specialize(cj.K_UPDATE_CHAIN, dt, n=n).variant == "aot"
+    s = cj.stats()
+    assert s["compiles_ok"] == 0 and s["aot_hits"] == 8
+
+
+@pytest.mark.parametrize("kw", [
+    dict(kernel=cj.K_UPDATE_CHAIN, dtype=cj.F64, n=0),
+    dict(kernel=cj.K_UPDATE_CHAIN, dtype=cj.F64, n=65),
+    dict(kernel=cj.K_UPDATE_CHAIN, dtype=cj.F64, n=4, layout_a=2),
+    dict(kernel=cj.K_UPDATE_CHAIN, dtype=5, n=4),
+    dict(kernel=cj.K_UPDATE_CHAIN, dtype=cj.F64, n=12, tile=(2, 64, 0, 0)),
+    dict(kernel=cj.K_UPDATE_CHAIN, dtype=cj.F64, n=8, flags=0x40),
+    dict(kernel=cj.K_LTIMES, dtype=cj.F64, layout_a=6, m=36, d=96),
+    dict(kernel=cj.K_LTIMES, dtype=cj.F64, m=0, d=96),
+    dict(kernel=cj.K_LTIMES, dtype=cj.F32, m=36, d=96, tile=(1, 128, 97, (4 << 8) | 12)),
+    dict(kernel=cj.K_LTIMES, dtype=cj.BF16, m=36, d=96),
+    dict(kernel=9, dtype=cj.F64, n=4),
+])
+def test_invalid_arguments(compile_only_sync, kw):
+    with pytest.raises(cj.CJError) as e:
+        cj.specialize(**kw)
+    assert e.value.status == cj.CJ_ERR_INVALID_ARG
+    assert cj.last_error()
+
+
+def test_not_initialised_and_launch_without_device():
+    with pytest.raises(cj.CJError) as e:
+        cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=4)
+    assert e.value.status == cj.CJ_ERR_NOT_INITIALIZED
+    cj.init(compile_only=True, sync=True)
+    try:
+        h = cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=4)
+        with pytest.raises(cj.CJError) as e:
+            cj.launch_update_chain(h, 1 << 20, 2 << 20, 10, batch=4)
+        assert e.value.status == cj.CJ_ERR_NO_DEVICE
+        with pytest.raises(cj.CJError) as e:
+            cj.launch_update_chain(h, 1 << 20, 2 << 20, 10, batch=-1)
+        assert e.value.status == cj.CJ_ERR_INVALID_ARG
+    finally:
+        cj.shutdown()
+
+
+def test_compile_failure_reports_log_and_keeps_generic(compile_only_sync):
+    with pytest.raises(cj.CJError) as e:
+        cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=6, flags=cj.FLAG_INJECT_COMPILE_ERROR)
+    assert e.value.status == cj.CJ_ERR_COMPILE
+    assert "this_identifier_does_not_exist" in cj.last_error()
+    h = cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=6, flags=cj.FLAG_INJECT_COMPILE_ERROR,
+                      allow_compile_error=True)
+    assert h.variant == "generic"
+    assert cj.stats()["compiles_failed"] == 1
+
+
+def test_async_compile_and_wait():
+    cj.init(compile_only=True, sync=False, compile_threads=2)
+    try:
+        hs = [cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=n) for n in (5, 6, 7)]
+        assert hs[0].wait(0) in (cj.CJ_ERR_TIMEOUT, cj.CJ_OK)
+        for h in hs:
+            assert h.wait(-1) == cj.CJ_OK
+            assert h.variant == "jit"
+        bad = cj.specialize(cj.K_LTIMES, cj.F64, m=4, d=4, flags=cj.FLAG_INJECT_COMPILE_ERROR)
+        assert bad.wait(-1) == cj.CJ_ERR_COMPILE
+        assert bad.variant == "generic"
+        s = cj.stats()
+        assert s["compiles_ok"] == 3 and s["compiles_failed"] == 1
+        assert s["compile_ms_p50"] > 0
+    finally:
+        cj.shutdown()
+
+
+NOFS_PROG = """
+import ctypes, sys
+sys.path.insert(0, {root!r})
+from paper_1904_08555_b300 import cj
+shim = ctypes.CDLL(None)
+shim.shim_log.restype = ctypes.c_char_p
+cj.init(compile_only=True, sync=True)
+shim.shim_arm(1)
+h1 = cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=11)
+h2 = cj.specialize(cj.K_LTIMES, cj.F32, layout_a=3, layout_b=1, m=36, d=96)
+h3 = cj.specialize(cj.K_UPDATE_CHAIN_GROUPED, cj.F32, n=20)
+shim.shim_arm(0)
+print("COUNT", shim.shim_count())
+print("LOG", shim.shim_log().decode().replace(chr(10), ";"))
+print("VARIANTS", h1.variant, h2.variant, h3.variant)
+"""
+
+
+def _run_nofs(tmp_path, unset_pwd):
+    shim = tmp_path / "nofs_shim.so"
+    subprocess.run(["gcc", "-shared", "-fPIC", "-O1", "-o", str(shim),
+                    os.path.join(ROOT, "tests", "support", "nofs_shim.c"), "-ldl"], check=True)
+    env = dict(os.environ, LD_PRELOAD=str(shim))
+    if unset_pwd:
+        env.pop("PWD", None)
+    else:
+        env["PWD"] = os.getcwd()
+    r = subprocess.run([sys.executable, "-c", NOFS_PROG.format(root=ROOT)], capture_output=True, text=True,
+                       env=env, timeout=300, cwd=os.getcwd())
+    assert r.returncode == 0, r.stderr
+    out = dict(l.split(" ", 1) for l in r.stdout.splitlines() if l.split(" ", 1)[0] in ("COUNT", "LOG", "VARIANTS"))
+    assert out["VARIANTS"] == "jit jit jit"
+    calls = [c for c in out.get("LOG", "").split(";") if c]
+    return int(out["COUNT"]), calls
+
+
+def test_no_file_system_access_during_compiles(tmp_path):
+    """Three JIT compiles after cj_init open, read, stat or dlopen nothing."""
+    count, calls = _run_nofs(tmp_path, unset_pwd=True)
+    assert count == 0, calls
+
+
+def test_compiles_open_no_file_when_pwd_is_set(tmp_path):
+    """With $PWD set, NVRTC's current-directory query stats $PWD and "."
+    (two metadata calls per compile); no file is opened or read."""
+    count, calls = _run_nofs(tmp_path, unset_pwd=False)
+    assert all(c.split()[0] in ("stat", "lstat") for c in calls), calls
+    assert {c.split(" ", 1)[1] for c in calls} <= {".", os.getcwd()}, calls
