@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Benchmark of the runtime-specialized update chain (FP64 size sweep).
+
+One step = for each N in {3, 4, 5, 7, 8, 12, 16, 24, 32}: cj_specialize
+(a cache hit: the lookup is part of the path) and cj_launch of the JIT
+instantiation over batch = floor(2^27 / N^2) instances with T = 64.
+Prints one JSON line (see the repository's bench contract); `value` is the
+whole-job FP64 GFLOP/s of the specialized kernels, `generic` the same for the
+generic runtime-N kernel, `aot` for the ahead-of-time set {4, 8, 16, 32}.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cj|reference]
+
+--impl reference times the CPU oracle (the plain FP64 C loops) on this
+host's cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "specialized vs generic GFLOP/s and % roofline at stated error; JIT compile ms p50"
+SWEEP_N = (3, 4, 5, 7, 8, 12, 16, 24, 32)
+AOT_N = (4, 8, 16, 32)
+T_STEPS = 64
+WORKLOAD = ("update chain X_{k+1} = X_k + X_k A/(N T), FP64 size sweep N in {3,4,5,7,8,12,16,24,32}, "
+            "T = 64, batch = floor(2^27/N^2) per N, row-major, entries U[-1,1) (SplitMix64 seed 0xC1A2)")
+
+
+def chain_flops(batch: int, n: int, steps: int) -> float:
+    return float(batch) * steps * (2.0 * n ** 3 + 2.0 * n ** 2)
+
+
+def chain_bytes(batch: int, n: int, esize: int) -> float:
+    return float(batch) * 2 * n * n * esize
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.device)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, v in zip(self.NAMES, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (barrier + max over ranks only; no data-path collective)
+# ---------------------------------------------------------------------------
+def dist_setup(n_gpus: int):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v: float) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def oracle_sample_sizes(budget_flops: float) -> dict:
+    per_n = budget_flops / len(SWEEP_N)
+    return {n: max(8, int(per_n / chain_flops(1, n, T_STEPS))) for n in SWEEP_N}
+
+
+def calibrated_sizes(seconds: float) -> dict:
+    """Sample sizes for about `seconds` of oracle time on this host's cores."""
+    sizes = oracle_sample_sizes(2e8 * (os.cpu_count() or 1))
+    f, s, _, _ = run_oracle_sweep(sizes)
+    return oracle_sample_sizes(f / s * seconds)
+
+
+def run_oracle_sweep(sizes: dict, rank_offset: int = 0):
+    """Oracle on the first sizes[n] instances of each size; returns (flops, seconds, outputs)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    flops, secs, outs = 0.0, 0.0, {}
+    for n in SWEEP_N:
+        A = synth.uniform_np(synth.SEED_CHAIN_SWEEP, synth.STREAM_A + rank_offset * synth.chain_batch(n) * n * n,
+                             sizes[n] * n * n).reshape(sizes[n], n, n)
+        t0 = time.perf_counter()
+        X = oracle.update_chain(A, T_STEPS, nthreads=cores)
+        secs += time.perf_counter() - t0
+        flops += chain_flops(sizes[n], n, T_STEPS)
+        outs[n] = X
+    return flops, secs, outs, cores
+
+
+def reference_arm(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sizes = calibrated_sizes(args.cpu_seconds / (args.steps + args.warmup))
+    for _ in range(args.warmup):
+        run_oracle_sweep(sizes)
+    tot_f, tot_s = 0.0, 0.0
+    for _ in range(args.steps):
+        f, s, _, cores = run_oracle_sweep(sizes)
+        tot_f += f
+        tot_s += s
+    value = tot_f / tot_s / 1e9
+    sample = (f"per step: the first {sizes[3]} (N=3) .. {sizes[32]} (N=32) instances of each of the "
+              f"{len(SWEEP_N)} sizes, {tot_f / args.steps / 1e9:.1f} GFLOP")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def cj_arm(args):
+    import torch
+    from paper_1904_08555_b300 import cj
+
+    world, rank, local = dist_setup(args.gpus)
+    dev = torch.cuda.current_device()
+    cj.init(sync=True, compile_threads=4, device=dev)
+    stream = torch.cuda.Stream()
+
+    # inputs: rank r holds instances [r*batch, (r+1)*batch) of each size
+    A, X, batch = {}, {}, {}
+    with torch.cuda.stream(stream):
+        for n in SWEEP_N:
+            b = synth.chain_batch(n)
+            batch[n] = b
+            A[n] = synth.uniform_torch(synth.SEED_CHAIN_SWEEP, synth.STREAM_A + rank * b * n * n, b * n * n,
+                                       "cuda").view(b, n, n)
+            X[n] = torch.empty_like(A[n])
+    stream.synchronize()
+
+    t0 = time.perf_counter()
+    spec = {n: cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=n, flags=cj.FLAG_NO_AOT) for n in SWEEP_N}
+    compile_wall = time.perf_counter() - t0
+    st = cj.stats()
+    gen = {n: cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=n, flags=cj.FLAG_GENERIC) for n in SWEEP_N}
+    aot = {n: cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=n) for n in AOT_N}
+    assert all(h.variant == "jit" for h in spec.values())
+    assert all(h.variant == "aot" for h in aot.values())
+
+    step_flops = sum(chain_flops(batch[n], n, T_STEPS) for n in SWEEP_N)
+
+    def run(kind, sizes, events=None):
+        for n in sizes:
+            if kind == "spec":
+                h = cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=n, flags=cj.FLAG_NO_AOT)
+            elif kind == "aot":
+                h = cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=n)
+            else:
+                h = cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=n, flags=cj.FLAG_GENERIC)
+            if events is not None:
+                events[n][0].record(stream)
+            cj.launch_update_chain(h, A[n], X[n], T_STEPS, stream=stream)
+            if events is not None:
+                events[n][1].record(stream)
+
+    def timed(kind, sizes, steps, warmup, clocks=None):
+        for _ in range(warmup):
+            run(kind, sizes)
+        stream.synchronize()
+        per = {n: [] for n in sizes}
+        barrier(world)
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        evs = []
+        e0.record(stream)
+        for _ in range(steps):
+            ev = {n: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for n in sizes}
+            run(kind, sizes, ev)
+            evs.append(ev)
+        e1.record(stream)
+        e1.synchronize()
+        torch.cuda.synchronize()
+        clk = clocks.stop() if clocks else None
+        barrier(world)
+        ms = e0.elapsed_time(e1)
+        for ev in evs:
+            for n in sizes:
+                per[n].append(ev[n][0].elapsed_time(ev[n][1]))
+        ms = max_over_ranks(world, ms)
+        return ms, {n: statistics.mean(v) for n, v in per.items()}, clk
+
+    sampler = ClockSampler(dev)
+    ms_spec, per_spec, clocks = timed("spec", SWEEP_N, args.steps, args.warmup, sampler)
+    ms_gen, per_gen, _ = timed("generic", SWEEP_N, args.steps, 1)
+    ms_aot, per_aot, _ = timed("aot", AOT_N, args.steps, 1)
+
+    value = world * step_flops * args.steps / (ms_spec * 1e-3) / 1e9
+    gen_value = world * step_flops * args.steps / (ms_gen * 1e-3) / 1e9
+    peak64 = cj.measure_fma_peak(cj.F64, stream.cuda_stream)
+    per_n = []
+    for n in SWEEP_N:
+        f = chain_flops(batch[n], n, T_STEPS)
+        row = {"N": n, "batch": batch[n], "spec_ms": per_spec[n], "generic_ms": per_gen[n],
+               "spec_gflops": f / per_spec[n] / 1e6, "generic_gflops": f / per_gen[n] / 1e6,
+               "speedup_vs_generic": per_gen[n] / per_spec[n],
+               "spec_frac_of_fp64_peak": f / per_spec[n] / 1e9 / peak64,
+               "spec_regs": spec[n].regs()[0], "generic_regs": gen[n].regs()[0]}
+        if n in AOT_N:
+            row["aot_ms"] = per_aot[n]
+            row["aot_gflops"] = f / per_aot[n] / 1e6
+        per_n.append(row)
+    dom = max(SWEEP_N, key=lambda n: per_spec[n])
+    achieved = chain_flops(batch[dom], dom, T_STEPS) / (per_spec[dom] * 1e-3) / 1e12
+
+    # end to end through the C ABI with host buffers: H2D of A, launch, D2H of X, every size
+    h2d = sum(chain_bytes(batch[n], n, 8) / 2 for n in SWEEP_N)
+    host_A = {n: A[n].cpu().pin_memory() for n in SWEEP_N}
+    host_X = {n: torch.empty(A[n].shape, dtype=torch.float64).pin_memory() for n in SWEEP_N}
+
+    def e2e_step():
+        for n in SWEEP_N:
+            A[n].copy_(host_A[n], non_blocking=True)
+            h = cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=n, flags=cj.FLAG_NO_AOT)
+            cj.launch_update_chain(h, A[n], X[n], T_STEPS, stream=stream)
+            host_X[n].copy_(X[n], non_blocking=True)
+
+    with torch.cuda.stream(stream):
+        e2e_step()
+        stream.synchronize()
+        barrier(world)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        e1.synchronize()
+    ms_e2e = max_over_ranks(world, e0.elapsed_time(e1))
+    e2e_value = world * step_flops * args.steps / (ms_e2e * 1e-3) / 1e9
+
+    st = cj.stats()
+    line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_spec / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "inputs larger than L2 (1.07 GB of A per size)",
+                       "instances_per_step_per_gpu": sum(batch.values())},
+            "generic": {"value": gen_value, "unit": "GFLOP/s", "ms_per_step": ms_gen / args.steps},
+            "speedup_vs_generic": value / gen_value,
+            "jit_compile_ms_p50": st["compile_ms_p50"], "jit_compile_ms_p95": st["compile_ms_p95"],
+            "lookup_ns_p50": st["lookup_ns_p50"], "compile_wall_s_9_sizes": compile_wall,
+            "fp64_fma_peak_tflops_measured": peak64,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
+                         "frac": achieved / peak64, "traffic": None,
+                         "kernel": f"update_chain<double,{dom},...> (N = {dom})",
+                         "peak_source": "measured FP64 FMA throughput (cj_measure_fma_peak)"},
+            "per_n": per_n,
+            "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(h2d)},
+            "gpu_launches": args.steps * len(SWEEP_N),
+            "clocks": clocks}
+
+    if rank == 0 and not args.no_cpu_baseline:
+        sizes = calibrated_sizes(args.cpu_seconds / 4)
+        f, s, outs, cores = run_oracle_sweep(sizes, rank_offset=0)
+        worst = 0.0
+        for n in SWEEP_N:
+            got = X[n][: sizes[n]].cpu().numpy()
+            ref = outs[n]
+            err = np.linalg.norm((got - ref).reshape(len(ref), -1), axis=1) / np.linalg.norm(ref.reshape(len(ref), -1), axis=1)
+            worst = max(worst, float(err.max()))
+        line["cpu_baseline"] = {"value": f / s / 1e9, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                                "sample": f"first {sizes[3]} (N=3) .. {sizes[32]} (N=32) instances of each size, "
+                                          f"{f / 1e9:.1f} GFLOP, {s:.1f} s"}
+        line["max_rel_frobenius_error_vs_oracle"] = worst
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    cj.shutdown()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=("cj", "reference"), default="cj")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=60.0,
+                   help="oracle time budget: reference arm whole run; cpu_baseline leg uses a quarter")
+    args = p.parse_args()
+    if args.warmup < 3:
+        p.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        cj_arm(args)
+
+
+if __name__ == "__main__":
+    main()

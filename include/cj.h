@@ -195,14 +195,21 @@ cj_status cj_group_plan_create(int32_t dtype, int64_t count, const int32_t *n, c
                                cj_group_plan *out);
 /* Launch every group on `cuda_stream`: groups run concurrently on forked
  * streams joined back into cuda_stream.  use_graph = 1: the first call
- * captures the whole launch into a CUDA graph and later calls replay it
- * (re-captured when a group's instantiation changed, e.g. from generic to
- * JIT).  Pools are caller-owned device memory. */
+ * captures the whole launch (counter reset included) into a CUDA graph on a
+ * stream of the plan's own and launches it on cuda_stream; later calls
+ * replay it (re-captured when the pools or a group's instantiation changed,
+ * e.g. from generic to JIT).  Pools are caller-owned device memory. */
 cj_status cj_group_plan_launch(cj_group_plan p, const void *A_pool, void *X_pool, void *cuda_stream,
                                int use_graph);
 /* Groups in the plan and pool elements it expects. */
 cj_status cj_group_plan_info(cj_group_plan p, int32_t *n_groups, int64_t *pool_elems);
 cj_status cj_group_plan_destroy(cj_group_plan p);
+
+/* Measured FMA throughput of this GPU in TFLOP/s (2 flops per FMA) for
+ * dtype CJ_F64 or CJ_F32: a kernel of independent fused multiply-add chains
+ * over every SM, timed with CUDA events on cuda_stream.  Used as the
+ * roofline denominator of the FP64/FP32 arithmetic-bound kernels. */
+cj_status cj_measure_fma_peak(int32_t dtype, void *cuda_stream, double *tflops);
 
 /* Thread-local description of the last error on this thread ("" if none). */
 const char *cj_last_error(void);

@@ -23,7 +23,7 @@ VARIANT_NAMES = ("generic", "aot", "jit")
 
 EXPORTS = ("cj_init", "cj_specialize", "cj_specialize_wait", "cj_launch", "cj_stats", "cj_handle_info",
            "cj_handle_regs", "cj_group_plan_create", "cj_group_plan_launch", "cj_group_plan_info",
-           "cj_group_plan_destroy", "cj_last_error", "cj_shutdown")
+           "cj_group_plan_destroy", "cj_measure_fma_peak", "cj_last_error", "cj_shutdown")
 
 
 class CJError(RuntimeError):
@@ -75,6 +75,7 @@ def load():
         L.cj_group_plan_launch.argtypes = [P, P, P, P, ctypes.c_int]
         L.cj_group_plan_info.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i64)]
         L.cj_group_plan_destroy.argtypes = [P]
+        L.cj_measure_fma_peak.argtypes = [i32, P, ctypes.POINTER(ctypes.c_double)]
         L.cj_last_error.restype = ctypes.c_char_p
         L.cj_shutdown.argtypes = []
         for name in EXPORTS:
@@ -193,6 +194,13 @@ def launch_grouped(h: Handle, items, A_pool, X_pool, counter, n_items: int, stre
     vals = [ctypes.c_void_p(_ptr(items)), ctypes.c_void_p(_ptr(A_pool)), ctypes.c_void_p(_ptr(X_pool)),
             ctypes.c_void_p(_ptr(counter))]
     _launch(h, vals, n_items, _stream(stream, A_pool, X_pool))
+
+
+def measure_fma_peak(dtype: int, stream=None) -> float:
+    """Measured FMA throughput (TFLOP/s) for F64 or F32 on the current device."""
+    out = ctypes.c_double(0.0)
+    _check(load().cj_measure_fma_peak(dtype, _stream(stream), ctypes.byref(out)), "cj_measure_fma_peak")
+    return out.value
 
 
 def stats() -> dict:

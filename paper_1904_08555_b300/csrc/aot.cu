@@ -28,7 +28,30 @@ static const GenericKernels kGeneric = {
      (const void *)&cj::update_chain_grouped_generic<float>},
 };
 
+// Roofline denominator: 8 independent FMA chains per thread and nothing else
+// in the loop.  The store is never taken (the chains converge near
+// b / (1 - a)), it only keeps the arithmetic alive.
+__device__ double cj_peak_sink;
+
+template <class T>
+__global__ void __launch_bounds__(256) peak_fma(int iters, T a, T b) {
+    T acc[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i] = (T)(threadIdx.x + i) * (T)1e-3;
+    for (int k = 0; k < iters; ++k) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[i] = cj::fmaT(acc[i], a, b);
+    }
+    T s = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += acc[i];
+    if (s == (T)-123456.0) cj_peak_sink = (double)s;
+}
+
 namespace cjint {
+const void *peak_fma_kernel(int dtype) {
+    return dtype == D_F64 ? (const void *)&peak_fma<double> : (const void *)&peak_fma<float>;
+}
 const AotKernel *aot_table(int *count) {
     *count = (int)(sizeof(kAotTable) / sizeof(kAotTable[0]));
     return kAotTable;

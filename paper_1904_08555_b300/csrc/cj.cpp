@@ -487,11 +487,11 @@ struct cj_group_plan_s {
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> join;
     cudaEvent_t fork = nullptr;
+    cudaStream_t capture = nullptr;   // graphs are captured here, then launched on the caller's stream
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     const void *g_A = nullptr;
     void *g_X = nullptr;
-    cudaStream_t g_stream = nullptr;
     std::vector<const void *> g_impls;
 };
 
@@ -503,6 +503,7 @@ void plan_free(cj_group_plan_s *p) {
     for (auto s : p->streams) cudaStreamDestroy(s);
     for (auto e : p->join) cudaEventDestroy(e);
     if (p->fork) cudaEventDestroy(p->fork);
+    if (p->capture) cudaStreamDestroy(p->capture);
     if (p->d_items) cudaFree(p->d_items);
     if (p->d_counters) cudaFree(p->d_counters);
     delete p;
@@ -899,6 +900,7 @@ CJ_API cj_status cj_group_plan_create(int32_t dtype, int64_t count, const int32_
         cudaEventCreateWithFlags(&p->join[i], cudaEventDisableTiming);
     }
     cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
+    cudaStreamCreateWithFlags(&p->capture, cudaStreamNonBlocking);
     {
         std::lock_guard<std::mutex> lk(G.mu);
         G.plans.push_back(p);
@@ -916,16 +918,16 @@ CJ_API cj_status cj_group_plan_launch(cj_group_plan p, const void *A_pool, void 
     if (!use_graph) return plan_record(p, A_pool, X_pool, st);
     std::vector<const void *> impls;
     for (auto &g : p->groups) impls.push_back(g.h->impl.load(std::memory_order_acquire));
-    if (!p->exec || p->g_A != A_pool || p->g_X != X_pool || p->g_stream != st || p->g_impls != impls) {
+    if (!p->exec || p->g_A != A_pool || p->g_X != X_pool || p->g_impls != impls) {
         if (p->exec) cudaGraphExecDestroy(p->exec);
         if (p->graph) cudaGraphDestroy(p->graph);
         p->exec = nullptr;
         p->graph = nullptr;
-        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-            return fail(CJ_ERR_CUDA, "stream capture could not start (legacy default stream cannot be captured)");
-        cj_status rc = plan_record(p, A_pool, X_pool, st);
+        if (cudaStreamBeginCapture(p->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return fail(CJ_ERR_CUDA, "stream capture could not start");
+        cj_status rc = plan_record(p, A_pool, X_pool, p->capture);
         cudaGraph_t g = nullptr;
-        cudaError_t e = cudaStreamEndCapture(st, &g);
+        cudaError_t e = cudaStreamEndCapture(p->capture, &g);
         if (rc != CJ_OK) {
             if (g) cudaGraphDestroy(g);
             return rc;
@@ -937,7 +939,6 @@ CJ_API cj_status cj_group_plan_launch(cj_group_plan p, const void *A_pool, void 
         p->graph = g;
         p->g_A = A_pool;
         p->g_X = X_pool;
-        p->g_stream = st;
         p->g_impls = impls;
     }
     if (cudaGraphLaunch(p->exec, st) != cudaSuccess) return fail(CJ_ERR_CUDA, "graph launch failed");
@@ -958,6 +959,37 @@ CJ_API cj_status cj_group_plan_destroy(cj_group_plan p) {
         G.plans.erase(std::remove(G.plans.begin(), G.plans.end(), p), G.plans.end());
     }
     plan_free(p);
+    return CJ_OK;
+}
+
+CJ_API cj_status cj_measure_fma_peak(int32_t dtype, void *cuda_stream, double *tflops) {
+    if (!G.inited) return fail(CJ_ERR_NOT_INITIALIZED, "cj_init has not been called");
+    if (G.compile_only) return fail(CJ_ERR_NO_DEVICE, "compile-only mode");
+    if (!tflops || (dtype != CJ_F64 && dtype != CJ_F32)) return fail(CJ_ERR_INVALID_ARG, "dtype must be f64 or f32");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    const void *k = cjint::peak_fma_kernel(dtype);
+    const unsigned grid = (unsigned)G.num_sms * 8u;
+    int iters = dtype == CJ_F64 ? 4096 : 65536;
+    double ad = 0.9999, bd = 1e-4;
+    float af = 0.9999f, bf = 1e-4f;
+    void *args_d[] = {&iters, &ad, &bd};
+    void *args_f[] = {&iters, &af, &bf};
+    void **args = dtype == CJ_F64 ? args_d : args_f;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaError_t err = cudaLaunchKernel(k, grid, 256, args, 0, st);   // warm-up
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3 && err == cudaSuccess; ++r) err = cudaLaunchKernel(k, grid, 256, args, 0, st);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess || ms <= 0) return fail(CJ_ERR_CUDA, "peak kernel failed: %s", cudaGetErrorString(err));
+    const double flops = 3.0 * 2.0 * 8.0 * iters * (double)grid * 256.0;
+    *tflops = flops / (ms * 1e-3) / 1e12;
     return CJ_OK;
 }
 

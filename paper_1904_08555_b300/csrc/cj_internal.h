@@ -32,5 +32,9 @@ struct GenericKernels {
 };
 const GenericKernels &generic_kernels();
 
+// FMA-throughput kernel (roofline denominator), indexed by dtype (0 f64, 1 f32):
+// kernel(int iters, T a, T b), 256 threads per block, 8 chains per thread.
+const void *peak_fma_kernel(int dtype);
+
 }  // namespace cjint
 #endif

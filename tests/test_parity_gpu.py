@@ -1,0 +1,299 @@
+"""GPU parity: libcj kernels (through the C ABI) against the CPU oracle.
+
+FP64 tolerance: 1e-12 relative Frobenius error per instance (update chain;
+max over instances) and over the whole output (LTimes).  FP32 variants are
+gated at 1e-5 against the FP64 oracle.  Sizes span several blocks and end in
+ragged tails; full-size launches are checked on seeded samples.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_1904_08555_b300 import cj
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    cj.init(sync=True, compile_threads=2)
+    yield
+    cj.shutdown()
+
+
+def relF_per_instance(x, ref):
+    x = x.reshape(ref.shape[0], -1).astype(np.float64)
+    ref = ref.reshape(ref.shape[0], -1)
+    return float(np.max(np.linalg.norm(x - ref, axis=1) / np.linalg.norm(ref, axis=1)))
+
+
+def tdtype(dt):
+    return torch.float64 if dt == cj.F64 else torch.float32
+
+
+def run_chain(h, A_np, steps, dt):
+    A = torch.from_numpy(A_np).to("cuda", tdtype(dt))
+    X = torch.full_like(A, float("nan"))
+    cj.launch_update_chain(h, A, X, steps)
+    torch.cuda.synchronize()
+    return X.cpu().numpy()
+
+
+def oracle_batch(n, steps):
+    return int(np.clip(3e7 // (n ** 3 * steps), 5, 700))
+
+
+CHAIN_SIZES = [1, 2, 3, 4, 5, 7, 8, 12, 16, 24, 31, 32, 33, 48, 64]
+
+
+@pytest.mark.parametrize("n", CHAIN_SIZES)
+@pytest.mark.parametrize("variant", ["default", "generic", "no_aot"])
+def test_update_chain_f64(n, variant):
+    steps = 64
+    flags = {"default": 0, "generic": cj.FLAG_GENERIC, "no_aot": cj.FLAG_NO_AOT}[variant]
+    h = cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=n, flags=flags)
+    expect = {"generic": "generic", "no_aot": "jit"}.get(variant, "aot" if n in (4, 8, 16, 32) else "jit")
+    assert h.variant == expect
+    batch = oracle_batch(n, steps) + 3
+    A = synth.chain_inputs_np(synth.SEED_CHAIN_SWEEP, batch, n)
+    ref = oracle.update_chain(A, steps, nthreads=8)
+    assert relF_per_instance(run_chain(h, A, steps, cj.F64), ref) <= TOL64
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 8, 13, 16, 40])
+@pytest.mark.parametrize("steps", [1, 100])
+def test_update_chain_col_major(n, steps):
+    for flags in (0, cj.FLAG_GENERIC):
+        h = cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=n, layout_a=1, flags=flags)
+        batch = oracle_batch(n, steps) + 1
+        A = synth.chain_inputs_np(synth.SEED_CHAIN_SWEEP, batch, n, layout=1)
+        ref = oracle.update_chain(A, steps, layout=1, nthreads=8)
+        assert relF_per_instance(run_chain(h, A, steps, cj.F64), ref) <= TOL64
+
+
+@pytest.mark.parametrize("n,tile", [(3, (2, 32, 0, 0)), (5, (2, 128, 0, 0)), (8, (2, 64, 0, 0)),
+                                    (8, (1, 1, 0, 0)), (12, (1, 3, 0, 0)), (24, (1, 16, 0, 0)),
+                                    (64, (1, 1, 0, 0)), (40, (1, 5, 0, 0))])
+def test_update_chain_explicit_tiles(n, tile):
+    steps = 32
+    h = cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=n, tile=tile)
+    assert h.variant == "jit"
+    batch = oracle_batch(n, steps) + 7
+    A = synth.chain_inputs_np(synth.SEED_CHAIN_SWEEP, batch, n)
+    ref = oracle.update_chain(A, steps, nthreads=8)
+    assert relF_per_instance(run_chain(h, A, steps, cj.F64), ref) <= TOL64
+
+
+@pytest.mark.parametrize("n", [3, 8, 16, 32, 48, 64])
+@pytest.mark.parametrize("generic", [False, True])
+def test_update_chain_f32_error(n, generic):
+    steps = 64
+    h = cj.specialize(cj.K_UPDATE_CHAIN, cj.F32, n=n, flags=cj.FLAG_GENERIC if generic else 0)
+    batch = oracle_batch(n, steps) + 2
+    A = synth.chain_inputs_np(synth.SEED_CHAIN_SWEEP, batch, n)
+    ref = oracle.update_chain(A, steps, nthreads=8)
+    assert relF_per_instance(run_chain(h, A, steps, cj.F32), ref) <= TOL32
+
+
+def test_small_config_all_variants():
+    """64 FP64 matrices, N = 8, T = 100: JIT, AoT and generic all match."""
+    A = synth.chain_inputs_np(synth.SEED_CHAIN_SMALL, 64, 8)
+    ref = oracle.update_chain(A, 100)
+    for flags, var in ((cj.FLAG_NO_AOT, "jit"), (0, "aot"), (cj.FLAG_GENERIC, "generic")):
+        h = cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=8, flags=flags)
+        assert h.variant == var
+        assert relF_per_instance(run_chain(h, A, 100, cj.F64), ref) <= TOL64
+
+
+def test_empty_batch_is_a_no_op():
+    h = cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=5)
+    X = torch.full((3, 5, 5), 7.0, device="cuda", dtype=torch.float64)
+    cj.launch_update_chain(h, X, X, 10, batch=0)
+    torch.cuda.synchronize()
+    assert torch.all(X == 7.0)
+
+
+def test_registers_specialized_vs_generic():
+    for n in (2, 4, 7):
+        spec = cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=n, flags=cj.FLAG_NO_AOT)
+        gen = cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=n, flags=cj.FLAG_GENERIC)
+        rs, _ = spec.regs()
+        rg, _ = gen.regs()
+        assert rs > 0 and rg > 0
+
+
+# ---------------------------------------------------------------------------
+# LTimes
+# ---------------------------------------------------------------------------
+
+def run_ltimes(h, L, x_canon, lin, lout, dt):
+    M, D = L.shape
+    _, G, Z = x_canon.shape
+    Lt = torch.from_numpy(L).to("cuda", tdtype(dt))
+    xt = torch.from_numpy(synth.to_layout(x_canon, lin).ravel()).to("cuda", tdtype(dt))
+    out = torch.full((M * G * Z,), float("nan"), device="cuda", dtype=tdtype(dt))
+    cj.launch_ltimes(h, Lt, xt, out, G, Z)
+    torch.cuda.synchronize()
+    return synth.from_layout(out.cpu().numpy(), lout, (M, G, Z)).astype(np.float64)
+
+
+def relF(x, ref):
+    return float(np.linalg.norm(x - ref) / np.linalg.norm(ref))
+
+
+@pytest.fixture(scope="module")
+def lt_small():
+    M, D, G, Z = 36, 96, 5, 37
+    L, x = synth.ltimes_inputs_np(synth.SEED_LTIMES, M, D, G, Z)
+    ref = oracle.ltimes(L, x.ravel(), G, Z, 0, 0, nthreads=4).reshape(M, G, Z)
+    return L, x, ref
+
+
+@pytest.mark.parametrize("lin", range(6))
+@pytest.mark.parametrize("lout", range(6))
+def test_ltimes_all_orders_f64(lt_small, lin, lout):
+    L, x, ref = lt_small
+    h = cj.specialize(cj.K_LTIMES, cj.F64, layout_a=lin, layout_b=lout, m=36, d=96)
+    assert h.variant == "jit"
+    out = run_ltimes(h, L, x, lin, lout, cj.F64)
+    assert relF(out, ref) <= TOL64
+    for m in range(36):
+        assert relF(out[m], ref[m]) <= TOL64
+
+
+@pytest.mark.parametrize("lin", range(6))
+@pytest.mark.parametrize("lout", [0, 3, 4])
+def test_ltimes_orders_f32(lt_small, lin, lout):
+    L, x, ref = lt_small
+    h = cj.specialize(cj.K_LTIMES, cj.F32, layout_a=lin, layout_b=lout, m=36, d=96)
+    assert relF(run_ltimes(h, L, x, lin, lout, cj.F32), ref) <= TOL32
+
+
+@pytest.mark.parametrize("lin,lout", [(0, 0), (1, 3), (3, 5), (5, 2)])
+@pytest.mark.parametrize("dt", [cj.F64, cj.F32])
+def test_ltimes_generic(lt_small, lin, lout, dt):
+    L, x, ref = lt_small
+    h = cj.specialize(cj.K_LTIMES, dt, layout_a=lin, layout_b=lout, m=36, d=96, flags=cj.FLAG_GENERIC)
+    assert h.variant == "generic"
+    assert relF(run_ltimes(h, L, x, lin, lout, dt), ref) <= (TOL64 if dt == cj.F64 else TOL32)
+
+
+@pytest.mark.parametrize("M,D,G,Z,lin,lout,tile", [
+    (4, 6, 3, 130, 0, 5, (0, 0, 0, 0)),
+    (37, 11, 33, 9, 4, 1, (0, 0, 0, 0)),             # partial moment group, ragged G
+    (36, 96, 32, 64, 2, 2, (4, 16, 192, (1 << 8) | 12)),
+    (36, 96, 32, 64, 1, 4, (32, 2, 64, (1 << 8) | 36)),
+    (64, 128, 2, 40, 3, 0, (1, 32, 256, (1 << 8) | 8)),
+])
+def test_ltimes_shapes_and_tiles(M, D, G, Z, lin, lout, tile):
+    L, x = synth.ltimes_inputs_np(synth.SEED_LTIMES, M, D, G, Z)
+    ref = oracle.ltimes(L, x.ravel(), G, Z, 0, 0).reshape(M, G, Z)
+    h = cj.specialize(cj.K_LTIMES, cj.F64, layout_a=lin, layout_b=lout, m=M, d=D, tile=tile)
+    assert relF(run_ltimes(h, L, x, lin, lout, cj.F64), ref) <= TOL64
+
+
+# ---------------------------------------------------------------------------
+# Grouped plan (uneven batch)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dt", [cj.F64, cj.F32])
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_grouped_plan_uneven(dt, use_graph):
+    n, t = synth.uneven_sizes(synth.SEED_UNEVEN, 400)
+    pool, off = synth.uneven_inputs_np(synth.SEED_UNEVEN, n)
+    ref = oracle.update_chain_uneven(n, t, off, pool)
+    plan = cj.GroupPlan(dt, n, t)
+    try:
+        assert plan.pool_elems == pool.size
+        A = torch.from_numpy(pool).to("cuda", tdtype(dt))
+        for rep in range(2):          # second launch replays the graph
+            X = torch.full_like(A, float("nan"))
+            plan.launch(A, X, stream=torch.cuda.current_stream(), use_graph=use_graph)
+            torch.cuda.synchronize()
+            Xh = X.cpu().numpy().astype(np.float64)
+            worst = 0.0
+            for k in range(len(n)):
+                sl = slice(off[k], off[k] + n[k] * n[k])
+                worst = max(worst, relF(Xh[sl], ref[sl]))
+            assert worst <= (TOL64 if dt == cj.F64 else TOL32), (rep, worst)
+    finally:
+        plan.destroy()
+
+
+def test_grouped_handle_direct_launch():
+    """One grouped instantiation over a hand-built work list (n = 20)."""
+    nn = 20
+    steps = np.array([128, 100, 77, 64, 64, 30, 17, 16, 16], dtype=np.int64)
+    cnt = len(steps)
+    pool = synth.uniform_np(synth.SEED_UNEVEN, 0, cnt * nn * nn)
+    ref = np.empty_like(pool)
+    for k in range(cnt):
+        ref[k * nn * nn:(k + 1) * nn * nn] = oracle.update_chain(
+            pool[k * nn * nn:(k + 1) * nn * nn].reshape(1, nn, nn), int(steps[k])).ravel()
+    items = np.zeros((cnt, 3), dtype=np.int64)
+    items[:, 0] = np.arange(cnt) * nn * nn
+    items[:, 1] = steps
+    for flags in (0, cj.FLAG_GENERIC):
+        h = cj.specialize(cj.K_UPDATE_CHAIN_GROUPED, cj.F64, n=nn, flags=flags)
+        it = torch.from_numpy(items).cuda()
+        A = torch.from_numpy(pool).cuda()
+        X = torch.full_like(A, float("nan"))
+        counter = torch.zeros(1, dtype=torch.int32, device="cuda")
+        cj.launch_grouped(h, it, A, X, counter, cnt)
+        torch.cuda.synchronize()
+        assert relF(X.cpu().numpy(), ref) <= TOL64
+
+
+# ---------------------------------------------------------------------------
+# Full-size launches, checked on seeded samples
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [3, 32])
+def test_full_size_sweep_sampled(n):
+    steps = 64
+    batch = synth.chain_batch(n)
+    A = synth.chain_inputs_torch(synth.SEED_CHAIN_SWEEP, batch, n, "cuda")
+    X = torch.empty_like(A)
+    h = cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=n, flags=cj.FLAG_NO_AOT)
+    cj.launch_update_chain(h, A, X, steps)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(17)
+    idx = np.unique(np.concatenate([[0, batch - 1], rng.integers(0, batch, 300)]))
+    idx_t = torch.from_numpy(idx).cuda()
+    a_s = A[idx_t].cpu().numpy()
+    np.testing.assert_array_equal(a_s[0], synth.chain_inputs_np(synth.SEED_CHAIN_SWEEP, 1, n)[0])
+    ref = oracle.update_chain(a_s, steps, nthreads=8)
+    assert relF_per_instance(X[idx_t].cpu().numpy(), ref) <= TOL64
+    del A, X
+
+
+@pytest.mark.parametrize("dt,lin,lout", [(cj.F64, 0, 3), (cj.F32, 4, 5)])
+def test_full_size_ltimes_sampled(dt, lin, lout):
+    M, D, G, Z = 36, 96, 32, 1 << 18
+    L, _ = synth.ltimes_inputs_np(synth.SEED_LTIMES, M, D, 1, 1)
+    x = synth.uniform_torch(synth.SEED_LTIMES, synth.STREAM_A, D * G * Z, "cuda").view(D, G, Z)
+    perm = synth.LAYOUT_PERMS[lin]
+    xin = x.permute(*perm).contiguous().to(tdtype(dt)).view(-1)
+    Lt = torch.from_numpy(L).to("cuda", tdtype(dt))
+    out = torch.empty(M * G * Z, device="cuda", dtype=tdtype(dt))
+    h = cj.specialize(cj.K_LTIMES, dt, layout_a=lin, layout_b=lout, m=M, d=D)
+    cj.launch_ltimes(h, Lt, xin, out, G, Z)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(5)
+    gs = rng.integers(0, G, 400)
+    zs = rng.integers(0, Z, 400)
+    cols = x[:, torch.from_numpy(gs).cuda(), torch.from_numpy(zs).cuda()].to(tdtype(dt)).double().cpu().numpy()
+    ref = oracle.ltimes(L, cols.ravel(), 1, len(gs), 0, 0).reshape(M, len(gs))
+    pout = out.view(*[(M, G, Z)[p] for p in synth.LAYOUT_PERMS[lout]])
+    inv = np.argsort(synth.LAYOUT_PERMS[lout])
+    canon = pout.permute(*inv)
+    got = canon[:, torch.from_numpy(gs).cuda(), torch.from_numpy(zs).cuda()].double().cpu().numpy()
+    assert relF(got, ref) <= (TOL64 if dt == cj.F64 else TOL32)
+    del x, xin, out
