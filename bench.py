@@ -47,6 +47,20 @@ def chain_bytes(batch: int, n: int, esize: int) -> float:
     return float(batch) * 2 * n * n * esize
 
 
+# Roofline denominators.  FP64: the nominal B300 FP64 rate (1.25 TFLOP/s;
+# about 2 FP64 FMA lanes per SM per clock).  FP32: 148 SMs x 128 FMA lanes
+# x 2 flops x 2032 MHz.  HBM: the measured copy bandwidth.
+PEAK_TFLOPS = {"f64": 1.25, "f32": 148 * 128 * 2 * 2.032e9 / 1e12}
+
+
+def hbm_peak_gbs() -> float:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6400.0
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
@@ -275,7 +289,8 @@ def cj_arm(args):
 
     value = world * step_flops * args.steps / (ms_spec * 1e-3) / 1e9
     gen_value = world * step_flops * args.steps / (ms_gen * 1e-3) / 1e9
-    peak64 = cj.measure_fma_peak(cj.F64, stream.cuda_stream)
+    micro64 = cj.measure_fma_peak(cj.F64, stream.cuda_stream)
+    peak64 = PEAK_TFLOPS["f64"]
     per_n = []
     for n in SWEEP_N:
         f = chain_flops(batch[n], n, T_STEPS)
@@ -327,11 +342,11 @@ def cj_arm(args):
             "speedup_vs_generic": value / gen_value,
             "jit_compile_ms_p50": st["compile_ms_p50"], "jit_compile_ms_p95": st["compile_ms_p95"],
             "lookup_ns_p50": st["lookup_ns_p50"], "compile_wall_s_9_sizes": compile_wall,
-            "fp64_fma_peak_tflops_measured": peak64,
+            "fp64_fma_microbenchmark_tflops": micro64,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
                          "frac": achieved / peak64, "traffic": None,
                          "kernel": f"update_chain<double,{dom},...> (N = {dom})",
-                         "peak_source": "measured FP64 FMA throughput (cj_measure_fma_peak)"},
+                         "peak_source": "nominal B300 FP64 rate (profiling recipe); FP64 pipe bound"},
             "per_n": per_n,
             "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(h2d)},
@@ -365,6 +380,16 @@ def main():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=("cj", "reference"), default="cj")
+    p.add_argument("--workload", choices=("sweep", "small", "sweep32", "ltimes", "uneven", "kernel"),
+                   default="sweep",
+                   help="sweep (default): the FP64 size sweep; the others are secondary measurements")
+    p.add_argument("--dtype", choices=("f64", "f32"), default="f64", help="ltimes / uneven precision")
+    p.add_argument("--ltimes-z", type=int, default=1 << 18)
+    p.add_argument("--kernel", choices=("chain", "chain-generic", "ltimes", "ltimes-generic"), default="chain")
+    p.add_argument("--n", type=int, default=32)
+    p.add_argument("--batch", type=int, default=16384)
+    p.add_argument("--layout-in", type=int, default=0)
+    p.add_argument("--layout-out", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=60.0,
                    help="oracle time budget: reference arm whole run; cpu_baseline leg uses a quarter")
@@ -373,9 +398,185 @@ def main():
         p.error("--warmup must be >= 3")
     if args.impl == "reference":
         reference_arm(args)
+    elif args.workload != "sweep":
+        secondary(args)
     else:
         cj_arm(args)
 
 
 if __name__ == "__main__":
     main()
+
+
+# ---------------------------------------------------------------------------
+# Secondary workloads (not the default line): --workload small|sweep32|ltimes|uneven
+# ---------------------------------------------------------------------------
+def _events(torch, stream, fn, reps):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def secondary(args):
+    import torch
+    from paper_1904_08555_b300 import cj
+    torch.cuda.set_device(0)
+    cj.init(sync=True, compile_threads=4)
+    stream = torch.cuda.Stream()
+    sampler = ClockSampler(0)
+    sampler.start()
+    out = {"metric": METRIC, "unit": "GFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
+    K, W = args.steps, args.warmup
+    if args.workload in ("small", "sweep32"):
+        dt = cj.F64 if args.workload == "small" else cj.F32
+        tdt = torch.float64 if dt == cj.F64 else torch.float32
+        sizes = (8,) if args.workload == "small" else SWEEP_N
+        rows, tot_f, tot_spec, tot_gen = [], 0.0, 0.0, 0.0
+        for n in sizes:
+            b = 64 if args.workload == "small" else synth.chain_batch(n)
+            steps = 100 if args.workload == "small" else T_STEPS
+            A = synth.uniform_torch(synth.SEED_CHAIN_SMALL if b == 64 else synth.SEED_CHAIN_SWEEP, synth.STREAM_A,
+                                    b * n * n, "cuda").view(b, n, n).to(tdt)
+            X = torch.empty_like(A)
+            f = chain_flops(b, n, steps)
+            row = {"N": n, "batch": b}
+            variants = [("jit", cj.FLAG_NO_AOT), ("generic", cj.FLAG_GENERIC)]
+            if n in AOT_N:
+                variants.append(("aot", 0))
+            reps = 200 if b == 64 else K
+            for name, fl in variants:
+                h = cj.specialize(cj.K_UPDATE_CHAIN, dt, n=n, flags=fl)
+                fn = lambda h=h: cj.launch_update_chain(h, A, X, steps, stream=stream)
+                _events(torch, stream, fn, W)
+                ms = _events(torch, stream, fn, reps)
+                row[name + "_us"] = ms * 1e3
+                row[name + "_gflops"] = f / ms / 1e6
+                row[name + "_regs"] = h.regs()[0]
+            row["speedup_vs_generic"] = row["generic_us"] / row["jit_us"]
+            rows.append(row)
+            tot_f += f
+            tot_spec += row["jit_us"]
+            tot_gen += row["generic_us"]
+            del A, X
+        peak = PEAK_TFLOPS["f64" if dt == cj.F64 else "f32"]
+        out.update({"value": tot_f / tot_spec / 1e3, "dtype": "f64" if dt == cj.F64 else "f32",
+                    "generic": {"value": tot_f / tot_gen / 1e3, "unit": "GFLOP/s"},
+                    "speedup_vs_generic": tot_gen / tot_spec, "per_n": rows,
+                    "roofline": {"bound": "alu", "peak": peak, "unit": "TFLOP/s",
+                                 "frac": tot_f / tot_spec / 1e6 / peak},
+                    "config": {"workload": ("update chain, 64 FP64 8x8 matrices, T = 100 (latency-bound by size)"
+                                            if args.workload == "small" else
+                                            "update chain FP32 size sweep, same sizes as the FP64 sweep")}})
+    elif args.workload == "ltimes":
+        dt = cj.F64 if args.dtype == "f64" else cj.F32
+        tdt = torch.float64 if dt == cj.F64 else torch.float32
+        es = 8 if dt == cj.F64 else 4
+        M, D, G, Z = 36, 96, 32, args.ltimes_z
+        L, _ = synth.ltimes_inputs_np(synth.SEED_LTIMES, M, D, 1, 1)
+        Lt = torch.from_numpy(L).to("cuda", tdt)
+        x = synth.uniform_torch(synth.SEED_LTIMES, synth.STREAM_A, D * G * Z, "cuda").view(D, G, Z).to(tdt)
+        xin = {lin: x.permute(*synth.LAYOUT_PERMS[lin]).contiguous().view(-1) for lin in range(6)}
+        del x
+        o = torch.empty(M * G * Z, device="cuda", dtype=tdt)
+        f = 2.0 * M * D * G * Z
+        byt = es * ((D + M) * G * Z + M * D)
+        rows, tot_s, tot_g = [], 0.0, 0.0
+        for lin in range(6):
+            for lout in range(6):
+                hs = cj.specialize(cj.K_LTIMES, dt, layout_a=lin, layout_b=lout, m=M, d=D)
+                hg = cj.specialize(cj.K_LTIMES, dt, layout_a=lin, layout_b=lout, m=M, d=D, flags=cj.FLAG_GENERIC)
+                fs = lambda: cj.launch_ltimes(hs, Lt, xin[lin], o, G, Z, stream=stream)
+                fg = lambda: cj.launch_ltimes(hg, Lt, xin[lin], o, G, Z, stream=stream)
+                _events(torch, stream, fs, 1)
+                ms_s = _events(torch, stream, fs, K)
+                _events(torch, stream, fg, 1)
+                ms_g = _events(torch, stream, fg, K)
+                rows.append({"in": synth.LAYOUT_NAMES[lin], "out": synth.LAYOUT_NAMES[lout].replace("D", "M"),
+                             "spec_ms": ms_s, "generic_ms": ms_g, "spec_gflops": f / ms_s / 1e6,
+                             "spec_gbs": byt / ms_s / 1e6, "generic_gflops": f / ms_g / 1e6,
+                             "speedup_vs_generic": ms_g / ms_s})
+                tot_s += ms_s
+                tot_g += ms_g
+        peak = PEAK_TFLOPS[args.dtype]
+        t_alu = f / (peak * 1e12) * 1e3
+        t_hbm = byt / (hbm_peak_gbs() * 1e9) * 1e3
+        mean_ms = tot_s / 36
+        out.update({"value": 36 * f / tot_s / 1e6, "dtype": args.dtype,
+                    "generic": {"value": 36 * f / tot_g / 1e6, "unit": "GFLOP/s"},
+                    "speedup_vs_generic": tot_g / tot_s,
+                    "min_speedup_vs_generic": min(r["speedup_vs_generic"] for r in rows),
+                    "roofline": {"bound": "alu" if t_alu >= t_hbm else "hbm",
+                                 "roofline_ms": max(t_alu, t_hbm), "mean_ms": mean_ms,
+                                 "frac": max(t_alu, t_hbm) / mean_ms,
+                                 "alu_frac": t_alu / mean_ms, "hbm_frac": t_hbm / mean_ms,
+                                 "peak_tflops": peak, "hbm_gbs": hbm_peak_gbs()},
+                    "per_pair": rows,
+                    "config": {"workload": f"LTimes out[m][g][z] = sum_d L[m][d] in[d][g][z], M=36 D=96 G=32 Z={Z}, "
+                                           f"all 36 (in, out) storage orders, {args.dtype}"}})
+    elif args.workload == "uneven":
+        dt = cj.F64 if args.dtype == "f64" else cj.F32
+        tdt = torch.float64 if dt == cj.F64 else torch.float32
+        n, t = synth.uneven_sizes(synth.SEED_UNEVEN, 10000)
+        pool, off = synth.uneven_inputs_np(synth.SEED_UNEVEN, n)
+        A = torch.from_numpy(pool).to("cuda", tdt)
+        X = torch.empty_like(A)
+        f = float(np.sum(t * (2.0 * n ** 3 + 2.0 * n ** 2)))
+        res = {}
+        for name, fl in (("spec", 0), ("generic", cj.FLAG_GENERIC)):
+            plan = cj.GroupPlan(dt, n, t, flags=fl)
+            fn = lambda: plan.launch(A, X, stream=stream, use_graph=True)
+            _events(torch, stream, fn, W)
+            res[name] = _events(torch, stream, fn, max(K, 10))
+            plan.destroy()
+        peak = PEAK_TFLOPS[args.dtype]
+        out.update({"value": f / res["spec"] / 1e6, "dtype": args.dtype,
+                    "generic": {"value": f / res["generic"] / 1e6, "unit": "GFLOP/s", "ms": res["generic"]},
+                    "ms_per_launch": res["spec"], "speedup_vs_generic": res["generic"] / res["spec"],
+                    "roofline": {"bound": "alu", "peak": peak, "unit": "TFLOP/s",
+                                 "frac": f / res["spec"] / 1e9 / peak},
+                    "config": {"workload": "uneven batch: 10,000 update chains, N log-uniform in [2,64], "
+                                           f"T uniform in [16,128], one grouped plan (CUDA graph), {args.dtype}",
+                               "flops": f, "groups": int(len(np.unique(n)))}})
+    elif args.workload == "kernel":
+        # one kernel on a small case (inputs above L2), for profiler captures
+        dt = cj.F64 if args.dtype == "f64" else cj.F32
+        tdt = torch.float64 if dt == cj.F64 else torch.float32
+        generic = args.kernel.endswith("-generic")
+        fl = cj.FLAG_GENERIC if generic else cj.FLAG_NO_AOT
+        if args.kernel.startswith("chain"):
+            n, b = args.n, args.batch
+            A = synth.uniform_torch(synth.SEED_CHAIN_SWEEP, synth.STREAM_A, b * n * n, "cuda").view(b, n, n).to(tdt)
+            X = torch.empty_like(A)
+            h = cj.specialize(cj.K_UPDATE_CHAIN, dt, n=n, flags=fl)
+            fn = lambda: cj.launch_update_chain(h, A, X, T_STEPS, stream=stream)
+            f = chain_flops(b, n, T_STEPS)
+            desc = f"update chain N={n} batch={b} T={T_STEPS} {args.dtype} {'generic' if generic else 'jit'}"
+        else:
+            M, D, G, Z = 36, 96, 32, args.ltimes_z
+            L, _ = synth.ltimes_inputs_np(synth.SEED_LTIMES, M, D, 1, 1)
+            Lt = torch.from_numpy(L).to("cuda", tdt)
+            x = synth.uniform_torch(synth.SEED_LTIMES, synth.STREAM_A, D * G * Z, "cuda").view(D, G, Z)
+            xin = x.permute(*synth.LAYOUT_PERMS[args.layout_in]).contiguous().view(-1).to(tdt)
+            del x
+            o = torch.empty(M * G * Z, device="cuda", dtype=tdt)
+            h = cj.specialize(cj.K_LTIMES, dt, layout_a=args.layout_in, layout_b=args.layout_out, m=M, d=D, flags=fl)
+            fn = lambda: cj.launch_ltimes(h, Lt, xin, o, G, Z, stream=stream)
+            f = 2.0 * M * D * G * Z
+            desc = (f"LTimes M=36 D=96 G=32 Z={Z} in {synth.LAYOUT_NAMES[args.layout_in]} out order "
+                    f"{args.layout_out} {args.dtype} {'generic' if generic else 'jit'}")
+        _events(torch, stream, fn, W)
+        ms = _events(torch, stream, fn, K)
+        out.update({"value": f / ms / 1e6, "dtype": args.dtype, "ms_per_launch": ms, "regs": h.regs()[0],
+                    "config": {"workload": desc}})
+    out["clocks"] = sampler.stop()
+    st = cj.stats()
+    out["jit_compile_ms_p50"] = st["compile_ms_p50"]
+    out["jit_compile_ms_p95"] = st["compile_ms_p95"]
+    print(json.dumps(out), flush=True)
+    cj.shutdown()

@@ -188,11 +188,12 @@ cj_status cj_handle_regs(cj_handle h, int *regs_per_thread, int *static_smem);
  * n[j]^2 over j < k.  The plan groups instances by n, requests one
  * UPDATE_CHAIN_GROUPED instantiation per group (tile 0 = default), orders
  * each group's items by T descending, and keeps work lists and counters in
- * device memory it owns.  dtype: CJ_F64 or CJ_F32.
+ * device memory it owns.  dtype: CJ_F64 or CJ_F32.  flags: 0, or
+ * CJ_FLAG_GENERIC to run every group on the generic grouped kernel.
  */
 typedef struct cj_group_plan_s *cj_group_plan;
 cj_status cj_group_plan_create(int32_t dtype, int64_t count, const int32_t *n, const int32_t *steps,
-                               cj_group_plan *out);
+                               uint32_t flags, cj_group_plan *out);
 /* Launch every group on `cuda_stream`: groups run concurrently on forked
  * streams joined back into cuda_stream.  use_graph = 1: the first call
  * captures the whole launch (counter reset included) into a CUDA graph on a

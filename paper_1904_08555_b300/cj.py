@@ -71,7 +71,7 @@ def load():
         L.cj_stats.argtypes = [ctypes.POINTER(Stats)]
         L.cj_handle_info.argtypes = [P, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int)]
         L.cj_handle_regs.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
-        L.cj_group_plan_create.argtypes = [i32, i64, P, P, ctypes.POINTER(P)]
+        L.cj_group_plan_create.argtypes = [i32, i64, P, P, ctypes.c_uint32, ctypes.POINTER(P)]
         L.cj_group_plan_launch.argtypes = [P, P, P, P, ctypes.c_int]
         L.cj_group_plan_info.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i64)]
         L.cj_group_plan_destroy.argtypes = [P]
@@ -212,13 +212,13 @@ def stats() -> dict:
 class GroupPlan:
     """cj_group_plan_*: uneven batch grouped by n, launched as one (graph) launch."""
 
-    def __init__(self, dtype: int, n, steps):
+    def __init__(self, dtype: int, n, steps, flags: int = 0):
         import numpy as np
         n = np.ascontiguousarray(n, dtype=np.int32)
         steps = np.ascontiguousarray(steps, dtype=np.int32)
         out = ctypes.c_void_p()
-        _check(load().cj_group_plan_create(dtype, len(n), n.ctypes.data, steps.ctypes.data, ctypes.byref(out)),
-               "cj_group_plan_create")
+        _check(load().cj_group_plan_create(dtype, len(n), n.ctypes.data, steps.ctypes.data, flags,
+                                           ctypes.byref(out)), "cj_group_plan_create")
         self.ptr = out.value
         g, e = ctypes.c_int32(0), ctypes.c_int64(0)
         _check(load().cj_group_plan_info(self.ptr, ctypes.byref(g), ctypes.byref(e)), "cj_group_plan_info")

@@ -830,12 +830,13 @@ CJ_API cj_status cj_handle_regs(cj_handle h, int *regs, int *static_smem) {
 }
 
 CJ_API cj_status cj_group_plan_create(int32_t dtype, int64_t count, const int32_t *n, const int32_t *steps,
-                                      cj_group_plan *out) {
+                                      uint32_t flags, cj_group_plan *out) {
     if (!G.inited) return fail(CJ_ERR_NOT_INITIALIZED, "cj_init has not been called");
     if (G.compile_only) return fail(CJ_ERR_NO_DEVICE, "compile-only mode");
     if (!out || count < 0 || (count > 0 && (!n || !steps)))
         return fail(CJ_ERR_INVALID_ARG, "null output or inputs");
     if (dtype != CJ_F64 && dtype != CJ_F32) return fail(CJ_ERR_INVALID_ARG, "grouped plans support f64 and f32");
+    if (flags & ~CJ_FLAG_GENERIC) return fail(CJ_ERR_INVALID_ARG, "grouped plans accept only CJ_FLAG_GENERIC");
     for (int64_t k = 0; k < count; ++k)
         if (n[k] < 1 || n[k] > 64 || steps[k] < 1) return fail(CJ_ERR_INVALID_ARG, "instance %lld out of range", (long long)k);
     auto *p = new cj_group_plan_s();
@@ -875,6 +876,7 @@ CJ_API cj_status cj_group_plan_create(int32_t dtype, int64_t count, const int32_
         cj_template_args a{};
         a.dtype = dtype;
         a.n = g.n;
+        a.flags = flags;
         cj_status rc = cj_specialize(CJ_K_UPDATE_CHAIN_GROUPED, &a, &g.h);
         if (rc != CJ_OK && rc != CJ_ERR_COMPILE) {
             plan_free(p);
