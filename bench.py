@@ -404,9 +404,6 @@ def main():
         cj_arm(args)
 
 
-if __name__ == "__main__":
-    main()
-
 
 # ---------------------------------------------------------------------------
 # Secondary workloads (not the default line): --workload small|sweep32|ltimes|uneven
@@ -580,3 +577,7 @@ def secondary(args):
     out["jit_compile_ms_p95"] = st["compile_ms_p95"]
     print(json.dumps(out), flush=True)
     cj.shutdown()
+
+
+if __name__ == "__main__":
+    main()

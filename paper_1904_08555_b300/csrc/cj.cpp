@@ -333,8 +333,11 @@ std::string name_expression(const cj_handle_s *h) {
 // ---------------------------------------------------------------------------
 // NVRTC specializer: in-memory sources and headers only.
 // ---------------------------------------------------------------------------
-const char *kNvrtcOpts[] = {"-arch=sm_103a", "-std=c++17", "-lineinfo"};
-constexpr int kNumNvrtcOpts = 3;
+// --no-cache: NVRTC would otherwise read and write the per-user CUDA compute
+// cache (~/.nv/ComputeCache) when a driver is present; the paper's design
+// requirement is that run-time compilation touches no file (Sec. 1).
+const char *kNvrtcOpts[] = {"-arch=sm_103a", "-std=c++17", "-lineinfo", "--no-cache"};
+constexpr int kNumNvrtcOpts = 4;
 
 struct CompileOut {
     nvrtcResult rc = NVRTC_SUCCESS;
