@@ -212,6 +212,38 @@ cj_status cj_group_plan_destroy(cj_group_plan p);
  * roofline denominator of the FP64/FP32 arithmetic-bound kernels. */
 cj_status cj_measure_fma_peak(int32_t dtype, void *cuda_stream, double *tflops);
 
+/*
+ * Allocation-free uneven update chain.  The paper has no counterpart: this
+ * entry point exists for callers that must not allocate device memory --
+ * code running under a device-memory budget owned by another allocator (a
+ * framework's caching allocator, an arena in an embedded or real-time
+ * deployment) and code on latency-critical paths, where cudaMalloc/cudaFree
+ * may synchronize the device.  It computes what cj_group_plan_create +
+ * cj_group_plan_launch compute for the same instances (same pool layout:
+ * instance k at the exclusive prefix sum of n[j]^2, row-major), using the
+ * generic runtime-N kernel per group, groups one after another on
+ * cuda_stream.  It calls no cudaMalloc/cudaFree and no allocating library
+ * routine, and does not need cj_init.
+ *   Scratch: the work list and per-n counters live in one fixed file-scope
+ *   __device__ array of CJ_NOALLOC_MAX_INSTANCES * 24 + 256 bytes (about
+ *   1.5 MiB) that every GPU which loads this library holds until the process
+ *   exits.  count > CJ_NOALLOC_MAX_INSTANCES returns CJ_ERR_INVALID_ARG.
+ *   The first call on a device looks up that array's device address (with
+ *   the device current) and sets kernel attributes; make that first call
+ *   before any stream capture on the device.
+ *   Every call reuses the same array and resets its counters at the start;
+ *   calls whose work overlaps on the GPU (other streams, or other host
+ *   threads on the same device) race on it and must be serialized by the
+ *   caller.  The work list is copied from host memory with cudaMemcpyAsync
+ *   on cuda_stream.
+ * dtype: CJ_F64 or CJ_F32; n[k] in 1..64; steps[k] >= 1; A_pool, X_pool are
+ * caller-owned device memory.  Errors: CJ_ERR_INVALID_ARG (bad arguments,
+ * too many instances), CJ_ERR_NO_DEVICE, CJ_ERR_CUDA (cj_last_error has the
+ * reason). */
+#define CJ_NOALLOC_MAX_INSTANCES 65536
+cj_status cj_update_chain_uneven_noalloc(int32_t dtype, int64_t count, const int32_t *n, const int32_t *steps,
+                                         const void *A_pool, void *X_pool, void *cuda_stream);
+
 /* Thread-local description of the last error on this thread ("" if none). */
 const char *cj_last_error(void);
 

@@ -23,7 +23,8 @@ VARIANT_NAMES = ("generic", "aot", "jit")
 
 EXPORTS = ("cj_init", "cj_specialize", "cj_specialize_wait", "cj_launch", "cj_stats", "cj_handle_info",
            "cj_handle_regs", "cj_group_plan_create", "cj_group_plan_launch", "cj_group_plan_info",
-           "cj_group_plan_destroy", "cj_measure_fma_peak", "cj_last_error", "cj_shutdown")
+           "cj_group_plan_destroy", "cj_measure_fma_peak", "cj_update_chain_uneven_noalloc", "cj_last_error",
+           "cj_shutdown")
 
 
 class CJError(RuntimeError):
@@ -76,6 +77,7 @@ def load():
         L.cj_group_plan_info.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i64)]
         L.cj_group_plan_destroy.argtypes = [P]
         L.cj_measure_fma_peak.argtypes = [i32, P, ctypes.POINTER(ctypes.c_double)]
+        L.cj_update_chain_uneven_noalloc.argtypes = [i32, i64, P, P, P, P, P]
         L.cj_last_error.restype = ctypes.c_char_p
         L.cj_shutdown.argtypes = []
         for name in EXPORTS:
@@ -201,6 +203,21 @@ def measure_fma_peak(dtype: int, stream=None) -> float:
     out = ctypes.c_double(0.0)
     _check(load().cj_measure_fma_peak(dtype, _stream(stream), ctypes.byref(out)), "cj_measure_fma_peak")
     return out.value
+
+
+NOALLOC_MAX_INSTANCES = 65536
+
+
+def update_chain_uneven_noalloc(dtype: int, n, steps, A_pool, X_pool, stream=None) -> None:
+    """cj_update_chain_uneven_noalloc: the uneven update chain without any
+    device allocation (scratch in a fixed array inside the library); for
+    callers that must not allocate device memory."""
+    import numpy as np
+    n = np.ascontiguousarray(n, dtype=np.int32)
+    steps = np.ascontiguousarray(steps, dtype=np.int32)
+    _check(load().cj_update_chain_uneven_noalloc(dtype, len(n), n.ctypes.data, steps.ctypes.data, _ptr(A_pool),
+                                                  _ptr(X_pool), _stream(stream, A_pool, X_pool)),
+           "cj_update_chain_uneven_noalloc")
 
 
 def stats() -> dict:

@@ -1000,6 +1000,10 @@ CJ_API cj_status cj_measure_fma_peak(int32_t dtype, void *cuda_stream, double *t
 
 CJ_API const char *cj_last_error(void) { return t_err.c_str(); }
 
+namespace cjint {
+void set_last_error(const char *msg) { t_err = msg; }
+}  // namespace cjint
+
 CJ_API cj_status cj_shutdown(void) {
     std::lock_guard<std::mutex> ilk(g_init_mu);
     if (!G.inited) return CJ_OK;

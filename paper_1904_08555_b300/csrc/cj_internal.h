@@ -3,6 +3,8 @@
 #ifndef CJ_INTERNAL_H
 #define CJ_INTERNAL_H
 
+#include <string>
+
 namespace cjint {
 
 enum { K_CHAIN = 1, K_LTIMES = 2, K_GROUPED = 3 };
@@ -35,6 +37,11 @@ const GenericKernels &generic_kernels();
 // FMA-throughput kernel (roofline denominator), indexed by dtype (0 f64, 1 f32):
 // kernel(int iters, T a, T b), 256 threads per block, 8 chains per thread.
 const void *peak_fma_kernel(int dtype);
+
+// Set the thread-local message returned by cj_last_error (used by the
+// allocation-free entry point in noalloc.cu).
+void set_last_error(const char *msg);
+inline void set_last_error(const std::string &msg) { set_last_error(msg.c_str()); }
 
 }  // namespace cjint
 #endif
