@@ -100,18 +100,26 @@ typedef struct {
  * else the default rule below.  Meaning of tile fields:
  *   update chain: {mapping, instances per block, 0, 0}; mapping 1 = one thread
  *     per row of X (A staged in shared memory), 2 = one thread per instance
- *     (X and A in registers, n <= 8), 3 = bf16 tensor-core warp tile.
- *     Default: n <= 4 -> {2, 128}; n <= 32 -> {1, max(1, 256 / n)};
+ *     (X and A in registers, n <= 8), 3 = bf16 tensor-core warp tile,
+ *     4 = FP64 tensor cores (mma.sync m8n8k4; one warp per 8 rows; f64 with
+ *     n in {8, 16, 24, 32}).
+ *     Default: f64 with n in {8, 16, 24, 32} -> {4, max(1, 64 / n)};
+ *     n <= 4 -> {2, 128}; n <= 32 -> {1, max(1, 256 / n)};
  *     else {1, max(1, 128 / n)}; bf16 -> {3, 1}.
- *   LTimes: {TG, TZ, threads, (R << 8) | S}: a block stages a TG x TZ box of
- *     (g, z) columns with all d in shared memory; each thread accumulates R
- *     columns x S moments (the last moment group may be partial), so
- *     threads = (TG * TZ / R) * ceil(m / S).  Default: columns CT = 64 (f64)
- *     or 128 (f32);
+ *   LTimes: {TG, TZ, threads, (PIPE << 20) | (MODE << 16) | (R << 8) | S}: a block stages a
+ *     TG x TZ box of (g, z) columns with all d in shared memory.  MODE 0: each
+ *     thread accumulates R columns x S moments on the FMA pipe (the last
+ *     moment group may be partial), threads = (TG * TZ / R) * ceil(m / S).
+ *     MODE 1 (f64, S = 8, d a multiple of 4): FP64 tensor cores (mma.sync
+ *     m8n8k4), each warp 8R columns x all moments, threads =
+ *     32 * TG * TZ / (8 R).  PIPE 1: two tile buffers, the next tile loaded with
+ *     cp.async while the current one is contracted.  Default: CT = 64 columns;
  *     call orders 1 and 4 "g-fast" (g is the fastest axis) and 0 and 2
  *     "z-fast"; TG = 1 if neither in nor out is g-fast, 8 if one is g-fast
  *     and the other z-fast, 32 otherwise; TZ = CT / TG;
- *     f64: R 1, S 9; f32: R 4, S 12 (m = 36: 256 and 96 threads).
+ *     f64 with d % 4 == 0: MODE 1, R 2, threads 128; other f64: R 1, S 9,
+ *     threads 64 * ceil(m / 9); f32: PIPE 1, R 2, S 12, threads
+ *     32 * ceil(m / 12) (m = 36: 96).
  */
 typedef struct {
     int32_t dtype, n, layout_a, layout_b, m, d;
@@ -243,6 +251,56 @@ cj_status cj_measure_fma_peak(int32_t dtype, void *cuda_stream, double *tflops);
 #define CJ_NOALLOC_MAX_INSTANCES 65536
 cj_status cj_update_chain_uneven_noalloc(int32_t dtype, int64_t count, const int32_t *n, const int32_t *steps,
                                          const void *A_pool, void *X_pool, void *cuda_stream);
+
+/*
+ * Autotuner and learned cost model (the paper's future work: profiling
+ * information used to guide autotuning of JIT-compiled code, Sec. 6).
+ *
+ * cj_candidates: the tile space searched for a request (tile fields ignored);
+ *   writes min(cap, count) tiles as int32[4] rows.
+ * cj_autotune: compiles every candidate (JIT) and times it on the caller's
+ *   device buffers (launch_args/batch as for cj_launch, each candidate
+ *   warmed once, then the median of reps launches, CUDA events on
+ *   cuda_stream).  best_tile gets the fastest; times_ms[i] (cap entries)
+ *   the time of candidate i in cj_candidates order (INFINITY if it did not
+ *   compile).
+ * cj_featurize: the CJ_FEATURES-float input vector of the cost model for
+ *   (request, tile) at `batch` instances (chain) or columns G*Z (LTimes)
+ *   and `steps` (chain T).
+ * cj_mlp_*: an in_features -> 64 -> 64 -> 1 ReLU network in FP32 on the
+ *   device (library-owned).  Parameters are one flat vector in the order
+ *   W1[64][F], b1[64], W2[64][64], b2[64], w3[64], b3.  forward: y = f(X)
+ *   for X[B][F] (device pointers).  grad: gradient of the mean squared
+ *   error (1/B) sum (y - t)^2 into grad (device, count floats) and the loss
+ *   into *loss (device, may be NULL), parameters unchanged.  train_step: the
+ *   same gradient, then one Adam step (beta1 0.9, beta2 0.999, eps 1e-8,
+ *   rate lr).  Deterministic: no atomics.  create draws weights from
+ *   SplitMix64(seed), U(-s, s) with s = sqrt(3 / fan_in), biases 0.
+ * cj_cost_model_use: install m (in_features == CJ_FEATURES) for
+ *   cj_specialize requests with tile = {0,0,0,0} when cj_config.use_cost_model
+ *   is set (NULL uninstalls); the decision is cached per request.
+ * cj_choose_tile: the candidate with the lowest predicted log time.
+ */
+#define CJ_FEATURES 32
+typedef struct cj_mlp_s *cj_mlp;
+cj_status cj_candidates(cj_kernel_id k, const cj_template_args *a, int32_t *tiles, int32_t cap, int32_t *count);
+cj_status cj_autotune(cj_kernel_id k, const cj_template_args *a, void *const *launch_args, int64_t batch,
+                      void *cuda_stream, int32_t reps, int32_t best_tile[4], float *times_ms, int32_t cap,
+                      int32_t *count);
+cj_status cj_featurize(cj_kernel_id k, const cj_template_args *a, int64_t batch, int32_t steps,
+                       const int32_t tile[4], float *out);
+cj_status cj_mlp_create(int32_t in_features, uint64_t seed, cj_mlp *out);
+cj_status cj_mlp_set_params(cj_mlp m, const float *host, int64_t count);
+cj_status cj_mlp_get_params(cj_mlp m, float *host, int64_t cap, int64_t *count);
+cj_status cj_mlp_forward(cj_mlp m, const float *X, int64_t B, float *y, void *cuda_stream);
+cj_status cj_mlp_grad(cj_mlp m, const float *X, const float *t, int64_t B, float *grad, float *loss,
+                      void *cuda_stream);
+cj_status cj_mlp_train_step(cj_mlp m, const float *X, const float *t, int64_t B, float lr, float *loss,
+                            void *cuda_stream);
+cj_status cj_mlp_destroy(cj_mlp m);
+cj_status cj_cost_model_use(cj_mlp m);
+cj_status cj_choose_tile(cj_kernel_id k, const cj_template_args *a, int64_t batch, int32_t steps,
+                         int32_t tile_out[4], float *predicted_log_time);
 
 /* Thread-local description of the last error on this thread ("" if none). */
 const char *cj_last_error(void);

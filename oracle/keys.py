@@ -22,15 +22,19 @@ All little-endian.  Fields that a kernel does not use are zeroed, so requests
 differing only there share an instantiation.
 
 Default tile resolution (tile all zero, no cost model):
+  update chain / grouped, f64 with n in {8, 16, 24, 32}:
+                                       (4 = FP64 tensor-core panels, max(1, 64 // n), 0, 0)
   update chain / grouped, f64 or f32:  n <= 4 -> (2 = instance per thread, 128, 0, 0)
                                        else   -> (1 = row per thread, ipb, 0, 0)
                                        with ipb = max(1, 256 // n) for n <= 32,
                                        max(1, 128 // n) above
   update chain, bf16:                  (3 = tensor-core warp tile, 1, 0, 0)
-  LTimes: (TG, TZ, threads, (R << 8) | S) with CT = 64 (f64) or 128 (f32)
+  LTimes: (TG, TZ, threads, (PIPE << 20) | (MODE << 16) | (R << 8) | S), CT = 64
       columns; orders 1, 4 are g-fast and 0, 2 z-fast; TG = 1 if neither in
       nor out is g-fast, 8 if one is g-fast and the other z-fast, else 32;
-      TZ = CT / TG; f64: R 1, S 9; f32: R 4, S 12; threads = (CT / R) * ceil(m / S).
+      TZ = CT / TG; f64 with d % 4 == 0: tensor-core mode, tile[3] = (1 << 16) | (2 << 8) | 8,
+      threads 128; other f64: R 1, S 9, threads 64 * ceil(m / 9); f32: pipelined,
+      tile[3] = (1 << 20) | (2 << 8) | 12, threads 32 * ceil(m / 12).
 Expected variant: GENERIC flag -> generic; else update chain f64/f32 with
 n in {4, 8, 16, 32}, default tile, AoT set enabled and no NO_AOT flag -> aot;
 else jit.
@@ -59,15 +63,18 @@ G_FAST = (1, 4)
 Z_FAST = (0, 2)
 
 
-def default_tile(kernel: int, dtype: int, n: int, layout_a: int = 0, layout_b: int = 0, m: int = 36) -> tuple:
+def default_tile(kernel: int, dtype: int, n: int, layout_a: int = 0, layout_b: int = 0, m: int = 36,
+                 d: int = 96) -> tuple:
     if kernel in (K_UPDATE_CHAIN, K_UPDATE_CHAIN_GROUPED):
         if dtype == BF16:
             return (3, 1, 0, 0)
+        if dtype == F64 and n % 8 == 0 and n <= 32:
+            return (4, max(1, 64 // n), 0, 0)
         if n <= 4:
             return (2, 128, 0, 0)
         return (1, max(1, (256 if n <= 32 else 128) // n), 0, 0)
     if kernel == K_LTIMES:
-        ct = 64 if dtype == F64 else 128
+        ct = 64
         gin, gout = layout_a in G_FAST, layout_b in G_FAST
         if not gin and not gout:
             tg = 1
@@ -75,8 +82,11 @@ def default_tile(kernel: int, dtype: int, n: int, layout_a: int = 0, layout_b: i
             tg = 8
         else:
             tg = 32
-        r, s = (1, 9) if dtype == F64 else (4, 12)
-        return (tg, ct // tg, (ct // r) * (-(-m // s)), (r << 8) | s)
+        if dtype == F64 and d % 4 == 0:
+            return (tg, ct // tg, ct // 16 * 32, (1 << 16) | (2 << 8) | 8)
+        if dtype == F32:
+            return (tg, ct // tg, 32 * (-(-m // 12)), (1 << 20) | (2 << 8) | 12)
+        return (tg, ct // tg, ct * (-(-m // 9)), (1 << 8) | 9)
     raise ValueError("unknown kernel")
 
 
@@ -92,7 +102,7 @@ def canonical_key(kernel: int, dtype: int, n=0, layout_a=0, layout_b=0, m=0, d=0
     if flags & FLAG_GENERIC:
         tile = (0, 0, 0, 0)            # the generic kernel has no tile template
     elif all(t == 0 for t in tile):
-        tile = default_tile(kernel, dtype, n, layout_a, layout_b, m)
+        tile = default_tile(kernel, dtype, n, layout_a, layout_b, m, d)
     return struct.pack("<HBBBBHHH4II", kernel, dtype, layout_a, layout_b, 0, n, m, d,
                        *tile, flags & KEY_FLAGS)
 

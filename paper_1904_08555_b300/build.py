@@ -28,7 +28,8 @@ EMBEDDED = [("cj_emb_geometry_h", "geometry.h"),
 
 
 def _sources():
-    srcs = [os.path.join(CSRC, f) for f in ("cj.cpp", "aot.cu", "noalloc.cu", "cj_internal.h")]
+    srcs = [os.path.join(CSRC, f) for f in ("cj.cpp", "aot.cu", "noalloc.cu", "tuner.cu", "cj_internal.h")]
+    srcs += [os.path.join(KDIR, "mlp.cuh")]
     srcs += [os.path.join(KDIR, f) for _, f in EMBEDDED]
     srcs += [os.path.join(ROOT, "include", "cj.h"), __file__]
     return srcs
@@ -73,9 +74,10 @@ def build(force: bool = False) -> str:
     _run([os.path.join(CUDA, "bin", "nvcc"), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
           "-Xcompiler", "-fvisibility=hidden", *inc, "-c", os.path.join(CSRC, "aot.cu"),
           "-o", os.path.join(OUT, "aot.o")])
-    _run([os.path.join(CUDA, "bin", "nvcc"), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-          "-Xcompiler", "-fvisibility=hidden", *inc, "-c", os.path.join(CSRC, "noalloc.cu"),
-          "-o", os.path.join(OUT, "noalloc.o")])
+    for unit in ("noalloc", "tuner"):
+        _run([os.path.join(CUDA, "bin", "nvcc"), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+              "-Xcompiler", "-fvisibility=hidden", *inc, "-c", os.path.join(CSRC, unit + ".cu"),
+              "-o", os.path.join(OUT, unit + ".o")])
     _run(["g++", "-O2", "-std=c++17", "-fPIC", "-fvisibility=hidden", "-Wall", *inc, "-c",
           os.path.join(CSRC, "cj.cpp"), "-o", os.path.join(OUT, "cj.o")])
     ver = os.path.join(OUT, "exports.map")
@@ -84,7 +86,7 @@ def build(force: bool = False) -> str:
     lib64 = os.path.join(CUDA, "lib64")
     tmp = LIB + ".tmp"
     _run(["g++", "-shared", "-o", tmp, os.path.join(OUT, "aot.o"), os.path.join(OUT, "noalloc.o"),
-          os.path.join(OUT, "cj.o"),
+          os.path.join(OUT, "tuner.o"), os.path.join(OUT, "cj.o"),
           "-L" + lib64, "-Wl,--start-group", "-lnvrtc_static", "-lnvrtc-builtins_static",
           "-lnvptxcompiler_static", "-Wl,--end-group", "-lcudart_static", "-lpthread", "-ldl", "-lrt",
           "-Wl,--exclude-libs,ALL", "-Wl,--version-script=" + ver, "-Wl,--gc-sections", "-s"])

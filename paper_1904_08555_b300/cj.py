@@ -23,8 +23,11 @@ VARIANT_NAMES = ("generic", "aot", "jit")
 
 EXPORTS = ("cj_init", "cj_specialize", "cj_specialize_wait", "cj_launch", "cj_stats", "cj_handle_info",
            "cj_handle_regs", "cj_group_plan_create", "cj_group_plan_launch", "cj_group_plan_info",
-           "cj_group_plan_destroy", "cj_measure_fma_peak", "cj_update_chain_uneven_noalloc", "cj_last_error",
-           "cj_shutdown")
+           "cj_group_plan_destroy", "cj_measure_fma_peak", "cj_update_chain_uneven_noalloc", "cj_candidates",
+           "cj_autotune", "cj_featurize", "cj_mlp_create", "cj_mlp_set_params", "cj_mlp_get_params",
+           "cj_mlp_forward", "cj_mlp_grad", "cj_mlp_train_step", "cj_mlp_destroy", "cj_cost_model_use",
+           "cj_choose_tile", "cj_last_error", "cj_shutdown")
+FEATURES = 32
 
 
 class CJError(RuntimeError):
@@ -78,6 +81,19 @@ def load():
         L.cj_group_plan_destroy.argtypes = [P]
         L.cj_measure_fma_peak.argtypes = [i32, P, ctypes.POINTER(ctypes.c_double)]
         L.cj_update_chain_uneven_noalloc.argtypes = [i32, i64, P, P, P, P, P]
+        TA = ctypes.POINTER(TemplateArgs)
+        L.cj_candidates.argtypes = [ctypes.c_int, TA, P, i32, ctypes.POINTER(i32)]
+        L.cj_autotune.argtypes = [ctypes.c_int, TA, ctypes.POINTER(P), i64, P, i32, P, P, i32, ctypes.POINTER(i32)]
+        L.cj_featurize.argtypes = [ctypes.c_int, TA, i64, i32, P, P]
+        L.cj_mlp_create.argtypes = [i32, ctypes.c_uint64, ctypes.POINTER(P)]
+        L.cj_mlp_set_params.argtypes = [P, P, i64]
+        L.cj_mlp_get_params.argtypes = [P, P, i64, ctypes.POINTER(i64)]
+        L.cj_mlp_forward.argtypes = [P, P, i64, P, P]
+        L.cj_mlp_grad.argtypes = [P, P, P, i64, P, P, P]
+        L.cj_mlp_train_step.argtypes = [P, P, P, i64, ctypes.c_float, P, P]
+        L.cj_mlp_destroy.argtypes = [P]
+        L.cj_cost_model_use.argtypes = [P]
+        L.cj_choose_tile.argtypes = [ctypes.c_int, TA, i64, i32, P, ctypes.POINTER(ctypes.c_float)]
         L.cj_last_error.restype = ctypes.c_char_p
         L.cj_shutdown.argtypes = []
         for name in EXPORTS:
@@ -249,3 +265,114 @@ class GroupPlan:
         if self.ptr:
             load().cj_group_plan_destroy(self.ptr)
             self.ptr = None
+
+
+# ---------------------------------------------------------------------------
+# autotuner and cost model
+# ---------------------------------------------------------------------------
+def _targs(dtype, n=0, layout_a=0, layout_b=0, m=0, d=0, tile=(0, 0, 0, 0), flags=0):
+    return TemplateArgs(dtype, n, layout_a, layout_b, m, d, (ctypes.c_int32 * 4)(*tile), flags)
+
+
+def candidates(kernel: int, dtype: int, n=0, layout_a=0, layout_b=0, m=0, d=0):
+    """Candidate tiles (list of 4-tuples) searched for this request."""
+    import numpy as np
+    a = _targs(dtype, n, layout_a, layout_b, m, d)
+    cnt = ctypes.c_int32(0)
+    _check(load().cj_candidates(kernel, ctypes.byref(a), None, 0, ctypes.byref(cnt)), "cj_candidates")
+    buf = np.zeros((cnt.value, 4), dtype=np.int32)
+    _check(load().cj_candidates(kernel, ctypes.byref(a), buf.ctypes.data, cnt.value, ctypes.byref(cnt)),
+           "cj_candidates")
+    return [tuple(int(v) for v in row) for row in buf]
+
+
+def featurize(kernel: int, dtype: int, batch: int, steps: int, tile, n=0, layout_a=0, layout_b=0, m=0, d=0):
+    import numpy as np
+    a = _targs(dtype, n, layout_a, layout_b, m, d)
+    t = np.ascontiguousarray(tile, dtype=np.int32)
+    out = np.zeros(FEATURES, dtype=np.float32)
+    _check(load().cj_featurize(kernel, ctypes.byref(a), batch, steps, t.ctypes.data, out.ctypes.data),
+           "cj_featurize")
+    return out
+
+
+def autotune(kernel: int, dtype: int, launch_vals, batch: int, stream, reps=3, n=0, layout_a=0, layout_b=0, m=0,
+             d=0):
+    """Exhaustive autotune on the caller's buffers; returns (best_tile, [(tile, ms), ...])."""
+    import numpy as np
+    a = _targs(dtype, n, layout_a, layout_b, m, d)
+    cands = candidates(kernel, dtype, n, layout_a, layout_b, m, d)
+    arr = (ctypes.c_void_p * len(launch_vals))(*[ctypes.cast(ctypes.pointer(v), ctypes.c_void_p) for v in launch_vals])
+    best = np.zeros(4, dtype=np.int32)
+    times = np.zeros(len(cands), dtype=np.float32)
+    cnt = ctypes.c_int32(0)
+    _check(load().cj_autotune(kernel, ctypes.byref(a), arr, batch, _stream(stream), reps, best.ctypes.data,
+                              times.ctypes.data, len(cands), ctypes.byref(cnt)), "cj_autotune")
+    return tuple(int(v) for v in best), list(zip(cands, [float(t) for t in times]))
+
+
+def chain_launch_vals(A, X, steps):
+    return [ctypes.c_void_p(_ptr(A)), ctypes.c_void_p(_ptr(X)), ctypes.c_int32(steps)]
+
+
+def ltimes_launch_vals(L, x, out, G, Z):
+    return [ctypes.c_void_p(_ptr(L)), ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(out)), ctypes.c_int64(G),
+            ctypes.c_int64(Z)]
+
+
+class MLP:
+    """The cost model's F -> 64 -> 64 -> 1 ReLU network (device-resident, FP32)."""
+
+    def __init__(self, in_features: int = FEATURES, seed: int = 0xC1A5):
+        out = ctypes.c_void_p()
+        _check(load().cj_mlp_create(in_features, seed, ctypes.byref(out)), "cj_mlp_create")
+        self.ptr = out.value
+        self.F = in_features
+        self.P = 64 * in_features + 64 + 64 * 64 + 64 + 64 + 1
+
+    def get_params(self):
+        import numpy as np
+        buf = np.zeros(self.P, dtype=np.float32)
+        cnt = ctypes.c_int64(0)
+        _check(load().cj_mlp_get_params(self.ptr, buf.ctypes.data, self.P, ctypes.byref(cnt)), "cj_mlp_get_params")
+        return buf
+
+    def set_params(self, v):
+        import numpy as np
+        v = np.ascontiguousarray(v, dtype=np.float32)
+        _check(load().cj_mlp_set_params(self.ptr, v.ctypes.data, v.size), "cj_mlp_set_params")
+
+    def forward(self, X, y, stream=None):
+        _check(load().cj_mlp_forward(self.ptr, _ptr(X), X.shape[0], _ptr(y), _stream(stream, X, y)),
+               "cj_mlp_forward")
+
+    def grad(self, X, t, grad, loss=None, stream=None):
+        _check(load().cj_mlp_grad(self.ptr, _ptr(X), _ptr(t), X.shape[0], _ptr(grad), _ptr(loss),
+                                  _stream(stream, X, t)), "cj_mlp_grad")
+
+    def train_step(self, X, t, lr, loss=None, stream=None):
+        _check(load().cj_mlp_train_step(self.ptr, _ptr(X), _ptr(t), X.shape[0], lr, _ptr(loss),
+                                        _stream(stream, X, t)), "cj_mlp_train_step")
+
+    def use_as_cost_model(self):
+        _check(load().cj_cost_model_use(self.ptr), "cj_cost_model_use")
+
+    def destroy(self):
+        if self.ptr:
+            load().cj_mlp_destroy(self.ptr)
+            self.ptr = None
+
+
+def clear_cost_model():
+    _check(load().cj_cost_model_use(None), "cj_cost_model_use")
+
+
+def choose_tile(kernel: int, dtype: int, batch: int, steps: int, n=0, layout_a=0, layout_b=0, m=0, d=0):
+    import numpy as np
+    a = _targs(dtype, n, layout_a, layout_b, m, d)
+    out = np.zeros(4, dtype=np.int32)
+    pred = ctypes.c_float(0)
+    _check(load().cj_choose_tile(kernel, ctypes.byref(a), batch, steps, out.ctypes.data, ctypes.byref(pred)),
+           "cj_choose_tile")
+    return tuple(int(v) for v in out), pred.value
+

@@ -17,6 +17,7 @@
 #include <nvrtc.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -164,6 +165,9 @@ struct State {
     std::vector<double> compile_ms;
     std::vector<double> lookup_ns;
     size_t lookup_pos = 0;
+    // cost-model decisions per request (key with tile 0), so the model runs
+    // once per distinct request and never on the lookup path of a hit
+    std::unordered_map<std::string, std::array<int, 4>> decisions;
     // A process that exits without cj_shutdown still stops its compile
     // threads here (no CUDA calls: the runtime may already be gone).
     ~State() {
@@ -205,10 +209,39 @@ void default_tile(int k, cj_template_args &a) {
     else tg = 32;
     a.tile[0] = tg;
     a.tile[1] = ct / tg;
-    // f64: R 1, S 9; f32: R 4, S 12; threads = (CT / R) * ceil(m / S)
-    const int r = a.dtype == CJ_F64 ? 1 : 4, s = a.dtype == CJ_F64 ? 9 : 12;
-    a.tile[2] = (ct / r) * ((a.m + s - 1) / s);
-    a.tile[3] = (r << 8) | s;
+    if (a.dtype == CJ_F64 && a.d % 4 == 0) {
+        // FP64 tensor cores: each warp 16 columns x all moments
+        a.tile[2] = (ct / 16) * 32;
+        a.tile[3] = (1 << 16) | (2 << 8) | 8;
+        return;
+    }
+    if (a.dtype == CJ_F32) {
+        // 64 columns, R 2, S 12, pipelined loads; threads = 32 * ceil(m / 12)
+        a.tile[0] = tg;
+        a.tile[1] = 64 / tg;
+        a.tile[2] = 32 * ((a.m + 11) / 12);
+        a.tile[3] = (1 << 20) | (2 << 8) | 12;
+        return;
+    }
+    // other f64: R 1, S 9; threads = CT * ceil(m / 9)
+    a.tile[2] = ct * ((a.m + 8) / 9);
+    a.tile[3] = (1 << 8) | 9;
+}
+
+void put16(unsigned char *p, uint32_t v) { p[0] = v & 0xff; p[1] = (v >> 8) & 0xff; }
+void put32(unsigned char *p, uint32_t v) { for (int i = 0; i < 4; ++i) p[i] = (v >> (8 * i)) & 0xff; }
+
+void make_key(int k, const cj_template_args &a, unsigned char *key) {
+    memset(key, 0, 32);
+    put16(key + 0, (uint32_t)k);
+    key[2] = (unsigned char)a.dtype;
+    key[3] = (unsigned char)a.layout_a;
+    key[4] = (unsigned char)a.layout_b;
+    put16(key + 6, (uint32_t)a.n);
+    put16(key + 8, (uint32_t)a.m);
+    put16(key + 10, (uint32_t)a.d);
+    for (int i = 0; i < 4; ++i) put32(key + 12 + 4 * i, (uint32_t)a.tile[i]);
+    put32(key + 28, a.flags & kKeyFlags);
 }
 
 cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_args &a) {
@@ -236,43 +269,60 @@ cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_
         for (int &t : a.tile) t = 0;
         return CJ_OK;
     }
-    if (a.tile[0] == 0 && a.tile[1] == 0 && a.tile[2] == 0 && a.tile[3] == 0) default_tile(k, a);
+    if (a.tile[0] == 0 && a.tile[1] == 0 && a.tile[2] == 0 && a.tile[3] == 0) {
+        bool chosen = false;
+        if (G.cfg.use_cost_model && !G.compile_only && k != CJ_K_UPDATE_CHAIN_GROUPED) {
+            unsigned char rk[32];
+            make_key(k, a, rk);
+            const std::string rs(reinterpret_cast<char *>(rk), 32);
+            {
+                std::lock_guard<std::mutex> lk(G.mu);
+                auto it = G.decisions.find(rs);
+                if (it != G.decisions.end()) {
+                    std::memcpy(a.tile, it->second.data(), sizeof a.tile);
+                    chosen = true;
+                }
+            }
+            if (!chosen && cjint::cost_model_tile(k, a, a.tile)) {
+                chosen = true;
+                std::array<int, 4> t{a.tile[0], a.tile[1], a.tile[2], a.tile[3]};
+                std::lock_guard<std::mutex> lk(G.mu);
+                G.decisions.emplace(rs, t);
+            }
+        }
+        if (!chosen) default_tile(k, a);
+    }
     // explicit tiles: check the kernel can be instantiated and launched
     if (k != CJ_K_LTIMES) {
         const int map = a.tile[0], ipb = a.tile[1];
-        if (map != 1 && map != 2) return fail(CJ_ERR_INVALID_ARG, "update chain mapping %d must be 1 or 2", map);
+        if (map != 1 && map != 2 && map != 4)
+            return fail(CJ_ERR_INVALID_ARG, "update chain mapping %d must be 1, 2 or 4", map);
         if (map == 2 && a.n > 8) return fail(CJ_ERR_INVALID_ARG, "mapping 2 needs n <= 8");
+        if (map == 4 && !cjint::chain_dmma_ok(a.n, a.dtype))
+            return fail(CJ_ERR_INVALID_ARG, "mapping 4 (FP64 tensor cores) needs f64 and n in {8, 16, 24, 32}");
         if (ipb < 1 || cjg::chain_threads(a.n, map, ipb) > 1024 || a.tile[2] || a.tile[3])
             return fail(CJ_ERR_INVALID_ARG, "bad instances-per-block %d for n = %d", ipb, a.n);
         if (k == CJ_K_UPDATE_CHAIN_GROUPED && ipb > 256) return fail(CJ_ERR_INVALID_ARG, "grouped ipb must be <= 256");
         if (cjg::chain_smem(a.n, map, ipb, esize(a.dtype)) > 220 * 1024)
             return fail(CJ_ERR_INVALID_ARG, "tile needs too much shared memory");
     } else {
-        const int tg = a.tile[0], tz = a.tile[1], nt = a.tile[2], r = a.tile[3] >> 8, s = a.tile[3] & 0xff;
-        if (tg < 1 || tz < 1 || r < 1 || s < 1 || nt < 32 || nt > 1024 || (tg * tz) % r ||
-            (tg * tz / r) * ((a.m + s - 1) / s) != nt)
+        const int tg = a.tile[0], tz = a.tile[1], nt = a.tile[2];
+        const int pipe = (a.tile[3] >> 20) & 0xf, mode = (a.tile[3] >> 16) & 0xf;
+        const int r = (a.tile[3] >> 8) & 0xff, s = a.tile[3] & 0xff;
+        if (pipe > 1 || (a.tile[3] >> 24)) return fail(CJ_ERR_INVALID_ARG, "LTimes tile flags 0x%x unknown", a.tile[3]);
+        if (mode == 1 && (a.dtype != CJ_F64 || s != 8 || a.d % 4 || r < 1 || (tg * tz) % (8 * r) ||
+                          (tg * tz / (8 * r)) * 32 != nt || nt > 1024))
+            return fail(CJ_ERR_INVALID_ARG, "LTimes tensor-core tile {%d,%d,%d,0x%x} invalid (f64, S = 8, d %% 4 == 0, "
+                        "threads = 32 * TG * TZ / (8 R))", a.tile[0], a.tile[1], a.tile[2], a.tile[3]);
+        if (mode > 1) return fail(CJ_ERR_INVALID_ARG, "LTimes compute mode %d unknown", mode);
+        if (mode == 0 && (tg < 1 || tz < 1 || r < 1 || s < 1 || nt < 32 || nt > 1024 || (tg * tz) % r ||
+                          (tg * tz / r) * ((a.m + s - 1) / s) != nt))
             return fail(CJ_ERR_INVALID_ARG, "LTimes tile {%d,%d,%d,%d} does not cover its block", a.tile[0],
                         a.tile[1], a.tile[2], a.tile[3]);
-        if (cjg::lt_smem(a.m, s, a.d, tg * tz, esize(a.dtype)) > 220 * 1024)
+        if (cjg::lt_smem(a.m, s, a.d, tg * tz, esize(a.dtype), pipe) > 220 * 1024)
             return fail(CJ_ERR_INVALID_ARG, "LTimes tile needs too much shared memory");
     }
     return CJ_OK;
-}
-
-void put16(unsigned char *p, uint32_t v) { p[0] = v & 0xff; p[1] = (v >> 8) & 0xff; }
-void put32(unsigned char *p, uint32_t v) { for (int i = 0; i < 4; ++i) p[i] = (v >> (8 * i)) & 0xff; }
-
-void make_key(int k, const cj_template_args &a, unsigned char *key) {
-    memset(key, 0, 32);
-    put16(key + 0, (uint32_t)k);
-    key[2] = (unsigned char)a.dtype;
-    key[3] = (unsigned char)a.layout_a;
-    key[4] = (unsigned char)a.layout_b;
-    put16(key + 6, (uint32_t)a.n);
-    put16(key + 8, (uint32_t)a.m);
-    put16(key + 10, (uint32_t)a.d);
-    for (int i = 0; i < 4; ++i) put32(key + 12 + 4 * i, (uint32_t)a.tile[i]);
-    put32(key + 28, a.flags & kKeyFlags);
 }
 
 // ---------------------------------------------------------------------------
@@ -307,7 +357,7 @@ void spec_geometry(const cj_handle_s *h, Impl &s) {
     const int es = esize(a.dtype);
     if (h->kernel == CJ_K_LTIMES) {
         s.threads = a.tile[2];
-        s.smem = (size_t)cjg::lt_smem(a.m, a.tile[3] & 0xff, a.d, a.tile[0] * a.tile[1], es);
+        s.smem = (size_t)cjg::lt_smem(a.m, a.tile[3] & 0xff, a.d, a.tile[0] * a.tile[1], es, (a.tile[3] >> 20) & 1);
     } else {
         s.ipb = a.tile[1];
         s.threads = cjg::chain_threads(a.n, a.tile[0], a.tile[1]);
@@ -325,8 +375,9 @@ std::string name_expression(const cj_handle_s *h) {
         snprintf(buf, sizeof buf, "cj::update_chain_grouped<%s, %d, %d, %d>", ctype(a.dtype), a.n, a.tile[0],
                  a.tile[1]);
     else
-        snprintf(buf, sizeof buf, "cj::ltimes<%s, %d, %d, %d, %d, %d, %d, %d, %d, %d>", ctype(a.dtype), a.m, a.d,
-                 a.layout_a, a.layout_b, a.tile[0], a.tile[1], a.tile[2], a.tile[3] >> 8, a.tile[3] & 0xff);
+        snprintf(buf, sizeof buf, "cj::ltimes<%s, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d>", ctype(a.dtype), a.m,
+                 a.d, a.layout_a, a.layout_b, a.tile[0], a.tile[1], a.tile[2], (a.tile[3] >> 8) & 0xff,
+                 a.tile[3] & 0xff, (a.tile[3] >> 16) & 0xf, (a.tile[3] >> 20) & 0xf);
     return buf;
 }
 
@@ -1024,6 +1075,7 @@ CJ_API cj_status cj_shutdown(void) {
     }
     G.cache.clear();
     G.queue.clear();
+    G.decisions.clear();
     G.inited = false;
     return CJ_OK;
 }

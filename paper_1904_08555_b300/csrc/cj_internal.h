@@ -5,15 +5,22 @@
 
 #include <string>
 
+#include "cj.h"
+
 namespace cjint {
 
 enum { K_CHAIN = 1, K_LTIMES = 2, K_GROUPED = 3 };
 enum { D_F64 = 0, D_F32 = 1, D_BF16 = 2 };
 
 // Default tile rule of the update chain kernels (documented in cj.h).
-constexpr int chain_default_map(int n, int dtype) { return dtype == D_BF16 ? 3 : (n <= 4 ? 2 : 1); }
+constexpr bool chain_dmma_ok(int n, int dtype) { return dtype == D_F64 && n % 8 == 0 && n <= 32; }
+constexpr int chain_default_map(int n, int dtype) {
+    return dtype == D_BF16 ? 3 : chain_dmma_ok(n, dtype) ? 4 : (n <= 4 ? 2 : 1);
+}
 constexpr int chain_default_ipb(int n, int dtype) {
-    return dtype == D_BF16 ? 1 : n <= 4 ? 128 : n <= 32 ? 256 / n : (128 / n > 1 ? 128 / n : 1);
+    return dtype == D_BF16 ? 1
+         : chain_dmma_ok(n, dtype) ? (64 / n > 1 ? 64 / n : 1)
+         : n <= 4 ? 128 : n <= 32 ? 256 / n : (128 / n > 1 ? 128 / n : 1);
 }
 
 struct AotKernel {
@@ -37,6 +44,10 @@ const GenericKernels &generic_kernels();
 // FMA-throughput kernel (roofline denominator), indexed by dtype (0 f64, 1 f32):
 // kernel(int iters, T a, T b), 256 threads per block, 8 chains per thread.
 const void *peak_fma_kernel(int dtype);
+
+// Cost-model tile choice for a request with tile = 0 (tuner.cu); false if no
+// model is installed or the query failed.
+bool cost_model_tile(int k, const cj_template_args &a, int *tile_out);
 
 // Set the thread-local message returned by cj_last_error (used by the
 // allocation-free entry point in noalloc.cu).

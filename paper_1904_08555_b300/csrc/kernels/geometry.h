@@ -25,9 +25,10 @@ CJ_HD constexpr int row_pitch(int nn, int esize) {
 // 32 banks.
 CJ_HD constexpr int inst_pitch(int nn) { return nn | 1; }
 
-// Threads per block of the update chain kernels.
+// Threads per block of the update chain kernels: mapping 2 one thread per
+// instance, mapping 4 one warp per 8 rows, mapping 1 one thread per row.
 CJ_HD constexpr int chain_threads(int n, int mapping, int ipb) {
-    return mapping == 2 ? ipb : ((ipb * n + 31) / 32) * 32;
+    return mapping == 2 ? ipb : mapping == 4 ? ipb * (n / 8) * 32 : ((ipb * n + 31) / 32) * 32;
 }
 
 // Rows of X kept in shared memory (instead of registers) above this size.
@@ -41,7 +42,7 @@ CJ_HD constexpr long chain_smem(int n, int mapping, int ipb, int esize) {
     return mapping == 2
         ? (long)ipb * inst_pitch(n * n) * esize
         : (long)ipb * row_pitch(n * n, esize) * esize +
-              (n > chain_reg_rows_max(esize)
+              (mapping == 1 && n > chain_reg_rows_max(esize)
                    ? (long)chain_threads(n, 1, ipb) * xrow_pitch(n) * esize
                    : 0L);
 }
@@ -57,8 +58,10 @@ CJ_HD constexpr long chain_generic_smem(int n, int ipb, int threads, int esize) 
 CJ_HD constexpr int lt_mpitch(int mpad, int esize) { return ((mpad * esize + 15) / 16) * 16 / esize; }
 // Column tile pitch: CT plus 16 bytes.
 CJ_HD constexpr int lt_cpitch(int ct, int esize) { return ct + 16 / esize; }
-CJ_HD constexpr long lt_smem(int m, int s, int d, int ct, int esize) {
-    return ((long)d * lt_mpitch((m + s - 1) / s * s, esize) + (long)(m > d ? m : d) * lt_cpitch(ct, esize)) *
+// pipe = 1: two tile buffers.
+CJ_HD constexpr long lt_smem(int m, int s, int d, int ct, int esize, int pipe = 0) {
+    return ((long)d * lt_mpitch((m + s - 1) / s * s, esize) +
+            (pipe ? 2L : 1L) * (long)(m > d ? m : d) * lt_cpitch(ct, esize)) *
            esize;
 }
 CJ_HD constexpr long lt_generic_smem(int m, int d, int cols, int esize) {

@@ -68,9 +68,65 @@ __device__ __forceinline__ void lt_box(T* __restrict__ g, T* s, long long G, lon
     }
 }
 
+// FP64 tensor-core contraction of one staged tile (MODE 1): warp w owns the
+// 8*R columns starting at 8*R*w and every moment, in blocks of 8.  For the
+// k-block of directions 4kb..4kb+3 it multiplies the (8 columns x 4 d) slice
+// of the staged `in` tile (mma A operand: a[col][d] at lane 4*col + d) by
+// the (4 d x 8 m) slice of L^T (B operand: b[d][m] at lane 4*m + d) into an
+// 8 x 8 (column x moment) accumulator (c[col][m] at lane 4*col + m/2,
+// component m%2).
+__device__ __forceinline__ void lt_dmma(double (&d)[2], double a, double b) {
+    asm("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+        : "+d"(d[0]), "+d"(d[1])
+        : "d"(a), "d"(b));
+}
+
+// Asynchronous variant of the box load (cp.async, one element per copy):
+// out-of-range elements are zero-filled (source size 0), nothing is read.
+template <class T, int LAY, int EX, int TG, int TZ, int CP, int NT>
+__device__ __forceinline__ void lt_box_async(const T* __restrict__ g, T* s, long long G, long long Z,
+                                             long long g0, long long z0, int tid) {
+    constexpr int a0 = lt_axis(LAY, 0), a1 = lt_axis(LAY, 1), a2 = lt_axis(LAY, 2);
+    constexpr int b0 = a0 == 0 ? EX : a0 == 1 ? TG : TZ;
+    constexpr int b1 = a1 == 0 ? EX : a1 == 1 ? TG : TZ;
+    constexpr int b2 = a2 == 0 ? EX : a2 == 1 ? TG : TZ;
+    constexpr int TOTAL = b0 * b1 * b2;
+    const long long ext[3] = {EX, G, Z};
+    long long st[3];
+    st[a2] = 1;
+    st[a1] = ext[a2];
+    st[a0] = ext[a2] * ext[a1];
+    const long long gbase = g0 * st[1] + z0 * st[2];
+#pragma unroll 4
+    for (int e = tid; e < TOTAL; e += NT) {
+        const int i2 = e % b2;
+        const int i1 = (e / b2) % b1;
+        const int i0 = e / (b2 * b1);
+        int c[3];
+        c[a0] = i0;
+        c[a1] = i1;
+        c[a2] = i2;
+        const int x = c[0], gl = c[1], zl = c[2];
+        const bool ok = (g0 + gl < G) && (z0 + zl < Z);
+        const T* src = ok ? g + gbase + (long long)x * st[0] + (long long)gl * st[1] + (long long)zl * st[2] : g;
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(s + x * CP + gl * TZ + zl);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(dst), "l"(src), "n"((int)sizeof(T)),
+                     "r"(ok ? (int)sizeof(T) : 0)
+                     : "memory");
+    }
+}
+__device__ __forceinline__ void lt_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void lt_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // Persistent kernel: L^T stays in shared memory; each block loops over
 // (g, z) tiles: stage the in box, contract, stage and store the out box.
-template <class T, int M, int D, int LIN, int LOUT, int TG, int TZ, int NT, int R, int S>
+// MODE 0: FMA pipe, each thread R columns x S moments.  MODE 1 (FP64 only,
+// S = 8, D a multiple of 4): FP64 tensor cores, each warp 8R columns x all
+// moments.  PIPE 1: two tile buffers; the next tile's box is loaded with
+// cp.async while the current one is contracted.
+template <class T, int M, int D, int LIN, int LOUT, int TG, int TZ, int NT, int R, int S, int MODE = 0,
+          int PIPE = 0>
 __global__ void __launch_bounds__(NT)
 ltimes(const T* __restrict__ L, const T* __restrict__ in, T* __restrict__ out, long long G, long long Z) {
     constexpr int CT = TG * TZ;
@@ -78,10 +134,14 @@ ltimes(const T* __restrict__ L, const T* __restrict__ in, T* __restrict__ out, l
     constexpr int MP = cjg::lt_mpitch(MG * S, (int)sizeof(T));
     constexpr int CP = cjg::lt_cpitch(CT, (int)sizeof(T));
     constexpr int QG = CT / R;   // column groups
-    static_assert(CT % R == 0 && QG * MG == NT, "tile does not cover the block");
+    static_assert(MODE == 1 || (CT % R == 0 && QG * MG == NT), "tile does not cover the block");
+    static_assert(MODE == 0 || (sizeof(T) == 8 && S == 8 && D % 4 == 0 && CT % (8 * R) == 0 &&
+                                (CT / (8 * R)) * 32 == NT), "tensor-core tile does not cover the block");
     extern __shared__ __align__(16) unsigned char cj_smem[];
+    constexpr int XR = M > D ? M : D;        // rows of a tile buffer
     T* sL = reinterpret_cast<T*>(cj_smem);   // [D][MP], L transposed
-    T* sX = sL + D * MP;                      // [D][CP] in tile, then [M][CP] out tile
+    T* sX0 = sL + D * MP;                     // [D][CP] in tile, then [M][CP] out tile
+    T* sX1 = sX0 + XR * CP;                   // second buffer (PIPE)
     const int tid = threadIdx.x;
     for (int e = tid; e < MP * D; e += NT) {
         const int m = e / D, d = e - m * D;
@@ -91,11 +151,61 @@ ltimes(const T* __restrict__ L, const T* __restrict__ in, T* __restrict__ out, l
     const long long ntiles = ntg * ntz;
     const int qg = tid % QG, sg = tid / QG;
     const int q0 = qg * R, m0 = sg * S;
-    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    if (PIPE && (long long)blockIdx.x < ntiles) {
+        const long long t0 = blockIdx.x;
+        lt_box_async<T, LIN, D, TG, TZ, CP, NT>(in, sX0, G, Z, (t0 / ntz) * TG, (t0 % ntz) * TZ, tid);
+    }
+    if (PIPE) lt_async_commit();
+    int buf = 0;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, buf ^= 1) {
         const long long g0 = (t / ntz) * TG, z0 = (t % ntz) * TZ;
+        T* sX = (PIPE && buf) ? sX1 : sX0;
+        __syncthreads();   // the other buffer's previous contents are no longer read
+        if (PIPE) {
+            const long long tn = t + gridDim.x;
+            if (tn < ntiles)
+                lt_box_async<T, LIN, D, TG, TZ, CP, NT>(in, buf ? sX0 : sX1, G, Z, (tn / ntz) * TG,
+                                                        (tn % ntz) * TZ, tid);
+            lt_async_commit();
+            lt_async_wait<1>();   // this tile's copies (all but the newest group) are done
+        } else {
+            lt_box<T, LIN, D, TG, TZ, CP, NT, true>(const_cast<T*>(in), sX, G, Z, g0, z0, tid);
+        }
         __syncthreads();
-        lt_box<T, LIN, D, TG, TZ, CP, NT, true>(const_cast<T*>(in), sX, G, Z, g0, z0, tid);
-        __syncthreads();
+        if constexpr (MODE == 1) {
+            const int lane = tid & 31, r = lane >> 2, t = lane & 3;
+            const int c0 = (tid >> 5) * 8 * R;
+            double acc[R][MG][2];
+#pragma unroll
+            for (int cb = 0; cb < R; ++cb)
+#pragma unroll
+                for (int nb = 0; nb < MG; ++nb) acc[cb][nb][0] = acc[cb][nb][1] = 0.0;
+#pragma unroll 2
+            for (int kb = 0; kb < D / 4; ++kb) {
+                double a[R], b[MG];
+#pragma unroll
+                for (int cb = 0; cb < R; ++cb) a[cb] = sX[(4 * kb + t) * CP + c0 + 8 * cb + r];
+#pragma unroll
+                for (int nb = 0; nb < MG; ++nb) b[nb] = sL[(4 * kb + t) * MP + 8 * nb + r];
+#pragma unroll
+                for (int cb = 0; cb < R; ++cb)
+#pragma unroll
+                    for (int nb = 0; nb < MG; ++nb) lt_dmma(acc[cb][nb], a[cb], b[nb]);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int cb = 0; cb < R; ++cb)
+#pragma unroll
+                for (int nb = 0; nb < MG; ++nb)
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) {
+                        const int m = 8 * nb + 2 * t + i;
+                        if (M % 8 == 0 || m < M) sX[m * CP + c0 + 8 * cb + r] = acc[cb][nb][i];
+                    }
+            __syncthreads();
+            lt_box<T, LOUT, M, TG, TZ, CP, NT, false>(out, sX, G, Z, g0, z0, tid);
+            continue;
+        }
         T acc[R][S];
 #pragma unroll
         for (int r = 0; r < R; ++r)
@@ -122,6 +232,7 @@ ltimes(const T* __restrict__ L, const T* __restrict__ in, T* __restrict__ out, l
         __syncthreads();
         lt_box<T, LOUT, M, TG, TZ, CP, NT, false>(out, sX, G, Z, g0, z0, tid);
     }
+    if (PIPE) lt_async_wait<0>();
 }
 
 // Generic: run-time M, D and strides; one thread per column q = g*Z + z

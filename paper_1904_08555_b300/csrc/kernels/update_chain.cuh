@@ -130,13 +130,85 @@ __device__ __forceinline__ void inst_chain_regs(const T* sa, int steps, T cc, T 
     }
 }
 
+// FP64 tensor cores (mapping 4, N a multiple of 8, N <= 32): one warp owns an
+// 8-row panel of X and computes P = X_panel A with mma.sync m8n8k4 (FP64 in,
+// FP64 accumulate).  Fragment layouts (PTX ISA, m8n8k4 .f64): A operand
+// a[r][k] at lane 4r+k; B operand b[k][n] at lane 4n+k; accumulator c[r][n]
+// at lane 4r + n/2, component n%2.  X stays in the accumulator layout; the
+// A operand of k-block kb (columns 4kb..4kb+3) is gathered from the row's
+// owners with two shuffles.  A_b's B fragments are loaded once into
+// registers.  The update X += c P is a separate FMA per element, as stated.
+__device__ __forceinline__ void dmma_m8n8k4(double (&d)[2], double a, double b) {
+    asm("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                 : "+d"(d[0]), "+d"(d[1])
+                 : "d"(a), "d"(b));
+}
+
+template <int N>
+__device__ __forceinline__ void panel_chain_dmma(const double* a_s, int panel, int steps, double cc,
+                                                 double (&x)[N / 8][2]) {
+    constexpr int NB = N / 8, KB = N / 4;
+    const int lane = threadIdx.x & 31, r = lane >> 2, t = lane & 3;
+    double b[KB][NB];
+#pragma unroll
+    for (int kb = 0; kb < KB; ++kb)
+#pragma unroll
+        for (int nb = 0; nb < NB; ++nb) b[kb][nb] = a_s[(4 * kb + t) * N + 8 * nb + r];
+    const int row = 8 * panel + r;
+#pragma unroll
+    for (int nb = 0; nb < NB; ++nb) {
+        x[nb][0] = (row == 8 * nb + 2 * t) ? 1.0 : 0.0;
+        x[nb][1] = (row == 8 * nb + 2 * t + 1) ? 1.0 : 0.0;
+    }
+    const int base = lane & ~3;
+    for (int k = 0; k < steps; ++k) {
+        double p[NB][2];
+#pragma unroll
+        for (int nb = 0; nb < NB; ++nb) p[nb][0] = p[nb][1] = 0.0;
+#pragma unroll
+        for (int kb = 0; kb < KB; ++kb) {
+            const int src = base | (2 * (kb & 1) + (t >> 1));
+            const double v0 = __shfl_sync(0xffffffffu, x[kb >> 1][0], src);
+            const double v1 = __shfl_sync(0xffffffffu, x[kb >> 1][1], src);
+            const double a = (t & 1) ? v1 : v0;
+#pragma unroll
+            for (int nb = 0; nb < NB; ++nb) dmma_m8n8k4(p[nb], a, b[kb][nb]);
+        }
+#pragma unroll
+        for (int nb = 0; nb < NB; ++nb) {
+            x[nb][0] = fmaT(cc, p[nb][0], x[nb][0]);
+            x[nb][1] = fmaT(cc, p[nb][1], x[nb][1]);
+        }
+    }
+}
+
 // Run the chain for the `ninst` instances staged at sA (pitch per geometry.h)
 // and leave each X_T in place of its A, in storage order LAYOUT.
 // steps_of(inst) and c_of(inst) give the per-instance T and c.
 template <class T, int N, int LAYOUT, int MAP, int IPB, class StepsOf, class COf>
 __device__ __forceinline__ void chain_block(T* sA, int ninst, int tid, StepsOf steps_of, COf c_of) {
     constexpr int NN = N * N;
-    if constexpr (MAP == 2) {
+    if constexpr (MAP == 4) {
+        static_assert(sizeof(T) == 8 && N % 8 == 0 && N <= 32, "mapping 4 is FP64 with N = 8, 16, 24, 32");
+        constexpr int P = cjg::row_pitch(NN, 8);
+        constexpr int NB = N / 8;
+        const int warp = tid >> 5;
+        const int inst = warp / NB, panel = warp - inst * NB;
+        const bool active = inst < ninst;   // uniform across the warp
+        double x[NB][2];
+        if (active) panel_chain_dmma<N>(sA + inst * P, panel, steps_of(inst), c_of(inst), x);
+        __syncthreads();
+        if (active) {
+            const int lane = tid & 31, row = 8 * panel + (lane >> 2), t = lane & 3;
+#pragma unroll
+            for (int nb = 0; nb < NB; ++nb)
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const int col = 8 * nb + 2 * t + i;
+                    sA[inst * P + (LAYOUT == 0 ? row * N + col : col * N + row)] = x[nb][i];
+                }
+        }
+    } else if constexpr (MAP == 2) {
         constexpr int P = cjg::inst_pitch(NN);
         const bool active = tid < ninst;
         T x[N][N];

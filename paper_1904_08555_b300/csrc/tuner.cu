@@ -1,0 +1,445 @@
+// tuner.cu -- autotuner and learned cost model (the paper's future work on
+// profiling-guided autotuning of JIT-compiled code, Sec. 6):
+//   * cj_candidates: the tile space V(kernel, dtype, N, orders) searched;
+//   * cj_autotune:   compile every candidate and time it on the caller's
+//                    buffers (exhaustive search; the fallback and the judge
+//                    of the model's regret);
+//   * cj_featurize:  the cost model's input vector for (request, tile);
+//   * cj_mlp_*:      the F -> 64 -> 64 -> 1 ReLU network that predicts the
+//                    log run time, with forward, gradient and Adam kernels;
+//   * cj_choose_tile / cost-model hook of cj_specialize: argmin of the
+//                    predicted time over V.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "cj.h"
+#include "cj_internal.h"
+#include "kernels/geometry.h"
+#include "kernels/mlp.cuh"
+
+#define CJ_API extern "C" __attribute__((visibility("default")))
+
+namespace {
+
+constexpr int H = 64;      // hidden width
+constexpr int BS = 64;     // samples per block in the gradient kernel
+
+cj_status tfail(cj_status s, const char *msg) {
+    cjint::set_last_error(msg);
+    return s;
+}
+
+int esize(int dtype) { return dtype == CJ_F64 ? 8 : 4; }
+
+// ---------------------------------------------------------------------------
+// Candidate tiles
+// ---------------------------------------------------------------------------
+bool g_fast(int lay) { return lay == 1 || lay == 4; }
+bool z_fast(int lay) { return lay == 0 || lay == 2; }
+
+void chain_candidates(const cj_template_args &a, std::vector<std::array<int, 4>> &out) {
+    const int n = a.n, es = esize(a.dtype);
+    auto ok = [&](int map, int ipb) {
+        return cjg::chain_threads(n, map, ipb) <= 1024 && cjg::chain_smem(n, map, ipb, es) <= 200 * 1024;
+    };
+    if (a.dtype == CJ_F64 && n % 8 == 0 && n <= 32)
+        for (int ipb : {1, 2, 4, 8})
+            if (ok(4, ipb)) out.push_back({4, ipb, 0, 0});
+    if (n <= 8)
+        for (int ipb : {32, 64, 128, 256})
+            if (ok(2, ipb)) out.push_back({2, ipb, 0, 0});
+    for (int ipb : {1, 2, 4, 8, 16, 32, 64})
+        if (ipb * n <= 1024 && ok(1, ipb)) out.push_back({1, ipb, 0, 0});
+}
+
+void ltimes_candidates(const cj_template_args &a, std::vector<std::array<int, 4>> &out) {
+    const int es = esize(a.dtype);
+    const bool gi = g_fast(a.layout_a), go = g_fast(a.layout_b);
+    std::vector<int> tgs;
+    const int rule = (!gi && !go) ? 1 : ((gi && z_fast(a.layout_b)) || (go && z_fast(a.layout_a))) ? 8 : 32;
+    tgs.push_back(rule);
+    tgs.push_back(rule == 1 ? 8 : 1);
+    auto push = [&](int tg, int ct, int mode, int r, int s, int pipe = 0) {
+        if (ct % tg) return;
+        int nt;
+        if (mode == 1) {
+            if (ct % (8 * r)) return;
+            nt = ct / (8 * r) * 32;
+        } else {
+            if (ct % r) return;
+            nt = (ct / r) * ((a.m + s - 1) / s);
+        }
+        if (nt < 32 || nt > 1024) return;
+        if (cjg::lt_smem(a.m, s, a.d, ct, es, pipe) > 200 * 1024) return;
+        out.push_back({tg, ct / tg, nt, (pipe << 20) | (mode << 16) | (r << 8) | s});
+    };
+    for (int tg : tgs) {
+        if (a.dtype == CJ_F64) {
+            if (a.d % 4 == 0)
+                for (int ct : {64, 128})
+                    for (int r : {1, 2, 4}) push(tg, ct, 1, r, 8);
+            push(tg, 64, 0, 1, 9);
+            push(tg, 64, 0, 1, 12);
+        } else {
+            for (int pipe : {1, 0})
+                for (int ct : {64, 128})
+                    for (auto rs : {std::pair<int, int>{2, 12}, {4, 12}, {4, 9}})
+                        push(tg, ct, 0, rs.first, rs.second, pipe);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Features
+// ---------------------------------------------------------------------------
+double lg2(double v) { return std::log2(std::max(v, 1.0)); }
+
+void featurize(int k, const cj_template_args &a, int64_t batch, int32_t steps, const int *tile, float *f) {
+    std::memset(f, 0, sizeof(float) * CJ_FEATURES);
+    f[0] = k == CJ_K_UPDATE_CHAIN;
+    f[1] = k == CJ_K_LTIMES;
+    f[2] = k == CJ_K_UPDATE_CHAIN_GROUPED;
+    f[3 + std::min(std::max(a.dtype, 0), 2)] = 1.f;
+    const int es = esize(a.dtype);
+    double flops, bytes;
+    if (k == CJ_K_LTIMES) {
+        const double cols = (double)batch;
+        flops = 2.0 * a.m * a.d * cols;
+        bytes = es * ((double)(a.d + a.m) * cols + a.m * a.d);
+        f[6] = lg2(a.m) / 6;
+        f[7] = lg2(a.d) / 7;
+        f[8 + (a.layout_a % 6)] = 1.f;
+        f[14 + (a.layout_b % 6)] = 1.f;
+        const int mode = (tile[3] >> 16) & 0xf, r = (tile[3] >> 8) & 0xff, s = tile[3] & 0xff;
+        f[26] = (tile[3] >> 20) & 1;
+        f[20] = lg2(tile[0]) / 5;
+        f[21] = lg2(tile[1]) / 7;
+        f[22] = lg2(tile[2]) / 10;
+        f[23] = r / 4.f;
+        f[24] = s / 16.f;
+        f[25] = mode;
+    } else {
+        const double n = a.n;
+        flops = (double)batch * steps * (2 * n * n * n + 2 * n * n);
+        bytes = (double)batch * 2 * n * n * es;
+        f[6] = lg2(n) / 6;
+        f[7] = n / 64;
+        f[8 + (a.layout_a & 1)] = 1.f;
+        f[20] = tile[0] == 1;
+        f[21] = tile[0] == 2;
+        f[22] = tile[0] == 4;
+        f[23] = lg2(tile[1]) / 8;
+        f[24] = lg2(cjg::chain_threads(a.n, tile[0], tile[1])) / 10;
+        f[25] = a.n % 8 == 0;
+        f[26] = steps / 128.f;
+    }
+    f[27] = lg2((double)batch) / 27;
+    f[28] = lg2(flops) / 45;
+    f[29] = lg2(bytes) / 35;
+    f[30] = (float)(std::log2(std::max(flops, 1.0) / std::max(bytes, 1.0)) / 10);
+    f[31] = 1.f;
+}
+
+cj_status candidates(int k, const cj_template_args &a, std::vector<std::array<int, 4>> &out) {
+    out.clear();
+    if (k == CJ_K_LTIMES) ltimes_candidates(a, out);
+    else chain_candidates(a, out);
+    if (out.empty()) return tfail(CJ_ERR_INVALID_ARG, "no candidate tile fits these arguments");
+    return CJ_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// MLP object
+// ---------------------------------------------------------------------------
+struct cj_mlp_s {
+    int F = 0, P = 0, step = 0;
+    float *theta = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr, *loss = nullptr;
+    float *partial = nullptr, *partial_loss = nullptr;
+    int64_t partial_blocks = 0;
+    float *feat = nullptr, *pred = nullptr;   // cost-model query buffers
+    std::mutex mu;
+};
+
+namespace {
+
+std::mutex g_model_mu;
+cj_mlp g_model = nullptr;   // used by cj_specialize for tile = 0 when use_cost_model
+
+uint64_t splitmix(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+size_t grad_smem(int F, int P) {
+    return sizeof(float) * ((size_t)((P + 3) & ~3) + (size_t)BS * F + 3u * BS * H + 2u * BS);
+}
+
+cj_status ensure_partials(cj_mlp m, int64_t blocks) {
+    if (blocks <= m->partial_blocks) return CJ_OK;
+    if (m->partial) cudaFree(m->partial);
+    if (m->partial_loss) cudaFree(m->partial_loss);
+    m->partial = m->partial_loss = nullptr;
+    if (cudaMalloc(&m->partial, sizeof(float) * blocks * m->P) != cudaSuccess ||
+        cudaMalloc(&m->partial_loss, sizeof(float) * blocks) != cudaSuccess) {
+        m->partial_blocks = 0;
+        return tfail(CJ_ERR_OOM, "cost model: could not allocate gradient partials");
+    }
+    m->partial_blocks = blocks;
+    return CJ_OK;
+}
+
+cj_status grad_pass(cj_mlp m, const float *X, const float *t, int64_t B, cudaStream_t st, int apply, float lr,
+                    float *grad_out, float *loss_out) {
+    const int64_t blocks = (B + BS - 1) / BS;
+    cj_status rc = ensure_partials(m, blocks);
+    if (rc != CJ_OK) return rc;
+    const size_t smem = grad_smem(m->F, m->P);
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(cj::mlp_grad_partial<H, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    });
+    cj::mlp_grad_partial<H, BS><<<(unsigned)blocks, BS, smem, st>>>(m->theta, X, t, m->F, B, m->partial,
+                                                                      m->partial_loss);
+    if (apply) m->step++;
+    cj::mlp_reduce_adam<<<(m->P + 255) / 256, 256, 0, st>>>(m->partial, m->partial_loss, (int)blocks, m->P, m->theta,
+                                                           m->m, m->v, grad_out, loss_out, B, m->step, lr, 0.9f,
+                                                           0.999f, 1e-8f, apply);
+    if (cudaGetLastError() != cudaSuccess) return tfail(CJ_ERR_CUDA, "cost model: gradient launch failed");
+    return CJ_OK;
+}
+
+cj_status forward(cj_mlp m, const float *X, int64_t B, float *y, cudaStream_t st) {
+    if (B == 0) return CJ_OK;
+    const size_t smem = sizeof(float) * m->P;
+    cj::mlp_forward<H><<<(unsigned)((B + 127) / 128), 128, smem, st>>>(m->theta, X, y, m->F, B);
+    if (cudaGetLastError() != cudaSuccess) return tfail(CJ_ERR_CUDA, "cost model: forward launch failed");
+    return CJ_OK;
+}
+
+// Predicted log run time of every candidate; returns the argmin.
+cj_status model_choose(cj_mlp m, int k, const cj_template_args &a, int64_t batch, int32_t steps, int *tile_out,
+                       float *pred_out) {
+    if (m->F != CJ_FEATURES) return tfail(CJ_ERR_INVALID_ARG, "cost model must have CJ_FEATURES inputs");
+    std::vector<std::array<int, 4>> cand;
+    cj_status rc = candidates(k, a, cand);
+    if (rc != CJ_OK) return rc;
+    std::vector<float> feat(cand.size() * CJ_FEATURES), pred(cand.size());
+    for (size_t i = 0; i < cand.size(); ++i) featurize(k, a, batch, steps, cand[i].data(), &feat[i * CJ_FEATURES]);
+    std::lock_guard<std::mutex> lk(m->mu);
+    if (!m->feat) {
+        if (cudaMalloc(&m->feat, sizeof(float) * 256 * CJ_FEATURES) != cudaSuccess ||
+            cudaMalloc(&m->pred, sizeof(float) * 256) != cudaSuccess)
+            return tfail(CJ_ERR_OOM, "cost model: query buffers");
+    }
+    if (cand.size() > 256) return tfail(CJ_ERR_INVALID_ARG, "too many candidates");
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+        return tfail(CJ_ERR_CUDA, "cost model: stream");
+    cudaMemcpyAsync(m->feat, feat.data(), sizeof(float) * feat.size(), cudaMemcpyHostToDevice, st);
+    rc = forward(m, m->feat, (int64_t)cand.size(), m->pred, st);
+    if (rc == CJ_OK) cudaMemcpyAsync(pred.data(), m->pred, sizeof(float) * pred.size(), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    if (rc != CJ_OK) return rc;
+    if (e != cudaSuccess) return tfail(CJ_ERR_CUDA, "cost model: query failed");
+    const size_t best = std::min_element(pred.begin(), pred.end()) - pred.begin();
+    std::memcpy(tile_out, cand[best].data(), sizeof(int) * 4);
+    if (pred_out) *pred_out = pred[best];
+    return CJ_OK;
+}
+
+}  // namespace
+
+namespace cjint {
+// Hook used by cj_specialize for tile = {0,0,0,0} when the config enables
+// the cost model and a model is installed.  Hints: chain batch 2^22/n^2
+// instances with T = 64, LTimes 2^21 columns.
+bool cost_model_tile(int k, const cj_template_args &a, int *tile_out) {
+    std::lock_guard<std::mutex> lk(g_model_mu);
+    if (!g_model) return false;
+    const int64_t batch = k == CJ_K_LTIMES ? (int64_t)1 << 21 : std::max<int64_t>(1, ((int64_t)1 << 22) / (a.n * a.n));
+    return model_choose(g_model, k, a, batch, 64, tile_out, nullptr) == CJ_OK;
+}
+}  // namespace cjint
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+CJ_API cj_status cj_candidates(cj_kernel_id k, const cj_template_args *a, int32_t *tiles, int32_t cap,
+                               int32_t *count) {
+    if (!a || !count || (cap > 0 && !tiles)) return tfail(CJ_ERR_INVALID_ARG, "null argument");
+    if (k == CJ_K_UPDATE_CHAIN_GROUPED && a->dtype != CJ_F64 && a->dtype != CJ_F32)
+        return tfail(CJ_ERR_INVALID_ARG, "grouped candidates need f64 or f32");
+    std::vector<std::array<int, 4>> cand;
+    cj_status rc = candidates((int)k, *a, cand);
+    if (rc != CJ_OK) return rc;
+    *count = (int32_t)cand.size();
+    for (int i = 0; i < std::min<int>(cap, (int)cand.size()); ++i) std::memcpy(tiles + 4 * i, cand[i].data(), 16);
+    return CJ_OK;
+}
+
+CJ_API cj_status cj_featurize(cj_kernel_id k, const cj_template_args *a, int64_t batch, int32_t steps,
+                              const int32_t tile[4], float *out) {
+    if (!a || !tile || !out || batch < 0) return tfail(CJ_ERR_INVALID_ARG, "null argument");
+    featurize((int)k, *a, batch, steps, tile, out);
+    return CJ_OK;
+}
+
+CJ_API cj_status cj_autotune(cj_kernel_id k, const cj_template_args *a, void *const *launch_args, int64_t batch,
+                             void *cuda_stream, int32_t reps, int32_t best_tile[4], float *times_ms, int32_t cap,
+                             int32_t *count) {
+    if (!a || !launch_args || !best_tile || !count || reps < 1) return tfail(CJ_ERR_INVALID_ARG, "null argument");
+    std::vector<std::array<int, 4>> cand;
+    cj_status rc = candidates((int)k, *a, cand);
+    if (rc != CJ_OK) return rc;
+    // compile everything first (queued in async mode), then time
+    std::vector<cj_handle> hs(cand.size());
+    for (size_t i = 0; i < cand.size(); ++i) {
+        cj_template_args r = *a;
+        std::memcpy(r.tile, cand[i].data(), 16);
+        r.flags = (r.flags & ~(uint32_t)CJ_FLAG_GENERIC) | CJ_FLAG_NO_AOT;
+        rc = cj_specialize(k, &r, &hs[i]);
+        if (rc != CJ_OK && rc != CJ_ERR_COMPILE) return rc;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    *count = (int32_t)cand.size();
+    for (size_t i = 0; i < cand.size(); ++i) {
+        float ms = INFINITY;
+        if (cj_specialize_wait(hs[i], -1) == CJ_OK) {
+            rc = cj_launch(hs[i], launch_args, batch, cuda_stream);   // warm-up
+            if (rc != CJ_OK) break;
+            std::vector<float> t(reps);
+            for (int r = 0; r < reps; ++r) {
+                cudaEventRecord(e0, st);
+                cj_launch(hs[i], launch_args, batch, cuda_stream);
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&t[r], e0, e1);
+            }
+            std::sort(t.begin(), t.end());
+            ms = t[reps / 2];
+        }
+        if (times_ms && (int)i < cap) times_ms[i] = ms;
+        if (ms < best) {
+            best = ms;
+            std::memcpy(best_tile, cand[i].data(), 16);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != CJ_OK) return rc;
+    if (best >= 1e30f) return tfail(CJ_ERR_COMPILE, "no candidate compiled");
+    return CJ_OK;
+}
+
+CJ_API cj_status cj_mlp_create(int32_t in_features, uint64_t seed, cj_mlp *out) {
+    if (!out || in_features < 1 || in_features > 64) return tfail(CJ_ERR_INVALID_ARG, "in_features must be 1..64");
+    auto *m = new cj_mlp_s();
+    m->F = in_features;
+    m->P = cj::MlpLayout<H>{in_features}.count();
+    const size_t bytes = sizeof(float) * m->P;
+    if (cudaMalloc(&m->theta, bytes) != cudaSuccess || cudaMalloc(&m->m, bytes) != cudaSuccess ||
+        cudaMalloc(&m->v, bytes) != cudaSuccess || cudaMalloc(&m->grad, bytes) != cudaSuccess ||
+        cudaMalloc(&m->loss, sizeof(float)) != cudaSuccess) {
+        cj_mlp_destroy(m);
+        return tfail(CJ_ERR_OOM, "cost model: parameter allocation failed");
+    }
+    // uniform(-s, s) weights with s = sqrt(3 / fan_in) (unit-variance inputs keep unit variance), zero biases
+    std::vector<float> h(m->P, 0.f);
+    const cj::MlpLayout<H> L{in_features};
+    auto fill = [&](int off, int cnt, int fan_in, uint64_t stream) {
+        const double s = std::sqrt(3.0 / fan_in);
+        for (int i = 0; i < cnt; ++i) {
+            const double u = (double)(splitmix(seed + stream, (uint64_t)i) >> 11) * 0x1.0p-53;
+            h[off + i] = (float)((2 * u - 1) * s);
+        }
+    };
+    fill(L.w1(), H * in_features, in_features, 1);
+    fill(L.w2(), H * H, H, 2);
+    fill(L.w3(), H, H, 3);
+    cj_status rc = cj_mlp_set_params(m, h.data(), m->P);
+    if (rc != CJ_OK) {
+        cj_mlp_destroy(m);
+        return rc;
+    }
+    *out = m;
+    return CJ_OK;
+}
+
+CJ_API cj_status cj_mlp_set_params(cj_mlp m, const float *host, int64_t count) {
+    if (!m || !host || count != m->P) return tfail(CJ_ERR_INVALID_ARG, "parameter count mismatch");
+    if (cudaMemcpy(m->theta, host, sizeof(float) * m->P, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(m->m, 0, sizeof(float) * m->P) != cudaSuccess ||
+        cudaMemset(m->v, 0, sizeof(float) * m->P) != cudaSuccess)
+        return tfail(CJ_ERR_CUDA, "cost model: parameter upload failed");
+    m->step = 0;
+    return CJ_OK;
+}
+
+CJ_API cj_status cj_mlp_get_params(cj_mlp m, float *host, int64_t cap, int64_t *count) {
+    if (!m || !count) return tfail(CJ_ERR_INVALID_ARG, "null argument");
+    *count = m->P;
+    if (host && cap >= m->P &&
+        cudaMemcpy(host, m->theta, sizeof(float) * m->P, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return tfail(CJ_ERR_CUDA, "cost model: parameter download failed");
+    return CJ_OK;
+}
+
+CJ_API cj_status cj_mlp_forward(cj_mlp m, const float *X, int64_t B, float *y, void *cuda_stream) {
+    if (!m || B < 0 || (B > 0 && (!X || !y))) return tfail(CJ_ERR_INVALID_ARG, "null argument");
+    return forward(m, X, B, y, reinterpret_cast<cudaStream_t>(cuda_stream));
+}
+
+CJ_API cj_status cj_mlp_grad(cj_mlp m, const float *X, const float *t, int64_t B, float *grad, float *loss,
+                             void *cuda_stream) {
+    if (!m || B < 1 || !X || !t || !grad) return tfail(CJ_ERR_INVALID_ARG, "null argument");
+    return grad_pass(m, X, t, B, reinterpret_cast<cudaStream_t>(cuda_stream), 0, 0.f, grad, loss);
+}
+
+CJ_API cj_status cj_mlp_train_step(cj_mlp m, const float *X, const float *t, int64_t B, float lr, float *loss,
+                                   void *cuda_stream) {
+    if (!m || B < 1 || !X || !t || lr <= 0.f) return tfail(CJ_ERR_INVALID_ARG, "bad argument");
+    return grad_pass(m, X, t, B, reinterpret_cast<cudaStream_t>(cuda_stream), 1, lr, m->grad, loss);
+}
+
+CJ_API cj_status cj_mlp_destroy(cj_mlp m) {
+    if (!m) return tfail(CJ_ERR_INVALID_ARG, "null model");
+    {
+        std::lock_guard<std::mutex> lk(g_model_mu);
+        if (g_model == m) g_model = nullptr;
+    }
+    for (float *p : {m->theta, m->m, m->v, m->grad, m->loss, m->partial, m->partial_loss, m->feat, m->pred})
+        if (p) cudaFree(p);
+    delete m;
+    return CJ_OK;
+}
+
+CJ_API cj_status cj_cost_model_use(cj_mlp m) {
+    if (m && m->F != CJ_FEATURES) return tfail(CJ_ERR_INVALID_ARG, "cost model must have CJ_FEATURES inputs");
+    std::lock_guard<std::mutex> lk(g_model_mu);
+    g_model = m;
+    return CJ_OK;
+}
+
+CJ_API cj_status cj_choose_tile(cj_kernel_id k, const cj_template_args *a, int64_t batch, int32_t steps,
+                                int32_t tile_out[4], float *predicted) {
+    if (!a || !tile_out || batch < 1) return tfail(CJ_ERR_INVALID_ARG, "null argument");
+    std::lock_guard<std::mutex> lk(g_model_mu);
+    if (!g_model) return tfail(CJ_ERR_INVALID_ARG, "no cost model installed (cj_cost_model_use)");
+    return model_choose(g_model, (int)k, *a, batch, steps, tile_out, predicted);
+}

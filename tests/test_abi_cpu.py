@@ -9,6 +9,7 @@ import subprocess
 import sys
 import textwrap
 
+import numpy as np
 import pytest
 
 from conftest import ROOT
@@ -86,11 +87,16 @@ def test_aot_sizes_are_not_compiled(compile_only_sync):
     dict(kernel=cj.K_UPDATE_CHAIN, dtype=cj.F64, n=4, layout_a=2),
     dict(kernel=cj.K_UPDATE_CHAIN, dtype=5, n=4),
     dict(kernel=cj.K_UPDATE_CHAIN, dtype=cj.F64, n=12, tile=(2, 64, 0, 0)),
+    dict(kernel=cj.K_UPDATE_CHAIN, dtype=cj.F32, n=16, tile=(4, 2, 0, 0)),
+    dict(kernel=cj.K_UPDATE_CHAIN, dtype=cj.F64, n=12, tile=(4, 2, 0, 0)),
+    dict(kernel=cj.K_UPDATE_CHAIN, dtype=cj.F64, n=40, tile=(4, 1, 0, 0)),
     dict(kernel=cj.K_UPDATE_CHAIN, dtype=cj.F64, n=8, flags=0x40),
     dict(kernel=cj.K_LTIMES, dtype=cj.F64, layout_a=6, m=36, d=96),
     dict(kernel=cj.K_LTIMES, dtype=cj.F64, m=0, d=96),
     dict(kernel=cj.K_LTIMES, dtype=cj.F32, m=36, d=96, tile=(1, 128, 97, (4 << 8) | 12)),
     dict(kernel=cj.K_LTIMES, dtype=cj.BF16, m=36, d=96),
+    dict(kernel=cj.K_LTIMES, dtype=cj.F32, m=36, d=96, tile=(1, 64, 128, (1 << 16) | (2 << 8) | 8)),
+    dict(kernel=cj.K_LTIMES, dtype=cj.F64, m=36, d=95, tile=(1, 64, 128, (1 << 16) | (2 << 8) | 8)),
     dict(kernel=9, dtype=cj.F64, n=4),
 ])
 def test_invalid_arguments(compile_only_sync, kw):
@@ -194,3 +200,23 @@ def test_compiles_open_no_file_when_pwd_is_set(tmp_path):
     count, calls = _run_nofs(tmp_path, unset_pwd=False)
     assert all(c.split()[0] in ("stat", "lstat") for c in calls), calls
     assert {c.split(" ", 1)[1] for c in calls} <= {".", os.getcwd()}, calls
+
+
+@pytest.mark.parametrize("req", [
+    dict(kernel=cj.K_UPDATE_CHAIN, dtype=cj.F64, n=3),
+    dict(kernel=cj.K_UPDATE_CHAIN, dtype=cj.F64, n=16),
+    dict(kernel=cj.K_UPDATE_CHAIN, dtype=cj.F32, n=64),
+    dict(kernel=cj.K_LTIMES, dtype=cj.F64, layout_a=1, layout_b=3, m=36, d=96),
+    dict(kernel=cj.K_LTIMES, dtype=cj.F32, layout_a=4, layout_b=0, m=36, d=96),
+])
+def test_every_candidate_tile_is_a_valid_request(compile_only_sync, req):
+    k = req.pop("kernel")
+    cands = cj.candidates(k, **req)
+    assert 2 <= len(cands) <= 16
+    assert len(set(cands)) == len(cands)
+    for tile in cands[:3]:
+        h = cj.specialize(k, tile=tile, **req)      # compiles in compile-only mode
+        assert h.variant in ("jit", "aot")         # the default tile may be an AoT kernel
+    for tile in cands:
+        f = cj.featurize(k, batch=1 << 16, steps=64, tile=tile, **req)
+        assert f.shape == (cj.FEATURES,) and np.all(np.isfinite(f)) and f[31] == 1.0

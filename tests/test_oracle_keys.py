@@ -5,16 +5,18 @@ from oracle import keys as K
 
 
 def test_hand_assembled_chain_key():
-    # kernel 1, f64, row-major, n=8, default tile (1, 32, 0, 0), no flags
+    # kernel 1, f64, row-major, n=8, default tile (4, 8, 0, 0) (FP64 tensor-core
+    # panels, 64 / n instances per block), no flags
     expect = bytes.fromhex("0100" "00" "00" "00" "00" "0800" "0000" "0000"
-                           "01000000" "20000000" "00000000" "00000000" "00000000")
+                           "04000000" "08000000" "00000000" "00000000" "00000000")
     assert K.canonical_key(K.K_UPDATE_CHAIN, K.F64, n=8) == expect
 
 
 def test_hand_assembled_ltimes_key():
-    # kernel 2, f32, in GZD(3), out ZGD(5), m=36, d=96, tile (1,128,96,(4<<8)|12)
+    # kernel 2, f32, in GZD(3), out ZGD(5), m=36, d=96, default tile
+    # (1, 64, 96, (1 << 20) | (2 << 8) | 12): 64 columns, pipelined, R 2, S 12
     expect = bytes.fromhex("0200" "01" "03" "05" "00" "0000" "2400" "6000"
-                           "01000000" "80000000" "60000000" "0c040000" "00000000")
+                           "01000000" "40000000" "60000000" "0c021000" "00000000")
     assert K.canonical_key(K.K_LTIMES, K.F32, layout_a=3, layout_b=5, m=36, d=96) == expect
 
 

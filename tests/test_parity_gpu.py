@@ -91,6 +91,25 @@ def test_update_chain_explicit_tiles(n, tile):
     assert relF_per_instance(run_chain(h, A, steps, cj.F64), ref) <= TOL64
 
 
+@pytest.mark.parametrize("n", [8, 16, 24, 32])
+@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("ipb", [1, 3])
+def test_update_chain_fp64_tensor_core_tiles(n, layout, ipb):
+    """Mapping 4 (mma.sync m8n8k4 panels) against the oracle and against the
+    FMA-pipe mapping 1 on the same inputs."""
+    steps = 64
+    batch = oracle_batch(n, steps) + 5
+    A = synth.chain_inputs_np(synth.SEED_CHAIN_SWEEP, batch, n, layout=layout)
+    ref = oracle.update_chain(A, steps, layout=layout, nthreads=8)
+    h4 = cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=n, layout_a=layout, tile=(4, ipb, 0, 0))
+    h1 = cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=n, layout_a=layout, tile=(1, 8, 0, 0))
+    x4 = run_chain(h4, A, steps, cj.F64)
+    x1 = run_chain(h1, A, steps, cj.F64)
+    assert relF_per_instance(x4, ref) <= TOL64
+    assert relF_per_instance(x1, ref) <= TOL64
+    assert relF_per_instance(x4, x1) <= TOL64
+
+
 @pytest.mark.parametrize("n", [3, 8, 16, 32, 48, 64])
 @pytest.mark.parametrize("generic", [False, True])
 def test_update_chain_f32_error(n, generic):
@@ -191,6 +210,10 @@ def test_ltimes_generic(lt_small, lin, lout, dt):
     (36, 96, 32, 64, 2, 2, (4, 16, 192, (1 << 8) | 12)),
     (36, 96, 32, 64, 1, 4, (32, 2, 64, (1 << 8) | 36)),
     (64, 128, 2, 40, 3, 0, (1, 32, 256, (1 << 8) | 8)),
+    (36, 96, 32, 64, 0, 3, (1, 64, 256, (1 << 8) | 9)),                       # FMA pipe, f64
+    (36, 96, 32, 64, 4, 5, (32, 2, 256, (1 << 16) | (1 << 8) | 8)),           # tensor cores, R = 1
+    (36, 96, 5, 37, 2, 1, (8, 16, 64, (1 << 16) | (4 << 8) | 8)),             # tensor cores, R = 4, ragged
+    (40, 8, 3, 100, 5, 0, (1, 64, 128, (1 << 16) | (2 << 8) | 8)),            # M multiple of 8
 ])
 def test_ltimes_shapes_and_tiles(M, D, G, Z, lin, lout, tile):
     L, x = synth.ltimes_inputs_np(synth.SEED_LTIMES, M, D, G, Z)
