@@ -88,10 +88,9 @@ void ltimes_candidates(const cj_template_args &a, std::vector<std::array<int, 4>
             push(tg, 64, 0, 1, 9);
             push(tg, 64, 0, 1, 12);
         } else {
-            for (int pipe : {1, 0})
-                for (int ct : {64, 128})
-                    for (auto rs : {std::pair<int, int>{2, 12}, {4, 12}, {4, 9}})
-                        push(tg, ct, 0, rs.first, rs.second, pipe);
+            for (int ct : {64, 128})
+                for (auto rs : {std::pair<int, int>{2, 12}, {4, 12}, {4, 9}}) push(tg, ct, 0, rs.first, rs.second, 1);
+            push(tg, 128, 0, 4, 12, 0);   // unpipelined baseline
         }
     }
 }
