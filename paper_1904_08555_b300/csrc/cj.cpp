@@ -948,7 +948,7 @@ CJ_API cj_status cj_group_plan_create(int32_t dtype, int64_t count, const int32_
         plan_free(p);
         return fail(CJ_ERR_CUDA, "grouped plan: work list upload failed");
     }
-    const size_t ns = std::min<size_t>(8, ng);
+    const size_t ns = std::min<size_t>(64, ng);   // one stream per group: groups run concurrently
     p->streams.resize(ns);
     p->join.resize(ns);
     for (size_t i = 0; i < ns; ++i) {
