@@ -380,16 +380,18 @@ def main():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=("cj", "reference"), default="cj")
-    p.add_argument("--workload", choices=("sweep", "small", "sweep32", "ltimes", "uneven", "kernel"),
+    p.add_argument("--workload", choices=("sweep", "small", "sweep32", "ltimes", "uneven", "kernel", "costmodel"),
                    default="sweep",
                    help="sweep (default): the FP64 size sweep; the others are secondary measurements")
-    p.add_argument("--dtype", choices=("f64", "f32"), default="f64", help="ltimes / uneven precision")
+    p.add_argument("--dtype", choices=("f64", "f32", "bf16"), default="f64", help="ltimes / uneven precision")
     p.add_argument("--ltimes-z", type=int, default=1 << 18)
     p.add_argument("--kernel", choices=("chain", "chain-generic", "ltimes", "ltimes-generic"), default="chain")
     p.add_argument("--n", type=int, default=32)
     p.add_argument("--batch", type=int, default=16384)
     p.add_argument("--layout-in", type=int, default=0)
     p.add_argument("--layout-out", type=int, default=0)
+    p.add_argument("--heldout", type=int, default=2000)
+    p.add_argument("--train-steps", type=int, default=4000)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=60.0,
                    help="oracle time budget: reference arm whole run; cpu_baseline leg uses a quarter")
@@ -423,7 +425,10 @@ def secondary(args):
     import torch
     from paper_1904_08555_b300 import cj
     torch.cuda.set_device(0)
-    cj.init(sync=True, compile_threads=4)
+    if args.workload == "costmodel":
+        cj.init(sync=False, compile_threads=os.cpu_count() or 4)
+    else:
+        cj.init(sync=True, compile_threads=4)
     stream = torch.cuda.Stream()
     sampler = ClockSampler(0)
     sampler.start()
@@ -517,7 +522,7 @@ def secondary(args):
                     "config": {"workload": f"LTimes out[m][g][z] = sum_d L[m][d] in[d][g][z], M=36 D=96 G=32 Z={Z}, "
                                            f"all 36 (in, out) storage orders, {args.dtype}"}})
     elif args.workload == "uneven":
-        dt = cj.F64 if args.dtype == "f64" else cj.F32
+        dt = {"f64": cj.F64, "f32": cj.F32, "bf16": cj.BF16}[args.dtype]
         tdt = torch.float64 if dt == cj.F64 else torch.float32
         n, t = synth.uneven_sizes(synth.SEED_UNEVEN, 10000)
         pool, off = synth.uneven_inputs_np(synth.SEED_UNEVEN, n)
@@ -531,7 +536,7 @@ def secondary(args):
             _events(torch, stream, fn, W)
             res[name] = _events(torch, stream, fn, max(K, 10))
             plan.destroy()
-        peak = PEAK_TFLOPS[args.dtype]
+        peak = PEAK_TFLOPS["f32" if args.dtype == "bf16" else args.dtype]
         out.update({"value": f / res["spec"] / 1e6, "dtype": args.dtype,
                     "generic": {"value": f / res["generic"] / 1e6, "unit": "GFLOP/s", "ms": res["generic"]},
                     "ms_per_launch": res["spec"], "speedup_vs_generic": res["generic"] / res["spec"],
@@ -571,6 +576,16 @@ def secondary(args):
         ms = _events(torch, stream, fn, K)
         out.update({"value": f / ms / 1e6, "dtype": args.dtype, "ms_per_launch": ms, "regs": h.regs()[0],
                     "config": {"workload": desc}})
+    elif args.workload == "costmodel":
+        from paper_1904_08555_b300 import costmodel
+        res = costmodel.run(n_heldout=args.heldout, train_steps=args.train_steps, log=lambda m: print(m, file=sys.stderr))
+        rg = res["regret"]
+        out.update({"metric": "cost-model regret t(chosen)/t(best exhaustive) - 1, geometric mean over held-out requests",
+                    "value": rg["model"]["geomean"], "unit": "fraction", "higher_is_better": False,
+                    "dtype": "f32 (network); f64/f32 kernels", "result": res,
+                    "config": {"workload": f"{res['heldout_requests']} held-out specialization requests (seed 0xC1A5): "
+                                           "chain/LTimes 50/50, N uniform in [2,64], orders uniform, f64/f32; chain "
+                                           "batch 2^22/N^2, T 64; LTimes M 36 D 96 G 32 Z 2^16"}})
     out["clocks"] = sampler.stop()
     st = cj.stats()
     out["jit_compile_ms_p50"] = st["compile_ms_p50"]

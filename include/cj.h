@@ -105,7 +105,9 @@ typedef struct {
  *     n in {8, 16, 24, 32}).
  *     Default: f64 with n in {8, 16, 24, 32} -> {4, max(1, 64 / n)};
  *     n <= 4 -> {2, 128}; n <= 32 -> {1, max(1, 256 / n)};
- *     else {1, max(1, 128 / n)}; bf16 -> {3, 1}.
+ *     else {1, max(1, 128 / n)}; bf16 -> {3, max(1, 128 / n16)} with n16 = n
+ *     rounded up to a multiple of 16 (mapping 3: one warp per 16 rows,
+ *     bf16 operands, fp32 accumulate and state).
  *   LTimes: {TG, TZ, threads, (PIPE << 20) | (MODE << 16) | (R << 8) | S}: a block stages a
  *     TG x TZ box of (g, z) columns with all d in shared memory.  MODE 0: each
  *     thread accumulates R columns x S moments on the FMA pipe (the last
@@ -196,7 +198,8 @@ cj_status cj_handle_regs(cj_handle h, int *regs_per_thread, int *static_smem);
  * n[j]^2 over j < k.  The plan groups instances by n, requests one
  * UPDATE_CHAIN_GROUPED instantiation per group (tile 0 = default), orders
  * each group's items by T descending, and keeps work lists and counters in
- * device memory it owns.  dtype: CJ_F64 or CJ_F32.  flags: 0, or
+ * device memory it owns.  dtype: CJ_F64, CJ_F32 or CJ_BF16 (pools in fp32;
+ * groups with n >= 16 on bf16 tensor cores, the others in fp32).  flags: 0, or
  * CJ_FLAG_GENERIC to run every group on the generic grouped kernel.
  */
 typedef struct cj_group_plan_s *cj_group_plan;

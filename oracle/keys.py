@@ -28,7 +28,8 @@ Default tile resolution (tile all zero, no cost model):
                                        else   -> (1 = row per thread, ipb, 0, 0)
                                        with ipb = max(1, 256 // n) for n <= 32,
                                        max(1, 128 // n) above
-  update chain, bf16:                  (3 = tensor-core warp tile, 1, 0, 0)
+  update chain, bf16:                  (3 = bf16 tensor-core panels, max(1, 128 // n16), 0, 0),
+                                       n16 = n rounded up to a multiple of 16
   LTimes: (TG, TZ, threads, (PIPE << 20) | (MODE << 16) | (R << 8) | S), CT = 64
       columns; orders 1, 4 are g-fast and 0, 2 z-fast; TG = 1 if neither in
       nor out is g-fast, 8 if one is g-fast and the other z-fast, else 32;
@@ -67,7 +68,7 @@ def default_tile(kernel: int, dtype: int, n: int, layout_a: int = 0, layout_b: i
                  d: int = 96) -> tuple:
     if kernel in (K_UPDATE_CHAIN, K_UPDATE_CHAIN_GROUPED):
         if dtype == BF16:
-            return (3, 1, 0, 0)
+            return (3, max(1, 128 // (-(-n // 16) * 16)), 0, 0)
         if dtype == F64 and n % 8 == 0 and n <= 32:
             return (4, max(1, 64 // n), 0, 0)
         if n <= 4:

@@ -261,8 +261,7 @@ cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_
         if (a.n < 1 || a.n > 64) return fail(CJ_ERR_INVALID_ARG, "n = %d outside 1..64", a.n);
         if (k == CJ_K_UPDATE_CHAIN_GROUPED) a.layout_a = 0;
         if (a.layout_a != 0 && a.layout_a != 1) return fail(CJ_ERR_INVALID_ARG, "layout %d must be 0 or 1", a.layout_a);
-        if (a.dtype == CJ_BF16)
-            return fail(CJ_ERR_INVALID_ARG, "the bf16 tensor-core update chain is not available in this build");
+        if (a.dtype == CJ_BF16 && a.n < 16) return fail(CJ_ERR_INVALID_ARG, "bf16 needs n >= 16");
         a.m = a.d = a.layout_b = 0;
     }
     if (a.flags & CJ_FLAG_GENERIC) {
@@ -295,8 +294,9 @@ cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_
     // explicit tiles: check the kernel can be instantiated and launched
     if (k != CJ_K_LTIMES) {
         const int map = a.tile[0], ipb = a.tile[1];
-        if (map != 1 && map != 2 && map != 4)
-            return fail(CJ_ERR_INVALID_ARG, "update chain mapping %d must be 1, 2 or 4", map);
+        if (map < 1 || map > 4) return fail(CJ_ERR_INVALID_ARG, "update chain mapping %d must be 1..4", map);
+        if ((map == 3) != (a.dtype == CJ_BF16))
+            return fail(CJ_ERR_INVALID_ARG, "mapping 3 (bf16 tensor cores) is the only mapping of dtype bf16");
         if (map == 2 && a.n > 8) return fail(CJ_ERR_INVALID_ARG, "mapping 2 needs n <= 8");
         if (map == 4 && !cjint::chain_dmma_ok(a.n, a.dtype))
             return fail(CJ_ERR_INVALID_ARG, "mapping 4 (FP64 tensor cores) needs f64 and n in {8, 16, 24, 32}");
@@ -889,7 +889,8 @@ CJ_API cj_status cj_group_plan_create(int32_t dtype, int64_t count, const int32_
     if (G.compile_only) return fail(CJ_ERR_NO_DEVICE, "compile-only mode");
     if (!out || count < 0 || (count > 0 && (!n || !steps)))
         return fail(CJ_ERR_INVALID_ARG, "null output or inputs");
-    if (dtype != CJ_F64 && dtype != CJ_F32) return fail(CJ_ERR_INVALID_ARG, "grouped plans support f64 and f32");
+    if (dtype != CJ_F64 && dtype != CJ_F32 && dtype != CJ_BF16)
+        return fail(CJ_ERR_INVALID_ARG, "grouped plans support f64, f32 and bf16");
     if (flags & ~CJ_FLAG_GENERIC) return fail(CJ_ERR_INVALID_ARG, "grouped plans accept only CJ_FLAG_GENERIC");
     for (int64_t k = 0; k < count; ++k)
         if (n[k] < 1 || n[k] > 64 || steps[k] < 1) return fail(CJ_ERR_INVALID_ARG, "instance %lld out of range", (long long)k);
@@ -928,7 +929,7 @@ CJ_API cj_status cj_group_plan_create(int32_t dtype, int64_t count, const int32_
                      [](const cj_group_plan_s::Group &x, const cj_group_plan_s::Group &y) { return x.cost > y.cost; });
     for (auto &g : p->groups) {
         cj_template_args a{};
-        a.dtype = dtype;
+        a.dtype = (dtype == CJ_BF16 && g.n < 16) ? CJ_F32 : dtype;   // bf16 runs n >= 16 on tensor cores
         a.n = g.n;
         a.flags = flags;
         cj_status rc = cj_specialize(CJ_K_UPDATE_CHAIN_GROUPED, &a, &g.h);

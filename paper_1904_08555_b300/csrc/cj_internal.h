@@ -18,7 +18,7 @@ constexpr int chain_default_map(int n, int dtype) {
     return dtype == D_BF16 ? 3 : chain_dmma_ok(n, dtype) ? 4 : (n <= 4 ? 2 : 1);
 }
 constexpr int chain_default_ipb(int n, int dtype) {
-    return dtype == D_BF16 ? 1
+    return dtype == D_BF16 ? (128 / ((n + 15) / 16 * 16) > 1 ? 128 / ((n + 15) / 16 * 16) : 1)
          : chain_dmma_ok(n, dtype) ? (64 / n > 1 ? 64 / n : 1)
          : n <= 4 ? 128 : n <= 32 ? 256 / n : (128 / n > 1 ? 128 / n : 1);
 }

@@ -26,9 +26,13 @@ CJ_HD constexpr int row_pitch(int nn, int esize) {
 CJ_HD constexpr int inst_pitch(int nn) { return nn | 1; }
 
 // Threads per block of the update chain kernels: mapping 2 one thread per
-// instance, mapping 4 one warp per 8 rows, mapping 1 one thread per row.
+// instance, mapping 4 one warp per 8 rows, mapping 3 one warp per 16 rows
+// (padded), mapping 1 one thread per row.
 CJ_HD constexpr int chain_threads(int n, int mapping, int ipb) {
-    return mapping == 2 ? ipb : mapping == 4 ? ipb * (n / 8) * 32 : ((ipb * n + 31) / 32) * 32;
+    return mapping == 2   ? ipb
+           : mapping == 4 ? ipb * (n / 8) * 32
+           : mapping == 3 ? ipb * ((n + 15) / 16) * 32
+                          : ((ipb * n + 31) / 32) * 32;
 }
 
 // Rows of X kept in shared memory (instead of registers) above this size.

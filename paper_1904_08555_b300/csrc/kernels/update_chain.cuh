@@ -182,13 +182,101 @@ __device__ __forceinline__ void panel_chain_dmma(const double* a_s, int panel, i
     }
 }
 
+// BF16 tensor cores (mapping 3, N >= 16, FP32 state): one warp owns a
+// 16-row panel of X (dimensions padded to multiples of 16 with zeros, which
+// keeps the padded rows and columns of X at zero) and computes
+// P = bf16(X_panel) bf16(A) with mma.sync m16n8k16 (bf16 in, fp32
+// accumulate), then X += c P in fp32.  Fragment layouts (PTX ISA, m16n8k16):
+// accumulator c0,c1 at (row g, cols 2t, 2t+1), c2,c3 at (row g+8, same
+// cols) with g = lane/4, t = lane%4; the A operand of k-tile kt is exactly
+// the accumulators of n-tiles 2kt and 2kt+1 rounded to bf16 and packed in
+// pairs, so the state never leaves registers.  B operand (A_b): registers
+// {A[k=2t][n=g], A[2t+1][g]} and {A[2t+8][g], A[2t+9][g]} per tile.
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
+    unsigned r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int N>
+__device__ __forceinline__ void panel_chain_bf16(const float* a_s, int panel, int steps, float cc,
+                                                 float (&x)[((N + 15) / 16) * 2][4]) {
+    constexpr int NP = ((N + 15) / 16) * 16;
+    constexpr int KT = NP / 16, NT = NP / 8;
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    auto A = [&](int l, int j) -> float { return (l < N && j < N) ? a_s[l * N + j] : 0.f; };
+    unsigned b[KT][NT][2];
+#pragma unroll
+    for (int kt = 0; kt < KT; ++kt)
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+            const int n = 8 * j + g, k0 = 16 * kt + 2 * t;
+            b[kt][j][0] = pack_bf16(A(k0, n), A(k0 + 1, n));
+            b[kt][j][1] = pack_bf16(A(k0 + 8, n), A(k0 + 9, n));
+        }
+    const int r0 = 16 * panel + g, r1 = r0 + 8;
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+        const int c = 8 * j + 2 * t;
+        x[j][0] = (r0 < N && r0 == c) ? 1.f : 0.f;
+        x[j][1] = (r0 < N && r0 == c + 1) ? 1.f : 0.f;
+        x[j][2] = (r1 < N && r1 == c) ? 1.f : 0.f;
+        x[j][3] = (r1 < N && r1 == c + 1) ? 1.f : 0.f;
+    }
+    for (int k = 0; k < steps; ++k) {
+        unsigned a[KT][4];
+#pragma unroll
+        for (int kt = 0; kt < KT; ++kt) {
+            a[kt][0] = pack_bf16(x[2 * kt][0], x[2 * kt][1]);
+            a[kt][1] = pack_bf16(x[2 * kt][2], x[2 * kt][3]);
+            a[kt][2] = pack_bf16(x[2 * kt + 1][0], x[2 * kt + 1][1]);
+            a[kt][3] = pack_bf16(x[2 * kt + 1][2], x[2 * kt + 1][3]);
+        }
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+            float p[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int kt = 0; kt < KT; ++kt) mma_bf16_16816(p, a[kt], b[kt][j][0], b[kt][j][1]);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) x[j][i] = __fmaf_rn(cc, p[i], x[j][i]);
+        }
+    }
+}
+
 // Run the chain for the `ninst` instances staged at sA (pitch per geometry.h)
 // and leave each X_T in place of its A, in storage order LAYOUT.
 // steps_of(inst) and c_of(inst) give the per-instance T and c.
 template <class T, int N, int LAYOUT, int MAP, int IPB, class StepsOf, class COf>
 __device__ __forceinline__ void chain_block(T* sA, int ninst, int tid, StepsOf steps_of, COf c_of) {
     constexpr int NN = N * N;
-    if constexpr (MAP == 4) {
+    if constexpr (MAP == 3) {
+        static_assert(sizeof(T) == 4 && N >= 16, "mapping 3 is bf16 operands with fp32 state, N >= 16");
+        constexpr int P = cjg::row_pitch(NN, 4);
+        constexpr int NPAN = (N + 15) / 16;
+        const int warp = tid >> 5;
+        const int inst = warp / NPAN, panel = warp - inst * NPAN;
+        const bool active = inst < ninst;   // uniform across the warp
+        float x[NPAN * 2][4];
+        if (active) panel_chain_bf16<N>(sA + inst * P, panel, steps_of(inst), (float)c_of(inst), x);
+        __syncthreads();
+        if (active) {
+            const int lane = tid & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+            for (int j = 0; j < NPAN * 2; ++j)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int row = 16 * panel + g + (i >= 2 ? 8 : 0), col = 8 * j + 2 * t + (i & 1);
+                    if (row < N && col < N) sA[inst * P + (LAYOUT == 0 ? row * N + col : col * N + row)] = x[j][i];
+                }
+        }
+    } else if constexpr (MAP == 4) {
         static_assert(sizeof(T) == 8 && N % 8 == 0 && N <= 32, "mapping 4 is FP64 with N = 8, 16, 24, 32");
         constexpr int P = cjg::row_pitch(NN, 8);
         constexpr int NB = N / 8;
