@@ -217,11 +217,12 @@ cj_status cj_group_plan_launch(cj_group_plan p, const void *A_pool, void *X_pool
 cj_status cj_group_plan_info(cj_group_plan p, int32_t *n_groups, int64_t *pool_elems);
 cj_status cj_group_plan_destroy(cj_group_plan p);
 
-/* Measured FMA throughput of this GPU in TFLOP/s (2 flops per FMA) for
- * dtype CJ_F64 or CJ_F32: a kernel of independent fused multiply-add chains
- * over every SM, timed with CUDA events on cuda_stream.  Used as the
- * roofline denominator of the FP64/FP32 arithmetic-bound kernels. */
-cj_status cj_measure_fma_peak(int32_t dtype, void *cuda_stream, double *tflops);
+/* Measured throughput of this GPU in TFLOP/s (2 flops per multiply-add) for
+ * dtype CJ_F64 or CJ_F32: tensor = 0, independent fused multiply-add chains
+ * over every SM; tensor = 1 (f64 only), independent mma.sync m8n8k4 FP64
+ * tensor-core chains.  Timed with CUDA events on cuda_stream.  The roofline
+ * denominators of the arithmetic-bound kernels. */
+cj_status cj_measure_fma_peak(int32_t dtype, int32_t tensor, void *cuda_stream, double *tflops);
 
 /*
  * Allocation-free uneven update chain.  The paper has no counterpart: this

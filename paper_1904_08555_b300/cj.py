@@ -79,7 +79,7 @@ def load():
         L.cj_group_plan_launch.argtypes = [P, P, P, P, ctypes.c_int]
         L.cj_group_plan_info.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i64)]
         L.cj_group_plan_destroy.argtypes = [P]
-        L.cj_measure_fma_peak.argtypes = [i32, P, ctypes.POINTER(ctypes.c_double)]
+        L.cj_measure_fma_peak.argtypes = [i32, i32, P, ctypes.POINTER(ctypes.c_double)]
         L.cj_update_chain_uneven_noalloc.argtypes = [i32, i64, P, P, P, P, P]
         TA = ctypes.POINTER(TemplateArgs)
         L.cj_candidates.argtypes = [ctypes.c_int, TA, P, i32, ctypes.POINTER(i32)]
@@ -214,10 +214,11 @@ def launch_grouped(h: Handle, items, A_pool, X_pool, counter, n_items: int, stre
     _launch(h, vals, n_items, _stream(stream, A_pool, X_pool))
 
 
-def measure_fma_peak(dtype: int, stream=None) -> float:
-    """Measured FMA throughput (TFLOP/s) for F64 or F32 on the current device."""
+def measure_fma_peak(dtype: int, stream=None, tensor: bool = False) -> float:
+    """Measured throughput (TFLOP/s) for F64 or F32; tensor=True: FP64 mma.sync."""
     out = ctypes.c_double(0.0)
-    _check(load().cj_measure_fma_peak(dtype, _stream(stream), ctypes.byref(out)), "cj_measure_fma_peak")
+    _check(load().cj_measure_fma_peak(dtype, int(tensor), _stream(stream), ctypes.byref(out)),
+           "cj_measure_fma_peak")
     return out.value
 
 

@@ -48,10 +48,35 @@ __global__ void __launch_bounds__(256) peak_fma(int iters, T a, T b) {
     if (s == (T)-123456.0) cj_peak_sink = (double)s;
 }
 
+// FP64 tensor-core rate: 8 independent mma.sync m8n8k4 accumulators per
+// warp (512 FMA per instruction); the same never-taken store.
+template <class T>
+__global__ void __launch_bounds__(256) peak_dmma(int iters, T a0, T b0) {
+    double c[8][2];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        c[i][0] = threadIdx.x * 1e-3;
+        c[i][1] = i * 1e-3;
+    }
+    const double a = a0 + threadIdx.x * 1e-9, b = b0;
+    for (int k = 0; k < iters; ++k) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                         : "+d"(c[i][0]), "+d"(c[i][1])
+                         : "d"(a), "d"(b));
+    }
+    double s = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += c[i][0] + c[i][1];
+    if (s == -123456.0) cj_peak_sink = s;
+}
+
 namespace cjint {
 const void *peak_fma_kernel(int dtype) {
     return dtype == D_F64 ? (const void *)&peak_fma<double> : (const void *)&peak_fma<float>;
 }
+const void *peak_dmma_kernel() { return (const void *)&peak_dmma<double>; }
 const AotKernel *aot_table(int *count) {
     *count = (int)(sizeof(kAotTable) / sizeof(kAotTable[0]));
     return kAotTable;

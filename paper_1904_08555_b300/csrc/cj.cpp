@@ -1019,14 +1019,15 @@ CJ_API cj_status cj_group_plan_destroy(cj_group_plan p) {
     return CJ_OK;
 }
 
-CJ_API cj_status cj_measure_fma_peak(int32_t dtype, void *cuda_stream, double *tflops) {
+CJ_API cj_status cj_measure_fma_peak(int32_t dtype, int32_t tensor, void *cuda_stream, double *tflops) {
     if (!G.inited) return fail(CJ_ERR_NOT_INITIALIZED, "cj_init has not been called");
     if (G.compile_only) return fail(CJ_ERR_NO_DEVICE, "compile-only mode");
-    if (!tflops || (dtype != CJ_F64 && dtype != CJ_F32)) return fail(CJ_ERR_INVALID_ARG, "dtype must be f64 or f32");
+    if (!tflops || (dtype != CJ_F64 && dtype != CJ_F32) || (tensor && dtype != CJ_F64))
+        return fail(CJ_ERR_INVALID_ARG, "dtype must be f64 or f32 (tensor: f64 only)");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
-    const void *k = cjint::peak_fma_kernel(dtype);
+    const void *k = tensor ? cjint::peak_dmma_kernel() : cjint::peak_fma_kernel(dtype);
     const unsigned grid = (unsigned)G.num_sms * 8u;
-    int iters = dtype == CJ_F64 ? 4096 : 65536;
+    int iters = tensor ? 1024 : dtype == CJ_F64 ? 4096 : 65536;
     double ad = 0.9999, bd = 1e-4;
     float af = 0.9999f, bf = 1e-4f;
     void *args_d[] = {&iters, &ad, &bd};
@@ -1045,7 +1046,10 @@ CJ_API cj_status cj_measure_fma_peak(int32_t dtype, void *cuda_stream, double *t
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (err != cudaSuccess || ms <= 0) return fail(CJ_ERR_CUDA, "peak kernel failed: %s", cudaGetErrorString(err));
-    const double flops = 3.0 * 2.0 * 8.0 * iters * (double)grid * 256.0;
+    // per thread and iteration: 8 FMA chains (2 flops each), or 8 mma.sync m8n8k4
+    // per warp (8 * 512 FMA per warp = 8 * 32 flops per thread)
+    const double per = tensor ? 8.0 * 32.0 : 8.0 * 2.0;
+    const double flops = 3.0 * per * iters * (double)grid * 256.0;
     *tflops = flops / (ms * 1e-3) / 1e12;
     return CJ_OK;
 }

@@ -44,6 +44,8 @@ const GenericKernels &generic_kernels();
 // FMA-throughput kernel (roofline denominator), indexed by dtype (0 f64, 1 f32):
 // kernel(int iters, T a, T b), 256 threads per block, 8 chains per thread.
 const void *peak_fma_kernel(int dtype);
+// FP64 tensor-core (mma.sync m8n8k4) rate kernel: kernel(int iters, double a, double b).
+const void *peak_dmma_kernel();
 
 // Cost-model tile choice for a request with tile = 0 (tuner.cu); false if no
 // model is installed or the query failed.
