@@ -103,8 +103,7 @@ typedef struct {
  *     (X and A in registers, n <= 8), 3 = bf16 tensor-core warp tile,
  *     4 = FP64 tensor cores (mma.sync m8n8k4; one warp per 8 rows; f64 with
  *     n in {8, 16, 24, 32}).
- *     Default: f64 with n in {8, 16, 24, 32} -> {4, max(1, 64 / n)};
- *     n <= 4 -> {2, 128}; n <= 32 -> {1, max(1, 256 / n)};
+ *     Default: n <= 4 -> {2, 128}; n <= 32 -> {1, max(1, 256 / n)};
  *     else {1, max(1, 128 / n)}; bf16 -> {3, max(1, 128 / n16)} with n16 = n
  *     rounded up to a multiple of 16 (mapping 3: one warp per 16 rows,
  *     bf16 operands, fp32 accumulate and state).
@@ -119,9 +118,10 @@ typedef struct {
  *     call orders 1 and 4 "g-fast" (g is the fastest axis) and 0 and 2
  *     "z-fast"; TG = 1 if neither in nor out is g-fast, 8 if one is g-fast
  *     and the other z-fast, 32 otherwise; TZ = CT / TG;
- *     f64 with d % 4 == 0: MODE 1, R 2, threads 128; other f64: R 1, S 9,
- *     threads 64 * ceil(m / 9); f32: PIPE 1, R 2, S 12, threads
- *     32 * ceil(m / 12) (m = 36: 96).
+ *     f64: R 1, S 9, threads 64 * ceil(m / 9) (m = 36: 256); f32: PIPE 1,
+ *     R 2, S 12, threads 32 * ceil(m / 12) (m = 36: 96).  The FP64
+ *     tensor-core mappings are autotuner candidates, not defaults: on B300
+ *     mma.sync f64 issues on the FP64 pipe and is not faster than DFMA.
  */
 typedef struct {
     int32_t dtype, n, layout_a, layout_b, m, d;

@@ -22,8 +22,6 @@ All little-endian.  Fields that a kernel does not use are zeroed, so requests
 differing only there share an instantiation.
 
 Default tile resolution (tile all zero, no cost model):
-  update chain / grouped, f64 with n in {8, 16, 24, 32}:
-                                       (4 = FP64 tensor-core panels, max(1, 64 // n), 0, 0)
   update chain / grouped, f64 or f32:  n <= 4 -> (2 = instance per thread, 128, 0, 0)
                                        else   -> (1 = row per thread, ipb, 0, 0)
                                        with ipb = max(1, 256 // n) for n <= 32,
@@ -33,8 +31,7 @@ Default tile resolution (tile all zero, no cost model):
   LTimes: (TG, TZ, threads, (PIPE << 20) | (MODE << 16) | (R << 8) | S), CT = 64
       columns; orders 1, 4 are g-fast and 0, 2 z-fast; TG = 1 if neither in
       nor out is g-fast, 8 if one is g-fast and the other z-fast, else 32;
-      TZ = CT / TG; f64 with d % 4 == 0: tensor-core mode, tile[3] = (1 << 16) | (2 << 8) | 8,
-      threads 128; other f64: R 1, S 9, threads 64 * ceil(m / 9); f32: pipelined,
+      TZ = CT / TG; f64: R 1, S 9, threads 64 * ceil(m / 9); f32: pipelined,
       tile[3] = (1 << 20) | (2 << 8) | 12, threads 32 * ceil(m / 12).
 Expected variant: GENERIC flag -> generic; else update chain f64/f32 with
 n in {4, 8, 16, 32}, default tile, AoT set enabled and no NO_AOT flag -> aot;
@@ -69,8 +66,6 @@ def default_tile(kernel: int, dtype: int, n: int, layout_a: int = 0, layout_b: i
     if kernel in (K_UPDATE_CHAIN, K_UPDATE_CHAIN_GROUPED):
         if dtype == BF16:
             return (3, max(1, 128 // (-(-n // 16) * 16)), 0, 0)
-        if dtype == F64 and n % 8 == 0 and n <= 32:
-            return (4, max(1, 64 // n), 0, 0)
         if n <= 4:
             return (2, 128, 0, 0)
         return (1, max(1, (256 if n <= 32 else 128) // n), 0, 0)
@@ -83,8 +78,6 @@ def default_tile(kernel: int, dtype: int, n: int, layout_a: int = 0, layout_b: i
             tg = 8
         else:
             tg = 32
-        if dtype == F64 and d % 4 == 0:
-            return (tg, ct // tg, ct // 16 * 32, (1 << 16) | (2 << 8) | 8)
         if dtype == F32:
             return (tg, ct // tg, 32 * (-(-m // 12)), (1 << 20) | (2 << 8) | 12)
         return (tg, ct // tg, ct * (-(-m // 9)), (1 << 8) | 9)

@@ -209,12 +209,6 @@ void default_tile(int k, cj_template_args &a) {
     else tg = 32;
     a.tile[0] = tg;
     a.tile[1] = ct / tg;
-    if (a.dtype == CJ_F64 && a.d % 4 == 0) {
-        // FP64 tensor cores: each warp 16 columns x all moments
-        a.tile[2] = (ct / 16) * 32;
-        a.tile[3] = (1 << 16) | (2 << 8) | 8;
-        return;
-    }
     if (a.dtype == CJ_F32) {
         // 64 columns, R 2, S 12, pipelined loads; threads = 32 * ceil(m / 12)
         a.tile[0] = tg;
@@ -1046,9 +1040,9 @@ CJ_API cj_status cj_measure_fma_peak(int32_t dtype, int32_t tensor, void *cuda_s
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (err != cudaSuccess || ms <= 0) return fail(CJ_ERR_CUDA, "peak kernel failed: %s", cudaGetErrorString(err));
-    // per thread and iteration: 8 FMA chains (2 flops each), or 8 mma.sync m8n8k4
-    // per warp (8 * 512 FMA per warp = 8 * 32 flops per thread)
-    const double per = tensor ? 8.0 * 32.0 : 8.0 * 2.0;
+    // per thread and iteration: 8 FMA chains (2 flops each), or 8 mma.sync
+    // m8n8k4 per warp (each 8 * 8 * 4 = 256 FMA = 512 flops, 16 per thread)
+    const double per = tensor ? 8.0 * 16.0 : 8.0 * 2.0;
     const double flops = 3.0 * per * iters * (double)grid * 256.0;
     *tflops = flops / (ms * 1e-3) / 1e12;
     return CJ_OK;

@@ -13,13 +13,12 @@ enum { K_CHAIN = 1, K_LTIMES = 2, K_GROUPED = 3 };
 enum { D_F64 = 0, D_F32 = 1, D_BF16 = 2 };
 
 // Default tile rule of the update chain kernels (documented in cj.h).
+// FP64 tensor cores (mapping 4) are a candidate only: on B300 mma.sync f64
+// issues on the same FP64 pipe as DFMA and is not faster (measured).
 constexpr bool chain_dmma_ok(int n, int dtype) { return dtype == D_F64 && n % 8 == 0 && n <= 32; }
-constexpr int chain_default_map(int n, int dtype) {
-    return dtype == D_BF16 ? 3 : chain_dmma_ok(n, dtype) ? 4 : (n <= 4 ? 2 : 1);
-}
+constexpr int chain_default_map(int n, int dtype) { return dtype == D_BF16 ? 3 : (n <= 4 ? 2 : 1); }
 constexpr int chain_default_ipb(int n, int dtype) {
     return dtype == D_BF16 ? (128 / ((n + 15) / 16 * 16) > 1 ? 128 / ((n + 15) / 16 * 16) : 1)
-         : chain_dmma_ok(n, dtype) ? (64 / n > 1 ? 64 / n : 1)
          : n <= 4 ? 128 : n <= 32 ? 256 / n : (128 / n > 1 ? 128 / n : 1);
 }
 

@@ -5,10 +5,10 @@ from oracle import keys as K
 
 
 def test_hand_assembled_chain_key():
-    # kernel 1, f64, row-major, n=8, default tile (4, 8, 0, 0) (FP64 tensor-core
-    # panels, 64 / n instances per block), no flags
+    # kernel 1, f64, row-major, n=8, default tile (1, 32, 0, 0) (one thread per
+    # row, 256 / n instances per block), no flags
     expect = bytes.fromhex("0100" "00" "00" "00" "00" "0800" "0000" "0000"
-                           "04000000" "08000000" "00000000" "00000000" "00000000")
+                           "01000000" "20000000" "00000000" "00000000" "00000000")
     assert K.canonical_key(K.K_UPDATE_CHAIN, K.F64, n=8) == expect
 
 

@@ -229,7 +229,7 @@ def test_ltimes_generic(lt_small, lin, lout, dt):
     (64, 128, 2, 40, 3, 0, (1, 32, 256, (1 << 8) | 8)),
     (36, 96, 32, 64, 0, 3, (1, 64, 256, (1 << 8) | 9)),                       # FMA pipe, f64
     (36, 96, 32, 64, 4, 5, (32, 2, 256, (1 << 16) | (1 << 8) | 8)),           # tensor cores, R = 1
-    (36, 96, 5, 37, 2, 1, (8, 16, 64, (1 << 16) | (4 << 8) | 8)),             # tensor cores, R = 4, ragged
+    (36, 96, 5, 37, 2, 1, (8, 16, 128, (1 << 16) | (4 << 8) | 8)),            # tensor cores, R = 4, ragged
     (40, 8, 3, 100, 5, 0, (1, 64, 128, (1 << 16) | (2 << 8) | 8)),            # M multiple of 8
 ])
 def test_ltimes_shapes_and_tiles(M, D, G, Z, lin, lout, tile):
