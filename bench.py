@@ -403,6 +403,15 @@ def main():
     args = p.parse_args()
     if args.warmup < 3:
         p.error("--warmup must be >= 3")
+    def lt_alt_tiles(lin, lout):
+        # extra LTimes tiles timed beside the default, per (in, out) pair
+        if args.dtype != "f32":
+            return []
+        gi, go = lin in (1, 4), lout in (1, 4)
+        tg = 1 if not (gi or go) else (8 if (gi and lout in (0, 2)) or (go and lin in (0, 2)) else 32)
+        return [("tf32x3", (tg, 64 // tg, 128, (1 << 20) | (2 << 16) | (1 << 8) | 8)),
+                ("tf32x3_ct128", (tg, 128 // tg, 256, (1 << 20) | (2 << 16) | (1 << 8) | 8))]
+    args.lt_alt_tiles = lt_alt_tiles
     if args.impl == "reference":
         reference_arm(args)
     elif args.workload != "sweep":
@@ -504,10 +513,18 @@ def secondary(args):
                 ms_s = _events(torch, stream, fs, K)
                 _events(torch, stream, fg, 1)
                 ms_g = _events(torch, stream, fg, K)
-                rows.append({"in": synth.LAYOUT_NAMES[lin], "out": synth.LAYOUT_NAMES[lout].replace("D", "M"),
-                             "spec_ms": ms_s, "generic_ms": ms_g, "spec_gflops": f / ms_s / 1e6,
-                             "spec_gbs": byt / ms_s / 1e6, "generic_gflops": f / ms_g / 1e6,
-                             "speedup_vs_generic": ms_g / ms_s})
+                row = {"in": synth.LAYOUT_NAMES[lin], "out": synth.LAYOUT_NAMES[lout].replace("D", "M"),
+                       "spec_ms": ms_s, "generic_ms": ms_g, "spec_gflops": f / ms_s / 1e6,
+                       "spec_gbs": byt / ms_s / 1e6, "generic_gflops": f / ms_g / 1e6,
+                       "speedup_vs_generic": ms_g / ms_s,
+                       "tile": list(int.from_bytes(bytes.fromhex(hs.key_hex)[12 + 4 * i:16 + 4 * i], "little")
+                                    for i in range(4))}
+                for name, alt in args.lt_alt_tiles(lin, lout):
+                    ha = cj.specialize(cj.K_LTIMES, dt, layout_a=lin, layout_b=lout, m=M, d=D, tile=alt)
+                    fa = lambda: cj.launch_ltimes(ha, Lt, xin[lin], o, G, Z, stream=stream)
+                    _events(torch, stream, fa, 1)
+                    row[name + "_ms"] = _events(torch, stream, fa, K)
+                rows.append(row)
                 tot_s += ms_s
                 tot_g += ms_g
         peak = PEAK_TFLOPS[args.dtype]

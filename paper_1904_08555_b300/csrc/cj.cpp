@@ -308,12 +308,16 @@ cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_
                           (tg * tz / (8 * r)) * 32 != nt || nt > 1024))
             return fail(CJ_ERR_INVALID_ARG, "LTimes tensor-core tile {%d,%d,%d,0x%x} invalid (f64, S = 8, d %% 4 == 0, "
                         "threads = 32 * TG * TZ / (8 R))", a.tile[0], a.tile[1], a.tile[2], a.tile[3]);
-        if (mode > 1) return fail(CJ_ERR_INVALID_ARG, "LTimes compute mode %d unknown", mode);
+        if (mode == 2 && (a.dtype != CJ_F32 || s != 8 || r != 1 || a.d % 8 || (tg * tz) % 16 ||
+                          (tg * tz / 16) * 32 != nt || nt > 1024))
+            return fail(CJ_ERR_INVALID_ARG, "LTimes 3xTF32 tile {%d,%d,%d,0x%x} invalid (f32, R = 1, S = 8, d %% 8 == 0, "
+                        "threads = 32 * TG * TZ / 16)", a.tile[0], a.tile[1], a.tile[2], a.tile[3]);
+        if (mode > 2) return fail(CJ_ERR_INVALID_ARG, "LTimes compute mode %d unknown", mode);
         if (mode == 0 && (tg < 1 || tz < 1 || r < 1 || s < 1 || nt < 32 || nt > 1024 || (tg * tz) % r ||
                           (tg * tz / r) * ((a.m + s - 1) / s) != nt))
             return fail(CJ_ERR_INVALID_ARG, "LTimes tile {%d,%d,%d,%d} does not cover its block", a.tile[0],
                         a.tile[1], a.tile[2], a.tile[3]);
-        if (cjg::lt_smem(a.m, s, a.d, tg * tz, esize(a.dtype), pipe) > 220 * 1024)
+        if (cjg::lt_smem(a.m, s, a.d, tg * tz, esize(a.dtype), pipe, mode) > 220 * 1024)
             return fail(CJ_ERR_INVALID_ARG, "LTimes tile needs too much shared memory");
     }
     return CJ_OK;
@@ -351,7 +355,8 @@ void spec_geometry(const cj_handle_s *h, Impl &s) {
     const int es = esize(a.dtype);
     if (h->kernel == CJ_K_LTIMES) {
         s.threads = a.tile[2];
-        s.smem = (size_t)cjg::lt_smem(a.m, a.tile[3] & 0xff, a.d, a.tile[0] * a.tile[1], es, (a.tile[3] >> 20) & 1);
+        s.smem = (size_t)cjg::lt_smem(a.m, a.tile[3] & 0xff, a.d, a.tile[0] * a.tile[1], es, (a.tile[3] >> 20) & 1,
+                                      (a.tile[3] >> 16) & 0xf);
     } else {
         s.ipb = a.tile[1];
         s.threads = cjg::chain_threads(a.n, a.tile[0], a.tile[1]);

@@ -60,12 +60,13 @@ CJ_HD constexpr long chain_generic_smem(int n, int ipb, int threads, int esize) 
 // LTimes: L is kept transposed, [d][m] with m padded to whole moment groups
 // of S and to a 16-byte multiple.
 CJ_HD constexpr int lt_mpitch(int mpad, int esize) { return ((mpad * esize + 15) / 16) * 16 / esize; }
-// Column tile pitch: CT plus 16 bytes.
-CJ_HD constexpr int lt_cpitch(int ct, int esize) { return ct + 16 / esize; }
-// pipe = 1: two tile buffers.
-CJ_HD constexpr long lt_smem(int m, int s, int d, int ct, int esize, int pipe = 0) {
-    return ((long)d * lt_mpitch((m + s - 1) / s * s, esize) +
-            (pipe ? 2L : 1L) * (long)(m > d ? m : d) * lt_cpitch(ct, esize)) *
+// Column tile pitch: CT plus 16 bytes (mode 2: plus 8 elements, so the four
+// k-rows of an mma fragment fall in different banks).
+CJ_HD constexpr int lt_cpitch(int ct, int esize, int mode = 0) { return ct + (mode == 2 ? 8 : 16 / esize); }
+// pipe = 1: two tile buffers; mode 2: a second copy of L^T (tf32 remainder).
+CJ_HD constexpr long lt_smem(int m, int s, int d, int ct, int esize, int pipe = 0, int mode = 0) {
+    return ((mode == 2 ? 2L : 1L) * d * lt_mpitch((m + s - 1) / s * s, esize) +
+            (pipe ? 2L : 1L) * (long)(m > d ? m : d) * lt_cpitch(ct, esize, mode)) *
            esize;
 }
 CJ_HD constexpr long lt_generic_smem(int m, int d, int cols, int esize) {

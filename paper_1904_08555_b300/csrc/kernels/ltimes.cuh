@@ -81,6 +81,25 @@ __device__ __forceinline__ void lt_dmma(double (&d)[2], double a, double b) {
         : "d"(a), "d"(b));
 }
 
+// 3xTF32 tensor-core step (MODE 2, FP32): a = a_hi + a_lo with both parts
+// rounded to tf32; a*b ~ a_hi*b_hi + a_hi*b_lo + a_lo*b_hi (the dropped
+// a_lo*b_lo term is ~2^-22 relative), accumulated in FP32 by mma.sync
+// m16n8k8.  Fragment layouts (PTX ISA, m16n8k8 .tf32): A a0 (row g, col t),
+// a1 (row g+8, col t), a2 (row g, col t+4), a3 (row g+8, col t+4); B b0
+// (k t, n g), b1 (k t+4, n g); accumulator c0,c1 (row g, cols 2t, 2t+1),
+// c2,c3 (row g+8, cols 2t, 2t+1); g = lane/4, t = lane%4.
+__device__ __forceinline__ unsigned to_tf32(float x) {
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void mma_tf32_1688(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
 // Asynchronous variant of the box load (cp.async, one element per copy):
 // out-of-range elements are zero-filled (source size 0), nothing is read.
 template <class T, int LAY, int EX, int TG, int TZ, int CP, int NT>
@@ -132,20 +151,30 @@ ltimes(const T* __restrict__ L, const T* __restrict__ in, T* __restrict__ out, l
     constexpr int CT = TG * TZ;
     constexpr int MG = (M + S - 1) / S;   // moment groups (the last may be partial)
     constexpr int MP = cjg::lt_mpitch(MG * S, (int)sizeof(T));
-    constexpr int CP = cjg::lt_cpitch(CT, (int)sizeof(T));
+    constexpr int CP = cjg::lt_cpitch(CT, (int)sizeof(T), MODE);
     constexpr int QG = CT / R;   // column groups
-    static_assert(MODE == 1 || (CT % R == 0 && QG * MG == NT), "tile does not cover the block");
-    static_assert(MODE == 0 || (sizeof(T) == 8 && S == 8 && D % 4 == 0 && CT % (8 * R) == 0 &&
+    static_assert(MODE != 0 || (CT % R == 0 && QG * MG == NT), "tile does not cover the block");
+    static_assert(MODE != 1 || (sizeof(T) == 8 && S == 8 && D % 4 == 0 && CT % (8 * R) == 0 &&
                                 (CT / (8 * R)) * 32 == NT), "tensor-core tile does not cover the block");
+    static_assert(MODE != 2 || (sizeof(T) == 4 && S == 8 && R == 1 && D % 8 == 0 && CT % 16 == 0 &&
+                                (CT / 16) * 32 == NT), "3xTF32 tile does not cover the block");
     extern __shared__ __align__(16) unsigned char cj_smem[];
     constexpr int XR = M > D ? M : D;        // rows of a tile buffer
     T* sL = reinterpret_cast<T*>(cj_smem);   // [D][MP], L transposed
     T* sX0 = sL + D * MP;                     // [D][CP] in tile, then [M][CP] out tile
     T* sX1 = sX0 + XR * CP;                   // second buffer (PIPE)
+    T* sLlo = sX0 + (PIPE ? 2 : 1) * XR * CP; // MODE 2: tf32 remainder of L^T
     const int tid = threadIdx.x;
     for (int e = tid; e < MP * D; e += NT) {
         const int m = e / D, d = e - m * D;
-        sL[d * MP + m] = m < M ? L[e] : T(0);
+        const T v = m < M ? L[e] : T(0);
+        if constexpr (MODE == 2) {
+            const unsigned hi = to_tf32((float)v);
+            sL[d * MP + m] = __uint_as_float(hi);
+            sLlo[d * MP + m] = __uint_as_float(to_tf32((float)v - __uint_as_float(hi)));
+        } else {
+            sL[d * MP + m] = v;
+        }
     }
     const long long ntg = (G + TG - 1) / TG, ntz = (Z + TZ - 1) / TZ;
     const long long ntiles = ntg * ntz;
@@ -172,6 +201,47 @@ ltimes(const T* __restrict__ L, const T* __restrict__ in, T* __restrict__ out, l
             lt_box<T, LIN, D, TG, TZ, CP, NT, true>(const_cast<T*>(in), sX, G, Z, g0, z0, tid);
         }
         __syncthreads();
+        if constexpr (MODE == 2) {
+            const int lane = tid & 31, g = lane >> 2, t = lane & 3;
+            const int q0 = (tid >> 5) * 16;
+            float acc[MG][4];
+#pragma unroll
+            for (int nb = 0; nb < MG; ++nb) acc[nb][0] = acc[nb][1] = acc[nb][2] = acc[nb][3] = 0.f;
+#pragma unroll 2
+            for (int kb = 0; kb < D / 8; ++kb) {
+                const float* x0 = reinterpret_cast<const float*>(sX) + (8 * kb + t) * CP + q0 + g;
+                const float* x4 = x0 + 4 * CP;
+                const float av[4] = {x0[0], x0[8], x4[0], x4[8]};
+                unsigned ahi[4], alo[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    ahi[i] = to_tf32(av[i]);
+                    alo[i] = to_tf32(av[i] - __uint_as_float(ahi[i]));
+                }
+                const float* l0 = reinterpret_cast<const float*>(sL) + (8 * kb + t) * MP + g;
+                const float* r0 = reinterpret_cast<const float*>(sLlo) + (8 * kb + t) * MP + g;
+#pragma unroll
+                for (int nb = 0; nb < MG; ++nb) {
+                    const unsigned bh0 = __float_as_uint(l0[8 * nb]), bh1 = __float_as_uint(l0[4 * MP + 8 * nb]);
+                    const unsigned bl0 = __float_as_uint(r0[8 * nb]), bl1 = __float_as_uint(r0[4 * MP + 8 * nb]);
+                    mma_tf32_1688(acc[nb], alo, bh0, bh1);
+                    mma_tf32_1688(acc[nb], ahi, bl0, bl1);
+                    mma_tf32_1688(acc[nb], ahi, bh0, bh1);
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int nb = 0; nb < MG; ++nb)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int m = 8 * nb + 2 * t + (i & 1);
+                    const int q = q0 + g + (i >= 2 ? 8 : 0);
+                    if (M % 8 == 0 || m < M) sX[m * CP + q] = acc[nb][i];
+                }
+            __syncthreads();
+            lt_box<T, LOUT, M, TG, TZ, CP, NT, false>(out, sX, G, Z, g0, z0, tid);
+            continue;
+        }
         if constexpr (MODE == 1) {
             const int lane = tid & 31, r = lane >> 2, t = lane & 3;
             const int c0 = (tid >> 5) * 8 * R;

@@ -72,12 +72,15 @@ void ltimes_candidates(const cj_template_args &a, std::vector<std::array<int, 4>
         if (mode == 1) {
             if (ct % (8 * r)) return;
             nt = ct / (8 * r) * 32;
+        } else if (mode == 2) {
+            if (ct % 16 || a.d % 8) return;
+            nt = ct / 16 * 32;
         } else {
             if (ct % r) return;
             nt = (ct / r) * ((a.m + s - 1) / s);
         }
         if (nt < 32 || nt > 1024) return;
-        if (cjg::lt_smem(a.m, s, a.d, ct, es, pipe) > 200 * 1024) return;
+        if (cjg::lt_smem(a.m, s, a.d, ct, es, pipe, mode) > 200 * 1024) return;
         out.push_back({tg, ct / tg, nt, (pipe << 20) | (mode << 16) | (r << 8) | s});
     };
     for (int tg : tgs) {
@@ -88,8 +91,10 @@ void ltimes_candidates(const cj_template_args &a, std::vector<std::array<int, 4>
             push(tg, 64, 0, 1, 9);
             push(tg, 64, 0, 1, 12);
         } else {
-            for (int ct : {64, 128})
-                for (auto rs : {std::pair<int, int>{2, 12}, {4, 12}, {4, 9}}) push(tg, ct, 0, rs.first, rs.second, 1);
+            for (int ct : {64, 128}) {
+                push(tg, ct, 2, 1, 8, 1);  // 3xTF32 tensor cores
+                for (auto rs : {std::pair<int, int>{2, 12}, {4, 12}}) push(tg, ct, 0, rs.first, rs.second, 1);
+            }
             push(tg, 128, 0, 4, 12, 0);   // unpipelined baseline
         }
     }

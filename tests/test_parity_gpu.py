@@ -212,6 +212,17 @@ def test_ltimes_orders_f32(lt_small, lin, lout):
     assert relF(run_ltimes(h, L, x, lin, lout, cj.F32), ref) <= TOL32
 
 
+@pytest.mark.parametrize("lin", range(6))
+@pytest.mark.parametrize("lout", [1, 5])
+@pytest.mark.parametrize("tg,tz,pipe", [(1, 64, 1), (8, 16, 0), (32, 4, 1)])
+def test_ltimes_f32_tf32x3(lt_small, lin, lout, tg, tz, pipe):
+    """3xTF32 tensor-core mode: FP32-level accuracy against the FP64 oracle."""
+    L, x, ref = lt_small
+    tile = (tg, tz, tg * tz // 16 * 32, (pipe << 20) | (2 << 16) | (1 << 8) | 8)
+    h = cj.specialize(cj.K_LTIMES, cj.F32, layout_a=lin, layout_b=lout, m=36, d=96, tile=tile)
+    assert relF(run_ltimes(h, L, x, lin, lout, cj.F32), ref) <= TOL32
+
+
 @pytest.mark.parametrize("lin,lout", [(0, 0), (1, 3), (3, 5), (5, 2)])
 @pytest.mark.parametrize("dt", [cj.F64, cj.F32])
 def test_ltimes_generic(lt_small, lin, lout, dt):
