@@ -134,19 +134,13 @@ def dist_setup(n_gpus: int):
 
 
 def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    from paper_1904_08555_b300 import shard
+    shard.barrier(world)
 
 
 def max_over_ranks(world, v: float) -> float:
-    if world == 1:
-        return v
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_1904_08555_b300 import shard
+    return shard.max_over_ranks(world, v, device="cuda")
 
 
 # ---------------------------------------------------------------------------
@@ -210,7 +204,7 @@ def reference_arm(args):
 # ---------------------------------------------------------------------------
 def cj_arm(args):
     import torch
-    from paper_1904_08555_b300 import cj
+    from paper_1904_08555_b300 import cj, shard
 
     world, rank, local = dist_setup(args.gpus)
     dev = torch.cuda.current_device()
@@ -223,8 +217,8 @@ def cj_arm(args):
         for n in SWEEP_N:
             b = synth.chain_batch(n)
             batch[n] = b
-            A[n] = synth.uniform_torch(synth.SEED_CHAIN_SWEEP, synth.STREAM_A + rank * b * n * n, b * n * n,
-                                       "cuda").view(b, n, n)
+            A[n] = synth.uniform_torch(synth.SEED_CHAIN_SWEEP, synth.STREAM_A + shard.element_offset(rank, b, n),
+                                       b * n * n, "cuda").view(b, n, n)
             X[n] = torch.empty_like(A[n])
     stream.synchronize()
 
