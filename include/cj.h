@@ -102,7 +102,8 @@ typedef struct {
  *     per row of X (A staged in shared memory), 2 = one thread per instance
  *     (X and A in registers, n <= 8), 3 = bf16 tensor-core warp tile,
  *     4 = FP64 tensor cores (mma.sync m8n8k4; one warp per 8 rows; f64 with
- *     n in {8, 16, 24, 32}).
+ *     n in {8, 16, 24, 32}), 5 = FP32 register blocks (one thread per 4x4
+ *     block of X A, X transposed in shared memory; f32, n % 4 == 0, n >= 8).
  *     Default: n <= 4 -> {2, 128}; n <= 32 -> {1, max(1, 256 / n)};
  *     else {1, max(1, 128 / n)}; bf16 -> {3, max(1, 128 / n16)} with n16 = n
  *     rounded up to a multiple of 16 (mapping 3: one warp per 16 rows,

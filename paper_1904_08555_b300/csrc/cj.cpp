@@ -288,7 +288,9 @@ cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_
     // explicit tiles: check the kernel can be instantiated and launched
     if (k != CJ_K_LTIMES) {
         const int map = a.tile[0], ipb = a.tile[1];
-        if (map < 1 || map > 4) return fail(CJ_ERR_INVALID_ARG, "update chain mapping %d must be 1..4", map);
+        if (map < 1 || map > 5) return fail(CJ_ERR_INVALID_ARG, "update chain mapping %d must be 1..5", map);
+        if (map == 5 && (a.dtype != CJ_F32 || a.n % 4 || a.n < 8))
+            return fail(CJ_ERR_INVALID_ARG, "mapping 5 (register blocks) needs f32 and n a multiple of 4, n >= 8");
         if ((map == 3) != (a.dtype == CJ_BF16))
             return fail(CJ_ERR_INVALID_ARG, "mapping 3 (bf16 tensor cores) is the only mapping of dtype bf16");
         if (map == 2 && a.n > 8) return fail(CJ_ERR_INVALID_ARG, "mapping 2 needs n <= 8");

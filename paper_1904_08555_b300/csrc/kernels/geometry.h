@@ -27,9 +27,10 @@ CJ_HD constexpr int inst_pitch(int nn) { return nn | 1; }
 
 // Threads per block of the update chain kernels: mapping 2 one thread per
 // instance, mapping 4 one warp per 8 rows, mapping 3 one warp per 16 rows
-// (padded), mapping 1 one thread per row.
+// (padded), mapping 5 one thread per 4x4 block, mapping 1 one thread per row.
 CJ_HD constexpr int chain_threads(int n, int mapping, int ipb) {
     return mapping == 2   ? ipb
+           : mapping == 5 ? ((ipb * (n / 4) * (n / 4) + 31) / 32) * 32
            : mapping == 4 ? ipb * (n / 8) * 32
            : mapping == 3 ? ipb * ((n + 15) / 16) * 32
                           : ((ipb * n + 31) / 32) * 32;
@@ -45,6 +46,8 @@ CJ_HD constexpr int xrow_pitch(int n) { return n | 1; }
 CJ_HD constexpr long chain_smem(int n, int mapping, int ipb, int esize) {
     return mapping == 2
         ? (long)ipb * inst_pitch(n * n) * esize
+        : mapping == 5
+        ? (long)ipb * row_pitch(n * n, esize) * esize + (long)ipb * n * (n + 4) * esize
         : (long)ipb * row_pitch(n * n, esize) * esize +
               (mapping == 1 && n > chain_reg_rows_max(esize)
                    ? (long)chain_threads(n, 1, ipb) * xrow_pitch(n) * esize

@@ -256,7 +256,66 @@ __device__ __forceinline__ void panel_chain_bf16(const float* a_s, int panel, in
 template <class T, int N, int LAYOUT, int MAP, int IPB, class StepsOf, class COf>
 __device__ __forceinline__ void chain_block(T* sA, int ninst, int tid, StepsOf steps_of, COf c_of) {
     constexpr int NN = N * N;
-    if constexpr (MAP == 3) {
+    if constexpr (MAP == 5) {
+        // FP32 register blocks: thread (inst, rb, cb) owns rows 4rb..4rb+3 and
+        // columns 4cb..4cb+3 of P = X A.  X is kept transposed in shared memory
+        // (xt[l][r], pitch N + 4) so both operands are 16-byte vector reads:
+        // 16 FMA per two shared-memory loads.  All threads of the block run
+        // the longest instance's step count so every barrier is uniform.
+        static_assert(sizeof(T) == 4 && N % 4 == 0 && N >= 8, "mapping 5 is FP32 with N a multiple of 4");
+        constexpr int P = cjg::row_pitch(NN, 4);
+        constexpr int B4 = N / 4, TPI = B4 * B4, XTP = N + 4;
+        T* xt_all = sA + IPB * P;
+        const int inst = tid / TPI, w = tid - inst * TPI;
+        const int rb = w % B4, cb = w / B4;
+        const bool active = inst < ninst;
+        int kmax = 0;
+        for (int q = 0; q < ninst; ++q) kmax = max(kmax, steps_of(q));
+        const int steps = active ? steps_of(inst) : 0;
+        const T cc = active ? c_of(inst) : T(0);
+        T* xt = xt_all + (active ? inst : 0) * N * XTP;
+        const T* a = sA + (active ? inst : 0) * P;
+        if (active)
+            for (int e = w; e < NN; e += TPI) {
+                const int l = e / N, r = e - l * N;
+                xt[l * XTP + r] = (l == r) ? T(1) : T(0);
+            }
+        __syncthreads();
+        for (int k = 0; k < kmax; ++k) {
+            float acc[4][4] = {};
+            const bool run = k < steps;
+            if (run) {
+#pragma unroll 4
+                for (int l = 0; l < N; ++l) {
+                    const float4 xv = *reinterpret_cast<const float4*>(xt + l * XTP + 4 * rb);
+                    const float4 av = *reinterpret_cast<const float4*>(a + l * N + 4 * cb);
+                    const float xr[4] = {xv.x, xv.y, xv.z, xv.w};
+                    const float ar[4] = {av.x, av.y, av.z, av.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) acc[i][j] = fmaT(xr[i], ar[j], acc[i][j]);
+                }
+            }
+            __syncthreads();   // every read of X_k is done
+            if (run) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        T* xp = xt + (4 * cb + j) * XTP + 4 * rb + i;
+                        *xp = fmaT(cc, acc[i][j], *xp);
+                    }
+            }
+            __syncthreads();   // X_{k+1} complete
+        }
+        // X_T into the staging area in storage order (A is no longer needed)
+        if (active)
+            for (int e = w; e < NN; e += TPI) {
+                const int i = e / N, j = e - i * N;
+                sA[inst * P + (LAYOUT == 0 ? i * N + j : j * N + i)] = xt[j * XTP + i];
+            }
+    } else if constexpr (MAP == 3) {
         static_assert(sizeof(T) == 4 && N >= 16, "mapping 3 is bf16 operands with fp32 state, N >= 16");
         constexpr int P = cjg::row_pitch(NN, 4);
         constexpr int NPAN = (N + 15) / 16;

@@ -110,6 +110,18 @@ def test_update_chain_fp64_tensor_core_tiles(n, layout, ipb):
     assert relF_per_instance(x4, x1) <= TOL64
 
 
+@pytest.mark.parametrize("n,ipb", [(8, 8), (12, 4), (16, 3), (32, 2), (48, 1), (64, 1)])
+@pytest.mark.parametrize("layout", [0, 1])
+def test_update_chain_f32_register_blocks(n, ipb, layout):
+    """Mapping 5 (4x4 register blocks, X transposed in shared memory)."""
+    steps = 64
+    h = cj.specialize(cj.K_UPDATE_CHAIN, cj.F32, n=n, layout_a=layout, tile=(5, ipb, 0, 0))
+    batch = oracle_batch(n, steps) + 2
+    A = synth.chain_inputs_np(synth.SEED_CHAIN_SWEEP, batch, n, layout=layout)
+    ref = oracle.update_chain(A, steps, layout=layout, nthreads=8)
+    assert relF_per_instance(run_chain(h, A, steps, cj.F32), ref) <= TOL32
+
+
 @pytest.mark.parametrize("n", [3, 8, 16, 32, 48, 64])
 @pytest.mark.parametrize("generic", [False, True])
 def test_update_chain_f32_error(n, generic):
@@ -291,15 +303,16 @@ def test_grouped_handle_direct_launch():
     items = np.zeros((cnt, 3), dtype=np.int64)
     items[:, 0] = np.arange(cnt) * nn * nn
     items[:, 1] = steps
-    for flags in (0, cj.FLAG_GENERIC):
-        h = cj.specialize(cj.K_UPDATE_CHAIN_GROUPED, cj.F64, n=nn, flags=flags)
+    for dt, tile, flags in ((cj.F64, (0, 0, 0, 0), 0), (cj.F64, (0, 0, 0, 0), cj.FLAG_GENERIC),
+                            (cj.F32, (5, 2, 0, 0), 0), (cj.F32, (1, 3, 0, 0), 0)):
+        h = cj.specialize(cj.K_UPDATE_CHAIN_GROUPED, dt, n=nn, tile=tile, flags=flags)
         it = torch.from_numpy(items).cuda()
-        A = torch.from_numpy(pool).cuda()
+        A = torch.from_numpy(pool).to("cuda", tdtype(dt))
         X = torch.full_like(A, float("nan"))
         counter = torch.zeros(1, dtype=torch.int32, device="cuda")
         cj.launch_grouped(h, it, A, X, counter, cnt)
         torch.cuda.synchronize()
-        assert relF(X.cpu().numpy(), ref) <= TOL64
+        assert relF(X.double().cpu().numpy(), ref) <= (TOL64 if dt == cj.F64 else TOL32), (dt, tile)
 
 
 # ---------------------------------------------------------------------------
