@@ -24,6 +24,8 @@
  *   CJ_K_LTIMES        -- out[m][g][z] = sum_d L[m][d] in[d][g][z], storage
  *                         orders of in and out chosen at run time (Kripke
  *                         LTimes, Sec. 5.2, Listings kripold/kripnew).
+ *   CJ_K_LPLUSTIMES    -- the adjoint contraction named beside LTimes
+ *                         (Sec. 5.2): in[d][g][z] += sum_m Lp[d][m] out[m][g][z].
  *   CJ_K_UPDATE_CHAIN_GROUPED -- the update chain over a work list of
  *                         instances of one size N but different step counts,
  *                         pulled by a persistent kernel (batch amortization of
@@ -60,7 +62,8 @@ typedef enum {
 typedef enum {
     CJ_K_UPDATE_CHAIN = 1,
     CJ_K_LTIMES = 2,
-    CJ_K_UPDATE_CHAIN_GROUPED = 3
+    CJ_K_UPDATE_CHAIN_GROUPED = 3,
+    CJ_K_LPLUSTIMES = 4
 } cj_kernel_id;
 
 typedef enum {
@@ -96,6 +99,10 @@ typedef struct {
  *                  Storage orders list (x, g, z) slowest to fastest, x = d for
  *                  in and m for out: 0 XGZ, 1 XZG, 2 GXZ, 3 GZX, 4 ZXG, 5 ZGX.
  *   UPDATE_CHAIN_GROUPED: dtype, n (1..64), tile (row-major only).
+ *   LPLUSTIMES:    as LTIMES (layout_a = order of the accumulated `in`,
+ *                  layout_b = order of the input `out`, m, d); the tile is
+ *                  an LTimes tile of the swapped problem (d output rows, m
+ *                  contracted, orders exchanged), defaults likewise.
  * tile = {0,0,0,0} means "choose": the cost model if enabled and loaded,
  * else the default rule below.  Meaning of tile fields:
  *   update chain: {mapping, instances per block, 0, 0}; mapping 1 = one thread
@@ -169,6 +176,10 @@ cj_status cj_specialize_wait(cj_handle h, int timeout_ms);
  *   LTIMES: {const T** L, const T** in, T** out, const int64_t* G,
  *     const int64_t* Z}; L is [m][d] row-major, in is d*G*Z elements in
  *     order layout_a, out is m*G*Z in order layout_b; batch is ignored.
+ *   LPLUSTIMES: {const T** Lp, const T** out, T** in, const int64_t* G,
+ *     const int64_t* Z}; Lp is [d][m] row-major, out is m*G*Z elements in
+ *     order layout_b (read), in is d*G*Z elements in order layout_a
+ *     (accumulated into).
  *   UPDATE_CHAIN_GROUPED: {const int64_t** worklist, const T** A_pool,
  *     T** X_pool, int32_t** counter}; batch = work items.  Item i is three
  *     int64 {element offset of A_i and X_i in the pools, T_i, reserved}; items

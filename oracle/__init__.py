@@ -13,6 +13,7 @@ Pinning status (all pinned by CPU tests under tests/test_oracle_*.py):
                     form, exact rational brute force, commutation, layout.
   ltimes         -- six-order agreement, L=[I|0], L=0, in=1, numpy GEMM,
                     exact rational brute force.
+  lplustimes     -- adjoint identity with ltimes, accumulation, numpy GEMM.
   mlp            -- central finite differences, linear least-squares closed
                     form, first Adam step closed form.
   eigen_bench    -- exact rational brute force for tiny sizes.
@@ -55,6 +56,8 @@ def _load():
         lib.oracle_ltimes.argtypes = [i32, i32, i64, i64, i32, i32, P, P, P, i32]
         lib.oracle_ltimes.restype = i32
         lib.oracle_ltimes_sample.argtypes = [i32, i32, i64, i64, i32, P, P, i64, P, P]
+        lib.oracle_lplustimes.argtypes = [i32, i32, i64, i64, i32, i32, P, P, P]
+        lib.oracle_lplustimes.restype = i32
         lib.oracle_ltimes_sample.restype = i32
         lib.oracle_mlp_forward.argtypes = [i32, i32, i64] + [P] * 10
         lib.oracle_mlp_forward.restype = None
@@ -112,6 +115,19 @@ def ltimes(L: np.ndarray, x_phys: np.ndarray, G: int, Z: int, layout_in: int,
     if rc != 0:
         raise ValueError("oracle_ltimes: invalid arguments")
     return out
+
+
+def lplustimes(Lp: np.ndarray, out_phys: np.ndarray, in_phys: np.ndarray, G: int, Z: int,
+               layout_in: int, layout_out: int) -> np.ndarray:
+    """in + Lp-contraction of out (new physical `in` buffer; Lp is [D][M])."""
+    Lp = _f64(Lp)
+    D, M = Lp.shape
+    out_phys = _f64(out_phys)
+    res = np.array(in_phys, dtype=np.float64, copy=True)
+    rc = _load().oracle_lplustimes(M, D, G, Z, layout_in, layout_out, _p(Lp), _p(out_phys), _p(res))
+    if rc != 0:
+        raise ValueError("oracle_lplustimes: invalid arguments")
+    return res
 
 
 def ltimes_sample(L: np.ndarray, x_phys: np.ndarray, G: int, Z: int, layout_in: int,

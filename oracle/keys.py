@@ -7,7 +7,7 @@ strings} (Sec. 4, Algorithm 1, first step); our key is the byte image of the
 same information for a fixed set of kernel templates:
 
   offset size field
-  0      u16  kernel id (1 update chain, 2 LTimes, 3 grouped update chain)
+  0      u16  kernel id (1 update chain, 2 LTimes, 3 grouped update chain, 4 LPlusTimes)
   2      u8   dtype (0 f64, 1 f32, 2 bf16 operands / f32 state)
   3      u8   layout_a (chain: 0 row-major, 1 column-major; LTimes: in order 0..5)
   4      u8   layout_b (LTimes: out order 0..5; else 0)
@@ -44,6 +44,7 @@ import struct
 K_UPDATE_CHAIN = 1
 K_LTIMES = 2
 K_UPDATE_CHAIN_GROUPED = 3
+K_LPLUSTIMES = 4
 
 F64, F32, BF16 = 0, 1, 2
 
@@ -69,6 +70,8 @@ def default_tile(kernel: int, dtype: int, n: int, layout_a: int = 0, layout_b: i
         if n <= 4:
             return (2, 128, 0, 0)
         return (1, max(1, (256 if n <= 32 else 128) // n), 0, 0)
+    if kernel == K_LPLUSTIMES:     # LTimes of the swapped problem
+        return default_tile(K_LTIMES, dtype, n, layout_b, layout_a, d, m)
     if kernel == K_LTIMES:
         ct = 64
         gin, gout = layout_a in G_FAST, layout_b in G_FAST
@@ -91,7 +94,7 @@ def canonical_key(kernel: int, dtype: int, n=0, layout_a=0, layout_b=0, m=0, d=0
         m = d = layout_b = 0
         if kernel == K_UPDATE_CHAIN_GROUPED:
             layout_a = 0
-    elif kernel == K_LTIMES:
+    elif kernel in (K_LTIMES, K_LPLUSTIMES):
         n = 0
     if flags & FLAG_GENERIC:
         tile = (0, 0, 0, 0)            # the generic kernel has no tile template

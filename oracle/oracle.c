@@ -188,6 +188,27 @@ int oracle_ltimes(int M, int D, int64_t G, int64_t Z, int layout_in, int layout_
     return 0;
 }
 
+/* LPlusTimes, the adjoint contraction named beside LTimes in Sec. 5.2:
+ *   in[d][g][z] = in[d][g][z] + sum_{m=0}^{M-1} Lp[d][m] * out[m][g][z]   (m ascending)
+ * Lp is [D][M] row-major; `in` (order layout_in) is accumulated into. */
+int oracle_lplustimes(int M, int D, int64_t G, int64_t Z, int layout_in, int layout_out,
+                      const double *Lp, const double *out, double *in)
+{
+    if (M < 1 || D < 1 || G < 0 || Z < 0 || layout_in < 0 || layout_in > 5 ||
+        layout_out < 0 || layout_out > 5) return -1;
+    for (int64_t g = 0; g < G; ++g)
+        for (int d = 0; d < D; ++d)
+            for (int64_t z = 0; z < Z; ++z) {
+                double sum = 0.0;
+                for (int m = 0; m < M; ++m)
+                    sum = sum + Lp[(int64_t)d * M + m] *
+                                out[phys_offset(layout_out, M, G, Z, m, g, z)];
+                const int64_t o = phys_offset(layout_in, D, G, Z, d, g, z);
+                in[o] = in[o] + sum;
+            }
+    return 0;
+}
+
 /* Sampled outputs: out at the canonical (m, g, z) triples listed in idx
  * (3 entries per sample).  Used to check full-size results one by one. */
 int oracle_ltimes_sample(int M, int D, int64_t G, int64_t Z, int layout_in,

@@ -15,7 +15,7 @@ CJ_OK, CJ_ERR_INVALID_ARG, CJ_ERR_NOT_INITIALIZED, CJ_ERR_NO_DEVICE = 0, 1, 2, 3
 CJ_ERR_UNSUPPORTED_ARCH, CJ_ERR_COMPILE, CJ_ERR_CUDA, CJ_ERR_OOM = 4, 5, 6, 7
 CJ_ERR_TIMEOUT, CJ_ERR_PENDING = 8, 9
 
-K_UPDATE_CHAIN, K_LTIMES, K_UPDATE_CHAIN_GROUPED = 1, 2, 3
+K_UPDATE_CHAIN, K_LTIMES, K_UPDATE_CHAIN_GROUPED, K_LPLUSTIMES = 1, 2, 3, 4
 F64, F32, BF16 = 0, 1, 2
 FLAG_GENERIC, FLAG_NO_AOT, FLAG_INJECT_COMPILE_ERROR = 0x1, 0x2, 0x100
 CFG_COMPILE_ONLY = 0x1
@@ -206,6 +206,13 @@ def launch_ltimes(h: Handle, L, x, out, G: int, Z: int, stream=None) -> None:
     vals = [ctypes.c_void_p(_ptr(L)), ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(out)),
             ctypes.c_int64(G), ctypes.c_int64(Z)]
     _launch(h, vals, Z, _stream(stream, L, x, out))
+
+
+def launch_lplustimes(h: Handle, Lp, out, x, G: int, Z: int, stream=None) -> None:
+    """x += Lp . out (LPlusTimes): Lp [d][m], out (m*G*Z, layout_b), x (d*G*Z, layout_a)."""
+    vals = [ctypes.c_void_p(_ptr(Lp)), ctypes.c_void_p(_ptr(out)), ctypes.c_void_p(_ptr(x)),
+            ctypes.c_int64(G), ctypes.c_int64(Z)]
+    _launch(h, vals, Z, _stream(stream, Lp, out, x))
 
 
 def launch_grouped(h: Handle, items, A_pool, X_pool, counter, n_items: int, stream=None) -> None:

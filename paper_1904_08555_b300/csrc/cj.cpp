@@ -193,19 +193,31 @@ const char *ctype(int dtype) { return dtype == CJ_F64 ? "double" : "float"; }
 // ---------------------------------------------------------------------------
 bool g_fast(int lay) { return lay == 1 || lay == 4; }
 bool z_fast(int lay) { return lay == 0 || lay == 2; }
+bool is_lt(int k) { return k == CJ_K_LTIMES || k == CJ_K_LPLUSTIMES; }
+
+// The LTimes kernel a request runs: LPlusTimes is LTimes of the swapped
+// problem (output rows d, contracted m, orders exchanged) with accumulation.
+struct LtView {
+    int m, d, lin, lout, acc;
+};
+LtView lt_view(int k, const cj_template_args &a) {
+    if (k == CJ_K_LPLUSTIMES) return {a.d, a.m, a.layout_b, a.layout_a, 1};
+    return {a.m, a.d, a.layout_a, a.layout_b, 0};
+}
 
 void default_tile(int k, cj_template_args &a) {
-    if (k == CJ_K_UPDATE_CHAIN || k == CJ_K_UPDATE_CHAIN_GROUPED) {
+    if (!is_lt(k)) {
         a.tile[0] = cjint::chain_default_map(a.n, a.dtype);
         a.tile[1] = cjint::chain_default_ipb(a.n, a.dtype);
         a.tile[2] = a.tile[3] = 0;
         return;
     }
-    const int ct = a.dtype == CJ_F64 ? 64 : 128;
-    const bool gi = g_fast(a.layout_a), go = g_fast(a.layout_b);
+    const int ct = 64;
+    const LtView v = lt_view(k, a);
+    const bool gi = g_fast(v.lin), go = g_fast(v.lout);
     int tg;
     if (!gi && !go) tg = 1;
-    else if ((gi && z_fast(a.layout_b)) || (go && z_fast(a.layout_a))) tg = 8;
+    else if ((gi && z_fast(v.lout)) || (go && z_fast(v.lin))) tg = 8;
     else tg = 32;
     a.tile[0] = tg;
     a.tile[1] = ct / tg;
@@ -213,12 +225,12 @@ void default_tile(int k, cj_template_args &a) {
         // 64 columns, R 2, S 12, pipelined loads; threads = 32 * ceil(m / 12)
         a.tile[0] = tg;
         a.tile[1] = 64 / tg;
-        a.tile[2] = 32 * ((a.m + 11) / 12);
+        a.tile[2] = 32 * ((v.m + 11) / 12);
         a.tile[3] = (1 << 20) | (2 << 8) | 12;
         return;
     }
     // other f64: R 1, S 9; threads = CT * ceil(m / 9)
-    a.tile[2] = ct * ((a.m + 8) / 9);
+    a.tile[2] = ct * ((v.m + 8) / 9);
     a.tile[3] = (1 << 8) | 9;
 }
 
@@ -240,11 +252,11 @@ void make_key(int k, const cj_template_args &a, unsigned char *key) {
 
 cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_args &a) {
     a = in;
-    if (k != CJ_K_UPDATE_CHAIN && k != CJ_K_LTIMES && k != CJ_K_UPDATE_CHAIN_GROUPED)
+    if (k != CJ_K_UPDATE_CHAIN && k != CJ_K_LTIMES && k != CJ_K_UPDATE_CHAIN_GROUPED && k != CJ_K_LPLUSTIMES)
         return fail(CJ_ERR_INVALID_ARG, "unknown kernel id %d", k);
     if (a.dtype < 0 || a.dtype > 2) return fail(CJ_ERR_INVALID_ARG, "dtype %d out of range", a.dtype);
     if (a.flags & ~kKeyFlags) return fail(CJ_ERR_INVALID_ARG, "unknown flag bits 0x%x", a.flags & ~kKeyFlags);
-    if (k == CJ_K_LTIMES) {
+    if (is_lt(k)) {
         if (a.dtype == CJ_BF16) return fail(CJ_ERR_INVALID_ARG, "LTimes supports f64 and f32 only");
         if (a.layout_a < 0 || a.layout_a > 5 || a.layout_b < 0 || a.layout_b > 5)
             return fail(CJ_ERR_INVALID_ARG, "LTimes storage orders must be 0..5");
@@ -264,7 +276,7 @@ cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_
     }
     if (a.tile[0] == 0 && a.tile[1] == 0 && a.tile[2] == 0 && a.tile[3] == 0) {
         bool chosen = false;
-        if (G.cfg.use_cost_model && !G.compile_only && k != CJ_K_UPDATE_CHAIN_GROUPED) {
+        if (G.cfg.use_cost_model && !G.compile_only && (k == CJ_K_UPDATE_CHAIN || k == CJ_K_LTIMES)) {
             unsigned char rk[32];
             make_key(k, a, rk);
             const std::string rs(reinterpret_cast<char *>(rk), 32);
@@ -286,7 +298,7 @@ cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_
         if (!chosen) default_tile(k, a);
     }
     // explicit tiles: check the kernel can be instantiated and launched
-    if (k != CJ_K_LTIMES) {
+    if (!is_lt(k)) {
         const int map = a.tile[0], ipb = a.tile[1];
         if (map < 1 || map > 5) return fail(CJ_ERR_INVALID_ARG, "update chain mapping %d must be 1..5", map);
         if (map == 5 && (a.dtype != CJ_F32 || a.n % 4 || a.n < 8))
@@ -303,23 +315,24 @@ cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_
             return fail(CJ_ERR_INVALID_ARG, "tile needs too much shared memory");
     } else {
         const int tg = a.tile[0], tz = a.tile[1], nt = a.tile[2];
+        const LtView v = lt_view(k, a);
         const int pipe = (a.tile[3] >> 20) & 0xf, mode = (a.tile[3] >> 16) & 0xf;
         const int r = (a.tile[3] >> 8) & 0xff, s = a.tile[3] & 0xff;
         if (pipe > 1 || (a.tile[3] >> 24)) return fail(CJ_ERR_INVALID_ARG, "LTimes tile flags 0x%x unknown", a.tile[3]);
-        if (mode == 1 && (a.dtype != CJ_F64 || s != 8 || a.d % 4 || r < 1 || (tg * tz) % (8 * r) ||
+        if (mode == 1 && (a.dtype != CJ_F64 || s != 8 || v.d % 4 || r < 1 || (tg * tz) % (8 * r) ||
                           (tg * tz / (8 * r)) * 32 != nt || nt > 1024))
             return fail(CJ_ERR_INVALID_ARG, "LTimes tensor-core tile {%d,%d,%d,0x%x} invalid (f64, S = 8, d %% 4 == 0, "
                         "threads = 32 * TG * TZ / (8 R))", a.tile[0], a.tile[1], a.tile[2], a.tile[3]);
-        if (mode == 2 && (a.dtype != CJ_F32 || s != 8 || r != 1 || a.d % 8 || (tg * tz) % 16 ||
+        if (mode == 2 && (a.dtype != CJ_F32 || s != 8 || r != 1 || v.d % 8 || (tg * tz) % 16 ||
                           (tg * tz / 16) * 32 != nt || nt > 1024))
             return fail(CJ_ERR_INVALID_ARG, "LTimes 3xTF32 tile {%d,%d,%d,0x%x} invalid (f32, R = 1, S = 8, d %% 8 == 0, "
                         "threads = 32 * TG * TZ / 16)", a.tile[0], a.tile[1], a.tile[2], a.tile[3]);
         if (mode > 2) return fail(CJ_ERR_INVALID_ARG, "LTimes compute mode %d unknown", mode);
         if (mode == 0 && (tg < 1 || tz < 1 || r < 1 || s < 1 || nt < 32 || nt > 1024 || (tg * tz) % r ||
-                          (tg * tz / r) * ((a.m + s - 1) / s) != nt))
+                          (tg * tz / r) * ((v.m + s - 1) / s) != nt))
             return fail(CJ_ERR_INVALID_ARG, "LTimes tile {%d,%d,%d,%d} does not cover its block", a.tile[0],
                         a.tile[1], a.tile[2], a.tile[3]);
-        if (cjg::lt_smem(a.m, s, a.d, tg * tz, esize(a.dtype), pipe, mode) > 220 * 1024)
+        if (cjg::lt_smem(v.m, s, v.d, tg * tz, esize(a.dtype), pipe, mode) > 220 * 1024)
             return fail(CJ_ERR_INVALID_ARG, "LTimes tile needs too much shared memory");
     }
     return CJ_OK;
@@ -339,10 +352,11 @@ void generic_impl(cj_handle_s *h) {
     const cj_template_args &a = h->a;
     const int di = dt_index(a.dtype), es = esize(a.dtype);
     g.variant = V_GENERIC;
-    if (h->kernel == CJ_K_LTIMES) {
+    if (is_lt(h->kernel)) {
+        const LtView v = lt_view(h->kernel, a);
         g.fn = G.gen_lt[di];
         g.threads = a.dtype == CJ_F64 ? 64 : 128;
-        g.smem = (size_t)cjg::lt_generic_smem(a.m, a.d, g.threads, es);
+        g.smem = (size_t)cjg::lt_generic_smem(v.m, v.d, g.threads, es);
     } else {
         g.fn = h->kernel == CJ_K_UPDATE_CHAIN ? G.gen_chain[di] : G.gen_grp[di];
         g.ipb = std::max(1, 128 / a.n);
@@ -355,9 +369,10 @@ void generic_impl(cj_handle_s *h) {
 void spec_geometry(const cj_handle_s *h, Impl &s) {
     const cj_template_args &a = h->a;
     const int es = esize(a.dtype);
-    if (h->kernel == CJ_K_LTIMES) {
+    if (is_lt(h->kernel)) {
+        const LtView v = lt_view(h->kernel, a);
         s.threads = a.tile[2];
-        s.smem = (size_t)cjg::lt_smem(a.m, a.tile[3] & 0xff, a.d, a.tile[0] * a.tile[1], es, (a.tile[3] >> 20) & 1,
+        s.smem = (size_t)cjg::lt_smem(v.m, a.tile[3] & 0xff, v.d, a.tile[0] * a.tile[1], es, (a.tile[3] >> 20) & 1,
                                       (a.tile[3] >> 16) & 0xf);
     } else {
         s.ipb = a.tile[1];
@@ -375,10 +390,12 @@ std::string name_expression(const cj_handle_s *h) {
     else if (h->kernel == CJ_K_UPDATE_CHAIN_GROUPED)
         snprintf(buf, sizeof buf, "cj::update_chain_grouped<%s, %d, %d, %d>", ctype(a.dtype), a.n, a.tile[0],
                  a.tile[1]);
-    else
-        snprintf(buf, sizeof buf, "cj::ltimes<%s, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d>", ctype(a.dtype), a.m,
-                 a.d, a.layout_a, a.layout_b, a.tile[0], a.tile[1], a.tile[2], (a.tile[3] >> 8) & 0xff,
-                 a.tile[3] & 0xff, (a.tile[3] >> 16) & 0xf, (a.tile[3] >> 20) & 0xf);
+    else {
+        const LtView v = lt_view(h->kernel, a);
+        snprintf(buf, sizeof buf, "cj::ltimes<%s, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d>", ctype(a.dtype), v.m,
+                 v.d, v.lin, v.lout, a.tile[0], a.tile[1], a.tile[2], (a.tile[3] >> 8) & 0xff, a.tile[3] & 0xff,
+                 (a.tile[3] >> 16) & 0xf, (a.tile[3] >> 20) & 0xf, v.acc);
+    }
     return buf;
 }
 
@@ -444,7 +461,7 @@ void finish(cj_handle_s *h, int state) {
 
 cj_status compile_handle(cj_handle_s *h) {
     const auto t0 = clk::now();
-    std::string src = h->kernel == CJ_K_LTIMES ? "#include \"ltimes.cuh\"\n" : "#include \"update_chain.cuh\"\n";
+    std::string src = is_lt(h->kernel) ? "#include \"ltimes.cuh\"\n" : "#include \"update_chain.cuh\"\n";
     if (h->a.flags & CJ_FLAG_INJECT_COMPILE_ERROR)
         src += "namespace cj { __device__ int injected_failure = this_identifier_does_not_exist; }\n";
     CompileOut c = nvrtc_compile(src, h->name_expr.c_str());
@@ -756,7 +773,7 @@ CJ_API cj_status cj_specialize_wait(cj_handle h, int timeout_ms) {
 CJ_API cj_status cj_launch(cj_handle h, void *const *args, int64_t batch, void *cuda_stream) {
     if (!G.inited) return fail(CJ_ERR_NOT_INITIALIZED, "cj_init has not been called");
     if (!h || !args || batch < 0) return fail(CJ_ERR_INVALID_ARG, "null handle/args or negative batch");
-    for (int i = 0; i < (h->kernel == CJ_K_LTIMES ? 5 : h->kernel == CJ_K_UPDATE_CHAIN ? 3 : 4); ++i)
+    for (int i = 0; i < (is_lt(h->kernel) ? 5 : h->kernel == CJ_K_UPDATE_CHAIN ? 3 : 4); ++i)
         if (!args[i]) return fail(CJ_ERR_INVALID_ARG, "argument %d is null", i);
     if (G.compile_only) return fail(CJ_ERR_NO_DEVICE, "library initialised in compile-only mode");
     const Impl *im = h->impl.load(std::memory_order_acquire);
@@ -780,7 +797,8 @@ CJ_API cj_status cj_launch(cj_handle h, void *const *args, int64_t batch, void *
             void *p[] = {&A, &X, &b, &steps, &c};
             r = drv.LaunchKernel(im->fn, grid, 1, 1, im->threads, 1, 1, (unsigned)im->smem, st, p, nullptr);
         }
-    } else if (h->kernel == CJ_K_LTIMES) {
+    } else if (is_lt(h->kernel)) {
+        const LtView v = lt_view(h->kernel, a);
         void *L = *reinterpret_cast<void *const *>(args[0]);
         void *in = *reinterpret_cast<void *const *>(args[1]);
         void *out = *reinterpret_cast<void *const *>(args[2]);
@@ -789,7 +807,7 @@ CJ_API cj_status cj_launch(cj_handle h, void *const *args, int64_t batch, void *
         if (!L || !in || !out || Gx < 0 || Zx < 0) return fail(CJ_ERR_INVALID_ARG, "null tensor or negative G/Z");
         if (Gx == 0 || Zx == 0) return CJ_OK;
         if (im->variant == V_GENERIC) {
-            int M = a.m, D = a.d;
+            int M = v.m, D = v.d, acc = v.acc;
             auto strides = [&](int lay, long long ex, long long *s) {
                 // s[axis] for axis 0 = x, 1 = g, 2 = z
                 const long long e[3] = {ex, Gx, Zx};
@@ -800,11 +818,11 @@ CJ_API cj_status cj_launch(cj_handle h, void *const *args, int64_t batch, void *
                 s[o[0]] = e[o[2]] * e[o[1]];
             };
             long long si[3], so[3];
-            strides(a.layout_a, D, si);
-            strides(a.layout_b, M, so);
+            strides(v.lin, D, si);
+            strides(v.lout, M, so);
             const long long cols = Gx * Zx;
             const unsigned grid = (unsigned)((cols + im->threads - 1) / im->threads);
-            void *p[] = {&L, &in, &out, &Gx, &Zx, &M, &D, &si[0], &si[1], &si[2], &so[0], &so[1], &so[2]};
+            void *p[] = {&L, &in, &out, &Gx, &Zx, &M, &D, &si[0], &si[1], &si[2], &so[0], &so[1], &so[2], &acc};
             r = drv.LaunchKernel(im->fn, grid, 1, 1, im->threads, 1, 1, (unsigned)im->smem, st, p, nullptr);
         } else {
             const long long ntiles = ((Gx + a.tile[0] - 1) / a.tile[0]) * ((Zx + a.tile[1] - 1) / a.tile[1]);

@@ -36,7 +36,7 @@ __host__ __device__ constexpr int lt_axis(int lay, int s) {
 // EX, G, Z, box origin (0, g0, z0)) and shared memory laid out as
 // s[x * CP + gl * TZ + zl].  Consecutive threads walk the box in storage
 // order, so each warp touches consecutive global addresses.
-template <class T, int LAY, int EX, int TG, int TZ, int CP, int NT, bool LOAD>
+template <class T, int LAY, int EX, int TG, int TZ, int CP, int NT, bool LOAD, bool ACC = false>
 __device__ __forceinline__ void lt_box(T* __restrict__ g, T* s, long long G, long long Z,
                                        long long g0, long long z0, int tid) {
     constexpr int a0 = lt_axis(LAY, 0), a1 = lt_axis(LAY, 1), a2 = lt_axis(LAY, 2);
@@ -64,7 +64,7 @@ __device__ __forceinline__ void lt_box(T* __restrict__ g, T* s, long long G, lon
         const long long goff = gbase + (long long)x * st[0] + (long long)gl * st[1] + (long long)zl * st[2];
         T* sp = s + x * CP + gl * TZ + zl;
         if (LOAD) *sp = ok ? g[goff] : T(0);
-        else if (ok) g[goff] = *sp;
+        else if (ok) g[goff] = ACC ? g[goff] + *sp : *sp;
     }
 }
 
@@ -143,9 +143,10 @@ __device__ __forceinline__ void lt_async_wait() { asm volatile("cp.async.wait_gr
 // MODE 0: FMA pipe, each thread R columns x S moments.  MODE 1 (FP64 only,
 // S = 8, D a multiple of 4): FP64 tensor cores, each warp 8R columns x all
 // moments.  PIPE 1: two tile buffers; the next tile's box is loaded with
-// cp.async while the current one is contracted.
+// cp.async while the current one is contracted.  ACC 1: out += result
+// (LPlusTimes accumulates into its output).
 template <class T, int M, int D, int LIN, int LOUT, int TG, int TZ, int NT, int R, int S, int MODE = 0,
-          int PIPE = 0>
+          int PIPE = 0, int ACC = 0>
 __global__ void __launch_bounds__(NT)
 ltimes(const T* __restrict__ L, const T* __restrict__ in, T* __restrict__ out, long long G, long long Z) {
     constexpr int CT = TG * TZ;
@@ -239,7 +240,7 @@ ltimes(const T* __restrict__ L, const T* __restrict__ in, T* __restrict__ out, l
                     if (M % 8 == 0 || m < M) sX[m * CP + q] = acc[nb][i];
                 }
             __syncthreads();
-            lt_box<T, LOUT, M, TG, TZ, CP, NT, false>(out, sX, G, Z, g0, z0, tid);
+            lt_box<T, LOUT, M, TG, TZ, CP, NT, false, ACC != 0>(out, sX, G, Z, g0, z0, tid);
             continue;
         }
         if constexpr (MODE == 1) {
@@ -273,7 +274,7 @@ ltimes(const T* __restrict__ L, const T* __restrict__ in, T* __restrict__ out, l
                         if (M % 8 == 0 || m < M) sX[m * CP + c0 + 8 * cb + r] = acc[cb][nb][i];
                     }
             __syncthreads();
-            lt_box<T, LOUT, M, TG, TZ, CP, NT, false>(out, sX, G, Z, g0, z0, tid);
+            lt_box<T, LOUT, M, TG, TZ, CP, NT, false, ACC != 0>(out, sX, G, Z, g0, z0, tid);
             continue;
         }
         T acc[R][S];
@@ -300,12 +301,12 @@ ltimes(const T* __restrict__ L, const T* __restrict__ in, T* __restrict__ out, l
 #pragma unroll
                 for (int r = 0; r < R; ++r) sX[(m0 + s) * CP + q0 + r] = acc[r][s];
         __syncthreads();
-        lt_box<T, LOUT, M, TG, TZ, CP, NT, false>(out, sX, G, Z, g0, z0, tid);
+        lt_box<T, LOUT, M, TG, TZ, CP, NT, false, ACC != 0>(out, sX, G, Z, g0, z0, tid);
     }
     if (PIPE) lt_async_wait<0>();
 }
 
-// Generic: run-time M, D and strides; one thread per column q = g*Z + z
+// Generic: run-time M, D, strides and accumulate flag; one thread per column q = g*Z + z
 // (z fastest), blockDim.x columns per block.  The column's D inputs are
 // staged in shared memory with the thread's own loads (coalesced only when z
 // is the fastest axis of `in`), L is read from shared memory.
@@ -313,7 +314,7 @@ template <class T>
 __global__ void __launch_bounds__(128)
 ltimes_generic(const T* __restrict__ L, const T* __restrict__ in, T* __restrict__ out, long long G,
                long long Z, int M, int D, long long si_x, long long si_g, long long si_z,
-               long long so_x, long long so_g, long long so_z) {
+               long long so_x, long long so_g, long long so_z, int acc) {
     extern __shared__ __align__(16) unsigned char cj_smem[];
     T* sL = reinterpret_cast<T*>(cj_smem);
     const int cols = blockDim.x;
@@ -330,7 +331,8 @@ ltimes_generic(const T* __restrict__ L, const T* __restrict__ in, T* __restrict_
     for (int m = 0; m < M; ++m) {
         T s = T(0);
         for (int d = 0; d < D; ++d) s = lt_fma(sL[m * D + d], sX[d * cols + tid], s);
-        out[m * so_x + g * so_g + z * so_z] = s;
+        T* o = out + m * so_x + g * so_g + z * so_z;
+        *o = acc ? *o + s : s;
     }
 }
 

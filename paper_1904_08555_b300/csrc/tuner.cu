@@ -103,20 +103,32 @@ void ltimes_candidates(const cj_template_args &a, std::vector<std::array<int, 4>
     }
 }
 
+// LPlusTimes runs the LTimes kernel of the swapped problem.
+cj_template_args lt_swapped(int k, const cj_template_args &a) {
+    if (k != CJ_K_LPLUSTIMES) return a;
+    cj_template_args s = a;
+    s.m = a.d;
+    s.d = a.m;
+    s.layout_a = a.layout_b;
+    s.layout_b = a.layout_a;
+    return s;
+}
+
 // ---------------------------------------------------------------------------
 // Features
 // ---------------------------------------------------------------------------
 double lg2(double v) { return std::log2(std::max(v, 1.0)); }
 
-void featurize(int k, const cj_template_args &a, int64_t batch, int32_t steps, const int *tile, float *f) {
+void featurize(int k, const cj_template_args &a0, int64_t batch, int32_t steps, const int *tile, float *f) {
     std::memset(f, 0, sizeof(float) * CJ_FEATURES);
+    const cj_template_args a = lt_swapped(k, a0);
     f[0] = k == CJ_K_UPDATE_CHAIN;
-    f[1] = k == CJ_K_LTIMES;
+    f[1] = k == CJ_K_LTIMES || k == CJ_K_LPLUSTIMES;
     f[2] = k == CJ_K_UPDATE_CHAIN_GROUPED;
     f[3 + std::min(std::max(a.dtype, 0), 2)] = 1.f;
     const int es = esize(a.dtype);
     double flops, bytes;
-    if (k == CJ_K_LTIMES) {
+    if (k == CJ_K_LTIMES || k == CJ_K_LPLUSTIMES) {
         const double cols = (double)batch;
         flops = 2.0 * a.m * a.d * cols;
         bytes = es * ((double)(a.d + a.m) * cols + a.m * a.d);
@@ -157,7 +169,7 @@ void featurize(int k, const cj_template_args &a, int64_t batch, int32_t steps, c
 
 cj_status candidates(int k, const cj_template_args &a, std::vector<std::array<int, 4>> &out) {
     out.clear();
-    if (k == CJ_K_LTIMES) ltimes_candidates(a, out);
+    if (k == CJ_K_LTIMES || k == CJ_K_LPLUSTIMES) ltimes_candidates(lt_swapped(k, a), out);
     else chain_candidates(a, out);
     if (out.empty()) return tfail(CJ_ERR_INVALID_ARG, "no candidate tile fits these arguments");
     return CJ_OK;

@@ -220,3 +220,12 @@ def test_every_candidate_tile_is_a_valid_request(compile_only_sync, req):
     for tile in cands:
         f = cj.featurize(k, batch=1 << 16, steps=64, tile=tile, **req)
         assert f.shape == (cj.FEATURES,) and np.all(np.isfinite(f)) and f[31] == 1.0
+
+
+def test_lplustimes_keys_and_compiles(compile_only_sync):
+    from oracle import keys as K
+    h = cj.specialize(cj.K_LPLUSTIMES, cj.F64, layout_a=3, layout_b=1, m=36, d=96)
+    assert h.key_hex == K.canonical_key(K.K_LPLUSTIMES, K.F64, layout_a=3, layout_b=1, m=36, d=96).hex()
+    assert h.variant == "jit"
+    assert cj.specialize(cj.K_LPLUSTIMES, cj.F32, layout_a=0, layout_b=5, m=36, d=96).variant == "jit"
+    assert len(cj.candidates(cj.K_LPLUSTIMES, cj.F32, layout_a=0, layout_b=5, m=36, d=96)) >= 4

@@ -99,3 +99,31 @@ def test_threads_do_not_change_results():
     phys = synth.to_layout(x, 2).ravel()
     np.testing.assert_array_equal(oracle.ltimes(L, phys, G, Z, 2, 4, nthreads=1),
                                   oracle.ltimes(L, phys, G, Z, 2, 4, nthreads=3))
+
+
+# ---------------------------------------------------------------------------
+# LPlusTimes (the adjoint contraction): in += Lp . out
+# ---------------------------------------------------------------------------
+
+def test_lplustimes_is_the_adjoint_of_ltimes():
+    """<LTimes(L, x), y> = <x, LPlusTimes(L^T, y)> for every pair of orders."""
+    M, D, G, Z = 5, 7, 3, 4
+    L, x = synth.ltimes_inputs_np(0xAD, M, D, G, Z)
+    y = synth.uniform_np(0xAE, 0, M * G * Z).reshape(M, G, Z)
+    for lin, lout in [(0, 0), (3, 1), (5, 4), (2, 5)]:
+        Lx = run(L, x, lin, lout)
+        back = oracle.lplustimes(L.T.copy(), synth.to_layout(y, lout).ravel(), np.zeros(D * G * Z), G, Z, lin, lout)
+        lhs = math.fsum((Lx * y).ravel())
+        rhs = math.fsum((x * synth.from_layout(back, lin, (D, G, Z))).ravel())
+        assert abs(lhs - rhs) <= 1e-13 * max(1.0, abs(lhs))
+
+
+def test_lplustimes_accumulates_and_matches_gemm():
+    M, D, G, Z = 4, 6, 2, 5
+    Lp = synth.uniform_np(0xB1, 0, D * M).reshape(D, M)
+    y = synth.uniform_np(0xB2, 0, M * G * Z).reshape(M, G, Z)
+    base = synth.uniform_np(0xB3, 0, D * G * Z).reshape(D, G, Z)
+    res = oracle.lplustimes(Lp, synth.to_layout(y, 4).ravel(), synth.to_layout(base, 1).ravel(), G, Z, 1, 4)
+    got = synth.from_layout(res, 1, (D, G, Z))
+    ref = base + (Lp @ y.reshape(M, G * Z)).reshape(D, G, Z)
+    assert np.max(np.abs(got - ref)) <= 1e-14 * np.max(np.abs(ref))

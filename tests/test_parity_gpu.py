@@ -361,3 +361,29 @@ def test_full_size_ltimes_sampled(dt, lin, lout):
     got = canon[:, torch.from_numpy(gs).cuda(), torch.from_numpy(zs).cuda()].double().cpu().numpy()
     assert relF(got, ref) <= (TOL64 if dt == cj.F64 else TOL32)
     del x, xin, out
+
+
+# ---------------------------------------------------------------------------
+# LPlusTimes: in += Lp . out
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("lin,lout", [(0, 0), (3, 1), (4, 5), (2, 3)])
+@pytest.mark.parametrize("dt", [cj.F64, cj.F32])
+@pytest.mark.parametrize("generic", [False, True])
+def test_lplustimes_accumulates(lin, lout, dt, generic):
+    M, D, G, Z = 36, 96, 5, 41
+    Lp = synth.uniform_np(0xC1A6, 0, D * M).reshape(D, M)
+    y = synth.uniform_np(0xC1A7, 0, M * G * Z).reshape(M, G, Z)
+    base = synth.uniform_np(0xC1A8, 0, D * G * Z).reshape(D, G, Z)
+    ref_phys = oracle.lplustimes(Lp, synth.to_layout(y, lout).ravel(), synth.to_layout(base, lin).ravel(), G, Z,
+                                 lin, lout)
+    h = cj.specialize(cj.K_LPLUSTIMES, dt, layout_a=lin, layout_b=lout, m=M, d=D,
+                      flags=cj.FLAG_GENERIC if generic else 0)
+    tt = tdtype(dt)
+    Lt = torch.from_numpy(Lp).to("cuda", tt)
+    yt = torch.from_numpy(synth.to_layout(y, lout).ravel()).to("cuda", tt)
+    xt = torch.from_numpy(synth.to_layout(base, lin).ravel()).to("cuda", tt)
+    cj.launch_lplustimes(h, Lt, yt, xt, G, Z)
+    torch.cuda.synchronize()
+    got = xt.double().cpu().numpy()
+    assert relF(got, ref_phys) <= (TOL64 if dt == cj.F64 else TOL32)
