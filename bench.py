@@ -53,6 +53,22 @@ def chain_bytes(batch: int, n: int, esize: int) -> float:
 PEAK_TFLOPS = {"f64": 1.25, "f32": 148 * 128 * 2 * 2.032e9 / 1e12}
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per instance of
+# the sweep's roofline kernel, from the ncu capture summarised in
+# profiles/update_chain_f64_n32_fma_pipe.md (16384 instances, scaled by the
+# instance count; the kernel's traffic grows in proportion).  None for any
+# other kernel: the counters then do not describe it.
+TRAFFIC_PER_INSTANCE = {"update_chain<double, 32, 0, 1, 8>": (135.372288e6 + 88.970752e6) / 16384}
+
+
+def measured_peak(key: str, default: float) -> float:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key])
+    except (OSError, KeyError, ValueError):
+        return default
+
+
 def hbm_peak_gbs() -> float:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -302,6 +318,11 @@ def cj_arm(args):
         per_n.append(row)
     dom = max(SWEEP_N, key=lambda n: per_spec[n])
     achieved = chain_flops(batch[dom], dom, T_STEPS) / (per_spec[dom] * 1e-3) / 1e12
+    dom_key = bytes.fromhex(spec[dom].key_hex)
+    dom_tile = [int.from_bytes(dom_key[12 + 4 * i:16 + 4 * i], "little") for i in range(2)]
+    dom_name = f"update_chain<double, {dom}, 0, {dom_tile[0]}, {dom_tile[1]}>"
+    traffic = TRAFFIC_PER_INSTANCE.get(dom_name)
+    traffic = traffic * batch[dom] if traffic is not None else None
 
     # end to end through the C ABI with host buffers: H2D of A, launch, D2H of X, every size
     h2d = sum(chain_bytes(batch[n], n, 8) / 2 for n in SWEEP_N)
@@ -342,8 +363,10 @@ def cj_arm(args):
             "fp64_fma_pipe_tflops_measured": micro64, "fp64_tensor_tflops_measured": tensor64,
             "fp64_nominal_tflops": PEAK_TFLOPS["f64"],
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
-                         "frac": achieved / peak64, "traffic": None,
-                         "kernel": f"update_chain<double,{dom},...> (N = {dom})",
+                         "frac": achieved / peak64, "traffic": traffic,
+                         "traffic_unit": "bytes per launch (ncu, scaled from 16384 instances)",
+                         "algorithmic_bytes": chain_bytes(batch[dom], dom, 8),
+                         "kernel": dom_name,
                          "peak_source": "nominal B300 FP64 rate, 1.25 TFLOP/s (profiling recipe); the measured "
                                         "FMA-chain and mma.sync f64 microbenchmarks are reported beside it"},
             "per_n": per_n,
@@ -456,12 +479,14 @@ def secondary(args):
             X = torch.empty_like(A)
             f = chain_flops(b, n, steps)
             row = {"N": n, "batch": b}
-            variants = [("jit", cj.FLAG_NO_AOT), ("generic", cj.FLAG_GENERIC)]
+            variants = [("jit", cj.FLAG_NO_AOT, (0, 0, 0, 0)), ("generic", cj.FLAG_GENERIC, (0, 0, 0, 0))]
             if n in AOT_N:
-                variants.append(("aot", 0))
+                variants.append(("aot", 0, (0, 0, 0, 0)))
+            if dt == cj.F32 and n % 4 == 0 and n >= 8:
+                variants.append(("regblock", 0, (5, max(1, 256 // ((n // 4) ** 2)), 0, 0)))
             reps = 200 if b == 64 else K
-            for name, fl in variants:
-                h = cj.specialize(cj.K_UPDATE_CHAIN, dt, n=n, flags=fl)
+            for name, fl, tile in variants:
+                h = cj.specialize(cj.K_UPDATE_CHAIN, dt, n=n, flags=fl, tile=tile)
                 fn = lambda h=h: cj.launch_update_chain(h, A, X, steps, stream=stream)
                 _events(torch, stream, fn, W)
                 ms = _events(torch, stream, fn, reps)
@@ -552,7 +577,7 @@ def secondary(args):
             _events(torch, stream, fn, W)
             res[name] = _events(torch, stream, fn, max(K, 10))
             plan.destroy()
-        peak = PEAK_TFLOPS["f32" if args.dtype == "bf16" else args.dtype]
+        peak = measured_peak("bf16_tflops", 1800.0) if args.dtype == "bf16" else PEAK_TFLOPS[args.dtype]
         out.update({"value": f / res["spec"] / 1e6, "dtype": args.dtype,
                     "generic": {"value": f / res["generic"] / 1e6, "unit": "GFLOP/s", "ms": res["generic"]},
                     "ms_per_launch": res["spec"], "speedup_vs_generic": res["generic"] / res["spec"],
