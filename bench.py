@@ -427,7 +427,8 @@ def main():
         gi, go = lin in (1, 4), lout in (1, 4)
         tg = 1 if not (gi or go) else (8 if (gi and lout in (0, 2)) or (go and lin in (0, 2)) else 32)
         return [("tf32x3", (tg, 64 // tg, 128, (1 << 20) | (2 << 16) | (1 << 8) | 8)),
-                ("tf32x3_ct128", (tg, 128 // tg, 256, (1 << 20) | (2 << 16) | (1 << 8) | 8))]
+                ("direct_r2", (tg, 256 // tg, 128, (3 << 16) | (2 << 8))),
+                ("direct_r1", (tg, 128 // tg, 128, (3 << 16) | (1 << 8)))]
     args.lt_alt_tiles = lt_alt_tiles
     if args.impl == "reference":
         reference_arm(args)

@@ -72,6 +72,10 @@ CJ_HD constexpr long lt_smem(int m, int s, int d, int ct, int esize, int pipe = 
             (pipe ? 2L : 1L) * (long)(m > d ? m : d) * lt_cpitch(ct, esize, mode)) *
            esize;
 }
+// Direct kernel (mode 3): L^T plus one out box.
+CJ_HD constexpr long lt_direct_smem(int m, int d, int ct, int esize) {
+    return ((long)d * lt_mpitch(m, esize) + (long)m * lt_cpitch(ct, esize)) * esize;
+}
 CJ_HD constexpr long lt_generic_smem(int m, int d, int cols, int esize) {
     return ((long)m * d + (long)d * cols) * esize;
 }

@@ -306,6 +306,104 @@ ltimes(const T* __restrict__ L, const T* __restrict__ in, T* __restrict__ out, l
     if (PIPE) lt_async_wait<0>();
 }
 
+// Direct FP32 kernel (MODE 3): no staging of `in`.  A block owns a TG x TZ
+// box of (g, z) columns; thread t owns R consecutive columns in the order of
+// `in`'s faster column axis and reads its columns straight from global memory
+// (coalesced across the warp; 16-byte vectors along d when d is fastest),
+// accumulating all M moments in registers against broadcast reads of L^T.
+// Only the out box goes through shared memory, so that it is stored
+// coalesced in any order of `out`.
+template <class T, int M, int D, int LIN, int LOUT, int TG, int TZ, int NT, int R, int ACC = 0>
+__global__ void __launch_bounds__(NT)
+ltimes_direct(const T* __restrict__ L, const T* __restrict__ in, T* __restrict__ out, long long G, long long Z) {
+    constexpr int CT = TG * TZ;
+    constexpr int MP = cjg::lt_mpitch(M, (int)sizeof(T));
+    constexpr int CP = cjg::lt_cpitch(CT, (int)sizeof(T));
+    static_assert(CT == NT * R, "tile does not cover the block");
+    // in's faster column axis: z unless g comes after z in the storage order
+    constexpr bool G_FASTER = lt_pos(LIN, 1) > lt_pos(LIN, 2);
+    constexpr bool D_FAST = lt_pos(LIN, 0) == 2;
+    extern __shared__ __align__(16) unsigned char cj_smem[];
+    T* sL = reinterpret_cast<T*>(cj_smem);   // [D][MP], L transposed
+    T* sO = sL + D * MP;                      // [M][CP] out box
+    const int tid = threadIdx.x;
+    for (int e = tid; e < MP * D; e += NT) {
+        const int m = e / D, d = e - m * D;
+        sL[d * MP + m] = m < M ? L[e] : T(0);
+    }
+    // strides of in along (d, g, z)
+    const long long ext[3] = {D, G, Z};
+    long long st[3];
+    st[lt_axis(LIN, 2)] = 1;
+    st[lt_axis(LIN, 1)] = ext[lt_axis(LIN, 2)];
+    st[lt_axis(LIN, 0)] = ext[lt_axis(LIN, 2)] * ext[lt_axis(LIN, 1)];
+    const long long ntg = (G + TG - 1) / TG, ntz = (Z + TZ - 1) / TZ;
+    const long long ntiles = ntg * ntz;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const long long g0 = (t / ntz) * TG, z0 = (t % ntz) * TZ;
+        long long off[R];
+        int sidx[R];
+        bool ok[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int c = tid * R + r;
+            const int gl = G_FASTER ? c % TG : c / TZ;
+            const int zl = G_FASTER ? c / TG : c % TZ;
+            ok[r] = (g0 + gl < G) && (z0 + zl < Z);
+            off[r] = ok[r] ? (g0 + gl) * st[1] + (z0 + zl) * st[2] : 0;
+            sidx[r] = gl * TZ + zl;
+        }
+        __syncthreads();   // sL ready (first tile); previous out box stored
+        T acc[R][M];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int m = 0; m < M; ++m) acc[r][m] = T(0);
+        if constexpr (D_FAST && sizeof(T) == 4 && D % 4 == 0) {
+#pragma unroll 2
+            for (int d = 0; d < D; d += 4) {
+                float4 xv[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    xv[r] = ok[r] ? __ldg(reinterpret_cast<const float4*>(in + off[r] + d)) : make_float4(0, 0, 0, 0);
+#pragma unroll
+                for (int dd = 0; dd < 4; ++dd) {
+                    const T* lrow = sL + (d + dd) * MP;
+#pragma unroll
+                    for (int m = 0; m < M; ++m) {
+                        const T lv = lrow[m];
+#pragma unroll
+                        for (int r = 0; r < R; ++r) {
+                            const T x = dd == 0 ? xv[r].x : dd == 1 ? xv[r].y : dd == 2 ? xv[r].z : xv[r].w;
+                            acc[r][m] = lt_fma(lv, x, acc[r][m]);
+                        }
+                    }
+                }
+            }
+        } else {
+#pragma unroll 4
+            for (int d = 0; d < D; ++d) {
+                T x[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) x[r] = ok[r] ? __ldg(in + off[r] + d * st[0]) : T(0);
+                const T* lrow = sL + d * MP;
+#pragma unroll
+                for (int m = 0; m < M; ++m) {
+                    const T lv = lrow[m];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) acc[r][m] = lt_fma(lv, x[r], acc[r][m]);
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int m = 0; m < M; ++m) sO[m * CP + sidx[r]] = acc[r][m];
+        __syncthreads();
+        lt_box<T, LOUT, M, TG, TZ, CP, NT, false, ACC != 0>(out, sO, G, Z, g0, z0, tid);
+    }
+}
+
 // Generic: run-time M, D, strides and accumulate flag; one thread per column q = g*Z + z
 // (z fastest), blockDim.x columns per block.  The column's D inputs are
 // staged in shared memory with the thread's own loads (coalesced only when z

@@ -78,6 +78,13 @@ void ltimes_candidates(const cj_template_args &a, std::vector<std::array<int, 4>
         } else if (mode == 2) {
             if (ct % 16 || a.d % 8) return;
             nt = ct / 16 * 32;
+        } else if (mode == 3) {
+            if (ct % r) return;
+            nt = ct / r;
+            if (nt < 32 || nt > 1024) return;
+            if (cjg::lt_direct_smem(a.m, a.d, ct, es) > 200 * 1024) return;
+            out.push_back({tg, ct / tg, nt, (3 << 16) | (r << 8) | s});
+            return;
         } else {
             if (ct % r) return;
             nt = (ct / r) * ((a.m + s - 1) / s);
@@ -96,8 +103,10 @@ void ltimes_candidates(const cj_template_args &a, std::vector<std::array<int, 4>
         } else {
             for (int ct : {64, 128}) {
                 push(tg, ct, 2, 1, 8, 1);  // 3xTF32 tensor cores
-                for (auto rs : {std::pair<int, int>{2, 12}, {4, 12}}) push(tg, ct, 0, rs.first, rs.second, 1);
+                push(tg, ct, 0, 2, 12, 1);
             }
+            for (auto cr : {std::pair<int, int>{128, 1}, {256, 2}, {256, 1}})
+                push(tg == 1 ? 1 : tg, cr.first, 3, cr.second, 0, 0);   // direct loads
             push(tg, 128, 0, 4, 12, 0);   // unpipelined baseline
         }
     }

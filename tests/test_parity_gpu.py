@@ -235,6 +235,17 @@ def test_ltimes_f32_tf32x3(lt_small, lin, lout, tg, tz, pipe):
     assert relF(run_ltimes(h, L, x, lin, lout, cj.F32), ref) <= TOL32
 
 
+@pytest.mark.parametrize("lin", range(6))
+@pytest.mark.parametrize("lout", [0, 3, 4])
+@pytest.mark.parametrize("tg,tz,r", [(1, 256, 2), (8, 16, 1), (32, 8, 2)])
+def test_ltimes_f32_direct(lt_small, lin, lout, tg, tz, r):
+    """Mode 3: direct global loads of `in`, staged out box (ragged G = 5, Z = 37)."""
+    L, x, ref = lt_small
+    tile = (tg, tz, tg * tz // r, (3 << 16) | (r << 8))
+    h = cj.specialize(cj.K_LTIMES, cj.F32, layout_a=lin, layout_b=lout, m=36, d=96, tile=tile)
+    assert relF(run_ltimes(h, L, x, lin, lout, cj.F32), ref) <= TOL32
+
+
 @pytest.mark.parametrize("lin,lout", [(0, 0), (1, 3), (3, 5), (5, 2)])
 @pytest.mark.parametrize("dt", [cj.F64, cj.F32])
 def test_ltimes_generic(lt_small, lin, lout, dt):
