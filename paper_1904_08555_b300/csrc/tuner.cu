@@ -2,7 +2,7 @@
 // profiling-guided autotuning of JIT-compiled code, Sec. 6):
 //   * cj_candidates: the tile space V(kernel, dtype, N, orders) searched;
 //   * cj_autotune:   compile every candidate and time it on the caller's
-//                    buffers (exhaustive search; the fallback and the judge
+//                    buffers (exhaustive search; the fallback, and the yardstick
 //                    of the model's regret);
 //   * cj_featurize:  the cost model's input vector for (request, tile);
 //   * cj_mlp_*:      the F -> 64 -> 64 -> 1 ReLU network that predicts the
