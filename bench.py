@@ -412,6 +412,7 @@ def main():
     p.add_argument("--batch", type=int, default=16384)
     p.add_argument("--layout-in", type=int, default=0)
     p.add_argument("--layout-out", type=int, default=0)
+    p.add_argument("--tile", type=int, nargs=4, default=None, help="explicit tile for --workload kernel")
     p.add_argument("--heldout", type=int, default=2000)
     p.add_argument("--train-steps", type=int, default=4000)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -597,7 +598,7 @@ def secondary(args):
             n, b = args.n, args.batch
             A = synth.uniform_torch(synth.SEED_CHAIN_SWEEP, synth.STREAM_A, b * n * n, "cuda").view(b, n, n).to(tdt)
             X = torch.empty_like(A)
-            h = cj.specialize(cj.K_UPDATE_CHAIN, dt, n=n, flags=fl)
+            h = cj.specialize(cj.K_UPDATE_CHAIN, dt, n=n, flags=fl, tile=tuple(args.tile) if args.tile else (0, 0, 0, 0))
             fn = lambda: cj.launch_update_chain(h, A, X, T_STEPS, stream=stream)
             f = chain_flops(b, n, T_STEPS)
             desc = f"update chain N={n} batch={b} T={T_STEPS} {args.dtype} {'generic' if generic else 'jit'}"
@@ -609,7 +610,8 @@ def secondary(args):
             xin = x.permute(*synth.LAYOUT_PERMS[args.layout_in]).contiguous().view(-1).to(tdt)
             del x
             o = torch.empty(M * G * Z, device="cuda", dtype=tdt)
-            h = cj.specialize(cj.K_LTIMES, dt, layout_a=args.layout_in, layout_b=args.layout_out, m=M, d=D, flags=fl)
+            h = cj.specialize(cj.K_LTIMES, dt, layout_a=args.layout_in, layout_b=args.layout_out, m=M, d=D, flags=fl,
+                              tile=tuple(args.tile) if args.tile else (0, 0, 0, 0))
             fn = lambda: cj.launch_ltimes(h, Lt, xin, o, G, Z, stream=stream)
             f = 2.0 * M * D * G * Z
             desc = (f"LTimes M=36 D=96 G=32 Z={Z} in {synth.LAYOUT_NAMES[args.layout_in]} out order "

@@ -310,38 +310,48 @@ ltimes(const T* __restrict__ L, const T* __restrict__ in, T* __restrict__ out, l
 // box of (g, z) columns; thread t owns R consecutive columns in the order of
 // `in`'s faster column axis and reads its columns straight from global memory
 // (coalesced across the warp; 16-byte vectors along d when d is fastest),
-// accumulating all M moments in registers against broadcast reads of L^T.
-// Only the out box goes through shared memory, so that it is stored
-// coalesced in any order of `out`.
+// accumulating all M moments in registers against 16-byte broadcast reads of
+// L^T.  When `out` orders its column axes like `in` (the same column axis
+// faster), each thread stores its columns straight from registers (coalesced,
+// or 16-byte vectors along m when m is fastest); otherwise the out box goes
+// through shared memory to be stored coalesced.
 template <class T, int M, int D, int LIN, int LOUT, int TG, int TZ, int NT, int R, int ACC = 0>
 __global__ void __launch_bounds__(NT)
 ltimes_direct(const T* __restrict__ L, const T* __restrict__ in, T* __restrict__ out, long long G, long long Z) {
     constexpr int CT = TG * TZ;
     constexpr int MP = cjg::lt_mpitch(M, (int)sizeof(T));
     constexpr int CP = cjg::lt_cpitch(CT, (int)sizeof(T));
+    constexpr int M4 = (M + 3) / 4;
     static_assert(CT == NT * R, "tile does not cover the block");
-    // in's faster column axis: z unless g comes after z in the storage order
+    static_assert(sizeof(T) == 4 && MP % 4 == 0, "direct mode is FP32");
+    // faster column axis of each tensor: g if g comes after z in its order
     constexpr bool G_FASTER = lt_pos(LIN, 1) > lt_pos(LIN, 2);
+    constexpr bool OUT_G_FASTER = lt_pos(LOUT, 1) > lt_pos(LOUT, 2);
     constexpr bool D_FAST = lt_pos(LIN, 0) == 2;
+    constexpr bool M_FAST = lt_pos(LOUT, 0) == 2;
+    constexpr bool DIRECT_OUT = G_FASTER == OUT_G_FASTER;
     extern __shared__ __align__(16) unsigned char cj_smem[];
-    T* sL = reinterpret_cast<T*>(cj_smem);   // [D][MP], L transposed
-    T* sO = sL + D * MP;                      // [M][CP] out box
+    T* sL = reinterpret_cast<T*>(cj_smem);   // [D][MP], L transposed, zero-padded
+    T* sO = sL + D * MP;                      // [M][CP] out box (staged stores)
     const int tid = threadIdx.x;
     for (int e = tid; e < MP * D; e += NT) {
         const int m = e / D, d = e - m * D;
         sL[d * MP + m] = m < M ? L[e] : T(0);
     }
-    // strides of in along (d, g, z)
     const long long ext[3] = {D, G, Z};
-    long long st[3];
+    long long st[3], so[3];
     st[lt_axis(LIN, 2)] = 1;
     st[lt_axis(LIN, 1)] = ext[lt_axis(LIN, 2)];
     st[lt_axis(LIN, 0)] = ext[lt_axis(LIN, 2)] * ext[lt_axis(LIN, 1)];
+    const long long exo[3] = {M, G, Z};
+    so[lt_axis(LOUT, 2)] = 1;
+    so[lt_axis(LOUT, 1)] = exo[lt_axis(LOUT, 2)];
+    so[lt_axis(LOUT, 0)] = exo[lt_axis(LOUT, 2)] * exo[lt_axis(LOUT, 1)];
     const long long ntg = (G + TG - 1) / TG, ntz = (Z + TZ - 1) / TZ;
     const long long ntiles = ntg * ntz;
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const long long g0 = (t / ntz) * TG, z0 = (t % ntz) * TZ;
-        long long off[R];
+        long long off[R], ooff[R];
         int sidx[R];
         bool ok[R];
 #pragma unroll
@@ -351,34 +361,48 @@ ltimes_direct(const T* __restrict__ L, const T* __restrict__ in, T* __restrict__
             const int zl = G_FASTER ? c / TG : c % TZ;
             ok[r] = (g0 + gl < G) && (z0 + zl < Z);
             off[r] = ok[r] ? (g0 + gl) * st[1] + (z0 + zl) * st[2] : 0;
+            ooff[r] = ok[r] ? (g0 + gl) * so[1] + (z0 + zl) * so[2] : 0;
             sidx[r] = gl * TZ + zl;
         }
-        __syncthreads();   // sL ready (first tile); previous out box stored
-        T acc[R][M];
+        if (!DIRECT_OUT || t == blockIdx.x) __syncthreads();   // sL ready; previous out box stored
+        T acc[R][M4 * 4];
 #pragma unroll
         for (int r = 0; r < R; ++r)
 #pragma unroll
-            for (int m = 0; m < M; ++m) acc[r][m] = T(0);
-        if constexpr (D_FAST && sizeof(T) == 4 && D % 4 == 0) {
+            for (int m = 0; m < M4 * 4; ++m) acc[r][m] = T(0);
+        auto step = [&](int d, const T (&x)[R]) {
+            const float4* lrow = reinterpret_cast<const float4*>(sL + d * MP);
+#pragma unroll
+            for (int m4 = 0; m4 < M4; ++m4) {
+                const float4 lv = lrow[m4];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    acc[r][4 * m4 + 0] = lt_fma(lv.x, x[r], acc[r][4 * m4 + 0]);
+                    acc[r][4 * m4 + 1] = lt_fma(lv.y, x[r], acc[r][4 * m4 + 1]);
+                    acc[r][4 * m4 + 2] = lt_fma(lv.z, x[r], acc[r][4 * m4 + 2]);
+                    acc[r][4 * m4 + 3] = lt_fma(lv.w, x[r], acc[r][4 * m4 + 3]);
+                }
+            }
+        };
+        if constexpr (D_FAST && D % 4 == 0) {
 #pragma unroll 2
             for (int d = 0; d < D; d += 4) {
                 float4 xv[R];
 #pragma unroll
                 for (int r = 0; r < R; ++r)
                     xv[r] = ok[r] ? __ldg(reinterpret_cast<const float4*>(in + off[r] + d)) : make_float4(0, 0, 0, 0);
+                T x0[R], x1[R], x2[R], x3[R];
 #pragma unroll
-                for (int dd = 0; dd < 4; ++dd) {
-                    const T* lrow = sL + (d + dd) * MP;
-#pragma unroll
-                    for (int m = 0; m < M; ++m) {
-                        const T lv = lrow[m];
-#pragma unroll
-                        for (int r = 0; r < R; ++r) {
-                            const T x = dd == 0 ? xv[r].x : dd == 1 ? xv[r].y : dd == 2 ? xv[r].z : xv[r].w;
-                            acc[r][m] = lt_fma(lv, x, acc[r][m]);
-                        }
-                    }
+                for (int r = 0; r < R; ++r) {
+                    x0[r] = xv[r].x;
+                    x1[r] = xv[r].y;
+                    x2[r] = xv[r].z;
+                    x3[r] = xv[r].w;
                 }
+                step(d, x0);
+                step(d + 1, x1);
+                step(d + 2, x2);
+                step(d + 3, x3);
             }
         } else {
 #pragma unroll 4
@@ -386,21 +410,41 @@ ltimes_direct(const T* __restrict__ L, const T* __restrict__ in, T* __restrict__
                 T x[R];
 #pragma unroll
                 for (int r = 0; r < R; ++r) x[r] = ok[r] ? __ldg(in + off[r] + d * st[0]) : T(0);
-                const T* lrow = sL + d * MP;
-#pragma unroll
-                for (int m = 0; m < M; ++m) {
-                    const T lv = lrow[m];
-#pragma unroll
-                    for (int r = 0; r < R; ++r) acc[r][m] = lt_fma(lv, x[r], acc[r][m]);
-                }
+                step(d, x);
             }
         }
+        if constexpr (DIRECT_OUT) {
 #pragma unroll
-        for (int r = 0; r < R; ++r)
+            for (int r = 0; r < R; ++r) {
+                if (!ok[r]) continue;
+                T* o = out + ooff[r];
+                if constexpr (M_FAST && M % 4 == 0) {
 #pragma unroll
-            for (int m = 0; m < M; ++m) sO[m * CP + sidx[r]] = acc[r][m];
-        __syncthreads();
-        lt_box<T, LOUT, M, TG, TZ, CP, NT, false, ACC != 0>(out, sO, G, Z, g0, z0, tid);
+                    for (int m4 = 0; m4 < M / 4; ++m4) {
+                        float4 v = make_float4(acc[r][4 * m4], acc[r][4 * m4 + 1], acc[r][4 * m4 + 2], acc[r][4 * m4 + 3]);
+                        float4* p = reinterpret_cast<float4*>(o) + m4;
+                        if (ACC) {
+                            const float4 w = *p;
+                            v.x += w.x; v.y += w.y; v.z += w.z; v.w += w.w;
+                        }
+                        *p = v;
+                    }
+                } else {
+#pragma unroll
+                    for (int m = 0; m < M; ++m) {
+                        T* p = o + m * so[0];
+                        *p = ACC ? *p + acc[r][m] : acc[r][m];
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int m = 0; m < M; ++m) sO[m * CP + sidx[r]] = acc[r][m];
+            __syncthreads();
+            lt_box<T, LOUT, M, TG, TZ, CP, NT, false, ACC != 0>(out, sO, G, Z, g0, z0, tid);
+        }
     }
 }
 
