@@ -496,6 +496,18 @@ def secondary(args):
                 row[name + "_gflops"] = f / ms / 1e6
                 row[name + "_regs"] = h.regs()[0]
             row["speedup_vs_generic"] = row["generic_us"] / row["jit_us"]
+            if args.workload == "small":
+                # the autotuner's choice for this exact batch (tile spaces include
+                # one instance per block, which a 64-instance batch needs)
+                best, times = cj.autotune(cj.K_UPDATE_CHAIN, dt, cj.chain_launch_vals(A, X, steps), b, stream,
+                                          reps=20, n=n)
+                h = cj.specialize(cj.K_UPDATE_CHAIN, dt, n=n, tile=best)
+                fn = lambda h=h: cj.launch_update_chain(h, A, X, steps, stream=stream)
+                _events(torch, stream, fn, W)
+                ms = _events(torch, stream, fn, reps)
+                row.update({"autotuned_tile": list(best), "autotuned_us": ms * 1e3, "autotuned_gflops": f / ms / 1e6,
+                            "autotuned_speedup_vs_generic": row["generic_us"] / (ms * 1e3),
+                            "candidates_us": {str(list(t)): v * 1e3 for t, v in times}})
             rows.append(row)
             tot_f += f
             tot_spec += row["jit_us"]
