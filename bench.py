@@ -429,7 +429,9 @@ def main():
         tg = 1 if not (gi or go) else (8 if (gi and lout in (0, 2)) or (go and lin in (0, 2)) else 32)
         return [("tf32x3", (tg, 64 // tg, 128, (1 << 20) | (2 << 16) | (1 << 8) | 8)),
                 ("direct_r2", (tg, 256 // tg, 128, (3 << 16) | (2 << 8))),
-                ("direct_r1", (tg, 128 // tg, 128, (3 << 16) | (1 << 8)))]
+                ("direct_r1", (tg, 128 // tg, 128, (3 << 16) | (1 << 8))),
+                ("direct_r2_s12", (tg, 128 // tg, 192, (3 << 16) | (2 << 8) | 12)),
+                ("direct_r4_s12", (tg, 256 // tg, 192, (3 << 16) | (4 << 8) | 12))]
     args.lt_alt_tiles = lt_alt_tiles
     if args.impl == "reference":
         reference_arm(args)

@@ -327,15 +327,18 @@ cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_
                           (tg * tz / 16) * 32 != nt || nt > 1024))
             return fail(CJ_ERR_INVALID_ARG, "LTimes 3xTF32 tile {%d,%d,%d,0x%x} invalid (f32, R = 1, S = 8, d %% 8 == 0, "
                         "threads = 32 * TG * TZ / 16)", a.tile[0], a.tile[1], a.tile[2], a.tile[3]);
-        if (mode == 3 && (a.dtype != CJ_F32 || pipe || r < 1 || r > 4 || tg * tz != nt * r || nt < 32 || nt > 1024))
-            return fail(CJ_ERR_INVALID_ARG, "LTimes direct tile {%d,%d,%d,0x%x} invalid (f32, no PIPE, "
-                        "threads * R = TG * TZ, R <= 4)", a.tile[0], a.tile[1], a.tile[2], a.tile[3]);
+        const int direct_groups = s ? (v.m + s - 1) / s : 1;   // moment groups of the direct kernel
+        if (mode == 3 && (a.dtype != CJ_F32 || pipe || r < 1 || r > 4 || (s != 0 && (s % 4 || s >= v.m)) ||
+                          (tg * tz) % r || (tg * tz / r) * direct_groups != nt || nt < 32 || nt > 1024))
+            return fail(CJ_ERR_INVALID_ARG, "LTimes direct tile {%d,%d,%d,0x%x} invalid (f32, no PIPE, R <= 4, S = 0 "
+                        "or a multiple of 4 below m, threads = TG * TZ / R * ceil(m / S))", a.tile[0], a.tile[1],
+                        a.tile[2], a.tile[3]);
         if (mode > 3) return fail(CJ_ERR_INVALID_ARG, "LTimes compute mode %d unknown", mode);
         if (mode == 0 && (tg < 1 || tz < 1 || r < 1 || s < 1 || nt < 32 || nt > 1024 || (tg * tz) % r ||
                           (tg * tz / r) * ((v.m + s - 1) / s) != nt))
             return fail(CJ_ERR_INVALID_ARG, "LTimes tile {%d,%d,%d,%d} does not cover its block", a.tile[0],
                         a.tile[1], a.tile[2], a.tile[3]);
-        if ((mode == 3 ? cjg::lt_direct_smem(v.m, v.d, tg * tz, esize(a.dtype))
+        if ((mode == 3 ? cjg::lt_direct_smem(v.m, v.d, tg * tz, esize(a.dtype), s)
                        : cjg::lt_smem(v.m, s, v.d, tg * tz, esize(a.dtype), pipe, mode)) > 220 * 1024)
             return fail(CJ_ERR_INVALID_ARG, "LTimes tile needs too much shared memory");
     }
@@ -377,7 +380,7 @@ void spec_geometry(const cj_handle_s *h, Impl &s) {
         const LtView v = lt_view(h->kernel, a);
         s.threads = a.tile[2];
         s.smem = ((a.tile[3] >> 16) & 0xf) == 3
-                     ? (size_t)cjg::lt_direct_smem(v.m, v.d, a.tile[0] * a.tile[1], es)
+                     ? (size_t)cjg::lt_direct_smem(v.m, v.d, a.tile[0] * a.tile[1], es, a.tile[3] & 0xff)
                      : (size_t)cjg::lt_smem(v.m, a.tile[3] & 0xff, v.d, a.tile[0] * a.tile[1], es,
                                             (a.tile[3] >> 20) & 1, (a.tile[3] >> 16) & 0xf);
     } else {
@@ -399,8 +402,9 @@ std::string name_expression(const cj_handle_s *h) {
     else {
         const LtView v = lt_view(h->kernel, a);
         if (((a.tile[3] >> 16) & 0xf) == 3)
-            snprintf(buf, sizeof buf, "cj::ltimes_direct<%s, %d, %d, %d, %d, %d, %d, %d, %d, %d>", ctype(a.dtype), v.m,
-                     v.d, v.lin, v.lout, a.tile[0], a.tile[1], a.tile[2], (a.tile[3] >> 8) & 0xff, v.acc);
+            snprintf(buf, sizeof buf, "cj::ltimes_direct<%s, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d>", ctype(a.dtype),
+                     v.m, v.d, v.lin, v.lout, a.tile[0], a.tile[1], a.tile[2], (a.tile[3] >> 8) & 0xff,
+                     a.tile[3] & 0xff, v.acc);
         else
             snprintf(buf, sizeof buf, "cj::ltimes<%s, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d>", ctype(a.dtype),
                      v.m, v.d, v.lin, v.lout, a.tile[0], a.tile[1], a.tile[2], (a.tile[3] >> 8) & 0xff,

@@ -39,6 +39,18 @@ CJ_HD constexpr int chain_threads(int n, int mapping, int ipb) {
 // Rows of X kept in shared memory (instead of registers) above this size.
 CJ_HD constexpr int chain_reg_rows_max(int esize) { return esize == 8 ? 32 : 48; }
 
+// Row length of A_b in shared memory: mapping 1 in FP32 pads each row to a
+// multiple of 4 so a thread reads A with 16-byte vectors (one shared-memory
+// load per four fused multiply-adds); every other mapping keeps rows of n.
+CJ_HD constexpr int chain_arow(int n, int mapping, int esize) {
+    return (mapping == 1 && esize == 4) ? (n + 3) / 4 * 4 : n;
+}
+
+// Elements between consecutive staged instances of the specialized kernels.
+CJ_HD constexpr int chain_pitch(int n, int mapping, int esize) {
+    return mapping == 2 ? inst_pitch(n * n) : row_pitch(n * chain_arow(n, mapping, esize), esize);
+}
+
 // Per-thread pitch of X rows kept in shared memory (odd: conflict-free).
 CJ_HD constexpr int xrow_pitch(int n) { return n | 1; }
 
@@ -48,7 +60,7 @@ CJ_HD constexpr long chain_smem(int n, int mapping, int ipb, int esize) {
         ? (long)ipb * inst_pitch(n * n) * esize
         : mapping == 5
         ? (long)ipb * row_pitch(n * n, esize) * esize + (long)ipb * n * (n + 4) * esize
-        : (long)ipb * row_pitch(n * n, esize) * esize +
+        : (long)ipb * chain_pitch(n, mapping, esize) * esize +
               (mapping == 1 && n > chain_reg_rows_max(esize)
                    ? (long)chain_threads(n, 1, ipb) * xrow_pitch(n) * esize
                    : 0L);
@@ -72,9 +84,13 @@ CJ_HD constexpr long lt_smem(int m, int s, int d, int ct, int esize, int pipe = 
             (pipe ? 2L : 1L) * (long)(m > d ? m : d) * lt_cpitch(ct, esize, mode)) *
            esize;
 }
-// Direct kernel (mode 3): L^T plus one out box.
-CJ_HD constexpr long lt_direct_smem(int m, int d, int ct, int esize) {
-    return ((long)d * lt_mpitch(m, esize) + (long)m * lt_cpitch(ct, esize)) * esize;
+// Direct kernel (mode 3, s moments per thread, 0 = all): L^T padded to whole
+// moment groups, plus one out box.
+CJ_HD constexpr int lt_direct_mpad(int m, int s) {
+    return (s == 0 || s >= m) ? (m + 3) / 4 * 4 : (m + s - 1) / s * s;
+}
+CJ_HD constexpr long lt_direct_smem(int m, int d, int ct, int esize, int s = 0) {
+    return ((long)d * lt_mpitch(lt_direct_mpad(m, s), esize) + (long)m * lt_cpitch(ct, esize)) * esize;
 }
 CJ_HD constexpr long lt_generic_smem(int m, int d, int cols, int esize) {
     return ((long)m * d + (long)d * cols) * esize;

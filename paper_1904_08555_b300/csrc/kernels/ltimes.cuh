@@ -310,19 +310,24 @@ ltimes(const T* __restrict__ L, const T* __restrict__ in, T* __restrict__ out, l
 // box of (g, z) columns; thread t owns R consecutive columns in the order of
 // `in`'s faster column axis and reads its columns straight from global memory
 // (coalesced across the warp; 16-byte vectors along d when d is fastest),
-// accumulating all M moments in registers against 16-byte broadcast reads of
-// L^T.  When `out` orders its column axes like `in` (the same column axis
+// accumulating S moments (S = 0: all M) in registers against 16-byte
+// broadcast reads of L^T; threads of one column group that own different
+// moment groups reread the same `in` values from L1.  When `out` orders its
+// column axes like `in` (the same column axis
 // faster), each thread stores its columns straight from registers (coalesced,
 // or 16-byte vectors along m when m is fastest); otherwise the out box goes
 // through shared memory to be stored coalesced.
-template <class T, int M, int D, int LIN, int LOUT, int TG, int TZ, int NT, int R, int ACC = 0>
+template <class T, int M, int D, int LIN, int LOUT, int TG, int TZ, int NT, int R, int S = 0, int ACC = 0>
 __global__ void __launch_bounds__(NT)
 ltimes_direct(const T* __restrict__ L, const T* __restrict__ in, T* __restrict__ out, long long G, long long Z) {
     constexpr int CT = TG * TZ;
-    constexpr int MP = cjg::lt_mpitch(M, (int)sizeof(T));
+    constexpr int SM_ = (S == 0 || S >= M) ? ((M + 3) / 4) * 4 : S;   // moments per thread
+    constexpr int MG = (M + SM_ - 1) / SM_;                            // moment groups
+    constexpr int MP = cjg::lt_mpitch(MG * SM_, (int)sizeof(T));
     constexpr int CP = cjg::lt_cpitch(CT, (int)sizeof(T));
-    constexpr int M4 = (M + 3) / 4;
-    static_assert(CT == NT * R, "tile does not cover the block");
+    constexpr int M4 = SM_ / 4;
+    constexpr int QG = CT / R;                                         // column groups
+    static_assert(SM_ % 4 == 0 && QG * MG == NT, "tile does not cover the block");
     static_assert(sizeof(T) == 4 && MP % 4 == 0, "direct mode is FP32");
     // faster column axis of each tensor: g if g comes after z in its order
     constexpr bool G_FASTER = lt_pos(LIN, 1) > lt_pos(LIN, 2);
@@ -349,6 +354,7 @@ ltimes_direct(const T* __restrict__ L, const T* __restrict__ in, T* __restrict__
     so[lt_axis(LOUT, 0)] = exo[lt_axis(LOUT, 2)] * exo[lt_axis(LOUT, 1)];
     const long long ntg = (G + TG - 1) / TG, ntz = (Z + TZ - 1) / TZ;
     const long long ntiles = ntg * ntz;
+    const int cg = tid % QG, m0 = (tid / QG) * SM_;
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const long long g0 = (t / ntz) * TG, z0 = (t % ntz) * TZ;
         long long off[R], ooff[R];
@@ -356,7 +362,7 @@ ltimes_direct(const T* __restrict__ L, const T* __restrict__ in, T* __restrict__
         bool ok[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int c = tid * R + r;
+            const int c = cg * R + r;
             const int gl = G_FASTER ? c % TG : c / TZ;
             const int zl = G_FASTER ? c / TG : c % TZ;
             ok[r] = (g0 + gl < G) && (z0 + zl < Z);
@@ -365,13 +371,13 @@ ltimes_direct(const T* __restrict__ L, const T* __restrict__ in, T* __restrict__
             sidx[r] = gl * TZ + zl;
         }
         if (!DIRECT_OUT || t == blockIdx.x) __syncthreads();   // sL ready; previous out box stored
-        T acc[R][M4 * 4];
+        T acc[R][SM_];
 #pragma unroll
         for (int r = 0; r < R; ++r)
 #pragma unroll
-            for (int m = 0; m < M4 * 4; ++m) acc[r][m] = T(0);
+            for (int m = 0; m < SM_; ++m) acc[r][m] = T(0);
         auto step = [&](int d, const T (&x)[R]) {
-            const float4* lrow = reinterpret_cast<const float4*>(sL + d * MP);
+            const float4* lrow = reinterpret_cast<const float4*>(sL + d * MP + m0);
 #pragma unroll
             for (int m4 = 0; m4 < M4; ++m4) {
                 const float4 lv = lrow[m4];
@@ -418,11 +424,11 @@ ltimes_direct(const T* __restrict__ L, const T* __restrict__ in, T* __restrict__
             for (int r = 0; r < R; ++r) {
                 if (!ok[r]) continue;
                 T* o = out + ooff[r];
-                if constexpr (M_FAST && M % 4 == 0) {
+                if constexpr (M_FAST && M % SM_ == 0) {
 #pragma unroll
-                    for (int m4 = 0; m4 < M / 4; ++m4) {
+                    for (int m4 = 0; m4 < M4; ++m4) {
                         float4 v = make_float4(acc[r][4 * m4], acc[r][4 * m4 + 1], acc[r][4 * m4 + 2], acc[r][4 * m4 + 3]);
-                        float4* p = reinterpret_cast<float4*>(o) + m4;
+                        float4* p = reinterpret_cast<float4*>(o + m0) + m4;
                         if (ACC) {
                             const float4 w = *p;
                             v.x += w.x; v.y += w.y; v.z += w.z; v.w += w.w;
@@ -431,8 +437,9 @@ ltimes_direct(const T* __restrict__ L, const T* __restrict__ in, T* __restrict__
                     }
                 } else {
 #pragma unroll
-                    for (int m = 0; m < M; ++m) {
-                        T* p = o + m * so[0];
+                    for (int m = 0; m < SM_; ++m) {
+                        if (M % SM_ != 0 && m0 + m >= M) break;
+                        T* p = o + (m0 + m) * so[0];
                         *p = ACC ? *p + acc[r][m] : acc[r][m];
                     }
                 }
@@ -441,7 +448,8 @@ ltimes_direct(const T* __restrict__ L, const T* __restrict__ in, T* __restrict__
 #pragma unroll
             for (int r = 0; r < R; ++r)
 #pragma unroll
-                for (int m = 0; m < M; ++m) sO[m * CP + sidx[r]] = acc[r][m];
+                for (int m = 0; m < SM_; ++m)
+                    if (M % SM_ == 0 || m0 + m < M) sO[(m0 + m) * CP + sidx[r]] = acc[r][m];
             __syncthreads();
             lt_box<T, LOUT, M, TG, TZ, CP, NT, false, ACC != 0>(out, sO, G, Z, g0, z0, tid);
         }

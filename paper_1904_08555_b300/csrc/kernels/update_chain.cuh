@@ -33,11 +33,11 @@ __device__ __forceinline__ const T* opaque_base(const T* base, int off) {
 }
 
 // Stage `ninst` consecutive instances (contiguous in global memory) into
-// shared memory as logical row-major matrices with pitch P.  Layout 1 stores
-// each instance column-major; it is transposed here so that the compute loop
-// is the same for both layouts.
+// shared memory as logical row-major matrices with rows of `ar` elements and
+// instance pitch P.  Layout 1 stores each instance column-major; it is
+// transposed here so that the compute loop is the same for both layouts.
 template <class T, int LAYOUT>
-__device__ __forceinline__ void chain_stage_in(T* sA, const T* __restrict__ gA, int ninst, int n,
+__device__ __forceinline__ void chain_stage_in(T* sA, const T* __restrict__ gA, int ninst, int n, int ar,
                                                int P, int tid, int nthreads) {
     const int nn = n * n;
     for (int e = tid; e < ninst * nn; e += nthreads) {
@@ -46,7 +46,7 @@ __device__ __forceinline__ void chain_stage_in(T* sA, const T* __restrict__ gA, 
         const int row = r / n, col = r - row * n;
         const int l = LAYOUT == 0 ? row : col;
         const int j = LAYOUT == 0 ? col : row;
-        sA[inst * P + l * n + j] = gA[e];
+        sA[inst * P + l * ar + j] = gA[e];
     }
 }
 
@@ -60,9 +60,29 @@ __device__ __forceinline__ void chain_stage_out(T* __restrict__ gX, const T* sA,
     }
 }
 
-// One thread, row i of one instance (A at sA + aoff, logical row-major):
-// T steps with the row of X in registers.
-template <class T, int N>
+// p += xl * (row of A at `arow`, N entries): 16-byte vector reads when the
+// row is padded to a multiple of 4 floats (AR % 4 == 0), scalar otherwise.
+template <class T, int N, int AR>
+__device__ __forceinline__ void row_axpy(const T* arow, T xl, T (&p)[N]) {
+    if constexpr (sizeof(T) == 4 && AR % 4 == 0) {
+        const float4* a4 = reinterpret_cast<const float4*>(arow);
+#pragma unroll
+        for (int q = 0; q < AR / 4; ++q) {
+            const float4 v = a4[q];
+            const float w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (4 * q + u < N) p[4 * q + u] = fmaT(xl, w[u], p[4 * q + u]);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < N; ++j) p[j] = fmaT(xl, arow[j], p[j]);
+    }
+}
+
+// One thread, row i of one instance (A at sA + aoff, logical row-major with
+// rows of AR elements): T steps with the row of X in registers.
+template <class T, int N, int AR>
 __device__ __forceinline__ void row_chain_regs(const T* sA, int aoff, int i, int steps, T cc, T (&x)[N]) {
 #pragma unroll
     for (int j = 0; j < N; ++j) x[j] = (j == i) ? T(1) : T(0);
@@ -72,11 +92,7 @@ __device__ __forceinline__ void row_chain_regs(const T* sA, int aoff, int i, int
 #pragma unroll
         for (int j = 0; j < N; ++j) p[j] = T(0);
 #pragma unroll
-        for (int l = 0; l < N; ++l) {
-            const T xl = x[l];
-#pragma unroll
-            for (int j = 0; j < N; ++j) p[j] = fmaT(xl, a[l * N + j], p[j]);
-        }
+        for (int l = 0; l < N; ++l) row_axpy<T, N, AR>(a + l * AR, x[l], p);
 #pragma unroll
         for (int j = 0; j < N; ++j) x[j] = fmaT(cc, p[j], x[j]);
     }
@@ -84,7 +100,7 @@ __device__ __forceinline__ void row_chain_regs(const T* sA, int aoff, int i, int
 
 // Same for large N: the row of X lives in the thread's own shared-memory row
 // xs (read once per N fused multiply-adds); the product row in registers.
-template <class T, int N>
+template <class T, int N, int AR>
 __device__ __forceinline__ void row_chain_smem(const T* a, T* xs, int i, int steps, T cc) {
     for (int j = 0; j < N; ++j) xs[j] = (j == i) ? T(1) : T(0);
     for (int k = 0; k < steps; ++k) {
@@ -92,11 +108,7 @@ __device__ __forceinline__ void row_chain_smem(const T* a, T* xs, int i, int ste
 #pragma unroll
         for (int j = 0; j < N; ++j) p[j] = T(0);
 #pragma unroll 2
-        for (int l = 0; l < N; ++l) {
-            const T xl = xs[l];
-#pragma unroll
-            for (int j = 0; j < N; ++j) p[j] = fmaT(xl, a[l * N + j], p[j]);
-        }
+        for (int l = 0; l < N; ++l) row_axpy<T, N, AR>(a + l * AR, xs[l], p);
 #pragma unroll
         for (int j = 0; j < N; ++j) xs[j] = fmaT(cc, p[j], xs[j]);
     }
@@ -368,14 +380,15 @@ __device__ __forceinline__ void chain_block(T* sA, int ninst, int tid, StepsOf s
                 for (int j = 0; j < N; ++j) sA[tid * P + (LAYOUT == 0 ? i * N + j : j * N + i)] = x[i][j];
         }
     } else {
-        constexpr int P = cjg::row_pitch(NN, (int)sizeof(T));
+        constexpr int P = cjg::chain_pitch(N, 1, (int)sizeof(T));
+        constexpr int AR = cjg::chain_arow(N, 1, (int)sizeof(T));
         constexpr bool XREG = N <= cjg::chain_reg_rows_max((int)sizeof(T));
         const int inst = tid / N;
         const int i = tid - inst * N;
         const bool active = inst < ninst;
         if constexpr (XREG) {
             T x[N];
-            if (active) row_chain_regs<T, N>(sA, inst * P, i, steps_of(inst), c_of(inst), x);
+            if (active) row_chain_regs<T, N, AR>(sA, inst * P, i, steps_of(inst), c_of(inst), x);
             __syncthreads();
             if (active) {
 #pragma unroll
@@ -384,7 +397,7 @@ __device__ __forceinline__ void chain_block(T* sA, int ninst, int tid, StepsOf s
         } else {
             constexpr int XP = cjg::xrow_pitch(N);
             T* xs = sA + IPB * P + tid * XP;
-            if (active) row_chain_smem<T, N>(sA + inst * P, xs, i, steps_of(inst), c_of(inst));
+            if (active) row_chain_smem<T, N, AR>(sA + inst * P, xs, i, steps_of(inst), c_of(inst));
             __syncthreads();
             if (active)
                 for (int j = 0; j < N; ++j) sA[inst * P + (LAYOUT == 0 ? i * N + j : j * N + i)] = xs[j];
@@ -401,7 +414,8 @@ __global__ void __launch_bounds__(cjg::chain_threads(N, MAP, IPB))
 update_chain(const T* __restrict__ A, T* __restrict__ X, long long batch, int steps, double c) {
     constexpr int NN = N * N;
     constexpr int NT = cjg::chain_threads(N, MAP, IPB);
-    constexpr int P = MAP == 2 ? cjg::inst_pitch(NN) : cjg::row_pitch(NN, (int)sizeof(T));
+    constexpr int P = cjg::chain_pitch(N, MAP, (int)sizeof(T));
+    constexpr int AR = cjg::chain_arow(N, MAP, (int)sizeof(T));
     extern __shared__ __align__(16) unsigned char cj_smem[];
     T* sA = reinterpret_cast<T*>(cj_smem);
     const long long b0 = (long long)blockIdx.x * IPB;
@@ -409,7 +423,7 @@ update_chain(const T* __restrict__ A, T* __restrict__ X, long long batch, int st
     const int ninst = (batch - b0) < IPB ? (int)(batch - b0) : IPB;
     const T cc = (T)c;
     const int tid = threadIdx.x;
-    chain_stage_in<T, LAYOUT>(sA, A + b0 * NN, ninst, N, P, tid, NT);
+    chain_stage_in<T, LAYOUT>(sA, A + b0 * NN, ninst, N, AR, P, tid, NT);
     __syncthreads();
     chain_block<T, N, LAYOUT, MAP, IPB>(
         sA, ninst, tid, [&](int) { return steps; }, [&](int) { return cc; });
@@ -452,8 +466,8 @@ update_chain_generic(const T* __restrict__ A, T* __restrict__ X, long long batch
     const long long b0 = (long long)blockIdx.x * ipb;
     if (b0 >= batch) return;
     const int ninst = (batch - b0) < ipb ? (int)(batch - b0) : ipb;
-    if (layout == 0) chain_stage_in<T, 0>(sA, A + b0 * nn, ninst, n, P, tid, nthreads);
-    else             chain_stage_in<T, 1>(sA, A + b0 * nn, ninst, n, P, tid, nthreads);
+    if (layout == 0) chain_stage_in<T, 0>(sA, A + b0 * nn, ninst, n, n, P, tid, nthreads);
+    else             chain_stage_in<T, 1>(sA, A + b0 * nn, ninst, n, n, P, tid, nthreads);
     __syncthreads();
     const int inst = tid / n;
     const int i = tid - inst * n;
@@ -480,7 +494,8 @@ update_chain_grouped(const long long* __restrict__ items, const T* __restrict__ 
                      T* __restrict__ X_pool, int* __restrict__ counter, long long n_items) {
     constexpr int NN = N * N;
     constexpr int NT = cjg::chain_threads(N, MAP, IPB);
-    constexpr int P = MAP == 2 ? cjg::inst_pitch(NN) : cjg::row_pitch(NN, (int)sizeof(T));
+    constexpr int P = cjg::chain_pitch(N, MAP, (int)sizeof(T));
+    constexpr int AR = cjg::chain_arow(N, MAP, (int)sizeof(T));
     extern __shared__ __align__(16) unsigned char cj_smem[];
     T* sA = reinterpret_cast<T*>(cj_smem);
     __shared__ long long s_off[IPB];
@@ -501,8 +516,9 @@ update_chain_grouped(const long long* __restrict__ items, const T* __restrict__ 
         }
         __syncthreads();
         for (int e = tid; e < ninst * NN; e += NT) {
-            const int inst = e / NN;
-            sA[inst * P + (e - inst * NN)] = A_pool[s_off[inst] + (e - inst * NN)];
+            const int inst = e / NN, r = e - inst * NN;
+            const int row = r / N, col = r - row * N;
+            sA[inst * P + row * AR + col] = A_pool[s_off[inst] + r];
         }
         __syncthreads();
         chain_block<T, N, 0, MAP, IPB>(

@@ -79,10 +79,10 @@ void ltimes_candidates(const cj_template_args &a, std::vector<std::array<int, 4>
             if (ct % 16 || a.d % 8) return;
             nt = ct / 16 * 32;
         } else if (mode == 3) {
-            if (ct % r) return;
-            nt = ct / r;
+            if (ct % r || (s && (s % 4 || s >= a.m))) return;
+            nt = ct / r * (s ? (a.m + s - 1) / s : 1);
             if (nt < 32 || nt > 1024) return;
-            if (cjg::lt_direct_smem(a.m, a.d, ct, es) > 200 * 1024) return;
+            if (cjg::lt_direct_smem(a.m, a.d, ct, es, s) > 200 * 1024) return;
             out.push_back({tg, ct / tg, nt, (3 << 16) | (r << 8) | s});
             return;
         } else {
@@ -105,8 +105,11 @@ void ltimes_candidates(const cj_template_args &a, std::vector<std::array<int, 4>
                 push(tg, ct, 2, 1, 8, 1);  // 3xTF32 tensor cores
                 push(tg, ct, 0, 2, 12, 1);
             }
-            for (auto cr : {std::pair<int, int>{128, 1}, {256, 2}, {256, 1}})
-                push(tg == 1 ? 1 : tg, cr.first, 3, cr.second, 0, 0);   // direct loads
+            push(tg, 256, 3, 2, 0, 0);                          // direct loads, all moments per thread
+            if (a.m > 12) {
+                push(tg, 128, 3, 2, 12, 0);                     // direct loads, 12 moments per thread
+                push(tg, 256, 3, 2, 12, 0);
+            }
             push(tg, 128, 0, 4, 12, 0);   // unpipelined baseline
         }
     }

@@ -97,6 +97,10 @@ def test_aot_sizes_are_not_compiled(compile_only_sync):
     dict(kernel=cj.K_LTIMES, dtype=cj.BF16, m=36, d=96),
     dict(kernel=cj.K_LTIMES, dtype=cj.F32, m=36, d=96, tile=(1, 64, 128, (1 << 16) | (2 << 8) | 8)),
     dict(kernel=cj.K_LTIMES, dtype=cj.F64, m=36, d=95, tile=(1, 64, 128, (1 << 16) | (2 << 8) | 8)),
+    dict(kernel=cj.K_LTIMES, dtype=cj.F32, m=36, d=96, tile=(1, 128, 320, (3 << 16) | (2 << 8) | 6)),
+    dict(kernel=cj.K_LTIMES, dtype=cj.F32, m=36, d=96, tile=(1, 128, 64, (3 << 16) | (2 << 8) | 36)),
+    dict(kernel=cj.K_LTIMES, dtype=cj.F32, m=36, d=96, tile=(1, 128, 128, (3 << 16) | (2 << 8) | 12)),
+    dict(kernel=cj.K_LTIMES, dtype=cj.F64, m=36, d=96, tile=(1, 128, 192, (3 << 16) | (2 << 8) | 12)),
     dict(kernel=9, dtype=cj.F64, n=4),
 ])
 def test_invalid_arguments(compile_only_sync, kw):

@@ -246,6 +246,31 @@ def test_ltimes_f32_direct(lt_small, lin, lout, tg, tz, r):
     assert relF(run_ltimes(h, L, x, lin, lout, cj.F32), ref) <= TOL32
 
 
+@pytest.mark.parametrize("lin", range(6))
+@pytest.mark.parametrize("lout", range(6))
+@pytest.mark.parametrize("tg,tz,r,s", [(1, 128, 2, 12), (8, 16, 1, 8), (32, 8, 4, 12)])
+def test_ltimes_f32_direct_split_moments(lt_small, lin, lout, tg, tz, r, s):
+    """Mode 3 with S moments per thread (S = 8 leaves a partial last group of 4)
+    over every storage-order pair: direct and staged stores."""
+    L, x, ref = lt_small
+    tile = (tg, tz, tg * tz // r * -(-36 // s), (3 << 16) | (r << 8) | s)
+    h = cj.specialize(cj.K_LTIMES, cj.F32, layout_a=lin, layout_b=lout, m=36, d=96, tile=tile)
+    assert relF(run_ltimes(h, L, x, lin, lout, cj.F32), ref) <= TOL32
+
+
+@pytest.mark.parametrize("M,D,G,Z,lin,lout,tile", [
+    (37, 12, 3, 50, 0, 0, (1, 64, 128, (3 << 16) | (2 << 8) | 12)),     # partial group, vector d loads
+    (37, 12, 3, 50, 3, 5, (8, 8, 192, (3 << 16) | (1 << 8) | 16)),      # partial group, staged out box
+    (9, 7, 4, 33, 1, 4, (32, 4, 128, (3 << 16) | (1 << 8))),            # M not a multiple of 4, scalar d
+    (64, 8, 2, 130, 3, 3, (1, 128, 256, (3 << 16) | (1 << 8) | 32)),    # M_FAST direct float4 stores
+])
+def test_ltimes_f32_direct_shapes(M, D, G, Z, lin, lout, tile):
+    L, x = synth.ltimes_inputs_np(synth.SEED_LTIMES, M, D, G, Z)
+    ref = oracle.ltimes(L, x.ravel(), G, Z, 0, 0).reshape(M, G, Z)
+    h = cj.specialize(cj.K_LTIMES, cj.F32, layout_a=lin, layout_b=lout, m=M, d=D, tile=tile)
+    assert relF(run_ltimes(h, L, x, lin, lout, cj.F32), ref) <= TOL32
+
+
 @pytest.mark.parametrize("lin,lout", [(0, 0), (1, 3), (3, 5), (5, 2)])
 @pytest.mark.parametrize("dt", [cj.F64, cj.F32])
 def test_ltimes_generic(lt_small, lin, lout, dt):
