@@ -427,7 +427,10 @@ def main():
             return []
         gi, go = lin in (1, 4), lout in (1, 4)
         tg = 1 if not (gi or go) else (8 if (gi and lout in (0, 2)) or (go and lin in (0, 2)) else 32)
-        return [("tf32x3", (tg, 64 // tg, 128, (1 << 20) | (2 << 16) | (1 << 8) | 8)),
+        return [("tc_s4p8", (tg, 128 // tg, 32 * 13, (4 << 16) | (4 << 8) | 8)),
+                ("tc_s3p8", (tg, 128 // tg, 32 * 13, (4 << 16) | (3 << 8) | 8)),
+                ("tc_s2p8", (tg, 128 // tg, 32 * 13, (4 << 16) | (2 << 8) | 8)),
+                ("tf32x3", (tg, 64 // tg, 128, (1 << 20) | (2 << 16) | (1 << 8) | 8)),
                 ("direct_r2", (tg, 256 // tg, 128, (3 << 16) | (2 << 8))),
                 ("direct_r1", (tg, 128 // tg, 128, (3 << 16) | (1 << 8))),
                 ("direct_r2_s12", (tg, 128 // tg, 192, (3 << 16) | (2 << 8) | 12)),

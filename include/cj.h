@@ -202,6 +202,18 @@ cj_status cj_handle_info(cj_handle h, char *key_hex, size_t cap, int *variant);
  * launches now (cuFuncGetAttribute), for the register comparison of Sec. 5. */
 cj_status cj_handle_regs(cj_handle h, int *regs_per_thread, int *static_smem);
 
+/* Bounded waits that expired in h's run-time-compiled kernel since the
+ * module was loaded (or last reset).  The tcgen05 LTimes kernels (tile mode
+ * 4) wait on shared-memory barriers for at most about a second each; a block
+ * whose wait expires stops, waits for its issued tensor-core work, frees its
+ * tensor memory, adds one to this counter and returns, leaving its part of
+ * `out` incomplete.  Synchronizes the device, then reads the counter of h's
+ * own module; reset != 0 zeroes it afterwards.  *count = 0 for handles with
+ * no such module (AoT, generic, or kernels without bounded waits).
+ * CJ_ERR_INVALID_ARG: null h or count; CJ_ERR_NO_DEVICE: compile-only mode;
+ * CJ_ERR_CUDA: the synchronize or the copy failed. */
+cj_status cj_handle_wait_timeouts(cj_handle h, uint32_t *count, int reset);
+
 /*
  * Grouped plan for an uneven batch (many instances of different N and T in
  * one launch; the lookup cost is paid once per distinct N, Sec. 5.1).

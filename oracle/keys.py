@@ -81,6 +81,9 @@ def default_tile(kernel: int, dtype: int, n: int, layout_a: int = 0, layout_b: i
             tg = 8
         else:
             tg = 32
+        if dtype == F32 and m <= 96:
+            # tensor-core mode 4: 128 columns, 2 operand stages, 8 producer warps
+            return (tg, 128 // tg, 32 * (5 + 8), (4 << 16) | (2 << 8) | 8)
         if dtype == F32:
             return (tg, ct // tg, 32 * (-(-m // 12)), (1 << 20) | (2 << 8) | 12)
         return (tg, ct // tg, ct * (-(-m // 9)), (1 << 8) | 9)

@@ -22,7 +22,7 @@ CFG_COMPILE_ONLY = 0x1
 VARIANT_NAMES = ("generic", "aot", "jit")
 
 EXPORTS = ("cj_init", "cj_specialize", "cj_specialize_wait", "cj_launch", "cj_stats", "cj_handle_info",
-           "cj_handle_regs", "cj_group_plan_create", "cj_group_plan_launch", "cj_group_plan_info",
+           "cj_handle_regs", "cj_handle_wait_timeouts", "cj_group_plan_create", "cj_group_plan_launch", "cj_group_plan_info",
            "cj_group_plan_destroy", "cj_measure_fma_peak", "cj_update_chain_uneven_noalloc", "cj_candidates",
            "cj_autotune", "cj_featurize", "cj_mlp_create", "cj_mlp_set_params", "cj_mlp_get_params",
            "cj_mlp_forward", "cj_mlp_grad", "cj_mlp_train_step", "cj_mlp_destroy", "cj_cost_model_use",
@@ -75,6 +75,7 @@ def load():
         L.cj_stats.argtypes = [ctypes.POINTER(Stats)]
         L.cj_handle_info.argtypes = [P, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int)]
         L.cj_handle_regs.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        L.cj_handle_wait_timeouts.argtypes = [P, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int]
         L.cj_group_plan_create.argtypes = [i32, i64, P, P, ctypes.c_uint32, ctypes.POINTER(P)]
         L.cj_group_plan_launch.argtypes = [P, P, P, P, ctypes.c_int]
         L.cj_group_plan_info.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i64)]
@@ -169,6 +170,12 @@ class Handle:
         r, s = ctypes.c_int(0), ctypes.c_int(0)
         _check(load().cj_handle_regs(self.ptr, ctypes.byref(r), ctypes.byref(s)), "cj_handle_regs")
         return r.value, s.value
+
+    def wait_timeouts(self, reset: bool = False) -> int:
+        """Expired bounded waits in this handle's JIT module (synchronizes the device)."""
+        c = ctypes.c_uint32(0)
+        _check(load().cj_handle_wait_timeouts(self.ptr, ctypes.byref(c), int(reset)), "cj_handle_wait_timeouts")
+        return c.value
 
     def wait(self, timeout_ms: int = -1) -> int:
         return load().cj_specialize_wait(self.ptr, timeout_ms)

@@ -64,6 +64,7 @@ struct Driver {
                                 CUlibraryOption *, void **, unsigned int) = nullptr;
     CUresult (*LibraryGetKernel)(CUkernel *, CUlibrary, const char *) = nullptr;
     CUresult (*LibraryUnload)(CUlibrary) = nullptr;
+    CUresult (*LibraryGetGlobal)(CUdeviceptr *, size_t *, CUlibrary, const char *) = nullptr;
     CUresult (*KernelGetFunction)(CUfunction *, CUkernel) = nullptr;
     CUresult (*FuncSetAttribute)(CUfunction, CUfunction_attribute, int) = nullptr;
     CUresult (*FuncGetAttribute)(int *, CUfunction_attribute, CUfunction) = nullptr;
@@ -86,7 +87,8 @@ bool entry(const char *name, F &fp) {
 
 bool load_driver() {
     return entry("cuLibraryLoadData", drv.LibraryLoadData) && entry("cuLibraryGetKernel", drv.LibraryGetKernel) &&
-           entry("cuLibraryUnload", drv.LibraryUnload) && entry("cuKernelGetFunction", drv.KernelGetFunction) &&
+           entry("cuLibraryUnload", drv.LibraryUnload) && entry("cuLibraryGetGlobal", drv.LibraryGetGlobal) &&
+           entry("cuKernelGetFunction", drv.KernelGetFunction) &&
            entry("cuFuncSetAttribute", drv.FuncSetAttribute) && entry("cuFuncGetAttribute", drv.FuncGetAttribute) &&
            entry("cuLaunchKernel", drv.LaunchKernel) &&
            entry("cuOccupancyMaxActiveBlocksPerMultiprocessor", drv.OccupancyMaxActiveBlocksPerMultiprocessor) &&
@@ -221,6 +223,13 @@ void default_tile(int k, cj_template_args &a) {
     else tg = 32;
     a.tile[0] = tg;
     a.tile[1] = ct / tg;
+    if (a.dtype == CJ_F32 && v.m <= 96) {
+        // tcgen05 3xTF32: 128 columns, 2 operand stages, 8 producer warps
+        a.tile[1] = 128 / tg;
+        a.tile[2] = 32 * (5 + 8);
+        a.tile[3] = (4 << 16) | (2 << 8) | 8;
+        return;
+    }
     if (a.dtype == CJ_F32) {
         // 64 columns, R 2, S 12, pipelined loads; threads = 32 * ceil(m / 12)
         a.tile[0] = tg;
@@ -318,7 +327,9 @@ cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_
         const LtView v = lt_view(k, a);
         const int pipe = (a.tile[3] >> 20) & 0xf, mode = (a.tile[3] >> 16) & 0xf;
         const int r = (a.tile[3] >> 8) & 0xff, s = a.tile[3] & 0xff;
-        if (pipe > 1 || (a.tile[3] >> 24)) return fail(CJ_ERR_INVALID_ARG, "LTimes tile flags 0x%x unknown", a.tile[3]);
+        // mode 4 reuses the pipe field as the producers' prefetch depth (0 = automatic)
+        if ((mode == 4 ? pipe > 8 : pipe > 1) || (a.tile[3] >> 24))
+            return fail(CJ_ERR_INVALID_ARG, "LTimes tile flags 0x%x unknown", a.tile[3]);
         if (mode == 1 && (a.dtype != CJ_F64 || s != 8 || v.d % 4 || r < 1 || (tg * tz) % (8 * r) ||
                           (tg * tz / (8 * r)) * 32 != nt || nt > 1024))
             return fail(CJ_ERR_INVALID_ARG, "LTimes tensor-core tile {%d,%d,%d,0x%x} invalid (f64, S = 8, d %% 4 == 0, "
@@ -333,13 +344,19 @@ cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_
             return fail(CJ_ERR_INVALID_ARG, "LTimes direct tile {%d,%d,%d,0x%x} invalid (f32, no PIPE, R <= 4, S = 0 "
                         "or a multiple of 4 below m, threads = TG * TZ / R * ceil(m / S))", a.tile[0], a.tile[1],
                         a.tile[2], a.tile[3]);
-        if (mode > 3) return fail(CJ_ERR_INVALID_ARG, "LTimes compute mode %d unknown", mode);
+        if (mode == 4 && (a.dtype != CJ_F32 || tg * tz != 128 || r < 2 || r > 8 ||
+                          (s != 2 && s != 4 && s != 8) || nt != 32 * (5 + s) || v.m > 128))
+            return fail(CJ_ERR_INVALID_ARG, "LTimes tcgen05 tile {%d,%d,%d,0x%x} invalid (f32, TG * TZ = 128, "
+                        "2 <= stages <= 8, producer warps 2/4/8, threads = 32 * (5 + producer warps), m <= 128)",
+                        a.tile[0], a.tile[1], a.tile[2], a.tile[3]);
+        if (mode > 4) return fail(CJ_ERR_INVALID_ARG, "LTimes compute mode %d unknown", mode);
         if (mode == 0 && (tg < 1 || tz < 1 || r < 1 || s < 1 || nt < 32 || nt > 1024 || (tg * tz) % r ||
                           (tg * tz / r) * ((v.m + s - 1) / s) != nt))
             return fail(CJ_ERR_INVALID_ARG, "LTimes tile {%d,%d,%d,%d} does not cover its block", a.tile[0],
                         a.tile[1], a.tile[2], a.tile[3]);
-        if ((mode == 3 ? cjg::lt_direct_smem(v.m, v.d, tg * tz, esize(a.dtype), s)
-                       : cjg::lt_smem(v.m, s, v.d, tg * tz, esize(a.dtype), pipe, mode)) > 220 * 1024)
+        if ((mode == 4   ? cjg::lt_tc_smem(v.m, v.d, r, tg, tz, v.lout)
+             : mode == 3 ? cjg::lt_direct_smem(v.m, v.d, tg * tz, esize(a.dtype), s)
+                         : cjg::lt_smem(v.m, s, v.d, tg * tz, esize(a.dtype), pipe, mode)) > 220 * 1024)
             return fail(CJ_ERR_INVALID_ARG, "LTimes tile needs too much shared memory");
     }
     return CJ_OK;
@@ -378,11 +395,12 @@ void spec_geometry(const cj_handle_s *h, Impl &s) {
     const int es = esize(a.dtype);
     if (is_lt(h->kernel)) {
         const LtView v = lt_view(h->kernel, a);
+        const int mode = (a.tile[3] >> 16) & 0xf;
         s.threads = a.tile[2];
-        s.smem = ((a.tile[3] >> 16) & 0xf) == 3
-                     ? (size_t)cjg::lt_direct_smem(v.m, v.d, a.tile[0] * a.tile[1], es, a.tile[3] & 0xff)
-                     : (size_t)cjg::lt_smem(v.m, a.tile[3] & 0xff, v.d, a.tile[0] * a.tile[1], es,
-                                            (a.tile[3] >> 20) & 1, (a.tile[3] >> 16) & 0xf);
+        s.smem = mode == 4   ? (size_t)cjg::lt_tc_smem(v.m, v.d, (a.tile[3] >> 8) & 0xff, a.tile[0], a.tile[1], v.lout)
+                 : mode == 3 ? (size_t)cjg::lt_direct_smem(v.m, v.d, a.tile[0] * a.tile[1], es, a.tile[3] & 0xff)
+                             : (size_t)cjg::lt_smem(v.m, a.tile[3] & 0xff, v.d, a.tile[0] * a.tile[1], es,
+                                                    (a.tile[3] >> 20) & 1, mode);
     } else {
         s.ipb = a.tile[1];
         s.threads = cjg::chain_threads(a.n, a.tile[0], a.tile[1]);
@@ -401,7 +419,10 @@ std::string name_expression(const cj_handle_s *h) {
                  a.tile[1]);
     else {
         const LtView v = lt_view(h->kernel, a);
-        if (((a.tile[3] >> 16) & 0xf) == 3)
+        if (((a.tile[3] >> 16) & 0xf) == 4)
+            snprintf(buf, sizeof buf, "cj::ltimes_tc<%d, %d, %d, %d, %d, %d, %d, %d, %d, %d>", v.m, v.d, v.lin, v.lout,
+                     a.tile[0], a.tile[1], (a.tile[3] >> 8) & 0xff, a.tile[3] & 0xff, (a.tile[3] >> 20) & 0xf, v.acc);
+        else if (((a.tile[3] >> 16) & 0xf) == 3)
             snprintf(buf, sizeof buf, "cj::ltimes_direct<%s, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d>", ctype(a.dtype),
                      v.m, v.d, v.lin, v.lout, a.tile[0], a.tile[1], a.tile[2], (a.tile[3] >> 8) & 0xff,
                      a.tile[3] & 0xff, v.acc);
@@ -913,6 +934,22 @@ CJ_API cj_status cj_handle_regs(cj_handle h, int *regs, int *static_smem) {
         return fail(CJ_ERR_CUDA, "cuFuncGetAttribute failed");
     if (static_smem && drv.FuncGetAttribute(static_smem, CU_FUNC_ATTRIBUTE_SHARED_SIZE_BYTES, im->fn) != CUDA_SUCCESS)
         return fail(CJ_ERR_CUDA, "cuFuncGetAttribute failed");
+    return CJ_OK;
+}
+
+CJ_API cj_status cj_handle_wait_timeouts(cj_handle h, uint32_t *count, int reset) {
+    if (!h || !count) return fail(CJ_ERR_INVALID_ARG, "null handle or count");
+    if (G.compile_only) return fail(CJ_ERR_NO_DEVICE, "compile-only mode");
+    *count = 0;
+    if (!h->lib) return CJ_OK;   // no JIT module: AoT or generic kernels, which do not wait
+    CUdeviceptr p = 0;
+    size_t bytes = 0;
+    if (drv.LibraryGetGlobal(&p, &bytes, h->lib, "cj_wait_timeouts") != CUDA_SUCCESS || bytes != sizeof(uint32_t))
+        return CJ_OK;              // a module without bounded waits
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(count, reinterpret_cast<void *>(p), sizeof(uint32_t), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        (reset && cudaMemset(reinterpret_cast<void *>(p), 0, sizeof(uint32_t)) != cudaSuccess))
+        return fail(CJ_ERR_CUDA, "reading the wait-timeout counter failed");
     return CJ_OK;
 }
 

@@ -92,6 +92,37 @@ CJ_HD constexpr int lt_direct_mpad(int m, int s) {
 CJ_HD constexpr long lt_direct_smem(int m, int d, int ct, int esize, int s = 0) {
     return ((long)d * lt_mpitch(lt_direct_mpad(m, s), esize) + (long)m * lt_cpitch(ct, esize)) * esize;
 }
+// tcgen05 kernel (mode 4, FP32): 128-column tiles, MMA N = moments padded to
+// 16, K = directions padded to 32; `stages` operand tiles (tf32 hi and lo,
+// 128 x 32 each), L's hi and lo parts, one out box, 1 KB alignment slack.
+CJ_HD constexpr int lt_tc_np(int m) { return (m + 15) / 16 * 16; }
+CJ_HD constexpr int lt_tc_dp(int d) { return (d + 31) / 32 * 32; }
+// Registers per thread for one block of 5 + nprod warps per SM: the warps are
+// spread over the SM's four sub-partitions of 16K registers each, so the
+// fullest one holds ceil(warps / 4) of them (multiples of 8, at most 255).
+CJ_HD constexpr int lt_tc_maxreg(int nprod) {
+    return 16384 / (32 * ((5 + nprod + 3) / 4)) / 8 * 8 > 255 ? 255 : 16384 / (32 * ((5 + nprod + 3) / 4)) / 8 * 8;
+}
+// Operand tile of one stage (128 columns x 32 directions, tf32): K-adjacent
+// core matrices LBO bytes apart, 8-row groups SBO bytes apart (both padded
+// by 16 bytes off a multiple of 128 so writes spread over all banks).
+constexpr unsigned LT_TC_A_LBO = 144, LT_TC_A_SBO = 8 * 144 + 16, LT_TC_A_BYTES = 16 * LT_TC_A_SBO;
+// Staged out box: runs of `run` floats along out's faster column axis,
+// padded by 4 floats when that spreads a warp's writes over all banks.
+CJ_HD constexpr int lt_tc_runp(int run) { return run >= 8 ? run + 4 : run; }
+// m-fastest out: one box row of mp floats per column, mp / 4 odd.
+CJ_HD constexpr int lt_tc_mp(int m) { return (m + 3) / 4 % 2 ? (m + 3) / 4 * 4 : (m + 3) / 4 * 4 + 4; }
+// Shared memory of the tcgen05 kernel; tg, tz and out's storage order fix
+// the box (out's fastest axis: z for orders 0 and 2, g for 1 and 4, m for 3
+// and 5).
+CJ_HD constexpr long lt_tc_box(int m, int tg, int tz, int lout) {
+    return lout == 3 || lout == 5 ? 128L * lt_tc_mp(m)
+                                  : (long)m * (128 / (lout == 1 || lout == 4 ? tg : tz)) *
+                                        lt_tc_runp(lout == 1 || lout == 4 ? tg : tz);
+}
+CJ_HD constexpr long lt_tc_smem(int m, int d, int stages, int tg, int tz, int lout) {
+    return 1024L + (long)stages * 2 * LT_TC_A_BYTES + 2L * lt_tc_np(m) * lt_tc_dp(d) * 4 + lt_tc_box(m, tg, tz, lout) * 4;
+}
 CJ_HD constexpr long lt_generic_smem(int m, int d, int cols, int esize) {
     return ((long)m * d + (long)d * cols) * esize;
 }

@@ -12,6 +12,9 @@
 #define CJ_LTIMES_CUH
 #include "geometry.h"
 
+// Bounded waits of the tcgen05 kernels that expired (each block counts once).
+__device__ unsigned int cj_wait_timeouts;
+
 namespace cj {
 
 __device__ __forceinline__ double lt_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
@@ -453,6 +456,533 @@ ltimes_direct(const T* __restrict__ L, const T* __restrict__ in, T* __restrict__
             __syncthreads();
             lt_box<T, LOUT, M, TG, TZ, CP, NT, false, ACC != 0>(out, sO, G, Z, g0, z0, tid);
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 5th-generation tensor cores (MODE 4, FP32 in and out).  The contraction of
+// a 128-column tile is the GEMM D[col][m] = sum_d in[d][col] L[m][d] with the
+// 128 columns as the MMA's M dimension, the moments (padded to NP, a
+// multiple of 16) as N and the directions (padded to DP, a multiple of 32)
+// as K.  Each product runs as three TF32 products, in_lo L_hi + in_hi L_lo +
+// in_hi L_hi (x = x_hi + x_lo, both parts rounded to tf32; the dropped
+// in_lo L_lo term is below FP32 rounding), on tcgen05.mma kind::tf32 with
+// the FP32 accumulator in tensor memory.
+//
+// Roles (warp w): w 0-3 epilogue (TMEM lanes 32w..32w+31 = tile columns),
+// w 4 allocates TMEM and one lane issues the MMAs, w 5.. (NPROD warps)
+// produce.  Producers read `in` from global memory in its own storage order
+// with whole-line warp accesses (a float4 of four adjacent columns per lane
+// at one direction when a column axis is fastest, 512 contiguous bytes per
+// warp; a column's 128-byte run of 32 directions per eight lanes when d is
+// fastest), split each value into tf32 hi/lo and write both into a
+// STAGES-deep ring of K-major operand tiles (128 columns x 32 directions, no
+// swizzle: 8x16-byte core matrices, K-adjacent ones LBO = 144 B apart, 8-row
+// groups SBO = 1168 B apart; the 16-byte pads make both write patterns
+// conflict-free).  L's hi/lo parts are laid out once per block with LBO =
+// 128 B and SBO = DP*32 B.  Two accumulators of NPA
+// columns let the epilogue of one tile overlap the MMAs of the next.  Every
+// wait is bounded (about a second): on expiry the block raises its abort
+// flag, counts the event in cj_wait_timeouts, drains its MMAs, frees TMEM
+// and returns.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned lt_smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void lt_mbar_init(unsigned bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void lt_mbar_arrive(unsigned bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool lt_mbar_test(unsigned bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long lt_globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the phase of parity `parity` to complete; false after about a
+// second, or at once when abort_flag (if given) is up.
+__device__ __forceinline__ bool lt_mbar_wait(unsigned bar, unsigned parity, volatile int* abort_flag) {
+    if (lt_mbar_test(bar, parity)) return true;
+    const unsigned long long t0 = lt_globaltimer();
+    for (;;) {
+        if (lt_mbar_test(bar, parity)) return true;
+        if (abort_flag && *abort_flag) return false;
+        if (lt_globaltimer() - t0 > 1000000000ull) return false;
+    }
+}
+__device__ __forceinline__ void lt_tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void lt_tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void lt_tc_commit(unsigned bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+// Shared-memory matrix descriptor, K-major without swizzle: start address,
+// leading byte offset (K-adjacent core matrices), stride byte offset (8-row
+// groups), descriptor version 1 at bit 46, swizzle mode 0.
+__device__ __forceinline__ unsigned long long lt_tc_desc(unsigned saddr, unsigned lbo, unsigned sbo) {
+    return (unsigned long long)((saddr & 0x3FFFFu) >> 4) | ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+__device__ __forceinline__ void lt_tc_mma_tf32(unsigned d_tmem, unsigned long long a, unsigned long long b,
+                                               unsigned idesc, unsigned accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// Columns c..c+15 of this thread's TMEM lane (warp w reads lanes 32(w%4)..).
+__device__ __forceinline__ void lt_tmem_ld16(unsigned taddr, float (&v)[16]) {
+    unsigned r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    // the registers are valid only after wait::ld; passing them through it
+    // keeps every use behind the wait
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15])
+                 :
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Store the staged out box of one tile (see ltimes_tc): units of V
+// consecutive elements along out's faster column axis A2 (1 = g, 2 = z),
+// walked in out's storage order by the 128 epilogue threads.  Box layout:
+// box[m * OUTER * RUNP + outer * RUNP + inner].
+template <int V, int M, int A2, int RUN, int OUTER, int RUNP, bool M_SLOWEST, int ACC>
+__device__ __forceinline__ void lt_tc_store_box(float* __restrict__ out, const float* box, long long G, long long Z,
+                                                long long g0, long long z0, const long long (&so)[3], int r) {
+    constexpr int NV = RUN / V, UNITS = M * OUTER * NV, MS = OUTER * RUNP;
+    for (int u = r; u < UNITS; u += 128) {
+        const int iv = u % NV, rest = u / NV;
+        const int o = M_SLOWEST ? rest % OUTER : rest / M;
+        const int m = M_SLOWEST ? rest / OUTER : rest % M;
+        const int inner = iv * V;
+        const long long g = g0 + (A2 == 1 ? inner : o), z = z0 + (A2 == 1 ? o : inner);
+        if (g >= G || z >= Z) continue;
+        float* p = out + m * so[0] + g * so[1] + z * so[2];
+        const float* q = box + m * MS + o * RUNP + inner;
+        if constexpr (V == 4) {
+            float4 x = *reinterpret_cast<const float4*>(q);
+            if (ACC) {
+                const float4 w = *reinterpret_cast<const float4*>(p);
+                x.x += w.x; x.y += w.y; x.z += w.z; x.w += w.w;
+            }
+            *reinterpret_cast<float4*>(p) = x;
+        } else {
+            *p = ACC ? *p + *q : *q;
+        }
+    }
+}
+
+// Same for out with m fastest: box[column * MP + m], columns in out's order
+// (outer column axis slower, A1 the faster one with extent RIN); units of V
+// consecutive moments.
+template <int V, int M, int A1, int RIN, int MP, int ACC>
+__device__ __forceinline__ void lt_tc_store_mbox(float* __restrict__ out, const float* box, long long G, long long Z,
+                                                 long long g0, long long z0, const long long (&so)[3], int r) {
+    constexpr int NV = M / V, UNITS = 128 * NV;
+    for (int u = r; u < UNITS; u += 128) {
+        const int mv = u % NV, ci = u / NV;
+        const int inner = ci % RIN, outer = ci / RIN;
+        const long long g = g0 + (A1 == 1 ? inner : outer), z = z0 + (A1 == 1 ? outer : inner);
+        if (g >= G || z >= Z) continue;
+        float* p = out + g * so[1] + z * so[2] + mv * V;
+        const float* q = box + ci * MP + mv * V;
+        if constexpr (V == 4) {
+            float4 x = *reinterpret_cast<const float4*>(q);
+            if (ACC) {
+                const float4 w = *reinterpret_cast<const float4*>(p);
+                x.x += w.x; x.y += w.y; x.z += w.z; x.w += w.w;
+            }
+            *reinterpret_cast<float4*>(p) = x;
+        } else {
+            *p = ACC ? *p + *q : *q;
+        }
+    }
+}
+
+template <int M, int D, int LIN, int LOUT, int TG, int TZ, int STAGES, int NPROD, int PF_ = 0, int ACC = 0>
+__global__ void __maxnreg__(cjg::lt_tc_maxreg(NPROD))
+ltimes_tc(const float* __restrict__ L, const float* __restrict__ in, float* __restrict__ out, long long G,
+          long long Z) {
+    constexpr int BM = 128, KB = 32;                 // tile columns, directions per stage
+    constexpr int NP = cjg::lt_tc_np(M), DP = cjg::lt_tc_dp(D), NKB = DP / KB;
+    constexpr int NPA = (NP + 31) / 32 * 32;         // TMEM columns per accumulator
+    constexpr int TCOLS = 2 * NPA <= 32 ? 32 : 2 * NPA <= 64 ? 64 : 2 * NPA <= 128 ? 128 : 2 * NPA <= 256 ? 256 : 512;
+    constexpr int PT = 32 * NPROD;                   // producer threads
+    constexpr int CH = BM * KB / 4 / PT;             // 16-byte chunks per producer thread per stage
+    constexpr unsigned A_LBO = cjg::LT_TC_A_LBO, A_SBO = cjg::LT_TC_A_SBO;
+    constexpr unsigned HALF = cjg::LT_TC_A_BYTES, STAGE_BYTES = 2u * HALF;
+    constexpr unsigned LBYTES = NP * DP * 4u;
+    constexpr unsigned B_SBO = (DP / 4) * 128u;
+    // kind::tf32, FP32 accumulator, both operands K-major, N = NP, M = 128
+    constexpr unsigned IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(NP >> 3) << 17) | ((128u >> 4) << 24);
+    static_assert(TG * TZ == BM && NP <= 256 && CH * PT * 4 == BM * KB && 8 % NPROD == 0, "tcgen05 LTimes tile");
+    constexpr bool G_FASTER = lt_pos(LIN, 1) > lt_pos(LIN, 2);
+    constexpr bool OUT_G_FASTER = lt_pos(LOUT, 1) > lt_pos(LOUT, 2);
+    constexpr bool D_FAST = lt_pos(LIN, 0) == 2;
+    constexpr bool M_FAST = lt_pos(LOUT, 0) == 2;
+    // Each thread stores its own tile row straight from registers when out
+    // has a column axis fastest and orders its column axes like in (a warp
+    // then writes 128 contiguous bytes per moment).  Otherwise the tile goes
+    // through a staged box in shared memory and is stored in out's order as
+    // float4 units:
+    //  * column axis fastest in out: runs along that axis (RUN floats, padded
+    //    to RUNP so the TMEM -> box writes spread over all banks), box index
+    //    m * MS + outer * RUNP + inner;
+    //  * m fastest in out: one row of MP floats per column, columns in out's
+    //    order (MP / 4 odd: conflict-free 16-byte writes), box index
+    //    column * MP + m.
+    constexpr bool DIRECT_OUT = !M_FAST && G_FASTER == OUT_G_FASTER;
+    constexpr int A2 = lt_axis(LOUT, 2);                  // 1 = g, 2 = z, 0 = m
+    constexpr int RUN = A2 == 1 ? TG : TZ, OUTER = BM / RUN;
+    constexpr int RUNP = cjg::lt_tc_runp(RUN), MS = OUTER * RUNP;
+    constexpr bool M_SLOWEST = lt_pos(LOUT, 0) == 0;
+    constexpr int A1 = lt_axis(LOUT, 1);                  // m fastest: out's faster column axis
+    constexpr int RIN = A1 == 1 ? TG : TZ, MP = cjg::lt_tc_mp(M);
+
+    extern __shared__ __align__(16) unsigned char cj_smem[];
+    __shared__ __align__(8) unsigned long long bars[2 * STAGES + 6];
+    __shared__ unsigned tmem_slot;
+    __shared__ int abort_flag;
+    unsigned char* base = cj_smem + ((1024u - (lt_smem_u32(cj_smem) & 1023u)) & 1023u);
+    unsigned char* ring = base;                                   // STAGES x [A_hi | A_lo]
+    float* sLhi = reinterpret_cast<float*>(base + STAGES * STAGE_BYTES);
+    float* sLlo = reinterpret_cast<float*>(base + STAGES * STAGE_BYTES + LBYTES);
+    float* sO = reinterpret_cast<float*>(base + STAGES * STAGE_BYTES + 2 * LBYTES);
+    const unsigned ring_u = lt_smem_u32(ring), lhi_u = lt_smem_u32(sLhi), llo_u = lt_smem_u32(sLlo);
+    const unsigned bar_u = lt_smem_u32(bars);
+    auto full_bar = [&](int s) { return bar_u + 8u * s; };
+    auto empty_bar = [&](int s) { return bar_u + 8u * (STAGES + s); };
+    auto accf_bar = [&](int a) { return bar_u + 8u * (2 * STAGES + a); };
+    auto acce_bar = [&](int a) { return bar_u + 8u * (2 * STAGES + 2 + a); };
+    const unsigned done_bar = bar_u + 8u * (2 * STAGES + 4);
+    const unsigned epi_bar = bar_u + 8u * (2 * STAGES + 5);   // the 128 epilogue threads
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            lt_mbar_init(full_bar(s), PT);
+            lt_mbar_init(empty_bar(s), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            lt_mbar_init(accf_bar(a), 1);
+            lt_mbar_init(acce_bar(a), 4 * 32);
+        }
+        lt_mbar_init(done_bar, 1);
+        lt_mbar_init(epi_bar, 4 * 32);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 4) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(lt_smem_u32(&tmem_slot)),
+                     "r"(TCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // L (hi and lo) in the K-major core-matrix layout, zero-padded to NP x DP
+    for (int e = tid; e < NP * DP; e += blockDim.x) {
+        const int n = e / DP, k = e - n * DP;
+        const float v = (n < M && k < D) ? L[n * D + k] : 0.f;
+        const unsigned hi = to_tf32(v);
+        const unsigned off = (k >> 2) * 128u + (n >> 3) * B_SBO + (n & 7) * 16u + (k & 3) * 4u;
+        reinterpret_cast<unsigned*>(reinterpret_cast<unsigned char*>(sLhi) + off)[0] = hi;
+        reinterpret_cast<unsigned*>(reinterpret_cast<unsigned char*>(sLlo) + off)[0] = to_tf32(v - __uint_as_float(hi));
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    lt_tc_fence_before();
+    __syncthreads();
+    lt_tc_fence_after();
+    const unsigned tmem = tmem_slot;
+    volatile int* abort_v = &abort_flag;
+    auto give_up = [&]() {
+        if (atomicExch(&abort_flag, 1) == 0) atomicAdd(&cj_wait_timeouts, 1u);
+    };
+
+    const long long ext[3] = {D, G, Z};
+    long long st[3], so[3];
+    st[lt_axis(LIN, 2)] = 1;
+    st[lt_axis(LIN, 1)] = ext[lt_axis(LIN, 2)];
+    st[lt_axis(LIN, 0)] = ext[lt_axis(LIN, 2)] * ext[lt_axis(LIN, 1)];
+    const long long exo[3] = {M, G, Z};
+    so[lt_axis(LOUT, 2)] = 1;
+    so[lt_axis(LOUT, 1)] = exo[lt_axis(LOUT, 2)];
+    so[lt_axis(LOUT, 0)] = exo[lt_axis(LOUT, 2)] * exo[lt_axis(LOUT, 1)];
+    // Tile t covers g-block t % ntg and z-block t / ntg: the tiles that share
+    // a z range (and so the cache lines of a g-fastest tensor) run at the
+    // same time on neighbouring blocks and meet in L2.
+    const long long ntg = (G + TG - 1) / TG;
+    const long long ntiles = ntg * ((Z + TZ - 1) / TZ);
+    const unsigned ntg32 = (unsigned)ntg;
+    // tile row r (0..127) -> (gl, zl), rows in the order of in's faster column axis
+    auto row_g = [&](int r) { return G_FASTER ? r % TG : r / TZ; };
+    auto row_z = [&](int r) { return G_FASTER ? r / TG : r % TZ; };
+
+    if (warp >= 5) {
+        // ---------------- producers ----------------
+        // Iteration i of this block is tile blockIdx.x + (i / NKB) * gridDim.x,
+        // K block i % NKB.  Loads run PF - 1 iterations ahead in a register
+        // ring of PF * CH float4 (PF_ = 0: what the register cap leaves), so
+        // several stages of `in` are in flight per thread while it waits for
+        // a free operand stage.  Tile indices fit 32 bits (G * Z < 2^38).
+        constexpr int PF_AUTO = (cjg::lt_tc_maxreg(NPROD) - 64) / (4 * CH);
+        constexpr int PF = PF_ > 0 ? PF_ : (PF_AUTO < 1 ? 1 : PF_AUTO > 8 ? 8 : PF_AUTO);
+        const int pt = tid - 5 * 32;
+        const long long n_it = (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x * NKB;
+        // Column-fastest `in`: warp wp loads direction quads kq = wp * UPW ..
+        // (UPW = 8 / NPROD), lane l columns 4l..4l+3 (a float4 when the
+        // fastest column axis has a multiple-of-4 extent, else scalars);
+        // v[4 * uu + dd] holds direction 4 kq + dd.  d-fastest `in`: chunk q
+        // of the stage is (row q >> 3, quad q & 7), a float4 along d.
+        constexpr int UPW = 8 / NPROD;
+        const int wp = pt >> 5, c0 = 4 * (pt & 31);
+        const long long fast_ext = G_FASTER ? G : Z;
+        const bool vec4 = D_FAST ? (D % 4 == 0) : (fast_ext % 4 == 0 && (G_FASTER ? TG : TZ) % 4 == 0);
+        auto load = [&](long long i, float4 (&v)[CH]) {
+            const unsigned t = blockIdx.x + (unsigned)(i / NKB) * gridDim.x;
+            const int kb = (int)(i % NKB);
+            const long long g0 = (long long)(t % ntg32) * TG, z0 = (long long)(t / ntg32) * TZ;
+            if constexpr (D_FAST) {
+#pragma unroll
+                for (int j = 0; j < CH; ++j) {
+                    const int q = j * PT + pt;
+                    const int r = q >> 3, d0 = kb * KB + (q & 7) * 4;
+                    const long long g = g0 + row_g(r), z = z0 + row_z(r);
+                    const bool ok = g < G && z < Z;
+                    const float* p = in + (ok ? g * st[1] + z * st[2] : 0);
+                    if (vec4) {
+                        v[j] = (ok && d0 < D) ? __ldg(reinterpret_cast<const float4*>(p + d0))
+                                              : make_float4(0.f, 0.f, 0.f, 0.f);
+                    } else {
+                        v[j].x = (ok && d0 + 0 < D) ? __ldg(p + d0 + 0) : 0.f;
+                        v[j].y = (ok && d0 + 1 < D) ? __ldg(p + d0 + 1) : 0.f;
+                        v[j].z = (ok && d0 + 2 < D) ? __ldg(p + d0 + 2) : 0.f;
+                        v[j].w = (ok && d0 + 3 < D) ? __ldg(p + d0 + 3) : 0.f;
+                    }
+                }
+            } else {
+                const long long g = g0 + row_g(c0), z = z0 + row_z(c0);   // first of the four columns
+                const long long cbase = g * st[1] + z * st[2];
+#pragma unroll
+                for (int uu = 0; uu < UPW; ++uu)
+#pragma unroll
+                    for (int dd = 0; dd < 4; ++dd) {
+                        const int d = kb * KB + (wp * UPW + uu) * 4 + dd;
+                        float4& x = v[4 * uu + dd];
+                        if (vec4) {
+                            x = (g < G && z < Z && d < D)
+                                    ? __ldg(reinterpret_cast<const float4*>(in + cbase + (long long)d * st[0]))
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+                        } else {
+                            float e[4];
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) {
+                                const long long gc = g0 + row_g(c0 + c), zc = z0 + row_z(c0 + c);
+                                e[c] = (gc < G && zc < Z && d < D)
+                                           ? __ldg(in + gc * st[1] + zc * st[2] + (long long)d * st[0])
+                                           : 0.f;
+                            }
+                            x = make_float4(e[0], e[1], e[2], e[3]);
+                        }
+                    }
+            }
+        };
+        float4 buf[PF][CH];
+#pragma unroll
+        for (int u = 0; u < PF - 1; ++u)
+            if (u < n_it) load(u, buf[u]);
+        bool live = true;
+        for (long long i0 = 0; live && i0 < n_it; i0 += PF) {
+#pragma unroll
+            for (int u = 0; u < PF; ++u) {
+                const long long i = i0 + u;
+                if (i >= n_it) break;
+                if (i + PF - 1 < n_it) load(i + PF - 1, buf[(u + PF - 1) % PF]);
+                const int s = (int)(i % STAGES);
+                if (!lt_mbar_wait(empty_bar(s), (unsigned)((i / STAGES) & 1) ^ 1u, abort_v)) {
+                    give_up();
+                    live = false;
+                    break;
+                }
+                unsigned char* hi = ring + s * STAGE_BYTES;
+                auto put = [&](unsigned off, float4 c) {   // one 16-byte row of a core matrix, hi and lo
+                    uint4 h, l;
+                    h.x = to_tf32(c.x); l.x = to_tf32(c.x - __uint_as_float(h.x));
+                    h.y = to_tf32(c.y); l.y = to_tf32(c.y - __uint_as_float(h.y));
+                    h.z = to_tf32(c.z); l.z = to_tf32(c.z - __uint_as_float(h.z));
+                    h.w = to_tf32(c.w); l.w = to_tf32(c.w - __uint_as_float(h.w));
+                    *reinterpret_cast<uint4*>(hi + off) = h;
+                    *reinterpret_cast<uint4*>(hi + HALF + off) = l;
+                };
+                if constexpr (D_FAST) {
+#pragma unroll
+                    for (int j = 0; j < CH; ++j) {
+                        const int q = j * PT + pt, r = q >> 3;
+                        put((q & 7) * A_LBO + (r >> 3) * A_SBO + (r & 7) * 16u, buf[u][j]);
+                    }
+                } else {
+                    // 4 x 4 transpose in registers: column c0 + c, directions 4 kq .. 4 kq + 3
+#pragma unroll
+                    for (int uu = 0; uu < UPW; ++uu)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const float4* w = &buf[u][4 * uu];
+                            const float4 col = c == 0 ? make_float4(w[0].x, w[1].x, w[2].x, w[3].x)
+                                             : c == 1 ? make_float4(w[0].y, w[1].y, w[2].y, w[3].y)
+                                             : c == 2 ? make_float4(w[0].z, w[1].z, w[2].z, w[3].z)
+                                                      : make_float4(w[0].w, w[1].w, w[2].w, w[3].w);
+                            const int r = c0 + c;
+                            put((wp * UPW + uu) * A_LBO + (r >> 3) * A_SBO + (r & 7) * 16u, col);
+                        }
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                lt_mbar_arrive(full_bar(s));
+            }
+        }
+    } else if (warp == 4) {
+        // ---------------- MMA issue (one lane) ----------------
+        if (lane == 0) {
+            int it = 0, tl = 0;
+            bool ok = true;
+            for (long long t = blockIdx.x; ok && t < ntiles; t += gridDim.x, ++tl) {
+                const int a = tl & 1;
+                if (!lt_mbar_wait(acce_bar(a), ((tl >> 1) & 1) ^ 1, abort_v)) {
+                    give_up();
+                    break;
+                }
+                lt_tc_fence_after();
+                const unsigned dt = tmem + a * NPA;
+                for (int kb = 0; kb < NKB; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    if (!lt_mbar_wait(full_bar(s), (it / STAGES) & 1, abort_v)) {
+                        give_up();
+                        ok = false;
+                        break;
+                    }
+                    lt_tc_fence_after();
+                    const unsigned ahi = ring_u + s * STAGE_BYTES, alo = ahi + HALF;
+#pragma unroll
+                    for (int j = 0; j < KB / 8; ++j) {
+                        const unsigned bo = (kb * (KB / 4) + 2 * j) * 128u;
+                        const unsigned long long dah = lt_tc_desc(ahi + 2 * j * A_LBO, A_LBO, A_SBO);
+                        const unsigned long long dal = lt_tc_desc(alo + 2 * j * A_LBO, A_LBO, A_SBO);
+                        const unsigned long long dbh = lt_tc_desc(lhi_u + bo, 128u, B_SBO);
+                        const unsigned long long dbl = lt_tc_desc(llo_u + bo, 128u, B_SBO);
+                        lt_tc_mma_tf32(dt, dal, dbh, IDESC, (kb | j) != 0);
+                        lt_tc_mma_tf32(dt, dah, dbl, IDESC, 1u);
+                        lt_tc_mma_tf32(dt, dah, dbh, IDESC, 1u);
+                    }
+                    lt_tc_commit(empty_bar(s));   // the stage is free once these MMAs have read it
+                }
+                if (!ok) break;
+                lt_tc_commit(accf_bar(a));
+            }
+            // drain: every MMA issued above completes before TMEM is freed
+            // (bounded, and not cut short by the abort flag)
+            lt_tc_commit(done_bar);
+            if (!lt_mbar_wait(done_bar, 0, nullptr)) give_up();
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue (warps 0-3: tile rows 32w..32w+31) ----------------
+        const int r = tid;   // TMEM lane = tile row
+        int tl = 0, epi_use = 0;
+        // all 128 epilogue threads meet (bounded; an mbarrier, so that a
+        // thread that gives up cannot leave the others blocked)
+        auto epi_sync = [&]() {
+            lt_mbar_arrive(epi_bar);
+            const bool met = lt_mbar_wait(epi_bar, epi_use & 1, abort_v);
+            ++epi_use;
+            return met;
+        };
+        for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
+            const int a = tl & 1;
+            if (!lt_mbar_wait(accf_bar(a), (tl >> 1) & 1, abort_v)) {
+                give_up();
+                break;
+            }
+            lt_tc_fence_after();
+            const long long g0 = (t % ntg) * TG, z0 = (t / ntg) * TZ;
+            const int gl = row_g(r), zl = row_z(r);
+            const bool ok = g0 + gl < G && z0 + zl < Z;
+            float* o = out + (ok ? (g0 + gl) * so[1] + (z0 + zl) * so[2] : 0);
+            if constexpr (!DIRECT_OUT) {
+                if (!epi_sync()) {   // the previous box has been stored
+                    give_up();
+                    break;
+                }
+            }
+            // 16 accumulator columns (moments) at a time: TMEM -> registers -> out or the box
+#pragma unroll
+            for (int c = 0; c < NP; c += 16) {
+                float v[16];
+                lt_tmem_ld16(tmem + ((unsigned)(warp * 32) << 16) + a * NPA + c, v);
+                if constexpr (DIRECT_OUT) {
+                    if (ok) {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            if (c + i >= M) break;
+                            float* pp = o + (c + i) * so[0];
+                            *pp = ACC ? *pp + v[i] : v[i];
+                        }
+                    }
+                } else if constexpr (M_FAST) {
+                    const int ci = (A1 == 1 ? zl : gl) * RIN + (A1 == 1 ? gl : zl);   // column in out's order
+#pragma unroll
+                    for (int i4 = 0; i4 < 4; ++i4)
+                        if (c + 4 * i4 < MP)
+                            *reinterpret_cast<float4*>(sO + ci * MP + c + 4 * i4) =
+                                make_float4(v[4 * i4], v[4 * i4 + 1], v[4 * i4 + 2], v[4 * i4 + 3]);
+                } else {
+                    const int oidx = (A2 == 1 ? zl : gl) * RUNP + (A2 == 1 ? gl : zl);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        if (c + i < M) sO[(c + i) * MS + oidx] = v[i];
+                }
+            }
+            lt_tc_fence_before();
+            lt_mbar_arrive(acce_bar(a));   // the accumulator may be overwritten
+            if constexpr (!DIRECT_OUT) {
+                if (!epi_sync()) {
+                    give_up();
+                    break;
+                }
+                if constexpr (M_FAST) {
+                    if (M % 4 == 0)
+                        lt_tc_store_mbox<(M % 4 == 0 ? 4 : 1), M, A1, RIN, MP, ACC>(out, sO, G, Z, g0, z0, so, r);
+                    else
+                        lt_tc_store_mbox<1, M, A1, RIN, MP, ACC>(out, sO, G, Z, g0, z0, so, r);
+                } else if (RUN % 4 == 0 && (A2 == 1 ? G : Z) % 4 == 0)
+                    lt_tc_store_box<(RUN % 4 == 0 ? 4 : 1), M, A2, RUN, OUTER, RUNP, M_SLOWEST, ACC>(out, sO, G, Z, g0, z0,
+                                                                                                  so, r);
+                else
+                    lt_tc_store_box<1, M, A2, RUN, OUTER, RUNP, M_SLOWEST, ACC>(out, sO, G, Z, g0, z0, so, r);
+            }
+        }
+    }
+    lt_tc_fence_before();
+    __syncthreads();
+    if (warp == 4) {
+        lt_tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS) : "memory");
     }
 }
 

@@ -78,6 +78,11 @@ void ltimes_candidates(const cj_template_args &a, std::vector<std::array<int, 4>
         } else if (mode == 2) {
             if (ct % 16 || a.d % 8) return;
             nt = ct / 16 * 32;
+        } else if (mode == 4) {   // tcgen05: r = stages, s = producer warps
+            if (ct != 128 || a.dtype != CJ_F32 || a.m > 128) return;
+            if (cjg::lt_tc_smem(a.m, a.d, r, tg, ct / tg, a.layout_b) > 220 * 1024) return;
+            out.push_back({tg, ct / tg, 32 * (5 + s), (4 << 16) | (r << 8) | s});
+            return;
         } else if (mode == 3) {
             if (ct % r || (s && (s % 4 || s >= a.m))) return;
             nt = ct / r * (s ? (a.m + s - 1) / s : 1);
@@ -101,16 +106,14 @@ void ltimes_candidates(const cj_template_args &a, std::vector<std::array<int, 4>
             push(tg, 64, 0, 1, 9);
             push(tg, 64, 0, 1, 12);
         } else {
-            for (int ct : {64, 128}) {
-                push(tg, ct, 2, 1, 8, 1);  // 3xTF32 tensor cores
-                push(tg, ct, 0, 2, 12, 1);
-            }
-            push(tg, 256, 3, 2, 0, 0);                          // direct loads, all moments per thread
-            if (a.m > 12) {
-                push(tg, 128, 3, 2, 12, 0);                     // direct loads, 12 moments per thread
-                push(tg, 256, 3, 2, 12, 0);
-            }
-            push(tg, 128, 0, 4, 12, 0);   // unpipelined baseline
+            push(tg, 128, 4, 2, 8);             // tcgen05 3xTF32: 2 operand stages, 8 producer warps
+            push(tg, 128, 4, 3, 8);             //                 3 operand stages
+            push(tg, 64, 2, 1, 8, 1);           // mma.sync 3xTF32
+            push(tg, 64, 0, 2, 12, 1);          // FMA, cp.async double buffer
+            push(tg, 128, 0, 2, 12, 1);
+            push(tg, 256, 3, 2, 0, 0);          // direct loads, all moments per thread
+            if (a.m > 12) push(tg, 128, 3, 2, 12, 0);   // direct loads, 12 moments per thread
+            push(tg, 128, 0, 4, 12, 0);         // unpipelined baseline
         }
     }
 }

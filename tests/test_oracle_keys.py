@@ -14,9 +14,10 @@ def test_hand_assembled_chain_key():
 
 def test_hand_assembled_ltimes_key():
     # kernel 2, f32, in GZD(3), out ZGD(5), m=36, d=96, default tile
-    # (1, 64, 96, (1 << 20) | (2 << 8) | 12): 64 columns, pipelined, R 2, S 12
+    # (1, 128, 416, (4 << 16) | (2 << 8) | 8): tensor-core mode 4, 128 columns,
+    # 2 operand stages, 8 producer warps (416 threads)
     expect = bytes.fromhex("0200" "01" "03" "05" "00" "0000" "2400" "6000"
-                           "01000000" "40000000" "60000000" "0c021000" "00000000")
+                           "01000000" "80000000" "a0010000" "08020400" "00000000")
     assert K.canonical_key(K.K_LTIMES, K.F32, layout_a=3, layout_b=5, m=36, d=96) == expect
 
 

@@ -271,6 +271,61 @@ def test_ltimes_f32_direct_shapes(M, D, G, Z, lin, lout, tile):
     assert relF(run_ltimes(h, L, x, lin, lout, cj.F32), ref) <= TOL32
 
 
+def tc_tile(lin, lout, stages=2, nprod=8, tg=None):
+    """tcgen05 tile (mode 4): 128 columns, box shape by the faster column axes."""
+    if tg is None:
+        gi, go = lin in (1, 4), lout in (1, 4)
+        tg = 1 if not (gi or go) else (8 if (gi and lout in (0, 2)) or (go and lin in (0, 2)) else 32)
+    return (tg, 128 // tg, 32 * (5 + nprod), (4 << 16) | (stages << 8) | nprod)
+
+
+@pytest.mark.parametrize("lin", range(6))
+@pytest.mark.parametrize("lout", range(6))
+@pytest.mark.parametrize("stages,nprod", [(2, 8), (4, 8), (3, 4)])
+def test_ltimes_f32_tcgen05(lt_small, lin, lout, stages, nprod):
+    """Mode 4: tcgen05.mma kind::tf32 (3xTF32), accumulator in tensor memory,
+    every storage-order pair, ragged G = 5, Z = 37."""
+    L, x, ref = lt_small
+    h = cj.specialize(cj.K_LTIMES, cj.F32, layout_a=lin, layout_b=lout, m=36, d=96,
+                      tile=tc_tile(lin, lout, stages, nprod))
+    assert h.variant == "jit"
+    assert relF(run_ltimes(h, L, x, lin, lout, cj.F32), ref) <= TOL32
+    assert h.wait_timeouts() == 0
+
+
+@pytest.mark.parametrize("lin,lout,tg", [(0, 0, None), (3, 5, None), (4, 1, None), (1, 4, 8), (2, 3, 1), (5, 0, 8)])
+def test_ltimes_f32_tcgen05_many_tiles_per_block(lin, lout, tg):
+    """2048 tiles over at most one block per SM: both accumulators and every
+    stage go through many phases."""
+    M, D, G, Z = 36, 96, 32, 8192
+    L, x = synth.ltimes_inputs_np(synth.SEED_LTIMES, M, D, G, Z)
+    ref = oracle.ltimes(L, x.ravel(), G, Z, 0, 0, nthreads=8).reshape(M, G, Z)
+    h = cj.specialize(cj.K_LTIMES, cj.F32, layout_a=lin, layout_b=lout, m=M, d=D, tile=tc_tile(lin, lout, tg=tg))
+    out = run_ltimes(h, L, x, lin, lout, cj.F32)
+    assert relF(out, ref) <= TOL32
+    for m in (0, 17, 35):
+        assert relF(out[m], ref[m]) <= TOL32
+    assert h.wait_timeouts() == 0
+
+
+@pytest.mark.parametrize("M,D,G,Z,lin,lout,stages,nprod", [
+    (36, 96, 6, 44, 4, 5, 4, 8),      # g-fastest in with G % 4 != 0: scalar column loads
+    (36, 96, 8, 64, 1, 0, 4, 4),      # g-fastest in, TG = 8 box
+    (37, 12, 3, 50, 0, 0, 4, 8),      # one K block, zero-padded d; N = 48
+    (9, 7, 4, 33, 1, 4, 2, 2),        # D % 4 != 0, scalar loads; N = 16
+    (4, 100, 2, 300, 2, 3, 3, 8),     # four K blocks, ragged; m-fastest out
+    (64, 128, 3, 70, 3, 3, 2, 8),     # d-fastest float4 loads; N = 64
+    (16, 32, 32, 5, 4, 5, 4, 4),      # g-fastest in, 32-wide g box
+])
+def test_ltimes_f32_tcgen05_shapes(M, D, G, Z, lin, lout, stages, nprod):
+    L, x = synth.ltimes_inputs_np(synth.SEED_LTIMES, M, D, G, Z)
+    ref = oracle.ltimes(L, x.ravel(), G, Z, 0, 0).reshape(M, G, Z)
+    h = cj.specialize(cj.K_LTIMES, cj.F32, layout_a=lin, layout_b=lout, m=M, d=D,
+                      tile=tc_tile(lin, lout, stages, nprod))
+    assert relF(run_ltimes(h, L, x, lin, lout, cj.F32), ref) <= TOL32
+    assert h.wait_timeouts() == 0
+
+
 @pytest.mark.parametrize("lin,lout", [(0, 0), (1, 3), (3, 5), (5, 2)])
 @pytest.mark.parametrize("dt", [cj.F64, cj.F32])
 def test_ltimes_generic(lt_small, lin, lout, dt):
@@ -423,3 +478,23 @@ def test_lplustimes_accumulates(lin, lout, dt, generic):
     torch.cuda.synchronize()
     got = xt.double().cpu().numpy()
     assert relF(got, ref_phys) <= (TOL64 if dt == cj.F64 else TOL32)
+
+
+@pytest.mark.parametrize("lin,lout", [(0, 0), (3, 1), (4, 5), (2, 3), (1, 4)])
+def test_lplustimes_tcgen05(lin, lout):
+    """LPlusTimes on mode 4 (the swapped problem: 96 output rows, K = 36)."""
+    M, D, G, Z = 36, 96, 5, 41
+    Lp = synth.uniform_np(0xC1A6, 0, D * M).reshape(D, M)
+    y = synth.uniform_np(0xC1A7, 0, M * G * Z).reshape(M, G, Z)
+    base = synth.uniform_np(0xC1A8, 0, D * G * Z).reshape(D, G, Z)
+    ref_phys = oracle.lplustimes(Lp, synth.to_layout(y, lout).ravel(), synth.to_layout(base, lin).ravel(), G, Z,
+                                 lin, lout)
+    h = cj.specialize(cj.K_LPLUSTIMES, cj.F32, layout_a=lin, layout_b=lout, m=M, d=D,
+                      tile=tc_tile(lout, lin, stages=3, nprod=4))
+    Lt = torch.from_numpy(Lp).to("cuda", torch.float32)
+    yt = torch.from_numpy(synth.to_layout(y, lout).ravel()).to("cuda", torch.float32)
+    xt = torch.from_numpy(synth.to_layout(base, lin).ravel()).to("cuda", torch.float32)
+    cj.launch_lplustimes(h, Lt, yt, xt, G, Z)
+    torch.cuda.synchronize()
+    assert relF(xt.double().cpu().numpy(), ref_phys) <= TOL32
+    assert h.wait_timeouts() == 0
