@@ -565,19 +565,34 @@ def secondary(args):
                 rows.append(row)
                 tot_s += ms_s
                 tot_g += ms_g
-        peak = PEAK_TFLOPS[args.dtype]
-        t_alu = f / (peak * 1e12) * 1e3
+        # Compute bound of the default kernel: FP32 runs 3xTF32 on the tensor
+        # cores (tile mode 4: three TF32 products per multiply-add, TF32 peak
+        # = measured bf16 x the nominal 1.1 / 2.25 ratio); FP64 runs on the
+        # FP64 pipe at its nominal rate.
+        tc = args.dtype == "f32" and all(((r["tile"][3] >> 16) & 0xF) == 4 for r in rows)
+        if tc:
+            peak = measured_peak("bf16_tflops", 1800.0) * 1.1 / 2.25
+            t_alu = 3 * f / (peak * 1e12) * 1e3
+        else:
+            peak = PEAK_TFLOPS[args.dtype]
+            t_alu = f / (peak * 1e12) * 1e3
         t_hbm = byt / (hbm_peak_gbs() * 1e9) * 1e3
         mean_ms = tot_s / 36
+        bound = "tensor" if tc and t_alu >= t_hbm else "alu" if t_alu >= t_hbm else "hbm"
+        rf = {"bound": bound, "roofline_ms": max(t_alu, t_hbm), "mean_ms": mean_ms,
+              "frac": max(t_alu, t_hbm) / mean_ms, "compute_frac": t_alu / mean_ms, "hbm_frac": t_hbm / mean_ms,
+              "compute_peak_tflops": peak, "compute_unit": "TF32 tensor (3 passes)" if tc else args.dtype + " pipe",
+              "hbm_gbs": hbm_peak_gbs()}
+        if bound == "hbm":
+            rf.update({"achieved": byt / mean_ms / 1e6, "peak": hbm_peak_gbs(), "unit": "GB/s",
+                       "algorithmic_bytes": byt})
+        else:
+            rf.update({"achieved": f / mean_ms / 1e9, "peak": peak, "unit": "TFLOP/s"})
         out.update({"value": 36 * f / tot_s / 1e6, "dtype": args.dtype,
                     "generic": {"value": 36 * f / tot_g / 1e6, "unit": "GFLOP/s"},
                     "speedup_vs_generic": tot_g / tot_s,
                     "min_speedup_vs_generic": min(r["speedup_vs_generic"] for r in rows),
-                    "roofline": {"bound": "alu" if t_alu >= t_hbm else "hbm",
-                                 "roofline_ms": max(t_alu, t_hbm), "mean_ms": mean_ms,
-                                 "frac": max(t_alu, t_hbm) / mean_ms,
-                                 "alu_frac": t_alu / mean_ms, "hbm_frac": t_hbm / mean_ms,
-                                 "peak_tflops": peak, "hbm_gbs": hbm_peak_gbs()},
+                    "roofline": rf,
                     "per_pair": rows,
                     "config": {"workload": f"LTimes out[m][g][z] = sum_d L[m][d] in[d][g][z], M=36 D=96 G=32 Z={Z}, "
                                            f"all 36 (in, out) storage orders, {args.dtype}"}})
