@@ -427,8 +427,9 @@ def main():
             return []
         gi, go = lin in (1, 4), lout in (1, 4)
         tg = 1 if not (gi or go) else (8 if (gi and lout in (0, 2)) or (go and lin in (0, 2)) else 32)
-        return [("tc_s4p8", (tg, 128 // tg, 32 * 13, (4 << 16) | (4 << 8) | 8)),
-                ("tc_s3p8", (tg, 128 // tg, 32 * 13, (4 << 16) | (3 << 8) | 8)),
+        return [("tma_b4", (tg, 128 // tg, 32 * 14, (4 << 20) | (5 << 16) | (2 << 8) | 8)),
+                ("tma_b3", (tg, 128 // tg, 32 * 14, (3 << 20) | (5 << 16) | (2 << 8) | 8)),
+                ("tma_b4c4", (tg, 128 // tg, 32 * 10, (4 << 20) | (5 << 16) | (2 << 8) | 4)),
                 ("tc_s2p8", (tg, 128 // tg, 32 * 13, (4 << 16) | (2 << 8) | 8)),
                 ("tf32x3", (tg, 64 // tg, 128, (1 << 20) | (2 << 16) | (1 << 8) | 8)),
                 ("direct_r2", (tg, 256 // tg, 128, (3 << 16) | (2 << 8))),
@@ -566,10 +567,10 @@ def secondary(args):
                 tot_s += ms_s
                 tot_g += ms_g
         # Compute bound of the default kernel: FP32 runs 3xTF32 on the tensor
-        # cores (tile mode 4: three TF32 products per multiply-add, TF32 peak
+        # cores (tile modes 4 and 5: three TF32 products per multiply-add, TF32 peak
         # = measured bf16 x the nominal 1.1 / 2.25 ratio); FP64 runs on the
         # FP64 pipe at its nominal rate.
-        tc = args.dtype == "f32" and all(((r["tile"][3] >> 16) & 0xF) == 4 for r in rows)
+        tc = args.dtype == "f32" and all(((r["tile"][3] >> 16) & 0xF) in (4, 5) for r in rows)
         if tc:
             peak = measured_peak("bf16_tflops", 1800.0) * 1.1 / 2.25
             t_alu = 3 * f / (peak * 1e12) * 1e3

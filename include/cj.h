@@ -144,6 +144,10 @@ typedef struct {
     uint64_t requests, cache_hits, compiles_ok, compiles_failed, aot_hits;
     uint64_t launches_generic, launches_aot, launches_jit;
     double compile_ms_p50, compile_ms_p95, lookup_ns_p50;
+    /* LTimes tile mode 5: launches fed by TMA, and launches that fell back to
+     * the mode-4 kernel because `in` admitted no tensor map (innermost extent
+     * not a multiple of 4 floats, or `in` not 16-byte aligned) */
+    uint64_t launches_tma, launches_tma_fallback;
 } cj_stats_t;
 
 /* Initialise the library for `device` (idempotent for the same device).

@@ -62,6 +62,24 @@ G_FAST = (1, 4)
 Z_FAST = (0, 2)
 
 
+def _tc_smem(m, d, stages, tg, tz, lout, boxes):
+    """Shared-memory bytes of the tensor-core LTimes kernel (restated from the
+    documented layout): 1 KiB alignment slack; `boxes` TMA boxes of 128 x 32
+    floats; per operand stage two 128 x 32 tf32 tiles in 16 groups of 1168
+    bytes; L's hi and lo parts (moments padded to 16, directions to 32); the
+    out box (m fastest: 128 rows of mp floats, mp a multiple of 4 with mp / 4
+    odd; otherwise m rows of 128 / run runs, each run padded by 4 floats when
+    it is at least 8 long, run = the box extent of out's fastest axis)."""
+    np_, dp = -(-m // 16) * 16, -(-d // 32) * 32
+    if lout in (3, 5):
+        b = -(-m // 4)
+        box = 128 * (4 * b if b % 2 else 4 * b + 4)
+    else:
+        run = tg if lout in (1, 4) else tz
+        box = m * (128 // run) * (run + 4 if run >= 8 else run)
+    return 1024 + boxes * 128 * 32 * 4 + stages * 2 * 16 * 1168 + 2 * np_ * dp * 4 + box * 4
+
+
 def default_tile(kernel: int, dtype: int, n: int, layout_a: int = 0, layout_b: int = 0, m: int = 36,
                  d: int = 96) -> tuple:
     if kernel in (K_UPDATE_CHAIN, K_UPDATE_CHAIN_GROUPED):
@@ -81,9 +99,15 @@ def default_tile(kernel: int, dtype: int, n: int, layout_a: int = 0, layout_b: i
             tg = 8
         else:
             tg = 32
-        if dtype == F32 and m <= 96:
-            # tensor-core mode 4: 128 columns, 2 operand stages, 8 producer warps
-            return (tg, 128 // tg, 32 * (5 + 8), (4 << 16) | (2 << 8) | 8)
+        if dtype == F32 and m <= 128:
+            # tensor-core modes: 128 columns, 2 operand stages, 8 converter
+            # warps; TMA-fed (mode 5) with the deepest box ring that fits in
+            # 220 KiB of shared memory, else register producers (mode 4)
+            for boxes in (4, 3, 2):
+                if _tc_smem(m, d, 2, tg, 128 // tg, layout_b, boxes) <= 220 * 1024:
+                    return (tg, 128 // tg, 32 * (6 + 8), (boxes << 20) | (5 << 16) | (2 << 8) | 8)
+            if _tc_smem(m, d, 2, tg, 128 // tg, layout_b, 0) <= 220 * 1024:
+                return (tg, 128 // tg, 32 * (5 + 8), (4 << 16) | (2 << 8) | 8)
         if dtype == F32:
             return (tg, ct // tg, 32 * (-(-m // 12)), (1 << 20) | (2 << 8) | 12)
         return (tg, ct // tg, ct * (-(-m // 9)), (1 << 8) | 9)

@@ -51,7 +51,8 @@ class TemplateArgs(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("requests", "cache_hits", "compiles_ok", "compiles_failed",
                                                "aot_hits", "launches_generic", "launches_aot", "launches_jit")] + \
-               [(n, ctypes.c_double) for n in ("compile_ms_p50", "compile_ms_p95", "lookup_ns_p50")]
+               [(n, ctypes.c_double) for n in ("compile_ms_p50", "compile_ms_p95", "lookup_ns_p50")] + \
+               [(n, ctypes.c_uint64) for n in ("launches_tma", "launches_tma_fallback")]
 
 
 _lib = None

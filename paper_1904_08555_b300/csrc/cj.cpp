@@ -72,6 +72,10 @@ struct Driver {
                              unsigned, CUstream, void **, void **) = nullptr;
     CUresult (*OccupancyMaxActiveBlocksPerMultiprocessor)(int *, CUfunction, int, size_t) = nullptr;
     CUresult (*GetErrorString)(CUresult, const char **) = nullptr;
+    CUresult (*TensorMapEncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                     const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                     CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                     CUtensorMapFloatOOBfill) = nullptr;
 } drv;
 
 template <class F>
@@ -92,7 +96,7 @@ bool load_driver() {
            entry("cuFuncSetAttribute", drv.FuncSetAttribute) && entry("cuFuncGetAttribute", drv.FuncGetAttribute) &&
            entry("cuLaunchKernel", drv.LaunchKernel) &&
            entry("cuOccupancyMaxActiveBlocksPerMultiprocessor", drv.OccupancyMaxActiveBlocksPerMultiprocessor) &&
-           entry("cuGetErrorString", drv.GetErrorString);
+           entry("cuGetErrorString", drv.GetErrorString) && entry("cuTensorMapEncodeTiled", drv.TensorMapEncodeTiled);
 }
 
 const char *cu_str(CUresult r) {
@@ -116,6 +120,11 @@ struct Impl {
     size_t smem = 0;
     int ipb = 0;            // update chain / grouped: instances per block or chunk
     int blocks_per_sm = 1;  // persistent kernels (LTimes specialized, grouped)
+    // LTimes mode 5 only: the mode-4 instantiation of the same tile, launched
+    // when `in` admits no TMA tensor map (see launch_ltimes_tc)
+    CUfunction fn2 = nullptr;
+    int threads2 = 0, blocks2 = 1;
+    size_t smem2 = 0;
 };
 
 }  // namespace
@@ -130,7 +139,7 @@ struct cj_handle_s {
     std::mutex mu;
     std::condition_variable cv;
     CUlibrary lib = nullptr;
-    std::string name_expr, error;
+    std::string name_expr, name_expr2, error;
     double compile_ms = 0;
 };
 
@@ -162,7 +171,7 @@ struct State {
     std::vector<cj_group_plan_s *> plans;
     // statistics
     std::atomic<uint64_t> requests{0}, hits{0}, ok{0}, failed{0}, aot_hits{0};
-    std::atomic<uint64_t> l_gen{0}, l_aot{0}, l_jit{0};
+    std::atomic<uint64_t> l_gen{0}, l_aot{0}, l_jit{0}, l_tma{0}, l_tma_fb{0};
     std::mutex smu;
     std::vector<double> compile_ms;
     std::vector<double> lookup_ns;
@@ -195,6 +204,11 @@ const char *ctype(int dtype) { return dtype == CJ_F64 ? "double" : "float"; }
 // ---------------------------------------------------------------------------
 bool g_fast(int lay) { return lay == 1 || lay == 4; }
 bool z_fast(int lay) { return lay == 0 || lay == 2; }
+// Axis (0 = d or m, 1 = g, 2 = z) at slot s (0 slowest .. 2 fastest) of storage order lay.
+int lt_axis_host(int lay, int s) {
+    static const int order[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    return order[lay][s];
+}
 bool is_lt(int k) { return k == CJ_K_LTIMES || k == CJ_K_LPLUSTIMES; }
 
 // The LTimes kernel a request runs: LPlusTimes is LTimes of the swapped
@@ -223,12 +237,23 @@ void default_tile(int k, cj_template_args &a) {
     else tg = 32;
     a.tile[0] = tg;
     a.tile[1] = ct / tg;
-    if (a.dtype == CJ_F32 && v.m <= 96) {
-        // tcgen05 3xTF32: 128 columns, 2 operand stages, 8 producer warps
+    if (a.dtype == CJ_F32 && v.m <= 128) {
+        // tcgen05 3xTF32, 128 columns, 2 operand stages, 8 converter/producer
+        // warps: fed by TMA with the deepest box ring (4, 3 or 2) that fits in
+        // shared memory (mode 5), else register producers (mode 4).  The box
+        // shape rule above keeps in's innermost box extent a multiple of 4.
         a.tile[1] = 128 / tg;
-        a.tile[2] = 32 * (5 + 8);
-        a.tile[3] = (4 << 16) | (2 << 8) | 8;
-        return;
+        for (int boxes = 4; boxes >= 2; --boxes)
+            if (cjg::lt_tc_smem(v.m, v.d, 2, tg, 128 / tg, v.lout, boxes) <= 220 * 1024) {
+                a.tile[2] = 32 * (6 + 8);
+                a.tile[3] = (boxes << 20) | (5 << 16) | (2 << 8) | 8;
+                return;
+            }
+        if (cjg::lt_tc_smem(v.m, v.d, 2, tg, 128 / tg, v.lout) <= 220 * 1024) {
+            a.tile[2] = 32 * (5 + 8);
+            a.tile[3] = (4 << 16) | (2 << 8) | 8;
+            return;
+        }
     }
     if (a.dtype == CJ_F32) {
         // 64 columns, R 2, S 12, pipelined loads; threads = 32 * ceil(m / 12)
@@ -327,8 +352,8 @@ cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_
         const LtView v = lt_view(k, a);
         const int pipe = (a.tile[3] >> 20) & 0xf, mode = (a.tile[3] >> 16) & 0xf;
         const int r = (a.tile[3] >> 8) & 0xff, s = a.tile[3] & 0xff;
-        // mode 4 reuses the pipe field as the producers' prefetch depth (0 = automatic)
-        if ((mode == 4 ? pipe > 8 : pipe > 1) || (a.tile[3] >> 24))
+        // modes 4 and 5 reuse the pipe field: producers' prefetch depth (0 = automatic) / TMA ring depth
+        if ((mode == 4 || mode == 5 ? pipe > 8 : pipe > 1) || (a.tile[3] >> 24))
             return fail(CJ_ERR_INVALID_ARG, "LTimes tile flags 0x%x unknown", a.tile[3]);
         if (mode == 1 && (a.dtype != CJ_F64 || s != 8 || v.d % 4 || r < 1 || (tg * tz) % (8 * r) ||
                           (tg * tz / (8 * r)) * 32 != nt || nt > 1024))
@@ -349,12 +374,23 @@ cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_
             return fail(CJ_ERR_INVALID_ARG, "LTimes tcgen05 tile {%d,%d,%d,0x%x} invalid (f32, TG * TZ = 128, "
                         "2 <= stages <= 8, producer warps 2/4/8, threads = 32 * (5 + producer warps), m <= 128)",
                         a.tile[0], a.tile[1], a.tile[2], a.tile[3]);
-        if (mode > 4) return fail(CJ_ERR_INVALID_ARG, "LTimes compute mode %d unknown", mode);
+        if (mode == 5) {
+            const int inner = lt_axis_host(v.lin, 2);   // innermost axis of `in`: its TMA box extent
+            const int ib = inner == 0 ? 32 : inner == 1 ? tg : tz;
+            if (a.dtype != CJ_F32 || tg * tz != 128 || r < 2 || r > 8 || (s != 2 && s != 4 && s != 8) ||
+                nt != 32 * (6 + s) || v.m > 128 || pipe < 2 || ib % 4)
+                return fail(CJ_ERR_INVALID_ARG, "LTimes tcgen05+TMA tile {%d,%d,%d,0x%x} invalid (f32, TG * TZ = 128, "
+                            "2 <= stages <= 8, converter warps 2/4/8, threads = 32 * (6 + converter warps), "
+                            "2 <= TMA boxes <= 8, in's innermost box extent a multiple of 4, m <= 128)",
+                            a.tile[0], a.tile[1], a.tile[2], a.tile[3]);
+        }
+        if (mode > 5) return fail(CJ_ERR_INVALID_ARG, "LTimes compute mode %d unknown", mode);
         if (mode == 0 && (tg < 1 || tz < 1 || r < 1 || s < 1 || nt < 32 || nt > 1024 || (tg * tz) % r ||
                           (tg * tz / r) * ((v.m + s - 1) / s) != nt))
             return fail(CJ_ERR_INVALID_ARG, "LTimes tile {%d,%d,%d,%d} does not cover its block", a.tile[0],
                         a.tile[1], a.tile[2], a.tile[3]);
-        if ((mode == 4   ? cjg::lt_tc_smem(v.m, v.d, r, tg, tz, v.lout)
+        if ((mode == 5   ? cjg::lt_tc_smem(v.m, v.d, r, tg, tz, v.lout, pipe)
+             : mode == 4 ? cjg::lt_tc_smem(v.m, v.d, r, tg, tz, v.lout)
              : mode == 3 ? cjg::lt_direct_smem(v.m, v.d, tg * tz, esize(a.dtype), s)
                          : cjg::lt_smem(v.m, s, v.d, tg * tz, esize(a.dtype), pipe, mode)) > 220 * 1024)
             return fail(CJ_ERR_INVALID_ARG, "LTimes tile needs too much shared memory");
@@ -397,7 +433,13 @@ void spec_geometry(const cj_handle_s *h, Impl &s) {
         const LtView v = lt_view(h->kernel, a);
         const int mode = (a.tile[3] >> 16) & 0xf;
         s.threads = a.tile[2];
-        s.smem = mode == 4   ? (size_t)cjg::lt_tc_smem(v.m, v.d, (a.tile[3] >> 8) & 0xff, a.tile[0], a.tile[1], v.lout)
+        if (mode == 5) {   // and its mode-4 twin
+            s.threads2 = 32 * (5 + (a.tile[3] & 0xff));
+            s.smem2 = (size_t)cjg::lt_tc_smem(v.m, v.d, (a.tile[3] >> 8) & 0xff, a.tile[0], a.tile[1], v.lout);
+        }
+        s.smem = mode == 5   ? (size_t)cjg::lt_tc_smem(v.m, v.d, (a.tile[3] >> 8) & 0xff, a.tile[0], a.tile[1], v.lout,
+                                                       (a.tile[3] >> 20) & 0xf)
+                 : mode == 4 ? (size_t)cjg::lt_tc_smem(v.m, v.d, (a.tile[3] >> 8) & 0xff, a.tile[0], a.tile[1], v.lout)
                  : mode == 3 ? (size_t)cjg::lt_direct_smem(v.m, v.d, a.tile[0] * a.tile[1], es, a.tile[3] & 0xff)
                              : (size_t)cjg::lt_smem(v.m, a.tile[3] & 0xff, v.d, a.tile[0] * a.tile[1], es,
                                                     (a.tile[3] >> 20) & 1, mode);
@@ -406,6 +448,17 @@ void spec_geometry(const cj_handle_s *h, Impl &s) {
         s.threads = cjg::chain_threads(a.n, a.tile[0], a.tile[1]);
         s.smem = (size_t)cjg::chain_smem(a.n, a.tile[0], a.tile[1], es);
     }
+}
+
+// Mode 5 also compiles its mode-4 twin (register producers) into the module.
+std::string fallback_name_expression(const cj_handle_s *h) {
+    const cj_template_args &a = h->a;
+    if (!is_lt(h->kernel) || ((a.tile[3] >> 16) & 0xf) != 5) return "";
+    const LtView v = lt_view(h->kernel, a);
+    char buf[256];
+    snprintf(buf, sizeof buf, "cj::ltimes_tc<%d, %d, %d, %d, %d, %d, %d, %d, 0, 0, %d>", v.m, v.d, v.lin, v.lout,
+             a.tile[0], a.tile[1], (a.tile[3] >> 8) & 0xff, a.tile[3] & 0xff, v.acc);
+    return buf;
 }
 
 std::string name_expression(const cj_handle_s *h) {
@@ -419,9 +472,11 @@ std::string name_expression(const cj_handle_s *h) {
                  a.tile[1]);
     else {
         const LtView v = lt_view(h->kernel, a);
-        if (((a.tile[3] >> 16) & 0xf) == 4)
-            snprintf(buf, sizeof buf, "cj::ltimes_tc<%d, %d, %d, %d, %d, %d, %d, %d, %d, %d>", v.m, v.d, v.lin, v.lout,
-                     a.tile[0], a.tile[1], (a.tile[3] >> 8) & 0xff, a.tile[3] & 0xff, (a.tile[3] >> 20) & 0xf, v.acc);
+        const int mode = (a.tile[3] >> 16) & 0xf;
+        if (mode == 4 || mode == 5)   // mode 5: the pipe field is the TMA ring depth; mode 4: the prefetch depth
+            snprintf(buf, sizeof buf, "cj::ltimes_tc<%d, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d>", v.m, v.d, v.lin,
+                     v.lout, a.tile[0], a.tile[1], (a.tile[3] >> 8) & 0xff, a.tile[3] & 0xff,
+                     mode == 4 ? (a.tile[3] >> 20) & 0xf : 0, mode == 5 ? (a.tile[3] >> 20) & 0xf : 0, v.acc);
         else if (((a.tile[3] >> 16) & 0xf) == 3)
             snprintf(buf, sizeof buf, "cj::ltimes_direct<%s, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d>", ctype(a.dtype),
                      v.m, v.d, v.lin, v.lout, a.tile[0], a.tile[1], a.tile[2], (a.tile[3] >> 8) & 0xff,
@@ -445,11 +500,11 @@ constexpr int kNumNvrtcOpts = 4;
 
 struct CompileOut {
     nvrtcResult rc = NVRTC_SUCCESS;
-    std::string log, lowered;
+    std::string log, lowered, lowered2;
     std::vector<char> cubin;
 };
 
-CompileOut nvrtc_compile(const std::string &src, const char *name_expr) {
+CompileOut nvrtc_compile(const std::string &src, const char *name_expr, const char *name_expr2 = nullptr) {
     CompileOut out;
     const char *hdr_src[3] = {cj_emb_geometry_h, cj_emb_update_chain_cuh, cj_emb_ltimes_cuh};
     const char *hdr_name[3] = {"geometry.h", "update_chain.cuh", "ltimes.cuh"};
@@ -457,6 +512,7 @@ CompileOut nvrtc_compile(const std::string &src, const char *name_expr) {
     out.rc = nvrtcCreateProgram(&prog, src.c_str(), "cj_instantiation.cu", 3, hdr_src, hdr_name);
     if (out.rc != NVRTC_SUCCESS) return out;
     if (name_expr) nvrtcAddNameExpression(prog, name_expr);
+    if (name_expr2) nvrtcAddNameExpression(prog, name_expr2);
     out.rc = nvrtcCompileProgram(prog, kNumNvrtcOpts, kNvrtcOpts);
     size_t ls = 0;
     nvrtcGetProgramLogSize(prog, &ls);
@@ -469,6 +525,11 @@ CompileOut nvrtc_compile(const std::string &src, const char *name_expr) {
             const char *low = nullptr;
             out.rc = nvrtcGetLoweredName(prog, name_expr, &low);
             if (out.rc == NVRTC_SUCCESS && low) out.lowered = low;
+        }
+        if (out.rc == NVRTC_SUCCESS && name_expr2) {
+            const char *low = nullptr;
+            out.rc = nvrtcGetLoweredName(prog, name_expr2, &low);
+            if (out.rc == NVRTC_SUCCESS && low) out.lowered2 = low;
         }
         size_t cs = 0;
         if (out.rc == NVRTC_SUCCESS) out.rc = nvrtcGetCUBINSize(prog, &cs);
@@ -499,7 +560,7 @@ cj_status compile_handle(cj_handle_s *h) {
     std::string src = is_lt(h->kernel) ? "#include \"ltimes.cuh\"\n" : "#include \"update_chain.cuh\"\n";
     if (h->a.flags & CJ_FLAG_INJECT_COMPILE_ERROR)
         src += "namespace cj { __device__ int injected_failure = this_identifier_does_not_exist; }\n";
-    CompileOut c = nvrtc_compile(src, h->name_expr.c_str());
+    CompileOut c = nvrtc_compile(src, h->name_expr.c_str(), h->name_expr2.empty() ? nullptr : h->name_expr2.c_str());
     if (c.rc != NVRTC_SUCCESS) {
         h->error = std::string("NVRTC: ") + nvrtcGetErrorString(c.rc) + "\n" + c.log;
         t_err = h->error;
@@ -518,6 +579,14 @@ cj_status compile_handle(cj_handle_s *h) {
         if (r == CUDA_SUCCESS) r = drv.KernelGetFunction(&s.fn, kern);
         if (r == CUDA_SUCCESS && s.smem > 48 * 1024)
             r = drv.FuncSetAttribute(s.fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)s.smem);
+        if (r == CUDA_SUCCESS && !c.lowered2.empty()) {
+            CUkernel k2 = nullptr;
+            r = drv.LibraryGetKernel(&k2, h->lib, c.lowered2.c_str());
+            if (r == CUDA_SUCCESS) r = drv.KernelGetFunction(&s.fn2, k2);
+            if (r == CUDA_SUCCESS && s.smem2 > 48 * 1024)
+                r = drv.FuncSetAttribute(s.fn2, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)s.smem2);
+            if (r == CUDA_SUCCESS) s.blocks2 = occupancy(s.fn2, s.threads2, s.smem2);
+        }
         if (r != CUDA_SUCCESS) {
             h->error = std::string("module load: ") + cu_str(r);
             t_err = h->error;
@@ -711,7 +780,7 @@ CJ_API cj_status cj_init(const cj_config *cfg, int device) {
     if (w.rc != NVRTC_SUCCESS) return fail(CJ_ERR_COMPILE, "NVRTC warm-up failed: %s", w.log.c_str());
     G.stop = false;
     G.requests = G.hits = G.ok = G.failed = G.aot_hits = 0;
-    G.l_gen = G.l_aot = G.l_jit = 0;
+    G.l_gen = G.l_aot = G.l_jit = G.l_tma = G.l_tma_fb = 0;
     {
         std::lock_guard<std::mutex> lk(G.smu);
         G.compile_ms.clear();
@@ -767,6 +836,7 @@ CJ_API cj_status cj_specialize(cj_kernel_id k, const cj_template_args *req, cj_h
                     G.aot_hits++;
                 } else {
                     h->name_expr = name_expression(h);
+                    h->name_expr2 = fallback_name_expression(h);
                     h->state = ST_PENDING;
                     if (!G.cfg.sync) {
                         G.queue.push_back(h);
@@ -803,6 +873,30 @@ CJ_API cj_status cj_specialize_wait(cj_handle h, int timeout_ms) {
         return fail(CJ_ERR_TIMEOUT, "instantiation still compiling");
     if (h->state.load() == ST_FAILED) return fail(CJ_ERR_COMPILE, "%s", h->error.c_str());
     return CJ_OK;
+}
+
+// TMA tensor map of the (D, G, Z) tensor `in` in storage order lin, box (32
+// directions, tg, tz): dimensions innermost first, row strides in bytes, a
+// 128-byte swizzle when d is innermost (its 128-byte box rows), zero fill
+// outside the tensor.  False when no map is possible: `in` not 16-byte
+// aligned, or the innermost extent or box extent not a multiple of 4 floats
+// (row strides and box starts must be 16-byte multiples).
+bool lt_tensor_map(CUtensorMap *m, const void *in, int lin, long long D, long long G, long long Z, int tg, int tz) {
+    const long long ext[3] = {D, G, Z};
+    const int box[3] = {32, tg, tz};
+    const int a2 = lt_axis_host(lin, 2), a1 = lt_axis_host(lin, 1), a0 = lt_axis_host(lin, 0);
+    if (reinterpret_cast<uintptr_t>(in) % 16 || ext[a2] % 4 || box[a2] % 4) return false;
+    for (long long e : ext)
+        if (e > 0xFFFFFFFFll) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)ext[a2], (cuuint64_t)ext[a1], (cuuint64_t)ext[a0]};
+    const cuuint64_t strides[2] = {(cuuint64_t)ext[a2] * 4, (cuuint64_t)(ext[a2] * ext[a1]) * 4};
+    const cuuint32_t bx[3] = {(cuuint32_t)box[a2], (cuuint32_t)box[a1], (cuuint32_t)box[a0]};
+    const cuuint32_t es[3] = {1, 1, 1};
+    return drv.TensorMapEncodeTiled(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(in), dims, strides, bx, es,
+                                    CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                    a2 == 0 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 CJ_API cj_status cj_launch(cj_handle h, void *const *args, int64_t batch, void *cuda_stream) {
@@ -861,10 +955,32 @@ CJ_API cj_status cj_launch(cj_handle h, void *const *args, int64_t batch, void *
             r = drv.LaunchKernel(im->fn, grid, 1, 1, im->threads, 1, 1, (unsigned)im->smem, st, p, nullptr);
         } else {
             const long long ntiles = ((Gx + a.tile[0] - 1) / a.tile[0]) * ((Zx + a.tile[1] - 1) / a.tile[1]);
-            const long long cap = (long long)G.num_sms * im->blocks_per_sm;
-            const unsigned grid = (unsigned)std::min(ntiles, cap);
-            void *p[] = {&L, &in, &out, &Gx, &Zx};
-            r = drv.LaunchKernel(im->fn, grid, 1, 1, im->threads, 1, 1, (unsigned)im->smem, st, p, nullptr);
+            const int mode = (a.tile[3] >> 16) & 0xf;
+            if (mode == 4 || mode == 5) {
+                // tcgen05 kernels take a TMA tensor map of `in` (unused in mode 4); mode 5
+                // falls back to its mode-4 twin when `in` admits none
+                CUtensorMap map;
+                memset(&map, 0, sizeof map);
+                CUfunction fn = im->fn;
+                int threads = im->threads, bps = im->blocks_per_sm;
+                size_t smem = im->smem;
+                const bool tma = mode == 5 && lt_tensor_map(&map, in, v.lin, v.d, Gx, Zx, a.tile[0], a.tile[1]);
+                if (mode == 5 && !tma) {
+                    fn = im->fn2;
+                    threads = im->threads2;
+                    smem = im->smem2;
+                    bps = im->blocks2;
+                }
+                if (mode == 5) (tma ? G.l_tma : G.l_tma_fb)++;
+                const unsigned grid = (unsigned)std::min(ntiles, (long long)G.num_sms * bps);
+                void *p[] = {&L, &in, &out, &Gx, &Zx, &map};
+                r = drv.LaunchKernel(fn, grid, 1, 1, threads, 1, 1, (unsigned)smem, st, p, nullptr);
+            } else {
+                const long long cap = (long long)G.num_sms * im->blocks_per_sm;
+                const unsigned grid = (unsigned)std::min(ntiles, cap);
+                void *p[] = {&L, &in, &out, &Gx, &Zx};
+                r = drv.LaunchKernel(im->fn, grid, 1, 1, im->threads, 1, 1, (unsigned)im->smem, st, p, nullptr);
+            }
         }
     } else {
         void *items = *reinterpret_cast<void *const *>(args[0]);
@@ -901,6 +1017,8 @@ CJ_API cj_status cj_stats(cj_stats_t *out) {
     out->launches_generic = G.l_gen;
     out->launches_aot = G.l_aot;
     out->launches_jit = G.l_jit;
+    out->launches_tma = G.l_tma;
+    out->launches_tma_fallback = G.l_tma_fb;
     std::lock_guard<std::mutex> lk(G.smu);
     out->compile_ms_p50 = percentile(G.compile_ms, 0.5);
     out->compile_ms_p95 = percentile(G.compile_ms, 0.95);

@@ -97,9 +97,10 @@ CJ_HD constexpr long lt_direct_smem(int m, int d, int ct, int esize, int s = 0) 
 // 128 x 32 each), L's hi and lo parts, one out box, 1 KB alignment slack.
 CJ_HD constexpr int lt_tc_np(int m) { return (m + 15) / 16 * 16; }
 CJ_HD constexpr int lt_tc_dp(int d) { return (d + 31) / 32 * 32; }
-// Registers per thread for one block of 5 + nprod warps per SM: the warps are
-// spread over the SM's four sub-partitions of 16K registers each, so the
-// fullest one holds ceil(warps / 4) of them (multiples of 8, at most 255).
+// Registers per thread for one block of 5 + nprod warps per SM (nprod counts
+// the TMA warp in mode 5): the warps are spread over the SM's four
+// sub-partitions of 16K registers each, so the fullest one holds
+// ceil(warps / 4) of them (multiples of 8, at most 255).
 CJ_HD constexpr int lt_tc_maxreg(int nprod) {
     return 16384 / (32 * ((5 + nprod + 3) / 4)) / 8 * 8 > 255 ? 255 : 16384 / (32 * ((5 + nprod + 3) / 4)) / 8 * 8;
 }
@@ -120,8 +121,11 @@ CJ_HD constexpr long lt_tc_box(int m, int tg, int tz, int lout) {
                                   : (long)m * (128 / (lout == 1 || lout == 4 ? tg : tz)) *
                                         lt_tc_runp(lout == 1 || lout == 4 ? tg : tz);
 }
-CJ_HD constexpr long lt_tc_smem(int m, int d, int stages, int tg, int tz, int lout) {
-    return 1024L + (long)stages * 2 * LT_TC_A_BYTES + 2L * lt_tc_np(m) * lt_tc_dp(d) * 4 + lt_tc_box(m, tg, tz, lout) * 4;
+// rawst: TMA boxes of `in` (128 columns x 32 directions) ahead of the operand
+// ring (mode 5; 0 in mode 4).
+CJ_HD constexpr long lt_tc_smem(int m, int d, int stages, int tg, int tz, int lout, int rawst = 0) {
+    return 1024L + (long)rawst * 128 * 32 * 4 + (long)stages * 2 * LT_TC_A_BYTES + 2L * lt_tc_np(m) * lt_tc_dp(d) * 4 +
+           lt_tc_box(m, tg, tz, lout) * 4;
 }
 CJ_HD constexpr long lt_generic_smem(int m, int d, int cols, int esize) {
     return ((long)m * d + (long)d * cols) * esize;

@@ -541,6 +541,23 @@ __device__ __forceinline__ void lt_tc_mma_tf32(unsigned d_tmem, unsigned long lo
         "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
         : "memory");
 }
+// A TMA tensor map (the driver's 128-byte CUtensorMap), passed by value as a
+// __grid_constant__ kernel parameter.
+struct alignas(64) cj_tmap {
+    unsigned long long v[16];
+};
+__device__ __forceinline__ void lt_mbar_expect_tx(unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// One box of a 3-D tensor map (coordinates innermost first) into shared
+// memory; completion is signalled on `bar` as transaction bytes.
+__device__ __forceinline__ void lt_tma_load_3d(unsigned dst, const cj_tmap* map, int c0, int c1, int c2, unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
 // Columns c..c+15 of this thread's TMEM lane (warp w reads lanes 32(w%4)..).
 __device__ __forceinline__ void lt_tmem_ld16(unsigned taddr, float (&v)[16]) {
     unsigned r[16];
@@ -619,15 +636,18 @@ __device__ __forceinline__ void lt_tc_store_mbox(float* __restrict__ out, const 
     }
 }
 
-template <int M, int D, int LIN, int LOUT, int TG, int TZ, int STAGES, int NPROD, int PF_ = 0, int ACC = 0>
-__global__ void __maxnreg__(cjg::lt_tc_maxreg(NPROD))
-ltimes_tc(const float* __restrict__ L, const float* __restrict__ in, float* __restrict__ out, long long G,
-          long long Z) {
+template <int M, int D, int LIN, int LOUT, int TG, int TZ, int STAGES, int NPROD, int PF_ = 0, int RAWST = 0,
+          int ACC = 0>
+__global__ void __maxnreg__(cjg::lt_tc_maxreg(NPROD + (RAWST > 0)))
+ltimes_tc(const float* __restrict__ L, const float* __restrict__ in, float* __restrict__ out, long long G, long long Z,
+          const __grid_constant__ cj_tmap tmap) {
     constexpr int BM = 128, KB = 32;                 // tile columns, directions per stage
     constexpr int NP = cjg::lt_tc_np(M), DP = cjg::lt_tc_dp(D), NKB = DP / KB;
     constexpr int NPA = (NP + 31) / 32 * 32;         // TMEM columns per accumulator
     constexpr int TCOLS = 2 * NPA <= 32 ? 32 : 2 * NPA <= 64 ? 64 : 2 * NPA <= 128 ? 128 : 2 * NPA <= 256 ? 256 : 512;
-    constexpr int PT = 32 * NPROD;                   // producer threads
+    constexpr int PT = 32 * NPROD;                   // producer (converter) threads
+    constexpr int PW0 = RAWST > 0 ? 6 : 5;           // first producer warp (warp 5 issues TMA in mode 5)
+    constexpr unsigned RAW_BYTES = BM * KB * 4u;     // one TMA box of `in`
     constexpr int CH = BM * KB / 4 / PT;             // 16-byte chunks per producer thread per stage
     constexpr unsigned A_LBO = cjg::LT_TC_A_LBO, A_SBO = cjg::LT_TC_A_SBO;
     constexpr unsigned HALF = cjg::LT_TC_A_BYTES, STAGE_BYTES = 2u * HALF;
@@ -636,6 +656,10 @@ ltimes_tc(const float* __restrict__ L, const float* __restrict__ in, float* __re
     // kind::tf32, FP32 accumulator, both operands K-major, N = NP, M = 128
     constexpr unsigned IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(NP >> 3) << 17) | ((128u >> 4) << 24);
     static_assert(TG * TZ == BM && NP <= 256 && CH * PT * 4 == BM * KB && 8 % NPROD == 0, "tcgen05 LTimes tile");
+    // a TMA box starts on a 16-byte boundary: its innermost extent (and so
+    // every innermost coordinate, a multiple of it) is a multiple of 4 floats
+    static_assert(RAWST == 0 || (lt_axis(LIN, 2) == 0 ? KB : lt_axis(LIN, 2) == 1 ? TG : TZ) % 4 == 0,
+                  "TMA box: innermost extent must be a multiple of 4");
     constexpr bool G_FASTER = lt_pos(LIN, 1) > lt_pos(LIN, 2);
     constexpr bool OUT_G_FASTER = lt_pos(LOUT, 1) > lt_pos(LOUT, 2);
     constexpr bool D_FAST = lt_pos(LIN, 0) == 2;
@@ -660,14 +684,15 @@ ltimes_tc(const float* __restrict__ L, const float* __restrict__ in, float* __re
     constexpr int RIN = A1 == 1 ? TG : TZ, MP = cjg::lt_tc_mp(M);
 
     extern __shared__ __align__(16) unsigned char cj_smem[];
-    __shared__ __align__(8) unsigned long long bars[2 * STAGES + 6];
+    __shared__ __align__(8) unsigned long long bars[2 * STAGES + 6 + 2 * RAWST];
     __shared__ unsigned tmem_slot;
     __shared__ int abort_flag;
     unsigned char* base = cj_smem + ((1024u - (lt_smem_u32(cj_smem) & 1023u)) & 1023u);
-    unsigned char* ring = base;                                   // STAGES x [A_hi | A_lo]
-    float* sLhi = reinterpret_cast<float*>(base + STAGES * STAGE_BYTES);
-    float* sLlo = reinterpret_cast<float*>(base + STAGES * STAGE_BYTES + LBYTES);
-    float* sO = reinterpret_cast<float*>(base + STAGES * STAGE_BYTES + 2 * LBYTES);
+    unsigned char* raw = base;                                    // RAWST TMA boxes (mode 5)
+    unsigned char* ring = base + RAWST * RAW_BYTES;               // STAGES x [A_hi | A_lo]
+    float* sLhi = reinterpret_cast<float*>(ring + STAGES * STAGE_BYTES);
+    float* sLlo = reinterpret_cast<float*>(ring + STAGES * STAGE_BYTES + LBYTES);
+    float* sO = reinterpret_cast<float*>(ring + STAGES * STAGE_BYTES + 2 * LBYTES);
     const unsigned ring_u = lt_smem_u32(ring), lhi_u = lt_smem_u32(sLhi), llo_u = lt_smem_u32(sLlo);
     const unsigned bar_u = lt_smem_u32(bars);
     auto full_bar = [&](int s) { return bar_u + 8u * s; };
@@ -676,6 +701,8 @@ ltimes_tc(const float* __restrict__ L, const float* __restrict__ in, float* __re
     auto acce_bar = [&](int a) { return bar_u + 8u * (2 * STAGES + 2 + a); };
     const unsigned done_bar = bar_u + 8u * (2 * STAGES + 4);
     const unsigned epi_bar = bar_u + 8u * (2 * STAGES + 5);   // the 128 epilogue threads
+    auto rawf_bar = [&](int s) { return bar_u + 8u * (2 * STAGES + 6 + s); };
+    auto rawe_bar = [&](int s) { return bar_u + 8u * (2 * STAGES + 6 + RAWST + s); };
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
@@ -689,6 +716,10 @@ ltimes_tc(const float* __restrict__ L, const float* __restrict__ in, float* __re
         }
         lt_mbar_init(done_bar, 1);
         lt_mbar_init(epi_bar, 4 * 32);
+        for (int s = 0; s < RAWST; ++s) {
+            lt_mbar_init(rawf_bar(s), 1);
+            lt_mbar_init(rawe_bar(s), PT);
+        }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -736,7 +767,85 @@ ltimes_tc(const float* __restrict__ L, const float* __restrict__ in, float* __re
     auto row_g = [&](int r) { return G_FASTER ? r % TG : r / TZ; };
     auto row_z = [&](int r) { return G_FASTER ? r / TG : r % TZ; };
 
-    if (warp >= 5) {
+    const long long n_it = (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x * NKB;   // this block's stages
+    if (RAWST > 0 && warp >= PW0) {
+        // ---------------- converters (mode 5) ----------------
+        // Raw box i (in's storage order; 128-byte swizzled rows when d is
+        // fastest) -> tf32 hi/lo K-major operand stage.  d fastest: chunk q is
+        // (row q >> 3, direction quad q & 7), one 16-byte read; otherwise
+        // chunk q is (row q & 127, quad q >> 7), four 4-byte reads at
+        // consecutive rows across the warp.
+        constexpr int RS = RAWST > 0 ? RAWST : 1;
+        constexpr int AI = lt_axis(LIN, 2), AM = lt_axis(LIN, 1);
+        constexpr int BI = AI == 0 ? KB : AI == 1 ? TG : TZ, BMID = AM == 0 ? KB : AM == 1 ? TG : TZ;
+        constexpr int SB0 = AI == 0 ? 1 : AM == 0 ? BI : BI * BMID;   // raw element strides of d, g, z
+        constexpr int SB1 = AI == 1 ? 1 : AM == 1 ? BI : BI * BMID;
+        constexpr int SB2 = AI == 2 ? 1 : AM == 2 ? BI : BI * BMID;
+        const int pt = tid - PW0 * 32;
+        for (long long i = 0; i < n_it; ++i) {
+            const int rs = (int)(i % RS), s = (int)(i % STAGES);
+            if (!lt_mbar_wait(rawf_bar(rs), (unsigned)((i / RS) & 1), abort_v) ||
+                !lt_mbar_wait(empty_bar(s), (unsigned)((i / STAGES) & 1) ^ 1u, abort_v)) {
+                give_up();
+                break;
+            }
+            const unsigned char* rb = raw + rs * RAW_BYTES;
+            unsigned char* hi = ring + s * STAGE_BYTES;
+#pragma unroll
+            for (int j = 0; j < CH; ++j) {
+                const int q = j * PT + pt;
+                float4 c;
+                int r, kq;
+                if constexpr (D_FAST) {
+                    r = q >> 3;
+                    kq = q & 7;
+                    c = *reinterpret_cast<const float4*>(rb + r * 128 + ((kq ^ (r & 7)) << 4));
+                } else {
+                    r = q & 127;
+                    kq = q >> 7;
+                    const float* rf = reinterpret_cast<const float*>(rb) + row_g(r) * SB1 + row_z(r) * SB2;
+                    c = make_float4(rf[(4 * kq) * SB0], rf[(4 * kq + 1) * SB0], rf[(4 * kq + 2) * SB0],
+                                    rf[(4 * kq + 3) * SB0]);
+                }
+                uint4 h, l;
+                h.x = to_tf32(c.x); l.x = to_tf32(c.x - __uint_as_float(h.x));
+                h.y = to_tf32(c.y); l.y = to_tf32(c.y - __uint_as_float(h.y));
+                h.z = to_tf32(c.z); l.z = to_tf32(c.z - __uint_as_float(h.z));
+                h.w = to_tf32(c.w); l.w = to_tf32(c.w - __uint_as_float(h.w));
+                const unsigned off = kq * A_LBO + (r >> 3) * A_SBO + (r & 7) * 16u;
+                *reinterpret_cast<uint4*>(hi + off) = h;
+                *reinterpret_cast<uint4*>(hi + HALF + off) = l;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            lt_mbar_arrive(full_bar(s));
+            lt_mbar_arrive(rawe_bar(rs));
+        }
+    } else if (RAWST > 0 && warp == 5) {
+        // ---------------- TMA issue (mode 5, one lane) ----------------
+        if (lane == 0) {
+            constexpr int RS = RAWST > 0 ? RAWST : 1;
+            long long issued = 0;
+            for (long long i = 0; i < n_it; ++i, ++issued) {
+                const int rs = (int)(i % RS);
+                if (!lt_mbar_wait(rawe_bar(rs), (unsigned)((i / RS) & 1) ^ 1u, abort_v)) {
+                    give_up();
+                    break;
+                }
+                const unsigned t = blockIdx.x + (unsigned)(i / NKB) * gridDim.x;
+                const int c[3] = {(int)(i % NKB) * KB, (int)(t % ntg32) * TG, (int)(t / ntg32) * TZ};   // d, g, z
+                lt_mbar_expect_tx(rawf_bar(rs), RAW_BYTES);
+                lt_tma_load_3d(lt_smem_u32(raw + rs * RAW_BYTES), &tmap, c[lt_axis(LIN, 2)], c[lt_axis(LIN, 1)],
+                               c[lt_axis(LIN, 0)], rawf_bar(rs));
+            }
+            // every issued box lands before the block can exit: wait (bounded,
+            // not cut short by the abort flag) for the last load into each slot
+            for (int s = 0; s < RS; ++s) {
+                const long long cnt = issued > s ? (issued - s + RS - 1) / RS : 0;
+                if (cnt > 0 && !lt_mbar_wait(rawf_bar(s), (unsigned)((cnt - 1) & 1), nullptr)) give_up();
+            }
+        }
+        __syncwarp();
+    } else if (RAWST == 0 && warp >= PW0) {
         // ---------------- producers ----------------
         // Iteration i of this block is tile blockIdx.x + (i / NKB) * gridDim.x,
         // K block i % NKB.  Loads run PF - 1 iterations ahead in a register
@@ -745,8 +854,7 @@ ltimes_tc(const float* __restrict__ L, const float* __restrict__ in, float* __re
         // a free operand stage.  Tile indices fit 32 bits (G * Z < 2^38).
         constexpr int PF_AUTO = (cjg::lt_tc_maxreg(NPROD) - 64) / (4 * CH);
         constexpr int PF = PF_ > 0 ? PF_ : (PF_AUTO < 1 ? 1 : PF_AUTO > 8 ? 8 : PF_AUTO);
-        const int pt = tid - 5 * 32;
-        const long long n_it = (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x * NKB;
+        const int pt = tid - PW0 * 32;
         // Column-fastest `in`: warp wp loads direction quads kq = wp * UPW ..
         // (UPW = 8 / NPROD), lane l columns 4l..4l+3 (a float4 when the
         // fastest column axis has a multiple-of-4 extent, else scalars);

@@ -78,6 +78,13 @@ void ltimes_candidates(const cj_template_args &a, std::vector<std::array<int, 4>
         } else if (mode == 2) {
             if (ct % 16 || a.d % 8) return;
             nt = ct / 16 * 32;
+        } else if (mode == 5) {   // tcgen05 + TMA: r = operand stages, s = converter warps, pipe = TMA boxes
+            static const int order[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+            const int inner = order[a.layout_a][2];
+            if (ct != 128 || a.dtype != CJ_F32 || a.m > 128 || (inner == 0 ? 32 : inner == 1 ? tg : ct / tg) % 4) return;
+            if (cjg::lt_tc_smem(a.m, a.d, r, tg, ct / tg, a.layout_b, pipe) > 220 * 1024) return;
+            out.push_back({tg, ct / tg, 32 * (6 + s), (pipe << 20) | (5 << 16) | (r << 8) | s});
+            return;
         } else if (mode == 4) {   // tcgen05: r = stages, s = producer warps
             if (ct != 128 || a.dtype != CJ_F32 || a.m > 128) return;
             if (cjg::lt_tc_smem(a.m, a.d, r, tg, ct / tg, a.layout_b) > 220 * 1024) return;
@@ -106,11 +113,11 @@ void ltimes_candidates(const cj_template_args &a, std::vector<std::array<int, 4>
             push(tg, 64, 0, 1, 9);
             push(tg, 64, 0, 1, 12);
         } else {
-            push(tg, 128, 4, 2, 8);             // tcgen05 3xTF32: 2 operand stages, 8 producer warps
-            push(tg, 128, 4, 3, 8);             //                 3 operand stages
+            push(tg, 128, 5, 2, 8, 4);          // tcgen05 3xTF32 fed by TMA: 4 boxes, 2 operand stages
+            push(tg, 128, 4, 2, 8);             // tcgen05 3xTF32, register producers: 2 operand stages
+            push(tg, 128, 4, 3, 8);             //                                     3 operand stages
             push(tg, 64, 2, 1, 8, 1);           // mma.sync 3xTF32
             push(tg, 64, 0, 2, 12, 1);          // FMA, cp.async double buffer
-            push(tg, 128, 0, 2, 12, 1);
             push(tg, 256, 3, 2, 0, 0);          // direct loads, all moments per thread
             if (a.m > 12) push(tg, 128, 3, 2, 12, 0);   // direct loads, 12 moments per thread
             push(tg, 128, 0, 4, 12, 0);         // unpipelined baseline

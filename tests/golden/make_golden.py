@@ -29,6 +29,11 @@ REQUESTS = [
     (K.K_LTIMES, K.F32, 0, 5, 1, 36, 96, (0, 0, 0, 0), 0),
     (K.K_LTIMES, K.F64, 0, 2, 4, 36, 96, (0, 0, 0, 0), K.FLAG_GENERIC),
     (K.K_LTIMES, K.F32, 0, 1, 1, 36, 96, (32, 4, 192, (2 << 8) | 12), 0),
+    (K.K_LTIMES, K.F32, 0, 0, 1, 64, 128, (0, 0, 0, 0), 0),             # tensor cores: fewer TMA boxes fit
+    (K.K_LTIMES, K.F32, 0, 4, 3, 64, 128, (0, 0, 0, 0), 0),
+    (K.K_LTIMES, K.F32, 0, 2, 4, 48, 100, (0, 0, 0, 0), 0),
+    (K.K_LPLUSTIMES, K.F32, 0, 1, 2, 36, 96, (0, 0, 0, 0), 0),          # swapped: 96 rows, K = 36
+    (K.K_LPLUSTIMES, K.F32, 0, 0, 0, 64, 128, (0, 0, 0, 0), 0),         # 128 rows
     (K.K_UPDATE_CHAIN_GROUPED, K.F64, 20, 0, 0, 0, 0, (0, 0, 0, 0), 0),
     (K.K_UPDATE_CHAIN_GROUPED, K.F32, 3, 1, 0, 0, 0, (0, 0, 0, 0), 0),  # layout forced 0
     (K.K_UPDATE_CHAIN, K.F64, 8, 0, 0, 0, 0, (0, 0, 0, 0), K.FLAG_INJECT_COMPILE_ERROR),

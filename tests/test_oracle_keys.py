@@ -14,10 +14,10 @@ def test_hand_assembled_chain_key():
 
 def test_hand_assembled_ltimes_key():
     # kernel 2, f32, in GZD(3), out ZGD(5), m=36, d=96, default tile
-    # (1, 128, 416, (4 << 16) | (2 << 8) | 8): tensor-core mode 4, 128 columns,
-    # 2 operand stages, 8 producer warps (416 threads)
+    # (1, 128, 448, (4 << 20) | (5 << 16) | (2 << 8) | 8): tensor cores fed by
+    # TMA (mode 5), 4 TMA boxes, 2 operand stages, 8 converter warps (448 threads)
     expect = bytes.fromhex("0200" "01" "03" "05" "00" "0000" "2400" "6000"
-                           "01000000" "80000000" "a0010000" "08020400" "00000000")
+                           "01000000" "80000000" "c0010000" "08024500" "00000000")
     assert K.canonical_key(K.K_LTIMES, K.F32, layout_a=3, layout_b=5, m=36, d=96) == expect
 
 

@@ -326,6 +326,83 @@ def test_ltimes_f32_tcgen05_shapes(M, D, G, Z, lin, lout, stages, nprod):
     assert h.wait_timeouts() == 0
 
 
+def tma_tile(lin, lout, boxes=4, stages=2, nconv=8, tg=None):
+    """tcgen05 tile fed by TMA (mode 5)."""
+    t = tc_tile(lin, lout, stages, nconv, tg)
+    return (t[0], t[1], 32 * (6 + nconv), (boxes << 20) | (5 << 16) | (stages << 8) | nconv)
+
+
+@pytest.fixture(scope="module")
+def lt_aligned():
+    """G and Z multiples of 4 (TMA-compatible for every order), Z ragged against every box."""
+    M, D, G, Z = 36, 96, 8, 200
+    L, x = synth.ltimes_inputs_np(synth.SEED_LTIMES, M, D, G, Z)
+    ref = oracle.ltimes(L, x.ravel(), G, Z, 0, 0, nthreads=4).reshape(M, G, Z)
+    return L, x, ref
+
+
+@pytest.mark.parametrize("lin", range(6))
+@pytest.mark.parametrize("lout", range(6))
+def test_ltimes_f32_tma(lt_aligned, lin, lout):
+    """Mode 5: TMA boxes of `in` -> converter warps -> tcgen05 3xTF32; every
+    storage-order pair runs on the TMA path."""
+    L, x, ref = lt_aligned
+    h = cj.specialize(cj.K_LTIMES, cj.F32, layout_a=lin, layout_b=lout, m=36, d=96, tile=tma_tile(lin, lout))
+    before = cj.stats()
+    assert relF(run_ltimes(h, L, x, lin, lout, cj.F32), ref) <= TOL32
+    after = cj.stats()
+    assert after["launches_tma"] == before["launches_tma"] + 1
+    assert after["launches_tma_fallback"] == before["launches_tma_fallback"]
+    assert h.wait_timeouts() == 0
+
+
+@pytest.mark.parametrize("lin,lout", [(0, 0), (1, 4), (4, 2), (3, 3), (5, 1), (2, 5)])
+def test_ltimes_f32_tma_fallback(lt_small, lin, lout):
+    """G = 5, Z = 37 admit no tensor map when g or z is innermost: the launch
+    runs the mode-4 twin compiled into the same module; d innermost (D = 96)
+    still runs on TMA."""
+    L, x, ref = lt_small
+    h = cj.specialize(cj.K_LTIMES, cj.F32, layout_a=lin, layout_b=lout, m=36, d=96, tile=tma_tile(lin, lout))
+    before = cj.stats()
+    assert relF(run_ltimes(h, L, x, lin, lout, cj.F32), ref) <= TOL32
+    after = cj.stats()
+    d_inner = lin in (3, 5)
+    assert after["launches_tma"] - before["launches_tma"] == (1 if d_inner else 0)
+    assert after["launches_tma_fallback"] - before["launches_tma_fallback"] == (0 if d_inner else 1)
+    assert h.wait_timeouts() == 0
+
+
+@pytest.mark.parametrize("lin,lout,tg", [(0, 0, None), (3, 5, None), (4, 1, None), (1, 4, 8), (2, 3, 1), (5, 0, 8)])
+def test_ltimes_f32_tma_many_tiles_per_block(lin, lout, tg):
+    M, D, G, Z = 36, 96, 32, 8192
+    L, x = synth.ltimes_inputs_np(synth.SEED_LTIMES, M, D, G, Z)
+    ref = oracle.ltimes(L, x.ravel(), G, Z, 0, 0, nthreads=8).reshape(M, G, Z)
+    h = cj.specialize(cj.K_LTIMES, cj.F32, layout_a=lin, layout_b=lout, m=M, d=D, tile=tma_tile(lin, lout, tg=tg))
+    before = cj.stats()["launches_tma"]
+    out = run_ltimes(h, L, x, lin, lout, cj.F32)
+    assert cj.stats()["launches_tma"] == before + 1
+    assert relF(out, ref) <= TOL32
+    assert h.wait_timeouts() == 0
+
+
+@pytest.mark.parametrize("M,D,G,Z,lin,lout,boxes,stages,nconv", [
+    (37, 12, 4, 52, 0, 0, 4, 2, 8),     # one K block, directions 12..31 from TMA zero fill
+    (9, 8, 4, 36, 1, 4, 2, 2, 2),       # g innermost, 32-wide g box
+    (4, 100, 4, 300, 2, 3, 3, 3, 4),    # four K blocks, ragged; m-fastest out
+    (64, 128, 3, 70, 3, 3, 2, 2, 8),    # d innermost (128-byte swizzle), ragged G and Z
+    (16, 40, 12, 24, 5, 2, 2, 2, 8),    # d innermost, D not a multiple of 32
+])
+def test_ltimes_f32_tma_shapes(M, D, G, Z, lin, lout, boxes, stages, nconv):
+    L, x = synth.ltimes_inputs_np(synth.SEED_LTIMES, M, D, G, Z)
+    ref = oracle.ltimes(L, x.ravel(), G, Z, 0, 0).reshape(M, G, Z)
+    h = cj.specialize(cj.K_LTIMES, cj.F32, layout_a=lin, layout_b=lout, m=M, d=D,
+                      tile=tma_tile(lin, lout, boxes, stages, nconv))
+    before = cj.stats()["launches_tma"]
+    assert relF(run_ltimes(h, L, x, lin, lout, cj.F32), ref) <= TOL32
+    assert cj.stats()["launches_tma"] == before + 1
+    assert h.wait_timeouts() == 0
+
+
 @pytest.mark.parametrize("lin,lout", [(0, 0), (1, 3), (3, 5), (5, 2)])
 @pytest.mark.parametrize("dt", [cj.F64, cj.F32])
 def test_ltimes_generic(lt_small, lin, lout, dt):
@@ -481,7 +558,8 @@ def test_lplustimes_accumulates(lin, lout, dt, generic):
 
 
 @pytest.mark.parametrize("lin,lout", [(0, 0), (3, 1), (4, 5), (2, 3), (1, 4)])
-def test_lplustimes_tcgen05(lin, lout):
+@pytest.mark.parametrize("mode5", [False, True])
+def test_lplustimes_tcgen05(lin, lout, mode5):
     """LPlusTimes on mode 4 (the swapped problem: 96 output rows, K = 36)."""
     M, D, G, Z = 36, 96, 5, 41
     Lp = synth.uniform_np(0xC1A6, 0, D * M).reshape(D, M)
@@ -490,7 +568,8 @@ def test_lplustimes_tcgen05(lin, lout):
     ref_phys = oracle.lplustimes(Lp, synth.to_layout(y, lout).ravel(), synth.to_layout(base, lin).ravel(), G, Z,
                                  lin, lout)
     h = cj.specialize(cj.K_LPLUSTIMES, cj.F32, layout_a=lin, layout_b=lout, m=M, d=D,
-                      tile=tc_tile(lout, lin, stages=3, nprod=4))
+                      tile=tma_tile(lout, lin, boxes=2, stages=2, nconv=4) if mode5
+                      else tc_tile(lout, lin, stages=3, nprod=4))
     Lt = torch.from_numpy(Lp).to("cuda", torch.float32)
     yt = torch.from_numpy(synth.to_layout(y, lout).ravel()).to("cuda", torch.float32)
     xt = torch.from_numpy(synth.to_layout(base, lin).ravel()).to("cuda", torch.float32)
