@@ -76,6 +76,11 @@ typedef enum {
 #define CJ_FLAG_GENERIC 0x1u      /* use the generic runtime-N kernel, never compile */
 #define CJ_FLAG_NO_AOT 0x2u       /* JIT compile even where an AoT specialization exists */
 #define CJ_FLAG_INJECT_COMPILE_ERROR 0x100u  /* test hook: submit a template that fails to compile */
+/* test hook (LTimes tile modes 4 and 5 only): compile the tensor-core kernel
+ * with producers that never signal a filled operand stage, so that every
+ * block's bounded wait expires (about a second); blocks then stop and
+ * cj_handle_wait_timeouts reports them, and `out` is left incomplete */
+#define CJ_FLAG_INJECT_WAIT_TIMEOUT 0x200u
 
 /* Config flags (cj_config.flags). */
 #define CJ_CFG_COMPILE_ONLY 0x1u  /* no device: compile to CUBIN, never load or launch */

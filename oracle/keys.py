@@ -51,7 +51,8 @@ F64, F32, BF16 = 0, 1, 2
 FLAG_GENERIC = 1
 FLAG_NO_AOT = 2
 FLAG_INJECT_COMPILE_ERROR = 0x100
-KEY_FLAGS = FLAG_GENERIC | FLAG_NO_AOT | FLAG_INJECT_COMPILE_ERROR
+FLAG_INJECT_WAIT_TIMEOUT = 0x200
+KEY_FLAGS = FLAG_GENERIC | FLAG_NO_AOT | FLAG_INJECT_COMPILE_ERROR | FLAG_INJECT_WAIT_TIMEOUT
 
 AOT_SIZES = (4, 8, 16, 32)
 

@@ -17,7 +17,7 @@ CJ_ERR_TIMEOUT, CJ_ERR_PENDING = 8, 9
 
 K_UPDATE_CHAIN, K_LTIMES, K_UPDATE_CHAIN_GROUPED, K_LPLUSTIMES = 1, 2, 3, 4
 F64, F32, BF16 = 0, 1, 2
-FLAG_GENERIC, FLAG_NO_AOT, FLAG_INJECT_COMPILE_ERROR = 0x1, 0x2, 0x100
+FLAG_GENERIC, FLAG_NO_AOT, FLAG_INJECT_COMPILE_ERROR, FLAG_INJECT_WAIT_TIMEOUT = 0x1, 0x2, 0x100, 0x200
 CFG_COMPILE_ONLY = 0x1
 VARIANT_NAMES = ("generic", "aot", "jit")
 

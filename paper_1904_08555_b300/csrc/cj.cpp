@@ -110,7 +110,8 @@ const char *cu_str(CUresult r) {
 // ---------------------------------------------------------------------------
 enum { ST_PENDING = 0, ST_READY = 1, ST_FAILED = 2, ST_GENERIC_ONLY = 3 };
 enum { V_GENERIC = 0, V_AOT = 1, V_JIT = 2 };
-constexpr uint32_t kKeyFlags = CJ_FLAG_GENERIC | CJ_FLAG_NO_AOT | CJ_FLAG_INJECT_COMPILE_ERROR;
+constexpr uint32_t kKeyFlags =
+    CJ_FLAG_GENERIC | CJ_FLAG_NO_AOT | CJ_FLAG_INJECT_COMPILE_ERROR | CJ_FLAG_INJECT_WAIT_TIMEOUT;
 
 // Everything a launch needs; immutable once published through Handle::impl.
 struct Impl {
@@ -304,6 +305,8 @@ cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_
         if (a.dtype == CJ_BF16 && a.n < 16) return fail(CJ_ERR_INVALID_ARG, "bf16 needs n >= 16");
         a.m = a.d = a.layout_b = 0;
     }
+    if ((a.flags & CJ_FLAG_INJECT_WAIT_TIMEOUT) && (!is_lt(k) || (a.flags & CJ_FLAG_GENERIC)))
+        return fail(CJ_ERR_INVALID_ARG, "the wait-timeout hook applies to specialized LTimes kernels only");
     if (a.flags & CJ_FLAG_GENERIC) {
         for (int &t : a.tile) t = 0;
         return CJ_OK;
@@ -385,6 +388,8 @@ cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_
                             a.tile[0], a.tile[1], a.tile[2], a.tile[3]);
         }
         if (mode > 5) return fail(CJ_ERR_INVALID_ARG, "LTimes compute mode %d unknown", mode);
+        if ((a.flags & CJ_FLAG_INJECT_WAIT_TIMEOUT) && mode != 4 && mode != 5)
+            return fail(CJ_ERR_INVALID_ARG, "the wait-timeout hook applies to tile modes 4 and 5 only");
         if (mode == 0 && (tg < 1 || tz < 1 || r < 1 || s < 1 || nt < 32 || nt > 1024 || (tg * tz) % r ||
                           (tg * tz / r) * ((v.m + s - 1) / s) != nt))
             return fail(CJ_ERR_INVALID_ARG, "LTimes tile {%d,%d,%d,%d} does not cover its block", a.tile[0],
@@ -456,8 +461,9 @@ std::string fallback_name_expression(const cj_handle_s *h) {
     if (!is_lt(h->kernel) || ((a.tile[3] >> 16) & 0xf) != 5) return "";
     const LtView v = lt_view(h->kernel, a);
     char buf[256];
-    snprintf(buf, sizeof buf, "cj::ltimes_tc<%d, %d, %d, %d, %d, %d, %d, %d, 0, 0, %d>", v.m, v.d, v.lin, v.lout,
-             a.tile[0], a.tile[1], (a.tile[3] >> 8) & 0xff, a.tile[3] & 0xff, v.acc);
+    snprintf(buf, sizeof buf, "cj::ltimes_tc<%d, %d, %d, %d, %d, %d, %d, %d, 0, 0, %d, %d>", v.m, v.d, v.lin, v.lout,
+             a.tile[0], a.tile[1], (a.tile[3] >> 8) & 0xff, a.tile[3] & 0xff, v.acc,
+             (a.flags & CJ_FLAG_INJECT_WAIT_TIMEOUT) ? 1 : 0);
     return buf;
 }
 
@@ -474,9 +480,10 @@ std::string name_expression(const cj_handle_s *h) {
         const LtView v = lt_view(h->kernel, a);
         const int mode = (a.tile[3] >> 16) & 0xf;
         if (mode == 4 || mode == 5)   // mode 5: the pipe field is the TMA ring depth; mode 4: the prefetch depth
-            snprintf(buf, sizeof buf, "cj::ltimes_tc<%d, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d>", v.m, v.d, v.lin,
-                     v.lout, a.tile[0], a.tile[1], (a.tile[3] >> 8) & 0xff, a.tile[3] & 0xff,
-                     mode == 4 ? (a.tile[3] >> 20) & 0xf : 0, mode == 5 ? (a.tile[3] >> 20) & 0xf : 0, v.acc);
+            snprintf(buf, sizeof buf, "cj::ltimes_tc<%d, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d>", v.m, v.d,
+                     v.lin, v.lout, a.tile[0], a.tile[1], (a.tile[3] >> 8) & 0xff, a.tile[3] & 0xff,
+                     mode == 4 ? (a.tile[3] >> 20) & 0xf : 0, mode == 5 ? (a.tile[3] >> 20) & 0xf : 0, v.acc,
+                     (a.flags & CJ_FLAG_INJECT_WAIT_TIMEOUT) ? 1 : 0);
         else if (((a.tile[3] >> 16) & 0xf) == 3)
             snprintf(buf, sizeof buf, "cj::ltimes_direct<%s, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d>", ctype(a.dtype),
                      v.m, v.d, v.lin, v.lout, a.tile[0], a.tile[1], a.tile[2], (a.tile[3] >> 8) & 0xff,

@@ -637,7 +637,7 @@ __device__ __forceinline__ void lt_tc_store_mbox(float* __restrict__ out, const 
 }
 
 template <int M, int D, int LIN, int LOUT, int TG, int TZ, int STAGES, int NPROD, int PF_ = 0, int RAWST = 0,
-          int ACC = 0>
+          int ACC = 0, int INJECT_TIMEOUT = 0>
 __global__ void __maxnreg__(cjg::lt_tc_maxreg(NPROD + (RAWST > 0)))
 ltimes_tc(const float* __restrict__ L, const float* __restrict__ in, float* __restrict__ out, long long G, long long Z,
           const __grid_constant__ cj_tmap tmap) {
@@ -817,7 +817,7 @@ ltimes_tc(const float* __restrict__ L, const float* __restrict__ in, float* __re
                 *reinterpret_cast<uint4*>(hi + HALF + off) = l;
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            lt_mbar_arrive(full_bar(s));
+            if (!INJECT_TIMEOUT) lt_mbar_arrive(full_bar(s));   // the hook: never signal a filled stage
             lt_mbar_arrive(rawe_bar(rs));
         }
     } else if (RAWST > 0 && warp == 5) {
@@ -962,7 +962,7 @@ ltimes_tc(const float* __restrict__ L, const float* __restrict__ in, float* __re
                         }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                lt_mbar_arrive(full_bar(s));
+                if (!INJECT_TIMEOUT) lt_mbar_arrive(full_bar(s));
             }
         }
     } else if (warp == 4) {

@@ -101,6 +101,9 @@ def test_aot_sizes_are_not_compiled(compile_only_sync):
     dict(kernel=cj.K_LTIMES, dtype=cj.F32, m=36, d=96, tile=(1, 128, 64, (3 << 16) | (2 << 8) | 36)),
     dict(kernel=cj.K_LTIMES, dtype=cj.F32, m=36, d=96, tile=(1, 128, 128, (3 << 16) | (2 << 8) | 12)),
     dict(kernel=cj.K_LTIMES, dtype=cj.F64, m=36, d=96, tile=(1, 128, 192, (3 << 16) | (2 << 8) | 12)),
+    dict(kernel=cj.K_UPDATE_CHAIN, dtype=cj.F64, n=8, flags=0x200),
+    dict(kernel=cj.K_LTIMES, dtype=cj.F32, m=36, d=96, flags=0x200 | 0x1),
+    dict(kernel=cj.K_LTIMES, dtype=cj.F32, m=36, d=96, tile=(1, 64, 96, (1 << 20) | (2 << 8) | 12), flags=0x200),
     dict(kernel=9, dtype=cj.F64, n=4),
 ])
 def test_invalid_arguments(compile_only_sync, kw):
@@ -233,3 +236,13 @@ def test_lplustimes_keys_and_compiles(compile_only_sync):
     assert h.variant == "jit"
     assert cj.specialize(cj.K_LPLUSTIMES, cj.F32, layout_a=0, layout_b=5, m=36, d=96).variant == "jit"
     assert len(cj.candidates(cj.K_LPLUSTIMES, cj.F32, layout_a=0, layout_b=5, m=36, d=96)) >= 4
+
+
+def test_wait_timeout_hook_is_part_of_the_key(compile_only_sync):
+    """The hook compiles a different kernel (its own key) and only for the
+    tensor-core tiles; the default FP32 LTimes tile is one."""
+    plain = cj.specialize(cj.K_LTIMES, cj.F32, m=36, d=96)
+    hooked = cj.specialize(cj.K_LTIMES, cj.F32, m=36, d=96, flags=cj.FLAG_INJECT_WAIT_TIMEOUT)
+    kp, kh = bytes.fromhex(plain.key_hex), bytes.fromhex(hooked.key_hex)
+    assert kp[:28] == kh[:28] and kh[28:] == (0x200).to_bytes(4, "little") and kp[28:] == bytes(4)
+    assert hooked.variant == "jit"
