@@ -120,21 +120,41 @@ typedef struct {
  *     else {1, max(1, 128 / n)}; bf16 -> {3, max(1, 128 / n16)} with n16 = n
  *     rounded up to a multiple of 16 (mapping 3: one warp per 16 rows,
  *     bf16 operands, fp32 accumulate and state).
- *   LTimes: {TG, TZ, threads, (PIPE << 20) | (MODE << 16) | (R << 8) | S}: a block stages a
- *     TG x TZ box of (g, z) columns with all d in shared memory.  MODE 0: each
- *     thread accumulates R columns x S moments on the FMA pipe (the last
- *     moment group may be partial), threads = (TG * TZ / R) * ceil(m / S).
+ *   LTimes: {TG, TZ, threads, (PIPE << 20) | (MODE << 16) | (R << 8) | S}: a
+ *     block covers TG x TZ (g, z) columns at a time (a persistent grid).
+ *     MODE 0: the box with all d is staged in shared memory and each thread
+ *     accumulates R columns x S moments on the FMA pipe (the last moment
+ *     group may be partial), threads = (TG * TZ / R) * ceil(m / S).
  *     MODE 1 (f64, S = 8, d a multiple of 4): FP64 tensor cores (mma.sync
  *     m8n8k4), each warp 8R columns x all moments, threads =
- *     32 * TG * TZ / (8 R).  PIPE 1: two tile buffers, the next tile loaded with
- *     cp.async while the current one is contracted.  Default: CT = 64 columns;
- *     call orders 1 and 4 "g-fast" (g is the fastest axis) and 0 and 2
- *     "z-fast"; TG = 1 if neither in nor out is g-fast, 8 if one is g-fast
- *     and the other z-fast, 32 otherwise; TZ = CT / TG;
+ *     32 * TG * TZ / (8 R).
+ *     MODE 2 (f32, R = 1, S = 8, d a multiple of 8): 3xTF32 on mma.sync
+ *     m16n8k8, threads = 32 * TG * TZ / 16.
+ *     PIPE 1 (modes 0-2): two tile buffers, the next tile loaded with cp.async
+ *     while the current one is contracted.
+ *     MODE 3 (f32, no PIPE, R <= 4): columns read straight from global memory,
+ *     S moments per thread (S = 0: all, else a multiple of 4 below m),
+ *     threads = TG * TZ / R * ceil(m / S).
+ *     MODE 4 (f32, TG * TZ = 128, m <= 128 after the LPlusTimes swap): 3xTF32
+ *     on tcgen05.mma kind::tf32 with the accumulator in tensor memory; R =
+ *     operand stages (2..8), S = producer warps (2, 4 or 8), threads =
+ *     32 * (5 + S), PIPE = the producers' register prefetch depth (0 auto).
+ *     MODE 5: as mode 4 with `in` brought in by TMA (PIPE = boxes in flight,
+ *     2..8; S = converter warps, threads = 32 * (6 + S); the box extent of
+ *     in's innermost axis must be a multiple of 4).  A launch whose `in`
+ *     admits no TMA tensor map (innermost extent not a multiple of 4, or not
+ *     16-byte aligned) runs the mode-4 kernel of the same tile instead
+ *     (cj_stats counts both).
+ *     Default: call orders 1 and 4 "g-fast" (g is the fastest axis) and 0
+ *     and 2 "z-fast"; TG = 1 if neither in nor out is g-fast, 8 if one is
+ *     g-fast and the other z-fast, 32 otherwise.  f32 with m <= 128: TZ =
+ *     128 / TG, MODE 5 with R 2, S 8 (448 threads) and the largest PIPE in
+ *     {4, 3, 2} that fits 220 KiB of shared memory, else MODE 4 with R 2, S 8
+ *     (416 threads) if that fits.  Otherwise CT = 64 columns, TZ = CT / TG;
  *     f64: R 1, S 9, threads 64 * ceil(m / 9) (m = 36: 256); f32: PIPE 1,
- *     R 2, S 12, threads 32 * ceil(m / 12) (m = 36: 96).  The FP64
- *     tensor-core mappings are autotuner candidates, not defaults: on B300
- *     mma.sync f64 issues on the FP64 pipe and is not faster than DFMA.
+ *     R 2, S 12, threads 32 * ceil(m / 12).  The FP64 tensor-core mappings
+ *     are autotuner candidates, not defaults: on B300 mma.sync f64 issues on
+ *     the FP64 pipe and is not faster than DFMA.
  */
 typedef struct {
     int32_t dtype, n, layout_a, layout_b, m, d;
@@ -196,8 +216,11 @@ cj_status cj_specialize_wait(cj_handle h, int timeout_ms);
  *     that must be 0 at launch (the kernel increments it once per chunk of
  *     items it hands out and once more per block).
  * T is double for CJ_F64, float for CJ_F32 and CJ_BF16 (fp32 state).
+ * LTimes / LPlusTimes tiles of modes 3-5 (the f32 defaults) move in and out
+ * in 16-byte vectors: both must be 16-byte aligned.
  * Never blocks on compilation.  Returns CJ_ERR_INVALID_ARG without launching
- * for null args or negative batch; CJ_ERR_CUDA if the launch failed. */
+ * for null args, negative batch or misaligned mode 3-5 tensors; CJ_ERR_CUDA if
+ * the launch failed. */
 cj_status cj_launch(cj_handle h, void *const *args, int64_t batch, void *cuda_stream);
 
 /* Counters since cj_init; compile times are NVRTC + module load wall time. */

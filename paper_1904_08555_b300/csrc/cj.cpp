@@ -911,6 +911,13 @@ CJ_API cj_status cj_launch(cj_handle h, void *const *args, int64_t batch, void *
     if (!h || !args || batch < 0) return fail(CJ_ERR_INVALID_ARG, "null handle/args or negative batch");
     for (int i = 0; i < (is_lt(h->kernel) ? 5 : h->kernel == CJ_K_UPDATE_CHAIN ? 3 : 4); ++i)
         if (!args[i]) return fail(CJ_ERR_INVALID_ARG, "argument %d is null", i);
+    if (is_lt(h->kernel) && !(h->a.flags & CJ_FLAG_GENERIC) && ((h->a.tile[3] >> 16) & 0xf) >= 3) {
+        // tile modes 3-5 move `in` and `out` in 16-byte vectors
+        const uintptr_t in = reinterpret_cast<uintptr_t>(*reinterpret_cast<void *const *>(args[1]));
+        const uintptr_t out = reinterpret_cast<uintptr_t>(*reinterpret_cast<void *const *>(args[2]));
+        if ((in | out) & 15)
+            return fail(CJ_ERR_INVALID_ARG, "tile modes 3-5 need 16-byte aligned in and out tensors");
+    }
     if (G.compile_only) return fail(CJ_ERR_NO_DEVICE, "library initialised in compile-only mode");
     const Impl *im = h->impl.load(std::memory_order_acquire);
     const cj_template_args &a = h->a;

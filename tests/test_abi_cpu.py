@@ -246,3 +246,17 @@ def test_wait_timeout_hook_is_part_of_the_key(compile_only_sync):
     kp, kh = bytes.fromhex(plain.key_hex), bytes.fromhex(hooked.key_hex)
     assert kp[:28] == kh[:28] and kh[28:] == (0x200).to_bytes(4, "little") and kp[28:] == bytes(4)
     assert hooked.variant == "jit"
+
+
+def test_vectorised_ltimes_tiles_reject_misaligned_tensors(compile_only_sync):
+    """Tile modes 3-5 move in/out in 16-byte vectors: a misaligned pointer is
+    refused before any device work (pointer values only, nothing is read)."""
+    h = cj.specialize(cj.K_LTIMES, cj.F32, m=36, d=96)           # default f32 tile: mode 5
+    assert (h.info()[0] and ((int.from_bytes(bytes.fromhex(h.key_hex)[24:28], "little") >> 16) & 0xF) == 5)
+    for in_ptr, out_ptr in ((1 << 20) + 4, 1 << 21), ((1 << 20), (1 << 21) + 8):
+        with pytest.raises(cj.CJError) as e:
+            cj.launch_ltimes(h, 1 << 19, in_ptr, out_ptr, 8, 64)
+        assert e.value.status == cj.CJ_ERR_INVALID_ARG and "16-byte" in cj.last_error()
+    with pytest.raises(cj.CJError) as e:                         # aligned: reaches the device check
+        cj.launch_ltimes(h, 1 << 19, 1 << 20, 1 << 21, 8, 64)
+    assert e.value.status == cj.CJ_ERR_NO_DEVICE
