@@ -492,6 +492,9 @@ def secondary(args):
                 variants.append(("aot", 0, (0, 0, 0, 0)))
             if dt == cj.F32 and n % 4 == 0 and n >= 8:
                 variants.append(("regblock", 0, (5, max(1, 256 // ((n // 4) ** 2)), 0, 0)))
+            if dt == cj.F32 and n <= 32 and args.workload != "small":
+                variants.append(("tworow", 0, (6, max(1, 256 // ((n + 1) // 2)), 0, 0)))
+                variants.append(("tworow128", 0, (6, max(1, 128 // ((n + 1) // 2)), 0, 0)))
             reps = 200 if b == 64 else K
             for name, fl, tile in variants:
                 h = cj.specialize(cj.K_UPDATE_CHAIN, dt, n=n, flags=fl, tile=tile)

@@ -115,8 +115,12 @@ typedef struct {
  *     (X and A in registers, n <= 8), 3 = bf16 tensor-core warp tile,
  *     4 = FP64 tensor cores (mma.sync m8n8k4; one warp per 8 rows; f64 with
  *     n in {8, 16, 24, 32}), 5 = FP32 register blocks (one thread per 4x4
- *     block of X A, X transposed in shared memory; f32, n % 4 == 0, n >= 8).
- *     Default: n <= 4 -> {2, 128}; n <= 32 -> {1, max(1, 256 / n)};
+ *     block of X A, X transposed in shared memory; f32, n >= 8, n padded to
+ *     a multiple of 4 with zeros), 6 = two rows of X per thread (rows h and
+ *     h + ceil(n / 2); f32).
+ *     Default: n <= 4 -> {2, 128}; f32 grouped with n >= 17 -> {5, 1};
+ *     f32 with n >= 9 -> {6, max(1, 128 / ceil(n / 2))}; otherwise n <= 32 ->
+ *     {1, max(1, 256 / n)};
  *     else {1, max(1, 128 / n)}; bf16 -> {3, max(1, 128 / n16)} with n16 = n
  *     rounded up to a multiple of 16 (mapping 3: one warp per 16 rows,
  *     bf16 operands, fp32 accumulate and state).

@@ -83,11 +83,15 @@ def _tc_smem(m, d, stages, tg, tz, lout, boxes):
 
 def default_tile(kernel: int, dtype: int, n: int, layout_a: int = 0, layout_b: int = 0, m: int = 36,
                  d: int = 96) -> tuple:
+    if kernel == K_UPDATE_CHAIN_GROUPED and dtype == F32 and n >= 17:
+        return (5, 1, 0, 0)            # one large instance per block, 4x4 register blocks
     if kernel in (K_UPDATE_CHAIN, K_UPDATE_CHAIN_GROUPED):
         if dtype == BF16:
             return (3, max(1, 128 // (-(-n // 16) * 16)), 0, 0)
         if n <= 4:
             return (2, 128, 0, 0)
+        if dtype == F32 and n >= 9:          # two rows of X per thread
+            return (6, max(1, 128 // ((n + 1) // 2)), 0, 0)
         return (1, max(1, (256 if n <= 32 else 128) // n), 0, 0)
     if kernel == K_LPLUSTIMES:     # LTimes of the swapped problem
         return default_tile(K_LTIMES, dtype, n, layout_b, layout_a, d, m)

@@ -227,6 +227,12 @@ void default_tile(int k, cj_template_args &a) {
         a.tile[0] = cjint::chain_default_map(a.n, a.dtype);
         a.tile[1] = cjint::chain_default_ipb(a.n, a.dtype);
         a.tile[2] = a.tile[3] = 0;
+        if (k == CJ_K_UPDATE_CHAIN_GROUPED && a.dtype == CJ_F32 && a.n >= 17) {
+            // uneven batches hold few large instances: one per block, on
+            // (n / 4)^2 threads (register blocks), shortens the longest chain
+            a.tile[0] = 5;
+            a.tile[1] = 1;
+        }
         return;
     }
     const int ct = 64;
@@ -337,9 +343,11 @@ cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_
     // explicit tiles: check the kernel can be instantiated and launched
     if (!is_lt(k)) {
         const int map = a.tile[0], ipb = a.tile[1];
-        if (map < 1 || map > 5) return fail(CJ_ERR_INVALID_ARG, "update chain mapping %d must be 1..5", map);
-        if (map == 5 && (a.dtype != CJ_F32 || a.n % 4 || a.n < 8))
-            return fail(CJ_ERR_INVALID_ARG, "mapping 5 (register blocks) needs f32 and n a multiple of 4, n >= 8");
+        if (map < 1 || map > 6) return fail(CJ_ERR_INVALID_ARG, "update chain mapping %d must be 1..6", map);
+        if (map == 6 && a.dtype != CJ_F32)
+            return fail(CJ_ERR_INVALID_ARG, "mapping 6 (two rows per thread) needs f32");
+        if (map == 5 && (a.dtype != CJ_F32 || a.n < 8))
+            return fail(CJ_ERR_INVALID_ARG, "mapping 5 (register blocks) needs f32 and n >= 8");
         if ((map == 3) != (a.dtype == CJ_BF16))
             return fail(CJ_ERR_INVALID_ARG, "mapping 3 (bf16 tensor cores) is the only mapping of dtype bf16");
         if (map == 2 && a.n > 8) return fail(CJ_ERR_INVALID_ARG, "mapping 2 needs n <= 8");

@@ -16,10 +16,15 @@ enum { D_F64 = 0, D_F32 = 1, D_BF16 = 2 };
 // FP64 tensor cores (mapping 4) are a candidate only: on B300 mma.sync f64
 // issues on the same FP64 pipe as DFMA and is not faster (measured).
 constexpr bool chain_dmma_ok(int n, int dtype) { return dtype == D_F64 && n % 8 == 0 && n <= 32; }
-constexpr int chain_default_map(int n, int dtype) { return dtype == D_BF16 ? 3 : (n <= 4 ? 2 : 1); }
+// FP32 n >= 9: two rows per thread (mapping 6), 128 / ceil(n / 2) instances.
+constexpr int chain_default_map(int n, int dtype) {
+    return dtype == D_BF16 ? 3 : n <= 4 ? 2 : (dtype == D_F32 && n >= 9) ? 6 : 1;
+}
 constexpr int chain_default_ipb(int n, int dtype) {
     return dtype == D_BF16 ? (128 / ((n + 15) / 16 * 16) > 1 ? 128 / ((n + 15) / 16 * 16) : 1)
-         : n <= 4 ? 128 : n <= 32 ? 256 / n : (128 / n > 1 ? 128 / n : 1);
+         : n <= 4 ? 128
+         : (dtype == D_F32 && n >= 9) ? (128 / ((n + 1) / 2) > 1 ? 128 / ((n + 1) / 2) : 1)
+         : n <= 32 ? 256 / n : (128 / n > 1 ? 128 / n : 1);
 }
 
 struct AotKernel {

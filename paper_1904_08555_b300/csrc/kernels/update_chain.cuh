@@ -98,6 +98,85 @@ __device__ __forceinline__ void row_chain_regs(const T* sA, int aoff, int i, int
     }
 }
 
+// Two rows of X per thread (mapping 6, FP32): each 16-byte read of A's row l
+// feeds eight fused multiply-adds (four per row).  i1 < 0: the second row is
+// absent (odd N) and stays zero.
+template <class T, int N, int AR>
+__device__ __forceinline__ void row2_chain_regs(const T* sA, int aoff, int i0, int i1, int steps, T cc,
+                                                T (&x0)[N], T (&x1)[N]) {
+    static_assert(sizeof(T) == 4 && AR % 4 == 0, "mapping 6 is FP32 with rows padded to 16 bytes");
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        x0[j] = (j == i0) ? T(1) : T(0);
+        x1[j] = (j == i1) ? T(1) : T(0);
+    }
+    for (int k = 0; k < steps; ++k) {
+        const T* a = a_in_regs<T, N>::value ? sA + aoff : opaque_base(sA, aoff);
+        T p0[N], p1[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) p0[j] = p1[j] = T(0);
+#pragma unroll
+        for (int l = 0; l < N; ++l) {
+            const float4* a4 = reinterpret_cast<const float4*>(a + l * AR);
+            const T u0 = x0[l], u1 = x1[l];
+#pragma unroll
+            for (int q = 0; q < AR / 4; ++q) {
+                const float4 v = a4[q];
+                const float w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (4 * q + e < N) {
+                        p0[4 * q + e] = fmaT(u0, w[e], p0[4 * q + e]);
+                        p1[4 * q + e] = fmaT(u1, w[e], p1[4 * q + e]);
+                    }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            x0[j] = fmaT(cc, p0[j], x0[j]);
+            x1[j] = fmaT(cc, p1[j], x1[j]);
+        }
+    }
+}
+
+// Mapping 6 for N > 32: the two rows of X live in the thread's own
+// shared-memory rows xs0 and xs1 (each element read once per N fused
+// multiply-adds); the two product rows in registers.
+template <class T, int N, int AR>
+__device__ __forceinline__ void row2_chain_smem(const T* a, T* xs0, T* xs1, int i0, int i1, int steps, T cc) {
+    static_assert(sizeof(T) == 4 && AR % 4 == 0, "mapping 6 is FP32 with rows padded to 16 bytes");
+    for (int j = 0; j < N; ++j) {
+        xs0[j] = (j == i0) ? T(1) : T(0);
+        xs1[j] = (j == i1) ? T(1) : T(0);
+    }
+    for (int k = 0; k < steps; ++k) {
+        T p0[N], p1[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) p0[j] = p1[j] = T(0);
+#pragma unroll(N > 48 ? 1 : 2)
+        for (int l = 0; l < N; ++l) {
+            const float4* a4 = reinterpret_cast<const float4*>(a + l * AR);
+            const T u0 = xs0[l], u1 = xs1[l];
+#pragma unroll
+            for (int q = 0; q < AR / 4; ++q) {
+                const float4 v = a4[q];
+                const float w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (4 * q + e < N) {
+                        p0[4 * q + e] = fmaT(u0, w[e], p0[4 * q + e]);
+                        p1[4 * q + e] = fmaT(u1, w[e], p1[4 * q + e]);
+                    }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            xs0[j] = fmaT(cc, p0[j], xs0[j]);
+            xs1[j] = fmaT(cc, p1[j], xs1[j]);
+        }
+    }
+}
+
 // Same for large N: the row of X lives in the thread's own shared-memory row
 // xs (read once per N fused multiply-adds); the product row in registers.
 template <class T, int N, int AR>
@@ -271,12 +350,16 @@ __device__ __forceinline__ void chain_block(T* sA, int ninst, int tid, StepsOf s
     if constexpr (MAP == 5) {
         // FP32 register blocks: thread (inst, rb, cb) owns rows 4rb..4rb+3 and
         // columns 4cb..4cb+3 of P = X A.  X is kept transposed in shared memory
-        // (xt[l][r], pitch N + 4) so both operands are 16-byte vector reads:
-        // 16 FMA per two shared-memory loads.  All threads of the block run
-        // the longest instance's step count so every barrier is uniform.
-        static_assert(sizeof(T) == 4 && N % 4 == 0 && N >= 8, "mapping 5 is FP32 with N a multiple of 4");
-        constexpr int P = cjg::row_pitch(NN, 4);
-        constexpr int B4 = N / 4, TPI = B4 * B4, XTP = N + 4;
+        // (xt[l][r], pitch NP + 4) so both operands are 16-byte vector reads:
+        // 16 FMA per two shared-memory loads.  N is padded to NP, a multiple
+        // of 4: A's padded columns are zeroed here, so X's padded rows and
+        // columns stay zero.  All threads of the block run the longest
+        // instance's step count so every barrier is uniform.
+        static_assert(sizeof(T) == 4 && N >= 8, "mapping 5 is FP32 with N >= 8");
+        constexpr int NP = (N + 3) / 4 * 4;
+        constexpr int P = cjg::chain_pitch(N, 5, 4), AR = cjg::chain_arow(N, 5, 4);
+        constexpr int B4 = NP / 4, TPI = B4 * B4, XTP = NP + 4;
+        static_assert(AR == NP, "mapping 5 stages A with rows of NP");
         T* xt_all = sA + IPB * P;
         const int inst = tid / TPI, w = tid - inst * TPI;
         const int rb = w % B4, cb = w / B4;
@@ -285,13 +368,20 @@ __device__ __forceinline__ void chain_block(T* sA, int ninst, int tid, StepsOf s
         for (int q = 0; q < ninst; ++q) kmax = max(kmax, steps_of(q));
         const int steps = active ? steps_of(inst) : 0;
         const T cc = active ? c_of(inst) : T(0);
-        T* xt = xt_all + (active ? inst : 0) * N * XTP;
-        const T* a = sA + (active ? inst : 0) * P;
-        if (active)
-            for (int e = w; e < NN; e += TPI) {
-                const int l = e / N, r = e - l * N;
-                xt[l * XTP + r] = (l == r) ? T(1) : T(0);
+        T* xt = xt_all + (active ? inst : 0) * NP * XTP;
+        T* a_w = sA + (active ? inst : 0) * P;
+        const T* a = a_w;
+        if (active) {
+            for (int e = w; e < NP * NP; e += TPI) {
+                const int l = e / NP, r = e - l * NP;
+                xt[l * XTP + r] = (l == r && l < N) ? T(1) : T(0);
             }
+            if constexpr (NP != N)
+                for (int e = w; e < N * (NP - N); e += TPI) {
+                    const int l = e / (NP - N), j = N + (e - l * (NP - N));
+                    a_w[l * NP + j] = T(0);
+                }
+        }
         __syncthreads();
         for (int k = 0; k < kmax; ++k) {
             float acc[4][4] = {};
@@ -300,7 +390,7 @@ __device__ __forceinline__ void chain_block(T* sA, int ninst, int tid, StepsOf s
 #pragma unroll 4
                 for (int l = 0; l < N; ++l) {
                     const float4 xv = *reinterpret_cast<const float4*>(xt + l * XTP + 4 * rb);
-                    const float4 av = *reinterpret_cast<const float4*>(a + l * N + 4 * cb);
+                    const float4 av = *reinterpret_cast<const float4*>(a + l * NP + 4 * cb);
                     const float xr[4] = {xv.x, xv.y, xv.z, xv.w};
                     const float ar[4] = {av.x, av.y, av.z, av.w};
 #pragma unroll
@@ -327,6 +417,36 @@ __device__ __forceinline__ void chain_block(T* sA, int ninst, int tid, StepsOf s
                 const int i = e / N, j = e - i * N;
                 sA[inst * P + (LAYOUT == 0 ? i * N + j : j * N + i)] = xt[j * XTP + i];
             }
+    } else if constexpr (MAP == 6) {
+        static_assert(sizeof(T) == 4, "mapping 6 is FP32");
+        constexpr int P = cjg::chain_pitch(N, 6, 4), AR = cjg::chain_arow(N, 6, 4), H = (N + 1) / 2;
+        const int inst = tid / H, h = tid - inst * H;
+        const bool active = inst < ninst;
+        const int i1 = h + H < N ? h + H : -1;
+        if constexpr (N <= 32) {
+            T x0[N], x1[N];
+            if (active) row2_chain_regs<T, N, AR>(sA, inst * P, h, i1, steps_of(inst), c_of(inst), x0, x1);
+            __syncthreads();
+            if (active) {
+#pragma unroll
+                for (int j = 0; j < N; ++j) sA[inst * P + (LAYOUT == 0 ? h * N + j : j * N + h)] = x0[j];
+                if (i1 >= 0) {
+#pragma unroll
+                    for (int j = 0; j < N; ++j) sA[inst * P + (LAYOUT == 0 ? i1 * N + j : j * N + i1)] = x1[j];
+                }
+            }
+        } else {
+            constexpr int XP = cjg::xrow_pitch(N);
+            T* xs0 = sA + IPB * P + (2 * tid) * XP;
+            T* xs1 = xs0 + XP;
+            if (active) row2_chain_smem<T, N, AR>(sA + inst * P, xs0, xs1, h, i1, steps_of(inst), c_of(inst));
+            __syncthreads();
+            if (active) {
+                for (int j = 0; j < N; ++j) sA[inst * P + (LAYOUT == 0 ? h * N + j : j * N + h)] = xs0[j];
+                if (i1 >= 0)
+                    for (int j = 0; j < N; ++j) sA[inst * P + (LAYOUT == 0 ? i1 * N + j : j * N + i1)] = xs1[j];
+            }
+        }
     } else if constexpr (MAP == 3) {
         static_assert(sizeof(T) == 4 && N >= 16, "mapping 3 is bf16 operands with fp32 state, N >= 16");
         constexpr int P = cjg::row_pitch(NN, 4);

@@ -52,13 +52,16 @@ void chain_candidates(const cj_template_args &a, std::vector<std::array<int, 4>>
     if (a.dtype == CJ_F64 && n % 8 == 0 && n <= 32)
         for (int ipb : {1, 2, 4, 8})
             if (ok(4, ipb)) out.push_back({4, ipb, 0, 0});
-    if (a.dtype == CJ_F32 && n % 4 == 0 && n >= 8)
+    if (a.dtype == CJ_F32 && n >= 8)
         for (int ipb : {1, 2, 4, 8, 16, 32})
             if (ok(5, ipb) && cjg::chain_threads(n, 5, ipb) >= 64) out.push_back({5, ipb, 0, 0});
+    if (a.dtype == CJ_F32)
+        for (int ipb : {1, 2, 4, 8, 16, 32})
+            if (ok(6, ipb) && cjg::chain_threads(n, 6, ipb) >= 64) out.push_back({6, ipb, 0, 0});
     if (n <= 8)
         for (int ipb : {32, 64, 128, 256})
             if (ok(2, ipb)) out.push_back({2, ipb, 0, 0});
-    for (int ipb : {1, 2, 4, 8, 16, 32, 64})
+    for (int ipb : {2, 4, 8, 16, 32, 64})
         if (ipb * n <= 1024 && ok(1, ipb)) out.push_back({1, ipb, 0, 0});
 }
 
@@ -173,10 +176,10 @@ void featurize(int k, const cj_template_args &a0, int64_t batch, int32_t steps, 
         f[6] = lg2(n) / 6;
         f[7] = n / 64;
         f[8 + (a.layout_a & 1)] = 1.f;
-        f[20] = tile[0] == 1;
+        f[20] = tile[0] == 1 || tile[0] == 6;
         f[21] = tile[0] == 2;
         f[22] = tile[0] == 4 || tile[0] == 5;   // register/tensor blocked panels
-        f[19] = tile[0] == 5;
+        f[19] = tile[0] == 5 ? 1.f : tile[0] == 6 ? 0.5f : 0.f;
         f[23] = lg2(tile[1]) / 8;
         f[24] = lg2(cjg::chain_threads(a.n, tile[0], tile[1])) / 10;
         f[25] = a.n % 8 == 0;

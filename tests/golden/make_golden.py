@@ -36,6 +36,7 @@ REQUESTS = [
     (K.K_LPLUSTIMES, K.F32, 0, 0, 0, 64, 128, (0, 0, 0, 0), 0),         # 128 rows
     (K.K_UPDATE_CHAIN_GROUPED, K.F64, 20, 0, 0, 0, 0, (0, 0, 0, 0), 0),
     (K.K_UPDATE_CHAIN_GROUPED, K.F32, 3, 1, 0, 0, 0, (0, 0, 0, 0), 0),  # layout forced 0
+    (K.K_UPDATE_CHAIN_GROUPED, K.F32, 45, 0, 0, 0, 0, (0, 0, 0, 0), 0),  # one large instance per block
     (K.K_UPDATE_CHAIN, K.F64, 8, 0, 0, 0, 0, (0, 0, 0, 0), K.FLAG_INJECT_COMPILE_ERROR),
 ]
 

@@ -110,13 +110,28 @@ def test_update_chain_fp64_tensor_core_tiles(n, layout, ipb):
     assert relF_per_instance(x4, x1) <= TOL64
 
 
-@pytest.mark.parametrize("n,ipb", [(8, 8), (12, 4), (16, 3), (32, 2), (48, 1), (64, 1)])
+@pytest.mark.parametrize("n,ipb", [(8, 8), (12, 4), (16, 3), (32, 2), (48, 1), (64, 1),
+                                   (9, 4), (13, 3), (30, 2), (45, 1), (61, 1), (63, 2)])
 @pytest.mark.parametrize("layout", [0, 1])
 def test_update_chain_f32_register_blocks(n, ipb, layout):
-    """Mapping 5 (4x4 register blocks, X transposed in shared memory)."""
+    """Mapping 5 (4x4 register blocks, X transposed in shared memory); n not a
+    multiple of 4 runs padded with zeros."""
     steps = 64
     h = cj.specialize(cj.K_UPDATE_CHAIN, cj.F32, n=n, layout_a=layout, tile=(5, ipb, 0, 0))
     batch = oracle_batch(n, steps) + 2
+    A = synth.chain_inputs_np(synth.SEED_CHAIN_SWEEP, batch, n, layout=layout)
+    ref = oracle.update_chain(A, steps, layout=layout, nthreads=8)
+    assert relF_per_instance(run_chain(h, A, steps, cj.F32), ref) <= TOL32
+
+
+@pytest.mark.parametrize("n,ipb", [(2, 32), (5, 16), (7, 9), (8, 8), (12, 4), (15, 5), (16, 3), (31, 2), (32, 8)])
+@pytest.mark.parametrize("layout", [0, 1])
+def test_update_chain_f32_two_rows_per_thread(n, ipb, layout):
+    """Mapping 6 (rows h and h + ceil(n/2) per thread; odd n leaves the last
+    thread's second row empty), ragged last block."""
+    steps = 64
+    h = cj.specialize(cj.K_UPDATE_CHAIN, cj.F32, n=n, layout_a=layout, tile=(6, ipb, 0, 0))
+    batch = oracle_batch(n, steps) + 3
     A = synth.chain_inputs_np(synth.SEED_CHAIN_SWEEP, batch, n, layout=layout)
     ref = oracle.update_chain(A, steps, layout=layout, nthreads=8)
     assert relF_per_instance(run_chain(h, A, steps, cj.F32), ref) <= TOL32
@@ -472,7 +487,7 @@ def test_grouped_handle_direct_launch():
     items[:, 0] = np.arange(cnt) * nn * nn
     items[:, 1] = steps
     for dt, tile, flags in ((cj.F64, (0, 0, 0, 0), 0), (cj.F64, (0, 0, 0, 0), cj.FLAG_GENERIC),
-                            (cj.F32, (5, 2, 0, 0), 0), (cj.F32, (1, 3, 0, 0), 0)):
+                            (cj.F32, (5, 2, 0, 0), 0), (cj.F32, (1, 3, 0, 0), 0), (cj.F32, (6, 3, 0, 0), 0)):
         h = cj.specialize(cj.K_UPDATE_CHAIN_GROUPED, dt, n=nn, tile=tile, flags=flags)
         it = torch.from_numpy(items).cuda()
         A = torch.from_numpy(pool).to("cuda", tdtype(dt))
