@@ -162,13 +162,17 @@ void featurize(int k, const cj_template_args &a0, int64_t batch, int32_t steps, 
         f[8 + (a.layout_a % 6)] = 1.f;
         f[14 + (a.layout_b % 6)] = 1.f;
         const int mode = (tile[3] >> 16) & 0xf, r = (tile[3] >> 8) & 0xff, s = tile[3] & 0xff;
-        f[26] = (tile[3] >> 20) & 1;
+        // f[2] and f[5] (grouped kernel, bf16) are always 0 for LTimes; here they
+        // flag the tcgen05 tiles (modes 4 and 5) and the TMA-fed one (mode 5)
+        f[2] = mode == 4 || mode == 5;
+        f[5] = mode == 5;
+        f[26] = ((tile[3] >> 20) & 0xf) / 8.f;   // cp.async flag, prefetch depth or TMA boxes
         f[20] = lg2(tile[0]) / 5;
         f[21] = lg2(tile[1]) / 7;
         f[22] = lg2(tile[2]) / 10;
-        f[23] = r / 4.f;
+        f[23] = r / 8.f;
         f[24] = s / 16.f;
-        f[25] = mode;
+        f[25] = mode / 5.f;
     } else {
         const double n = a.n;
         flops = (double)batch * steps * (2 * n * n * n + 2 * n * n);
