@@ -402,7 +402,7 @@ def main():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=("cj", "reference"), default="cj")
-    p.add_argument("--workload", choices=("sweep", "small", "sweep32", "ltimes", "uneven", "kernel", "costmodel"),
+    p.add_argument("--workload", choices=("sweep", "small", "sweep32", "ltimes", "uneven", "kernel", "costmodel", "eigen"),
                    default="sweep",
                    help="sweep (default): the FP64 size sweep; the others are secondary measurements")
     p.add_argument("--dtype", choices=("f64", "f32", "bf16"), default="f64", help="ltimes / uneven precision")
@@ -656,6 +656,42 @@ def secondary(args):
         ms = _events(torch, stream, fn, K)
         out.update({"value": f / ms / 1e6, "dtype": args.dtype, "ms_per_launch": ms, "regs": h.regs()[0],
                     "config": {"workload": desc}})
+    elif args.workload == "eigen":
+        # the paper's literal Eigen recurrence (Listing eigen1), batched: random
+        # starts in [-1, 1), c = 5e-5, 64 repeats, batch = 2^24 / N^2 per size
+        dt = cj.F64 if args.dtype == "f64" else cj.F32
+        tdt = torch.float64 if dt == cj.F64 else torch.float32
+        rep, c = 64, 5e-5
+        rows, tot_f, tot_s, tot_g = [], 0.0, 0.0, 0.0
+        for n in range(1, 17):
+            b = (1 << 24) // (n * n)
+            M0 = synth.uniform_torch(synth.SEED_CHAIN_SWEEP, synth.STREAM_A, b * n * n, "cuda").to(tdt)
+            M = torch.empty_like(M0)
+            f = float(b) * rep * (2.0 * n ** 3 + 3.0 * n ** 2)
+            row = {"N": n, "batch": b}
+            for name, fl in (("spec", 0), ("generic", cj.FLAG_GENERIC)):
+                h = cj.specialize(cj.K_EIGEN_RECURRENCE, dt, n=n, flags=fl)
+                fn = lambda h=h: cj.launch_eigen(h, M0, M, rep, c, batch=b, stream=stream)
+                _events(torch, stream, fn, W)
+                ms = _events(torch, stream, fn, K)
+                row.update({name + "_ms": ms, name + "_gflops": f / ms / 1e6, name + "_regs": h.regs()[0]})
+            row["speedup_vs_generic"] = row["generic_ms"] / row["spec_ms"]
+            rows.append(row)
+            tot_f += f
+            tot_s += row["spec_ms"]
+            tot_g += row["generic_ms"]
+            del M0, M
+        peak = PEAK_TFLOPS[args.dtype]
+        out.update({"value": tot_f / tot_s / 1e6, "dtype": args.dtype,
+                    "generic": {"value": tot_f / tot_g / 1e6, "unit": "GFLOP/s"},
+                    "speedup_vs_generic": tot_g / tot_s,
+                    "min_speedup_vs_generic": min(r["speedup_vs_generic"] for r in rows),
+                    "per_n": rows,
+                    "roofline": {"bound": "alu", "peak": peak, "unit": "TFLOP/s",
+                                 "frac": tot_f / tot_s / 1e9 / peak},
+                    "config": {"workload": "Eigen literal recurrence M = Ones + 5e-5 (M + M M) (Listing eigen1), "
+                                           f"N = 1..16, 64 repeats, batch 2^24/N^2, random starts, {args.dtype}",
+                               "flops_per_instance_step": "2 N^3 + 3 N^2"}})
     elif args.workload == "costmodel":
         from paper_1904_08555_b300 import costmodel
         res = costmodel.run(n_heldout=args.heldout, train_steps=args.train_steps, log=lambda m: print(m, file=sys.stderr))

@@ -30,6 +30,12 @@
  *                         instances of one size N but different step counts,
  *                         pulled by a persistent kernel (batch amortization of
  *                         the instantiation lookup, Sec. 5.1).
+ *   CJ_K_EIGEN_RECURRENCE -- the Eigen benchmark's literal recurrence (Sec. 5,
+ *                         Listing eigen1) batched: per instance
+ *                         M_{k+1} = Ones + c (M_k + M_k M_k), k = 0..R-1, from a
+ *                         caller-given M_0 (the listing: c = 5e-5, M_0(i, j) =
+ *                         i + N j).  It grows without bound; compare over few
+ *                         repeats.
  *
  * Thread safety: every function may be called from any host thread.
  * cj_specialize serialises on one mutex; cj_launch takes no lock.
@@ -63,7 +69,8 @@ typedef enum {
     CJ_K_UPDATE_CHAIN = 1,
     CJ_K_LTIMES = 2,
     CJ_K_UPDATE_CHAIN_GROUPED = 3,
-    CJ_K_LPLUSTIMES = 4
+    CJ_K_LPLUSTIMES = 4,
+    CJ_K_EIGEN_RECURRENCE = 5
 } cj_kernel_id;
 
 typedef enum {
@@ -104,6 +111,7 @@ typedef struct {
  *                  Storage orders list (x, g, z) slowest to fastest, x = d for
  *                  in and m for out: 0 XGZ, 1 XZG, 2 GXZ, 3 GZX, 4 ZXG, 5 ZGX.
  *   UPDATE_CHAIN_GROUPED: dtype, n (1..64), tile (row-major only).
+ *   EIGEN_RECURRENCE: dtype (f64/f32), n (1..32), tile (row-major only).
  *   LPLUSTIMES:    as LTIMES (layout_a = order of the accumulated `in`,
  *                  layout_b = order of the input `out`, m, d); the tile is
  *                  an LTimes tile of the swapped problem (d output rows, m
@@ -124,6 +132,9 @@ typedef struct {
  *     else {1, max(1, 128 / n)}; bf16 -> {3, max(1, 128 / n16)} with n16 = n
  *     rounded up to a multiple of 16 (mapping 3: one warp per 16 rows,
  *     bf16 operands, fp32 accumulate and state).
+ *   Eigen recurrence: {1, instances per block, 0, 0} (one thread per row;
+ *     M_k of every instance in shared memory, two buffers).  Default: instances
+ *     per block max(1, 128 / n), fewer if both buffers would exceed 96 KiB.
  *   LTimes: {TG, TZ, threads, (PIPE << 20) | (MODE << 16) | (R << 8) | S}: a
  *     block covers TG x TZ (g, z) columns at a time (a persistent grid).
  *     MODE 0: the box with all d is staged in shared memory and each thread
@@ -213,6 +224,9 @@ cj_status cj_specialize_wait(cj_handle h, int timeout_ms);
  *     const int64_t* Z}; Lp is [d][m] row-major, out is m*G*Z elements in
  *     order layout_b (read), in is d*G*Z elements in order layout_a
  *     (accumulated into).
+ *   EIGEN_RECURRENCE: {const T** M0, T** M, const int32_t* repeat, const
+ *     double* c}; M0 and M are batch*n*n elements (row-major instances); repeat
+ *     >= 0 steps (0 copies M0 to M).
  *   UPDATE_CHAIN_GROUPED: {const int64_t** worklist, const T** A_pool,
  *     T** X_pool, int32_t** counter}; batch = work items.  Item i is three
  *     int64 {element offset of A_i and X_i in the pools, T_i, reserved}; items

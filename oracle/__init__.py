@@ -17,6 +17,7 @@ Pinning status (all pinned by CPU tests under tests/test_oracle_*.py):
   mlp            -- central finite differences, linear least-squares closed
                     form, first Adam step closed form.
   eigen_bench    -- exact rational brute force for tiny sizes.
+  eigen_recurrence -- the same recurrence over a batch of starts and any c.
 """
 from __future__ import annotations
 
@@ -67,6 +68,8 @@ def _load():
         lib.oracle_adam.restype = None
         lib.oracle_eigen_bench.argtypes = [i32, i32, P]
         lib.oracle_eigen_bench.restype = None
+        lib.oracle_eigen_recurrence.argtypes = [ctypes.c_longlong, i32, i32, ctypes.c_double, P, P]
+        lib.oracle_eigen_recurrence.restype = None
         _lib = lib
     return _lib
 
@@ -210,3 +213,18 @@ def eigen_bench(n: int, repeat: int) -> np.ndarray:
     out = np.empty((n, n))
     _load().oracle_eigen_bench(n, repeat, _p(out))
     return out
+
+
+def eigen_recurrence(M0: np.ndarray, repeat: int, c: float = 5e-5) -> np.ndarray:
+    """Batched M_{k+1} = Ones + c (M_k + M_k M_k) from starts M0 [batch][n][n] (Sec. 5, Listing eigen1)."""
+    M0 = np.ascontiguousarray(M0, dtype=np.float64)
+    b, n, _ = M0.shape
+    out = np.empty_like(M0)
+    _load().oracle_eigen_recurrence(b, n, repeat, c, _p(M0), _p(out))
+    return out
+
+
+def eigen_start(n: int) -> np.ndarray:
+    """The listing's start M_0(i, j) = i + n j."""
+    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    return (i + n * j).astype(np.float64)

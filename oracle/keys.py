@@ -45,6 +45,7 @@ K_UPDATE_CHAIN = 1
 K_LTIMES = 2
 K_UPDATE_CHAIN_GROUPED = 3
 K_LPLUSTIMES = 4
+K_EIGEN_RECURRENCE = 5
 
 F64, F32, BF16 = 0, 1, 2
 
@@ -83,6 +84,14 @@ def _tc_smem(m, d, stages, tg, tz, lout, boxes):
 
 def default_tile(kernel: int, dtype: int, n: int, layout_a: int = 0, layout_b: int = 0, m: int = 36,
                  d: int = 96) -> tuple:
+    if kernel == K_EIGEN_RECURRENCE:
+        # one thread per row, max(1, 128 // n) instances per block, fewer while
+        # the two buffers (rows of n + 1 elements) exceed 96 KiB
+        es = 8 if dtype == F64 else 4
+        ipb = max(1, 128 // n)
+        while ipb > 1 and 2 * ipb * n * (n + 1) * es > 96 * 1024:
+            ipb -= 1
+        return (1, ipb, 0, 0)
     if kernel == K_UPDATE_CHAIN_GROUPED and dtype == F32 and n >= 17:
         return (5, 1, 0, 0)            # one large instance per block, 4x4 register blocks
     if kernel in (K_UPDATE_CHAIN, K_UPDATE_CHAIN_GROUPED):
@@ -122,9 +131,9 @@ def default_tile(kernel: int, dtype: int, n: int, layout_a: int = 0, layout_b: i
 def canonical_key(kernel: int, dtype: int, n=0, layout_a=0, layout_b=0, m=0, d=0,
                   tile=(0, 0, 0, 0), flags=0) -> bytes:
     tile = tuple(tile)
-    if kernel in (K_UPDATE_CHAIN, K_UPDATE_CHAIN_GROUPED):
+    if kernel in (K_UPDATE_CHAIN, K_UPDATE_CHAIN_GROUPED, K_EIGEN_RECURRENCE):
         m = d = layout_b = 0
-        if kernel == K_UPDATE_CHAIN_GROUPED:
+        if kernel in (K_UPDATE_CHAIN_GROUPED, K_EIGEN_RECURRENCE):
             layout_a = 0
     elif kernel in (K_LTIMES, K_LPLUSTIMES):
         n = 0

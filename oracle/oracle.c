@@ -20,6 +20,7 @@
  *                            hand-derived backward pass and Adam step (the
  *                            paper's future-work autotuning, Sec. 6).
  *   oracle_eigen_bench    -- the paper's literal Eigen recurrence
+ *   oracle_eigen_recurrence -- the same recurrence over a batch of starts, any c
  *                            M = Ones + 5e-5 (M + M M) (Sec. 5, Listing eigen1).
  */
 #include <math.h>
@@ -350,6 +351,29 @@ void oracle_adam(int64_t count, double *theta, const double *grad, double *m, do
 /*   m(i,j) = i + size*j initially; repeat: m = Ones + 5e-5 * (m + m*m).     */
 /* Output m after `repeat` iterations, row-major.                            */
 /* ------------------------------------------------------------------------ */
+/* The same recurrence for a batch of caller-given starts M0 (batch*n*n,     */
+/* row-major) and scale c: M_{k+1} = Ones + c * (M_k + M_k * M_k).           */
+void oracle_eigen_recurrence(long long batch, int n, int repeat, double c, const double *M0, double *out)
+{
+    double *m = (double *)malloc(sizeof(double) * n * n);
+    double *q = (double *)malloc(sizeof(double) * n * n);
+    for (long long b = 0; b < batch; ++b) {
+        memcpy(m, M0 + b * n * n, sizeof(double) * n * n);
+        for (int r = 0; r < repeat; ++r) {
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < n; ++j) {
+                    double s = 0.0;
+                    for (int l = 0; l < n; ++l) s = s + m[i * n + l] * m[l * n + j];
+                    q[i * n + j] = s;
+                }
+            for (int i = 0; i < n * n; ++i) m[i] = 1.0 + c * (m[i] + q[i]);
+        }
+        memcpy(out + b * n * n, m, sizeof(double) * n * n);
+    }
+    free(m);
+    free(q);
+}
+
 void oracle_eigen_bench(int n, int repeat, double *out)
 {
     double *m = (double *)malloc(sizeof(double) * n * n);

@@ -15,7 +15,7 @@ CJ_OK, CJ_ERR_INVALID_ARG, CJ_ERR_NOT_INITIALIZED, CJ_ERR_NO_DEVICE = 0, 1, 2, 3
 CJ_ERR_UNSUPPORTED_ARCH, CJ_ERR_COMPILE, CJ_ERR_CUDA, CJ_ERR_OOM = 4, 5, 6, 7
 CJ_ERR_TIMEOUT, CJ_ERR_PENDING = 8, 9
 
-K_UPDATE_CHAIN, K_LTIMES, K_UPDATE_CHAIN_GROUPED, K_LPLUSTIMES = 1, 2, 3, 4
+K_UPDATE_CHAIN, K_LTIMES, K_UPDATE_CHAIN_GROUPED, K_LPLUSTIMES, K_EIGEN_RECURRENCE = 1, 2, 3, 4, 5
 F64, F32, BF16 = 0, 1, 2
 FLAG_GENERIC, FLAG_NO_AOT, FLAG_INJECT_COMPILE_ERROR, FLAG_INJECT_WAIT_TIMEOUT = 0x1, 0x2, 0x100, 0x200
 CFG_COMPILE_ONLY = 0x1
@@ -221,6 +221,14 @@ def launch_lplustimes(h: Handle, Lp, out, x, G: int, Z: int, stream=None) -> Non
     vals = [ctypes.c_void_p(_ptr(Lp)), ctypes.c_void_p(_ptr(out)), ctypes.c_void_p(_ptr(x)),
             ctypes.c_int64(G), ctypes.c_int64(Z)]
     _launch(h, vals, Z, _stream(stream, Lp, out, x))
+
+
+def launch_eigen(h: Handle, M0, M, repeat: int, c: float = 5e-5, batch=None, stream=None) -> None:
+    """M_{k+1} = Ones + c (M_k + M_k M_k), repeat times, from M0 (batch*n*n, row-major) into M."""
+    if batch is None:
+        batch = M0.numel() // (h.n * h.n) if hasattr(M0, "numel") else 0
+    vals = [ctypes.c_void_p(_ptr(M0)), ctypes.c_void_p(_ptr(M)), ctypes.c_int32(repeat), ctypes.c_double(c)]
+    _launch(h, vals, batch, _stream(stream, M0, M))
 
 
 def launch_grouped(h: Handle, items, A_pool, X_pool, counter, n_items: int, stream=None) -> None:

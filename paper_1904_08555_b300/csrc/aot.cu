@@ -26,6 +26,7 @@ static const GenericKernels kGeneric = {
     {(const void *)&cj::ltimes_generic<double>, (const void *)&cj::ltimes_generic<float>},
     {(const void *)&cj::update_chain_grouped_generic<double>,
      (const void *)&cj::update_chain_grouped_generic<float>},
+    {(const void *)&cj::eigen_recurrence_generic<double>, (const void *)&cj::eigen_recurrence_generic<float>},
 };
 
 // Roofline denominator: 8 independent FMA chains per thread and nothing else

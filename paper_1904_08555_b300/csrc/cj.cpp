@@ -163,7 +163,7 @@ struct State {
     int busy = 0;
     std::condition_variable idle_cv;
     std::vector<std::thread> workers;
-    CUfunction gen_chain[2]{}, gen_lt[2]{}, gen_grp[2]{};
+    CUfunction gen_chain[2]{}, gen_lt[2]{}, gen_grp[2]{}, gen_eig[2]{};
     struct Aot {
         cjint::AotKernel k;
         CUfunction fn;
@@ -211,6 +211,13 @@ int lt_axis_host(int lay, int s) {
     return order[lay][s];
 }
 bool is_lt(int k) { return k == CJ_K_LTIMES || k == CJ_K_LPLUSTIMES; }
+bool is_eig(int k) { return k == CJ_K_EIGEN_RECURRENCE; }
+// Eigen recurrence default: rows per block up to 128 threads, both buffers within 96 KiB.
+int eig_default_ipb(int n, int es) {
+    int ipb = std::max(1, 128 / n);
+    while (ipb > 1 && cjg::eig_smem(n, ipb, es) > 96 * 1024) --ipb;
+    return ipb;
+}
 
 // The LTimes kernel a request runs: LPlusTimes is LTimes of the swapped
 // problem (output rows d, contracted m, orders exchanged) with accumulation.
@@ -223,6 +230,12 @@ LtView lt_view(int k, const cj_template_args &a) {
 }
 
 void default_tile(int k, cj_template_args &a) {
+    if (is_eig(k)) {
+        a.tile[0] = 1;
+        a.tile[1] = eig_default_ipb(a.n, esize(a.dtype));
+        a.tile[2] = a.tile[3] = 0;
+        return;
+    }
     if (!is_lt(k)) {
         a.tile[0] = cjint::chain_default_map(a.n, a.dtype);
         a.tile[1] = cjint::chain_default_ipb(a.n, a.dtype);
@@ -293,7 +306,8 @@ void make_key(int k, const cj_template_args &a, unsigned char *key) {
 
 cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_args &a) {
     a = in;
-    if (k != CJ_K_UPDATE_CHAIN && k != CJ_K_LTIMES && k != CJ_K_UPDATE_CHAIN_GROUPED && k != CJ_K_LPLUSTIMES)
+    if (k != CJ_K_UPDATE_CHAIN && k != CJ_K_LTIMES && k != CJ_K_UPDATE_CHAIN_GROUPED && k != CJ_K_LPLUSTIMES &&
+        k != CJ_K_EIGEN_RECURRENCE)
         return fail(CJ_ERR_INVALID_ARG, "unknown kernel id %d", k);
     if (a.dtype < 0 || a.dtype > 2) return fail(CJ_ERR_INVALID_ARG, "dtype %d out of range", a.dtype);
     if (a.flags & ~kKeyFlags) return fail(CJ_ERR_INVALID_ARG, "unknown flag bits 0x%x", a.flags & ~kKeyFlags);
@@ -304,6 +318,10 @@ cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_
         if (a.m < 1 || a.m > 64 || a.d < 1 || a.d > 128)
             return fail(CJ_ERR_INVALID_ARG, "LTimes needs 1 <= m <= 64 and 1 <= d <= 128");
         a.n = 0;
+    } else if (is_eig(k)) {
+        if (a.n < 1 || a.n > 32) return fail(CJ_ERR_INVALID_ARG, "Eigen recurrence n = %d outside 1..32", a.n);
+        if (a.dtype == CJ_BF16) return fail(CJ_ERR_INVALID_ARG, "the Eigen recurrence supports f64 and f32 only");
+        a.layout_a = a.layout_b = a.m = a.d = 0;   // row-major only
     } else {
         if (a.n < 1 || a.n > 64) return fail(CJ_ERR_INVALID_ARG, "n = %d outside 1..64", a.n);
         if (k == CJ_K_UPDATE_CHAIN_GROUPED) a.layout_a = 0;
@@ -341,6 +359,13 @@ cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_
         if (!chosen) default_tile(k, a);
     }
     // explicit tiles: check the kernel can be instantiated and launched
+    if (is_eig(k)) {
+        if (a.tile[0] != 1 || a.tile[1] < 1 || a.tile[2] || a.tile[3] || cjg::chain_threads(a.n, 1, a.tile[1]) > 1024 ||
+            cjg::eig_smem(a.n, a.tile[1], esize(a.dtype)) > 220 * 1024)
+            return fail(CJ_ERR_INVALID_ARG, "Eigen recurrence tile {%d,%d,%d,%d} invalid ({1, instances per block, 0, 0})",
+                        a.tile[0], a.tile[1], a.tile[2], a.tile[3]);
+        return CJ_OK;
+    }
     if (!is_lt(k)) {
         const int map = a.tile[0], ipb = a.tile[1];
         if (map < 1 || map > 6) return fail(CJ_ERR_INVALID_ARG, "update chain mapping %d must be 1..6", map);
@@ -425,7 +450,12 @@ void generic_impl(cj_handle_s *h) {
     const cj_template_args &a = h->a;
     const int di = dt_index(a.dtype), es = esize(a.dtype);
     g.variant = V_GENERIC;
-    if (is_lt(h->kernel)) {
+    if (is_eig(h->kernel)) {
+        g.fn = G.gen_eig[di];
+        g.ipb = eig_default_ipb(a.n, es);
+        g.threads = cjg::chain_threads(a.n, 1, g.ipb);
+        g.smem = (size_t)cjg::eig_smem(a.n, g.ipb, es);
+    } else if (is_lt(h->kernel)) {
         const LtView v = lt_view(h->kernel, a);
         g.fn = G.gen_lt[di];
         g.threads = a.dtype == CJ_F64 ? 64 : 128;
@@ -442,7 +472,11 @@ void generic_impl(cj_handle_s *h) {
 void spec_geometry(const cj_handle_s *h, Impl &s) {
     const cj_template_args &a = h->a;
     const int es = esize(a.dtype);
-    if (is_lt(h->kernel)) {
+    if (is_eig(h->kernel)) {
+        s.ipb = a.tile[1];
+        s.threads = cjg::chain_threads(a.n, 1, a.tile[1]);
+        s.smem = (size_t)cjg::eig_smem(a.n, a.tile[1], es);
+    } else if (is_lt(h->kernel)) {
         const LtView v = lt_view(h->kernel, a);
         const int mode = (a.tile[3] >> 16) & 0xf;
         s.threads = a.tile[2];
@@ -481,6 +515,8 @@ std::string name_expression(const cj_handle_s *h) {
     if (h->kernel == CJ_K_UPDATE_CHAIN)
         snprintf(buf, sizeof buf, "cj::update_chain<%s, %d, %d, %d, %d>", ctype(a.dtype), a.n, a.layout_a,
                  a.tile[0], a.tile[1]);
+    else if (is_eig(h->kernel))
+        snprintf(buf, sizeof buf, "cj::eigen_recurrence<%s, %d, %d>", ctype(a.dtype), a.n, a.tile[1]);
     else if (h->kernel == CJ_K_UPDATE_CHAIN_GROUPED)
         snprintf(buf, sizeof buf, "cj::update_chain_grouped<%s, %d, %d, %d>", ctype(a.dtype), a.n, a.tile[0],
                  a.tile[1]);
@@ -774,7 +810,7 @@ CJ_API cj_status cj_init(const cj_config *cfg, int device) {
         const auto &gk = cjint::generic_kernels();
         for (int d = 0; d < 2; ++d)
             if (!prep(gk.chain[d], &G.gen_chain[d]) || !prep(gk.ltimes[d], &G.gen_lt[d]) ||
-                !prep(gk.grouped[d], &G.gen_grp[d]))
+                !prep(gk.grouped[d], &G.gen_grp[d]) || !prep(gk.eigen[d], &G.gen_eig[d]))
                 return fail(CJ_ERR_CUDA, "could not load the generic kernels");
         int na = 0;
         const cjint::AotKernel *tab = cjint::aot_table(&na);
@@ -917,7 +953,7 @@ bool lt_tensor_map(CUtensorMap *m, const void *in, int lin, long long D, long lo
 CJ_API cj_status cj_launch(cj_handle h, void *const *args, int64_t batch, void *cuda_stream) {
     if (!G.inited) return fail(CJ_ERR_NOT_INITIALIZED, "cj_init has not been called");
     if (!h || !args || batch < 0) return fail(CJ_ERR_INVALID_ARG, "null handle/args or negative batch");
-    for (int i = 0; i < (is_lt(h->kernel) ? 5 : h->kernel == CJ_K_UPDATE_CHAIN ? 3 : 4); ++i)
+    for (int i = 0; i < (is_lt(h->kernel) ? 5 : h->kernel == CJ_K_UPDATE_CHAIN ? 3 : 4); ++i)   // Eigen: 4
         if (!args[i]) return fail(CJ_ERR_INVALID_ARG, "argument %d is null", i);
     if (is_lt(h->kernel) && !(h->a.flags & CJ_FLAG_GENERIC) && ((h->a.tile[3] >> 16) & 0xf) >= 3) {
         // tile modes 3-5 move `in` and `out` in 16-byte vectors
@@ -946,6 +982,23 @@ CJ_API cj_status cj_launch(cj_handle h, void *const *args, int64_t batch, void *
             r = drv.LaunchKernel(im->fn, grid, 1, 1, im->threads, 1, 1, (unsigned)im->smem, st, p, nullptr);
         } else {
             void *p[] = {&A, &X, &b, &steps, &c};
+            r = drv.LaunchKernel(im->fn, grid, 1, 1, im->threads, 1, 1, (unsigned)im->smem, st, p, nullptr);
+        }
+    } else if (is_eig(h->kernel)) {
+        void *M0 = *reinterpret_cast<void *const *>(args[0]);
+        void *M = *reinterpret_cast<void *const *>(args[1]);
+        int rep = *reinterpret_cast<const int32_t *>(args[2]);
+        double c = *reinterpret_cast<const double *>(args[3]);
+        if (!M0 || !M || rep < 0) return fail(CJ_ERR_INVALID_ARG, "null M0/M or negative repeat");
+        if (batch == 0) return CJ_OK;
+        long long b = batch;
+        const unsigned grid = (unsigned)((batch + im->ipb - 1) / im->ipb);
+        if (im->variant == V_GENERIC) {
+            int n = a.n, ipb = im->ipb;
+            void *p[] = {&M0, &M, &b, &rep, &c, &n, &ipb};
+            r = drv.LaunchKernel(im->fn, grid, 1, 1, im->threads, 1, 1, (unsigned)im->smem, st, p, nullptr);
+        } else {
+            void *p[] = {&M0, &M, &b, &rep, &c};
             r = drv.LaunchKernel(im->fn, grid, 1, 1, im->threads, 1, 1, (unsigned)im->smem, st, p, nullptr);
         }
     } else if (is_lt(h->kernel)) {

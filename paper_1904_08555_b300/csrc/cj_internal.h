@@ -42,6 +42,7 @@ struct GenericKernels {
     const void *chain[2];
     const void *ltimes[2];
     const void *grouped[2];
+    const void *eigen[2];
 };
 const GenericKernels &generic_kernels();
 

@@ -70,6 +70,11 @@ CJ_HD constexpr long chain_smem(int n, int mapping, int ipb, int esize) {
                                         : 0L);
 }
 
+// Eigen recurrence (both kernels): two buffers of M per instance, rows of
+// n + 1 elements (odd: a warp's row writes spread over all banks).
+CJ_HD constexpr int eig_rp(int n) { return n + 1; }
+CJ_HD constexpr long eig_smem(int n, int ipb, int esize) { return 2L * ipb * n * eig_rp(n) * esize; }
+
 // Generic update chain: A pitch uses row_pitch; each thread keeps its row of
 // X and of the product in shared memory with pitch xrow_pitch(n).
 CJ_HD constexpr long chain_generic_smem(int n, int ipb, int threads, int esize) {

@@ -601,6 +601,123 @@ update_chain_generic(const T* __restrict__ A, T* __restrict__ X, long long batch
 }
 
 // ---------------------------------------------------------------------------
+// The paper's literal Eigen benchmark recurrence (Sec. 5, Listing eigen1):
+//     M_{k+1} = Ones + c (M_k + M_k M_k),   k = 0 .. R-1,   per instance,
+// the listing's case being c = 5e-5 and M_0(i, j) = i + N j, which the caller
+// passes.  Unlike the update chain, row i of M_{k+1} needs every row of M_k,
+// so a block keeps M_k of each of its instances in shared memory (two
+// buffers, rows of N + 1, one barrier per step); thread (instance, i) keeps
+// its own row in registers and reads the other rows as broadcasts.  Each
+// element is formed as 1 + c * (m + q) with a separate multiply and add, the
+// order the listing writes.  Row-major.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double eig_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float eig_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double eig_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float eig_add(float a, float b) { return __fadd_rn(a, b); }
+
+// Instances [0, ninst) of a block between global memory (contiguous, row-major)
+// and a shared-memory buffer with rows of eig_rp(n).
+template <class T>
+__device__ __forceinline__ void eig_load(T* buf, const T* __restrict__ g, int ninst, int n, int tid, int nthreads) {
+    const int rp = cjg::eig_rp(n), nn = n * n;
+    for (int e = tid; e < ninst * nn; e += nthreads) {
+        const int inst = e / nn, r = e - inst * nn, i = r / n;
+        buf[inst * n * rp + i * rp + (r - i * n)] = g[e];
+    }
+}
+template <class T>
+__device__ __forceinline__ void eig_store(T* __restrict__ g, const T* buf, int ninst, int n, int tid, int nthreads) {
+    const int rp = cjg::eig_rp(n), nn = n * n;
+    for (int e = tid; e < ninst * nn; e += nthreads) {
+        const int inst = e / nn, r = e - inst * nn, i = r / n;
+        g[e] = buf[inst * n * rp + i * rp + (r - i * n)];
+    }
+}
+
+template <class T, int N, int IPB>
+__global__ void __launch_bounds__(cjg::chain_threads(N, 1, IPB))
+eigen_recurrence(const T* __restrict__ M0, T* __restrict__ M, long long batch, int repeat, double c) {
+    constexpr int NN = N * N, NT = cjg::chain_threads(N, 1, IPB), RP = cjg::eig_rp(N), P = N * RP;
+    extern __shared__ __align__(16) unsigned char cj_smem[];
+    T* cur = reinterpret_cast<T*>(cj_smem);
+    T* nxt = cur + IPB * P;
+    const long long b0 = (long long)blockIdx.x * IPB;
+    if (b0 >= batch) return;
+    const int ninst = (batch - b0) < IPB ? (int)(batch - b0) : IPB;
+    const int tid = threadIdx.x;
+    eig_load<T>(cur, M0 + b0 * NN, ninst, N, tid, NT);
+    __syncthreads();
+    const int inst = tid / N, i = tid - inst * N;
+    const bool active = inst < ninst;
+    const T cc = (T)c;
+    T x[N];
+    if (active) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) x[j] = cur[inst * P + i * RP + j];
+    }
+    for (int k = 0; k < repeat; ++k) {
+        if (active) {
+            const T* m = opaque_base(cur, inst * P);
+            T q[N];
+#pragma unroll
+            for (int j = 0; j < N; ++j) q[j] = T(0);
+#pragma unroll
+            for (int l = 0; l < N; ++l) {
+                const T xl = x[l];
+#pragma unroll
+                for (int j = 0; j < N; ++j) q[j] = fmaT(xl, m[l * RP + j], q[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                x[j] = eig_add(T(1), eig_mul(cc, eig_add(x[j], q[j])));
+                nxt[inst * P + i * RP + j] = x[j];
+            }
+        }
+        __syncthreads();   // M_{k+1} complete; M_k no longer read
+        T* t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    eig_store<T>(M + b0 * NN, cur, ninst, N, tid, NT);
+}
+
+// Generic: run-time n (1..64) and instances per block; every row in shared memory.
+template <class T>
+__global__ void __launch_bounds__(256)
+eigen_recurrence_generic(const T* __restrict__ M0, T* __restrict__ M, long long batch, int repeat, double c, int n,
+                         int ipb) {
+    extern __shared__ __align__(16) unsigned char cj_smem[];
+    const int rp = cjg::eig_rp(n), p = n * rp, nn = n * n;
+    T* cur = reinterpret_cast<T*>(cj_smem);
+    T* nxt = cur + ipb * p;
+    const long long b0 = (long long)blockIdx.x * ipb;
+    if (b0 >= batch) return;
+    const int ninst = (batch - b0) < ipb ? (int)(batch - b0) : ipb;
+    const int tid = threadIdx.x, nthreads = blockDim.x;
+    eig_load<T>(cur, M0 + b0 * nn, ninst, n, tid, nthreads);
+    __syncthreads();
+    const int inst = tid / n, i = tid - inst * n;
+    const bool active = inst < ninst;
+    const T cc = (T)c;
+    for (int k = 0; k < repeat; ++k) {
+        if (active) {
+            const T* m = cur + inst * p;
+            for (int j = 0; j < n; ++j) {
+                T s = T(0);
+                for (int l = 0; l < n; ++l) s = fmaT(m[i * rp + l], m[l * rp + j], s);
+                nxt[inst * p + i * rp + j] = eig_add(T(1), eig_mul(cc, eig_add(m[i * rp + j], s)));
+            }
+        }
+        __syncthreads();
+        T* t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    eig_store<T>(M + b0 * nn, cur, ninst, n, tid, nthreads);
+}
+
+// ---------------------------------------------------------------------------
 // Grouped persistent kernel: instances of one size N with different step
 // counts, listed in a work list (sorted by T descending by the host).  Each
 // block repeatedly takes the next chunk of IPB consecutive items from a

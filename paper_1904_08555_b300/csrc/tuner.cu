@@ -199,7 +199,11 @@ void featurize(int k, const cj_template_args &a0, int64_t batch, int32_t steps, 
 cj_status candidates(int k, const cj_template_args &a, std::vector<std::array<int, 4>> &out) {
     out.clear();
     if (k == CJ_K_LTIMES || k == CJ_K_LPLUSTIMES) ltimes_candidates(lt_swapped(k, a), out);
-    else chain_candidates(a, out);
+    else if (k == CJ_K_EIGEN_RECURRENCE) {
+        for (int ipb : {1, 2, 4, 8, 16, 32, 64})
+            if (cjg::chain_threads(a.n, 1, ipb) <= 1024 && cjg::eig_smem(a.n, ipb, esize(a.dtype)) <= 200 * 1024)
+                out.push_back({1, ipb, 0, 0});
+    } else chain_candidates(a, out);
     if (out.empty()) return tfail(CJ_ERR_INVALID_ARG, "no candidate tile fits these arguments");
     return CJ_OK;
 }

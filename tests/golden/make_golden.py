@@ -38,6 +38,9 @@ REQUESTS = [
     (K.K_UPDATE_CHAIN_GROUPED, K.F32, 3, 1, 0, 0, 0, (0, 0, 0, 0), 0),  # layout forced 0
     (K.K_UPDATE_CHAIN_GROUPED, K.F32, 45, 0, 0, 0, 0, (0, 0, 0, 0), 0),  # one large instance per block
     (K.K_UPDATE_CHAIN, K.F64, 8, 0, 0, 0, 0, (0, 0, 0, 0), K.FLAG_INJECT_COMPILE_ERROR),
+    (K.K_EIGEN_RECURRENCE, K.F64, 16, 1, 2, 36, 96, (0, 0, 0, 0), 0),   # unused fields zeroed
+    (K.K_EIGEN_RECURRENCE, K.F32, 32, 0, 0, 0, 0, (0, 0, 0, 0), 0),
+    (K.K_EIGEN_RECURRENCE, K.F64, 3, 0, 0, 0, 0, (0, 0, 0, 0), K.FLAG_GENERIC),
 ]
 
 

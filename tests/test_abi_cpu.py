@@ -104,6 +104,10 @@ def test_aot_sizes_are_not_compiled(compile_only_sync):
     dict(kernel=cj.K_UPDATE_CHAIN, dtype=cj.F64, n=8, flags=0x200),
     dict(kernel=cj.K_LTIMES, dtype=cj.F32, m=36, d=96, flags=0x200 | 0x1),
     dict(kernel=cj.K_LTIMES, dtype=cj.F32, m=36, d=96, tile=(1, 64, 96, (1 << 20) | (2 << 8) | 12), flags=0x200),
+    dict(kernel=cj.K_EIGEN_RECURRENCE, dtype=cj.F64, n=33),
+    dict(kernel=cj.K_EIGEN_RECURRENCE, dtype=cj.BF16, n=8),
+    dict(kernel=cj.K_EIGEN_RECURRENCE, dtype=cj.F64, n=8, tile=(2, 4, 0, 0)),
+    dict(kernel=cj.K_EIGEN_RECURRENCE, dtype=cj.F64, n=8, tile=(1, 200, 0, 0)),
     dict(kernel=9, dtype=cj.F64, n=4),
 ])
 def test_invalid_arguments(compile_only_sync, kw):
@@ -260,3 +264,15 @@ def test_vectorised_ltimes_tiles_reject_misaligned_tensors(compile_only_sync):
     with pytest.raises(cj.CJError) as e:                         # aligned: reaches the device check
         cj.launch_ltimes(h, 1 << 19, 1 << 20, 1 << 21, 8, 64)
     assert e.value.status == cj.CJ_ERR_NO_DEVICE
+
+
+def test_eigen_recurrence_requests(compile_only_sync):
+    """Kernel 5 compiles for n = 1..32 in f64 and f32 (a sample), its key zeroes
+    the unused fields, and its candidates are all valid requests."""
+    for n in (1, 2, 7, 16, 32):
+        for dt in (cj.F64, cj.F32):
+            h = cj.specialize(cj.K_EIGEN_RECURRENCE, dt, n=n, layout_a=1, m=5, d=7)
+            key = bytes.fromhex(h.key_hex)
+            assert key[3:5] == bytes(2) and key[8:12] == bytes(4) and h.variant == "jit"
+            for tile in cj.candidates(cj.K_EIGEN_RECURRENCE, dt, n=n):
+                cj.specialize(cj.K_EIGEN_RECURRENCE, dt, n=n, tile=tile)

@@ -164,3 +164,32 @@ def test_paper_eigen_recurrence_exact_small():
         M = [[1 + h * (M[i][j] + Q[i][j]) for j in range(n)] for i in range(n)]
     ref = np.array([[float(v) for v in r] for r in M])
     assert relF(oracle.eigen_bench(n, rep), ref) <= 1e-15
+
+
+@pytest.mark.parametrize("n,rep", [(1, 3), (2, 2), (3, 2)])
+def test_eigen_recurrence_batched_exact_small(n, rep):
+    """The batched form against exact rational arithmetic on random integer
+    starts (each step: Q = M M, then M = 1 + c (M + Q) with the double nearest
+    the given c)."""
+    rng = np.random.default_rng(n * 10 + rep)
+    M0 = rng.integers(-4, 5, size=(3, n, n)).astype(np.float64)
+    h = Fraction(3e-3)
+    got = oracle.eigen_recurrence(M0, rep, 3e-3)
+    for b in range(3):
+        M = [[Fraction(int(M0[b, i, j])) for j in range(n)] for i in range(n)]
+        for _ in range(rep):
+            Q = [[sum(M[i][l] * M[l][j] for l in range(n)) for j in range(n)] for i in range(n)]
+            M = [[1 + h * (M[i][j] + Q[i][j]) for j in range(n)] for i in range(n)]
+        ref = np.array([[float(v) for v in r] for r in M])
+        assert relF(got[b], ref) <= 1e-15
+
+
+def test_eigen_recurrence_special_cases():
+    """Zero repeats copy the start; c = 0 gives Ones after one step exactly;
+    the listing's start reproduces the literal single-matrix loop bit for bit."""
+    M0 = synth.uniform_np(7, 0, 2 * 5 * 5).reshape(2, 5, 5)
+    np.testing.assert_array_equal(oracle.eigen_recurrence(M0, 0), M0)
+    np.testing.assert_array_equal(oracle.eigen_recurrence(M0, 1, 0.0), np.ones_like(M0))
+    for n, rep in ((4, 5), (16, 3)):
+        start = oracle.eigen_start(n)[None]
+        np.testing.assert_array_equal(oracle.eigen_recurrence(start, rep)[0], oracle.eigen_bench(n, rep))
