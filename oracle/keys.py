@@ -86,10 +86,11 @@ def default_tile(kernel: int, dtype: int, n: int, layout_a: int = 0, layout_b: i
                  d: int = 96) -> tuple:
     if kernel == K_EIGEN_RECURRENCE:
         # one thread per row, max(1, 128 // n) instances per block, fewer while
-        # the two buffers (rows of n + 1 elements) exceed 96 KiB
+        # the two buffers exceed 96 KiB; a row is an odd number of 16-byte units
         es = 8 if dtype == F64 else 4
+        rp = ((-(-n * es // 16)) | 1) * 16 // es
         ipb = max(1, 128 // n)
-        while ipb > 1 and 2 * ipb * n * (n + 1) * es > 96 * 1024:
+        while ipb > 1 and 2 * ipb * n * rp * es > 96 * 1024:
             ipb -= 1
         return (1, ipb, 0, 0)
     if kernel == K_UPDATE_CHAIN_GROUPED and dtype == F32 and n >= 17:

@@ -70,10 +70,13 @@ CJ_HD constexpr long chain_smem(int n, int mapping, int ipb, int esize) {
                                         : 0L);
 }
 
-// Eigen recurrence (both kernels): two buffers of M per instance, rows of
-// n + 1 elements (odd: a warp's row writes spread over all banks).
-CJ_HD constexpr int eig_rp(int n) { return n + 1; }
-CJ_HD constexpr long eig_smem(int n, int ipb, int esize) { return 2L * ipb * n * eig_rp(n) * esize; }
+// Eigen recurrence (both kernels): two buffers of M per instance.  Rows are
+// a whole, odd number of 16-byte units: 16-byte aligned for vector reads of a
+// row, and consecutive rows start in different bank groups.
+CJ_HD constexpr int eig_rp(int n, int esize) {
+    return ((n * esize + 15) / 16 | 1) * 16 / esize;
+}
+CJ_HD constexpr long eig_smem(int n, int ipb, int esize) { return 2L * ipb * n * eig_rp(n, esize) * esize; }
 
 // Generic update chain: A pitch uses row_pitch; each thread keeps its row of
 // X and of the product in shared memory with pitch xrow_pitch(n).

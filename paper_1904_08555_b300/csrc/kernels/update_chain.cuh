@@ -617,10 +617,10 @@ __device__ __forceinline__ double eig_add(double a, double b) { return __dadd_rn
 __device__ __forceinline__ float eig_add(float a, float b) { return __fadd_rn(a, b); }
 
 // Instances [0, ninst) of a block between global memory (contiguous, row-major)
-// and a shared-memory buffer with rows of eig_rp(n).
+// and a shared-memory buffer with rows of eig_rp(n, sizeof(T)).
 template <class T>
 __device__ __forceinline__ void eig_load(T* buf, const T* __restrict__ g, int ninst, int n, int tid, int nthreads) {
-    const int rp = cjg::eig_rp(n), nn = n * n;
+    const int rp = cjg::eig_rp(n, (int)sizeof(T)), nn = n * n;
     for (int e = tid; e < ninst * nn; e += nthreads) {
         const int inst = e / nn, r = e - inst * nn, i = r / n;
         buf[inst * n * rp + i * rp + (r - i * n)] = g[e];
@@ -628,7 +628,7 @@ __device__ __forceinline__ void eig_load(T* buf, const T* __restrict__ g, int ni
 }
 template <class T>
 __device__ __forceinline__ void eig_store(T* __restrict__ g, const T* buf, int ninst, int n, int tid, int nthreads) {
-    const int rp = cjg::eig_rp(n), nn = n * n;
+    const int rp = cjg::eig_rp(n, (int)sizeof(T)), nn = n * n;
     for (int e = tid; e < ninst * nn; e += nthreads) {
         const int inst = e / nn, r = e - inst * nn, i = r / n;
         g[e] = buf[inst * n * rp + i * rp + (r - i * n)];
@@ -638,7 +638,7 @@ __device__ __forceinline__ void eig_store(T* __restrict__ g, const T* buf, int n
 template <class T, int N, int IPB>
 __global__ void __launch_bounds__(cjg::chain_threads(N, 1, IPB))
 eigen_recurrence(const T* __restrict__ M0, T* __restrict__ M, long long batch, int repeat, double c) {
-    constexpr int NN = N * N, NT = cjg::chain_threads(N, 1, IPB), RP = cjg::eig_rp(N), P = N * RP;
+    constexpr int NN = N * N, NT = cjg::chain_threads(N, 1, IPB), RP = cjg::eig_rp(N, (int)sizeof(T)), P = N * RP;
     extern __shared__ __align__(16) unsigned char cj_smem[];
     T* cur = reinterpret_cast<T*>(cj_smem);
     T* nxt = cur + IPB * P;
@@ -665,8 +665,22 @@ eigen_recurrence(const T* __restrict__ M0, T* __restrict__ M, long long batch, i
 #pragma unroll
             for (int l = 0; l < N; ++l) {
                 const T xl = x[l];
+                // row l of M_k (a broadcast within the instance) in 16-byte vectors
+                constexpr int V = 16 / (int)sizeof(T);
 #pragma unroll
-                for (int j = 0; j < N; ++j) q[j] = fmaT(xl, m[l * RP + j], q[j]);
+                for (int q4 = 0; q4 < (N + V - 1) / V; ++q4) {
+                    T w[V];
+                    if constexpr (V == 4) {
+                        const float4 t = reinterpret_cast<const float4*>(m + l * RP)[q4];
+                        w[0] = t.x; w[1] = t.y; w[2] = t.z; w[3] = t.w;
+                    } else {
+                        const double2 t = reinterpret_cast<const double2*>(m + l * RP)[q4];
+                        w[0] = t.x; w[1] = t.y;
+                    }
+#pragma unroll
+                    for (int e = 0; e < V; ++e)
+                        if (V * q4 + e < N) q[V * q4 + e] = fmaT(xl, w[e], q[V * q4 + e]);
+                }
             }
 #pragma unroll
             for (int j = 0; j < N; ++j) {
@@ -688,7 +702,7 @@ __global__ void __launch_bounds__(256)
 eigen_recurrence_generic(const T* __restrict__ M0, T* __restrict__ M, long long batch, int repeat, double c, int n,
                          int ipb) {
     extern __shared__ __align__(16) unsigned char cj_smem[];
-    const int rp = cjg::eig_rp(n), p = n * rp, nn = n * n;
+    const int rp = cjg::eig_rp(n, (int)sizeof(T)), p = n * rp, nn = n * n;
     T* cur = reinterpret_cast<T*>(cj_smem);
     T* nxt = cur + ipb * p;
     const long long b0 = (long long)blockIdx.x * ipb;
