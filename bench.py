@@ -427,15 +427,9 @@ def main():
             return []
         gi, go = lin in (1, 4), lout in (1, 4)
         tg = 1 if not (gi or go) else (8 if (gi and lout in (0, 2)) or (go and lin in (0, 2)) else 32)
-        return [("tma_b4", (tg, 128 // tg, 32 * 14, (4 << 20) | (5 << 16) | (2 << 8) | 8)),
-                ("tma_b3", (tg, 128 // tg, 32 * 14, (3 << 20) | (5 << 16) | (2 << 8) | 8)),
-                ("tma_b4c4", (tg, 128 // tg, 32 * 10, (4 << 20) | (5 << 16) | (2 << 8) | 4)),
-                ("tc_s2p8", (tg, 128 // tg, 32 * 13, (4 << 16) | (2 << 8) | 8)),
+        return [("tc_s2p8", (tg, 128 // tg, 32 * 13, (4 << 16) | (2 << 8) | 8)),
                 ("tf32x3", (tg, 64 // tg, 128, (1 << 20) | (2 << 16) | (1 << 8) | 8)),
-                ("direct_r2", (tg, 256 // tg, 128, (3 << 16) | (2 << 8))),
-                ("direct_r1", (tg, 128 // tg, 128, (3 << 16) | (1 << 8))),
-                ("direct_r2_s12", (tg, 128 // tg, 192, (3 << 16) | (2 << 8) | 12)),
-                ("direct_r4_s12", (tg, 256 // tg, 192, (3 << 16) | (4 << 8) | 12))]
+                ("direct_r2", (tg, 256 // tg, 128, (3 << 16) | (2 << 8)))]
     args.lt_alt_tiles = lt_alt_tiles
     if args.impl == "reference":
         reference_arm(args)
