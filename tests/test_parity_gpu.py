@@ -502,27 +502,31 @@ def test_grouped_handle_direct_launch():
 # Full-size launches, checked on seeded samples
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("n", [3, 32])
-def test_full_size_sweep_sampled(n):
+@pytest.mark.parametrize("n,dt", [(3, cj.F64), (32, cj.F64), (12, cj.F32), (32, cj.F32)])
+def test_full_size_sweep_sampled(n, dt):
     steps = 64
     batch = synth.chain_batch(n)
-    A = synth.chain_inputs_torch(synth.SEED_CHAIN_SWEEP, batch, n, "cuda")
+    A = synth.chain_inputs_torch(synth.SEED_CHAIN_SWEEP, batch, n, "cuda").to(tdtype(dt))
     X = torch.empty_like(A)
-    h = cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=n, flags=cj.FLAG_NO_AOT)
+    h = cj.specialize(cj.K_UPDATE_CHAIN, dt, n=n, flags=cj.FLAG_NO_AOT)
     cj.launch_update_chain(h, A, X, steps)
     torch.cuda.synchronize()
     rng = np.random.default_rng(17)
     idx = np.unique(np.concatenate([[0, batch - 1], rng.integers(0, batch, 300)]))
     idx_t = torch.from_numpy(idx).cuda()
-    a_s = A[idx_t].cpu().numpy()
-    np.testing.assert_array_equal(a_s[0], synth.chain_inputs_np(synth.SEED_CHAIN_SWEEP, 1, n)[0])
+    a_s = A[idx_t].double().cpu().numpy()
+    if dt == cj.F64:
+        np.testing.assert_array_equal(a_s[0], synth.chain_inputs_np(synth.SEED_CHAIN_SWEEP, 1, n)[0])
     ref = oracle.update_chain(a_s, steps, nthreads=8)
-    assert relF_per_instance(X[idx_t].cpu().numpy(), ref) <= TOL64
+    assert relF_per_instance(X[idx_t].double().cpu().numpy(), ref) <= (TOL64 if dt == cj.F64 else TOL32)
     del A, X
 
 
-@pytest.mark.parametrize("dt,lin,lout", [(cj.F64, 0, 3), (cj.F32, 4, 5)])
+@pytest.mark.parametrize("dt,lin,lout", [(cj.F64, 0, 3), (cj.F32, 4, 5), (cj.F32, 0, 0), (cj.F32, 1, 2),
+                                         (cj.F32, 3, 4)])
 def test_full_size_ltimes_sampled(dt, lin, lout):
+    """Full size (Z = 2^18) in the bench's launch configuration (the default
+    tile: f32 = tensor cores fed by TMA), checked on 400 sampled columns."""
     M, D, G, Z = 36, 96, 32, 1 << 18
     L, _ = synth.ltimes_inputs_np(synth.SEED_LTIMES, M, D, 1, 1)
     x = synth.uniform_torch(synth.SEED_LTIMES, synth.STREAM_A, D * G * Z, "cuda").view(D, G, Z)
@@ -531,8 +535,12 @@ def test_full_size_ltimes_sampled(dt, lin, lout):
     Lt = torch.from_numpy(L).to("cuda", tdtype(dt))
     out = torch.empty(M * G * Z, device="cuda", dtype=tdtype(dt))
     h = cj.specialize(cj.K_LTIMES, dt, layout_a=lin, layout_b=lout, m=M, d=D)
+    tma0 = cj.stats()["launches_tma"]
     cj.launch_ltimes(h, Lt, xin, out, G, Z)
     torch.cuda.synchronize()
+    assert cj.stats()["launches_tma"] - tma0 == (1 if dt == cj.F32 else 0)
+    if dt == cj.F32:
+        assert h.wait_timeouts() == 0
     rng = np.random.default_rng(5)
     gs = rng.integers(0, G, 400)
     zs = rng.integers(0, Z, 400)
