@@ -407,7 +407,8 @@ def main():
                    help="sweep (default): the FP64 size sweep; the others are secondary measurements")
     p.add_argument("--dtype", choices=("f64", "f32", "bf16"), default="f64", help="ltimes / uneven precision")
     p.add_argument("--ltimes-z", type=int, default=1 << 18)
-    p.add_argument("--kernel", choices=("chain", "chain-generic", "ltimes", "ltimes-generic"), default="chain")
+    p.add_argument("--kernel", choices=("chain", "chain-generic", "ltimes", "ltimes-generic", "eigen", "eigen-generic"),
+                   default="chain")
     p.add_argument("--n", type=int, default=32)
     p.add_argument("--batch", type=int, default=16384)
     p.add_argument("--layout-in", type=int, default=0)
@@ -620,11 +621,20 @@ def secondary(args):
                                "flops": f, "groups": int(len(np.unique(n)))}})
     elif args.workload == "kernel":
         # one kernel on a small case (inputs above L2), for profiler captures
-        dt = cj.F64 if args.dtype == "f64" else cj.F32
-        tdt = torch.float64 if dt == cj.F64 else torch.float32
+        dt = {"f64": cj.F64, "f32": cj.F32, "bf16": cj.BF16}[args.dtype]
+        tdt = torch.float64 if dt == cj.F64 else torch.float32     # bf16 chains keep fp32 state
         generic = args.kernel.endswith("-generic")
         fl = cj.FLAG_GENERIC if generic else cj.FLAG_NO_AOT
-        if args.kernel.startswith("chain"):
+        if args.kernel.startswith("eigen"):
+            n, b = args.n, args.batch
+            M0 = synth.uniform_torch(synth.SEED_CHAIN_SWEEP, synth.STREAM_A, b * n * n, "cuda").to(tdt)
+            Mo = torch.empty_like(M0)
+            h = cj.specialize(cj.K_EIGEN_RECURRENCE, dt, n=n, flags=cj.FLAG_GENERIC if generic else 0,
+                              tile=tuple(args.tile) if args.tile else (0, 0, 0, 0))
+            fn = lambda: cj.launch_eigen(h, M0, Mo, T_STEPS, 5e-5, batch=b, stream=stream)
+            f = float(b) * T_STEPS * (2.0 * n ** 3 + 3.0 * n ** 2)
+            desc = f"Eigen recurrence N={n} batch={b} repeats={T_STEPS} {args.dtype} {'generic' if generic else 'jit'}"
+        elif args.kernel.startswith("chain"):
             n, b = args.n, args.batch
             A = synth.uniform_torch(synth.SEED_CHAIN_SWEEP, synth.STREAM_A, b * n * n, "cuda").view(b, n, n).to(tdt)
             X = torch.empty_like(A)
