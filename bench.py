@@ -58,7 +58,7 @@ PEAK_TFLOPS = {"f64": 1.25, "f32": 148 * 128 * 2 * 2.032e9 / 1e12}
 # profiles/update_chain_f64_n32_fma_pipe.md (16384 instances, scaled by the
 # instance count; the kernel's traffic grows in proportion).  None for any
 # other kernel: the counters then do not describe it.
-TRAFFIC_PER_INSTANCE = {"update_chain<double, 32, 0, 1, 8>": (135.372288e6 + 88.970752e6) / 16384}
+TRAFFIC_PER_INSTANCE = {"update_chain<double, 32, 0, 1, 8>": (135.625472e6 + 89.003520e6) / 16384}
 
 
 def measured_peak(key: str, default: float) -> float:
