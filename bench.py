@@ -607,8 +607,13 @@ def secondary(args):
         X = torch.empty_like(A)
         f = float(np.sum(t * (2.0 * n ** 3 + 2.0 * n ** 2)))
         res = {}
-        for name, fl in (("spec", 0), ("generic", cj.FLAG_GENERIC)):
+        changed = 0
+        for name, fl in (("default_tiles", 0), ("spec", 0), ("generic", cj.FLAG_GENERIC)):
             plan = cj.GroupPlan(dt, n, t, flags=fl)
+            if name == "spec":
+                # the plan's tiles chosen by its own autotuner (every candidate of the
+                # 16 most expensive groups timed on the group's own work list)
+                changed = plan.autotune(A, X, stream=stream, max_groups=16, reps=3)
             fn = lambda: plan.launch(A, X, stream=stream, use_graph=True)
             _events(torch, stream, fn, W)
             res[name] = _events(torch, stream, fn, max(K, 10))
@@ -616,11 +621,15 @@ def secondary(args):
         peak = measured_peak("bf16_tflops", 1800.0) if args.dtype == "bf16" else PEAK_TFLOPS[args.dtype]
         out.update({"value": f / res["spec"] / 1e6, "dtype": args.dtype,
                     "generic": {"value": f / res["generic"] / 1e6, "unit": "GFLOP/s", "ms": res["generic"]},
+                    "default_tiles": {"value": f / res["default_tiles"] / 1e6, "unit": "GFLOP/s",
+                                      "ms": res["default_tiles"]},
+                    "autotuned_groups_changed": changed,
                     "ms_per_launch": res["spec"], "speedup_vs_generic": res["generic"] / res["spec"],
                     "roofline": {"bound": "alu", "peak": peak, "unit": "TFLOP/s",
                                  "frac": f / res["spec"] / 1e9 / peak},
                     "config": {"workload": "uneven batch: 10,000 update chains, N log-uniform in [2,64], "
-                                           f"T uniform in [16,128], one grouped plan (CUDA graph), {args.dtype}",
+                                           f"T uniform in [16,128], one grouped plan (CUDA graph), autotuned tiles, "
+                                           f"{args.dtype}",
                                "flops": f, "groups": int(len(np.unique(n)))}})
     elif args.workload == "kernel":
         # one kernel on a small case (inputs above L2), for profiler captures

@@ -288,6 +288,19 @@ cj_status cj_group_plan_create(int32_t dtype, int64_t count, const int32_t *n, c
 cj_status cj_group_plan_launch(cj_group_plan p, const void *A_pool, void *X_pool, void *cuda_stream,
                                int use_graph);
 /* Groups in the plan and pool elements it expects. */
+/* Autotune a plan's tiles (the batching pattern's autotuned tiles): for each
+ * of the max_groups most expensive groups (0: all), every candidate tile of
+ * the grouped kernel (cj_candidates, at most 256 instances per chunk) is
+ * compiled and timed on the group's own work list on `stream` (median of reps
+ * launches after one warm-up, CUDA events); the fastest replaces the group's
+ * tile, and the next graph launch re-captures.  X_pool is written: every timed
+ * launch computes its group's instances.  *changed (may be NULL) receives the
+ * number of groups whose tile changed.  Synchronous; compiles run on the
+ * background threads in async mode.  CJ_ERR_INVALID_ARG: null plan or pools;
+ * CJ_ERR_NO_DEVICE in compile-only mode; CJ_ERR_CUDA if a launch or timing
+ * call failed. */
+cj_status cj_group_plan_autotune(cj_group_plan p, const void *A_pool, void *X_pool, void *cuda_stream,
+                                 int32_t max_groups, int32_t reps, int32_t *changed);
 cj_status cj_group_plan_info(cj_group_plan p, int32_t *n_groups, int64_t *pool_elems);
 cj_status cj_group_plan_destroy(cj_group_plan p);
 

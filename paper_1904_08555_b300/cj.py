@@ -22,7 +22,8 @@ CFG_COMPILE_ONLY = 0x1
 VARIANT_NAMES = ("generic", "aot", "jit")
 
 EXPORTS = ("cj_init", "cj_specialize", "cj_specialize_wait", "cj_launch", "cj_stats", "cj_handle_info",
-           "cj_handle_regs", "cj_handle_wait_timeouts", "cj_group_plan_create", "cj_group_plan_launch", "cj_group_plan_info",
+           "cj_handle_regs", "cj_handle_wait_timeouts", "cj_group_plan_create", "cj_group_plan_launch",
+           "cj_group_plan_autotune", "cj_group_plan_info",
            "cj_group_plan_destroy", "cj_measure_fma_peak", "cj_update_chain_uneven_noalloc", "cj_candidates",
            "cj_autotune", "cj_featurize", "cj_mlp_create", "cj_mlp_set_params", "cj_mlp_get_params",
            "cj_mlp_forward", "cj_mlp_grad", "cj_mlp_train_step", "cj_mlp_destroy", "cj_cost_model_use",
@@ -79,6 +80,7 @@ def load():
         L.cj_handle_wait_timeouts.argtypes = [P, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int]
         L.cj_group_plan_create.argtypes = [i32, i64, P, P, ctypes.c_uint32, ctypes.POINTER(P)]
         L.cj_group_plan_launch.argtypes = [P, P, P, P, ctypes.c_int]
+        L.cj_group_plan_autotune.argtypes = [P, P, P, P, i32, i32, ctypes.POINTER(i32)]
         L.cj_group_plan_info.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i64)]
         L.cj_group_plan_destroy.argtypes = [P]
         L.cj_measure_fma_peak.argtypes = [i32, i32, P, ctypes.POINTER(ctypes.c_double)]
@@ -284,6 +286,13 @@ class GroupPlan:
     def launch(self, A_pool, X_pool, stream=None, use_graph=True) -> None:
         _check(load().cj_group_plan_launch(self.ptr, _ptr(A_pool), _ptr(X_pool), _stream(stream, A_pool, X_pool),
                                            int(use_graph)), "cj_group_plan_launch")
+
+    def autotune(self, A_pool, X_pool, stream=None, max_groups: int = 0, reps: int = 3) -> int:
+        """Time every candidate tile per group (most expensive first) and keep the fastest; returns groups changed."""
+        ch = ctypes.c_int32(0)
+        _check(load().cj_group_plan_autotune(self.ptr, _ptr(A_pool), _ptr(X_pool), _stream(stream, A_pool, X_pool),
+                                             max_groups, reps, ctypes.byref(ch)), "cj_group_plan_autotune")
+        return ch.value
 
     def destroy(self) -> None:
         if self.ptr:

@@ -1265,6 +1265,83 @@ CJ_API cj_status cj_group_plan_launch(cj_group_plan p, const void *A_pool, void 
     return CJ_OK;
 }
 
+CJ_API cj_status cj_group_plan_autotune(cj_group_plan p, const void *A_pool, void *X_pool, void *cuda_stream,
+                                        int32_t max_groups, int32_t reps, int32_t *changed) {
+    if (!G.inited) return fail(CJ_ERR_NOT_INITIALIZED, "cj_init has not been called");
+    if (G.compile_only) return fail(CJ_ERR_NO_DEVICE, "compile-only mode");
+    if (!p || (p->pool_elems > 0 && (!A_pool || !X_pool)) || max_groups < 0)
+        return fail(CJ_ERR_INVALID_ARG, "null plan or pool, or negative group count");
+    if (reps < 1) reps = 3;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    const size_t ng = max_groups > 0 ? std::min<size_t>((size_t)max_groups, p->groups.size()) : p->groups.size();
+    int nchg = 0;
+    // 1. request every candidate tile of the tuned groups (the most expensive
+    //    first: groups are kept sorted by cost); in async mode they compile in
+    //    parallel on the background threads
+    std::vector<std::vector<cj_handle>> cand(ng);
+    for (size_t g = 0; g < ng; ++g) {
+        cj_template_args a{};
+        a.dtype = (p->dtype == CJ_BF16 && p->groups[g].n < 16) ? CJ_F32 : p->dtype;
+        a.n = p->groups[g].n;
+        int32_t tiles[4 * 16], cnt = 0;
+        if (cj_candidates(CJ_K_UPDATE_CHAIN_GROUPED, &a, tiles, 16, &cnt) != CJ_OK) continue;
+        for (int32_t c = 0; c < cnt; ++c) {
+            if (tiles[4 * c + 1] > 256) continue;   // grouped chunks hold at most 256 instances
+            cj_template_args t = a;
+            for (int i = 0; i < 4; ++i) t.tile[i] = tiles[4 * c + i];
+            cj_handle h = nullptr;
+            if (cj_specialize(CJ_K_UPDATE_CHAIN_GROUPED, &t, &h) == CJ_OK) cand[g].push_back(h);
+        }
+    }
+    // 2. time each compiled candidate on the group's own work list (counter
+    //    reset before every launch; each launch writes correct X for the group)
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return fail(CJ_ERR_CUDA, "event creation failed");
+    cj_status rc = CJ_OK;
+    for (size_t g = 0; g < ng && rc == CJ_OK; ++g) {
+        auto &gr = p->groups[g];
+        void *items = p->d_items + 3 * gr.first_item;
+        void *counter = p->d_counters + g;
+        const void *a = A_pool;
+        void *x = X_pool;
+        void *args[4] = {&items, &a, &x, &counter};
+        float best = 0;
+        cj_handle best_h = nullptr;
+        for (cj_handle h : cand[g]) {
+            if (cj_specialize_wait(h, -1) != CJ_OK) continue;   // failed compiles are not candidates
+            std::vector<float> ms;
+            for (int r = 0; r <= reps && rc == CJ_OK; ++r) {    // r = 0 warms up
+                if (cudaMemsetAsync(counter, 0, sizeof(int), st) != cudaSuccess || cudaEventRecord(e0, st) != cudaSuccess)
+                    rc = fail(CJ_ERR_CUDA, "grouped autotune: memset/event failed");
+                else if ((rc = cj_launch(h, args, gr.n_items, st)) == CJ_OK) {
+                    float t = 0;
+                    if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                        cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
+                        rc = fail(CJ_ERR_CUDA, "grouped autotune: timing failed");
+                    else if (r > 0)
+                        ms.push_back(t);
+                }
+            }
+            if (rc != CJ_OK) break;
+            std::sort(ms.begin(), ms.end());
+            const float med = ms[ms.size() / 2];
+            if (!best_h || med < best) {
+                best = med;
+                best_h = h;
+            }
+        }
+        if (best_h && best_h != gr.h) {
+            gr.h = best_h;   // the next graph launch re-captures (the launch function changed)
+            ++nchg;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (changed) *changed = nchg;
+    return rc;
+}
+
 CJ_API cj_status cj_group_plan_info(cj_group_plan p, int32_t *n_groups, int64_t *pool_elems) {
     if (!p) return fail(CJ_ERR_INVALID_ARG, "null plan");
     if (n_groups) *n_groups = (int32_t)p->groups.size();

@@ -49,6 +49,11 @@ void chain_candidates(const cj_template_args &a, std::vector<std::array<int, 4>>
     auto ok = [&](int map, int ipb) {
         return cjg::chain_threads(n, map, ipb) <= 1024 && cjg::chain_smem(n, map, ipb, es) <= 200 * 1024;
     };
+    if (a.dtype == CJ_BF16) {   // mapping 3 is the only BF16 mapping
+        for (int ipb : {1, 2, 4, 8})
+            if (ok(3, ipb)) out.push_back({3, ipb, 0, 0});
+        return;
+    }
     if (a.dtype == CJ_F64 && n % 8 == 0 && n <= 32)
         for (int ipb : {1, 2, 4, 8})
             if (ok(4, ipb)) out.push_back({4, ipb, 0, 0});

@@ -473,6 +473,29 @@ def test_grouped_plan_uneven(dt, use_graph):
         plan.destroy()
 
 
+@pytest.mark.parametrize("dt", [cj.F64, cj.F32, cj.BF16])
+def test_grouped_plan_autotune_keeps_results(dt):
+    """Plan autotuning: every group's candidates are timed on its own work
+    list, the fastest is kept, the graph re-captures, results still match."""
+    n, t = synth.uneven_sizes(synth.SEED_UNEVEN, 300)
+    pool, off = synth.uneven_inputs_np(synth.SEED_UNEVEN, n)
+    ref = oracle.update_chain_uneven(n, t, off, pool)
+    plan = cj.GroupPlan(dt, n, t)
+    try:
+        A = torch.from_numpy(pool).to("cuda", tdtype(dt))
+        X = torch.full_like(A, float("nan"))
+        changed = plan.autotune(A, X, stream=torch.cuda.current_stream(), max_groups=6, reps=2)
+        assert 0 <= changed <= 6
+        X.fill_(float("nan"))
+        plan.launch(A, X, stream=torch.cuda.current_stream(), use_graph=True)
+        torch.cuda.synchronize()
+        Xh = X.double().cpu().numpy()
+        worst = max(relF(Xh[off[k]:off[k] + n[k] * n[k]], ref[off[k]:off[k] + n[k] * n[k]]) for k in range(len(n)))
+        assert worst <= {cj.F64: TOL64, cj.F32: TOL32, cj.BF16: 2e-2}[dt]
+    finally:
+        plan.destroy()
+
+
 def test_grouped_handle_direct_launch():
     """One grouped instantiation over a hand-built work list (n = 20)."""
     nn = 20
