@@ -337,8 +337,9 @@ bool cost_model_tile(int k, const cj_template_args &a, int *tile_out) {
 CJ_API cj_status cj_candidates(cj_kernel_id k, const cj_template_args *a, int32_t *tiles, int32_t cap,
                                int32_t *count) {
     if (!a || !count || (cap > 0 && !tiles)) return tfail(CJ_ERR_INVALID_ARG, "null argument");
-    if (k == CJ_K_UPDATE_CHAIN_GROUPED && a->dtype != CJ_F64 && a->dtype != CJ_F32)
-        return tfail(CJ_ERR_INVALID_ARG, "grouped candidates need f64 or f32");
+    if (a->dtype == CJ_BF16 && k != CJ_K_UPDATE_CHAIN && k != CJ_K_UPDATE_CHAIN_GROUPED)
+        return tfail(CJ_ERR_INVALID_ARG, "bf16 candidates exist for the update chain only");
+    if (a->dtype == CJ_BF16 && a->n < 16) return tfail(CJ_ERR_INVALID_ARG, "bf16 update chains need n >= 16");
     std::vector<std::array<int, 4>> cand;
     cj_status rc = candidates((int)k, *a, cand);
     if (rc != CJ_OK) return rc;
