@@ -481,7 +481,7 @@ void spec_geometry(const cj_handle_s *h, Impl &s) {
         const int mode = (a.tile[3] >> 16) & 0xf;
         s.threads = a.tile[2];
         if (mode == 5) {   // and its mode-4 twin
-            s.threads2 = 32 * (5 + (a.tile[3] & 0xff));
+            s.threads2 = 32 * (5 + std::min(a.tile[3] & 0xff, 8));
             s.smem2 = (size_t)cjg::lt_tc_smem(v.m, v.d, (a.tile[3] >> 8) & 0xff, a.tile[0], a.tile[1], v.lout);
         }
         s.smem = mode == 5   ? (size_t)cjg::lt_tc_smem(v.m, v.d, (a.tile[3] >> 8) & 0xff, a.tile[0], a.tile[1], v.lout,
@@ -503,8 +503,9 @@ std::string fallback_name_expression(const cj_handle_s *h) {
     if (!is_lt(h->kernel) || ((a.tile[3] >> 16) & 0xf) != 5) return "";
     const LtView v = lt_view(h->kernel, a);
     char buf[256];
+    // register producers split a stage's 8 direction quads over warps: at most 8 of them
     snprintf(buf, sizeof buf, "cj::ltimes_tc<%d, %d, %d, %d, %d, %d, %d, %d, 0, 0, %d, %d>", v.m, v.d, v.lin, v.lout,
-             a.tile[0], a.tile[1], (a.tile[3] >> 8) & 0xff, a.tile[3] & 0xff, v.acc,
+             a.tile[0], a.tile[1], (a.tile[3] >> 8) & 0xff, std::min(a.tile[3] & 0xff, 8), v.acc,
              (a.flags & CJ_FLAG_INJECT_WAIT_TIMEOUT) ? 1 : 0);
     return buf;
 }

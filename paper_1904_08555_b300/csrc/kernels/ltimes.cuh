@@ -655,7 +655,9 @@ ltimes_tc(const float* __restrict__ L, const float* __restrict__ in, float* __re
     constexpr unsigned B_SBO = (DP / 4) * 128u;
     // kind::tf32, FP32 accumulator, both operands K-major, N = NP, M = 128
     constexpr unsigned IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(NP >> 3) << 17) | ((128u >> 4) << 24);
-    static_assert(TG * TZ == BM && NP <= 256 && CH * PT * 4 == BM * KB && 8 % NPROD == 0, "tcgen05 LTimes tile");
+    // register producers split the 8 direction quads of a stage over warps; converters only need whole chunks
+    static_assert(TG * TZ == BM && NP <= 256 && CH * PT * 4 == BM * KB && (RAWST > 0 ? 32 : 8) % NPROD == 0,
+                  "tcgen05 LTimes tile");
     // a TMA box starts on a 16-byte boundary: its innermost extent (and so
     // every innermost coordinate, a multiple of it) is a multiple of 4 floats
     static_assert(RAWST == 0 || (lt_axis(LIN, 2) == 0 ? KB : lt_axis(LIN, 2) == 1 ? TG : TZ) % 4 == 0,
@@ -860,7 +862,7 @@ ltimes_tc(const float* __restrict__ L, const float* __restrict__ in, float* __re
         // fastest column axis has a multiple-of-4 extent, else scalars);
         // v[4 * uu + dd] holds direction 4 kq + dd.  d-fastest `in`: chunk q
         // of the stage is (row q >> 3, quad q & 7), a float4 along d.
-        constexpr int UPW = 8 / NPROD;
+        constexpr int UPW = 8 / NPROD > 0 ? 8 / NPROD : 1;
         const int wp = pt >> 5, c0 = 4 * (pt & 31);
         const long long fast_ext = G_FASTER ? G : Z;
         const bool vec4 = D_FAST ? (D % 4 == 0) : (fast_ext % 4 == 0 && (G_FASTER ? TG : TZ) % 4 == 0);
