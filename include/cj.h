@@ -296,7 +296,8 @@ cj_status cj_group_plan_launch(cj_group_plan p, const void *A_pool, void *X_pool
  * tile, and the next graph launch re-captures.  X_pool is written: every timed
  * launch computes its group's instances.  *changed (may be NULL) receives the
  * number of groups whose tile changed.  Synchronous; compiles run on the
- * background threads in async mode.  CJ_ERR_INVALID_ARG: null plan or pools;
+ * background threads in async mode.  Not to be called while another thread
+ * launches or destroys the same plan.  CJ_ERR_INVALID_ARG: null plan or pools;
  * CJ_ERR_NO_DEVICE in compile-only mode; CJ_ERR_CUDA if a launch or timing
  * call failed. */
 cj_status cj_group_plan_autotune(cj_group_plan p, const void *A_pool, void *X_pool, void *cuda_stream,
