@@ -7,35 +7,46 @@ strings} (Sec. 4, Algorithm 1, first step); our key is the byte image of the
 same information for a fixed set of kernel templates:
 
   offset size field
-  0      u16  kernel id (1 update chain, 2 LTimes, 3 grouped update chain, 4 LPlusTimes)
+  0      u16  kernel id (1 update chain, 2 LTimes, 3 grouped update chain,
+                          4 LPlusTimes, 5 Eigen recurrence)
   2      u8   dtype (0 f64, 1 f32, 2 bf16 operands / f32 state)
   3      u8   layout_a (chain: 0 row-major, 1 column-major; LTimes: in order 0..5)
   4      u8   layout_b (LTimes: out order 0..5; else 0)
   5      u8   reserved, 0
-  6      u16  n (chain matrix size; else 0)
+  6      u16  n (chain / Eigen matrix size; else 0)
   8      u16  m (LTimes moments; else 0)
   10     u16  d (LTimes directions; else 0)
   12     u32x4 tile parameters after default resolution
-  28     u32  flags that select code (GENERIC, NO_AOT, INJECT_COMPILE_ERROR)
+  28     u32  flags that select code (GENERIC, NO_AOT, INJECT_COMPILE_ERROR,
+              INJECT_WAIT_TIMEOUT)
 
 All little-endian.  Fields that a kernel does not use are zeroed, so requests
 differing only there share an instantiation.
 
 Default tile resolution (tile all zero, no cost model):
-  update chain / grouped, f64 or f32:  n <= 4 -> (2 = instance per thread, 128, 0, 0)
-                                       else   -> (1 = row per thread, ipb, 0, 0)
-                                       with ipb = max(1, 256 // n) for n <= 32,
-                                       max(1, 128 // n) above
-  update chain, bf16:                  (3 = bf16 tensor-core panels, max(1, 128 // n16), 0, 0),
-                                       n16 = n rounded up to a multiple of 16
-  LTimes: (TG, TZ, threads, (PIPE << 20) | (MODE << 16) | (R << 8) | S), CT = 64
-      columns; orders 1, 4 are g-fast and 0, 2 z-fast; TG = 1 if neither in
-      nor out is g-fast, 8 if one is g-fast and the other z-fast, else 32;
-      TZ = CT / TG; f64: R 1, S 9, threads 64 * ceil(m / 9); f32: pipelined,
-      tile[3] = (1 << 20) | (2 << 8) | 12, threads 32 * ceil(m / 12).
+  update chain / grouped, bf16:   (3 = bf16 tensor-core panels, max(1, 128 // n16), 0, 0),
+                                  n16 = n rounded up to a multiple of 16
+  f64 or f32, n <= 4:             (2 = instance per thread, 128, 0, 0)
+  grouped f32, n >= 17:           (5 = 4x4 register blocks, 1, 0, 0)
+  f32, n >= 9:                    (6 = two rows per thread, max(1, 128 // ceil(n / 2)), 0, 0)
+  otherwise:                      (1 = row per thread, ipb, 0, 0) with
+                                  ipb = max(1, 256 // n) for n <= 32, max(1, 128 // n) above
+  Eigen recurrence: (1, ipb, 0, 0), ipb = max(1, 128 // n), lowered while the
+      two shared buffers (rows padded to an odd number of 16-byte units)
+      exceed 96 KiB.
+  LTimes: (TG, TZ, threads, (PIPE << 20) | (MODE << 16) | (R << 8) | S);
+      orders 1, 4 are g-fast and 0, 2 z-fast; TG = 1 if neither in nor out
+      is g-fast, 8 if one is g-fast and the other z-fast, else 32.
+      f32 with m <= 128: TZ = 128 // TG; mode 5 (TMA-fed tcgen05, R 2, S 8,
+      448 threads) with the largest PIPE in (4, 3, 2) whose shared memory
+      fits 220 KiB, else mode 4 (R 2, S 8, 416 threads) if that fits.
+      Otherwise CT = 64 columns, TZ = CT // TG; f64: R 1, S 9, threads
+      64 * ceil(m / 9); f32: PIPE 1, R 2, S 12, threads 32 * ceil(m / 12).
+  LPlusTimes: the LTimes default of the swapped problem (orders exchanged,
+      m and d exchanged).
 Expected variant: GENERIC flag -> generic; else update chain f64/f32 with
-n in {4, 8, 16, 32}, default tile, AoT set enabled and no NO_AOT flag -> aot;
-else jit.
+n in {4, 8, 16, 32}, default tile, AoT set enabled and neither NO_AOT nor
+INJECT_COMPILE_ERROR -> aot; else jit.
 """
 from __future__ import annotations
 

@@ -7,7 +7,6 @@ import os
 import re
 import subprocess
 import sys
-import textwrap
 
 import numpy as np
 import pytest

@@ -27,7 +27,7 @@ def test_generic_flag_drops_tile_and_keeps_flag():
 
 
 def test_golden_file_is_current():
-    import os, subprocess, sys
+    import os
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     with open(os.path.join(root, "tests", "golden", "keys.txt")) as f:
         before = f.read()
