@@ -14,14 +14,22 @@
  *   oracle_update_chain   -- the batched update chain of the paper's Eigen
  *                            benchmark (Sec. 5, Listings eigen1/eigen2),
  *                            in the stable form X_{k+1} = X_k + c X_k A.
+ *   oracle_update_chain_uneven -- the same chain over a work list of
+ *                            instances with their own n and T.
  *   oracle_ltimes         -- Kripke's LTimes contraction (Sec. 5.2, Listing
  *                            kripold: six storage orders chosen at run time).
- *   oracle_mlp_*          -- the cost model's 3-layer MLP, MSE loss,
+ *   oracle_lplustimes     -- its adjoint, in[d][g][z] += sum_m L+[d][m]
+ *                            out[m][g][z], with the same storage orders.
+ *   oracle_ltimes_sample  -- single output elements of LTimes, for sampled
+ *                            checks at sizes the full oracle cannot finish.
+ *   oracle_mlp_*, oracle_adam -- the cost model's 3-layer MLP, MSE loss,
  *                            hand-derived backward pass and Adam step (the
  *                            paper's future-work autotuning, Sec. 6).
  *   oracle_eigen_bench    -- the paper's literal Eigen recurrence
- *   oracle_eigen_recurrence -- the same recurrence over a batch of starts, any c
- *                            M = Ones + 5e-5 (M + M M) (Sec. 5, Listing eigen1).
+ *                            M = Ones + 5e-5 (M + M M) from
+ *                            M(i, j) = i + n j (Sec. 5, Listing eigen1).
+ *   oracle_eigen_recurrence -- the same recurrence over a batch of starting
+ *                            matrices, for any constant c.
  */
 #include <math.h>
 #include <pthread.h>
@@ -351,6 +359,7 @@ void oracle_adam(int64_t count, double *theta, const double *grad, double *m, do
 /*   m(i,j) = i + size*j initially; repeat: m = Ones + 5e-5 * (m + m*m).     */
 /* Output m after `repeat` iterations, row-major.                            */
 /* ------------------------------------------------------------------------ */
+
 /* The same recurrence for a batch of caller-given starts M0 (batch*n*n,     */
 /* row-major) and scale c: M_{k+1} = Ones + c * (M_k + M_k * M_k).           */
 void oracle_eigen_recurrence(long long batch, int n, int repeat, double c, const double *M0, double *out)
