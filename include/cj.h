@@ -284,7 +284,14 @@ cj_status cj_group_plan_create(int32_t dtype, int64_t count, const int32_t *n, c
  * captures the whole launch (counter reset included) into a CUDA graph on a
  * stream of the plan's own and launches it on cuda_stream; later calls
  * replay it (re-captured when the pools or a group's instantiation changed,
- * e.g. from generic to JIT).  Pools are caller-owned device memory. */
+ * e.g. from generic to JIT).  use_graph = 0: one kernel per group on the
+ * plan's streams (up to 64), launched from the calling thread.  The GPU
+ * overlaps independent streams only as far as the CUDA context has
+ * hardware work queues: CUDA_DEVICE_MAX_CONNECTIONS (default 8, at most
+ * 32), which must be set in the environment before the context is created.
+ * With 32, long FP64 plans ran faster with use_graph = 0 than as a graph,
+ * whose overlap did not change with the setting; time both for a given
+ * plan.  Pools are caller-owned device memory. */
 cj_status cj_group_plan_launch(cj_group_plan p, const void *A_pool, void *X_pool, void *cuda_stream,
                                int use_graph);
 /* Groups in the plan and pool elements it expects. */

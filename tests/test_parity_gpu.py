@@ -474,9 +474,11 @@ def test_grouped_plan_uneven(dt, use_graph):
 
 
 @pytest.mark.parametrize("dt", [cj.F64, cj.F32, cj.BF16])
-def test_grouped_plan_autotune_keeps_results(dt):
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_grouped_plan_autotune_keeps_results(dt, use_graph):
     """Plan autotuning: every group's candidates are timed on its own work
-    list, the fastest is kept, the graph re-captures, results still match."""
+    list, the fastest is kept, the graph re-captures (or the streams launch
+    the new tiles), results still match."""
     n, t = synth.uneven_sizes(synth.SEED_UNEVEN, 300)
     pool, off = synth.uneven_inputs_np(synth.SEED_UNEVEN, n)
     ref = oracle.update_chain_uneven(n, t, off, pool)
@@ -487,7 +489,7 @@ def test_grouped_plan_autotune_keeps_results(dt):
         changed = plan.autotune(A, X, stream=torch.cuda.current_stream(), max_groups=6, reps=2)
         assert 0 <= changed <= 6
         X.fill_(float("nan"))
-        plan.launch(A, X, stream=torch.cuda.current_stream(), use_graph=True)
+        plan.launch(A, X, stream=torch.cuda.current_stream(), use_graph=use_graph)
         torch.cuda.synchronize()
         Xh = X.double().cpu().numpy()
         worst = max(relF(Xh[off[k]:off[k] + n[k] * n[k]], ref[off[k]:off[k] + n[k] * n[k]]) for k in range(len(n)))
