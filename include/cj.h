@@ -291,7 +291,10 @@ cj_status cj_group_plan_create(int32_t dtype, int64_t count, const int32_t *n, c
  * 32), which must be set in the environment before the context is created.
  * With 32, long FP64 plans ran faster with use_graph = 0 than as a graph,
  * whose overlap did not change with the setting; time both for a given
- * plan.  Pools are caller-owned device memory. */
+ * plan.  A plan owns one set of work counters: launches of the same plan are
+ * ordered by cuda_stream, so two launches on streams the caller does not
+ * order against each other race (use one plan per concurrent stream).  Pools
+ * are caller-owned device memory. */
 cj_status cj_group_plan_launch(cj_group_plan p, const void *A_pool, void *X_pool, void *cuda_stream,
                                int use_graph);
 /* Groups in the plan and pool elements it expects. */
