@@ -32,8 +32,9 @@ Default tile resolution (tile all zero, no cost model):
   otherwise:                      (1 = row per thread, ipb, 0, 0) with
                                   ipb = max(1, 256 // n) for n <= 32, max(1, 128 // n) above
   Eigen recurrence: (1, ipb, 0, 0), ipb = max(1, 128 // n), lowered while the
-      two shared buffers (rows padded to an odd number of 16-byte units)
-      exceed 96 KiB.
+      two shared buffers (rows padded to an odd number of 16-byte units,
+      instances to 16 bytes modulo 128 where a half-warp's rows would share
+      banks) exceed 96 KiB.
   LTimes: (TG, TZ, threads, (PIPE << 20) | (MODE << 16) | (R << 8) | S);
       orders 1, 4 are g-fast and 0, 2 z-fast; TG = 1 if neither in nor out
       is g-fast, 8 if one is g-fast and the other z-fast, else 32.
@@ -97,11 +98,18 @@ def default_tile(kernel: int, dtype: int, n: int, layout_a: int = 0, layout_b: i
                  d: int = 96) -> tuple:
     if kernel == K_EIGEN_RECURRENCE:
         # one thread per row, max(1, 128 // n) instances per block, fewer while
-        # the two buffers exceed 96 KiB; a row is an odd number of 16-byte units
+        # the two buffers exceed 96 KiB; a row is an odd number of 16-byte units;
+        # an instance is n rows, padded by 16-byte units to 16 bytes modulo 128
+        # when two instances read by one half-warp (threads 16k .. 16k + 15,
+        # thread t on instance t // n) would start a multiple of 128 bytes apart
         es = 8 if dtype == F64 else 4
         rp = ((-(-n * es // 16)) | 1) * 16 // es
+        units = n * rp * es // 16
+        collide = any((d * n * rp * es) % 128 == 0
+                      for k in range(n) for d in range(1, (16 * k + 15) // n - (16 * k) // n + 1))
+        ip = n * rp + ((1 - units) % 8) * (16 // es) if collide else n * rp
         ipb = max(1, 128 // n)
-        while ipb > 1 and 2 * ipb * n * rp * es > 96 * 1024:
+        while ipb > 1 and 2 * ipb * ip * es > 96 * 1024:
             ipb -= 1
         return (1, ipb, 0, 0)
     if kernel == K_UPDATE_CHAIN_GROUPED and dtype == F32 and n >= 17:

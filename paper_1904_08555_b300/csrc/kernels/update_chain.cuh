@@ -606,7 +606,7 @@ update_chain_generic(const T* __restrict__ A, T* __restrict__ X, long long batch
 // the listing's case being c = 5e-5 and M_0(i, j) = i + N j, which the caller
 // passes.  Unlike the update chain, row i of M_{k+1} needs every row of M_k,
 // so a block keeps M_k of each of its instances in shared memory (two
-// buffers, rows of N + 1, one barrier per step); thread (instance, i) keeps
+// buffers, padded rows and instances, one barrier per step); thread (instance, i) keeps
 // its own row in registers and reads the other rows as broadcasts.  Each
 // element is formed as 1 + c * (m + q) with a separate multiply and add, the
 // order the listing writes.  Row-major.
@@ -617,28 +617,30 @@ __device__ __forceinline__ double eig_add(double a, double b) { return __dadd_rn
 __device__ __forceinline__ float eig_add(float a, float b) { return __fadd_rn(a, b); }
 
 // Instances [0, ninst) of a block between global memory (contiguous, row-major)
-// and a shared-memory buffer with rows of eig_rp(n, sizeof(T)).
+// and a shared-memory buffer with rows of eig_rp(n, sizeof(T)) and instances
+// eig_ip(n, sizeof(T)) apart.
 template <class T>
 __device__ __forceinline__ void eig_load(T* buf, const T* __restrict__ g, int ninst, int n, int tid, int nthreads) {
-    const int rp = cjg::eig_rp(n, (int)sizeof(T)), nn = n * n;
+    const int rp = cjg::eig_rp(n, (int)sizeof(T)), ip = cjg::eig_ip(n, (int)sizeof(T)), nn = n * n;
     for (int e = tid; e < ninst * nn; e += nthreads) {
         const int inst = e / nn, r = e - inst * nn, i = r / n;
-        buf[inst * n * rp + i * rp + (r - i * n)] = g[e];
+        buf[inst * ip + i * rp + (r - i * n)] = g[e];
     }
 }
 template <class T>
 __device__ __forceinline__ void eig_store(T* __restrict__ g, const T* buf, int ninst, int n, int tid, int nthreads) {
-    const int rp = cjg::eig_rp(n, (int)sizeof(T)), nn = n * n;
+    const int rp = cjg::eig_rp(n, (int)sizeof(T)), ip = cjg::eig_ip(n, (int)sizeof(T)), nn = n * n;
     for (int e = tid; e < ninst * nn; e += nthreads) {
         const int inst = e / nn, r = e - inst * nn, i = r / n;
-        g[e] = buf[inst * n * rp + i * rp + (r - i * n)];
+        g[e] = buf[inst * ip + i * rp + (r - i * n)];
     }
 }
 
 template <class T, int N, int IPB>
 __global__ void __launch_bounds__(cjg::chain_threads(N, 1, IPB))
 eigen_recurrence(const T* __restrict__ M0, T* __restrict__ M, long long batch, int repeat, double c) {
-    constexpr int NN = N * N, NT = cjg::chain_threads(N, 1, IPB), RP = cjg::eig_rp(N, (int)sizeof(T)), P = N * RP;
+    constexpr int NN = N * N, NT = cjg::chain_threads(N, 1, IPB), RP = cjg::eig_rp(N, (int)sizeof(T)),
+                  P = cjg::eig_ip(N, (int)sizeof(T));
     extern __shared__ __align__(16) unsigned char cj_smem[];
     T* cur = reinterpret_cast<T*>(cj_smem);
     T* nxt = cur + IPB * P;
@@ -702,7 +704,7 @@ __global__ void __launch_bounds__(256)
 eigen_recurrence_generic(const T* __restrict__ M0, T* __restrict__ M, long long batch, int repeat, double c, int n,
                          int ipb) {
     extern __shared__ __align__(16) unsigned char cj_smem[];
-    const int rp = cjg::eig_rp(n, (int)sizeof(T)), p = n * rp, nn = n * n;
+    const int rp = cjg::eig_rp(n, (int)sizeof(T)), p = cjg::eig_ip(n, (int)sizeof(T)), nn = n * n;
     T* cur = reinterpret_cast<T*>(cj_smem);
     T* nxt = cur + ipb * p;
     const long long b0 = (long long)blockIdx.x * ipb;
