@@ -132,9 +132,12 @@ typedef struct {
  *     else {1, max(1, 128 / n)}; bf16 -> {3, max(1, 128 / n16)} with n16 = n
  *     rounded up to a multiple of 16 (mapping 3: one warp per 16 rows,
  *     bf16 operands, fp32 accumulate and state).
- *   Eigen recurrence: {1, instances per block, 0, 0} (one thread per row;
- *     M_k of every instance in shared memory, two buffers).  Default: instances
- *     per block max(1, 128 / n), fewer if both buffers would exceed 96 KiB.
+ *   Eigen recurrence: {mapping, instances per block, 0, 0}; M_k of every
+ *     instance in shared memory, two buffers; mapping 1 = one thread per row
+ *     of M, 2 = two rows per thread (rows h and h + ceil(n / 2); f32 only;
+ *     same results bit for bit).  Default: f32 with n >= 2 -> mapping 2,
+ *     else 1; instances per block max(1, 128 / t) with t = ceil(n / 2) or n
+ *     threads per instance, fewer if both buffers would exceed 96 KiB.
  *   LTimes: {TG, TZ, threads, (PIPE << 20) | (MODE << 16) | (R << 8) | S}: a
  *     block covers TG x TZ (g, z) columns at a time (a persistent grid).
  *     MODE 0: the box with all d is staged in shared memory and each thread

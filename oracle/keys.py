@@ -31,10 +31,12 @@ Default tile resolution (tile all zero, no cost model):
   f32, n >= 9:                    (6 = two rows per thread, max(1, 128 // ceil(n / 2)), 0, 0)
   otherwise:                      (1 = row per thread, ipb, 0, 0) with
                                   ipb = max(1, 256 // n) for n <= 32, max(1, 128 // n) above
-  Eigen recurrence: (1, ipb, 0, 0), ipb = max(1, 128 // n), lowered while the
-      two shared buffers (rows padded to an odd number of 16-byte units,
-      instances to 16 bytes modulo 128 where a half-warp's rows would share
-      banks) exceed 96 KiB.
+  Eigen recurrence: (mapping, ipb, 0, 0); mapping 2 (two rows per thread)
+      for f32 with n >= 2, else 1; ipb = max(1, 128 // tpi) with tpi =
+      ceil(n / 2) or n threads per instance, lowered while the two shared
+      buffers (rows padded to an odd number of 16-byte units, instances to 16
+      bytes modulo 128 where a half-warp's rows would share banks) exceed
+      96 KiB.
   LTimes: (TG, TZ, threads, (PIPE << 20) | (MODE << 16) | (R << 8) | S);
       orders 1, 4 are g-fast and 0, 2 z-fast; TG = 1 if neither in nor out
       is g-fast, 8 if one is g-fast and the other z-fast, else 32.
@@ -97,21 +99,25 @@ def _tc_smem(m, d, stages, tg, tz, lout, boxes):
 def default_tile(kernel: int, dtype: int, n: int, layout_a: int = 0, layout_b: int = 0, m: int = 36,
                  d: int = 96) -> tuple:
     if kernel == K_EIGEN_RECURRENCE:
-        # one thread per row, max(1, 128 // n) instances per block, fewer while
-        # the two buffers exceed 96 KiB; a row is an odd number of 16-byte units;
-        # an instance is n rows, padded by 16-byte units to 16 bytes modulo 128
-        # when two instances read by one half-warp (threads 16k .. 16k + 15,
-        # thread t on instance t // n) would start a multiple of 128 bytes apart
+        # f32 with n >= 2: two rows per thread (mapping 2, tpi = ceil(n / 2)
+        # threads per instance), else one (mapping 1, tpi = n);
+        # max(1, 128 // tpi) instances per block, fewer while the two buffers
+        # exceed 96 KiB; a row is an odd number of 16-byte units; an instance is
+        # n rows, padded by 16-byte units to 16 bytes modulo 128 when two
+        # instances read by one half-warp (threads 16k .. 16k + 15, thread t on
+        # instance t // tpi) would start a multiple of 128 bytes apart
         es = 8 if dtype == F64 else 4
+        mapping = 2 if dtype == F32 and n >= 2 else 1
+        tpi = (n + 1) // 2 if mapping == 2 else n
         rp = ((-(-n * es // 16)) | 1) * 16 // es
         units = n * rp * es // 16
         collide = any((d * n * rp * es) % 128 == 0
-                      for k in range(n) for d in range(1, (16 * k + 15) // n - (16 * k) // n + 1))
+                      for k in range(tpi) for d in range(1, (16 * k + 15) // tpi - (16 * k) // tpi + 1))
         ip = n * rp + ((1 - units) % 8) * (16 // es) if collide else n * rp
-        ipb = max(1, 128 // n)
+        ipb = max(1, 128 // tpi)
         while ipb > 1 and 2 * ipb * ip * es > 96 * 1024:
             ipb -= 1
-        return (1, ipb, 0, 0)
+        return (mapping, ipb, 0, 0)
     if kernel == K_UPDATE_CHAIN_GROUPED and dtype == F32 and n >= 17:
         return (5, 1, 0, 0)            # one large instance per block, 4x4 register blocks
     if kernel in (K_UPDATE_CHAIN, K_UPDATE_CHAIN_GROUPED):

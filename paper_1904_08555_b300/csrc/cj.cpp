@@ -212,10 +212,13 @@ int lt_axis_host(int lay, int s) {
 }
 bool is_lt(int k) { return k == CJ_K_LTIMES || k == CJ_K_LPLUSTIMES; }
 bool is_eig(int k) { return k == CJ_K_EIGEN_RECURRENCE; }
-// Eigen recurrence default: rows per block up to 128 threads, both buffers within 96 KiB.
-int eig_default_ipb(int n, int es) {
-    int ipb = std::max(1, 128 / n);
-    while (ipb > 1 && cjg::eig_smem(n, ipb, es) > 96 * 1024) --ipb;
+// Eigen recurrence default: f32 with n >= 2 two rows per thread (mapping 2),
+// else one; instances per block up to 128 threads, both buffers within 96 KiB.
+int eig_default_map(int n, int dtype) { return dtype == CJ_F32 && n >= 2 ? 2 : 1; }
+int eig_default_ipb(int n, int es, int map = 1) {
+    const int tpi = map == 2 ? (n + 1) / 2 : n;
+    int ipb = std::max(1, 128 / tpi);
+    while (ipb > 1 && cjg::eig_smem(n, ipb, es, map) > 96 * 1024) --ipb;
     return ipb;
 }
 
@@ -231,8 +234,8 @@ LtView lt_view(int k, const cj_template_args &a) {
 
 void default_tile(int k, cj_template_args &a) {
     if (is_eig(k)) {
-        a.tile[0] = 1;
-        a.tile[1] = eig_default_ipb(a.n, esize(a.dtype));
+        a.tile[0] = eig_default_map(a.n, a.dtype);
+        a.tile[1] = eig_default_ipb(a.n, esize(a.dtype), a.tile[0]);
         a.tile[2] = a.tile[3] = 0;
         return;
     }
@@ -360,9 +363,13 @@ cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_
     }
     // explicit tiles: check the kernel can be instantiated and launched
     if (is_eig(k)) {
-        if (a.tile[0] != 1 || a.tile[1] < 1 || a.tile[2] || a.tile[3] || cjg::chain_threads(a.n, 1, a.tile[1]) > 1024 ||
-            cjg::eig_smem(a.n, a.tile[1], esize(a.dtype)) > 220 * 1024)
-            return fail(CJ_ERR_INVALID_ARG, "Eigen recurrence tile {%d,%d,%d,%d} invalid ({1, instances per block, 0, 0})",
+        // mapping 1: one row per thread; 2: two rows per thread (f32)
+        const int map = a.tile[0];
+        if ((map != 1 && !(map == 2 && a.dtype == CJ_F32)) || a.tile[1] < 1 || a.tile[2] || a.tile[3] ||
+            cjg::chain_threads(a.n, map == 2 ? 6 : 1, a.tile[1]) > 1024 ||
+            cjg::eig_smem(a.n, a.tile[1], esize(a.dtype), map) > 220 * 1024)
+            return fail(CJ_ERR_INVALID_ARG,
+                        "Eigen recurrence tile {%d,%d,%d,%d} invalid ({1, or 2 for f32; instances per block, 0, 0})",
                         a.tile[0], a.tile[1], a.tile[2], a.tile[3]);
         return CJ_OK;
     }
@@ -474,8 +481,8 @@ void spec_geometry(const cj_handle_s *h, Impl &s) {
     const int es = esize(a.dtype);
     if (is_eig(h->kernel)) {
         s.ipb = a.tile[1];
-        s.threads = cjg::chain_threads(a.n, 1, a.tile[1]);
-        s.smem = (size_t)cjg::eig_smem(a.n, a.tile[1], es);
+        s.threads = cjg::chain_threads(a.n, a.tile[0] == 2 ? 6 : 1, a.tile[1]);
+        s.smem = (size_t)cjg::eig_smem(a.n, a.tile[1], es, a.tile[0]);
     } else if (is_lt(h->kernel)) {
         const LtView v = lt_view(h->kernel, a);
         const int mode = (a.tile[3] >> 16) & 0xf;
@@ -517,7 +524,8 @@ std::string name_expression(const cj_handle_s *h) {
         snprintf(buf, sizeof buf, "cj::update_chain<%s, %d, %d, %d, %d>", ctype(a.dtype), a.n, a.layout_a,
                  a.tile[0], a.tile[1]);
     else if (is_eig(h->kernel))
-        snprintf(buf, sizeof buf, "cj::eigen_recurrence<%s, %d, %d>", ctype(a.dtype), a.n, a.tile[1]);
+        snprintf(buf, sizeof buf, "cj::eigen_recurrence%s<%s, %d, %d>", a.tile[0] == 2 ? "2" : "", ctype(a.dtype),
+                 a.n, a.tile[1]);
     else if (h->kernel == CJ_K_UPDATE_CHAIN_GROUPED)
         snprintf(buf, sizeof buf, "cj::update_chain_grouped<%s, %d, %d, %d>", ctype(a.dtype), a.n, a.tile[0],
                  a.tile[1]);

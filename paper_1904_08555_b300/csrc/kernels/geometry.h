@@ -76,27 +76,31 @@ CJ_HD constexpr long chain_smem(int n, int mapping, int ipb, int esize) {
 CJ_HD constexpr int eig_rp(int n, int esize) {
     return ((n * esize + 15) / 16 | 1) * 16 / esize;
 }
-// Thread t works on instance t / n and reads one row of that instance's M per
-// load, the same row as the instance's other threads (a broadcast).  A warp's
-// 16-byte shared-memory loads are served per half-warp, so two instances
-// whose rows sit in the same half-warp's load collide when their addresses
-// differ by a multiple of 128 bytes (same banks).  Half-warp k spans
-// instances 16k / n .. (16k + 15) / n, a pattern that repeats every n.
-CJ_HD constexpr bool eig_collide(int n, int pitch_bytes) {
-    for (int k = 0; k < n; ++k)
-        for (int d = 1; d <= (16 * k + 15) / n - (16 * k) / n; ++d)
+// Thread t works on instance t / tpi (tpi threads per instance: n with one
+// row per thread, ceil(n / 2) with two) and reads one row of that instance's
+// M per load, the same row as the instance's other threads (a broadcast).  A
+// warp's 16-byte shared-memory loads are served per half-warp, so two
+// instances whose rows sit in the same half-warp's load collide when their
+// addresses differ by a multiple of 128 bytes (same banks).  Half-warp k
+// spans instances 16k / tpi .. (16k + 15) / tpi, a pattern that repeats every
+// tpi.
+CJ_HD constexpr bool eig_collide(int tpi, int pitch_bytes) {
+    for (int k = 0; k < tpi; ++k)
+        for (int d = 1; d <= (16 * k + 15) / tpi - (16 * k) / tpi; ++d)
             if ((d * pitch_bytes) % 128 == 0) return true;
     return false;
 }
-// Instance pitch: n rows of eig_rp; where instances collide, padded by whole
-// 16-byte units to 16 bytes modulo 128, which puts the instances of a
-// half-warp in different banks (up to 8 of them).
-CJ_HD constexpr int eig_ip(int n, int esize) {
-    return eig_collide(n, n * eig_rp(n, esize) * esize)
+// Instance pitch for `rows` rows of M per thread: n rows of eig_rp; where
+// instances collide, padded by whole 16-byte units to 16 bytes modulo 128,
+// which puts the instances of a half-warp in different banks (up to 8).
+CJ_HD constexpr int eig_ip(int n, int esize, int rows = 1) {
+    return eig_collide((n + rows - 1) / rows, n * eig_rp(n, esize) * esize)
                ? n * eig_rp(n, esize) + (((1 - n * eig_rp(n, esize) * esize / 16) % 8 + 8) % 8) * (16 / esize)
                : n * eig_rp(n, esize);
 }
-CJ_HD constexpr long eig_smem(int n, int ipb, int esize) { return 2L * ipb * eig_ip(n, esize) * esize; }
+CJ_HD constexpr long eig_smem(int n, int ipb, int esize, int rows = 1) {
+    return 2L * ipb * eig_ip(n, esize, rows) * esize;
+}
 
 // Generic update chain: A pitch uses row_pitch; each thread keeps its row of
 // X and of the product in shared memory with pitch xrow_pitch(n).

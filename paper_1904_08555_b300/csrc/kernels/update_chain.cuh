@@ -618,18 +618,20 @@ __device__ __forceinline__ float eig_add(float a, float b) { return __fadd_rn(a,
 
 // Instances [0, ninst) of a block between global memory (contiguous, row-major)
 // and a shared-memory buffer with rows of eig_rp(n, sizeof(T)) and instances
-// eig_ip(n, sizeof(T)) apart.
+// ip elements apart.
 template <class T>
-__device__ __forceinline__ void eig_load(T* buf, const T* __restrict__ g, int ninst, int n, int tid, int nthreads) {
-    const int rp = cjg::eig_rp(n, (int)sizeof(T)), ip = cjg::eig_ip(n, (int)sizeof(T)), nn = n * n;
+__device__ __forceinline__ void eig_load(T* buf, const T* __restrict__ g, int ninst, int n, int ip, int tid,
+                                         int nthreads) {
+    const int rp = cjg::eig_rp(n, (int)sizeof(T)), nn = n * n;
     for (int e = tid; e < ninst * nn; e += nthreads) {
         const int inst = e / nn, r = e - inst * nn, i = r / n;
         buf[inst * ip + i * rp + (r - i * n)] = g[e];
     }
 }
 template <class T>
-__device__ __forceinline__ void eig_store(T* __restrict__ g, const T* buf, int ninst, int n, int tid, int nthreads) {
-    const int rp = cjg::eig_rp(n, (int)sizeof(T)), ip = cjg::eig_ip(n, (int)sizeof(T)), nn = n * n;
+__device__ __forceinline__ void eig_store(T* __restrict__ g, const T* buf, int ninst, int n, int ip, int tid,
+                                          int nthreads) {
+    const int rp = cjg::eig_rp(n, (int)sizeof(T)), nn = n * n;
     for (int e = tid; e < ninst * nn; e += nthreads) {
         const int inst = e / nn, r = e - inst * nn, i = r / n;
         g[e] = buf[inst * ip + i * rp + (r - i * n)];
@@ -648,7 +650,7 @@ eigen_recurrence(const T* __restrict__ M0, T* __restrict__ M, long long batch, i
     if (b0 >= batch) return;
     const int ninst = (batch - b0) < IPB ? (int)(batch - b0) : IPB;
     const int tid = threadIdx.x;
-    eig_load<T>(cur, M0 + b0 * NN, ninst, N, tid, NT);
+    eig_load<T>(cur, M0 + b0 * NN, ninst, N, P, tid, NT);
     __syncthreads();
     const int inst = tid / N, i = tid - inst * N;
     const bool active = inst < ninst;
@@ -695,7 +697,90 @@ eigen_recurrence(const T* __restrict__ M0, T* __restrict__ M, long long batch, i
         cur = nxt;
         nxt = t;
     }
-    eig_store<T>(M + b0 * NN, cur, ninst, N, tid, NT);
+    eig_store<T>(M + b0 * NN, cur, ninst, N, P, tid, NT);
+}
+
+// Two rows per thread (tile mapping 2, FP32): thread (instance, h) forms rows
+// h and h + ceil(N / 2) of M_{k+1}, so every element of row l read from
+// shared memory feeds two multiply-adds instead of one; the one-row kernel is
+// bound by shared-memory wavefronts at N >= 9.  Per element the operations
+// and their order are the one-row kernel's (l ascending, one FMA per term,
+// then 1 + c (m + q) with a separate multiply and add), so the results are the
+// same bit for bit.  The thread of a half-row (h = ceil(N / 2) - 1, N odd)
+// has no second row; it runs the same loop with zeros and stores one row.
+template <class T, int N, int IPB>
+__global__ void __launch_bounds__(cjg::chain_threads(N, 6, IPB))
+eigen_recurrence2(const T* __restrict__ M0, T* __restrict__ M, long long batch, int repeat, double c) {
+    constexpr int H = (N + 1) / 2, NN = N * N, NT = cjg::chain_threads(N, 6, IPB),
+                  RP = cjg::eig_rp(N, (int)sizeof(T)), P = cjg::eig_ip(N, (int)sizeof(T), 2);
+    extern __shared__ __align__(16) unsigned char cj_smem[];
+    T* cur = reinterpret_cast<T*>(cj_smem);
+    T* nxt = cur + IPB * P;
+    const long long b0 = (long long)blockIdx.x * IPB;
+    if (b0 >= batch) return;
+    const int ninst = (batch - b0) < IPB ? (int)(batch - b0) : IPB;
+    const int tid = threadIdx.x;
+    eig_load<T>(cur, M0 + b0 * NN, ninst, N, P, tid, NT);
+    __syncthreads();
+    const int inst = tid / H, h = tid - inst * H;
+    const bool active = inst < ninst;
+    const bool two = h + H < N;
+    const T cc = (T)c;
+    T x0[N], x1[N];
+    if (active) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            x0[j] = cur[inst * P + h * RP + j];
+            x1[j] = two ? cur[inst * P + (h + H) * RP + j] : T(0);
+        }
+    }
+    for (int k = 0; k < repeat; ++k) {
+        if (active) {
+            const T* m = opaque_base(cur, inst * P);
+            T q0[N], q1[N];
+#pragma unroll
+            for (int j = 0; j < N; ++j) q0[j] = q1[j] = T(0);
+#pragma unroll
+            for (int l = 0; l < N; ++l) {
+                const T xl0 = x0[l], xl1 = x1[l];
+                constexpr int V = 16 / (int)sizeof(T);
+#pragma unroll
+                for (int q4 = 0; q4 < (N + V - 1) / V; ++q4) {
+                    T w[V];
+                    if constexpr (V == 4) {
+                        const float4 t = reinterpret_cast<const float4*>(m + l * RP)[q4];
+                        w[0] = t.x; w[1] = t.y; w[2] = t.z; w[3] = t.w;
+                    } else {
+                        const double2 t = reinterpret_cast<const double2*>(m + l * RP)[q4];
+                        w[0] = t.x; w[1] = t.y;
+                    }
+#pragma unroll
+                    for (int e = 0; e < V; ++e)
+                        if (V * q4 + e < N) {
+                            q0[V * q4 + e] = fmaT(xl0, w[e], q0[V * q4 + e]);
+                            q1[V * q4 + e] = fmaT(xl1, w[e], q1[V * q4 + e]);
+                        }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                x0[j] = eig_add(T(1), eig_mul(cc, eig_add(x0[j], q0[j])));
+                nxt[inst * P + h * RP + j] = x0[j];
+            }
+            if (two) {
+#pragma unroll
+                for (int j = 0; j < N; ++j) {
+                    x1[j] = eig_add(T(1), eig_mul(cc, eig_add(x1[j], q1[j])));
+                    nxt[inst * P + (h + H) * RP + j] = x1[j];
+                }
+            }
+        }
+        __syncthreads();   // M_{k+1} complete; M_k no longer read
+        T* t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    eig_store<T>(M + b0 * NN, cur, ninst, N, P, tid, NT);
 }
 
 // Generic: run-time n (1..64) and instances per block; every row in shared memory.
@@ -711,7 +796,7 @@ eigen_recurrence_generic(const T* __restrict__ M0, T* __restrict__ M, long long 
     if (b0 >= batch) return;
     const int ninst = (batch - b0) < ipb ? (int)(batch - b0) : ipb;
     const int tid = threadIdx.x, nthreads = blockDim.x;
-    eig_load<T>(cur, M0 + b0 * nn, ninst, n, tid, nthreads);
+    eig_load<T>(cur, M0 + b0 * nn, ninst, n, p, tid, nthreads);
     __syncthreads();
     const int inst = tid / n, i = tid - inst * n;
     const bool active = inst < ninst;
@@ -730,7 +815,7 @@ eigen_recurrence_generic(const T* __restrict__ M0, T* __restrict__ M, long long 
         cur = nxt;
         nxt = t;
     }
-    eig_store<T>(M + b0 * nn, cur, ninst, n, tid, nthreads);
+    eig_store<T>(M + b0 * nn, cur, ninst, n, p, tid, nthreads);
 }
 
 // ---------------------------------------------------------------------------

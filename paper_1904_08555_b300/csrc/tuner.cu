@@ -205,9 +205,13 @@ cj_status candidates(int k, const cj_template_args &a, std::vector<std::array<in
     out.clear();
     if (k == CJ_K_LTIMES || k == CJ_K_LPLUSTIMES) ltimes_candidates(lt_swapped(k, a), out);
     else if (k == CJ_K_EIGEN_RECURRENCE) {
-        for (int ipb : {1, 2, 4, 8, 16, 32, 64})
-            if (cjg::chain_threads(a.n, 1, ipb) <= 1024 && cjg::eig_smem(a.n, ipb, esize(a.dtype)) <= 200 * 1024)
-                out.push_back({1, ipb, 0, 0});
+        for (int map : {1, 2}) {
+            if (map == 2 && a.dtype != CJ_F32) continue;
+            for (int ipb : {1, 2, 4, 8, 16, 32, 64})
+                if (cjg::chain_threads(a.n, map == 2 ? 6 : 1, ipb) <= 1024 &&
+                    cjg::eig_smem(a.n, ipb, esize(a.dtype), map) <= 200 * 1024)
+                    out.push_back({map, ipb, 0, 0});
+        }
     } else chain_candidates(a, out);
     if (out.empty()) return tfail(CJ_ERR_INVALID_ARG, "no candidate tile fits these arguments");
     return CJ_OK;

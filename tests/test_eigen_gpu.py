@@ -73,3 +73,20 @@ def test_zero_repeats_copy_the_start():
     M0 = synth.uniform_np(3, 0, 10 * n * n).reshape(10, n, n)
     h = cj.specialize(cj.K_EIGEN_RECURRENCE, cj.F64, n=n)
     np.testing.assert_array_equal(run(h, M0, 0, 5e-5, cj.F64), M0)
+
+
+@pytest.mark.parametrize("n,ipb", [(1, 3), (2, 128), (5, 7), (8, 32), (9, 25), (13, 18), (16, 16), (17, 14),
+                                   (24, 10), (31, 8), (32, 8)])
+def test_two_rows_per_thread_f32(n, ipb):
+    """Tile mapping 2 (two rows of M per thread, FP32) against the FP64
+    oracle, on a batch ragged against the tile, and bit for bit against the
+    one-row kernel: per element both do the same operations in the same order."""
+    rep, c = 40, 5e-5
+    batch = 301
+    M0 = synth.uniform_np(synth.SEED_CHAIN_SWEEP, synth.STREAM_A, batch * n * n).reshape(batch, n, n)
+    ref = oracle.eigen_recurrence(M0, rep, c)
+    h2 = cj.specialize(cj.K_EIGEN_RECURRENCE, cj.F32, n=n, tile=(2, ipb, 0, 0))
+    h1 = cj.specialize(cj.K_EIGEN_RECURRENCE, cj.F32, n=n, tile=(1, max(1, 128 // n), 0, 0))
+    got2 = run(h2, M0, rep, c, cj.F32)
+    assert rel_per_instance(got2, ref) <= TOL32
+    np.testing.assert_array_equal(got2, run(h1, M0, rep, c, cj.F32))
