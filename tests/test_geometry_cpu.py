@@ -1,0 +1,98 @@
+"""Shared-memory geometry of the Eigen recurrence kernels, on the CPU.
+
+geometry.h is compiled for the host with g++ and its row pitch (eig_rp),
+instance pitch (eig_ip) and buffer size (eig_smem) are checked against a
+brute-force model of the shared-memory reads: thread t of a block works on
+instance t // tpi (tpi = n threads per instance with one row per thread,
+ceil(n / 2) with two), all threads of an instance read the same row (a
+broadcast), and a warp's 16-byte loads are served per half-warp, where two
+different addresses in the same 16-byte bank group (address // 16 mod 8)
+cost an extra pass."""
+import os
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1904_08555_b300", "csrc", "kernels")
+
+PROG = r"""
+#include <cstdio>
+#include <initializer_list>
+#include "geometry.h"
+int main() {
+    for (int es : {4, 8})
+        for (int rows : {1, 2})
+            for (int n = 1; n <= 32; ++n)
+                std::printf("%d %d %d %d %d %ld\n", es, rows, n, cjg::eig_rp(n, es), cjg::eig_ip(n, es, rows),
+                            cjg::eig_smem(n, 3, es, rows));
+    return 0;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def table(tmp_path_factory):
+    d = tmp_path_factory.mktemp("geom")
+    src, exe = d / "geom.cpp", d / "geom"
+    src.write_text(PROG)
+    subprocess.run(["g++", "-std=c++17", "-O1", "-I", CSRC, "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    rows = {}
+    for line in out.split("\n"):
+        if line.strip():
+            es, r, n, rp, ip, smem = (int(v) for v in line.split())
+            rows[(es, r, n)] = (rp, ip, smem)
+    assert len(rows) == 2 * 2 * 32
+    return rows
+
+
+def half_warp_collides(n, rows, pitch_bytes, threads=1024):
+    """Brute force: does any half-warp of a `threads`-thread block read two
+    different instance rows that fall in the same 16-byte bank group?"""
+    tpi = -(-n // rows)
+    for start in range(0, threads, 16):
+        groups = {}
+        for t in range(start, start + 16):
+            addr = (t // tpi) * pitch_bytes          # row 0 of the thread's instance
+            g = (addr // 16) % 8
+            if g in groups and groups[g] != addr:
+                return True
+            groups[g] = addr
+    return False
+
+
+def max_instances_per_half_warp(n, rows, threads=1024):
+    tpi = -(-n // rows)
+    return max(len({t // tpi for t in range(s, s + 16)}) for s in range(0, threads, 16))
+
+
+def test_row_pitch_is_an_odd_number_of_16_byte_units(table):
+    for (es, _, n), (rp, _, _) in table.items():
+        assert rp >= n and (rp * es) % 16 == 0 and (rp * es // 16) % 2 == 1
+
+
+def test_instance_pitch_against_brute_force(table):
+    for (es, r, n), (rp, ip, smem) in table.items():
+        plain = n * rp * es
+        got = ip * es
+        assert smem == 2 * 3 * got
+        assert got % 16 == 0 and plain <= got < plain + 128
+        if half_warp_collides(n, r, plain):
+            # padded to 16 bytes modulo 128; that removes every collision the
+            # eight bank groups allow
+            assert got % 128 == 16, (es, r, n)
+            if max_instances_per_half_warp(n, r) <= 8:
+                assert not half_warp_collides(n, r, got), (es, r, n)
+        else:
+            assert got == plain, (es, r, n)       # no padding where nothing collides
+
+
+def test_known_cases(table):
+    # f32, one row per thread: n = 8 (two instances per half-warp, 384-byte
+    # pitch) is padded by one 16-byte unit; n = 16 (one instance per
+    # half-warp) is not
+    assert table[(4, 1, 8)][1] * 4 == 384 + 16
+    assert table[(4, 1, 16)][1] * 4 == 16 * 20 * 4
+    # f32, two rows per thread: n = 16 puts two instances in a half-warp
+    assert table[(4, 2, 16)][1] * 4 == 16 * 20 * 4 + 16
