@@ -96,3 +96,38 @@ def test_known_cases(table):
     assert table[(4, 1, 16)][1] * 4 == 16 * 20 * 4
     # f32, two rows per thread: n = 16 puts two instances in a half-warp
     assert table[(4, 2, 16)][1] * 4 == 16 * 20 * 4 + 16
+
+
+LT_PROG = r"""
+#include <cstdio>
+#include <initializer_list>
+#include "geometry.h"
+int main() {
+    for (int m : {1, 5, 16, 17, 36, 64, 100, 128})
+        for (int d : {1, 31, 32, 33, 96, 128})
+            for (int stages : {2, 3, 8})
+                for (int tg : {1, 8, 32})
+                    for (int lout = 0; lout < 6; ++lout)
+                        for (int boxes : {0, 2, 4})
+                            std::printf("%d %d %d %d %d %d %ld\n", m, d, stages, tg, lout, boxes,
+                                        cjg::lt_tc_smem(m, d, stages, tg, 128 / tg, lout, boxes));
+    return 0;
+}
+"""
+
+
+def test_tensor_core_ltimes_smem_matches_the_key_restatement(tmp_path):
+    """The tcgen05 LTimes kernel's shared-memory size in geometry.h equals the
+    restatement the default-tile oracle uses (oracle/keys.py), over a grid of
+    moments, directions, operand stages, column tiles, out orders and TMA
+    boxes."""
+    from oracle import keys as K
+    src, exe = tmp_path / "lt.cpp", tmp_path / "lt"
+    src.write_text(LT_PROG)
+    subprocess.run(["g++", "-std=c++17", "-O1", "-I", CSRC, "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    lines = [l for l in out if l.strip()]
+    assert len(lines) == 8 * 6 * 3 * 3 * 6 * 3
+    for l in lines:
+        m, d, stages, tg, lout, boxes, smem = (int(v) for v in l.split())
+        assert K._tc_smem(m, d, stages, tg, 128 // tg, lout, boxes) == smem, l
