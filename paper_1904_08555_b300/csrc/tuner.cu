@@ -185,12 +185,15 @@ void featurize(int k, const cj_template_args &a0, int64_t batch, int32_t steps, 
         f[6] = lg2(n) / 6;
         f[7] = n / 64;
         f[8 + (a.layout_a & 1)] = 1.f;
-        f[20] = tile[0] == 1 || tile[0] == 6;
-        f[21] = tile[0] == 2;
-        f[22] = tile[0] == 4 || tile[0] == 5;   // register/tensor blocked panels
-        f[19] = tile[0] == 5 ? 1.f : tile[0] == 6 ? 0.5f : 0.f;
+        // the Eigen recurrence's mappings are the chain's thread shapes: 1 = one
+        // row per thread (chain mapping 1), 2 = two rows per thread (mapping 6)
+        const int map = k == CJ_K_EIGEN_RECURRENCE ? (tile[0] == 2 ? 6 : 1) : tile[0];
+        f[20] = map == 1 || map == 6;
+        f[21] = map == 2;
+        f[22] = map == 4 || map == 5;   // register/tensor blocked panels
+        f[19] = map == 5 ? 1.f : map == 6 ? 0.5f : 0.f;
         f[23] = lg2(tile[1]) / 8;
-        f[24] = lg2(cjg::chain_threads(a.n, tile[0], tile[1])) / 10;
+        f[24] = lg2(cjg::chain_threads(a.n, map, tile[1])) / 10;
         f[25] = a.n % 8 == 0;
         f[26] = steps / 128.f;
     }

@@ -232,6 +232,23 @@ def test_every_candidate_tile_is_a_valid_request(compile_only_sync, req):
         assert f.shape == (cj.FEATURES,) and np.all(np.isfinite(f)) and f[31] == 1.0
 
 
+def test_eigen_tile_features_follow_the_thread_mapping(compile_only_sync):
+    """Eigen recurrence tiles are featurized by their thread shape: mapping 1
+    like the chain's one row per thread, mapping 2 like its two rows per
+    thread (chain mapping 6), with the block's real thread count."""
+    import math
+    for n in (5, 16, 31):
+        kw = dict(batch=4096, steps=64, n=n)
+        e1 = cj.featurize(cj.K_EIGEN_RECURRENCE, cj.F32, tile=(1, 4, 0, 0), **kw)
+        e2 = cj.featurize(cj.K_EIGEN_RECURRENCE, cj.F32, tile=(2, 4, 0, 0), **kw)
+        c1 = cj.featurize(cj.K_UPDATE_CHAIN, cj.F32, tile=(1, 4, 0, 0), **kw)
+        c6 = cj.featurize(cj.K_UPDATE_CHAIN, cj.F32, tile=(6, 4, 0, 0), **kw)
+        assert e2[21] == 0 and e2[20] == 1 and e2[19] == 0.5
+        assert math.isclose(float(e2[24]), math.log2(((4 * ((n + 1) // 2) + 31) // 32) * 32) / 10, rel_tol=1e-6)
+        np.testing.assert_array_equal(e1[19:25], c1[19:25])
+        np.testing.assert_array_equal(e2[19:25], c6[19:25])
+
+
 def test_lplustimes_keys_and_compiles(compile_only_sync):
     from oracle import keys as K
     h = cj.specialize(cj.K_LPLUSTIMES, cj.F64, layout_a=3, layout_b=1, m=36, d=96)
