@@ -107,6 +107,8 @@ def test_aot_sizes_are_not_compiled(compile_only_sync):
     dict(kernel=cj.K_EIGEN_RECURRENCE, dtype=cj.BF16, n=8),
     dict(kernel=cj.K_EIGEN_RECURRENCE, dtype=cj.F64, n=8, tile=(2, 4, 0, 0)),
     dict(kernel=cj.K_EIGEN_RECURRENCE, dtype=cj.F64, n=8, tile=(1, 200, 0, 0)),
+    dict(kernel=cj.K_EIGEN_RECURRENCE, dtype=cj.F32, n=32, tile=(2, 200, 0, 0)),
+    dict(kernel=cj.K_EIGEN_RECURRENCE, dtype=cj.F32, n=8, tile=(3, 4, 0, 0)),
     dict(kernel=9, dtype=cj.F64, n=4),
 ])
 def test_invalid_arguments(compile_only_sync, kw):
