@@ -251,6 +251,27 @@ def test_eigen_tile_features_follow_the_thread_mapping(compile_only_sync):
         np.testing.assert_array_equal(e2[19:25], c6[19:25])
 
 
+def test_plain_c_client(tmp_path):
+    """The boundary is C: include/cj.h compiles as C99 with every warning an
+    error, and a C program linked against libcj.so initialises it
+    (compile-only), specializes, reads the key and stats, sees an
+    out-of-range request refused, and shuts down."""
+    from oracle import keys as K
+    cj.load()
+    exe = tmp_path / "c_client"
+    libdir = os.path.dirname(cj.lib_path())
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    "-o", str(exe), os.path.join(ROOT, "tests", "support", "c_client.c"),
+                    cj.lib_path(), "-Wl,-rpath," + libdir], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    key, variant, refused, requests, compiles_ok = r.stdout.split()
+    assert key == K.canonical_key(K.K_UPDATE_CHAIN, K.F64, n=12).hex()
+    assert int(variant) == K.expected_variant(K.K_UPDATE_CHAIN, K.F64, 12) == K.VARIANT_JIT
+    assert int(refused) == cj.CJ_ERR_INVALID_ARG
+    assert int(requests) >= 1 and int(compiles_ok) >= 1
+
+
 def test_lplustimes_keys_and_compiles(compile_only_sync):
     from oracle import keys as K
     h = cj.specialize(cj.K_LPLUSTIMES, cj.F64, layout_a=3, layout_b=1, m=36, d=96)
