@@ -383,8 +383,11 @@ cj_status cj_update_chain_uneven_noalloc(int32_t dtype, int64_t count, const int
  *   SplitMix64(seed), U(-s, s) with s = sqrt(3 / fan_in), biases 0.
  * cj_cost_model_use: install m (in_features == CJ_FEATURES) for
  *   cj_specialize requests with tile = {0,0,0,0} when cj_config.use_cost_model
- *   is set (NULL uninstalls); the decision is cached per request.
- * cj_choose_tile: the candidate with the lowest predicted log time.
+ *   is set (NULL uninstalls); the decision is cached per request.  Only
+ *   UPDATE_CHAIN and LTIMES requests consult it; the other kernels keep
+ *   their default rule.
+ * cj_choose_tile: the candidate with the lowest predicted log time, for any
+ *   kernel with candidates (a model trained on other kernels extrapolates).
  */
 #define CJ_FEATURES 32
 typedef struct cj_mlp_s *cj_mlp;
