@@ -131,3 +131,33 @@ def test_tensor_core_ltimes_smem_matches_the_key_restatement(tmp_path):
     for l in lines:
         m, d, stages, tg, lout, boxes, smem = (int(v) for v in l.split())
         assert K._tc_smem(m, d, stages, tg, 128 // tg, lout, boxes) == smem, l
+
+
+REG_PROG = r"""
+#include <cstdio>
+#include "geometry.h"
+int main() {
+    for (int w = 0; w <= 16; ++w) std::printf("%d %d\n", w, cjg::lt_tc_maxreg(w));
+    return 0;
+}
+"""
+
+
+def test_tensor_core_register_cap_fits_the_sub_partitions(tmp_path):
+    """lt_tc_maxreg(w) is the per-thread register cap of a tcgen05 LTimes
+    block of 5 + w warps (mode 4: w producer warps; mode 5: w converter warps
+    plus the TMA warp).  The warps spread over the SM's four sub-partitions of
+    16,384 registers, so the busiest holds ceil((5 + w) / 4) warps: the cap
+    must fit there, be a multiple of 8 no larger than 255, and be the largest
+    such value."""
+    src, exe = tmp_path / "reg.cpp", tmp_path / "reg"
+    src.write_text(REG_PROG)
+    subprocess.run(["g++", "-std=c++17", "-O1", "-I", CSRC, "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    for line in (l for l in out if l.strip()):
+        w, regs = (int(v) for v in line.split())
+        busiest = -(-(5 + w) // 4)
+        assert regs % 8 == 0 and 0 < regs <= 255
+        assert busiest * 32 * regs <= 16384
+        assert regs + 8 > 255 or busiest * 32 * (regs + 8) > 16384
+        assert (5 + w) * 32 * regs <= 65536      # the whole block fits the SM's register file
