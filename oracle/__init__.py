@@ -6,7 +6,8 @@ imports it and shares no code with it.
 
 The arithmetic lives in ``oracle.c`` (plain scalar FP64 C, -ffp-contract=off);
 this module only builds it with gcc and marshals numpy arrays.  Key encoding
-(``keys.py``) is pure Python.
+(``keys.py``) is pure Python and holds only the key contract (byte format,
+zeroed fields, flags, the variant rule), no rule for choosing a tile.
 
 Pinning status (all pinned by CPU tests under tests/test_oracle_*.py):
   update_chain   -- zero input, identity, diagonal, binary-powering closed
@@ -18,6 +19,8 @@ Pinning status (all pinned by CPU tests under tests/test_oracle_*.py):
                     form, first Adam step closed form.
   eigen_bench    -- exact rational brute force for tiny sizes.
   eigen_recurrence -- the same recurrence over a batch of starts and any c.
+  keys           -- keys assembled by hand from the documented byte format;
+                    the variant rule against its statement.
 """
 from __future__ import annotations
 

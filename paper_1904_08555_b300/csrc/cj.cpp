@@ -1292,9 +1292,9 @@ CJ_API cj_status cj_group_plan_autotune(cj_group_plan p, const void *A_pool, voi
         cj_template_args a{};
         a.dtype = (p->dtype == CJ_BF16 && p->groups[g].n < 16) ? CJ_F32 : p->dtype;
         a.n = p->groups[g].n;
-        int32_t tiles[4 * 16], cnt = 0;
-        if (cj_candidates(CJ_K_UPDATE_CHAIN_GROUPED, &a, tiles, 16, &cnt) != CJ_OK) continue;
-        for (int32_t c = 0; c < cnt; ++c) {
+        int32_t tiles[4 * 32], cnt = 0;
+        if (cj_candidates(CJ_K_UPDATE_CHAIN_GROUPED, &a, tiles, 32, &cnt) != CJ_OK) continue;
+        for (int32_t c = 0; c < std::min<int32_t>(cnt, 32); ++c) {
             if (tiles[4 * c + 1] > 256) continue;   // grouped chunks hold at most 256 instances
             cj_template_args t = a;
             for (int i = 0; i < 4; ++i) t.tile[i] = tiles[4 * c + i];
@@ -1407,6 +1407,11 @@ CJ_API const char *cj_last_error(void) { return t_err.c_str(); }
 
 namespace cjint {
 void set_last_error(const char *msg) { t_err = msg; }
+void default_tile_of(int k, const cj_template_args &a, int tile_out[4]) {
+    cj_template_args r = a;
+    default_tile(k, r);
+    for (int i = 0; i < 4; ++i) tile_out[i] = r.tile[i];
+}
 }  // namespace cjint
 
 CJ_API cj_status cj_shutdown(void) {

@@ -56,6 +56,10 @@ const void *peak_dmma_kernel();
 // model is installed or the query failed.
 bool cost_model_tile(int k, const cj_template_args &a, int *tile_out);
 
+// The tile the library's default rule picks for request a of kernel k (the
+// rule documented in cj.h; no cost model).
+void default_tile_of(int k, const cj_template_args &a, int tile_out[4]);
+
 // Set the thread-local message returned by cj_last_error (used by the
 // allocation-free entry point in noalloc.cu).
 void set_last_error(const char *msg);

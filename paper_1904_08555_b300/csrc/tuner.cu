@@ -217,6 +217,12 @@ cj_status candidates(int k, const cj_template_args &a, std::vector<std::array<in
         }
     } else chain_candidates(a, out);
     if (out.empty()) return tfail(CJ_ERR_INVALID_ARG, "no candidate tile fits these arguments");
+    // the default rule's tile is always searched too (first, if the space
+    // above does not hold it), so a tuned choice is never worse than the
+    // default on the autotuner's own timings
+    std::array<int, 4> def{};
+    cjint::default_tile_of(k, a, def.data());
+    if (std::find(out.begin(), out.end(), def) == out.end()) out.insert(out.begin(), def);
     return CJ_OK;
 }
 

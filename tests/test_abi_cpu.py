@@ -51,9 +51,9 @@ def golden_requests():
 
 
 def test_golden_keys_and_dispatch(compile_only_sync):
+    """Requests that name their tile: the key and the variant are the
+    golden ones, bit for bit."""
     for (k, dt, n, la, lb, m, d, t0, t1, t2, t3, fl), key, var in golden_requests():
-        if dt == cj.BF16:
-            continue   # the bf16 kernel has its own tests
         h = cj.specialize(k, dt, n, la, lb, m, d, (t0, t1, t2, t3), fl, allow_compile_error=True)
         got_key, got_var = h.info()
         assert got_key == key, (k, dt, n, la, lb, fl)
@@ -61,6 +61,72 @@ def test_golden_keys_and_dispatch(compile_only_sync):
         if fl & cj.FLAG_INJECT_COMPILE_ERROR:
             expect = 0      # failed compiles keep the generic kernel
         assert got_var == expect, (k, dt, n, la, lb, fl)
+
+
+DEFAULT_TILE_REQUESTS = [
+    # kernel, dtype, n, layout_a, layout_b, m, d, flags
+    (cj.K_UPDATE_CHAIN, cj.F64, n, la, 0, 0, 0, 0) for n in (1, 3, 4, 5, 8, 12, 16, 32, 40, 64) for la in (0, 1)
+] + [
+    (cj.K_UPDATE_CHAIN, cj.F32, n, 0, 0, 0, 0, 0) for n in (2, 4, 7, 9, 16, 24, 32, 48, 64)
+] + [
+    (cj.K_UPDATE_CHAIN, cj.BF16, n, 0, 0, 0, 0, 0) for n in (16, 40, 64)
+] + [
+    (cj.K_UPDATE_CHAIN, cj.F64, 8, 0, 0, 0, 0, cj.FLAG_NO_AOT),
+    (cj.K_UPDATE_CHAIN, cj.F32, 16, 1, 0, 0, 0, cj.FLAG_NO_AOT),
+] + [
+    (cj.K_UPDATE_CHAIN_GROUPED, dt, n, 0, 0, 0, 0, 0) for dt in (cj.F64, cj.F32) for n in (2, 9, 17, 64)
+] + [
+    (cj.K_UPDATE_CHAIN_GROUPED, cj.BF16, n, 0, 0, 0, 0, 0) for n in (16, 48)
+] + [
+    (cj.K_LTIMES, dt, 0, la, lb, 36, 96, 0) for dt in (cj.F64, cj.F32) for la, lb in ((0, 0), (1, 3), (4, 2), (5, 5))
+] + [
+    (cj.K_LTIMES, cj.F32, 0, 0, 1, 64, 128, 0),
+    (cj.K_LTIMES, cj.F32, 0, 2, 4, 48, 100, 0),
+    (cj.K_LPLUSTIMES, cj.F32, 0, 1, 2, 36, 96, 0),
+    (cj.K_LPLUSTIMES, cj.F64, 0, 3, 0, 36, 96, 0),
+] + [
+    (cj.K_EIGEN_RECURRENCE, dt, n, 0, 0, 0, 0, 0) for dt in (cj.F64, cj.F32) for n in (1, 2, 8, 16, 31)
+]
+
+
+def test_default_tile_requests_resolve_to_a_candidate(compile_only_sync):
+    """Requests that leave the tile to the library (tile 0, no cost model):
+    the tile the library resolves is one of the request's candidates
+    (cj_candidates), the handle's key is the canonical key of the request
+    with that tile (every other field bit for bit), and the variant follows
+    the contract's rule (ahead-of-time kernel for the f64/f32 update chain at
+    n in {4, 8, 16, 32}, else a run-time compile).  Which candidate the
+    default rule picks is the library's performance choice and is not
+    restated here."""
+    from oracle import keys as K
+    for (k, dt, n, la, lb, m, d, fl) in DEFAULT_TILE_REQUESTS:
+        h = cj.specialize(k, dt, n, la, lb, m, d, (0, 0, 0, 0), fl)
+        key_hex, var = h.info()
+        tile = K.parse_key(bytes.fromhex(key_hex))["tile"]
+        assert tile in cj.candidates(k, dt, n, la, lb, m, d), (k, dt, n, la, lb, tile)
+        assert key_hex == K.canonical_key(k, dt, n, la, lb, m, d, tile, fl).hex(), (k, dt, n, la, lb)
+        assert var == K.expected_variant(k, dt, n, True, fl), (k, dt, n, la, lb, fl)
+
+
+def test_explicit_resolved_tile_is_the_same_instantiation(compile_only_sync):
+    """A request naming the tile that a default request resolved to has the
+    same key, so the cache returns the same handle: at the ahead-of-time
+    sizes that is the ahead-of-time kernel (an explicit specialization wins,
+    Sec. 2); any other candidate is a different instantiation, compiled at
+    run time."""
+    from oracle import keys as K
+    for dt in (cj.F64, cj.F32):
+        for n in K.AOT_SIZES:
+            h0 = cj.specialize(cj.K_UPDATE_CHAIN, dt, n=n)
+            assert h0.variant == "aot"
+            tile = K.parse_key(bytes.fromhex(h0.key_hex))["tile"]
+            assert cj.specialize(cj.K_UPDATE_CHAIN, dt, n=n, tile=tile) == h0
+            other = next(t for t in cj.candidates(cj.K_UPDATE_CHAIN, dt, n=n) if t != tile)
+            h1 = cj.specialize(cj.K_UPDATE_CHAIN, dt, n=n, tile=other)
+            assert h1 != h0 and h1.variant == "jit"
+            assert h1.key_hex == K.canonical_key(K.K_UPDATE_CHAIN, dt, n, tile=other).hex()
+    s = cj.stats()
+    assert s["aot_hits"] == 8 and s["cache_hits"] >= 8
 
 
 def test_cache_returns_same_handle(compile_only_sync):
@@ -266,8 +332,10 @@ def test_plain_c_client(tmp_path):
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr
     key, variant, refused, requests, compiles_ok = r.stdout.split()
-    assert key == K.canonical_key(K.K_UPDATE_CHAIN, K.F64, n=12).hex()
-    assert int(variant) == K.expected_variant(K.K_UPDATE_CHAIN, K.F64, 12) == K.VARIANT_JIT
+    tile = K.parse_key(bytes.fromhex(key))["tile"]
+    assert key == K.canonical_key(K.K_UPDATE_CHAIN, K.F64, n=12, tile=tile).hex()
+    assert tile in cj.candidates(cj.K_UPDATE_CHAIN, cj.F64, n=12)
+    assert int(variant) == K.expected_variant(K.K_UPDATE_CHAIN, K.F64, 12, True) == K.VARIANT_JIT
     assert int(refused) == cj.CJ_ERR_INVALID_ARG
     assert int(requests) >= 1 and int(compiles_ok) >= 1
 
@@ -275,7 +343,8 @@ def test_plain_c_client(tmp_path):
 def test_lplustimes_keys_and_compiles(compile_only_sync):
     from oracle import keys as K
     h = cj.specialize(cj.K_LPLUSTIMES, cj.F64, layout_a=3, layout_b=1, m=36, d=96)
-    assert h.key_hex == K.canonical_key(K.K_LPLUSTIMES, K.F64, layout_a=3, layout_b=1, m=36, d=96).hex()
+    tile = K.parse_key(bytes.fromhex(h.key_hex))["tile"]
+    assert h.key_hex == K.canonical_key(K.K_LPLUSTIMES, K.F64, layout_a=3, layout_b=1, m=36, d=96, tile=tile).hex()
     assert h.variant == "jit"
     assert cj.specialize(cj.K_LPLUSTIMES, cj.F32, layout_a=0, layout_b=5, m=36, d=96).variant == "jit"
     assert len(cj.candidates(cj.K_LPLUSTIMES, cj.F32, layout_a=0, layout_b=5, m=36, d=96)) >= 4

@@ -116,12 +116,31 @@ int main() {
 """
 
 
-def test_tensor_core_ltimes_smem_matches_the_key_restatement(tmp_path):
+def _tc_smem_model(m, d, stages, tg, tz, lout, boxes):
+    """Shared-memory bytes of the tcgen05 LTimes kernel, summed buffer by
+    buffer from the layout the kernel documents: 1 KiB of alignment slack;
+    `boxes` TMA boxes of 128 x 32 floats; per operand stage two 128 x 32 tf32
+    tiles (hi, lo) of 16 core-matrix groups of 1168 bytes (8 rows x 144-byte
+    K-adjacent units, with the 16-byte pads); L's hi and lo parts with the
+    moments padded to 16 and the directions to 32; the staged out box: for
+    m fastest, 128 rows of mp floats (mp a multiple of 4 with mp / 4 odd),
+    otherwise m rows of 128 / run runs, each padded by 4 floats when at
+    least 8 long (run = the box extent of out's fastest axis)."""
+    np_, dp = -(-m // 16) * 16, -(-d // 32) * 32
+    if lout in (3, 5):
+        b = -(-m // 4)
+        box = 128 * (4 * b if b % 2 else 4 * b + 4)
+    else:
+        run = tg if lout in (1, 4) else tz
+        box = m * (128 // run) * (run + 4 if run >= 8 else run)
+    return 1024 + boxes * 128 * 32 * 4 + stages * 2 * 16 * 1168 + 2 * np_ * dp * 4 + box * 4
+
+
+def test_tensor_core_ltimes_smem_matches_its_layout(tmp_path):
     """The tcgen05 LTimes kernel's shared-memory size in geometry.h equals the
-    restatement the default-tile oracle uses (oracle/keys.py), over a grid of
+    sum of its buffers as the kernel's layout describes them, over a grid of
     moments, directions, operand stages, column tiles, out orders and TMA
     boxes."""
-    from oracle import keys as K
     src, exe = tmp_path / "lt.cpp", tmp_path / "lt"
     src.write_text(LT_PROG)
     subprocess.run(["g++", "-std=c++17", "-O1", "-I", CSRC, "-o", str(exe), str(src)], check=True)
@@ -130,7 +149,7 @@ def test_tensor_core_ltimes_smem_matches_the_key_restatement(tmp_path):
     assert len(lines) == 8 * 6 * 3 * 3 * 6 * 3
     for l in lines:
         m, d, stages, tg, lout, boxes, smem = (int(v) for v in l.split())
-        assert K._tc_smem(m, d, stages, tg, 128 // tg, lout, boxes) == smem, l
+        assert _tc_smem_model(m, d, stages, tg, 128 // tg, lout, boxes) == smem, l
 
 
 REG_PROG = r"""
