@@ -191,6 +191,14 @@ typedef struct {
      * the mode-4 kernel because `in` admitted no tensor map (innermost extent
      * not a multiple of 4 floats, or `in` not 16-byte aligned) */
     uint64_t launches_tma, launches_tma_fallback;
+    /* Expired bounded waits of the tensor-core LTimes kernels (tile modes 4
+     * and 5), summed over every run-time-compiled module and not yet cleared
+     * through cj_handle_wait_timeouts(reset != 0).  A block whose wait expired
+     * stopped early: any output written by a launch before a non-zero count
+     * was seen is incomplete and must not be used.  Reading it synchronizes
+     * the device when such a module is loaded (cj_stats then waits for all
+     * queued work); it is 0 without synchronizing otherwise. */
+    uint64_t wait_timeouts;
 } cj_stats_t;
 
 /* Initialise the library for `device` (idempotent for the same device).
@@ -244,7 +252,8 @@ cj_status cj_specialize_wait(cj_handle h, int timeout_ms);
  * the launch failed. */
 cj_status cj_launch(cj_handle h, void *const *args, int64_t batch, void *cuda_stream);
 
-/* Counters since cj_init; compile times are NVRTC + module load wall time. */
+/* Counters since cj_init; compile times are NVRTC + module load wall time.
+ * CJ_ERR_CUDA if reading wait_timeouts failed (the other fields are set). */
 cj_status cj_stats(cj_stats_t *out);
 
 /* Canonical key (64 hex chars + NUL, needs cap >= 65) and the variant that
@@ -300,6 +309,12 @@ cj_status cj_group_plan_create(int32_t dtype, int64_t count, const int32_t *n, c
  * are caller-owned device memory. */
 cj_status cj_group_plan_launch(cj_group_plan p, const void *A_pool, void *X_pool, void *cuda_stream,
                                int use_graph);
+/* Wait up to timeout_ms (negative: forever) for the instantiations of every
+ * group of p to finish compiling.  CJ_OK: every group launches its
+ * specialized kernel.  CJ_ERR_TIMEOUT: some are still compiling (launches
+ * meanwhile use the generic grouped kernel for them).  CJ_ERR_COMPILE: a
+ * group's compilation failed; that group keeps the generic kernel. */
+cj_status cj_group_plan_wait(cj_group_plan p, int timeout_ms);
 /* Groups in the plan and pool elements it expects. */
 /* Autotune a plan's tiles (the batching pattern's autotuned tiles): for each
  * of the max_groups most expensive groups (0: all), every candidate tile of
@@ -342,13 +357,18 @@ cj_status cj_measure_fma_peak(int32_t dtype, int32_t tensor, void *cuda_stream, 
  *   1.5 MiB) that every GPU which loads this library holds until the process
  *   exits.  count > CJ_NOALLOC_MAX_INSTANCES returns CJ_ERR_INVALID_ARG.
  *   The first call on a device looks up that array's device address (with
- *   the device current) and sets kernel attributes; make that first call
- *   before any stream capture on the device.
+ *   the device current) and sets kernel attributes.  cj_shutdown forgets
+ *   this set-up; a caller that resets a device (cudaDeviceReset) calls
+ *   cj_shutdown before the next call on it.
  *   Every call reuses the same array and resets its counters at the start;
  *   calls whose work overlaps on the GPU (other streams, or other host
  *   threads on the same device) race on it and must be serialized by the
- *   caller.  The work list is copied from host memory with cudaMemcpyAsync
- *   on cuda_stream.
+ *   caller.  The work list is built in pageable host memory that the call
+ *   owns and copied with cudaMemcpyAsync on cuda_stream: the CUDA runtime
+ *   stages such a copy, so the call returns only after the work queued
+ *   earlier on cuda_stream has finished, and the call must not be made while
+ *   cuda_stream (or its device, in global capture mode) is being captured
+ *   into a CUDA graph.
  * dtype: CJ_F64 or CJ_F32; n[k] in 1..64; steps[k] >= 1; A_pool, X_pool are
  * caller-owned device memory.  Errors: CJ_ERR_INVALID_ARG (bad arguments,
  * too many instances), CJ_ERR_NO_DEVICE, CJ_ERR_CUDA (cj_last_error has the

@@ -23,7 +23,7 @@ VARIANT_NAMES = ("generic", "aot", "jit")
 
 EXPORTS = ("cj_init", "cj_specialize", "cj_specialize_wait", "cj_launch", "cj_stats", "cj_handle_info",
            "cj_handle_regs", "cj_handle_wait_timeouts", "cj_group_plan_create", "cj_group_plan_launch",
-           "cj_group_plan_autotune", "cj_group_plan_info",
+           "cj_group_plan_autotune", "cj_group_plan_wait", "cj_group_plan_info",
            "cj_group_plan_destroy", "cj_measure_fma_peak", "cj_update_chain_uneven_noalloc", "cj_candidates",
            "cj_autotune", "cj_featurize", "cj_mlp_create", "cj_mlp_set_params", "cj_mlp_get_params",
            "cj_mlp_forward", "cj_mlp_grad", "cj_mlp_train_step", "cj_mlp_destroy", "cj_cost_model_use",
@@ -53,7 +53,7 @@ class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("requests", "cache_hits", "compiles_ok", "compiles_failed",
                                                "aot_hits", "launches_generic", "launches_aot", "launches_jit")] + \
                [(n, ctypes.c_double) for n in ("compile_ms_p50", "compile_ms_p95", "lookup_ns_p50")] + \
-               [(n, ctypes.c_uint64) for n in ("launches_tma", "launches_tma_fallback")]
+               [(n, ctypes.c_uint64) for n in ("launches_tma", "launches_tma_fallback", "wait_timeouts")]
 
 
 _lib = None
@@ -81,6 +81,7 @@ def load():
         L.cj_group_plan_create.argtypes = [i32, i64, P, P, ctypes.c_uint32, ctypes.POINTER(P)]
         L.cj_group_plan_launch.argtypes = [P, P, P, P, ctypes.c_int]
         L.cj_group_plan_autotune.argtypes = [P, P, P, P, i32, i32, ctypes.POINTER(i32)]
+        L.cj_group_plan_wait.argtypes = [P, ctypes.c_int]
         L.cj_group_plan_info.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i64)]
         L.cj_group_plan_destroy.argtypes = [P]
         L.cj_measure_fma_peak.argtypes = [i32, i32, P, ctypes.POINTER(ctypes.c_double)]
@@ -250,6 +251,22 @@ def measure_fma_peak(dtype: int, stream=None, tensor: bool = False) -> float:
 NOALLOC_MAX_INSTANCES = 65536
 
 
+def _check_pool(t, dtype: int, elems: int, where: str) -> None:
+    """A pool tensor must be a contiguous CUDA tensor of the dtype's element
+    type (fp32 state for BF16) holding at least `elems` elements; otherwise
+    the kernels would read or write past the caller's memory.  Raw integer
+    device addresses are passed through unchecked."""
+    if t is None or isinstance(t, int):
+        return
+    import torch
+    want = torch.float64 if dtype == F64 else torch.float32
+    if not t.is_cuda or t.dtype != want or not t.is_contiguous() or t.numel() < elems:
+        raise CJError(CJ_ERR_INVALID_ARG, where,
+                      f"pool must be a contiguous CUDA {want} tensor of at least {elems} elements "
+                      f"(got {t.dtype}, {t.numel()} elements, device {t.device}, "
+                      f"contiguous {t.is_contiguous()})")
+
+
 def update_chain_uneven_noalloc(dtype: int, n, steps, A_pool, X_pool, stream=None) -> None:
     """cj_update_chain_uneven_noalloc: the uneven update chain without any
     device allocation (scratch in a fixed array inside the library); for
@@ -257,6 +274,9 @@ def update_chain_uneven_noalloc(dtype: int, n, steps, A_pool, X_pool, stream=Non
     import numpy as np
     n = np.ascontiguousarray(n, dtype=np.int32)
     steps = np.ascontiguousarray(steps, dtype=np.int32)
+    elems = int(np.sum(n.astype(np.int64) ** 2))
+    _check_pool(A_pool, dtype, elems, "cj_update_chain_uneven_noalloc")
+    _check_pool(X_pool, dtype, elems, "cj_update_chain_uneven_noalloc")
     _check(load().cj_update_chain_uneven_noalloc(dtype, len(n), n.ctypes.data, steps.ctypes.data, _ptr(A_pool),
                                                   _ptr(X_pool), _stream(stream, A_pool, X_pool)),
            "cj_update_chain_uneven_noalloc")
@@ -279,20 +299,29 @@ class GroupPlan:
         _check(load().cj_group_plan_create(dtype, len(n), n.ctypes.data, steps.ctypes.data, flags,
                                            ctypes.byref(out)), "cj_group_plan_create")
         self.ptr = out.value
+        self.dtype = dtype
         g, e = ctypes.c_int32(0), ctypes.c_int64(0)
         _check(load().cj_group_plan_info(self.ptr, ctypes.byref(g), ctypes.byref(e)), "cj_group_plan_info")
         self.n_groups, self.pool_elems = g.value, e.value
 
     def launch(self, A_pool, X_pool, stream=None, use_graph=True) -> None:
+        _check_pool(A_pool, self.dtype, self.pool_elems, "cj_group_plan_launch")
+        _check_pool(X_pool, self.dtype, self.pool_elems, "cj_group_plan_launch")
         _check(load().cj_group_plan_launch(self.ptr, _ptr(A_pool), _ptr(X_pool), _stream(stream, A_pool, X_pool),
                                            int(use_graph)), "cj_group_plan_launch")
 
     def autotune(self, A_pool, X_pool, stream=None, max_groups: int = 0, reps: int = 3) -> int:
         """Time every candidate tile per group (most expensive first) and keep the fastest; returns groups changed."""
+        _check_pool(A_pool, self.dtype, self.pool_elems, "cj_group_plan_autotune")
+        _check_pool(X_pool, self.dtype, self.pool_elems, "cj_group_plan_autotune")
         ch = ctypes.c_int32(0)
         _check(load().cj_group_plan_autotune(self.ptr, _ptr(A_pool), _ptr(X_pool), _stream(stream, A_pool, X_pool),
                                              max_groups, reps, ctypes.byref(ch)), "cj_group_plan_autotune")
         return ch.value
+
+    def wait(self, timeout_ms: int = -1) -> None:
+        """Block until every group's instantiation is compiled (async mode)."""
+        _check(load().cj_group_plan_wait(self.ptr, timeout_ms), "cj_group_plan_wait")
 
     def destroy(self) -> None:
         if self.ptr:

@@ -140,6 +140,7 @@ struct cj_handle_s {
     std::mutex mu;
     std::condition_variable cv;
     CUlibrary lib = nullptr;
+    CUdeviceptr wait_count = 0;   // the module's cj_wait_timeouts, if it has bounded waits
     std::string name_expr, name_expr2, error;
     double compile_ms = 0;
 };
@@ -655,6 +656,10 @@ cj_status compile_handle(cj_handle_s *h) {
             return CJ_ERR_COMPILE;
         }
         s.blocks_per_sm = occupancy(s.fn, s.threads, s.smem);
+        CUdeviceptr wp = 0;
+        size_t wbytes = 0;
+        if (drv.LibraryGetGlobal(&wp, &wbytes, h->lib, "cj_wait_timeouts") == CUDA_SUCCESS && wbytes == sizeof(uint32_t))
+            h->wait_count = wp;
         h->impl.store(&h->spec, std::memory_order_release);
     }
     h->compile_ms = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
@@ -1103,10 +1108,32 @@ CJ_API cj_status cj_stats(cj_stats_t *out) {
     out->launches_jit = G.l_jit;
     out->launches_tma = G.l_tma;
     out->launches_tma_fallback = G.l_tma_fb;
-    std::lock_guard<std::mutex> lk(G.smu);
-    out->compile_ms_p50 = percentile(G.compile_ms, 0.5);
-    out->compile_ms_p95 = percentile(G.compile_ms, 0.95);
-    out->lookup_ns_p50 = percentile(G.lookup_ns, 0.5);
+    {
+        std::lock_guard<std::mutex> lk(G.smu);
+        out->compile_ms_p50 = percentile(G.compile_ms, 0.5);
+        out->compile_ms_p95 = percentile(G.compile_ms, 0.95);
+        out->lookup_ns_p50 = percentile(G.lookup_ns, 0.5);
+    }
+    // expired bounded waits: the counters of every module that has them,
+    // read after all queued work has finished
+    out->wait_timeouts = 0;
+    if (G.compile_only) return CJ_OK;
+    std::vector<CUdeviceptr> counters;
+    {
+        std::lock_guard<std::mutex> lk(G.mu);
+        for (const auto &kv : G.cache)
+            if (kv.second->state.load(std::memory_order_acquire) == ST_READY && kv.second->wait_count)
+                counters.push_back(kv.second->wait_count);
+    }
+    if (counters.empty()) return CJ_OK;
+    if (cudaDeviceSynchronize() != cudaSuccess)
+        return fail(CJ_ERR_CUDA, "cj_stats: device synchronize failed: %s", cudaGetErrorString(cudaGetLastError()));
+    for (CUdeviceptr p : counters) {
+        uint32_t c = 0;
+        if (cudaMemcpy(&c, reinterpret_cast<void *>(p), sizeof c, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return fail(CJ_ERR_CUDA, "cj_stats: reading a wait-timeout counter failed");
+        out->wait_timeouts += c;
+    }
     return CJ_OK;
 }
 
@@ -1143,11 +1170,9 @@ CJ_API cj_status cj_handle_wait_timeouts(cj_handle h, uint32_t *count, int reset
     if (!h || !count) return fail(CJ_ERR_INVALID_ARG, "null handle or count");
     if (G.compile_only) return fail(CJ_ERR_NO_DEVICE, "compile-only mode");
     *count = 0;
-    if (!h->lib) return CJ_OK;   // no JIT module: AoT or generic kernels, which do not wait
-    CUdeviceptr p = 0;
-    size_t bytes = 0;
-    if (drv.LibraryGetGlobal(&p, &bytes, h->lib, "cj_wait_timeouts") != CUDA_SUCCESS || bytes != sizeof(uint32_t))
-        return CJ_OK;              // a module without bounded waits
+    // no JIT module (AoT or generic kernels), or a module without bounded waits
+    if (h->state.load(std::memory_order_acquire) != ST_READY || !h->wait_count) return CJ_OK;
+    const CUdeviceptr p = h->wait_count;
     if (cudaDeviceSynchronize() != cudaSuccess ||
         cudaMemcpy(count, reinterpret_cast<void *>(p), sizeof(uint32_t), cudaMemcpyDeviceToHost) != cudaSuccess ||
         (reset && cudaMemset(reinterpret_cast<void *>(p), 0, sizeof(uint32_t)) != cudaSuccess))
@@ -1351,6 +1376,23 @@ CJ_API cj_status cj_group_plan_autotune(cj_group_plan p, const void *A_pool, voi
     return rc;
 }
 
+CJ_API cj_status cj_group_plan_wait(cj_group_plan p, int timeout_ms) {
+    if (!G.inited) return fail(CJ_ERR_NOT_INITIALIZED, "cj_init has not been called");
+    if (!p) return fail(CJ_ERR_INVALID_ARG, "null plan");
+    const auto end = clk::now() + std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms);
+    cj_status worst = CJ_OK;
+    for (auto &g : p->groups) {
+        int left = -1;
+        if (timeout_ms >= 0)
+            left = (int)std::max<long long>(
+                0, std::chrono::duration_cast<std::chrono::milliseconds>(end - clk::now()).count());
+        const cj_status rc = cj_specialize_wait(g.h, left);
+        if (rc == CJ_ERR_TIMEOUT) return rc;
+        if (rc != CJ_OK) worst = rc;
+    }
+    return worst == CJ_OK ? CJ_OK : fail(worst, "a group's instantiation failed to compile; it runs generic");
+}
+
 CJ_API cj_status cj_group_plan_info(cj_group_plan p, int32_t *n_groups, int64_t *pool_elems) {
     if (!p) return fail(CJ_ERR_INVALID_ARG, "null plan");
     if (n_groups) *n_groups = (int32_t)p->groups.size();
@@ -1435,6 +1477,7 @@ CJ_API cj_status cj_shutdown(void) {
     G.cache.clear();
     G.queue.clear();
     G.decisions.clear();
+    cjint::noalloc_forget();
     G.inited = false;
     return CJ_OK;
 }

@@ -15,7 +15,7 @@ import synth
 from paper_1904_08555_b300 import cj
 
 torch = pytest.importorskip("torch")
-pytestmark = pytest.mark.gpu
+pytestmark = [pytest.mark.gpu, pytest.mark.injects_wait_timeouts]
 
 TOL32 = 1e-5
 
@@ -43,6 +43,7 @@ def test_expired_waits_are_reported_and_the_context_survives(tile):
     assert bad.wait_timeouts(reset=True) == 0
     cj.launch_ltimes(bad, Lt, xt, out, G, Z)
     torch.cuda.synchronize()                    # returns: no block waits forever
+    assert cj.stats()["wait_timeouts"] >= 1    # surfaced in the library-wide counters
     n = bad.wait_timeouts(reset=True)
     assert 1 <= n <= 16, n
     assert bad.wait_timeouts() == 0             # reset
@@ -53,3 +54,4 @@ def test_expired_waits_are_reported_and_the_context_survives(tile):
     got = out.double().cpu().numpy().reshape(M, G, Z)
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= TOL32
     assert good.wait_timeouts() == 0
+    assert cj.stats()["wait_timeouts"] == 0     # the total over all modules, after the reset
