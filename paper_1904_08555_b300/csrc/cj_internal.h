@@ -60,6 +60,9 @@ bool cost_model_tile(int k, const cj_template_args &a, int *tile_out);
 // rule documented in cj.h; no cost model).
 void default_tile_of(int k, const cj_template_args &a, int tile_out[4]);
 
+// Drop the allocation-free entry point's per-device set-up (noalloc.cu).
+void noalloc_forget();
+
 // Set the thread-local message returned by cj_last_error (used by the
 // allocation-free entry point in noalloc.cu).
 void set_last_error(const char *msg);

@@ -119,10 +119,12 @@ cj_status scratch_for_current_device(int *dev_out, void **out) {
         const void *k64 = (const void *)&chain_uneven_noalloc<double>;
         const void *k32 = (const void *)&chain_uneven_noalloc<float>;
         int optin = 0;
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         cudaFuncAttributes fa64{}, fa32{};
-        cudaFuncGetAttributes(&fa64, k64);
-        cudaFuncGetAttributes(&fa32, k32);
+        if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess ||
+            (e = cudaFuncGetAttributes(&fa64, k64)) != cudaSuccess ||
+            (e = cudaFuncGetAttributes(&fa32, k32)) != cudaSuccess)
+            return na_fail(CJ_ERR_CUDA, std::string("cj_update_chain_uneven_noalloc: reading the device or kernel "
+                                                    "attributes failed: ") + cudaGetErrorString(e));
         if (cudaFuncSetAttribute(k64, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  optin - (int)fa64.sharedSizeBytes) != cudaSuccess ||
             cudaFuncSetAttribute(k32, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -171,6 +173,14 @@ cj_status run(const std::vector<long long> &items, const std::vector<int> &group
 }
 
 }  // namespace
+
+// Forget the per-device set-up (called by cj_shutdown): after a
+// cudaDeviceReset the array's address and the kernels' attributes belong to a
+// context that no longer exists, so the next call must look them up again.
+void cjint::noalloc_forget() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto &p : g_scratch) p = nullptr;
+}
 
 extern "C" __attribute__((visibility("default"))) cj_status
 cj_update_chain_uneven_noalloc(int32_t dtype, int64_t count, const int32_t *n, const int32_t *steps,
