@@ -98,14 +98,31 @@ def update_chain(A: np.ndarray, steps: int, layout: int = 0, nthreads: int = 1) 
 
 
 def update_chain_uneven(n: np.ndarray, t: np.ndarray, offsets: np.ndarray,
-                        A_pool: np.ndarray) -> np.ndarray:
+                        A_pool: np.ndarray, nthreads: int = 1) -> np.ndarray:
+    """X pool of the uneven chain.  nthreads > 1 splits the instance list into
+    contiguous slices run by host threads (the foreign call releases the
+    interpreter lock); instances are independent and each slice writes only
+    its own instances, so the arithmetic is unchanged."""
     n = np.ascontiguousarray(n, dtype=np.int64)
     t = np.ascontiguousarray(t, dtype=np.int64)
     offsets = np.ascontiguousarray(offsets, dtype=np.int64)
     A_pool = _f64(A_pool)
     X_pool = np.zeros_like(A_pool)
-    rc = _load().oracle_update_chain_uneven(len(n), _p(n), _p(t), _p(offsets), _p(A_pool), _p(X_pool))
-    if rc != 0:
+    lib = _load()
+
+    def run(k0, k1):
+        return lib.oracle_update_chain_uneven(k1 - k0, _p(n[k0:]), _p(t[k0:]), _p(offsets[k0:]), _p(A_pool),
+                                              _p(X_pool))
+
+    nthreads = max(1, min(int(nthreads), len(n)))
+    if nthreads == 1:
+        rcs = [run(0, len(n))]
+    else:
+        from concurrent.futures import ThreadPoolExecutor
+        bounds = [len(n) * i // nthreads for i in range(nthreads + 1)]
+        with ThreadPoolExecutor(nthreads) as ex:
+            rcs = list(ex.map(run, bounds[:-1], bounds[1:]))
+    if any(rc != 0 for rc in rcs):
         raise ValueError("oracle_update_chain_uneven: invalid arguments")
     return X_pool
 
