@@ -195,7 +195,10 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    sizes = calibrated_sizes(args.cpu_seconds / (args.steps + args.warmup))
+    # every step is one oracle sweep over the same sample as the cpu_baseline
+    # leg of the GPU arm (about --cpu-seconds of work), so both legs time
+    # the oracle the same way
+    sizes = calibrated_sizes(args.cpu_seconds)
     for _ in range(args.warmup):
         run_oracle_sweep(sizes)
     tot_f, tot_s = 0.0, 0.0
@@ -224,7 +227,10 @@ def cj_arm(args):
 
     world, rank, local = dist_setup(args.gpus)
     dev = torch.cuda.current_device()
-    cj.init(sync=True, compile_threads=4, device=dev)
+    # asynchronous specializer: instantiations compile on background threads
+    # in parallel; every timed launch below waits for its handle first
+    compile_threads = min(16, os.cpu_count() or 4)
+    cj.init(sync=False, compile_threads=compile_threads, device=dev)
     stream = torch.cuda.Stream()
 
     # inputs: rank r holds instances [r*batch, (r+1)*batch) of each size
@@ -240,8 +246,11 @@ def cj_arm(args):
 
     t0 = time.perf_counter()
     spec = {n: cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=n, flags=cj.FLAG_NO_AOT) for n in SWEEP_N}
+    for h in spec.values():
+        assert h.wait() == cj.CJ_OK
     compile_wall = time.perf_counter() - t0
     st = cj.stats()
+    sweep_compile = {"p50": st["compile_ms_p50"], "p95": st["compile_ms_p95"], "keys": len(SWEEP_N)}
     gen = {n: cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=n, flags=cj.FLAG_GENERIC) for n in SWEEP_N}
     aot = {n: cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=n) for n in AOT_N}
     assert all(h.variant == "jit" for h in spec.values())
@@ -359,7 +368,9 @@ def cj_arm(args):
             "generic": {"value": gen_value, "unit": "GFLOP/s", "ms_per_step": ms_gen / args.steps},
             "speedup_vs_generic": value / gen_value,
             "jit_compile_ms_p50": st["compile_ms_p50"], "jit_compile_ms_p95": st["compile_ms_p95"],
+            "jit_compile_ms_sweep_keys": sweep_compile, "jit_compile_threads": compile_threads,
             "lookup_ns_p50": st["lookup_ns_p50"], "compile_wall_s_9_sizes": compile_wall,
+
             "fp64_fma_pipe_tflops_measured": micro64, "fp64_tensor_tflops_measured": tensor64,
             "fp64_nominal_tflops": PEAK_TFLOPS["f64"],
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
@@ -376,7 +387,7 @@ def cj_arm(args):
             "clocks": clocks}
 
     if rank == 0 and not args.no_cpu_baseline:
-        sizes = calibrated_sizes(args.cpu_seconds / 4)
+        sizes = calibrated_sizes(args.cpu_seconds)   # the reference arm's per-step sample
         f, s, outs, cores = run_oracle_sweep(sizes, rank_offset=0)
         worst = 0.0
         for n in SWEEP_N:
@@ -388,6 +399,28 @@ def cj_arm(args):
                                 "sample": f"first {sizes[3]} (N=3) .. {sizes[32]} (N=32) instances of each size, "
                                           f"{f / 1e9:.1f} GFLOP, {s:.1f} s"}
         line["max_rel_frobenius_error_vs_oracle"] = worst
+    # the other workloads, in the same run: config 1 (64 x N = 8), config 3
+    # (LTimes, 36 orders, FP64 and FP32) and config 4 (10,000-instance uneven
+    # batch, FP64 / FP32 / BF16), each with its error against the oracle
+    workloads = {}
+    if rank == 0 and not args.sweep_only:
+        del A, X, host_A, host_X
+        torch.cuda.empty_cache()
+        lt_reps = max(3, min(args.steps, 5))
+        with torch.cuda.stream(stream):
+            workloads["config1_small"] = run_config1(torch, cj, stream, args.warmup)
+            for d in ("f64", "f32"):
+                _request_ltimes(cj, d)
+                workloads["config3_ltimes_" + d] = run_config3(torch, cj, stream, d, 1 << 18, lt_reps)
+            st13 = cj.stats()
+            ref = uneven_reference(("f64", "f32", "bf16"))
+            for d in ("f64", "f32", "bf16"):
+                workloads["config4_uneven_" + d] = run_config4(torch, cj, stream, d, 10, args.warmup, ref)
+        workloads["jit_compile_ms_configs_1_to_3"] = {"p50": st13["compile_ms_p50"], "p95": st13["compile_ms_p95"],
+                                                      "compiles": st13["compiles_ok"],
+                                                      "compile_threads": compile_threads}
+    line["workloads"] = workloads
+    line["wait_timeouts"] = cj.stats()["wait_timeouts"]
     if rank == 0:
         print(json.dumps(line), flush=True)
     cj.shutdown()
@@ -417,8 +450,9 @@ def main():
     p.add_argument("--heldout", type=int, default=2000)
     p.add_argument("--train-steps", type=int, default=4000)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-seconds", type=float, default=60.0,
-                   help="oracle time budget: reference arm whole run; cpu_baseline leg uses a quarter")
+    p.add_argument("--sweep-only", action="store_true", help="default line without the config 1/3/4 sub-objects")
+    p.add_argument("--cpu-seconds", type=float, default=4.0,
+                   help="oracle seconds per sweep sample: one reference-arm step, and the cpu_baseline leg")
     args = p.parse_args()
     if args.warmup < 3:
         p.error("--warmup must be >= 3")
@@ -434,15 +468,15 @@ def main():
     args.lt_alt_tiles = lt_alt_tiles
     if args.impl == "reference":
         reference_arm(args)
-    elif args.workload != "sweep":
-        if args.workload == "uneven":
-            # 32 hardware work queues instead of 8, so that up to 32 of the plan's
-            # group kernels overlap when it is launched on its streams; read when
-            # the CUDA context is created, hence before torch touches the device
-            os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
-        secondary(args)
     else:
-        cj_arm(args)
+        # 32 hardware work queues instead of 8, so that up to 32 of a grouped
+        # plan's kernels overlap when it is launched on its streams; read when
+        # the CUDA context is created, hence before torch touches the device
+        os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+        if args.workload != "sweep":
+            secondary(args)
+        else:
+            cj_arm(args)
 
 
 
@@ -460,6 +494,244 @@ def _events(torch, stream, fn, reps):
     return e0.elapsed_time(e1) / reps
 
 
+def _key_tile(h):
+    key = bytes.fromhex(h.key_hex)
+    return [int.from_bytes(key[12 + 4 * i:16 + 4 * i], "little") for i in range(4)]
+
+
+def _relF_rows(got, ref):
+    got = got.reshape(ref.shape[0], -1)
+    ref = ref.reshape(ref.shape[0], -1)
+    return np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+
+
+def run_config1(torch, cj, stream, W):
+    """64 FP64 8x8 chains, T = 100: the library's default tile, the tile the
+    autotuner picks for this batch, the AoT specialization and the generic
+    kernel, each checked against the oracle on every instance."""
+    import oracle
+    n, b, steps, reps = 8, 64, 100, 200
+    A_np = synth.chain_inputs_np(synth.SEED_CHAIN_SMALL, b, n)
+    ref = oracle.update_chain(A_np, steps)
+    A = torch.from_numpy(A_np).cuda()
+    X = torch.empty_like(A)
+    f = chain_flops(b, n, steps)
+    row, worst = {"N": n, "batch": b, "T": steps}, 0.0
+
+    def timed(name, h):
+        nonlocal worst
+        assert h.wait() == cj.CJ_OK
+        fn = lambda: cj.launch_update_chain(h, A, X, steps, stream=stream)
+        _events(torch, stream, fn, W)
+        ms = _events(torch, stream, fn, reps)
+        stream.synchronize()
+        worst = max(worst, float(_relF_rows(X.cpu().numpy(), ref).max()))
+        row.update({name + "_us": ms * 1e3, name + "_gflops": f / ms / 1e6, name + "_regs": h.regs()[0],
+                    name + "_tile": _key_tile(h)})
+
+    timed("default", cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=n, flags=cj.FLAG_NO_AOT))
+    timed("aot", cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=n))
+    timed("generic", cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=n, flags=cj.FLAG_GENERIC))
+    # the autotuner's choice for this exact batch (tile spaces include one
+    # instance per block, which a 64-instance batch needs)
+    best, times = cj.autotune(cj.K_UPDATE_CHAIN, cj.F64, cj.chain_launch_vals(A, X, steps), b, stream, reps=20, n=n)
+    timed("autotuned", cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=n, tile=best))
+    row["candidates_us"] = {str(list(t)): v * 1e3 for t, v in times}
+    return {"value": f / row["autotuned_us"] / 1e3, "dtype": "f64", "us": row["autotuned_us"],
+            "generic": {"value": f / row["generic_us"] / 1e3, "unit": "GFLOP/s", "us": row["generic_us"]},
+            "speedup_vs_generic": row["generic_us"] / row["autotuned_us"],
+            "default_tile_speedup_vs_generic": row["generic_us"] / row["default_us"],
+            "max_rel_frobenius_error_vs_oracle": worst, "per_n": [row],
+            "roofline": {"bound": "alu", "peak": PEAK_TFLOPS["f64"], "unit": "TFLOP/s",
+                         "frac": f / row["autotuned_us"] / 1e6 / PEAK_TFLOPS["f64"],
+                         "note": "latency-bound by size: 64 instances on 148 SMs"},
+            "config": {"workload": "update chain, 64 FP64 8x8 matrices, T = 100 (seed 0xC1A1); value = the "
+                                   "autotuned JIT instantiation, the default tile beside it"}}
+
+
+def _request_ltimes(cj, dtype):
+    """Request the 36 default-tile LTimes instantiations at once (they compile
+    in parallel in asynchronous mode) and wait for all of them."""
+    dt = cj.F64 if dtype == "f64" else cj.F32
+    hs = [cj.specialize(cj.K_LTIMES, dt, layout_a=lin, layout_b=lout, m=36, d=96)
+          for lin in range(6) for lout in range(6)]
+    for h in hs:
+        assert h.wait() == cj.CJ_OK
+
+
+def run_config3(torch, cj, stream, dtype, Z, reps, alt_tiles=None, samples=384):
+    """LTimes over all 36 (in, out) storage orders at M 36, D 96, G 32: the
+    default (specialized) tile and the generic kernel, mean ms per order pair;
+    each timed output checked against the oracle on `samples` seeded columns;
+    expired bounded waits of the tensor-core kernels read afterwards."""
+    import oracle
+    dt = cj.F64 if dtype == "f64" else cj.F32
+    tdt = torch.float64 if dt == cj.F64 else torch.float32
+    es = 8 if dt == cj.F64 else 4
+    M, D, G = 36, 96, 32
+    L, _ = synth.ltimes_inputs_np(synth.SEED_LTIMES, M, D, 1, 1)
+    Lt = torch.from_numpy(L).to("cuda", tdt)
+    x = synth.uniform_torch(synth.SEED_LTIMES, synth.STREAM_A, D * G * Z, "cuda").view(D, G, Z).to(tdt)
+    rng = np.random.default_rng(0xC1A3)
+    gs = torch.from_numpy(rng.integers(0, G, samples)).cuda()
+    zs = torch.from_numpy(rng.integers(0, Z, samples)).cuda()
+    cols = x[:, gs, zs].double().cpu().numpy()
+    ref = oracle.ltimes(L, cols.ravel(), 1, samples, 0, 0)          # [m][sample]
+    xin = {lin: x.permute(*synth.LAYOUT_PERMS[lin]).contiguous().view(-1) for lin in range(6)}
+    del x
+    o = torch.empty(M * G * Z, device="cuda", dtype=tdt)
+    f = 2.0 * M * D * G * Z
+    byt = es * ((D + M) * G * Z + M * D)
+
+    def err_of(lout):
+        pout = o.view(*[(M, G, Z)[p] for p in synth.LAYOUT_PERMS[lout]])
+        canon = pout.permute(*np.argsort(synth.LAYOUT_PERMS[lout]).tolist())
+        got = canon[:, gs, zs].double().cpu().numpy()
+        return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+    wt0 = cj.stats()["wait_timeouts"]
+    rows, tot_s, tot_g, worst = [], 0.0, 0.0, 0.0
+    for lin in range(6):
+        for lout in range(6):
+            hs = cj.specialize(cj.K_LTIMES, dt, layout_a=lin, layout_b=lout, m=M, d=D)
+            hg = cj.specialize(cj.K_LTIMES, dt, layout_a=lin, layout_b=lout, m=M, d=D, flags=cj.FLAG_GENERIC)
+            fs = lambda: cj.launch_ltimes(hs, Lt, xin[lin], o, G, Z, stream=stream)
+            fg = lambda: cj.launch_ltimes(hg, Lt, xin[lin], o, G, Z, stream=stream)
+            _events(torch, stream, fs, 1)
+            ms_s = _events(torch, stream, fs, reps)
+            e_s = err_of(lout)
+            _events(torch, stream, fg, 1)
+            ms_g = _events(torch, stream, fg, reps)
+            e_g = err_of(lout)
+            worst = max(worst, e_s, e_g)
+            row = {"in": synth.LAYOUT_NAMES[lin], "out": synth.LAYOUT_NAMES[lout].replace("D", "M"),
+                   "spec_ms": ms_s, "generic_ms": ms_g, "spec_gbs": byt / ms_s / 1e6,
+                   "speedup_vs_generic": ms_g / ms_s, "spec_rel_err": e_s, "tile": _key_tile(hs)}
+            for name, alt in (alt_tiles(lin, lout) if alt_tiles else []):
+                ha = cj.specialize(cj.K_LTIMES, dt, layout_a=lin, layout_b=lout, m=M, d=D, tile=alt)
+                ha.wait()
+                fa = lambda: cj.launch_ltimes(ha, Lt, xin[lin], o, G, Z, stream=stream)
+                _events(torch, stream, fa, 1)
+                row[name + "_ms"] = _events(torch, stream, fa, reps)
+            rows.append(row)
+            tot_s += ms_s
+            tot_g += ms_g
+    wait_timeouts = cj.stats()["wait_timeouts"] - wt0
+    del xin, o
+    # Compute bound of the default kernel: FP32 runs 3xTF32 on the tensor
+    # cores (tile modes 4 and 5: three TF32 products per multiply-add, TF32 peak
+    # = measured bf16 x the nominal 1.1 / 2.25 ratio); FP64 runs on the
+    # FP64 pipe at its nominal rate.
+    tc = dt == cj.F32 and all(((r["tile"][3] >> 16) & 0xF) in (4, 5) for r in rows)
+    if tc:
+        peak = measured_peak("bf16_tflops", 1800.0) * 1.1 / 2.25
+        t_alu = 3 * f / (peak * 1e12) * 1e3
+    else:
+        peak = PEAK_TFLOPS[dtype]
+        t_alu = f / (peak * 1e12) * 1e3
+    t_hbm = byt / (hbm_peak_gbs() * 1e9) * 1e3
+    mean_ms = tot_s / 36
+    bound = "tensor" if tc and t_alu >= t_hbm else "alu" if t_alu >= t_hbm else "hbm"
+    rf = {"bound": bound, "roofline_ms": max(t_alu, t_hbm), "mean_ms": mean_ms,
+          "frac": max(t_alu, t_hbm) / mean_ms, "compute_frac": t_alu / mean_ms, "hbm_frac": t_hbm / mean_ms,
+          "compute_peak_tflops": peak, "compute_unit": "TF32 tensor (3 passes)" if tc else dtype + " pipe",
+          "hbm_gbs": hbm_peak_gbs()}
+    if bound == "hbm":
+        rf.update({"achieved": byt / mean_ms / 1e6, "peak": hbm_peak_gbs(), "unit": "GB/s",
+                   "algorithmic_bytes": byt})
+    else:
+        rf.update({"achieved": f / mean_ms / 1e9, "peak": peak, "unit": "TFLOP/s"})
+    return {"value": 36 * f / tot_s / 1e6, "dtype": dtype, "mean_ms": mean_ms,
+            "generic": {"value": 36 * f / tot_g / 1e6, "unit": "GFLOP/s", "mean_ms": tot_g / 36},
+            "speedup_vs_generic": tot_g / tot_s,
+            "min_speedup_vs_generic": min(r["speedup_vs_generic"] for r in rows),
+            "max_rel_frobenius_error_vs_oracle": worst,
+            "error_sample": f"{samples} seeded (g, z) columns x all 36 moments, every order pair, both kernels",
+            "wait_timeouts": wait_timeouts, "valid": wait_timeouts == 0,
+            "roofline": rf, "per_pair": rows,
+            "config": {"workload": f"LTimes out[m][g][z] = sum_d L[m][d] in[d][g][z], M=36 D=96 G=32 Z={Z}, "
+                                   f"all 36 (in, out) storage orders, {dtype} (seed 0xC1A3)"}}
+
+
+def uneven_reference(dtypes):
+    """Oracle X of the 10,000-instance uneven batch: from the FP64 pool, and
+    from the pool rounded to FP32 (what the FP32 and BF16 plans read)."""
+    import oracle
+    n, t = synth.uneven_sizes(synth.SEED_UNEVEN, 10000)
+    pool, off = synth.uneven_inputs_np(synth.SEED_UNEVEN, n)
+    cores = os.cpu_count() or 1
+    ref = {"n": n, "t": t, "pool": pool, "off": off}
+    if "f64" in dtypes:
+        ref["f64"] = oracle.update_chain_uneven(n, t, off, pool, nthreads=cores)
+    if "f32" in dtypes or "bf16" in dtypes:
+        ref["f32"] = oracle.update_chain_uneven(n, t, off, pool.astype(np.float32).astype(np.float64),
+                                                nthreads=cores)
+    return ref
+
+
+def _uneven_errors(got, ref, n, off):
+    errs = np.empty(len(n))
+    for nn in np.unique(n):
+        idx = np.nonzero(n == nn)[0]
+        rows = off[idx][:, None] + np.arange(nn * nn)[None, :]
+        errs[idx] = np.linalg.norm(got[rows] - ref[rows], axis=1) / np.linalg.norm(ref[rows], axis=1)
+    return errs
+
+
+def run_config4(torch, cj, stream, dtype, K, W, ref):
+    """The 10,000-instance uneven batch through grouped plans: default tiles,
+    tiles autotuned per group, and the generic kernels, each in both launch
+    forms (one CUDA graph; one kernel per group on the plan's streams), the
+    faster form reported; every instance of the reported plan's output
+    checked against the oracle."""
+    dt = {"f64": cj.F64, "f32": cj.F32, "bf16": cj.BF16}[dtype]
+    tdt = torch.float64 if dt == cj.F64 else torch.float32
+    n, t, pool, off = ref["n"], ref["t"], ref["pool"], ref["off"]
+    A = torch.from_numpy(pool).to("cuda", tdt)
+    X = torch.empty_like(A)
+    f = float(np.sum(t * (2.0 * n ** 3 + 2.0 * n ** 2)))
+    res, modes, changed, errs = {}, {}, 0, None
+    for name, fl in (("default_tiles", 0), ("spec", 0), ("generic", cj.FLAG_GENERIC)):
+        plan = cj.GroupPlan(dt, n, t, flags=fl)
+        plan.wait()
+        if name == "spec":
+            # the plan's tiles chosen by its own autotuner (every candidate of the
+            # 16 most expensive groups timed on the group's own work list)
+            changed = plan.autotune(A, X, stream=stream, max_groups=16, reps=3)
+        for use_graph in (True, False):
+            fn = lambda: plan.launch(A, X, stream=stream, use_graph=use_graph)
+            _events(torch, stream, fn, W)
+            modes[(name, use_graph)] = _events(torch, stream, fn, max(K, 10))
+            if name == "spec":
+                stream.synchronize()
+                e = _uneven_errors(X.double().cpu().numpy(), ref["f64" if dt == cj.F64 else "f32"], n, off)
+                errs = e if errs is None else np.maximum(errs, e)
+        res[name] = min(modes[(name, True)], modes[(name, False)])
+        plan.destroy()
+    del A, X
+    peak = measured_peak("bf16_tflops", 1800.0) if dtype == "bf16" else PEAK_TFLOPS[dtype]
+    if dtype == "bf16":
+        err = {"max_rel_frobenius_error_vs_oracle_n_ge_16": float(errs[n >= 16].max()),
+               "max_rel_frobenius_error_vs_oracle_n_lt_16_fp32": float(errs[n < 16].max())}
+    else:
+        err = {"max_rel_frobenius_error_vs_oracle": float(errs.max())}
+    return {"value": f / res["spec"] / 1e6, "dtype": dtype, **err,
+            "error_sample": "every instance of the autotuned plan's output, both launch forms",
+            "generic": {"value": f / res["generic"] / 1e6, "unit": "GFLOP/s", "ms": res["generic"]},
+            "default_tiles": {"value": f / res["default_tiles"] / 1e6, "unit": "GFLOP/s",
+                              "ms": res["default_tiles"]},
+            "autotuned_groups_changed": changed,
+            "launch_ms": {f"{k}_{'graph' if g else 'streams'}": v for (k, g), v in modes.items()},
+            "hw_queues": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS", "8"),
+            "ms_per_launch": res["spec"], "speedup_vs_generic": res["generic"] / res["spec"],
+            "roofline": {"bound": "alu" if dtype != "bf16" else "tensor", "peak": peak, "unit": "TFLOP/s",
+                         "frac": f / res["spec"] / 1e9 / peak},
+            "config": {"workload": "uneven batch: 10,000 update chains, N log-uniform in [2,64], "
+                                   "T uniform in [16,128] (seed 0xC1A4), one grouped plan (graph or streams, "
+                                   f"faster), autotuned tiles, {dtype}",
+                       "flops": f, "groups": int(len(np.unique(n)))}}
+
+
 def secondary(args):
     import torch
     from paper_1904_08555_b300 import cj
@@ -474,175 +746,51 @@ def secondary(args):
     out = {"metric": METRIC, "unit": "GFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
     K, W = args.steps, args.warmup
-    if args.workload in ("small", "sweep32"):
-        dt = cj.F64 if args.workload == "small" else cj.F32
-        tdt = torch.float64 if dt == cj.F64 else torch.float32
-        sizes = (8,) if args.workload == "small" else SWEEP_N
+    if args.workload == "small":
+        out.update(run_config1(torch, cj, stream, W))
+    elif args.workload == "sweep32":
+        dt, tdt = cj.F32, torch.float32
         rows, tot_f, tot_spec, tot_gen = [], 0.0, 0.0, 0.0
-        for n in sizes:
-            b = 64 if args.workload == "small" else synth.chain_batch(n)
-            steps = 100 if args.workload == "small" else T_STEPS
-            A = synth.uniform_torch(synth.SEED_CHAIN_SMALL if b == 64 else synth.SEED_CHAIN_SWEEP, synth.STREAM_A,
-                                    b * n * n, "cuda").view(b, n, n).to(tdt)
+        for n in SWEEP_N:
+            b = synth.chain_batch(n)
+            A = synth.uniform_torch(synth.SEED_CHAIN_SWEEP, synth.STREAM_A, b * n * n, "cuda").view(b, n, n).to(tdt)
             X = torch.empty_like(A)
-            f = chain_flops(b, n, steps)
+            f = chain_flops(b, n, T_STEPS)
             row = {"N": n, "batch": b}
             variants = [("jit", cj.FLAG_NO_AOT, (0, 0, 0, 0)), ("generic", cj.FLAG_GENERIC, (0, 0, 0, 0))]
             if n in AOT_N:
                 variants.append(("aot", 0, (0, 0, 0, 0)))
-            if dt == cj.F32 and n % 4 == 0 and n >= 8:
+            if n % 4 == 0 and n >= 8:
                 variants.append(("regblock", 0, (5, max(1, 256 // ((n // 4) ** 2)), 0, 0)))
-            if dt == cj.F32 and n <= 32 and args.workload != "small":
+            if n <= 32:
                 variants.append(("tworow", 0, (6, max(1, 256 // ((n + 1) // 2)), 0, 0)))
                 variants.append(("tworow128", 0, (6, max(1, 128 // ((n + 1) // 2)), 0, 0)))
-            reps = 200 if b == 64 else K
             for name, fl, tile in variants:
                 h = cj.specialize(cj.K_UPDATE_CHAIN, dt, n=n, flags=fl, tile=tile)
-                fn = lambda h=h: cj.launch_update_chain(h, A, X, steps, stream=stream)
+                fn = lambda h=h: cj.launch_update_chain(h, A, X, T_STEPS, stream=stream)
                 _events(torch, stream, fn, W)
-                ms = _events(torch, stream, fn, reps)
+                ms = _events(torch, stream, fn, K)
                 row[name + "_us"] = ms * 1e3
                 row[name + "_gflops"] = f / ms / 1e6
                 row[name + "_regs"] = h.regs()[0]
             row["speedup_vs_generic"] = row["generic_us"] / row["jit_us"]
-            if args.workload == "small":
-                # the autotuner's choice for this exact batch (tile spaces include
-                # one instance per block, which a 64-instance batch needs)
-                best, times = cj.autotune(cj.K_UPDATE_CHAIN, dt, cj.chain_launch_vals(A, X, steps), b, stream,
-                                          reps=20, n=n)
-                h = cj.specialize(cj.K_UPDATE_CHAIN, dt, n=n, tile=best)
-                fn = lambda h=h: cj.launch_update_chain(h, A, X, steps, stream=stream)
-                _events(torch, stream, fn, W)
-                ms = _events(torch, stream, fn, reps)
-                row.update({"autotuned_tile": list(best), "autotuned_us": ms * 1e3, "autotuned_gflops": f / ms / 1e6,
-                            "autotuned_speedup_vs_generic": row["generic_us"] / (ms * 1e3),
-                            "candidates_us": {str(list(t)): v * 1e3 for t, v in times}})
             rows.append(row)
             tot_f += f
-            # config 1's JIT instantiation is the one the autotuner chose for this batch
-            # (the default tile, sized for large batches, is reported beside it)
-            tot_spec += row["autotuned_us"] if args.workload == "small" else row["jit_us"]
+            tot_spec += row["jit_us"]
             tot_gen += row["generic_us"]
             del A, X
-        peak = PEAK_TFLOPS["f64" if dt == cj.F64 else "f32"]
-        out.update({"value": tot_f / tot_spec / 1e3, "dtype": "f64" if dt == cj.F64 else "f32",
+        peak = PEAK_TFLOPS["f32"]
+        out.update({"value": tot_f / tot_spec / 1e3, "dtype": "f32",
                     "generic": {"value": tot_f / tot_gen / 1e3, "unit": "GFLOP/s"},
                     "speedup_vs_generic": tot_gen / tot_spec, "per_n": rows,
                     "roofline": {"bound": "alu", "peak": peak, "unit": "TFLOP/s",
                                  "frac": tot_f / tot_spec / 1e6 / peak},
-                    "config": {"workload": ("update chain, 64 FP64 8x8 matrices, T = 100 (latency-bound by size); "
-                                            "the autotuned JIT instantiation"
-                                            if args.workload == "small" else
-                                            "update chain FP32 size sweep, same sizes as the FP64 sweep")}})
+                    "config": {"workload": "update chain FP32 size sweep, same sizes as the FP64 sweep"}})
     elif args.workload == "ltimes":
-        dt = cj.F64 if args.dtype == "f64" else cj.F32
-        tdt = torch.float64 if dt == cj.F64 else torch.float32
-        es = 8 if dt == cj.F64 else 4
-        M, D, G, Z = 36, 96, 32, args.ltimes_z
-        L, _ = synth.ltimes_inputs_np(synth.SEED_LTIMES, M, D, 1, 1)
-        Lt = torch.from_numpy(L).to("cuda", tdt)
-        x = synth.uniform_torch(synth.SEED_LTIMES, synth.STREAM_A, D * G * Z, "cuda").view(D, G, Z).to(tdt)
-        xin = {lin: x.permute(*synth.LAYOUT_PERMS[lin]).contiguous().view(-1) for lin in range(6)}
-        del x
-        o = torch.empty(M * G * Z, device="cuda", dtype=tdt)
-        f = 2.0 * M * D * G * Z
-        byt = es * ((D + M) * G * Z + M * D)
-        rows, tot_s, tot_g = [], 0.0, 0.0
-        for lin in range(6):
-            for lout in range(6):
-                hs = cj.specialize(cj.K_LTIMES, dt, layout_a=lin, layout_b=lout, m=M, d=D)
-                hg = cj.specialize(cj.K_LTIMES, dt, layout_a=lin, layout_b=lout, m=M, d=D, flags=cj.FLAG_GENERIC)
-                fs = lambda: cj.launch_ltimes(hs, Lt, xin[lin], o, G, Z, stream=stream)
-                fg = lambda: cj.launch_ltimes(hg, Lt, xin[lin], o, G, Z, stream=stream)
-                _events(torch, stream, fs, 1)
-                ms_s = _events(torch, stream, fs, K)
-                _events(torch, stream, fg, 1)
-                ms_g = _events(torch, stream, fg, K)
-                row = {"in": synth.LAYOUT_NAMES[lin], "out": synth.LAYOUT_NAMES[lout].replace("D", "M"),
-                       "spec_ms": ms_s, "generic_ms": ms_g, "spec_gflops": f / ms_s / 1e6,
-                       "spec_gbs": byt / ms_s / 1e6, "generic_gflops": f / ms_g / 1e6,
-                       "speedup_vs_generic": ms_g / ms_s,
-                       "tile": list(int.from_bytes(bytes.fromhex(hs.key_hex)[12 + 4 * i:16 + 4 * i], "little")
-                                    for i in range(4))}
-                for name, alt in args.lt_alt_tiles(lin, lout):
-                    ha = cj.specialize(cj.K_LTIMES, dt, layout_a=lin, layout_b=lout, m=M, d=D, tile=alt)
-                    fa = lambda: cj.launch_ltimes(ha, Lt, xin[lin], o, G, Z, stream=stream)
-                    _events(torch, stream, fa, 1)
-                    row[name + "_ms"] = _events(torch, stream, fa, K)
-                rows.append(row)
-                tot_s += ms_s
-                tot_g += ms_g
-        # Compute bound of the default kernel: FP32 runs 3xTF32 on the tensor
-        # cores (tile modes 4 and 5: three TF32 products per multiply-add, TF32 peak
-        # = measured bf16 x the nominal 1.1 / 2.25 ratio); FP64 runs on the
-        # FP64 pipe at its nominal rate.
-        tc = args.dtype == "f32" and all(((r["tile"][3] >> 16) & 0xF) in (4, 5) for r in rows)
-        if tc:
-            peak = measured_peak("bf16_tflops", 1800.0) * 1.1 / 2.25
-            t_alu = 3 * f / (peak * 1e12) * 1e3
-        else:
-            peak = PEAK_TFLOPS[args.dtype]
-            t_alu = f / (peak * 1e12) * 1e3
-        t_hbm = byt / (hbm_peak_gbs() * 1e9) * 1e3
-        mean_ms = tot_s / 36
-        bound = "tensor" if tc and t_alu >= t_hbm else "alu" if t_alu >= t_hbm else "hbm"
-        rf = {"bound": bound, "roofline_ms": max(t_alu, t_hbm), "mean_ms": mean_ms,
-              "frac": max(t_alu, t_hbm) / mean_ms, "compute_frac": t_alu / mean_ms, "hbm_frac": t_hbm / mean_ms,
-              "compute_peak_tflops": peak, "compute_unit": "TF32 tensor (3 passes)" if tc else args.dtype + " pipe",
-              "hbm_gbs": hbm_peak_gbs()}
-        if bound == "hbm":
-            rf.update({"achieved": byt / mean_ms / 1e6, "peak": hbm_peak_gbs(), "unit": "GB/s",
-                       "algorithmic_bytes": byt})
-        else:
-            rf.update({"achieved": f / mean_ms / 1e9, "peak": peak, "unit": "TFLOP/s"})
-        out.update({"value": 36 * f / tot_s / 1e6, "dtype": args.dtype,
-                    "generic": {"value": 36 * f / tot_g / 1e6, "unit": "GFLOP/s"},
-                    "speedup_vs_generic": tot_g / tot_s,
-                    "min_speedup_vs_generic": min(r["speedup_vs_generic"] for r in rows),
-                    "roofline": rf,
-                    "per_pair": rows,
-                    "config": {"workload": f"LTimes out[m][g][z] = sum_d L[m][d] in[d][g][z], M=36 D=96 G=32 Z={Z}, "
-                                           f"all 36 (in, out) storage orders, {args.dtype}"}})
+        out.update(run_config3(torch, cj, stream, args.dtype, args.ltimes_z, K, alt_tiles=args.lt_alt_tiles))
     elif args.workload == "uneven":
-        dt = {"f64": cj.F64, "f32": cj.F32, "bf16": cj.BF16}[args.dtype]
-        tdt = torch.float64 if dt == cj.F64 else torch.float32
-        n, t = synth.uneven_sizes(synth.SEED_UNEVEN, 10000)
-        pool, off = synth.uneven_inputs_np(synth.SEED_UNEVEN, n)
-        A = torch.from_numpy(pool).to("cuda", tdt)
-        X = torch.empty_like(A)
-        f = float(np.sum(t * (2.0 * n ** 3 + 2.0 * n ** 2)))
-        res = {}
-        modes = {}
-        changed = 0
-        for name, fl in (("default_tiles", 0), ("spec", 0), ("generic", cj.FLAG_GENERIC)):
-            plan = cj.GroupPlan(dt, n, t, flags=fl)
-            if name == "spec":
-                # the plan's tiles chosen by its own autotuner (every candidate of the
-                # 16 most expensive groups timed on the group's own work list)
-                changed = plan.autotune(A, X, stream=stream, max_groups=16, reps=3)
-            # both launch forms of the plan: one CUDA graph, or one kernel per
-            # group on the plan's own streams; the faster one is reported
-            for use_graph in (True, False):
-                fn = lambda: plan.launch(A, X, stream=stream, use_graph=use_graph)
-                _events(torch, stream, fn, W)
-                modes[(name, use_graph)] = _events(torch, stream, fn, max(K, 10))
-            res[name] = min(modes[(name, True)], modes[(name, False)])
-            plan.destroy()
-        peak = measured_peak("bf16_tflops", 1800.0) if args.dtype == "bf16" else PEAK_TFLOPS[args.dtype]
-        out.update({"value": f / res["spec"] / 1e6, "dtype": args.dtype,
-                    "generic": {"value": f / res["generic"] / 1e6, "unit": "GFLOP/s", "ms": res["generic"]},
-                    "default_tiles": {"value": f / res["default_tiles"] / 1e6, "unit": "GFLOP/s",
-                                      "ms": res["default_tiles"]},
-                    "autotuned_groups_changed": changed,
-                    "launch_ms": {f"{k}_{'graph' if g else 'streams'}": v for (k, g), v in modes.items()},
-                    "hw_queues": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS", "8"),
-                    "ms_per_launch": res["spec"], "speedup_vs_generic": res["generic"] / res["spec"],
-                    "roofline": {"bound": "alu", "peak": peak, "unit": "TFLOP/s",
-                                 "frac": f / res["spec"] / 1e9 / peak},
-                    "config": {"workload": "uneven batch: 10,000 update chains, N log-uniform in [2,64], "
-                                           f"T uniform in [16,128], one grouped plan (graph or streams, faster), autotuned tiles, "
-                                           f"{args.dtype}",
-                               "flops": f, "groups": int(len(np.unique(n)))}})
+        ref = uneven_reference((args.dtype,))
+        out.update(run_config4(torch, cj, stream, args.dtype, K, W, ref))
     elif args.workload == "kernel":
         # one kernel on a small case (inputs above L2), for profiler captures
         dt = {"f64": cj.F64, "f32": cj.F32, "bf16": cj.BF16}[args.dtype]
