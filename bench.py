@@ -576,7 +576,7 @@ def run_config3(torch, cj, stream, dtype, Z, reps, alt_tiles=None, samples=384):
     gs = torch.from_numpy(rng.integers(0, G, samples)).cuda()
     zs = torch.from_numpy(rng.integers(0, Z, samples)).cuda()
     cols = x[:, gs, zs].double().cpu().numpy()
-    ref = oracle.ltimes(L, cols.ravel(), 1, samples, 0, 0)          # [m][sample]
+    ref = oracle.ltimes(L, cols.ravel(), 1, samples, 0, 0).reshape(M, samples)   # [m][sample]
     xin = {lin: x.permute(*synth.LAYOUT_PERMS[lin]).contiguous().view(-1) for lin in range(6)}
     del x
     o = torch.empty(M * G * Z, device="cuda", dtype=tdt)
@@ -875,9 +875,11 @@ def secondary(args):
         out.update({"metric": "cost-model regret t(chosen)/t(best exhaustive) - 1, geometric mean over held-out requests",
                     "value": rg["model"]["geomean"], "unit": "fraction", "higher_is_better": False,
                     "dtype": "f32 (network); f64/f32 kernels", "result": res,
-                    "config": {"workload": f"{res['heldout_requests']} held-out specialization requests (seed 0xC1A5): "
-                                           "chain/LTimes 50/50, N uniform in [2,64], orders uniform, f64/f32; chain "
-                                           "batch 2^22/N^2, T 64; LTimes M 36 D 96 G 32 Z 2^16"}})
+                    "config": {"workload": f"{res['heldout_requests']} unseen specialization requests (seed 0xC1A5): "
+                                           "chain/LTimes 50/50; chain N uniform over the sizes in [2,64] not trained "
+                                           "on, f64/f32 (+bf16 at N >= 16); LTimes over the 18 order pairs not "
+                                           "trained on, f64/f32; chain batch 2^22/N^2, T 64; LTimes M 36 D 96 G 32 "
+                                           "Z 2^16"}})
     out["clocks"] = sampler.stop()
     st = cj.stats()
     out["jit_compile_ms_p50"] = st["compile_ms_p50"]
