@@ -73,6 +73,8 @@ def _load():
         lib.oracle_eigen_bench.restype = None
         lib.oracle_eigen_recurrence.argtypes = [ctypes.c_longlong, i32, i32, ctypes.c_double, P, P]
         lib.oracle_eigen_recurrence.restype = None
+        lib.oracle_mass.argtypes = [i32, i32, i32, i64, P, P, P, P, i32]
+        lib.oracle_mass.restype = i32
         _lib = lib
     return _lib
 
@@ -248,3 +250,19 @@ def eigen_start(n: int) -> np.ndarray:
     """The listing's start M_0(i, j) = i + n j."""
     i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
     return (i + n * j).astype(np.float64)
+
+
+def mass(B1: np.ndarray, op: np.ndarray, x: np.ndarray, dim: int, nthreads: int = 1) -> np.ndarray:
+    """Mass operator of tensor-product elements: y_e = B^T diag(op_e) B x_e,
+    B the dim-fold Kronecker product of B1 (Q x D).  x: [ne][D^dim], op:
+    [ne][Q^dim] (first index fastest within an element); returns y like x."""
+    B1 = _f64(B1)
+    Q, D = B1.shape
+    x = _f64(x).reshape(-1, D ** dim)
+    op = _f64(op).reshape(-1, Q ** dim)
+    assert x.shape[0] == op.shape[0]
+    y = np.empty_like(x)
+    rc = _load().oracle_mass(dim, D, Q, x.shape[0], _p(B1), _p(op), _p(x), _p(y), nthreads)
+    if rc != 0:
+        raise ValueError("oracle_mass: invalid arguments")
+    return y

@@ -30,6 +30,10 @@
  *                            M(i, j) = i + n j (Sec. 5, Listing eigen1).
  *   oracle_eigen_recurrence -- the same recurrence over a batch of starting
  *                            matrices, for any constant c.
+ *   oracle_mass           -- the mass operator of tensor-product finite
+ *                            elements (the Laghos kernel of Sec. 5), from its
+ *                            finite-element definition y = B^T diag(op) B x
+ *                            with B a Kronecker product formed explicitly.
  */
 #include <math.h>
 #include <pthread.h>
@@ -401,4 +405,90 @@ void oracle_eigen_bench(int n, int repeat, double *out)
     memcpy(out, m, sizeof(double) * n * n);
     free(m);
     free(q);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Mass operator of tensor-product finite elements (the Laghos kernel of    */
+/* Sec. 5, whose specializations are keyed on the dimension, the dofs per   */
+/* dimension and the quadrature points per dimension).  The paper does not  */
+/* state the operator; this is its standard finite-element definition      */
+/* ("partial assembly" of the mass matrix):                                 */
+/*                                                                           */
+/*   y_e = B^T diag(op_e) B x_e    for every element e,                     */
+/*                                                                           */
+/* with B the Kronecker product of DIM copies of the 1-D basis matrix       */
+/* B1[q][d] = phi_d(xi_q) (Q x D, row-major): B[k][j] = prod_i B1[k_i][j_i] */
+/* for quadrature multi-index k and dof multi-index j.  x_e, y_e hold D^DIM */
+/* values, op_e Q^DIM values (quadrature weight x |J| x density), each with */
+/* the first index fastest: j = (j_3 D + j_2) D + j_1.                      */
+/* Here B is formed explicitly, entry by entry, and applied as two dense    */
+/* matrix-vector products (no sum factorization).                           */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int dim, D, Q;
+    int64_t e0, e1;
+    const double *B1, *op, *x;
+    double *y;
+} mass_job;
+
+static void *mass_worker(void *arg)
+{
+    mass_job *j = (mass_job *)arg;
+    const int D = j->D, Q = j->Q, dim = j->dim;
+    int nd = 1, nq = 1;
+    for (int i = 0; i < dim; ++i) {
+        nd *= D;
+        nq *= Q;
+    }
+    double *B = (double *)malloc(sizeof(double) * (size_t)nq * nd);
+    double *u = (double *)malloc(sizeof(double) * (size_t)nq);
+    for (int k = 0; k < nq; ++k)
+        for (int jj = 0; jj < nd; ++jj) {
+            double v = 1.0;
+            int kr = k, jr = jj;
+            for (int i = 0; i < dim; ++i) {
+                v = v * j->B1[(kr % Q) * D + (jr % D)];
+                kr /= Q;
+                jr /= D;
+            }
+            B[(size_t)k * nd + jj] = v;
+        }
+    for (int64_t e = j->e0; e < j->e1; ++e) {
+        const double *x = j->x + e * nd, *op = j->op + e * nq;
+        double *y = j->y + e * nd;
+        for (int k = 0; k < nq; ++k) {
+            double s = 0.0;
+            for (int jj = 0; jj < nd; ++jj) s = s + B[(size_t)k * nd + jj] * x[jj];
+            u[k] = op[k] * s;
+        }
+        for (int jj = 0; jj < nd; ++jj) {
+            double s = 0.0;
+            for (int k = 0; k < nq; ++k) s = s + B[(size_t)k * nd + jj] * u[k];
+            y[jj] = s;
+        }
+    }
+    free(B);
+    free(u);
+    return NULL;
+}
+
+/* Returns 0 on success, -1 on invalid arguments (dim not 1..3, D or Q < 1). */
+int oracle_mass(int dim, int D, int Q, int64_t ne, const double *B1, const double *op, const double *x, double *y,
+                int nthreads)
+{
+    if (dim < 1 || dim > 3 || D < 1 || Q < 1 || ne < 0) return -1;
+    if (nthreads < 1) nthreads = 1;
+    if ((int64_t)nthreads > ne) nthreads = ne > 0 ? (int)ne : 1;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * nthreads);
+    mass_job *jobs = (mass_job *)malloc(sizeof(mass_job) * nthreads);
+    for (int t = 0; t < nthreads; ++t) {
+        mass_job jb = {dim, D, Q, ne * t / nthreads, ne * (t + 1) / nthreads, B1, op, x, y};
+        jobs[t] = jb;
+        pthread_create(&th[t], NULL, mass_worker, &jobs[t]);
+    }
+    for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+    free(th);
+    free(jobs);
+    return 0;
 }
