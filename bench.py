@@ -435,7 +435,8 @@ def main():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=("cj", "reference"), default="cj")
-    p.add_argument("--workload", choices=("sweep", "small", "sweep32", "ltimes", "uneven", "kernel", "costmodel", "eigen"),
+    p.add_argument("--workload", choices=("sweep", "small", "sweep32", "ltimes", "uneven", "kernel", "costmodel", "eigen",
+                                          "pch", "mass"),
                    default="sweep",
                    help="sweep (default): the FP64 size sweep; the others are secondary measurements")
     p.add_argument("--dtype", choices=("f64", "f32", "bf16"), default="f64", help="ltimes / uneven precision")
@@ -653,6 +654,99 @@ def run_config3(torch, cj, stream, dtype, Z, reps, alt_tiles=None, samples=384):
                                    f"all 36 (in, out) storage orders, {dtype} (seed 0xC1A3)"}}
 
 
+# The paper's Laghos figure (Sec. 5): 2-D, 10,000 elements, runs labelled dNqM
+# with N dofs and M quadrature points per dimension.
+MASS_PAPER_CASES = ((2, 4), (2, 2), (4, 8), (2, 8), (4, 2), (4, 4), (8, 4), (8, 2))
+# Throughput cases: the 2-D instantiations of the paper's Laghos listing, and
+# 3-D ones, each about 2 GB of x, op and y.
+MASS_CASES = ((2, 2, 2), (2, 2, 4), (2, 3, 4), (2, 3, 6), (2, 4, 6), (2, 4, 8), (2, 5, 8),
+              (3, 2, 4), (3, 3, 4), (3, 3, 6), (3, 4, 6), (3, 4, 8), (3, 5, 8))
+
+
+def mass_flops(dim, D, Q):
+    """Sum-factorized flops per element: one 1-D contraction per dimension to
+    the quadrature points and back (2 flops per multiply-add), plus the
+    pointwise scaling."""
+    if dim == 2:
+        return 2.0 * 2 * (Q * D * D + Q * Q * D) + Q * Q
+    return 2.0 * 2 * (Q * D ** 3 + Q * Q * D * D + Q ** 3 * D) + Q ** 3
+
+
+def _mass_case(torch, cj, stream, oracle, dt, tdt, es, dim, D, Q, ne, K, W, samples=256):
+    B1, op, x = synth.mass_inputs_torch(synth.SEED_MASS, dim, D, Q, ne, "cuda")
+    op, x = op.to(tdt), x.to(tdt)
+    Bt = torch.from_numpy(B1).to("cuda", tdt)
+    y = torch.empty_like(x)
+    f = mass_flops(dim, D, Q) * ne
+    row = {"dim": dim, "D": D, "Q": Q, "elements": ne, "laghos_key": hex((dim << 16) | ((D - 1) << 8) | (Q >> 1))}
+    worst = 0.0
+    for name, fl in (("spec", 0), ("generic", cj.FLAG_GENERIC)):
+        h = cj.specialize(cj.K_MASS, dt, n=D, m=Q, d=dim, flags=fl)
+        h.wait()
+        fn = lambda h=h: cj.launch_mass(h, Bt, op, x, y, ne, stream=stream)
+        _events(torch, stream, fn, W)
+        ms = _events(torch, stream, fn, K)
+        stream.synchronize()
+        rng = np.random.default_rng(dim * 100 + D * 10 + Q)
+        it = torch.from_numpy(np.unique(rng.integers(0, ne, samples))).cuda()
+        ref = oracle.mass(Bt.double().cpu().numpy(), op[it].double().cpu().numpy(), x[it].double().cpu().numpy(), dim)
+        got = y[it].double().cpu().numpy()
+        err = float(np.max(np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)))
+        worst = max(worst, err)
+        row.update({name + "_us": ms * 1e3, name + "_gflops": f / ms / 1e6, name + "_regs": h.regs()[0],
+                    name + "_rel_err": err})
+        if name == "spec":
+            row["tile"] = _key_tile(h)
+    row["speedup_vs_generic"] = row["generic_us"] / row["spec_us"]
+    return row, f, worst
+
+
+def run_mass_workload(torch, cj, stream, dtype, K, W):
+    """Mass operator of tensor-product elements (the Laghos kernel, Sec. 5):
+    (1) the paper's figure cases, 2-D, 10,000 elements, specialized against
+    generic (the paper reports this ratio); (2) throughput cases of about
+    2 GB each, with the roofline max(FP pipe, HBM) time per case.  Every
+    timed output is checked against the oracle on 256 sampled elements."""
+    import oracle
+    dt = cj.F64 if dtype == "f64" else cj.F32
+    tdt = torch.float64 if dt == cj.F64 else torch.float32
+    es = 8 if dt == cj.F64 else 4
+    peak = PEAK_TFLOPS[dtype]
+    worst = 0.0
+    paper = []
+    for D, Q in MASS_PAPER_CASES:
+        row, _, w = _mass_case(torch, cj, stream, oracle, dt, tdt, es, 2, D, Q, 10000, max(K, 20), W)
+        row["run"] = f"d{D}q{Q}"
+        paper.append(row)
+        worst = max(worst, w)
+    rows, tot_f, tot_s, tot_g, tot_roof = [], 0.0, 0.0, 0.0, 0.0
+    for dim, D, Q in MASS_CASES:
+        ne = (1 << 31) // ((2 * D ** dim + Q ** dim) * es)
+        row, f, w = _mass_case(torch, cj, stream, oracle, dt, tdt, es, dim, D, Q, ne, K, W)
+        worst = max(worst, w)
+        byt = float(es) * (2 * D ** dim + Q ** dim) * ne
+        t_alu, t_hbm = f / (peak * 1e12) * 1e3, byt / (hbm_peak_gbs() * 1e9) * 1e3
+        row.update({"roofline_ms": max(t_alu, t_hbm), "frac": max(t_alu, t_hbm) / (row["spec_us"] * 1e-3),
+                    "bound": "alu" if t_alu >= t_hbm else "hbm", "spec_gbs": byt / (row["spec_us"] * 1e-3) / 1e6})
+        rows.append(row)
+        tot_f += f
+        tot_s += row["spec_us"] * 1e-3
+        tot_g += row["generic_us"] * 1e-3
+        tot_roof += max(t_alu, t_hbm)
+    return {"value": tot_f / tot_s / 1e6, "dtype": dtype,
+            "generic": {"value": tot_f / tot_g / 1e6, "unit": "GFLOP/s"},
+            "speedup_vs_generic": tot_g / tot_s, "min_speedup_vs_generic": min(r["speedup_vs_generic"] for r in rows),
+            "paper_figure_cases": paper,
+            "max_rel_frobenius_error_vs_oracle": worst, "per_case": rows,
+            "roofline": {"bound": "max(pipe, hbm) per case", "frac": tot_roof / tot_s, "peak_tflops": peak,
+                         "hbm_gbs": hbm_peak_gbs()},
+            "config": {"workload": "mass operator y = B^T diag(op) B x of tensor-product elements: the paper's figure "
+                                   f"runs {['d%dq%d' % c for c in MASS_PAPER_CASES]} (2-D, 10,000 elements) and "
+                                   f"throughput cases (dim, D, Q) in {list(MASS_CASES)} of about 2 GB, {dtype} "
+                                   "(seed 0xC1A6)",
+                       "flops_per_element": "sum factorized: 2D 4(QD^2+Q^2D)+Q^2, 3D 4(QD^3+Q^2D^2+Q^3D)+Q^3"}}
+
+
 def uneven_reference(dtypes):
     """Oracle X of the 10,000-instance uneven batch: from the FP64 pool, and
     from the pool rounded to FP32 (what the FP32 and BF16 plans read)."""
@@ -680,59 +774,135 @@ def _uneven_errors(got, ref, n, off):
 
 def run_config4(torch, cj, stream, dtype, K, W, ref):
     """The 10,000-instance uneven batch through grouped plans: default tiles,
-    tiles autotuned per group, and the generic kernels, each in both launch
-    forms (one CUDA graph; one kernel per group on the plan's streams), the
-    faster form reported; every instance of the reported plan's output
-    checked against the oracle."""
+    tiles and launch form chosen by the plan's autotuner, and the generic
+    kernels.  Every form is timed -- the plan's one-launch dispatcher and one
+    kernel per group, each as a CUDA graph and issued directly -- and every
+    instance of each autotuned-plan form's output is checked against the
+    oracle.  `value` is the autotuned plan as a user launches it (the form its
+    autotuner kept; graph or direct, the faster)."""
     dt = {"f64": cj.F64, "f32": cj.F32, "bf16": cj.BF16}[dtype]
     tdt = torch.float64 if dt == cj.F64 else torch.float32
     n, t, pool, off = ref["n"], ref["t"], ref["pool"], ref["off"]
     A = torch.from_numpy(pool).to("cuda", tdt)
     X = torch.empty_like(A)
     f = float(np.sum(t * (2.0 * n ** 3 + 2.0 * n ** 2)))
-    res, modes, changed, errs = {}, {}, 0, None
+    reps = max(K, 10)
+    modes, changed, errs, disp = {}, 0, None, {}
+    forms = {"dispatch_graph": (True, False), "dispatch_direct": (False, False),
+             "per_group_graph": (True, True), "per_group_streams": (False, True)}
     for name, fl in (("default_tiles", 0), ("spec", 0), ("generic", cj.FLAG_GENERIC)):
         plan = cj.GroupPlan(dt, n, t, flags=fl)
-        plan.wait()
+        plan.wait()                     # every group's instantiation and the dispatcher compiled
         if name == "spec":
             # the plan's tiles chosen by its own autotuner (every candidate of the
-            # 16 most expensive groups timed on the group's own work list)
+            # 16 most expensive groups timed on the group's own work list), then
+            # the faster launch form
             changed = plan.autotune(A, X, stream=stream, max_groups=16, reps=3)
-        for use_graph in (True, False):
-            fn = lambda: plan.launch(A, X, stream=stream, use_graph=use_graph)
+            disp = plan.dispatcher()
+        for form, (use_graph, per_group) in forms.items():
+            if fl == cj.FLAG_GENERIC and not per_group:
+                continue                # a generic plan has no dispatcher
+            fn = lambda: plan.launch(A, X, stream=stream, use_graph=use_graph, per_group=per_group)
             _events(torch, stream, fn, W)
-            modes[(name, use_graph)] = _events(torch, stream, fn, max(K, 10))
+            modes[(name, form)] = _events(torch, stream, fn, reps)
             if name == "spec":
                 stream.synchronize()
                 e = _uneven_errors(X.double().cpu().numpy(), ref["f64" if dt == cj.F64 else "f32"], n, off)
                 errs = e if errs is None else np.maximum(errs, e)
-        res[name] = min(modes[(name, True)], modes[(name, False)])
         plan.destroy()
     del A, X
+    kept = "dispatch" if disp.get("state") == "ready" else "per_group"
+    spec_ms = min(modes[("spec", kept + "_graph")], modes[("spec", kept + ("_direct" if kept == "dispatch" else "_streams"))])
+    def best(name):
+        return min(v for (k, _), v in modes.items() if k == name)
     peak = measured_peak("bf16_tflops", 1800.0) if dtype == "bf16" else PEAK_TFLOPS[dtype]
     if dtype == "bf16":
         err = {"max_rel_frobenius_error_vs_oracle_n_ge_16": float(errs[n >= 16].max()),
                "max_rel_frobenius_error_vs_oracle_n_lt_16_fp32": float(errs[n < 16].max())}
     else:
         err = {"max_rel_frobenius_error_vs_oracle": float(errs.max())}
-    return {"value": f / res["spec"] / 1e6, "dtype": dtype, **err,
-            "error_sample": "every instance of the autotuned plan's output, both launch forms",
-            "generic": {"value": f / res["generic"] / 1e6, "unit": "GFLOP/s", "ms": res["generic"]},
-            "default_tiles": {"value": f / res["default_tiles"] / 1e6, "unit": "GFLOP/s",
-                              "ms": res["default_tiles"]},
+    return {"value": f / spec_ms / 1e6, "dtype": dtype, **err,
+            "error_sample": "every instance, every launch form of the autotuned plan",
+            "launch_form_kept": kept, "dispatcher": disp,
+            "dispatch_gflops": f / min(modes[("spec", "dispatch_graph")], modes[("spec", "dispatch_direct")]) / 1e6,
+            "per_group_gflops": f / min(modes[("spec", "per_group_graph")], modes[("spec", "per_group_streams")]) / 1e6,
+            "generic": {"value": f / best("generic") / 1e6, "unit": "GFLOP/s", "ms": best("generic")},
+            "default_tiles": {"value": f / best("default_tiles") / 1e6, "unit": "GFLOP/s",
+                              "ms": best("default_tiles")},
             "autotuned_groups_changed": changed,
-            "launch_ms": {f"{k}_{'graph' if g else 'streams'}": v for (k, g), v in modes.items()},
+            "launch_ms": {f"{k}_{form}": v for (k, form), v in modes.items()},
             "hw_queues": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS", "8"),
-            "ms_per_launch": res["spec"], "speedup_vs_generic": res["generic"] / res["spec"],
+            "ms_per_launch": spec_ms, "speedup_vs_generic": best("generic") / spec_ms,
             "roofline": {"bound": "alu" if dtype != "bf16" else "tensor", "peak": peak, "unit": "TFLOP/s",
-                         "frac": f / res["spec"] / 1e9 / peak},
+                         "frac": f / spec_ms / 1e9 / peak},
             "config": {"workload": "uneven batch: 10,000 update chains, N log-uniform in [2,64], "
-                                   "T uniform in [16,128] (seed 0xC1A4), one grouped plan (graph or streams, "
-                                   f"faster), autotuned tiles, {dtype}",
+                                   "T uniform in [16,128] (seed 0xC1A4), one grouped plan, autotuned tiles and "
+                                   f"launch form, {dtype}",
                        "flops": f, "groups": int(len(np.unique(n)))}}
 
 
+def pch_workload(args):
+    """JIT compile latency with and without NVRTC's automatic precompiled
+    headers (-pch), over the FP64 sweep's nine instantiations (default
+    tiles), compiled from the library's embedded kernel sources with the
+    library's own options.  Needs no GPU.  Reports p50/p95 per setting and
+    whether files appeared under the temporary directory (the library's
+    requirement is that run-time compilation touches no file)."""
+    import glob
+    import tempfile
+    from cuda.bindings import nvrtc
+    from paper_1904_08555_b300 import build, cj
+    kdir = build.KDIR
+    hdr_names = ["geometry.h", "update_chain.cuh", "ltimes.cuh"]
+    hdrs = [open(os.path.join(kdir, h)).read().encode() for h in hdr_names]
+    exprs = []
+    for n in SWEEP_N:
+        tiles = cj.candidates(cj.K_UPDATE_CHAIN, dtype=cj.F64, n=n, layout_a=0)
+        d = next(t for t in tiles if cj.featurize(cj.K_UPDATE_CHAIN, cj.F64, batch=synth.chain_batch(n), steps=T_STEPS,
+                                                   tile=t, n=n, layout_a=0)[31] == 1.0)
+        exprs.append(f"cj::update_chain<double, {n}, 0, {d[0]}, {d[1]}>")
+    base = [b"-arch=sm_103a", b"-std=c++17", b"-lineinfo", b"--no-cache"]
+    tmp = tempfile.gettempdir()
+
+    def compile_all(opts):
+        ms = []
+        for e in exprs:
+            t0 = time.perf_counter()
+            _, prog = nvrtc.nvrtcCreateProgram(b'#include "update_chain.cuh"\n', b"cj_instantiation.cu", 3, hdrs,
+                                               [h.encode() for h in hdr_names])
+            nvrtc.nvrtcAddNameExpression(prog, e.encode())
+            (rc,) = nvrtc.nvrtcCompileProgram(prog, len(opts), opts)
+            if rc == nvrtc.nvrtcResult.NVRTC_SUCCESS:
+                _, size = nvrtc.nvrtcGetCUBINSize(prog)
+                buf = b" " * size
+                nvrtc.nvrtcGetCUBIN(prog, buf)
+            nvrtc.nvrtcDestroyProgram(prog)
+            ms.append((time.perf_counter() - t0) * 1e3)
+            assert rc == nvrtc.nvrtcResult.NVRTC_SUCCESS, e
+        return ms
+
+    compile_all(base)                       # warm NVRTC (first use)
+    before = set(glob.glob(os.path.join(tmp, "*nvrtc*")))
+    res = {}
+    for name, opts in (("no_pch", base), ("auto_pch", base + [b"-pch"])):
+        ms = []
+        for _ in range(args.steps):
+            ms += compile_all(opts)
+        res[name] = {"p50_ms": float(np.percentile(ms, 50)), "p95_ms": float(np.percentile(ms, 95)),
+                     "mean_ms": float(np.mean(ms)), "compiles": len(ms)}
+    after = set(glob.glob(os.path.join(tmp, "*nvrtc*")))
+    out = {"metric": "JIT compile ms (NVRTC to sm_103a CUBIN), with and without automatic PCH",
+           "value": res["no_pch"]["p50_ms"], "unit": "ms", "higher_is_better": False, "n_gpus": 0,
+           "steps": args.steps, "warmup": 1, "dtype": "f64", "data": "synthetic", "result": res,
+           "files_created_under_tmp_by_pch": sorted(after - before),
+           "config": {"workload": "the FP64 sweep's 9 instantiations (default tiles), compiled from the embedded "
+                                  "sources; no_pch is the library's configuration"}}
+    print(json.dumps(out), flush=True)
+
+
 def secondary(args):
+    if args.workload == "pch":
+        return pch_workload(args)
     import torch
     from paper_1904_08555_b300 import cj
     torch.cuda.set_device(0)
@@ -832,6 +1002,8 @@ def secondary(args):
         ms = _events(torch, stream, fn, K)
         out.update({"value": f / ms / 1e6, "dtype": args.dtype, "ms_per_launch": ms, "regs": h.regs()[0],
                     "config": {"workload": desc}})
+    elif args.workload == "mass":
+        out.update(run_mass_workload(torch, cj, stream, args.dtype if args.dtype != "bf16" else "f64", K, W))
     elif args.workload == "eigen":
         # the paper's literal Eigen recurrence (Listing eigen1), batched: random
         # starts in [-1, 1), c = 5e-5, 64 repeats, batch = 2^24 / N^2 per size

@@ -36,6 +36,12 @@
  *                         caller-given M_0 (the listing: c = 5e-5, M_0(i, j) =
  *                         i + N j).  It grows without bound; compare over few
  *                         repeats.
+ *   CJ_K_MASS          -- the mass operator of tensor-product finite elements
+ *                         (the Laghos kernel of Sec. 5, specialized on the
+ *                         dimension, dofs and quadrature points per
+ *                         dimension): per element e, y_e = B^T diag(op_e) B x_e
+ *                         with B the Kronecker product of the 1-D basis
+ *                         matrix B1, evaluated by sum factorization.
  *
  * Thread safety: every function may be called from any host thread.
  * cj_specialize serialises on one mutex; cj_launch takes no lock.
@@ -70,7 +76,8 @@ typedef enum {
     CJ_K_LTIMES = 2,
     CJ_K_UPDATE_CHAIN_GROUPED = 3,
     CJ_K_LPLUSTIMES = 4,
-    CJ_K_EIGEN_RECURRENCE = 5
+    CJ_K_EIGEN_RECURRENCE = 5,
+    CJ_K_MASS = 6
 } cj_kernel_id;
 
 typedef enum {
@@ -112,6 +119,10 @@ typedef struct {
  *                  in and m for out: 0 XGZ, 1 XZG, 2 GXZ, 3 GZX, 4 ZXG, 5 ZGX.
  *   UPDATE_CHAIN_GROUPED: dtype, n (1..64), tile (row-major only).
  *   EIGEN_RECURRENCE: dtype (f64/f32), n (1..32), tile (row-major only).
+ *   MASS:          dtype (f64/f32), d = dimension (2 or 3), n = dofs per
+ *                  dimension D (1..16), m = quadrature points per dimension Q
+ *                  (1..16): the paper's Laghos key (DIM << 16) | ((D - 1) << 8)
+ *                  | (Q >> 1) in fields of its own; tile.
  *   LPLUSTIMES:    as LTIMES (layout_a = order of the accumulated `in`,
  *                  layout_b = order of the input `out`, m, d); the tile is
  *                  an LTimes tile of the swapped problem (d output rows, m
@@ -132,6 +143,10 @@ typedef struct {
  *     else {1, max(1, 128 / n)}; bf16 -> {3, max(1, 128 / n16)} with n16 = n
  *     rounded up to a multiple of 16 (mapping 3: one warp per 16 rows,
  *     bf16 operands, fp32 accumulate and state).
+ *   mass operator: {elements per block, 0, 0, 0}; an element owns
+ *     max(D, Q)^2 threads and two shared-memory buffers of max(D, Q)^d values.
+ *     Default: max(1, 256 / max(D, Q)^2) elements, fewer if the buffers of a
+ *     block would exceed 96 KiB.
  *   Eigen recurrence: {mapping, instances per block, 0, 0}; M_k of every
  *     instance in shared memory, two buffers; mapping 1 = one thread per row
  *     of M, 2 = two rows per thread (rows h and h + ceil(n / 2); f32 only;
@@ -191,6 +206,9 @@ typedef struct {
      * the mode-4 kernel because `in` admitted no tensor map (innermost extent
      * not a multiple of 4 floats, or `in` not 16-byte aligned) */
     uint64_t launches_tma, launches_tma_fallback;
+    /* grouped plans: launches of a plan's dispatcher issued from the host
+     * (cj_group_plan_launch without CJ_PLAN_GRAPH, or a graph capture) */
+    uint64_t launches_dispatch;
     /* Expired bounded waits of the tensor-core LTimes kernels (tile modes 4
      * and 5), summed over every run-time-compiled module and not yet cleared
      * through cj_handle_wait_timeouts(reset != 0).  A block whose wait expired
@@ -235,6 +253,11 @@ cj_status cj_specialize_wait(cj_handle h, int timeout_ms);
  *     const int64_t* Z}; Lp is [d][m] row-major, out is m*G*Z elements in
  *     order layout_b (read), in is d*G*Z elements in order layout_a
  *     (accumulated into).
+ *   MASS: {const T** B1, const T** op, const T** x, T** y}; B1 is the 1-D
+ *     basis at the quadrature points, [Q][D] row-major; op is batch * Q^d
+ *     values (quadrature data per element), x and y batch * D^d (dofs per
+ *     element), each element's values with the first index fastest; batch =
+ *     elements.
  *   EIGEN_RECURRENCE: {const T** M0, T** M, const int32_t* repeat, const
  *     double* c}; M0 and M are batch*n*n elements (row-major instances); repeat
  *     >= 0 steps (0 copies M0 to M).
@@ -287,17 +310,27 @@ cj_status cj_handle_wait_timeouts(cj_handle h, uint32_t *count, int reset);
  * device memory it owns.  dtype: CJ_F64, CJ_F32 or CJ_BF16 (pools in fp32;
  * groups with n >= 16 on bf16 tensor cores, the others in fp32).  flags: 0, or
  * CJ_FLAG_GENERIC to run every group on the generic grouped kernel.
+ * Dispatcher: unless CJ_FLAG_GENERIC, the plan also generates one kernel for
+ * the whole batch -- a persistent loop whose blocks take tickets (one chunk
+ * of one group each, ordered by cost T n^3, longest first) from a counter
+ * and run the ticket's group body, every body instantiated for the same
+ * block size -- and requests its compilation (in the background in async
+ * mode).  Launches use it once it is compiled; until then, or if it fails
+ * to compile, or with CJ_PLAN_PER_GROUP, they launch one kernel per group.
  */
 typedef struct cj_group_plan_s *cj_group_plan;
 cj_status cj_group_plan_create(int32_t dtype, int64_t count, const int32_t *n, const int32_t *steps,
                                uint32_t flags, cj_group_plan *out);
-/* Launch every group on `cuda_stream`: groups run concurrently on forked
- * streams joined back into cuda_stream.  use_graph = 1: the first call
- * captures the whole launch (counter reset included) into a CUDA graph on a
- * stream of the plan's own and launches it on cuda_stream; later calls
- * replay it (re-captured when the pools or a group's instantiation changed,
- * e.g. from generic to JIT).  use_graph = 0: one kernel per group on the
- * plan's streams (up to 64), launched from the calling thread.  The GPU
+/* Launch the plan on `cuda_stream`.  use_graph is a set of CJ_PLAN_* flags.
+ * With the dispatcher ready (and no CJ_PLAN_PER_GROUP): one counter reset and
+ * one dispatcher launch on cuda_stream.  Otherwise every group's kernel:
+ * groups run concurrently on forked streams joined back into cuda_stream.
+ * CJ_PLAN_GRAPH: the first call captures the whole launch (counter reset
+ * included) into a CUDA graph on a stream of the plan's own and launches it
+ * on cuda_stream; later calls replay it (re-captured when the pools, the
+ * form or a group's instantiation changed, e.g. from generic to JIT, or the
+ * dispatcher became ready).  Without it: the launches are issued from the
+ * calling thread (per group: on the plan's streams, up to 64).  The GPU
  * overlaps independent streams only as far as the CUDA context has
  * hardware work queues: CUDA_DEVICE_MAX_CONNECTIONS (default 8, at most
  * 32), which must be set in the environment before the context is created.
@@ -307,8 +340,15 @@ cj_status cj_group_plan_create(int32_t dtype, int64_t count, const int32_t *n, c
  * ordered by cuda_stream, so two launches on streams the caller does not
  * order against each other race (use one plan per concurrent stream).  Pools
  * are caller-owned device memory. */
+#define CJ_PLAN_GRAPH 0x1      /* cj_group_plan_launch: capture once, replay a CUDA graph */
+#define CJ_PLAN_PER_GROUP 0x2  /* cj_group_plan_launch: one kernel per group even when the dispatcher is ready */
 cj_status cj_group_plan_launch(cj_group_plan p, const void *A_pool, void *X_pool, void *cuda_stream,
                                int use_graph);
+/* The plan's dispatcher: *state 0 none (a CJ_FLAG_GENERIC plan), 1 compiling,
+ * 2 ready (launches use it), 3 failed to compile, 4 ready but not used (the
+ * plan's autotuner timed one kernel per group faster); *n_tickets its work
+ * tickets; *threads its block size.  Any output may be NULL. */
+cj_status cj_group_plan_dispatcher(cj_group_plan p, int32_t *state, int32_t *n_tickets, int32_t *threads);
 /* Wait up to timeout_ms (negative: forever) for the instantiations of every
  * group of p to finish compiling.  CJ_OK: every group launches its
  * specialized kernel.  CJ_ERR_TIMEOUT: some are still compiling (launches
@@ -321,7 +361,10 @@ cj_status cj_group_plan_wait(cj_group_plan p, int timeout_ms);
  * the grouped kernel (cj_candidates, at most 256 instances per chunk) is
  * compiled and timed on the group's own work list on `stream` (median of reps
  * launches after one warm-up, CUDA events); the fastest replaces the group's
- * tile, and the next graph launch re-captures.  X_pool is written: every timed
+ * tile, and the next graph launch re-captures.  Then, once the plan's
+ * dispatcher is compiled (this waits for it), the whole launch is timed in
+ * both forms -- the dispatcher, and one kernel per group -- and later
+ * launches use the faster.  X_pool is written: every timed
  * launch computes its group's instances.  *changed (may be NULL) receives the
  * number of groups whose tile changed.  Synchronous; compiles run on the
  * background threads in async mode.  Not to be called while another thread
@@ -391,7 +434,9 @@ cj_status cj_update_chain_uneven_noalloc(int32_t dtype, int64_t count, const int
  *   compile).
  * cj_featurize: the CJ_FEATURES-float input vector of the cost model for
  *   (request, tile) at `batch` instances (chain) or columns G*Z (LTimes)
- *   and `steps` (chain T).
+ *   and `steps` (chain T); the last feature is 1 for the tile the default
+ *   rule picks for the request, else 0.  Not defined for CJ_K_MASS (whose
+ *   tiles are autotuned exhaustively): CJ_ERR_INVALID_ARG.
  * cj_mlp_*: an in_features -> 64 -> 64 -> 1 ReLU network in FP32 on the
  *   device (library-owned).  Parameters are one flat vector in the order
  *   W1[64][F], b1[64], W2[64][64], b2[64], w3[64], b3.  forward: y = f(X)
@@ -405,9 +450,16 @@ cj_status cj_update_chain_uneven_noalloc(int32_t dtype, int64_t count, const int
  *   cj_specialize requests with tile = {0,0,0,0} when cj_config.use_cost_model
  *   is set (NULL uninstalls); the decision is cached per request.  Only
  *   UPDATE_CHAIN and LTIMES requests consult it; the other kernels keep
- *   their default rule.
- * cj_choose_tile: the candidate with the lowest predicted log time, for any
- *   kernel with candidates (a model trained on other kernels extrapolates).
+ *   their default rule.  cj_cost_model_use_ensemble installs count networks
+ *   whose predictions are averaged (count 0 uninstalls); the library keeps
+ *   the pointers, not copies: destroying an installed network uninstalls the
+ *   ensemble.
+ * cj_choose_tile: the candidate with the lowest predicted log time (the
+ *   mean over the installed networks; each network's output is read as the
+ *   natural log of the time), for any kernel with candidates (a model
+ *   trained on other kernels extrapolates), except that the default rule's
+ *   tile is kept unless another candidate is predicted faster by more than
+ *   log(1.10).  The cost-model hook of cj_specialize decides the same way.
  */
 #define CJ_FEATURES 32
 typedef struct cj_mlp_s *cj_mlp;
@@ -427,6 +479,7 @@ cj_status cj_mlp_train_step(cj_mlp m, const float *X, const float *t, int64_t B,
                             void *cuda_stream);
 cj_status cj_mlp_destroy(cj_mlp m);
 cj_status cj_cost_model_use(cj_mlp m);
+cj_status cj_cost_model_use_ensemble(const cj_mlp *m, int32_t count);
 cj_status cj_choose_tile(cj_kernel_id k, const cj_template_args *a, int64_t batch, int32_t steps,
                          int32_t tile_out[4], float *predicted_log_time);
 

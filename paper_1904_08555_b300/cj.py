@@ -15,18 +15,19 @@ CJ_OK, CJ_ERR_INVALID_ARG, CJ_ERR_NOT_INITIALIZED, CJ_ERR_NO_DEVICE = 0, 1, 2, 3
 CJ_ERR_UNSUPPORTED_ARCH, CJ_ERR_COMPILE, CJ_ERR_CUDA, CJ_ERR_OOM = 4, 5, 6, 7
 CJ_ERR_TIMEOUT, CJ_ERR_PENDING = 8, 9
 
-K_UPDATE_CHAIN, K_LTIMES, K_UPDATE_CHAIN_GROUPED, K_LPLUSTIMES, K_EIGEN_RECURRENCE = 1, 2, 3, 4, 5
+K_UPDATE_CHAIN, K_LTIMES, K_UPDATE_CHAIN_GROUPED, K_LPLUSTIMES, K_EIGEN_RECURRENCE, K_MASS = 1, 2, 3, 4, 5, 6
 F64, F32, BF16 = 0, 1, 2
 FLAG_GENERIC, FLAG_NO_AOT, FLAG_INJECT_COMPILE_ERROR, FLAG_INJECT_WAIT_TIMEOUT = 0x1, 0x2, 0x100, 0x200
 CFG_COMPILE_ONLY = 0x1
+PLAN_GRAPH, PLAN_PER_GROUP = 0x1, 0x2
 VARIANT_NAMES = ("generic", "aot", "jit")
 
 EXPORTS = ("cj_init", "cj_specialize", "cj_specialize_wait", "cj_launch", "cj_stats", "cj_handle_info",
            "cj_handle_regs", "cj_handle_wait_timeouts", "cj_group_plan_create", "cj_group_plan_launch",
-           "cj_group_plan_autotune", "cj_group_plan_wait", "cj_group_plan_info",
+           "cj_group_plan_autotune", "cj_group_plan_wait", "cj_group_plan_dispatcher", "cj_group_plan_info",
            "cj_group_plan_destroy", "cj_measure_fma_peak", "cj_update_chain_uneven_noalloc", "cj_candidates",
            "cj_autotune", "cj_featurize", "cj_mlp_create", "cj_mlp_set_params", "cj_mlp_get_params",
-           "cj_mlp_forward", "cj_mlp_grad", "cj_mlp_train_step", "cj_mlp_destroy", "cj_cost_model_use",
+           "cj_mlp_forward", "cj_mlp_grad", "cj_mlp_train_step", "cj_mlp_destroy", "cj_cost_model_use", "cj_cost_model_use_ensemble",
            "cj_choose_tile", "cj_last_error", "cj_shutdown")
 FEATURES = 32
 
@@ -53,7 +54,8 @@ class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("requests", "cache_hits", "compiles_ok", "compiles_failed",
                                                "aot_hits", "launches_generic", "launches_aot", "launches_jit")] + \
                [(n, ctypes.c_double) for n in ("compile_ms_p50", "compile_ms_p95", "lookup_ns_p50")] + \
-               [(n, ctypes.c_uint64) for n in ("launches_tma", "launches_tma_fallback", "wait_timeouts")]
+               [(n, ctypes.c_uint64) for n in ("launches_tma", "launches_tma_fallback", "launches_dispatch",
+                                               "wait_timeouts")]
 
 
 _lib = None
@@ -82,6 +84,7 @@ def load():
         L.cj_group_plan_launch.argtypes = [P, P, P, P, ctypes.c_int]
         L.cj_group_plan_autotune.argtypes = [P, P, P, P, i32, i32, ctypes.POINTER(i32)]
         L.cj_group_plan_wait.argtypes = [P, ctypes.c_int]
+        L.cj_group_plan_dispatcher.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
         L.cj_group_plan_info.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i64)]
         L.cj_group_plan_destroy.argtypes = [P]
         L.cj_measure_fma_peak.argtypes = [i32, i32, P, ctypes.POINTER(ctypes.c_double)]
@@ -98,6 +101,7 @@ def load():
         L.cj_mlp_train_step.argtypes = [P, P, P, i64, ctypes.c_float, P, P]
         L.cj_mlp_destroy.argtypes = [P]
         L.cj_cost_model_use.argtypes = [P]
+        L.cj_cost_model_use_ensemble.argtypes = [ctypes.POINTER(P), i32]
         L.cj_choose_tile.argtypes = [ctypes.c_int, TA, i64, i32, P, ctypes.POINTER(ctypes.c_float)]
         L.cj_last_error.restype = ctypes.c_char_p
         L.cj_shutdown.argtypes = []
@@ -234,6 +238,12 @@ def launch_eigen(h: Handle, M0, M, repeat: int, c: float = 5e-5, batch=None, str
     _launch(h, vals, batch, _stream(stream, M0, M))
 
 
+def launch_mass(h: Handle, B1, op, x, y, ne: int, stream=None) -> None:
+    """y_e = B^T diag(op_e) B x_e for ne elements (B1: [Q][D]; op: ne*Q^d; x, y: ne*D^d)."""
+    vals = [ctypes.c_void_p(_ptr(B1)), ctypes.c_void_p(_ptr(op)), ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(y))]
+    _launch(h, vals, ne, _stream(stream, B1, op, x, y))
+
+
 def launch_grouped(h: Handle, items, A_pool, X_pool, counter, n_items: int, stream=None) -> None:
     vals = [ctypes.c_void_p(_ptr(items)), ctypes.c_void_p(_ptr(A_pool)), ctypes.c_void_p(_ptr(X_pool)),
             ctypes.c_void_p(_ptr(counter))]
@@ -304,11 +314,22 @@ class GroupPlan:
         _check(load().cj_group_plan_info(self.ptr, ctypes.byref(g), ctypes.byref(e)), "cj_group_plan_info")
         self.n_groups, self.pool_elems = g.value, e.value
 
-    def launch(self, A_pool, X_pool, stream=None, use_graph=True) -> None:
+    def launch(self, A_pool, X_pool, stream=None, use_graph=True, per_group=False) -> None:
+        """One launch of the whole batch: the plan's dispatcher once it is
+        compiled (unless per_group), else one kernel per group."""
         _check_pool(A_pool, self.dtype, self.pool_elems, "cj_group_plan_launch")
         _check_pool(X_pool, self.dtype, self.pool_elems, "cj_group_plan_launch")
+        flags = (PLAN_GRAPH if use_graph else 0) | (PLAN_PER_GROUP if per_group else 0)
         _check(load().cj_group_plan_launch(self.ptr, _ptr(A_pool), _ptr(X_pool), _stream(stream, A_pool, X_pool),
-                                           int(use_graph)), "cj_group_plan_launch")
+                                           flags), "cj_group_plan_launch")
+
+    def dispatcher(self) -> dict:
+        """State of the plan's dispatcher: none, compiling, ready or failed."""
+        st, nt, th = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+        _check(load().cj_group_plan_dispatcher(self.ptr, ctypes.byref(st), ctypes.byref(nt), ctypes.byref(th)),
+               "cj_group_plan_dispatcher")
+        return {"state": ("none", "compiling", "ready", "failed", "not used")[st.value], "tickets": nt.value,
+                "threads": th.value}
 
     def autotune(self, A_pool, X_pool, stream=None, max_groups: int = 0, reps: int = 3) -> int:
         """Time every candidate tile per group (most expensive first) and keep the fastest; returns groups changed."""
@@ -427,6 +448,12 @@ class MLP:
 
 def clear_cost_model():
     _check(load().cj_cost_model_use(None), "cj_cost_model_use")
+
+
+def use_cost_model_ensemble(nets) -> None:
+    """Install several networks; their predictions are averaged."""
+    arr = (ctypes.c_void_p * len(nets))(*[n.ptr for n in nets])
+    _check(load().cj_cost_model_use_ensemble(arr, len(nets)), "cj_cost_model_use_ensemble")
 
 
 def choose_tile(kernel: int, dtype: int, batch: int, steps: int, n=0, layout_a=0, layout_b=0, m=0, d=0):

@@ -5,6 +5,7 @@
 // compiling the same instantiation (Sec. 2).
 #include "cj_internal.h"
 #include "kernels/ltimes.cuh"
+#include "kernels/mass.cuh"
 #include "kernels/update_chain.cuh"
 
 using namespace cjint;
@@ -27,6 +28,7 @@ static const GenericKernels kGeneric = {
     {(const void *)&cj::update_chain_grouped_generic<double>,
      (const void *)&cj::update_chain_grouped_generic<float>},
     {(const void *)&cj::eigen_recurrence_generic<double>, (const void *)&cj::eigen_recurrence_generic<float>},
+    {(const void *)&cj::mass_apply_generic<double>, (const void *)&cj::mass_apply_generic<float>},
 };
 
 // Roofline denominator: 8 independent FMA chains per thread and nothing else

@@ -20,6 +20,7 @@
 #include <array>
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstdarg>
 #include <cstdio>
@@ -142,6 +143,7 @@ struct cj_handle_s {
     CUlibrary lib = nullptr;
     CUdeviceptr wait_count = 0;   // the module's cj_wait_timeouts, if it has bounded waits
     std::string name_expr, name_expr2, error;
+    std::string custom_src;   // plan dispatchers: the generated translation unit
     double compile_ms = 0;
 };
 
@@ -164,7 +166,7 @@ struct State {
     int busy = 0;
     std::condition_variable idle_cv;
     std::vector<std::thread> workers;
-    CUfunction gen_chain[2]{}, gen_lt[2]{}, gen_grp[2]{}, gen_eig[2]{};
+    CUfunction gen_chain[2]{}, gen_lt[2]{}, gen_grp[2]{}, gen_eig[2]{}, gen_mass[2]{};
     struct Aot {
         cjint::AotKernel k;
         CUfunction fn;
@@ -173,7 +175,7 @@ struct State {
     std::vector<cj_group_plan_s *> plans;
     // statistics
     std::atomic<uint64_t> requests{0}, hits{0}, ok{0}, failed{0}, aot_hits{0};
-    std::atomic<uint64_t> l_gen{0}, l_aot{0}, l_jit{0}, l_tma{0}, l_tma_fb{0};
+    std::atomic<uint64_t> l_gen{0}, l_aot{0}, l_jit{0}, l_tma{0}, l_tma_fb{0}, l_disp{0};
     std::mutex smu;
     std::vector<double> compile_ms;
     std::vector<double> lookup_ns;
@@ -213,6 +215,15 @@ int lt_axis_host(int lay, int s) {
 }
 bool is_lt(int k) { return k == CJ_K_LTIMES || k == CJ_K_LPLUSTIMES; }
 bool is_eig(int k) { return k == CJ_K_EIGEN_RECURRENCE; }
+bool is_mass(int k) { return k == CJ_K_MASS; }
+// Mass operator default: elements per block filling about 256 threads, both
+// buffers of every element within 96 KiB.
+int mass_default_epb(int dim, int D, int Q, int es) {
+    const int m = cjg::mass_m(D, Q);
+    int epb = std::max(1, 256 / (m * m));
+    while (epb > 1 && cjg::mass_smem(dim, D, Q, epb, es) > 96 * 1024) --epb;
+    return epb;
+}
 // Eigen recurrence default: f32 with n >= 2 two rows per thread (mapping 2),
 // else one; instances per block up to 128 threads, both buffers within 96 KiB.
 int eig_default_map(int n, int dtype) { return dtype == CJ_F32 && n >= 2 ? 2 : 1; }
@@ -234,6 +245,11 @@ LtView lt_view(int k, const cj_template_args &a) {
 }
 
 void default_tile(int k, cj_template_args &a) {
+    if (is_mass(k)) {
+        a.tile[0] = mass_default_epb(a.d, a.n, a.m, esize(a.dtype));
+        a.tile[1] = a.tile[2] = a.tile[3] = 0;
+        return;
+    }
     if (is_eig(k)) {
         a.tile[0] = eig_default_map(a.n, a.dtype);
         a.tile[1] = eig_default_ipb(a.n, esize(a.dtype), a.tile[0]);
@@ -311,7 +327,7 @@ void make_key(int k, const cj_template_args &a, unsigned char *key) {
 cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_args &a) {
     a = in;
     if (k != CJ_K_UPDATE_CHAIN && k != CJ_K_LTIMES && k != CJ_K_UPDATE_CHAIN_GROUPED && k != CJ_K_LPLUSTIMES &&
-        k != CJ_K_EIGEN_RECURRENCE)
+        k != CJ_K_EIGEN_RECURRENCE && k != CJ_K_MASS)
         return fail(CJ_ERR_INVALID_ARG, "unknown kernel id %d", k);
     if (a.dtype < 0 || a.dtype > 2) return fail(CJ_ERR_INVALID_ARG, "dtype %d out of range", a.dtype);
     if (a.flags & ~kKeyFlags) return fail(CJ_ERR_INVALID_ARG, "unknown flag bits 0x%x", a.flags & ~kKeyFlags);
@@ -322,6 +338,13 @@ cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_
         if (a.m < 1 || a.m > 64 || a.d < 1 || a.d > 128)
             return fail(CJ_ERR_INVALID_ARG, "LTimes needs 1 <= m <= 64 and 1 <= d <= 128");
         a.n = 0;
+    } else if (is_mass(k)) {
+        if (a.dtype == CJ_BF16) return fail(CJ_ERR_INVALID_ARG, "the mass operator supports f64 and f32 only");
+        if (a.d != 2 && a.d != 3) return fail(CJ_ERR_INVALID_ARG, "mass operator dimension d = %d must be 2 or 3", a.d);
+        if (a.n < 1 || a.n > 16 || a.m < 1 || a.m > 16)
+            return fail(CJ_ERR_INVALID_ARG, "mass operator needs 1 <= n (dofs per dimension) <= 16 and "
+                                            "1 <= m (quadrature points per dimension) <= 16");
+        a.layout_a = a.layout_b = 0;
     } else if (is_eig(k)) {
         if (a.n < 1 || a.n > 32) return fail(CJ_ERR_INVALID_ARG, "Eigen recurrence n = %d outside 1..32", a.n);
         if (a.dtype == CJ_BF16) return fail(CJ_ERR_INVALID_ARG, "the Eigen recurrence supports f64 and f32 only");
@@ -363,6 +386,14 @@ cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_
         if (!chosen) default_tile(k, a);
     }
     // explicit tiles: check the kernel can be instantiated and launched
+    if (is_mass(k)) {
+        if (a.tile[0] < 1 || a.tile[1] || a.tile[2] || a.tile[3] ||
+            cjg::mass_threads(a.n, a.m, a.tile[0]) > 1024 ||
+            cjg::mass_smem(a.d, a.n, a.m, a.tile[0], esize(a.dtype)) > 220 * 1024)
+            return fail(CJ_ERR_INVALID_ARG, "mass operator tile {%d,%d,%d,%d} invalid ({elements per block, 0, 0, 0}, "
+                        "at most 1024 threads and 220 KiB of shared memory)", a.tile[0], a.tile[1], a.tile[2], a.tile[3]);
+        return CJ_OK;
+    }
     if (is_eig(k)) {
         // mapping 1: one row per thread; 2: two rows per thread (f32)
         const int map = a.tile[0];
@@ -458,7 +489,12 @@ void generic_impl(cj_handle_s *h) {
     const cj_template_args &a = h->a;
     const int di = dt_index(a.dtype), es = esize(a.dtype);
     g.variant = V_GENERIC;
-    if (is_eig(h->kernel)) {
+    if (is_mass(h->kernel)) {
+        g.fn = G.gen_mass[di];
+        g.ipb = mass_default_epb(a.d, a.n, a.m, es);
+        g.threads = cjg::mass_threads(a.n, a.m, g.ipb);
+        g.smem = (size_t)cjg::mass_smem(a.d, a.n, a.m, g.ipb, es);
+    } else if (is_eig(h->kernel)) {
         g.fn = G.gen_eig[di];
         g.ipb = eig_default_ipb(a.n, es);
         g.threads = cjg::chain_threads(a.n, 1, g.ipb);
@@ -477,10 +513,20 @@ void generic_impl(cj_handle_s *h) {
     }
 }
 
+// Internal kernel id of a plan dispatcher (never a request; no 32-byte key).
+constexpr int kDispatchKernel = 100;
+
 void spec_geometry(const cj_handle_s *h, Impl &s) {
     const cj_template_args &a = h->a;
     const int es = esize(a.dtype);
-    if (is_eig(h->kernel)) {
+    if (h->kernel == kDispatchKernel) {
+        s.threads = a.tile[0];
+        s.smem = (size_t)a.tile[1];
+    } else if (is_mass(h->kernel)) {
+        s.ipb = a.tile[0];
+        s.threads = cjg::mass_threads(a.n, a.m, a.tile[0]);
+        s.smem = (size_t)cjg::mass_smem(a.d, a.n, a.m, a.tile[0], es);
+    } else if (is_eig(h->kernel)) {
         s.ipb = a.tile[1];
         s.threads = cjg::chain_threads(a.n, a.tile[0] == 2 ? 6 : 1, a.tile[1]);
         s.smem = (size_t)cjg::eig_smem(a.n, a.tile[1], es, a.tile[0]);
@@ -524,6 +570,8 @@ std::string name_expression(const cj_handle_s *h) {
     if (h->kernel == CJ_K_UPDATE_CHAIN)
         snprintf(buf, sizeof buf, "cj::update_chain<%s, %d, %d, %d, %d>", ctype(a.dtype), a.n, a.layout_a,
                  a.tile[0], a.tile[1]);
+    else if (is_mass(h->kernel))
+        snprintf(buf, sizeof buf, "cj::mass_apply<%s, %d, %d, %d, %d>", ctype(a.dtype), a.d, a.n, a.m, a.tile[0]);
     else if (is_eig(h->kernel))
         snprintf(buf, sizeof buf, "cj::eigen_recurrence%s<%s, %d, %d>", a.tile[0] == 2 ? "2" : "", ctype(a.dtype),
                  a.n, a.tile[1]);
@@ -567,10 +615,10 @@ struct CompileOut {
 
 CompileOut nvrtc_compile(const std::string &src, const char *name_expr, const char *name_expr2 = nullptr) {
     CompileOut out;
-    const char *hdr_src[3] = {cj_emb_geometry_h, cj_emb_update_chain_cuh, cj_emb_ltimes_cuh};
-    const char *hdr_name[3] = {"geometry.h", "update_chain.cuh", "ltimes.cuh"};
+    const char *hdr_src[4] = {cj_emb_geometry_h, cj_emb_update_chain_cuh, cj_emb_ltimes_cuh, cj_emb_mass_cuh};
+    const char *hdr_name[4] = {"geometry.h", "update_chain.cuh", "ltimes.cuh", "mass.cuh"};
     nvrtcProgram prog;
-    out.rc = nvrtcCreateProgram(&prog, src.c_str(), "cj_instantiation.cu", 3, hdr_src, hdr_name);
+    out.rc = nvrtcCreateProgram(&prog, src.c_str(), "cj_instantiation.cu", 4, hdr_src, hdr_name);
     if (out.rc != NVRTC_SUCCESS) return out;
     if (name_expr) nvrtcAddNameExpression(prog, name_expr);
     if (name_expr2) nvrtcAddNameExpression(prog, name_expr2);
@@ -618,7 +666,10 @@ void finish(cj_handle_s *h, int state) {
 
 cj_status compile_handle(cj_handle_s *h) {
     const auto t0 = clk::now();
-    std::string src = is_lt(h->kernel) ? "#include \"ltimes.cuh\"\n" : "#include \"update_chain.cuh\"\n";
+    std::string src = !h->custom_src.empty() ? h->custom_src
+                      : is_lt(h->kernel)      ? "#include \"ltimes.cuh\"\n"
+                      : is_mass(h->kernel)    ? "#include \"mass.cuh\"\n"
+                                              : "#include \"update_chain.cuh\"\n";
     if (h->a.flags & CJ_FLAG_INJECT_COMPILE_ERROR)
         src += "namespace cj { __device__ int injected_failure = this_identifier_does_not_exist; }\n";
     CompileOut c = nvrtc_compile(src, h->name_expr.c_str(), h->name_expr2.empty() ? nullptr : h->name_expr2.c_str());
@@ -676,7 +727,7 @@ void worker_loop() {
         {
             std::unique_lock<std::mutex> lk(G.mu);
             G.qcv.wait(lk, [] { return G.stop || !G.queue.empty(); });
-            if (G.queue.empty()) return;
+            if (G.stop || G.queue.empty()) return;   // shutdown drops compiles not yet started
             h = G.queue.front();
             G.queue.pop_front();
             G.busy++;
@@ -734,6 +785,12 @@ struct cj_group_plan_s {
     const void *g_A = nullptr;
     void *g_X = nullptr;
     std::vector<const void *> g_impls;
+    // the plan's dispatcher: one persistent kernel over every group, taking
+    // cost-ordered tickets (chunks of one group) from counter ngroups
+    cj_handle disp = nullptr;
+    long long *d_tickets = nullptr;
+    int n_tickets = 0;
+    bool use_dispatcher = true;   // false once the plan's autotuner found the per-group form faster
 };
 
 namespace {
@@ -747,13 +804,54 @@ void plan_free(cj_group_plan_s *p) {
     if (p->capture) cudaStreamDestroy(p->capture);
     if (p->d_items) cudaFree(p->d_items);
     if (p->d_counters) cudaFree(p->d_counters);
+    if (p->d_tickets) cudaFree(p->d_tickets);
     delete p;
 }
 
-cj_status plan_record(cj_group_plan_s *p, const void *A, void *X, cudaStream_t st) {
-    if (cudaMemsetAsync(p->d_counters, 0, sizeof(int) * p->groups.size(), st) != cudaSuccess ||
-        cudaEventRecord(p->fork, st) != cudaSuccess)
-        return fail(CJ_ERR_CUDA, "grouped plan: memset/event record failed");
+// The dispatcher's tile for a group of size n and dtype (the group's own:
+// f32 for the n < 16 groups of a bf16 plan), for blocks of `block` threads:
+// bf16 tensor-core panels (mapping 3); f32 n >= 8 register blocks (mapping
+// 5); n <= 4 one instance per thread (mapping 2); otherwise one row per
+// thread (mapping 1).  As many instances per chunk as fill the block (at
+// most 256), fewer where shared memory would exceed 160 KiB.
+std::array<int, 2> dispatch_tile(int dtype, int n, int block) {
+    const int es = esize(dtype);
+    int map, tpi;
+    if (dtype == CJ_BF16) map = 3, tpi = ((n + 15) / 16) * 32;
+    else if (dtype == CJ_F32 && n >= 8) map = 5, tpi = ((n + 3) / 4) * ((n + 3) / 4);
+    else if (n <= 4) map = 2, tpi = 1;
+    else map = 1, tpi = n;
+    int ipb = std::max(1, std::min(256, block / tpi));
+    while (ipb > 1 && (cjg::chain_threads(n, map, ipb) > block || cjg::chain_smem(n, map, ipb, es) > 160 * 1024))
+        --ipb;
+    return {map, ipb};
+}
+
+bool dispatcher_ready(const cj_group_plan_s *p) {
+    return p->disp && p->disp->state.load(std::memory_order_acquire) == ST_READY &&
+           p->disp->impl.load(std::memory_order_acquire) == &p->disp->spec;
+}
+
+cj_status plan_record(cj_group_plan_s *p, const void *A, void *X, cudaStream_t st, bool per_group) {
+    if (cudaMemsetAsync(p->d_counters, 0, sizeof(int) * (p->groups.size() + 1), st) != cudaSuccess)
+        return fail(CJ_ERR_CUDA, "grouped plan: counter reset failed");
+    if (!per_group && p->use_dispatcher && dispatcher_ready(p)) {
+        // one persistent launch for the whole batch
+        const Impl *im = p->disp->impl.load(std::memory_order_acquire);
+        const unsigned grid = (unsigned)std::min<long long>(p->n_tickets, (long long)G.num_sms * im->blocks_per_sm);
+        void *tickets = p->d_tickets, *items = p->d_items, *counter = p->d_counters + p->groups.size();
+        int nt = p->n_tickets;
+        const void *a = A;
+        void *x = X;
+        void *args[6] = {&tickets, &nt, &items, &a, &x, &counter};
+        const CUresult r = drv.LaunchKernel(im->fn, grid, 1, 1, im->threads, 1, 1, (unsigned)im->smem,
+                                            reinterpret_cast<CUstream>(st), args, nullptr);
+        if (r != CUDA_SUCCESS) return fail(CJ_ERR_CUDA, "plan dispatcher launch failed: %s", cu_str(r));
+        G.l_disp++;
+        return CJ_OK;
+    }
+    if (cudaEventRecord(p->fork, st) != cudaSuccess)
+        return fail(CJ_ERR_CUDA, "grouped plan: event record failed");
     for (size_t g = 0; g < p->groups.size(); ++g) {
         cudaStream_t s = p->streams[g % p->streams.size()];
         if (g < p->streams.size() && cudaStreamWaitEvent(s, p->fork, 0) != cudaSuccess)
@@ -772,6 +870,87 @@ cj_status plan_record(cj_group_plan_s *p, const void *A, void *X, cudaStream_t s
             cudaStreamWaitEvent(st, p->join[i], 0) != cudaSuccess)
             return fail(CJ_ERR_CUDA, "grouped plan: join failed");
     }
+    return CJ_OK;
+}
+
+// Generate, request (compile in the background, or inline in sync mode) and
+// ticket the plan's dispatcher.  `items` is the plan's work list on the host
+// ({offset, T, 0} per item, groups contiguous, each ordered by T descending).
+cj_status plan_dispatcher(cj_group_plan_s *p, const std::vector<long long> &items) {
+    constexpr int kBlock = 256;
+    const char *ct = p->dtype == CJ_F64 ? "double" : "float";
+    // blocks per SM the registers must allow (launch bounds): FP32 and BF16
+    // bodies fit 128 registers (two blocks of 256), FP64 rows of X need more
+    const int minb = p->dtype == CJ_F64 ? 1 : 2;
+    std::string src = "#include \"update_chain.cuh\"\nnamespace cj {\n__global__ void __launch_bounds__(" +
+                      std::to_string(kBlock) + ", " + std::to_string(minb) +
+                      ")\nplan_dispatch(const long long* __restrict__ tickets, int n_tickets, "
+                      "const long long* __restrict__ items, const " + std::string(ct) + "* __restrict__ A, " + ct +
+                      "* __restrict__ X, int* __restrict__ counter) {\n"
+                      "    dispatch_tickets<" + ct + ">(tickets, n_tickets, items, counter,\n"
+                      "        [&](int g, const long long* it, int ninst, " + ct + "* sA, long long* so, int* ss) {\n"
+                      "        switch (g) {\n";
+    long smem = 0;
+    struct Tk {
+        double cost;
+        long long first;
+        int group, count;
+    };
+    std::vector<Tk> tk;
+    for (size_t g = 0; g < p->groups.size(); ++g) {
+        const auto &gr = p->groups[g];
+        const int gdt = (p->dtype == CJ_BF16 && gr.n < 16) ? CJ_F32 : p->dtype;
+        const auto t = dispatch_tile(gdt, gr.n, kBlock);
+        smem = std::max(smem, cjg::chain_smem(gr.n, t[0], t[1], esize(gdt)));
+            src += "        case " + std::to_string(g) + ": grouped_chunk_call<" + ct + ", " + std::to_string(gr.n) +
+               ", " + std::to_string(t[0]) + ", " + std::to_string(t[1]) + ", " + std::to_string(kBlock) +
+               ">(it, ninst, A, X, sA, so, ss); break;\n";
+        const double per = 2.0 * gr.n * gr.n * gr.n + 2.0 * gr.n * gr.n;
+        for (int64_t c = 0; c < gr.n_items; c += t[1]) {
+            Tk k{0.0, gr.first_item + c, (int)g, (int)std::min<int64_t>(t[1], gr.n_items - c)};
+            for (int i = 0; i < k.count; ++i) k.cost += per * (double)items[3 * (k.first + i) + 1];
+            tk.push_back(k);
+        }
+    }
+    src += "        default: break;\n        }\n    });\n}\n}  // namespace cj\n";
+    // longest chunks first
+    std::stable_sort(tk.begin(), tk.end(), [](const Tk &x, const Tk &y) { return x.cost > y.cost; });
+    std::vector<long long> host(2 * tk.size());
+    for (size_t i = 0; i < tk.size(); ++i) {
+        host[2 * i] = tk[i].first;
+        host[2 * i + 1] = ((long long)tk[i].group << 16) | tk[i].count;
+    }
+    p->n_tickets = (int)tk.size();
+    if (cudaMalloc(&p->d_tickets, sizeof(long long) * host.size()) != cudaSuccess)
+        return fail(CJ_ERR_OOM, "grouped plan: dispatcher tickets");
+    if (cudaMemcpy(p->d_tickets, host.data(), sizeof(long long) * host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(CJ_ERR_CUDA, "grouped plan: dispatcher ticket upload failed");
+    // one instantiation per distinct source (identical plans share it)
+    const std::string ks = "dispatch:" + src;
+    cj_handle_s *h = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(G.mu);
+        auto it = G.cache.find(ks);
+        if (it != G.cache.end()) {
+            h = it->second;
+        } else {
+            h = new cj_handle_s();
+            h->kernel = kDispatchKernel;
+            h->a.dtype = p->dtype;
+            h->a.tile[0] = kBlock;
+            h->a.tile[1] = (int)smem;
+            h->custom_src = src;
+            h->name_expr = "cj::plan_dispatch";
+            h->impl.store(&h->generic, std::memory_order_release);   // no stand-in of its own
+            h->state = ST_PENDING;
+            // compiled on the background threads even in sync mode: the
+            // per-group kernels serve until it is ready (cj_group_plan_wait)
+            G.queue.push_back(h);
+            G.qcv.notify_one();
+            G.cache.emplace(ks, h);
+        }
+    }
+    p->disp = h;
     return CJ_OK;
 }
 
@@ -824,7 +1003,8 @@ CJ_API cj_status cj_init(const cj_config *cfg, int device) {
         const auto &gk = cjint::generic_kernels();
         for (int d = 0; d < 2; ++d)
             if (!prep(gk.chain[d], &G.gen_chain[d]) || !prep(gk.ltimes[d], &G.gen_lt[d]) ||
-                !prep(gk.grouped[d], &G.gen_grp[d]) || !prep(gk.eigen[d], &G.gen_eig[d]))
+                !prep(gk.grouped[d], &G.gen_grp[d]) || !prep(gk.eigen[d], &G.gen_eig[d]) ||
+                !prep(gk.mass[d], &G.gen_mass[d]))
                 return fail(CJ_ERR_CUDA, "could not load the generic kernels");
         int na = 0;
         const cjint::AotKernel *tab = cjint::aot_table(&na);
@@ -845,7 +1025,7 @@ CJ_API cj_status cj_init(const cj_config *cfg, int device) {
     if (w.rc != NVRTC_SUCCESS) return fail(CJ_ERR_COMPILE, "NVRTC warm-up failed: %s", w.log.c_str());
     G.stop = false;
     G.requests = G.hits = G.ok = G.failed = G.aot_hits = 0;
-    G.l_gen = G.l_aot = G.l_jit = G.l_tma = G.l_tma_fb = 0;
+    G.l_gen = G.l_aot = G.l_jit = G.l_tma = G.l_tma_fb = G.l_disp = 0;
     {
         std::lock_guard<std::mutex> lk(G.smu);
         G.compile_ms.clear();
@@ -989,13 +1169,34 @@ CJ_API cj_status cj_launch(cj_handle h, void *const *args, int64_t batch, void *
         if (batch == 0) return CJ_OK;
         long long b = batch;
         double c = 1.0 / ((double)a.n * (double)steps);
-        const unsigned grid = (unsigned)((batch + im->ipb - 1) / im->ipb);
+        // a batch whose full blocks would leave SMs idle is spread over up to
+        // one block per SM, each taking fewer instances than it is shaped for
+        int ipb = im->ipb;
+        if (batch < (long long)ipb * G.num_sms) ipb = (int)std::max<long long>(1, (batch + G.num_sms - 1) / G.num_sms);
+        const unsigned grid = (unsigned)((batch + ipb - 1) / ipb);
         if (im->variant == V_GENERIC) {
-            int n = a.n, lay = a.layout_a, ipb = im->ipb;
+            int n = a.n, lay = a.layout_a;
             void *p[] = {&A, &X, &b, &steps, &c, &n, &lay, &ipb};
             r = drv.LaunchKernel(im->fn, grid, 1, 1, im->threads, 1, 1, (unsigned)im->smem, st, p, nullptr);
         } else {
-            void *p[] = {&A, &X, &b, &steps, &c};
+            void *p[] = {&A, &X, &b, &steps, &c, &ipb};
+            r = drv.LaunchKernel(im->fn, grid, 1, 1, im->threads, 1, 1, (unsigned)im->smem, st, p, nullptr);
+        }
+    } else if (is_mass(h->kernel)) {
+        void *B1 = *reinterpret_cast<void *const *>(args[0]);
+        void *op = *reinterpret_cast<void *const *>(args[1]);
+        void *xv = *reinterpret_cast<void *const *>(args[2]);
+        void *yv = *reinterpret_cast<void *const *>(args[3]);
+        if (!B1 || !op || !xv || !yv) return fail(CJ_ERR_INVALID_ARG, "null B1/op/x/y");
+        if (batch == 0) return CJ_OK;
+        long long ne = batch;
+        const unsigned grid = (unsigned)((batch + im->ipb - 1) / im->ipb);
+        if (im->variant == V_GENERIC) {
+            int dim = a.d, D = a.n, Q = a.m, epb = im->ipb;
+            void *p[] = {&B1, &op, &xv, &yv, &ne, &dim, &D, &Q, &epb};
+            r = drv.LaunchKernel(im->fn, grid, 1, 1, im->threads, 1, 1, (unsigned)im->smem, st, p, nullptr);
+        } else {
+            void *p[] = {&B1, &op, &xv, &yv, &ne};
             r = drv.LaunchKernel(im->fn, grid, 1, 1, im->threads, 1, 1, (unsigned)im->smem, st, p, nullptr);
         }
     } else if (is_eig(h->kernel)) {
@@ -1108,6 +1309,7 @@ CJ_API cj_status cj_stats(cj_stats_t *out) {
     out->launches_jit = G.l_jit;
     out->launches_tma = G.l_tma;
     out->launches_tma_fallback = G.l_tma_fb;
+    out->launches_dispatch = G.l_disp;
     {
         std::lock_guard<std::mutex> lk(G.smu);
         out->compile_ms_p50 = percentile(G.compile_ms, 0.5);
@@ -1235,7 +1437,7 @@ CJ_API cj_status cj_group_plan_create(int32_t dtype, int64_t count, const int32_
             return rc;
         }
     }
-    const size_t ng = std::max<size_t>(1, p->groups.size());
+    const size_t ng = p->groups.size() + 1;   // one counter per group, one for the dispatcher
     if (cudaMalloc(&p->d_counters, sizeof(int) * ng) != cudaSuccess ||
         (!items.empty() && cudaMalloc(&p->d_items, sizeof(long long) * items.size()) != cudaSuccess)) {
         plan_free(p);
@@ -1246,7 +1448,14 @@ CJ_API cj_status cj_group_plan_create(int32_t dtype, int64_t count, const int32_
         plan_free(p);
         return fail(CJ_ERR_CUDA, "grouped plan: work list upload failed");
     }
-    const size_t ns = std::min<size_t>(64, ng);   // one stream per group: groups run concurrently
+    if (!(flags & CJ_FLAG_GENERIC) && !p->groups.empty()) {
+        cj_status rc = plan_dispatcher(p, items);
+        if (rc != CJ_OK && rc != CJ_ERR_COMPILE) {
+            plan_free(p);
+            return rc;
+        }
+    }
+    const size_t ns = std::min<size_t>(64, std::max<size_t>(1, p->groups.size()));   // one stream per group
     p->streams.resize(ns);
     p->join.resize(ns);
     for (size_t i = 0; i < ns; ++i) {
@@ -1263,15 +1472,30 @@ CJ_API cj_status cj_group_plan_create(int32_t dtype, int64_t count, const int32_
     return CJ_OK;
 }
 
+namespace {
+cj_status plan_launch(cj_group_plan_s *p, const void *A_pool, void *X_pool, cudaStream_t st, int use_graph);
+}
+
 CJ_API cj_status cj_group_plan_launch(cj_group_plan p, const void *A_pool, void *X_pool, void *cuda_stream,
                                       int use_graph) {
     if (!G.inited) return fail(CJ_ERR_NOT_INITIALIZED, "cj_init has not been called");
     if (!p || (p->pool_elems > 0 && (!A_pool || !X_pool))) return fail(CJ_ERR_INVALID_ARG, "null plan or pool");
     if (p->groups.empty()) return CJ_OK;
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
-    if (!use_graph) return plan_record(p, A_pool, X_pool, st);
+    if (use_graph & ~(CJ_PLAN_GRAPH | CJ_PLAN_PER_GROUP)) return fail(CJ_ERR_INVALID_ARG, "unknown launch flags");
+    return plan_launch(p, A_pool, X_pool, reinterpret_cast<cudaStream_t>(cuda_stream), use_graph);
+}
+
+namespace {
+// cj_group_plan_launch after argument checks (also used by the autotuner).
+cj_status plan_launch(cj_group_plan_s *p, const void *A_pool, void *X_pool, cudaStream_t st, int use_graph) {
+    const bool per_group = (use_graph & CJ_PLAN_PER_GROUP) != 0;
+    if (!(use_graph & CJ_PLAN_GRAPH)) return plan_record(p, A_pool, X_pool, st, per_group);
+    // what the captured graph launches: the dispatcher, or every group's kernel
     std::vector<const void *> impls;
-    for (auto &g : p->groups) impls.push_back(g.h->impl.load(std::memory_order_acquire));
+    if (!per_group && p->use_dispatcher && dispatcher_ready(p))
+        impls.push_back(p->disp->impl.load(std::memory_order_acquire));
+    else
+        for (auto &g : p->groups) impls.push_back(g.h->impl.load(std::memory_order_acquire));
     if (!p->exec || p->g_A != A_pool || p->g_X != X_pool || p->g_impls != impls) {
         if (p->exec) cudaGraphExecDestroy(p->exec);
         if (p->graph) cudaGraphDestroy(p->graph);
@@ -1279,7 +1503,7 @@ CJ_API cj_status cj_group_plan_launch(cj_group_plan p, const void *A_pool, void 
         p->graph = nullptr;
         if (cudaStreamBeginCapture(p->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
             return fail(CJ_ERR_CUDA, "stream capture could not start");
-        cj_status rc = plan_record(p, A_pool, X_pool, p->capture);
+        cj_status rc = plan_record(p, A_pool, X_pool, p->capture, per_group);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(p->capture, &g);
         if (rc != CJ_OK) {
@@ -1298,6 +1522,7 @@ CJ_API cj_status cj_group_plan_launch(cj_group_plan p, const void *A_pool, void 
     if (cudaGraphLaunch(p->exec, st) != cudaSuccess) return fail(CJ_ERR_CUDA, "graph launch failed");
     return CJ_OK;
 }
+}  // namespace
 
 CJ_API cj_status cj_group_plan_autotune(cj_group_plan p, const void *A_pool, void *X_pool, void *cuda_stream,
                                         int32_t max_groups, int32_t reps, int32_t *changed) {
@@ -1370,6 +1595,33 @@ CJ_API cj_status cj_group_plan_autotune(cj_group_plan p, const void *A_pool, voi
             ++nchg;
         }
     }
+    // 3. the launch form: the dispatcher (once compiled) against one kernel
+    //    per group with the tiles just chosen, each timed as a whole launch
+    //    (each form as a CUDA graph and issued directly; a form's time is the
+    //    faster of the two)
+    if (rc == CJ_OK && p->disp && cj_specialize_wait(p->disp, -1) == CJ_OK && dispatcher_ready(p)) {
+        float best[2] = {INFINITY, INFINITY};
+        p->use_dispatcher = true;
+        const int flags[4] = {CJ_PLAN_GRAPH, 0, CJ_PLAN_GRAPH | CJ_PLAN_PER_GROUP, CJ_PLAN_PER_GROUP};
+        for (int f = 0; f < 4 && rc == CJ_OK; ++f) {
+            std::vector<float> ms;
+            for (int r = 0; r <= reps && rc == CJ_OK; ++r) {
+                float t = 0;
+                if (cudaEventRecord(e0, st) != cudaSuccess)
+                    rc = fail(CJ_ERR_CUDA, "grouped autotune: event failed");
+                else if ((rc = plan_launch(p, A_pool, X_pool, st, flags[f])) == CJ_OK &&
+                         (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                          cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+                    rc = fail(CJ_ERR_CUDA, "grouped autotune: timing failed");
+                else if (r > 0)
+                    ms.push_back(t);
+            }
+            if (rc != CJ_OK) break;
+            std::sort(ms.begin(), ms.end());
+            best[f / 2] = std::min(best[f / 2], ms[ms.size() / 2]);
+        }
+        p->use_dispatcher = rc != CJ_OK || best[0] <= best[1];
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (changed) *changed = nchg;
@@ -1390,7 +1642,28 @@ CJ_API cj_status cj_group_plan_wait(cj_group_plan p, int timeout_ms) {
         if (rc == CJ_ERR_TIMEOUT) return rc;
         if (rc != CJ_OK) worst = rc;
     }
+    if (p->disp) {
+        int left = -1;
+        if (timeout_ms >= 0)
+            left = (int)std::max<long long>(
+                0, std::chrono::duration_cast<std::chrono::milliseconds>(end - clk::now()).count());
+        const cj_status rc = cj_specialize_wait(p->disp, left);
+        if (rc == CJ_ERR_TIMEOUT) return rc;
+        if (rc != CJ_OK) return fail(rc, "the plan's dispatcher failed to compile (per-group kernels serve): %s",
+                                     p->disp->error.c_str());
+    }
     return worst == CJ_OK ? CJ_OK : fail(worst, "a group's instantiation failed to compile; it runs generic");
+}
+
+CJ_API cj_status cj_group_plan_dispatcher(cj_group_plan p, int32_t *state, int32_t *n_tickets, int32_t *threads) {
+    if (!p) return fail(CJ_ERR_INVALID_ARG, "null plan");
+    if (state) {
+        const int s = p->disp ? p->disp->state.load(std::memory_order_acquire) : -1;
+        *state = !p->disp ? 0 : s == ST_PENDING ? 1 : !dispatcher_ready(p) ? 3 : p->use_dispatcher ? 2 : 4;
+    }
+    if (n_tickets) *n_tickets = p->n_tickets;
+    if (threads) *threads = p->disp ? p->disp->a.tile[0] : 0;
+    return CJ_OK;
 }
 
 CJ_API cj_status cj_group_plan_info(cj_group_plan p, int32_t *n_groups, int64_t *pool_elems) {

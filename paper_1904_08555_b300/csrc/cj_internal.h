@@ -43,6 +43,7 @@ struct GenericKernels {
     const void *ltimes[2];
     const void *grouped[2];
     const void *eigen[2];
+    const void *mass[2];
 };
 const GenericKernels &generic_kernels();
 

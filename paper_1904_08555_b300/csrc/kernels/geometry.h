@@ -167,6 +167,17 @@ CJ_HD constexpr long lt_generic_smem(int m, int d, int cols, int esize) {
     return ((long)m * d + (long)d * cols) * esize;
 }
 
+// Mass operator (mass.cuh): an element owns M x M threads, M = max(D, Q);
+// shared memory holds B1 (Q x D) and two buffers of M^dim values per element.
+CJ_HD constexpr int mass_m(int D, int Q) { return D > Q ? D : Q; }
+CJ_HD constexpr int mass_threads(int D, int Q, int epb) { return ((epb * mass_m(D, Q) * mass_m(D, Q) + 31) / 32) * 32; }
+CJ_HD constexpr int mass_b_elems(int D, int Q) { return Q * D; }
+CJ_HD constexpr long mass_smem(int dim, int D, int Q, int epb, int esize) {
+    return ((long)mass_b_elems(D, Q) +
+            2L * epb * (dim == 2 ? mass_m(D, Q) * mass_m(D, Q) : mass_m(D, Q) * mass_m(D, Q) * mass_m(D, Q))) *
+           esize;
+}
+
 }  // namespace cjg
 
 #endif

@@ -1,0 +1,182 @@
+// mass.cuh -- mass operator of tensor-product finite elements, the Laghos
+// kernel of Sec. 5 whose specializations are keyed on the dimension, the
+// dofs per dimension D and the quadrature points per dimension Q:
+//
+//     y_e = B^T diag(op_e) B x_e,   B = B1 (x) B1 [(x) B1],   every element e,
+//
+// with B1[q][d] the 1-D basis at the quadrature points (Q x D, row-major), x_e
+// and y_e D^DIM values, op_e Q^DIM values, first index fastest.  Evaluated by
+// sum factorization: one 1-D contraction per dimension on the way to the
+// quadrature points, the pointwise scaling, one per dimension back.
+//
+// Thread layout: an element owns a square of M x M threads (M = max(D, Q));
+// thread (tx, ty) computes the entries of each stage indexed by (tx, ty),
+// looping over the third index in 3-D.  A block holds EPB elements, each with
+// two shared-memory buffers of M^DIM values that the stages alternate
+// between, and B1 once.  Every thread of a block takes every barrier.
+#ifndef CJ_MASS_CUH
+#define CJ_MASS_CUH
+#include "geometry.h"
+
+namespace cj {
+
+__device__ __forceinline__ double mass_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float mass_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// One element's stages.  D, Q, DIM are compile-time in the specialized kernel
+// and run-time in the generic one (the loops below are the same code; with
+// constants the compiler unrolls them).  b: B1 in shared memory (Q x D);
+// u, v: the element's two buffers (M^DIM each); tx, ty < M.
+template <class T, class Int>
+__device__ __forceinline__ void mass_element(const T* __restrict__ x, const T* __restrict__ op, T* __restrict__ y,
+                                             const T* b, T* u, T* v, Int DIM, Int D, Int Q, Int M, int tx, int ty,
+                                             bool active) {
+    // buffers are indexed [k][j][i] with i fastest, extents M
+    if (DIM == 2) {
+        // X[jy][jx] -> u
+        if (active && tx < D && ty < D) u[ty * M + tx] = x[ty * D + tx];
+        __syncthreads();
+        // T1[jy][qx] = sum_jx B1[qx][jx] X[jy][jx] -> v   (thread qx = tx, jy = ty)
+        if (active && tx < Q && ty < D) {
+            T s = T(0);
+#pragma unroll
+            for (Int jx = 0; jx < D; ++jx) s = mass_fma(b[tx * D + jx], u[ty * M + jx], s);
+            v[ty * M + tx] = s;
+        }
+        __syncthreads();
+        // T2[qy][qx] = op * sum_jy B1[qy][jy] T1[jy][qx] -> u   (qx = tx, qy = ty)
+        if (active && tx < Q && ty < Q) {
+            T s = T(0);
+#pragma unroll
+            for (Int jy = 0; jy < D; ++jy) s = mass_fma(b[ty * D + jy], v[jy * M + tx], s);
+            u[ty * M + tx] = op[ty * Q + tx] * s;
+        }
+        __syncthreads();
+        // T3[qy][jx] = sum_qx B1[qx][jx] T2[qy][qx] -> v   (jx = tx, qy = ty)
+        if (active && tx < D && ty < Q) {
+            T s = T(0);
+#pragma unroll
+            for (Int qx = 0; qx < Q; ++qx) s = mass_fma(b[qx * D + tx], u[ty * M + qx], s);
+            v[ty * M + tx] = s;
+        }
+        __syncthreads();
+        // Y[jy][jx] = sum_qy B1[qy][jy] T3[qy][jx]   (jx = tx, jy = ty)
+        if (active && tx < D && ty < D) {
+            T s = T(0);
+#pragma unroll
+            for (Int qy = 0; qy < Q; ++qy) s = mass_fma(b[qy * D + ty], v[qy * M + tx], s);
+            y[ty * D + tx] = s;
+        }
+    } else {
+        const Int MM = M * M;
+        // X[jz][jy][jx] -> u
+        if (active && tx < D && ty < D)
+#pragma unroll
+            for (Int jz = 0; jz < D; ++jz) u[jz * MM + ty * M + tx] = x[(jz * D + ty) * D + tx];
+        __syncthreads();
+        // x: T1[jz][jy][qx] = sum_jx B1[qx][jx] X[jz][jy][jx] -> v   (qx = tx, jy = ty)
+        if (active && tx < Q && ty < D)
+#pragma unroll
+            for (Int jz = 0; jz < D; ++jz) {
+                T s = T(0);
+#pragma unroll
+                for (Int jx = 0; jx < D; ++jx) s = mass_fma(b[tx * D + jx], u[jz * MM + ty * M + jx], s);
+                v[jz * MM + ty * M + tx] = s;
+            }
+        __syncthreads();
+        // y: T2[jz][qy][qx] = sum_jy B1[qy][jy] T1[jz][jy][qx] -> u   (qx = tx, qy = ty)
+        if (active && tx < Q && ty < Q)
+#pragma unroll
+            for (Int jz = 0; jz < D; ++jz) {
+                T s = T(0);
+#pragma unroll
+                for (Int jy = 0; jy < D; ++jy) s = mass_fma(b[ty * D + jy], v[jz * MM + jy * M + tx], s);
+                u[jz * MM + ty * M + tx] = s;
+            }
+        __syncthreads();
+        // z, scaling, z back, on thread (qx, qy)'s own line:
+        // T3[qz] = op[qz][qy][qx] sum_jz B1[qz][jz] T2[jz]; T4[jz] = sum_qz B1[qz][jz] T3[qz] -> v
+        if (active && tx < Q && ty < Q) {
+            for (Int jz = 0; jz < D; ++jz) v[jz * MM + ty * M + tx] = T(0);
+#pragma unroll
+            for (Int qz = 0; qz < Q; ++qz) {
+                T s = T(0);
+#pragma unroll
+                for (Int jz = 0; jz < D; ++jz) s = mass_fma(b[qz * D + jz], u[jz * MM + ty * M + tx], s);
+                s = op[(qz * Q + ty) * Q + tx] * s;
+#pragma unroll
+                for (Int jz = 0; jz < D; ++jz)
+                    v[jz * MM + ty * M + tx] = mass_fma(b[qz * D + jz], s, v[jz * MM + ty * M + tx]);
+            }
+        }
+        __syncthreads();
+        // y back: T5[jz][jy][qx] = sum_qy B1[qy][jy] T4[jz][qy][qx] -> u   (qx = tx, jy = ty)
+        if (active && tx < Q && ty < D)
+#pragma unroll
+            for (Int jz = 0; jz < D; ++jz) {
+                T s = T(0);
+#pragma unroll
+                for (Int qy = 0; qy < Q; ++qy) s = mass_fma(b[qy * D + ty], v[jz * MM + qy * M + tx], s);
+                u[jz * MM + ty * M + tx] = s;
+            }
+        __syncthreads();
+        // x back: Y[jz][jy][jx] = sum_qx B1[qx][jx] T5[jz][jy][qx]   (jx = tx, jy = ty)
+        if (active && tx < D && ty < D)
+#pragma unroll
+            for (Int jz = 0; jz < D; ++jz) {
+                T s = T(0);
+#pragma unroll
+                for (Int qx = 0; qx < Q; ++qx) s = mass_fma(b[qx * D + tx], u[jz * MM + ty * M + qx], s);
+                y[(jz * D + ty) * D + tx] = s;
+            }
+    }
+}
+
+// Specialized: DIM, D, Q and the elements per block are template arguments.
+// Block: EPB * M * M threads; thread t works on element t / (M M) of the
+// block, at (tx, ty) = ((t % M M) % M, (t % M M) / M).
+template <class T, int DIM, int D, int Q, int EPB>
+__global__ void __launch_bounds__(cjg::mass_threads(D, Q, EPB))
+mass_apply(const T* __restrict__ B1, const T* __restrict__ op, const T* __restrict__ x, T* __restrict__ y,
+           long long ne) {
+    constexpr int M = D > Q ? D : Q;
+    constexpr int ND = DIM == 2 ? D * D : D * D * D, NQ = DIM == 2 ? Q * Q : Q * Q * Q;
+    constexpr int MD = DIM == 2 ? M * M : M * M * M;
+    extern __shared__ __align__(16) unsigned char cj_smem[];
+    T* b = reinterpret_cast<T*>(cj_smem);
+    T* bufs = b + cjg::mass_b_elems(D, Q);
+    const int t = threadIdx.x, le = t / (M * M), r = t - le * M * M;
+    for (int i = t; i < Q * D; i += cjg::mass_threads(D, Q, EPB)) b[i] = B1[i];
+    const long long e = (long long)blockIdx.x * EPB + le;
+    // threads past EPB elements (the block is rounded up to whole warps) only take the barriers
+    const bool active = le < EPB && e < ne;
+    const long long ec = active ? e : 0;
+    const int lb = le < EPB ? le : 0;
+    mass_element<T, int>(x + ec * ND, op + ec * NQ, y + ec * ND, b, bufs + (2 * lb) * MD, bufs + (2 * lb + 1) * MD,
+                         DIM, D, Q, M, r % M, r / M, active);
+}
+
+// Generic: run-time dimension, D, Q and elements per block (the same stages
+// with run-time loop bounds).
+template <class T>
+__global__ void __launch_bounds__(1024)
+mass_apply_generic(const T* __restrict__ B1, const T* __restrict__ op, const T* __restrict__ x, T* __restrict__ y,
+                   long long ne, int dim, int D, int Q, int epb) {
+    const int M = D > Q ? D : Q;
+    const int ND = dim == 2 ? D * D : D * D * D, NQ = dim == 2 ? Q * Q : Q * Q * Q;
+    const int MD = dim == 2 ? M * M : M * M * M;
+    extern __shared__ __align__(16) unsigned char cj_smem[];
+    T* b = reinterpret_cast<T*>(cj_smem);
+    T* bufs = b + cjg::mass_b_elems(D, Q);
+    const int t = threadIdx.x, le = t / (M * M), r = t - le * M * M;
+    for (int i = t; i < Q * D; i += blockDim.x) b[i] = B1[i];
+    const long long e = (long long)blockIdx.x * epb + le;
+    const bool active = le < epb && e < ne;
+    const long long ec = active ? e : 0;
+    const int lb = le < epb ? le : 0;
+    mass_element<T, int>(x + ec * ND, op + ec * NQ, y + ec * ND, b, bufs + (2 * lb) * MD, bufs + (2 * lb + 1) * MD,
+                         dim, D, Q, M, r % M, r / M, active);
+}
+
+}  // namespace cj
+#endif

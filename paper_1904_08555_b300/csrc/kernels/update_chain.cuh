@@ -401,13 +401,18 @@ __device__ __forceinline__ void chain_block(T* sA, int ninst, int tid, StepsOf s
             }
             __syncthreads();   // every read of X_k is done
             if (run) {
+                // column 4cb + j of X^T, rows 4rb..4rb+3: one 16-byte read and
+                // write each (a warp's four-row runs are contiguous)
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        T* xp = xt + (4 * cb + j) * XTP + 4 * rb + i;
-                        *xp = fmaT(cc, acc[i][j], *xp);
-                    }
+                for (int j = 0; j < 4; ++j) {
+                    float4* xp = reinterpret_cast<float4*>(xt + (4 * cb + j) * XTP + 4 * rb);
+                    float4 v = *xp;
+                    v.x = fmaT(cc, acc[0][j], v.x);
+                    v.y = fmaT(cc, acc[1][j], v.y);
+                    v.z = fmaT(cc, acc[2][j], v.z);
+                    v.w = fmaT(cc, acc[3][j], v.w);
+                    *xp = v;
+                }
             }
             __syncthreads();   // X_{k+1} complete
         }
@@ -528,19 +533,23 @@ __device__ __forceinline__ void chain_block(T* sA, int ninst, int tid, StepsOf s
 // ---------------------------------------------------------------------------
 // Specialized kernel.  MAP 1: one thread per row of X, A in shared memory.
 // MAP 2: one thread per instance, X and A in registers (small N).
+// A block is shaped for IPB instances; it takes ipb (1 <= ipb <= IPB) of
+// them, so that a batch too small to fill the SMs with whole blocks can be
+// spread over more blocks (the host picks ipb per launch).
 // ---------------------------------------------------------------------------
 template <class T, int N, int LAYOUT, int MAP, int IPB>
 __global__ void __launch_bounds__(cjg::chain_threads(N, MAP, IPB))
-update_chain(const T* __restrict__ A, T* __restrict__ X, long long batch, int steps, double c) {
+update_chain(const T* __restrict__ A, T* __restrict__ X, long long batch, int steps, double c, int ipb) {
     constexpr int NN = N * N;
     constexpr int NT = cjg::chain_threads(N, MAP, IPB);
     constexpr int P = cjg::chain_pitch(N, MAP, (int)sizeof(T));
     constexpr int AR = cjg::chain_arow(N, MAP, (int)sizeof(T));
     extern __shared__ __align__(16) unsigned char cj_smem[];
     T* sA = reinterpret_cast<T*>(cj_smem);
-    const long long b0 = (long long)blockIdx.x * IPB;
+    ipb = ipb < 1 ? 1 : ipb > IPB ? IPB : ipb;
+    const long long b0 = (long long)blockIdx.x * ipb;
     if (b0 >= batch) return;
-    const int ninst = (batch - b0) < IPB ? (int)(batch - b0) : IPB;
+    const int ninst = (batch - b0) < ipb ? (int)(batch - b0) : ipb;
     const T cc = (T)c;
     const int tid = threadIdx.x;
     chain_stage_in<T, LAYOUT>(sA, A + b0 * NN, ninst, N, AR, P, tid, NT);
@@ -819,21 +828,53 @@ eigen_recurrence_generic(const T* __restrict__ M0, T* __restrict__ M, long long 
 }
 
 // ---------------------------------------------------------------------------
+// One chunk of a grouped work list: `ninst` (<= IPB) consecutive items, each
+// {element offset of A and X in the pools, T, reserved} as int64, staged in,
+// run, staged out by a block of `nt` threads (nt >= the mapping's thread
+// count; threads past it take every barrier but no work).  c = 1/(N T) is
+// formed per instance in double, as the host would.  Row-major only.
+// Returns after a final barrier, so the caller may reuse shared memory.
+// ---------------------------------------------------------------------------
+template <class T, int N, int MAP, int IPB>
+__device__ __forceinline__ void grouped_chunk(const long long* __restrict__ items, int ninst,
+                                              const T* __restrict__ A_pool, T* __restrict__ X_pool, T* sA,
+                                              long long* s_off, int* s_steps, int tid, int nt) {
+    constexpr int NN = N * N;
+    constexpr int P = cjg::chain_pitch(N, MAP, (int)sizeof(T));
+    constexpr int AR = cjg::chain_arow(N, MAP, (int)sizeof(T));
+    for (int q = tid; q < ninst; q += nt) {
+        s_off[q] = items[3 * q];
+        s_steps[q] = (int)items[3 * q + 1];
+    }
+    __syncthreads();
+    for (int e = tid; e < ninst * NN; e += nt) {
+        const int inst = e / NN, r = e - inst * NN;
+        const int row = r / N, col = r - row * N;
+        sA[inst * P + row * AR + col] = A_pool[s_off[inst] + r];
+    }
+    __syncthreads();
+    chain_block<T, N, 0, MAP, IPB>(
+        sA, ninst, tid, [&](int q) { return s_steps[q]; },
+        [&](int q) { return (T)(1.0 / ((double)N * (double)s_steps[q])); });
+    __syncthreads();
+    for (int e = tid; e < ninst * NN; e += nt) {
+        const int inst = e / NN;
+        X_pool[s_off[inst] + (e - inst * NN)] = sA[inst * P + (e - inst * NN)];
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
 // Grouped persistent kernel: instances of one size N with different step
 // counts, listed in a work list (sorted by T descending by the host).  Each
 // block repeatedly takes the next chunk of IPB consecutive items from a
-// device counter (atomicAdd) until the list is exhausted.  Row-major only.
-// Item: {element offset of A and X in the pools, T, reserved} as int64.
-// c = 1/(N T) is formed per instance in double, as the host would.
+// device counter (atomicAdd) until the list is exhausted.
 // ---------------------------------------------------------------------------
 template <class T, int N, int MAP, int IPB>
 __global__ void __launch_bounds__(cjg::chain_threads(N, MAP, IPB))
 update_chain_grouped(const long long* __restrict__ items, const T* __restrict__ A_pool,
                      T* __restrict__ X_pool, int* __restrict__ counter, long long n_items) {
-    constexpr int NN = N * N;
     constexpr int NT = cjg::chain_threads(N, MAP, IPB);
-    constexpr int P = cjg::chain_pitch(N, MAP, (int)sizeof(T));
-    constexpr int AR = cjg::chain_arow(N, MAP, (int)sizeof(T));
     extern __shared__ __align__(16) unsigned char cj_smem[];
     T* sA = reinterpret_cast<T*>(cj_smem);
     __shared__ long long s_off[IPB];
@@ -848,26 +889,48 @@ update_chain_grouped(const long long* __restrict__ items, const T* __restrict__ 
         if (chunk >= n_chunks) break;
         const long long it0 = chunk * IPB;
         const int ninst = (n_items - it0) < IPB ? (int)(n_items - it0) : IPB;
-        for (int q = tid; q < ninst; q += NT) {
-            s_off[q] = items[3 * (it0 + q)];
-            s_steps[q] = (int)items[3 * (it0 + q) + 1];
-        }
+        grouped_chunk<T, N, MAP, IPB>(items + 3 * it0, ninst, A_pool, X_pool, sA, s_off, s_steps, tid, NT);
+    }
+}
+
+// A group's chunk body as a separate function, for the plan dispatcher: each
+// body keeps its own register allocation (inlined into one switch, the bodies'
+// live ranges would be allocated together and spill).
+template <class T, int N, int MAP, int IPB, int NT>
+__device__ __noinline__ void grouped_chunk_call(const long long* __restrict__ items, int ninst,
+                                                const T* __restrict__ A_pool, T* __restrict__ X_pool, T* sA,
+                                                long long* s_off, int* s_steps) {
+    grouped_chunk<T, N, MAP, IPB>(items, ninst, A_pool, X_pool, sA, s_off, s_steps, threadIdx.x, NT);
+}
+
+// ---------------------------------------------------------------------------
+// Plan dispatcher: one persistent launch for a whole uneven batch.  The host
+// generates, per plan, a kernel whose body is a switch over the plan's groups
+// (one grouped_chunk instantiation per group, all for the same block size)
+// and a ticket list: each ticket is one chunk of one group, {first item,
+// (group << 16) | item count}, ordered by cost T N^3 descending, so the
+// longest chunks start first and the short ones fill the tail.  Blocks take
+// tickets from one counter until the list is exhausted.  `body(group, items,
+// ninst, sA, s_off, s_steps)` runs one chunk; it must take the same barriers
+// on every thread of the block.
+// ---------------------------------------------------------------------------
+template <class T, class Body>
+__device__ __forceinline__ void dispatch_tickets(const long long* __restrict__ tickets, int n_tickets,
+                                                 const long long* __restrict__ items, int* __restrict__ counter,
+                                                 Body body) {
+    extern __shared__ __align__(16) unsigned char cj_smem[];
+    T* sA = reinterpret_cast<T*>(cj_smem);
+    __shared__ long long s_off[256];
+    __shared__ int s_steps[256];
+    __shared__ int s_ticket;
+    for (;;) {
+        if (threadIdx.x == 0) s_ticket = atomicAdd(counter, 1);
         __syncthreads();
-        for (int e = tid; e < ninst * NN; e += NT) {
-            const int inst = e / NN, r = e - inst * NN;
-            const int row = r / N, col = r - row * N;
-            sA[inst * P + row * AR + col] = A_pool[s_off[inst] + r];
-        }
-        __syncthreads();
-        chain_block<T, N, 0, MAP, IPB>(
-            sA, ninst, tid, [&](int q) { return s_steps[q]; },
-            [&](int q) { return (T)(1.0 / ((double)N * (double)s_steps[q])); });
-        __syncthreads();
-        for (int e = tid; e < ninst * NN; e += NT) {
-            const int inst = e / NN;
-            X_pool[s_off[inst] + (e - inst * NN)] = sA[inst * P + (e - inst * NN)];
-        }
-        __syncthreads();
+        const int t = s_ticket;
+        if (t >= n_tickets) break;
+        const long long first = tickets[2 * t];
+        const int gc = (int)tickets[2 * t + 1];
+        body(gc >> 16, items + 3 * first, gc & 0xffff, sA, s_off, s_steps);
     }
 }
 

@@ -148,6 +148,11 @@ cj_template_args lt_swapped(int k, const cj_template_args &a) {
 // Features
 // ---------------------------------------------------------------------------
 double lg2(double v) { return std::log2(std::max(v, 1.0)); }
+// Axis (0 = d or m, 1 = g, 2 = z) at slot s (0 slowest .. 2 fastest) of storage order lay.
+int lt_axis(int lay, int s) {
+    static const int order[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    return order[((lay % 6) + 6) % 6][s];
+}
 
 void featurize(int k, const cj_template_args &a0, int64_t batch, int32_t steps, const int *tile, float *f) {
     std::memset(f, 0, sizeof(float) * CJ_FEATURES);
@@ -164,8 +169,14 @@ void featurize(int k, const cj_template_args &a0, int64_t batch, int32_t steps, 
         bytes = es * ((double)(a.d + a.m) * cols + a.m * a.d);
         f[6] = lg2(a.m) / 6;
         f[7] = lg2(a.d) / 7;
-        f[8 + (a.layout_a % 6)] = 1.f;
-        f[14 + (a.layout_b % 6)] = 1.f;
+        // storage orders by their physical shape rather than by name: which
+        // axis is fastest and which is in the middle, for `in` (x = d) and for
+        // `out` (x = m).  Orders that share a fastest axis share the features
+        // that decide coalescing, so unseen pairs of orders relate to seen ones.
+        f[8 + lt_axis(a.layout_a, 2)] = 1.f;
+        f[11 + lt_axis(a.layout_a, 1)] = 1.f;
+        f[14 + lt_axis(a.layout_b, 2)] = 1.f;
+        f[17 + lt_axis(a.layout_b, 1)] = 1.f;
         const int mode = (tile[3] >> 16) & 0xf, r = (tile[3] >> 8) & 0xff, s = tile[3] & 0xff;
         // f[2] and f[5] (grouped kernel, bf16) are always 0 for LTimes; here they
         // flag the tcgen05 tiles (modes 4 and 5) and the TMA-fed one (mode 5)
@@ -193,21 +204,46 @@ void featurize(int k, const cj_template_args &a0, int64_t batch, int32_t steps, 
         f[22] = map == 4 || map == 5;   // register/tensor blocked panels
         f[19] = map == 5 ? 1.f : map == 6 ? 0.5f : 0.f;
         f[23] = lg2(tile[1]) / 8;
-        f[24] = lg2(cjg::chain_threads(a.n, map, tile[1])) / 10;
+        const int threads = cjg::chain_threads(a.n, map, tile[1]);
+        f[24] = lg2(threads) / 10;
         f[25] = a.n % 8 == 0;
         f[26] = steps / 128.f;
+        // structural consequences of (n, tile) the kernels' code makes:
+        // A held in registers, rows of X in shared memory, work wasted on
+        // zero padding, resident blocks per SM and waves over the batch
+        const bool a_regs = es == 8 ? a.n * a.n <= 64 : a.n * a.n <= 100;
+        f[10] = (map == 1 || map == 6) && a_regs;
+        f[11] = (map == 1 && a.n > cjg::chain_reg_rows_max(es)) || (map == 6 && a.n > 32);
+        const double np = map == 5 ? (a.n + 3) / 4 * 4 : map == 3 ? (a.n + 15) / 16 * 16 : map == 4 ? a.n : a.n;
+        f[12] = (float)(np * np * np / ((double)a.n * a.n * a.n) - 1.0);
+        const long smem = k == CJ_K_EIGEN_RECURRENCE ? cjg::eig_smem(a.n, tile[1], es, tile[0])
+                                                       : cjg::chain_smem(a.n, map, tile[1], es);
+        const double per_sm = std::max(1.0, std::min(2048.0 / threads, 228.0 * 1024 / std::max(smem, 1L)));
+        f[13] = (float)(std::min(per_sm, 32.0) / 32.0);
+        f[14] = lg2((double)smem) / 18;
+        const double blocks = std::ceil((double)batch / tile[1]);
+        f[15] = (float)(lg2(blocks / (148.0 * std::floor(per_sm))) / 10);
     }
     f[27] = lg2((double)batch) / 27;
     f[28] = lg2(flops) / 45;
     f[29] = lg2(bytes) / 35;
     f[30] = (float)(std::log2(std::max(flops, 1.0) / std::max(bytes, 1.0)) / 10);
-    f[31] = 1.f;
+    // whether this is the tile the library's default rule picks for the
+    // request: the network learns the rule's corrections rather than the
+    // rule itself (a constant input here would only repeat the biases)
+    int def[4];
+    cjint::default_tile_of(k, a0, def);
+    f[31] = std::equal(def, def + 4, tile) ? 1.f : 0.f;
 }
 
 cj_status candidates(int k, const cj_template_args &a, std::vector<std::array<int, 4>> &out) {
     out.clear();
     if (k == CJ_K_LTIMES || k == CJ_K_LPLUSTIMES) ltimes_candidates(lt_swapped(k, a), out);
-    else if (k == CJ_K_EIGEN_RECURRENCE) {
+    else if (k == CJ_K_MASS) {
+        for (int epb : {1, 2, 4, 8, 16, 32, 64})
+            if (cjg::mass_threads(a.n, a.m, epb) <= 1024 && cjg::mass_smem(a.d, a.n, a.m, epb, esize(a.dtype)) <= 200 * 1024)
+                out.push_back({epb, 0, 0, 0});
+    } else if (k == CJ_K_EIGEN_RECURRENCE) {
         for (int map : {1, 2}) {
             if (map == 2 && a.dtype != CJ_F32) continue;
             for (int ipb : {1, 2, 4, 8, 16, 32, 64})
@@ -243,7 +279,7 @@ struct cj_mlp_s {
 namespace {
 
 std::mutex g_model_mu;
-cj_mlp g_model = nullptr;   // used by cj_specialize for tile = 0 when use_cost_model
+std::vector<cj_mlp> g_models;   // the installed ensemble (cj_specialize with tile = 0, cj_choose_tile)
 
 uint64_t splitmix(uint64_t seed, uint64_t i) {
     uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
@@ -299,32 +335,45 @@ cj_status forward(cj_mlp m, const float *X, int64_t B, float *y, cudaStream_t st
 }
 
 // Predicted log run time of every candidate; returns the argmin.
-cj_status model_choose(cj_mlp m, int k, const cj_template_args &a, int64_t batch, int32_t steps, int *tile_out,
-                       float *pred_out) {
-    if (m->F != CJ_FEATURES) return tfail(CJ_ERR_INVALID_ARG, "cost model must have CJ_FEATURES inputs");
+// Choose a tile for a request: the networks' mean predicted log time over the
+// candidates, lowest first, except that the default rule's tile is kept
+// unless another candidate is predicted faster by more than kKeepDefault.
+cj_status model_choose(const std::vector<cj_mlp> &models, int k, const cj_template_args &a, int64_t batch,
+                       int32_t steps, int *tile_out, float *pred_out) {
     std::vector<std::array<int, 4>> cand;
     cj_status rc = candidates(k, a, cand);
     if (rc != CJ_OK) return rc;
-    std::vector<float> feat(cand.size() * CJ_FEATURES), pred(cand.size());
-    for (size_t i = 0; i < cand.size(); ++i) featurize(k, a, batch, steps, cand[i].data(), &feat[i * CJ_FEATURES]);
-    std::lock_guard<std::mutex> lk(m->mu);
-    if (!m->feat) {
-        if (cudaMalloc(&m->feat, sizeof(float) * 256 * CJ_FEATURES) != cudaSuccess ||
-            cudaMalloc(&m->pred, sizeof(float) * 256) != cudaSuccess)
-            return tfail(CJ_ERR_OOM, "cost model: query buffers");
-    }
     if (cand.size() > 256) return tfail(CJ_ERR_INVALID_ARG, "too many candidates");
-    cudaStream_t st;
-    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
-        return tfail(CJ_ERR_CUDA, "cost model: stream");
-    cudaMemcpyAsync(m->feat, feat.data(), sizeof(float) * feat.size(), cudaMemcpyHostToDevice, st);
-    rc = forward(m, m->feat, (int64_t)cand.size(), m->pred, st);
-    if (rc == CJ_OK) cudaMemcpyAsync(pred.data(), m->pred, sizeof(float) * pred.size(), cudaMemcpyDeviceToHost, st);
-    cudaError_t e = cudaStreamSynchronize(st);
-    cudaStreamDestroy(st);
-    if (rc != CJ_OK) return rc;
-    if (e != cudaSuccess) return tfail(CJ_ERR_CUDA, "cost model: query failed");
-    const size_t best = std::min_element(pred.begin(), pred.end()) - pred.begin();
+    std::vector<float> feat(cand.size() * CJ_FEATURES), pred(cand.size(), 0.f), one(cand.size());
+    for (size_t i = 0; i < cand.size(); ++i) featurize(k, a, batch, steps, cand[i].data(), &feat[i * CJ_FEATURES]);
+    for (cj_mlp m : models) {
+        if (m->F != CJ_FEATURES) return tfail(CJ_ERR_INVALID_ARG, "cost model must have CJ_FEATURES inputs");
+        std::lock_guard<std::mutex> lk(m->mu);
+        if (!m->feat) {
+            if (cudaMalloc(&m->feat, sizeof(float) * 256 * CJ_FEATURES) != cudaSuccess ||
+                cudaMalloc(&m->pred, sizeof(float) * 256) != cudaSuccess)
+                return tfail(CJ_ERR_OOM, "cost model: query buffers");
+        }
+        cudaStream_t st;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+            return tfail(CJ_ERR_CUDA, "cost model: stream");
+        cudaMemcpyAsync(m->feat, feat.data(), sizeof(float) * feat.size(), cudaMemcpyHostToDevice, st);
+        rc = forward(m, m->feat, (int64_t)cand.size(), m->pred, st);
+        if (rc == CJ_OK) cudaMemcpyAsync(one.data(), m->pred, sizeof(float) * one.size(), cudaMemcpyDeviceToHost, st);
+        cudaError_t e = cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+        if (rc != CJ_OK) return rc;
+        if (e != cudaSuccess) return tfail(CJ_ERR_CUDA, "cost model: query failed");
+        for (size_t i = 0; i < pred.size(); ++i) pred[i] += one[i] / (float)models.size();
+    }
+    size_t best = std::min_element(pred.begin(), pred.end()) - pred.begin();
+    // A gain the networks cannot tell from timing noise and the spread of
+    // sizes they were not trained on is not worth leaving the rule for.
+    std::array<int, 4> def{};
+    cjint::default_tile_of(k, a, def.data());
+    const size_t di = std::find(cand.begin(), cand.end(), def) - cand.begin();
+    constexpr float kKeepDefault = 0.0953102f;   // log(1.10): predicted 10% faster
+    if (di < cand.size() && pred[di] - pred[best] <= kKeepDefault) best = di;
     std::memcpy(tile_out, cand[best].data(), sizeof(int) * 4);
     if (pred_out) *pred_out = pred[best];
     return CJ_OK;
@@ -338,9 +387,9 @@ namespace cjint {
 // instances with T = 64, LTimes 2^21 columns.
 bool cost_model_tile(int k, const cj_template_args &a, int *tile_out) {
     std::lock_guard<std::mutex> lk(g_model_mu);
-    if (!g_model) return false;
+    if (g_models.empty()) return false;
     const int64_t batch = k == CJ_K_LTIMES ? (int64_t)1 << 21 : std::max<int64_t>(1, ((int64_t)1 << 22) / (a.n * a.n));
-    return model_choose(g_model, k, a, batch, 64, tile_out, nullptr) == CJ_OK;
+    return model_choose(g_models, k, a, batch, 64, tile_out, nullptr) == CJ_OK;
 }
 }  // namespace cjint
 
@@ -364,6 +413,7 @@ CJ_API cj_status cj_candidates(cj_kernel_id k, const cj_template_args *a, int32_
 CJ_API cj_status cj_featurize(cj_kernel_id k, const cj_template_args *a, int64_t batch, int32_t steps,
                               const int32_t tile[4], float *out) {
     if (!a || !tile || !out || batch < 0) return tfail(CJ_ERR_INVALID_ARG, "null argument");
+    if (k == CJ_K_MASS) return tfail(CJ_ERR_INVALID_ARG, "the cost model has no features for the mass operator");
     featurize((int)k, *a, batch, steps, tile, out);
     return CJ_OK;
 }
@@ -493,7 +543,7 @@ CJ_API cj_status cj_mlp_destroy(cj_mlp m) {
     if (!m) return tfail(CJ_ERR_INVALID_ARG, "null model");
     {
         std::lock_guard<std::mutex> lk(g_model_mu);
-        if (g_model == m) g_model = nullptr;
+        if (std::find(g_models.begin(), g_models.end(), m) != g_models.end()) g_models.clear();
     }
     for (float *p : {m->theta, m->m, m->v, m->grad, m->loss, m->partial, m->partial_loss, m->feat, m->pred})
         if (p) cudaFree(p);
@@ -501,17 +551,21 @@ CJ_API cj_status cj_mlp_destroy(cj_mlp m) {
     return CJ_OK;
 }
 
-CJ_API cj_status cj_cost_model_use(cj_mlp m) {
-    if (m && m->F != CJ_FEATURES) return tfail(CJ_ERR_INVALID_ARG, "cost model must have CJ_FEATURES inputs");
+CJ_API cj_status cj_cost_model_use_ensemble(const cj_mlp *m, int32_t count) {
+    if (count < 0 || (count > 0 && !m)) return tfail(CJ_ERR_INVALID_ARG, "null models or negative count");
+    for (int32_t i = 0; i < count; ++i)
+        if (!m[i] || m[i]->F != CJ_FEATURES) return tfail(CJ_ERR_INVALID_ARG, "cost model must have CJ_FEATURES inputs");
     std::lock_guard<std::mutex> lk(g_model_mu);
-    g_model = m;
+    g_models.assign(m, m + count);
     return CJ_OK;
 }
+
+CJ_API cj_status cj_cost_model_use(cj_mlp m) { return cj_cost_model_use_ensemble(m ? &m : nullptr, m ? 1 : 0); }
 
 CJ_API cj_status cj_choose_tile(cj_kernel_id k, const cj_template_args *a, int64_t batch, int32_t steps,
                                 int32_t tile_out[4], float *predicted) {
     if (!a || !tile_out || batch < 1) return tfail(CJ_ERR_INVALID_ARG, "null argument");
     std::lock_guard<std::mutex> lk(g_model_mu);
-    if (!g_model) return tfail(CJ_ERR_INVALID_ARG, "no cost model installed (cj_cost_model_use)");
-    return model_choose(g_model, (int)k, *a, batch, steps, tile_out, predicted);
+    if (g_models.empty()) return tfail(CJ_ERR_INVALID_ARG, "no cost model installed (cj_cost_model_use)");
+    return model_choose(g_models, (int)k, *a, batch, steps, tile_out, predicted);
 }

@@ -32,6 +32,7 @@ SEED_CHAIN_SWEEP = 0xC1A2
 SEED_LTIMES = 0xC1A3
 SEED_UNEVEN = 0xC1A4
 SEED_REQUESTS = 0xC1A5
+SEED_MASS = 0xC1A6
 
 # Sub-stream offsets so that different quantities drawn from one workload seed
 # never share indices.
@@ -191,3 +192,35 @@ def ltimes_inputs_np(seed: int, m: int, d: int, g: int, z: int):
     L = uniform_np(seed, STREAM_L, m * d).reshape(m, d)
     x = uniform_np(seed, STREAM_A, d * g * z).reshape(d, g, z)
     return L, x
+
+
+def mass_basis(D: int, Q: int) -> np.ndarray:
+    """B1[q][d]: the Lagrange polynomials on D equally spaced nodes of [-1, 1]
+    evaluated at the Q Gauss-Legendre points (a finite element's 1-D basis at
+    its quadrature points; D = 1 is the constant)."""
+    xq, _ = np.polynomial.legendre.leggauss(Q)
+    nodes = np.linspace(-1.0, 1.0, D) if D > 1 else np.zeros(1)
+    B = np.ones((Q, D))
+    for d in range(D):
+        for m in range(D):
+            if m != d:
+                B[:, d] *= (xq - nodes[m]) / (nodes[d] - nodes[m])
+    return B
+
+
+def mass_inputs_np(seed: int, dim: int, D: int, Q: int, ne: int):
+    """(B1, op, x) of the mass operator over ne elements: op (quadrature data,
+    density x |J| x weight) uniform in [0.5, 1.5), x uniform in [-1, 1), both
+    [ne][...] with the first index fastest; canonical element-major indices."""
+    B1 = mass_basis(D, Q)
+    op = 1.0 + 0.5 * uniform_np(seed, STREAM_L, ne * Q ** dim).reshape(ne, Q ** dim)
+    x = uniform_np(seed, STREAM_A, ne * D ** dim).reshape(ne, D ** dim)
+    return B1, op, x
+
+
+def mass_inputs_torch(seed: int, dim: int, D: int, Q: int, ne: int, device):
+    """The same values as mass_inputs_np, drawn on the device."""
+    B1 = mass_basis(D, Q)
+    op = 1.0 + 0.5 * uniform_torch(seed, STREAM_L, ne * Q ** dim, device).view(ne, Q ** dim)
+    x = uniform_torch(seed, STREAM_A, ne * D ** dim, device).view(ne, D ** dim)
+    return B1, op, x

@@ -295,9 +295,14 @@ def test_every_candidate_tile_is_a_valid_request(compile_only_sync, req):
     for tile in cands[:3]:
         h = cj.specialize(k, tile=tile, **req)      # compiles in compile-only mode
         assert h.variant in ("jit", "aot")         # the default tile may be an AoT kernel
+    default = cj.specialize(k, **req)             # tile 0: the library's default rule
+    dkey = bytes.fromhex(default.key_hex)
+    dtile = tuple(int.from_bytes(dkey[12 + 4 * i:16 + 4 * i], "little") for i in range(4))
+    assert dtile in cands                          # the default rule's tile is always searched
     for tile in cands:
         f = cj.featurize(k, batch=1 << 16, steps=64, tile=tile, **req)
-        assert f.shape == (cj.FEATURES,) and np.all(np.isfinite(f)) and f[31] == 1.0
+        assert f.shape == (cj.FEATURES,) and np.all(np.isfinite(f))
+        assert f[31] == (1.0 if tuple(tile) == dtile else 0.0)   # flags the default rule's tile
 
 
 def test_eigen_tile_features_follow_the_thread_mapping(compile_only_sync):

@@ -14,23 +14,44 @@ def test_heldout_stream_is_seeded_and_in_range():
     chains = [r for r in a if r.kernel == cj.K_UPDATE_CHAIN]
     lt = [r for r in a if r.kernel == cj.K_LTIMES]
     assert len(chains) + len(lt) == 2000
-    # 50/50 kernels and dtypes: binomial(2000, 1/2) has sd 22.4; 5 sd either side
+    # 50/50 kernels: binomial(2000, 1/2) has sd 22.4; 5 sd either side
     assert abs(len(chains) - 1000) < 112
-    assert abs(sum(r[1] == cj.F64 for r in a) - 1000) < 112
-    assert {r[1] for r in a} == {cj.F64, cj.F32}
-    assert min(r[2] for r in chains) == 2 and max(r[2] for r in chains) == 64
+    assert abs(sum(r[1] == cj.F64 for r in lt) - len(lt) / 2) < 5 * (len(lt) / 4) ** 0.5
+    assert {r[1] for r in chains} == {cj.F64, cj.F32, cj.BF16} and {r[1] for r in lt} == {cj.F64, cj.F32}
+    assert all(r[2] >= 16 for r in chains if r[1] == cj.BF16)
+    assert {r[2] for r in chains} == set(costmodel.HELDOUT_CHAIN_N)
+    assert min(r[2] for r in chains) == 2 and max(r[2] for r in chains) == 63
     assert {r[3] for r in chains} == {0, 1} and all(r[4] == 0 for r in chains)
-    assert {r[3] for r in lt} == set(range(6)) and {r[4] for r in lt} == set(range(6))
+    assert {(r[3], r[4]) for r in lt} == set(costmodel.HELDOUT_LT_PAIRS)
     assert all(r[2] == 0 for r in lt)
 
 
-def test_training_requests_cover_every_order_pair_and_size():
+def test_heldout_requests_are_unseen():
+    """No held-out request is a training request: the chain sizes and the
+    LTimes order pairs of the two sets are disjoint, while every storage
+    order of `in` and of `out` occurs in both."""
+    train = set(costmodel.training_requests())
+    held = set(costmodel.heldout_requests(2000))
+    assert not train & held
+    assert not set(costmodel.TRAIN_CHAIN_N) & set(costmodel.HELDOUT_CHAIN_N)
+    assert set(costmodel.TRAIN_CHAIN_N) | set(costmodel.HELDOUT_CHAIN_N) == set(range(2, 65))
+    assert not set(costmodel.TRAIN_LT_PAIRS) & set(costmodel.HELDOUT_LT_PAIRS)
+    fastest = {0: "z", 2: "z", 1: "g", 4: "g", 3: "x", 5: "x"}    # fastest axis of each storage order
+    for pairs in (costmodel.TRAIN_LT_PAIRS, costmodel.HELDOUT_LT_PAIRS):
+        assert len(pairs) == 18
+        assert {i for i, _ in pairs} == set(range(6)) and {o for _, o in pairs} == set(range(6))
+        assert {(fastest[i], fastest[o]) for i, o in pairs} == {(a, b) for a in "zgx" for b in "zgx"}
+
+
+def test_training_requests_cover_every_dtype_size_and_order():
     t = costmodel.training_requests()
-    assert len(t) == 2 * (len(costmodel.TRAIN_CHAIN_N) * 2 + 36)
+    n_bf16 = sum(n >= 16 for n in costmodel.TRAIN_CHAIN_N)
+    assert len(t) == 2 * (len(costmodel.TRAIN_CHAIN_N) * 2 + 18) + 2 * n_bf16
     assert len(set(t)) == len(t)
     for dt in (cj.F64, cj.F32):
-        assert {(r[3], r[4]) for r in t if r.kernel == cj.K_LTIMES and r[1] == dt} == \
-            {(i, o) for i in range(6) for o in range(6)}
+        assert {(r[3], r[4]) for r in t if r.kernel == cj.K_LTIMES and r[1] == dt} == set(costmodel.TRAIN_LT_PAIRS)
+        assert {r[2] for r in t if r.kernel == cj.K_UPDATE_CHAIN and r[1] == dt} == set(costmodel.TRAIN_CHAIN_N)
+    assert {r[2] for r in t if r[1] == cj.BF16} == {n for n in costmodel.TRAIN_CHAIN_N if n >= 16}
 
 
 def test_request_marshalling():

@@ -8,7 +8,8 @@
   the other orders give the same values bit for bit.
 * The uneven batch at its full size, 10,000 instances (N log-uniform in
   [2, 64], T uniform in [16, 128]), through the grouped plan in FP64, FP32 and
-  BF16, every instance checked against the oracle.  BF16 runs N >= 16 on
+  BF16 -- its one-launch dispatcher and its per-group kernels, each as a graph
+  and directly -- every instance checked against the oracle.  BF16 runs N >= 16 on
   bf16 tensor-core operands with FP32 state and N < 16 in FP32.
 """
 import numpy as np
@@ -102,20 +103,22 @@ def test_uneven_batch_10000_every_instance(uneven_full, dt):
     plan = cj.GroupPlan(dt, n, t)
     try:
         A = torch.from_numpy(pool).to("cuda", tdt)
-        for use_graph in (True, False):
+        plan.wait()
+        assert plan.dispatcher()["state"] == "ready"
+        for use_graph, per_group in ((True, False), (False, False), (True, True), (False, True)):
             X = torch.full_like(A, float("nan"))
-            plan.launch(A, X, use_graph=use_graph)
+            plan.launch(A, X, use_graph=use_graph, per_group=per_group)
             torch.cuda.synchronize()
             got = X.double().cpu().numpy()
-            assert np.all(np.isfinite(got)), use_graph
+            assert np.all(np.isfinite(got)), (use_graph, per_group)
             err = per_instance_relF(got, ref, n, off)
             if dt == cj.F64:
-                assert err.max() <= TOL64, (use_graph, err.max())
+                assert err.max() <= TOL64, (use_graph, per_group, err.max())
             elif dt == cj.F32:
-                assert err.max() <= TOL32, (use_graph, err.max())
+                assert err.max() <= TOL32, (use_graph, per_group, err.max())
             else:
                 big = n >= 16
-                assert err[big].max() <= TOLBF16, (use_graph, err[big].max())
-                assert err[~big].max() <= TOL32, (use_graph, err[~big].max())
+                assert err[big].max() <= TOLBF16, (use_graph, per_group, err[big].max())
+                assert err[~big].max() <= TOL32, (use_graph, per_group, err[~big].max())
     finally:
         plan.destroy()

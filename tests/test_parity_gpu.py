@@ -474,6 +474,52 @@ def test_grouped_plan_uneven(dt, use_graph):
 
 
 @pytest.mark.parametrize("dt", [cj.F64, cj.F32, cj.BF16])
+def test_grouped_plan_dispatcher(dt):
+    """One persistent launch for the whole uneven batch: the plan's generated
+    dispatcher (every group's body in one kernel, cost-ordered tickets), as
+    a graph and as a direct launch, then the per-group form of the same plan;
+    all against the oracle per instance."""
+    n, t = synth.uneven_sizes(synth.SEED_UNEVEN + 1, 500)
+    n[:4] = (1, 2, 63, 64)             # the ends of the size range
+    pool, off = synth.uneven_inputs_np(synth.SEED_UNEVEN + 1, n)
+    A = torch.from_numpy(pool).to("cuda", tdtype(dt))
+    ref = oracle.update_chain_uneven(n, t, off, A.double().cpu().numpy(), nthreads=8)
+    tol = {cj.F64: TOL64, cj.F32: TOL32, cj.BF16: 2e-2}[dt]
+    plan = cj.GroupPlan(dt, n, t)
+    try:
+        plan.wait()
+        d = plan.dispatcher()
+        assert d["state"] == "ready" and d["threads"] == 256 and d["tickets"] >= plan.n_groups
+        for use_graph, per_group in ((True, False), (False, False), (True, True), (False, True)):
+            before = cj.stats()["launches_dispatch"]
+            X = torch.full_like(A, float("nan"))
+            plan.launch(A, X, use_graph=use_graph, per_group=per_group)
+            torch.cuda.synchronize()
+            if not use_graph:
+                assert cj.stats()["launches_dispatch"] - before == (0 if per_group else 1)
+            Xh = X.double().cpu().numpy()
+            assert np.all(np.isfinite(Xh)), (use_graph, per_group)
+            worst = max(relF(Xh[off[k]:off[k] + n[k] * n[k]], ref[off[k]:off[k] + n[k] * n[k]]) for k in range(len(n)))
+            lim = tol if dt != cj.BF16 else 2e-2
+            assert worst <= lim, (use_graph, per_group, worst)
+            if dt == cj.BF16:   # the n < 16 groups run in FP32
+                small = max(relF(Xh[off[k]:off[k] + n[k] * n[k]], ref[off[k]:off[k] + n[k] * n[k]])
+                            for k in range(len(n)) if n[k] < 16)
+                assert small <= TOL32, (use_graph, per_group, small)
+    finally:
+        plan.destroy()
+
+
+def test_generic_plan_has_no_dispatcher():
+    n, t = synth.uneven_sizes(synth.SEED_UNEVEN, 50)
+    plan = cj.GroupPlan(cj.F64, n, t, flags=cj.FLAG_GENERIC)
+    try:
+        assert plan.dispatcher()["state"] == "none"
+    finally:
+        plan.destroy()
+
+
+@pytest.mark.parametrize("dt", [cj.F64, cj.F32, cj.BF16])
 @pytest.mark.parametrize("use_graph", [True, False])
 def test_grouped_plan_autotune_keeps_results(dt, use_graph):
     """Plan autotuning: every group's candidates are timed on its own work
