@@ -55,10 +55,11 @@ PEAK_TFLOPS = {"f64": 1.25, "f32": 148 * 128 * 2 * 2.032e9 / 1e12}
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per instance of
 # the sweep's roofline kernel, from the ncu capture summarised in
-# profiles/update_chain_f64_n32_fma_pipe.md (16384 instances, scaled by the
-# instance count; the kernel's traffic grows in proportion).  None for any
-# other kernel: the counters then do not describe it.
-TRAFFIC_PER_INSTANCE = {"update_chain<double, 32, 0, 1, 8>": (135.625472e6 + 89.003520e6) / 16384}
+# profiles/update_chain_f64_n32_dram_traffic.md (65,536 instances, 1.07 GB of
+# A and X: the writes leave L2 except its last ~40 MB; scaled by the instance
+# count, the kernel's traffic grows in proportion).  None for any other
+# kernel: the counters then do not describe it.
+TRAFFIC_PER_INSTANCE = {"update_chain<double, 32, 0, 1, 8>": (550.644736e6 + 494.461952e6) / 65536}
 
 
 def measured_peak(key: str, default: float) -> float:
@@ -375,7 +376,8 @@ def cj_arm(args):
             "fp64_nominal_tflops": PEAK_TFLOPS["f64"],
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
                          "frac": achieved / peak64, "traffic": traffic,
-                         "traffic_unit": "bytes per launch (ncu, scaled from 16384 instances)",
+                         "traffic_unit": "bytes per launch (ncu dram read + write at 65,536 instances, scaled "
+                                         "to the launch's instances)",
                          "algorithmic_bytes": chain_bytes(batch[dom], dom, 8),
                          "kernel": dom_name,
                          "peak_source": "nominal B300 FP64 rate, 1.25 TFLOP/s (profiling recipe); the measured "
