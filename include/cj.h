@@ -136,7 +136,11 @@ typedef struct {
  *     n in {8, 16, 24, 32}), 5 = FP32 register blocks (one thread per 4x4
  *     block of X A, X transposed in shared memory; f32, n >= 8, n padded to
  *     a multiple of 4 with zeros), 6 = two rows of X per thread (rows h and
- *     h + ceil(n / 2); f32).
+ *     h + ceil(n / 2); f32), 7 = bf16 on the tcgen05 tensor cores (bf16,
+ *     16 <= n <= 64, one instance per block at a time: {7, 1}; accumulator in
+ *     tensor memory, fp32 state in registers; a persistent grid whose blocks
+ *     keep their tensor memory; bounded waits counted like the LTimes tensor-
+ *     core kernels', see cj_handle_wait_timeouts).
  *     Default: n <= 4 -> {2, 128}; f32 grouped with n >= 17 -> {5, 1};
  *     f32 with n >= 9 -> {6, max(1, 128 / ceil(n / 2))}; otherwise n <= 32 ->
  *     {1, max(1, 256 / n)};

@@ -25,7 +25,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 EMBEDDED = [("cj_emb_geometry_h", "geometry.h"),
             ("cj_emb_update_chain_cuh", "update_chain.cuh"),
             ("cj_emb_ltimes_cuh", "ltimes.cuh"),
-            ("cj_emb_mass_cuh", "mass.cuh")]
+            ("cj_emb_mass_cuh", "mass.cuh"),
+            ("cj_emb_chain_tc_cuh", "chain_tc.cuh")]
 
 
 def _sources():

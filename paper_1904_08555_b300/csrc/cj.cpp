@@ -407,13 +407,15 @@ cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_
     }
     if (!is_lt(k)) {
         const int map = a.tile[0], ipb = a.tile[1];
-        if (map < 1 || map > 6) return fail(CJ_ERR_INVALID_ARG, "update chain mapping %d must be 1..6", map);
+        if (map < 1 || map > 7) return fail(CJ_ERR_INVALID_ARG, "update chain mapping %d must be 1..7", map);
         if (map == 6 && a.dtype != CJ_F32)
             return fail(CJ_ERR_INVALID_ARG, "mapping 6 (two rows per thread) needs f32");
         if (map == 5 && (a.dtype != CJ_F32 || a.n < 8))
             return fail(CJ_ERR_INVALID_ARG, "mapping 5 (register blocks) needs f32 and n >= 8");
-        if ((map == 3) != (a.dtype == CJ_BF16))
-            return fail(CJ_ERR_INVALID_ARG, "mapping 3 (bf16 tensor cores) is the only mapping of dtype bf16");
+        if ((map == 3 || map == 7) != (a.dtype == CJ_BF16))
+            return fail(CJ_ERR_INVALID_ARG, "mappings 3 and 7 (bf16 tensor cores) are the mappings of dtype bf16");
+        if (map == 7 && (ipb != 1 || (a.flags & CJ_FLAG_INJECT_WAIT_TIMEOUT)))
+            return fail(CJ_ERR_INVALID_ARG, "mapping 7 (tcgen05) takes one instance per block");
         if (map == 2 && a.n > 8) return fail(CJ_ERR_INVALID_ARG, "mapping 2 needs n <= 8");
         if (map == 4 && !cjint::chain_dmma_ok(a.n, a.dtype))
             return fail(CJ_ERR_INVALID_ARG, "mapping 4 (FP64 tensor cores) needs f64 and n in {8, 16, 24, 32}");
@@ -567,7 +569,11 @@ std::string fallback_name_expression(const cj_handle_s *h) {
 std::string name_expression(const cj_handle_s *h) {
     const cj_template_args &a = h->a;
     char buf[256];
-    if (h->kernel == CJ_K_UPDATE_CHAIN)
+    if (h->kernel == CJ_K_UPDATE_CHAIN && a.tile[0] == 7)
+        snprintf(buf, sizeof buf, "cj::update_chain_tc<%d, %d>", a.n, a.layout_a);
+    else if (h->kernel == CJ_K_UPDATE_CHAIN_GROUPED && a.tile[0] == 7)
+        snprintf(buf, sizeof buf, "cj::update_chain_grouped_tc<%d>", a.n);
+    else if (h->kernel == CJ_K_UPDATE_CHAIN)
         snprintf(buf, sizeof buf, "cj::update_chain<%s, %d, %d, %d, %d>", ctype(a.dtype), a.n, a.layout_a,
                  a.tile[0], a.tile[1]);
     else if (is_mass(h->kernel))
@@ -615,10 +621,11 @@ struct CompileOut {
 
 CompileOut nvrtc_compile(const std::string &src, const char *name_expr, const char *name_expr2 = nullptr) {
     CompileOut out;
-    const char *hdr_src[4] = {cj_emb_geometry_h, cj_emb_update_chain_cuh, cj_emb_ltimes_cuh, cj_emb_mass_cuh};
-    const char *hdr_name[4] = {"geometry.h", "update_chain.cuh", "ltimes.cuh", "mass.cuh"};
+    const char *hdr_src[5] = {cj_emb_geometry_h, cj_emb_update_chain_cuh, cj_emb_ltimes_cuh, cj_emb_mass_cuh,
+                              cj_emb_chain_tc_cuh};
+    const char *hdr_name[5] = {"geometry.h", "update_chain.cuh", "ltimes.cuh", "mass.cuh", "chain_tc.cuh"};
     nvrtcProgram prog;
-    out.rc = nvrtcCreateProgram(&prog, src.c_str(), "cj_instantiation.cu", 4, hdr_src, hdr_name);
+    out.rc = nvrtcCreateProgram(&prog, src.c_str(), "cj_instantiation.cu", 5, hdr_src, hdr_name);
     if (out.rc != NVRTC_SUCCESS) return out;
     if (name_expr) nvrtcAddNameExpression(prog, name_expr);
     if (name_expr2) nvrtcAddNameExpression(prog, name_expr2);
@@ -669,6 +676,7 @@ cj_status compile_handle(cj_handle_s *h) {
     std::string src = !h->custom_src.empty() ? h->custom_src
                       : is_lt(h->kernel)      ? "#include \"ltimes.cuh\"\n"
                       : is_mass(h->kernel)    ? "#include \"mass.cuh\"\n"
+                      : h->a.tile[0] == 7     ? "#include \"chain_tc.cuh\"\n"
                                               : "#include \"update_chain.cuh\"\n";
     if (h->a.flags & CJ_FLAG_INJECT_COMPILE_ERROR)
         src += "namespace cj { __device__ int injected_failure = this_identifier_does_not_exist; }\n";
@@ -691,6 +699,10 @@ cj_status compile_handle(cj_handle_s *h) {
         if (r == CUDA_SUCCESS) r = drv.KernelGetFunction(&s.fn, kern);
         if (r == CUDA_SUCCESS && s.smem > 48 * 1024)
             r = drv.FuncSetAttribute(s.fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)s.smem);
+        // a plan dispatcher's residency is set by its registers: let shared
+        // memory take the whole carveout so that it never limits it further
+        if (r == CUDA_SUCCESS && h->kernel == kDispatchKernel)
+            r = drv.FuncSetAttribute(s.fn, CU_FUNC_ATTRIBUTE_PREFERRED_SHARED_MEMORY_CARVEOUT, 100);
         if (r == CUDA_SUCCESS && !c.lowered2.empty()) {
             CUkernel k2 = nullptr;
             r = drv.LibraryGetKernel(&k2, h->lib, c.lowered2.c_str());
@@ -707,6 +719,21 @@ cj_status compile_handle(cj_handle_s *h) {
             return CJ_ERR_COMPILE;
         }
         s.blocks_per_sm = occupancy(s.fn, s.threads, s.smem);
+        if (!is_lt(h->kernel) && !is_eig(h->kernel) && !is_mass(h->kernel) && h->kernel != kDispatchKernel &&
+            h->a.tile[0] == 7) {
+            // The occupancy query answers one block per SM for this kernel;
+            // count the resident blocks from its registers, shared memory and
+            // threads, capped so that their accumulator columns, held for the
+            // block's life, fit the SM's 512 (an overcount only makes the
+            // extra blocks wait for an SM)
+            int regs = 0, stat = 0;
+            drv.FuncGetAttribute(&regs, CU_FUNC_ATTRIBUTE_NUM_REGS, s.fn);
+            drv.FuncGetAttribute(&stat, CU_FUNC_ATTRIBUTE_SHARED_SIZE_BYTES, s.fn);
+            const int warps = (s.threads + 31) / 32;
+            const int by_regs = 65536 / std::max(1, warps * ((std::max(regs, 1) * 32 + 255) / 256 * 256));
+            const int by_smem = (G.smem_optin + 1024) / (int)(s.smem + stat + 1024);
+            s.blocks_per_sm = std::max(1, std::min({by_regs, by_smem, 64 / warps, 512 / (h->a.n <= 32 ? 32 : 64)}));
+        }
         CUdeviceptr wp = 0;
         size_t wbytes = 0;
         if (drv.LibraryGetGlobal(&wp, &wbytes, h->lib, "cj_wait_timeouts") == CUDA_SUCCESS && wbytes == sizeof(uint32_t))
@@ -876,12 +903,13 @@ cj_status plan_record(cj_group_plan_s *p, const void *A, void *X, cudaStream_t s
 // Generate, request (compile in the background, or inline in sync mode) and
 // ticket the plan's dispatcher.  `items` is the plan's work list on the host
 // ({offset, T, 0} per item, groups contiguous, each ordered by T descending).
-cj_status plan_dispatcher(cj_group_plan_s *p, const std::vector<long long> &items) {
-    constexpr int kBlock = 256;
+constexpr int kDispatchBlock = 256;
+
+// The dispatcher's source for `minb` resident blocks per SM (the launch
+// bounds' register cap), and its shared-memory need.
+std::string dispatcher_source(const cj_group_plan_s *p, int minb, long *smem_out) {
+    constexpr int kBlock = kDispatchBlock;
     const char *ct = p->dtype == CJ_F64 ? "double" : "float";
-    // blocks per SM the registers must allow (launch bounds): FP32 and BF16
-    // bodies fit 128 registers (two blocks of 256), FP64 rows of X need more
-    const int minb = p->dtype == CJ_F64 ? 1 : 2;
     std::string src = "#include \"update_chain.cuh\"\nnamespace cj {\n__global__ void __launch_bounds__(" +
                       std::to_string(kBlock) + ", " + std::to_string(minb) +
                       ")\nplan_dispatch(const long long* __restrict__ tickets, int n_tickets, "
@@ -891,6 +919,60 @@ cj_status plan_dispatcher(cj_group_plan_s *p, const std::vector<long long> &item
                       "        [&](int g, const long long* it, int ninst, " + ct + "* sA, long long* so, int* ss) {\n"
                       "        switch (g) {\n";
     long smem = 0;
+    for (size_t g = 0; g < p->groups.size(); ++g) {
+        const auto &gr = p->groups[g];
+        const int gdt = (p->dtype == CJ_BF16 && gr.n < 16) ? CJ_F32 : p->dtype;
+        const auto t = dispatch_tile(gdt, gr.n, kBlock);
+        smem = std::max(smem, cjg::chain_smem(gr.n, t[0], t[1], esize(gdt)));
+        src += "        case " + std::to_string(g) + ": grouped_chunk_call<" + ct + ", " + std::to_string(gr.n) +
+               ", " + std::to_string(t[0]) + ", " + std::to_string(t[1]) + ", " + std::to_string(kBlock) +
+               ">(it, ninst, A, X, sA, so, ss); break;\n";
+    }
+    src += "        default: break;\n        }\n    });\n}\n}  // namespace cj\n";
+    *smem_out = smem;
+    return src;
+}
+
+// Request (compile in the background) the dispatcher variant for `minb`;
+// identical plans share it.
+cj_handle_s *request_dispatcher(const cj_group_plan_s *p, int minb) {
+    long smem = 0;
+    const std::string src = dispatcher_source(p, minb, &smem);
+    const std::string ks = "dispatch:" + src;
+    std::lock_guard<std::mutex> lk(G.mu);
+    auto it = G.cache.find(ks);
+    if (it != G.cache.end()) return it->second;
+    auto *h = new cj_handle_s();
+    h->kernel = kDispatchKernel;
+    h->a.dtype = p->dtype;
+    h->a.tile[0] = kDispatchBlock;
+    h->a.tile[1] = (int)smem;
+    h->a.tile[2] = minb;
+    h->custom_src = src;
+    h->name_expr = "cj::plan_dispatch";
+    h->impl.store(&h->generic, std::memory_order_release);   // no stand-in of its own
+    h->state = ST_PENDING;
+    // compiled on the background threads even in sync mode: the per-group
+    // kernels serve until it is ready (cj_group_plan_wait)
+    G.queue.push_back(h);
+    G.qcv.notify_one();
+    G.cache.emplace(ks, h);
+    return h;
+}
+
+// Dispatcher variants by resident blocks per SM (the register cap of the
+// launch bounds): the first is requested at plan creation, the others by the
+// plan's autotuner.  FP32 bodies fit 128 registers (two blocks of 256
+// threads) without spilling and 80 (three) with small spills in the n < 8
+// bodies; BF16 tensor-core bodies want more; FP64 rows of X need up to 255.
+std::vector<int> dispatcher_minb(int dtype) {
+    return dtype == CJ_F64 ? std::vector<int>{1} : dtype == CJ_F32 ? std::vector<int>{2, 3} : std::vector<int>{2, 1};
+}
+
+// Ticket the plan's work and request its first dispatcher variant.  `items`
+// is the plan's work list on the host ({offset, T, 0} per item, groups
+// contiguous, each ordered by T descending).
+cj_status plan_dispatcher(cj_group_plan_s *p, const std::vector<long long> &items) {
     struct Tk {
         double cost;
         long long first;
@@ -900,11 +982,7 @@ cj_status plan_dispatcher(cj_group_plan_s *p, const std::vector<long long> &item
     for (size_t g = 0; g < p->groups.size(); ++g) {
         const auto &gr = p->groups[g];
         const int gdt = (p->dtype == CJ_BF16 && gr.n < 16) ? CJ_F32 : p->dtype;
-        const auto t = dispatch_tile(gdt, gr.n, kBlock);
-        smem = std::max(smem, cjg::chain_smem(gr.n, t[0], t[1], esize(gdt)));
-            src += "        case " + std::to_string(g) + ": grouped_chunk_call<" + ct + ", " + std::to_string(gr.n) +
-               ", " + std::to_string(t[0]) + ", " + std::to_string(t[1]) + ", " + std::to_string(kBlock) +
-               ">(it, ninst, A, X, sA, so, ss); break;\n";
+        const auto t = dispatch_tile(gdt, gr.n, kDispatchBlock);
         const double per = 2.0 * gr.n * gr.n * gr.n + 2.0 * gr.n * gr.n;
         for (int64_t c = 0; c < gr.n_items; c += t[1]) {
             Tk k{0.0, gr.first_item + c, (int)g, (int)std::min<int64_t>(t[1], gr.n_items - c)};
@@ -912,7 +990,6 @@ cj_status plan_dispatcher(cj_group_plan_s *p, const std::vector<long long> &item
             tk.push_back(k);
         }
     }
-    src += "        default: break;\n        }\n    });\n}\n}  // namespace cj\n";
     // longest chunks first
     std::stable_sort(tk.begin(), tk.end(), [](const Tk &x, const Tk &y) { return x.cost > y.cost; });
     std::vector<long long> host(2 * tk.size());
@@ -925,32 +1002,7 @@ cj_status plan_dispatcher(cj_group_plan_s *p, const std::vector<long long> &item
         return fail(CJ_ERR_OOM, "grouped plan: dispatcher tickets");
     if (cudaMemcpy(p->d_tickets, host.data(), sizeof(long long) * host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(CJ_ERR_CUDA, "grouped plan: dispatcher ticket upload failed");
-    // one instantiation per distinct source (identical plans share it)
-    const std::string ks = "dispatch:" + src;
-    cj_handle_s *h = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(G.mu);
-        auto it = G.cache.find(ks);
-        if (it != G.cache.end()) {
-            h = it->second;
-        } else {
-            h = new cj_handle_s();
-            h->kernel = kDispatchKernel;
-            h->a.dtype = p->dtype;
-            h->a.tile[0] = kBlock;
-            h->a.tile[1] = (int)smem;
-            h->custom_src = src;
-            h->name_expr = "cj::plan_dispatch";
-            h->impl.store(&h->generic, std::memory_order_release);   // no stand-in of its own
-            h->state = ST_PENDING;
-            // compiled on the background threads even in sync mode: the
-            // per-group kernels serve until it is ready (cj_group_plan_wait)
-            G.queue.push_back(h);
-            G.qcv.notify_one();
-            G.cache.emplace(ks, h);
-        }
-    }
-    p->disp = h;
+    p->disp = request_dispatcher(p, dispatcher_minb(p->dtype)[0]);
     return CJ_OK;
 }
 
@@ -1173,7 +1225,9 @@ CJ_API cj_status cj_launch(cj_handle h, void *const *args, int64_t batch, void *
         // one block per SM, each taking fewer instances than it is shaped for
         int ipb = im->ipb;
         if (batch < (long long)ipb * G.num_sms) ipb = (int)std::max<long long>(1, (batch + G.num_sms - 1) / G.num_sms);
-        const unsigned grid = (unsigned)((batch + ipb - 1) / ipb);
+        unsigned grid = (unsigned)((batch + ipb - 1) / ipb);
+        if (im->variant != V_GENERIC && a.tile[0] == 7)   // persistent: blocks keep their tensor memory
+            grid = (unsigned)std::min<long long>(batch, (long long)G.num_sms * im->blocks_per_sm);
         if (im->variant == V_GENERIC) {
             int n = a.n, lay = a.layout_a;
             void *p[] = {&A, &X, &b, &steps, &c, &n, &lay, &ipb};
@@ -1534,6 +1588,13 @@ CJ_API cj_status cj_group_plan_autotune(cj_group_plan p, const void *A_pool, voi
     cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
     const size_t ng = max_groups > 0 ? std::min<size_t>((size_t)max_groups, p->groups.size()) : p->groups.size();
     int nchg = 0;
+    // 0. the dispatcher's other variants start compiling now, beside the groups' candidates
+    std::vector<cj_handle_s *> variants;
+    if (p->disp) {
+        variants.push_back(p->disp);
+        const std::vector<int> mb = dispatcher_minb(p->dtype);
+        for (size_t i = 1; i < mb.size(); ++i) variants.push_back(request_dispatcher(p, mb[i]));
+    }
     // 1. request every candidate tile of the tuned groups (the most expensive
     //    first: groups are kept sorted by cost); in async mode they compile in
     //    parallel on the background threads
@@ -1595,32 +1656,49 @@ CJ_API cj_status cj_group_plan_autotune(cj_group_plan p, const void *A_pool, voi
             ++nchg;
         }
     }
-    // 3. the launch form: the dispatcher (once compiled) against one kernel
-    //    per group with the tiles just chosen, each timed as a whole launch
-    //    (each form as a CUDA graph and issued directly; a form's time is the
-    //    faster of the two)
-    if (rc == CJ_OK && p->disp && cj_specialize_wait(p->disp, -1) == CJ_OK && dispatcher_ready(p)) {
-        float best[2] = {INFINITY, INFINITY};
-        p->use_dispatcher = true;
-        const int flags[4] = {CJ_PLAN_GRAPH, 0, CJ_PLAN_GRAPH | CJ_PLAN_PER_GROUP, CJ_PLAN_PER_GROUP};
-        for (int f = 0; f < 4 && rc == CJ_OK; ++f) {
-            std::vector<float> ms;
-            for (int r = 0; r <= reps && rc == CJ_OK; ++r) {
-                float t = 0;
-                if (cudaEventRecord(e0, st) != cudaSuccess)
-                    rc = fail(CJ_ERR_CUDA, "grouped autotune: event failed");
-                else if ((rc = plan_launch(p, A_pool, X_pool, st, flags[f])) == CJ_OK &&
-                         (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                          cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
-                    rc = fail(CJ_ERR_CUDA, "grouped autotune: timing failed");
-                else if (r > 0)
-                    ms.push_back(t);
-            }
-            if (rc != CJ_OK) break;
-            std::sort(ms.begin(), ms.end());
-            best[f / 2] = std::min(best[f / 2], ms[ms.size() / 2]);
+    // 3. the launch form: every compiled dispatcher variant against one
+    //    kernel per group with the tiles just chosen, each timed as a whole
+    //    launch, as a CUDA graph and issued directly (a form's time is the
+    //    faster of the two); the fastest is kept
+    auto time_form = [&](int flags, float *out) {
+        std::vector<float> ms;
+        for (int r = 0; r <= reps && rc == CJ_OK; ++r) {
+            float t = 0;
+            if (cudaEventRecord(e0, st) != cudaSuccess)
+                rc = fail(CJ_ERR_CUDA, "grouped autotune: event failed");
+            else if ((rc = plan_launch(p, A_pool, X_pool, st, flags)) == CJ_OK &&
+                     (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                      cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+                rc = fail(CJ_ERR_CUDA, "grouped autotune: timing failed");
+            else if (r > 0)
+                ms.push_back(t);
         }
-        p->use_dispatcher = rc != CJ_OK || best[0] <= best[1];
+        if (rc == CJ_OK) {
+            std::sort(ms.begin(), ms.end());
+            *out = std::min(*out, ms[ms.size() / 2]);
+        }
+    };
+    if (rc == CJ_OK && !variants.empty()) {
+        float best_disp = INFINITY, best_group = INFINITY;
+        cj_handle_s *best_h = p->disp;
+        p->use_dispatcher = true;
+        for (cj_handle_s *v : variants) {
+            if (rc != CJ_OK) break;
+            if (cj_specialize_wait(v, -1) != CJ_OK) continue;   // a variant that failed to compile
+            p->disp = v;
+            if (!dispatcher_ready(p)) continue;
+            float t = INFINITY;
+            time_form(CJ_PLAN_GRAPH, &t);
+            time_form(0, &t);
+            if (t < best_disp) {
+                best_disp = t;
+                best_h = v;
+            }
+        }
+        p->disp = best_h;
+        time_form(CJ_PLAN_GRAPH | CJ_PLAN_PER_GROUP, &best_group);
+        time_form(CJ_PLAN_PER_GROUP, &best_group);
+        p->use_dispatcher = rc != CJ_OK || best_disp <= best_group;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

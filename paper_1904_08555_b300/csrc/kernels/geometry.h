@@ -30,7 +30,8 @@ CJ_HD constexpr int inst_pitch(int nn) { return nn | 1; }
 // (padded), mapping 5 one thread per 4x4 block, mapping 6 one thread per two
 // rows, mapping 1 one thread per row.
 CJ_HD constexpr int chain_threads(int n, int mapping, int ipb) {
-    return mapping == 2   ? ipb
+    return mapping == 7   ? 128
+           : mapping == 2 ? ipb
            : mapping == 6 ? ((ipb * ((n + 1) / 2) + 31) / 32) * 32
            : mapping == 5 ? ((ipb * ((n + 3) / 4) * ((n + 3) / 4) + 31) / 32) * 32
            : mapping == 4 ? ipb * (n / 8) * 32
@@ -59,7 +60,9 @@ CJ_HD constexpr int xrow_pitch(int n) { return n | 1; }
 
 // Bytes of dynamic shared memory of the specialized update chain kernel.
 CJ_HD constexpr long chain_smem(int n, int mapping, int ipb, int esize) {
-    return mapping == 2
+    return mapping == 7
+        ? 128L * ((n + 15) / 16 * 16) * 2 + (long)((n + 15) / 16 * 16) * ((n + 15) / 16 * 16) * 2
+        : mapping == 2
         ? (long)ipb * inst_pitch(n * n) * esize
         : mapping == 5
         ? (long)ipb * chain_pitch(n, 5, esize) * esize + (long)ipb * ((n + 3) / 4 * 4) * ((n + 3) / 4 * 4 + 4) * esize

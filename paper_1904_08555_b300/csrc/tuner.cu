@@ -49,9 +49,10 @@ void chain_candidates(const cj_template_args &a, std::vector<std::array<int, 4>>
     auto ok = [&](int map, int ipb) {
         return cjg::chain_threads(n, map, ipb) <= 1024 && cjg::chain_smem(n, map, ipb, es) <= 200 * 1024;
     };
-    if (a.dtype == CJ_BF16) {   // mapping 3 is the only BF16 mapping
+    if (a.dtype == CJ_BF16) {   // mma.sync panels (mapping 3) and tcgen05 (mapping 7)
         for (int ipb : {1, 2, 4, 8})
             if (ok(3, ipb)) out.push_back({3, ipb, 0, 0});
+        out.push_back({7, 1, 0, 0});
         return;
     }
     if (a.dtype == CJ_F64 && n % 8 == 0 && n <= 32)
@@ -203,6 +204,7 @@ void featurize(int k, const cj_template_args &a0, int64_t batch, int32_t steps, 
         f[21] = map == 2;
         f[22] = map == 4 || map == 5;   // register/tensor blocked panels
         f[19] = map == 5 ? 1.f : map == 6 ? 0.5f : 0.f;
+        f[16] = map == 7;   // tcgen05 tensor cores
         f[23] = lg2(tile[1]) / 8;
         const int threads = cjg::chain_threads(a.n, map, tile[1]);
         f[24] = lg2(threads) / 10;
