@@ -465,9 +465,12 @@ def main():
             return []
         gi, go = lin in (1, 4), lout in (1, 4)
         tg = 1 if not (gi or go) else (8 if (gi and lout in (0, 2)) or (go and lin in (0, 2)) else 32)
-        return [("tc_s2p8", (tg, 128 // tg, 32 * 13, (4 << 16) | (2 << 8) | 8)),
+        alts = [("tc_s2p8", (tg, 128 // tg, 32 * 13, (4 << 16) | (2 << 8) | 8)),
                 ("tf32x3", (tg, 64 // tg, 128, (1 << 20) | (2 << 16) | (1 << 8) | 8)),
                 ("direct_r2", (tg, 256 // tg, 128, (3 << 16) | (2 << 8)))]
+        if tg == 8:   # in and out have different fastest column axes: a 16 x 8 TMA box beside the rule's 8 x 16
+            alts.append(("tma_tg16", (16, 8, 32 * 14, (4 << 20) | (5 << 16) | (2 << 8) | 8)))
+        return alts
     args.lt_alt_tiles = lt_alt_tiles
     if args.impl == "reference":
         reference_arm(args)

@@ -351,8 +351,10 @@ cj_status cj_group_plan_launch(cj_group_plan p, const void *A_pool, void *X_pool
 /* The plan's dispatcher: *state 0 none (a CJ_FLAG_GENERIC plan), 1 compiling,
  * 2 ready (launches use it), 3 failed to compile, 4 ready but not used (the
  * plan's autotuner timed one kernel per group faster); *n_tickets its work
- * tickets; *threads its block size.  Any output may be NULL. */
-cj_status cj_group_plan_dispatcher(cj_group_plan p, int32_t *state, int32_t *n_tickets, int32_t *threads);
+ * tickets; *threads its block size; *blocks_per_sm the resident blocks per SM
+ * of the variant in use (0 until it is compiled).  Any output may be NULL. */
+cj_status cj_group_plan_dispatcher(cj_group_plan p, int32_t *state, int32_t *n_tickets, int32_t *threads,
+                                   int32_t *blocks_per_sm);
 /* Wait up to timeout_ms (negative: forever) for the instantiations of every
  * group of p to finish compiling.  CJ_OK: every group launches its
  * specialized kernel.  CJ_ERR_TIMEOUT: some are still compiling (launches

@@ -84,7 +84,8 @@ def load():
         L.cj_group_plan_launch.argtypes = [P, P, P, P, ctypes.c_int]
         L.cj_group_plan_autotune.argtypes = [P, P, P, P, i32, i32, ctypes.POINTER(i32)]
         L.cj_group_plan_wait.argtypes = [P, ctypes.c_int]
-        L.cj_group_plan_dispatcher.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        L.cj_group_plan_dispatcher.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                               ctypes.POINTER(i32)]
         L.cj_group_plan_info.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i64)]
         L.cj_group_plan_destroy.argtypes = [P]
         L.cj_measure_fma_peak.argtypes = [i32, i32, P, ctypes.POINTER(ctypes.c_double)]
@@ -325,11 +326,11 @@ class GroupPlan:
 
     def dispatcher(self) -> dict:
         """State of the plan's dispatcher: none, compiling, ready or failed."""
-        st, nt, th = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
-        _check(load().cj_group_plan_dispatcher(self.ptr, ctypes.byref(st), ctypes.byref(nt), ctypes.byref(th)),
-               "cj_group_plan_dispatcher")
+        st, nt, th, bp = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+        _check(load().cj_group_plan_dispatcher(self.ptr, ctypes.byref(st), ctypes.byref(nt), ctypes.byref(th),
+                                               ctypes.byref(bp)), "cj_group_plan_dispatcher")
         return {"state": ("none", "compiling", "ready", "failed", "not used")[st.value], "tickets": nt.value,
-                "threads": th.value}
+                "threads": th.value, "blocks_per_sm": bp.value}
 
     def autotune(self, A_pool, X_pool, stream=None, max_groups: int = 0, reps: int = 3) -> int:
         """Time every candidate tile per group (most expensive first) and keep the fastest; returns groups changed."""

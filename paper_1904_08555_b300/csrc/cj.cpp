@@ -818,6 +818,15 @@ struct cj_group_plan_s {
     long long *d_tickets = nullptr;
     int n_tickets = 0;
     bool use_dispatcher = true;   // false once the plan's autotuner found the per-group form faster
+    // every dispatcher variant requested for this plan, with its own tickets
+    // (disp, d_tickets, n_tickets above are the one in use)
+    struct DispForm {
+        cj_handle h = nullptr;
+        long long *d_tickets = nullptr;
+        int n_tickets = 0;
+    };
+    std::vector<DispForm> disp_forms;
+    std::vector<long long> h_items;   // the work list on the host
 };
 
 namespace {
@@ -831,7 +840,8 @@ void plan_free(cj_group_plan_s *p) {
     if (p->capture) cudaStreamDestroy(p->capture);
     if (p->d_items) cudaFree(p->d_items);
     if (p->d_counters) cudaFree(p->d_counters);
-    if (p->d_tickets) cudaFree(p->d_tickets);
+    for (auto &f : p->disp_forms)
+        if (f.d_tickets) cudaFree(f.d_tickets);
     delete p;
 }
 
@@ -839,9 +849,9 @@ void plan_free(cj_group_plan_s *p) {
 // f32 for the n < 16 groups of a bf16 plan), for blocks of `block` threads:
 // bf16 tensor-core panels (mapping 3); f32 n >= 8 register blocks (mapping
 // 5); n <= 4 one instance per thread (mapping 2); otherwise one row per
-// thread (mapping 1).  As many instances per chunk as fill the block (at
+// thread (mapping 1).  `rule` selects among tile rules (one so far).  As many instances per chunk as fill the block (at
 // most 256), fewer where shared memory would exceed 160 KiB.
-std::array<int, 2> dispatch_tile(int dtype, int n, int block) {
+std::array<int, 2> dispatch_tile(int dtype, int n, int block, int rule = 0) {
     const int es = esize(dtype);
     int map, tpi;
     if (dtype == CJ_BF16) map = 3, tpi = ((n + 15) / 16) * 32;
@@ -907,7 +917,14 @@ constexpr int kDispatchBlock = 256;
 
 // The dispatcher's source for `minb` resident blocks per SM (the launch
 // bounds' register cap), and its shared-memory need.
-std::string dispatcher_source(const cj_group_plan_s *p, int minb, long *smem_out) {
+// A dispatcher variant: resident blocks per SM the launch bounds must allow
+// (the register cap) and the tile rule.
+struct DispVariant {
+    int minb, rule;
+};
+
+std::string dispatcher_source(const cj_group_plan_s *p, DispVariant v, long *smem_out) {
+    const int minb = v.minb;
     constexpr int kBlock = kDispatchBlock;
     const char *ct = p->dtype == CJ_F64 ? "double" : "float";
     std::string src = "#include \"update_chain.cuh\"\nnamespace cj {\n__global__ void __launch_bounds__(" +
@@ -922,7 +939,7 @@ std::string dispatcher_source(const cj_group_plan_s *p, int minb, long *smem_out
     for (size_t g = 0; g < p->groups.size(); ++g) {
         const auto &gr = p->groups[g];
         const int gdt = (p->dtype == CJ_BF16 && gr.n < 16) ? CJ_F32 : p->dtype;
-        const auto t = dispatch_tile(gdt, gr.n, kBlock);
+        const auto t = dispatch_tile(gdt, gr.n, kBlock, v.rule);
         smem = std::max(smem, cjg::chain_smem(gr.n, t[0], t[1], esize(gdt)));
         src += "        case " + std::to_string(g) + ": grouped_chunk_call<" + ct + ", " + std::to_string(gr.n) +
                ", " + std::to_string(t[0]) + ", " + std::to_string(t[1]) + ", " + std::to_string(kBlock) +
@@ -933,11 +950,11 @@ std::string dispatcher_source(const cj_group_plan_s *p, int minb, long *smem_out
     return src;
 }
 
-// Request (compile in the background) the dispatcher variant for `minb`;
-// identical plans share it.
-cj_handle_s *request_dispatcher(const cj_group_plan_s *p, int minb) {
+// Request (compile in the background) a dispatcher variant; identical plans
+// share it.
+cj_handle_s *request_dispatcher(const cj_group_plan_s *p, DispVariant v) {
     long smem = 0;
-    const std::string src = dispatcher_source(p, minb, &smem);
+    const std::string src = dispatcher_source(p, v, &smem);
     const std::string ks = "dispatch:" + src;
     std::lock_guard<std::mutex> lk(G.mu);
     auto it = G.cache.find(ks);
@@ -947,7 +964,8 @@ cj_handle_s *request_dispatcher(const cj_group_plan_s *p, int minb) {
     h->a.dtype = p->dtype;
     h->a.tile[0] = kDispatchBlock;
     h->a.tile[1] = (int)smem;
-    h->a.tile[2] = minb;
+    h->a.tile[2] = v.minb;
+    h->a.tile[3] = v.rule;
     h->custom_src = src;
     h->name_expr = "cj::plan_dispatch";
     h->impl.store(&h->generic, std::memory_order_release);   // no stand-in of its own
@@ -960,19 +978,20 @@ cj_handle_s *request_dispatcher(const cj_group_plan_s *p, int minb) {
     return h;
 }
 
-// Dispatcher variants by resident blocks per SM (the register cap of the
-// launch bounds): the first is requested at plan creation, the others by the
-// plan's autotuner.  FP32 bodies fit 128 registers (two blocks of 256
+// Dispatcher variants: the first is requested at plan creation, the others
+// by the plan's autotuner.  FP32 bodies fit 128 registers (two blocks of 256
 // threads) without spilling and 80 (three) with small spills in the n < 8
 // bodies; BF16 tensor-core bodies want more; FP64 rows of X need up to 255.
-std::vector<int> dispatcher_minb(int dtype) {
-    return dtype == CJ_F64 ? std::vector<int>{1} : dtype == CJ_F32 ? std::vector<int>{2, 3} : std::vector<int>{2, 1};
+std::vector<DispVariant> dispatcher_variants(int dtype) {
+    if (dtype == CJ_F64) return {{1, 0}};
+    if (dtype == CJ_F32) return {{2, 0}, {3, 0}};
+    return {{2, 0}, {1, 0}};
 }
 
-// Ticket the plan's work and request its first dispatcher variant.  `items`
-// is the plan's work list on the host ({offset, T, 0} per item, groups
-// contiguous, each ordered by T descending).
-cj_status plan_dispatcher(cj_group_plan_s *p, const std::vector<long long> &items) {
+// Ticket the plan's work for variant v (each ticket one chunk of one group,
+// chunks as large as v's body for that group takes), upload the tickets and
+// request v's kernel.
+cj_status make_dispatch_form(cj_group_plan_s *p, DispVariant v, cj_group_plan_s::DispForm *out) {
     struct Tk {
         double cost;
         long long first;
@@ -982,11 +1001,11 @@ cj_status plan_dispatcher(cj_group_plan_s *p, const std::vector<long long> &item
     for (size_t g = 0; g < p->groups.size(); ++g) {
         const auto &gr = p->groups[g];
         const int gdt = (p->dtype == CJ_BF16 && gr.n < 16) ? CJ_F32 : p->dtype;
-        const auto t = dispatch_tile(gdt, gr.n, kDispatchBlock);
+        const auto t = dispatch_tile(gdt, gr.n, kDispatchBlock, v.rule);
         const double per = 2.0 * gr.n * gr.n * gr.n + 2.0 * gr.n * gr.n;
         for (int64_t c = 0; c < gr.n_items; c += t[1]) {
             Tk k{0.0, gr.first_item + c, (int)g, (int)std::min<int64_t>(t[1], gr.n_items - c)};
-            for (int i = 0; i < k.count; ++i) k.cost += per * (double)items[3 * (k.first + i) + 1];
+            for (int i = 0; i < k.count; ++i) k.cost += per * (double)p->h_items[3 * (k.first + i) + 1];
             tk.push_back(k);
         }
     }
@@ -997,12 +1016,32 @@ cj_status plan_dispatcher(cj_group_plan_s *p, const std::vector<long long> &item
         host[2 * i] = tk[i].first;
         host[2 * i + 1] = ((long long)tk[i].group << 16) | tk[i].count;
     }
-    p->n_tickets = (int)tk.size();
-    if (cudaMalloc(&p->d_tickets, sizeof(long long) * host.size()) != cudaSuccess)
+    out->n_tickets = (int)tk.size();
+    if (cudaMalloc(&out->d_tickets, sizeof(long long) * host.size()) != cudaSuccess)
         return fail(CJ_ERR_OOM, "grouped plan: dispatcher tickets");
-    if (cudaMemcpy(p->d_tickets, host.data(), sizeof(long long) * host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    if (cudaMemcpy(out->d_tickets, host.data(), sizeof(long long) * host.size(), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
         return fail(CJ_ERR_CUDA, "grouped plan: dispatcher ticket upload failed");
-    p->disp = request_dispatcher(p, dispatcher_minb(p->dtype)[0]);
+    out->h = request_dispatcher(p, v);
+    return CJ_OK;
+}
+
+void use_dispatch_form(cj_group_plan_s *p, const cj_group_plan_s::DispForm &f) {
+    p->disp = f.h;
+    p->d_tickets = f.d_tickets;
+    p->n_tickets = f.n_tickets;
+}
+
+// The plan's first dispatcher variant, requested at plan creation.  `items`
+// is the plan's work list on the host ({offset, T, 0} per item, groups
+// contiguous, each ordered by T descending).
+cj_status plan_dispatcher(cj_group_plan_s *p, const std::vector<long long> &items) {
+    p->h_items = items;
+    cj_group_plan_s::DispForm f;
+    const cj_status rc = make_dispatch_form(p, dispatcher_variants(p->dtype)[0], &f);
+    p->disp_forms.push_back(f);   // freed with the plan even if the upload failed
+    if (rc != CJ_OK) return rc;
+    use_dispatch_form(p, f);
     return CJ_OK;
 }
 
@@ -1589,11 +1628,17 @@ CJ_API cj_status cj_group_plan_autotune(cj_group_plan p, const void *A_pool, voi
     const size_t ng = max_groups > 0 ? std::min<size_t>((size_t)max_groups, p->groups.size()) : p->groups.size();
     int nchg = 0;
     // 0. the dispatcher's other variants start compiling now, beside the groups' candidates
-    std::vector<cj_handle_s *> variants;
     if (p->disp) {
-        variants.push_back(p->disp);
-        const std::vector<int> mb = dispatcher_minb(p->dtype);
-        for (size_t i = 1; i < mb.size(); ++i) variants.push_back(request_dispatcher(p, mb[i]));
+        const std::vector<DispVariant> vs = dispatcher_variants(p->dtype);
+        for (size_t i = p->disp_forms.size(); i < vs.size(); ++i) {
+            cj_group_plan_s::DispForm f;
+            const cj_status rf = make_dispatch_form(p, vs[i], &f);
+            if (rf != CJ_OK) {
+                if (f.d_tickets) cudaFree(f.d_tickets);
+                return rf;
+            }
+            p->disp_forms.push_back(f);
+        }
     }
     // 1. request every candidate tile of the tuned groups (the most expensive
     //    first: groups are kept sorted by cost); in async mode they compile in
@@ -1678,24 +1723,24 @@ CJ_API cj_status cj_group_plan_autotune(cj_group_plan p, const void *A_pool, voi
             *out = std::min(*out, ms[ms.size() / 2]);
         }
     };
-    if (rc == CJ_OK && !variants.empty()) {
+    if (rc == CJ_OK && !p->disp_forms.empty()) {
         float best_disp = INFINITY, best_group = INFINITY;
-        cj_handle_s *best_h = p->disp;
+        cj_group_plan_s::DispForm best_f{p->disp, p->d_tickets, p->n_tickets};
         p->use_dispatcher = true;
-        for (cj_handle_s *v : variants) {
+        for (const auto &f : p->disp_forms) {
             if (rc != CJ_OK) break;
-            if (cj_specialize_wait(v, -1) != CJ_OK) continue;   // a variant that failed to compile
-            p->disp = v;
+            if (cj_specialize_wait(f.h, -1) != CJ_OK) continue;   // a variant that failed to compile
+            use_dispatch_form(p, f);
             if (!dispatcher_ready(p)) continue;
             float t = INFINITY;
             time_form(CJ_PLAN_GRAPH, &t);
             time_form(0, &t);
             if (t < best_disp) {
                 best_disp = t;
-                best_h = v;
+                best_f = f;
             }
         }
-        p->disp = best_h;
+        use_dispatch_form(p, best_f);
         time_form(CJ_PLAN_GRAPH | CJ_PLAN_PER_GROUP, &best_group);
         time_form(CJ_PLAN_PER_GROUP, &best_group);
         p->use_dispatcher = rc != CJ_OK || best_disp <= best_group;
@@ -1733,7 +1778,8 @@ CJ_API cj_status cj_group_plan_wait(cj_group_plan p, int timeout_ms) {
     return worst == CJ_OK ? CJ_OK : fail(worst, "a group's instantiation failed to compile; it runs generic");
 }
 
-CJ_API cj_status cj_group_plan_dispatcher(cj_group_plan p, int32_t *state, int32_t *n_tickets, int32_t *threads) {
+CJ_API cj_status cj_group_plan_dispatcher(cj_group_plan p, int32_t *state, int32_t *n_tickets, int32_t *threads,
+                                          int32_t *blocks_per_sm) {
     if (!p) return fail(CJ_ERR_INVALID_ARG, "null plan");
     if (state) {
         const int s = p->disp ? p->disp->state.load(std::memory_order_acquire) : -1;
@@ -1741,6 +1787,7 @@ CJ_API cj_status cj_group_plan_dispatcher(cj_group_plan p, int32_t *state, int32
     }
     if (n_tickets) *n_tickets = p->n_tickets;
     if (threads) *threads = p->disp ? p->disp->a.tile[0] : 0;
+    if (blocks_per_sm) *blocks_per_sm = dispatcher_ready(p) ? p->disp->spec.blocks_per_sm : 0;
     return CJ_OK;
 }
 

@@ -216,7 +216,7 @@ void featurize(int k, const cj_template_args &a0, int64_t batch, int32_t steps, 
         const bool a_regs = es == 8 ? a.n * a.n <= 64 : a.n * a.n <= 100;
         f[10] = (map == 1 || map == 6) && a_regs;
         f[11] = (map == 1 && a.n > cjg::chain_reg_rows_max(es)) || (map == 6 && a.n > 32);
-        const double np = map == 5 ? (a.n + 3) / 4 * 4 : map == 3 ? (a.n + 15) / 16 * 16 : map == 4 ? a.n : a.n;
+        const double np = map == 5 ? (a.n + 3) / 4 * 4 : (map == 3 || map == 7) ? (a.n + 15) / 16 * 16 : a.n;
         f[12] = (float)(np * np * np / ((double)a.n * a.n * a.n) - 1.0);
         const long smem = k == CJ_K_EIGEN_RECURRENCE ? cjg::eig_smem(a.n, tile[1], es, tile[0])
                                                        : cjg::chain_smem(a.n, map, tile[1], es);
