@@ -465,11 +465,14 @@ def main():
             return []
         gi, go = lin in (1, 4), lout in (1, 4)
         tg = 1 if not (gi or go) else (8 if (gi and lout in (0, 2)) or (go and lin in (0, 2)) else 32)
-        alts = [("tc_s2p8", (tg, 128 // tg, 32 * 13, (4 << 16) | (2 << 8) | 8)),
-                ("tf32x3", (tg, 64 // tg, 128, (1 << 20) | (2 << 16) | (1 << 8) | 8)),
-                ("direct_r2", (tg, 256 // tg, 128, (3 << 16) | (2 << 8)))]
-        if tg == 8:   # in and out have different fastest column axes: a 16 x 8 TMA box beside the rule's 8 x 16
-            alts.append(("tma_tg16", (16, 8, 32 * 14, (4 << 20) | (5 << 16) | (2 << 8) | 8)))
+        def tmem(boxes, stages, nconv, g=tg):   # tcgen05 with the A operand in tensor memory (mode 6)
+            return (g, 128 // g, 32 * (6 + nconv), (boxes << 20) | (6 << 16) | (stages << 8) | nconv)
+        alts = [("tma_b4s2", (tg, 128 // tg, 32 * 14, (4 << 20) | (5 << 16) | (2 << 8) | 8)),
+                ("tc_s2p8", (tg, 128 // tg, 32 * 13, (4 << 16) | (2 << 8) | 8)),
+                ("tmem_b4s2", tmem(4, 2, 8)), ("tmem_b6s4", tmem(6, 4, 8)), ("tmem_b8s6", tmem(8, 6, 8)),
+                ("tmem_b6s4c4", tmem(6, 4, 4))]
+        if tg == 8:   # in and out have different fastest column axes: a 16 x 8 box beside the rule's 8 x 16
+            alts.append(("tmem_b6s4_tg16", tmem(6, 4, 8, 16)))
         return alts
     args.lt_alt_tiles = lt_alt_tiles
     if args.impl == "reference":
@@ -597,6 +600,10 @@ def run_config3(torch, cj, stream, dtype, Z, reps, alt_tiles=None, samples=384):
 
     wt0 = cj.stats()["wait_timeouts"]
     rows, tot_s, tot_g, worst = [], 0.0, 0.0, 0.0
+    # every alternative tile is requested first, so that they compile side by side
+    alts = {(lin, lout): [(name, cj.specialize(cj.K_LTIMES, dt, layout_a=lin, layout_b=lout, m=M, d=D, tile=alt))
+                          for name, alt in (alt_tiles(lin, lout) if alt_tiles else [])]
+            for lin in range(6) for lout in range(6)}
     for lin in range(6):
         for lout in range(6):
             hs = cj.specialize(cj.K_LTIMES, dt, layout_a=lin, layout_b=lout, m=M, d=D)
@@ -613,22 +620,23 @@ def run_config3(torch, cj, stream, dtype, Z, reps, alt_tiles=None, samples=384):
             row = {"in": synth.LAYOUT_NAMES[lin], "out": synth.LAYOUT_NAMES[lout].replace("D", "M"),
                    "spec_ms": ms_s, "generic_ms": ms_g, "spec_gbs": byt / ms_s / 1e6,
                    "speedup_vs_generic": ms_g / ms_s, "spec_rel_err": e_s, "tile": _key_tile(hs)}
-            for name, alt in (alt_tiles(lin, lout) if alt_tiles else []):
-                ha = cj.specialize(cj.K_LTIMES, dt, layout_a=lin, layout_b=lout, m=M, d=D, tile=alt)
+            for name, ha in alts[(lin, lout)]:
                 ha.wait()
                 fa = lambda: cj.launch_ltimes(ha, Lt, xin[lin], o, G, Z, stream=stream)
                 _events(torch, stream, fa, 1)
                 row[name + "_ms"] = _events(torch, stream, fa, reps)
+                row[name + "_rel_err"] = e_a = err_of(lout)
+                worst = max(worst, e_a)
             rows.append(row)
             tot_s += ms_s
             tot_g += ms_g
     wait_timeouts = cj.stats()["wait_timeouts"] - wt0
     del xin, o
     # Compute bound of the default kernel: FP32 runs 3xTF32 on the tensor
-    # cores (tile modes 4 and 5: three TF32 products per multiply-add, TF32 peak
+    # cores (tile modes 4-6: three TF32 products per multiply-add, TF32 peak
     # = measured bf16 x the nominal 1.1 / 2.25 ratio); FP64 runs on the
     # FP64 pipe at its nominal rate.
-    tc = dt == cj.F32 and all(((r["tile"][3] >> 16) & 0xF) in (4, 5) for r in rows)
+    tc = dt == cj.F32 and all(((r["tile"][3] >> 16) & 0xF) in (4, 5, 6) for r in rows)
     if tc:
         peak = measured_peak("bf16_tflops", 1800.0) * 1.1 / 2.25
         t_alu = 3 * f / (peak * 1e12) * 1e3
@@ -652,7 +660,7 @@ def run_config3(torch, cj, stream, dtype, Z, reps, alt_tiles=None, samples=384):
             "speedup_vs_generic": tot_g / tot_s,
             "min_speedup_vs_generic": min(r["speedup_vs_generic"] for r in rows),
             "max_rel_frobenius_error_vs_oracle": worst,
-            "error_sample": f"{samples} seeded (g, z) columns x all 36 moments, every order pair, both kernels",
+            "error_sample": f"{samples} seeded (g, z) columns x all 36 moments, every order pair, every kernel timed",
             "wait_timeouts": wait_timeouts, "valid": wait_timeouts == 0,
             "roofline": rf, "per_pair": rows,
             "config": {"workload": f"LTimes out[m][g][z] = sum_d L[m][d] in[d][g][z], M=36 D=96 G=32 Z={Z}, "
@@ -815,6 +823,21 @@ def run_config4(torch, cj, stream, dtype, K, W, ref):
                 e = _uneven_errors(X.double().cpu().numpy(), ref["f64" if dt == cj.F64 else "f32"], n, off)
                 errs = e if errs is None else np.maximum(errs, e)
         plan.destroy()
+    # every dispatcher variant pinned in turn (its tiles come from the
+    # dispatcher's own rule, not from the groups' autotuned tiles), as a graph
+    variants_ms = {}
+    plan = cj.GroupPlan(dt, n, t)
+    plan.wait()
+    for v in range(plan.use_dispatcher()):
+        plan.use_dispatcher(v)
+        fn = lambda: plan.launch(A, X, stream=stream, use_graph=True)
+        _events(torch, stream, fn, W)
+        d = plan.dispatcher()
+        variants_ms[f"{v} (blocks/SM {d['blocks_per_sm']})"] = _events(torch, stream, fn, reps)
+        stream.synchronize()
+        e = _uneven_errors(X.double().cpu().numpy(), ref["f64" if dt == cj.F64 else "f32"], n, off)
+        errs = np.maximum(errs, e)
+    plan.destroy()
     del A, X
     kept = "dispatch" if disp.get("state") == "ready" else "per_group"
     spec_ms = min(modes[("spec", kept + "_graph")], modes[("spec", kept + ("_direct" if kept == "dispatch" else "_streams"))])
@@ -827,8 +850,8 @@ def run_config4(torch, cj, stream, dtype, K, W, ref):
     else:
         err = {"max_rel_frobenius_error_vs_oracle": float(errs.max())}
     return {"value": f / spec_ms / 1e6, "dtype": dtype, **err,
-            "error_sample": "every instance, every launch form of the autotuned plan",
-            "launch_form_kept": kept, "dispatcher": disp,
+            "error_sample": "every instance, every launch form of the autotuned plan and every dispatcher variant",
+            "launch_form_kept": kept, "dispatcher": disp, "dispatcher_variants_ms": variants_ms,
             "dispatch_gflops": f / min(modes[("spec", "dispatch_graph")], modes[("spec", "dispatch_direct")]) / 1e6,
             "per_group_gflops": f / min(modes[("spec", "per_group_graph")], modes[("spec", "per_group_streams")]) / 1e6,
             "generic": {"value": f / best("generic") / 1e6, "unit": "GFLOP/s", "ms": best("generic")},

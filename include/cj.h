@@ -90,7 +90,7 @@ typedef enum {
 #define CJ_FLAG_GENERIC 0x1u      /* use the generic runtime-N kernel, never compile */
 #define CJ_FLAG_NO_AOT 0x2u       /* JIT compile even where an AoT specialization exists */
 #define CJ_FLAG_INJECT_COMPILE_ERROR 0x100u  /* test hook: submit a template that fails to compile */
-/* test hook (LTimes tile modes 4 and 5 only): compile the tensor-core kernel
+/* test hook (LTimes tile modes 4-6 only): compile the tensor-core kernel
  * with producers that never signal a filled operand stage, so that every
  * block's bounded wait expires (about a second); blocks then stop and
  * cj_handle_wait_timeouts reports them, and `out` is left incomplete */
@@ -140,9 +140,13 @@ typedef struct {
  *     16 <= n <= 64, one instance per block at a time: {7, 1}; accumulator in
  *     tensor memory, fp32 state in registers; a persistent grid whose blocks
  *     keep their tensor memory; bounded waits counted like the LTimes tensor-
- *     core kernels', see cj_handle_wait_timeouts).
+ *     core kernels', see cj_handle_wait_timeouts), 8 = FP32 register blocks
+ *     of 4 rows x 8 columns (as 5 with columns padded to a multiple of 8:
+ *     three 16-byte shared-memory reads per 32 fused multiply-adds).
  *     Default: n <= 4 -> {2, 128}; f32 grouped with n >= 17 -> {5, 1};
- *     f32 with n >= 9 -> {6, max(1, 128 / ceil(n / 2))}; otherwise n <= 32 ->
+ *     f32 with n >= 32 -> {8, max(1, round(128 / t))}, t = ceil(n / 4) *
+ *     ceil(n / 8) threads per instance; f32 with n >= 9 ->
+ *     {6, max(1, 128 / ceil(n / 2))}; otherwise n <= 32 ->
  *     {1, max(1, 256 / n)};
  *     else {1, max(1, 128 / n)}; bf16 -> {3, max(1, 128 / n16)} with n16 = n
  *     rounded up to a multiple of 16 (mapping 3: one warp per 16 rows,
@@ -182,11 +186,19 @@ typedef struct {
  *     admits no TMA tensor map (innermost extent not a multiple of 4, or not
  *     16-byte aligned) runs the mode-4 kernel of the same tile instead
  *     (cj_stats counts both).
+ *     MODE 6: as mode 5 with the tf32 operand of `in` in tensor memory
+ *     instead of shared memory (the converters write it with tcgen05.st and
+ *     the MMAs read it from there): R = TMEM operand stages of 64 columns
+ *     (2 <= R, 2 * ceil32(ceil16(m)) + 64 R <= 512), S = converter warps (4
+ *     or 8), threads = 32 * (6 + S), PIPE = boxes in flight (2..8).  Its
+ *     fallback without a tensor map is the mode-4 kernel with R 2, S 8.
  *     Default: call orders 1 and 4 "g-fast" (g is the fastest axis) and 0
  *     and 2 "z-fast"; TG = 1 if neither in nor out is g-fast, 8 if one is
  *     g-fast and the other z-fast, 32 otherwise.  f32 with m <= 128: TZ =
- *     128 / TG, MODE 5 with R 2, S 8 (448 threads) and the largest PIPE in
- *     {4, 3, 2} that fits 220 KiB of shared memory, else MODE 4 with R 2, S 8
+ *     128 / TG, MODE 6 with R 4, S 4 (320 threads) and the largest PIPE in
+ *     {6, ..., 2} that fits 220 KiB of shared memory (and the mode-4
+ *     fallback fits too), else MODE 5 with R 2, S 8 (448 threads) and the
+ *     largest PIPE in {4, 3, 2} that fits, else MODE 4 with R 2, S 8
  *     (416 threads) if that fits.  Otherwise CT = 64 columns, TZ = CT / TG;
  *     f64: R 1, S 9, threads 64 * ceil(m / 9) (m = 36: 256); f32: PIPE 1,
  *     R 2, S 12, threads 32 * ceil(m / 12).  The FP64 tensor-core mappings
@@ -206,15 +218,15 @@ typedef struct {
     uint64_t requests, cache_hits, compiles_ok, compiles_failed, aot_hits;
     uint64_t launches_generic, launches_aot, launches_jit;
     double compile_ms_p50, compile_ms_p95, lookup_ns_p50;
-    /* LTimes tile mode 5: launches fed by TMA, and launches that fell back to
+    /* LTimes tile modes 5 and 6: launches fed by TMA, and launches that fell back to
      * the mode-4 kernel because `in` admitted no tensor map (innermost extent
      * not a multiple of 4 floats, or `in` not 16-byte aligned) */
     uint64_t launches_tma, launches_tma_fallback;
     /* grouped plans: launches of a plan's dispatcher issued from the host
      * (cj_group_plan_launch without CJ_PLAN_GRAPH, or a graph capture) */
     uint64_t launches_dispatch;
-    /* Expired bounded waits of the tensor-core LTimes kernels (tile modes 4
-     * and 5), summed over every run-time-compiled module and not yet cleared
+    /* Expired bounded waits of the tensor-core LTimes kernels (tile modes
+     * 4-6), summed over every run-time-compiled module and not yet cleared
      * through cj_handle_wait_timeouts(reset != 0).  A block whose wait expired
      * stopped early: any output written by a launch before a non-zero count
      * was seen is incomplete and must not be used.  Reading it synchronizes
@@ -272,10 +284,10 @@ cj_status cj_specialize_wait(cj_handle h, int timeout_ms);
  *     that must be 0 at launch (the kernel increments it once per chunk of
  *     items it hands out and once more per block).
  * T is double for CJ_F64, float for CJ_F32 and CJ_BF16 (fp32 state).
- * LTimes / LPlusTimes tiles of modes 3-5 (the f32 defaults) move in and out
+ * LTimes / LPlusTimes tiles of modes 3-6 (the f32 defaults) move in and out
  * in 16-byte vectors: both must be 16-byte aligned.
  * Never blocks on compilation.  Returns CJ_ERR_INVALID_ARG without launching
- * for null args, negative batch or misaligned mode 3-5 tensors; CJ_ERR_CUDA if
+ * for null args, negative batch or misaligned mode 3-6 tensors; CJ_ERR_CUDA if
  * the launch failed. */
 cj_status cj_launch(cj_handle h, void *const *args, int64_t batch, void *cuda_stream);
 
@@ -292,8 +304,8 @@ cj_status cj_handle_info(cj_handle h, char *key_hex, size_t cap, int *variant);
 cj_status cj_handle_regs(cj_handle h, int *regs_per_thread, int *static_smem);
 
 /* Bounded waits that expired in h's run-time-compiled kernel since the
- * module was loaded (or last reset).  The tcgen05 LTimes kernels (tile mode
- * 4) wait on shared-memory barriers for at most about a second each; a block
+ * module was loaded (or last reset).  The tcgen05 LTimes kernels (tile modes
+ * 4-6) wait on shared-memory barriers for at most about a second each; a block
  * whose wait expires stops, waits for its issued tensor-core work, frees its
  * tensor memory, adds one to this counter and returns, leaving its part of
  * `out` incomplete.  Synchronizes the device, then reads the counter of h's
@@ -355,6 +367,16 @@ cj_status cj_group_plan_launch(cj_group_plan p, const void *A_pool, void *X_pool
  * of the variant in use (0 until it is compiled).  Any output may be NULL. */
 cj_status cj_group_plan_dispatcher(cj_group_plan p, int32_t *state, int32_t *n_tickets, int32_t *threads,
                                    int32_t *blocks_per_sm);
+/* Pin the plan's dispatcher to variant `variant` (0 .. *variants - 1; the
+ * variants differ in the register cap of the launch bounds and, for f32, in
+ * the tile rule of the n >= 16 groups: rule 0 = 4 x 4 register blocks
+ * (mapping 5), rule 1 = 4 x 8 (mapping 8)).  Compiles it if needed (waits),
+ * and makes later launches (and graph captures) use it, as the plan's
+ * autotuner does with the fastest.  variant < 0 only reports *variants (may
+ * be NULL; 0 for a plan without a dispatcher).  CJ_ERR_INVALID_ARG: null
+ * plan, no dispatcher or variant out of range; CJ_ERR_COMPILE: it failed to
+ * compile; CJ_ERR_NO_DEVICE in compile-only mode. */
+cj_status cj_group_plan_use_dispatcher(cj_group_plan p, int32_t variant, int32_t *variants);
 /* Wait up to timeout_ms (negative: forever) for the instantiations of every
  * group of p to finish compiling.  CJ_OK: every group launches its
  * specialized kernel.  CJ_ERR_TIMEOUT: some are still compiling (launches

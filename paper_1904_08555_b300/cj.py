@@ -24,7 +24,8 @@ VARIANT_NAMES = ("generic", "aot", "jit")
 
 EXPORTS = ("cj_init", "cj_specialize", "cj_specialize_wait", "cj_launch", "cj_stats", "cj_handle_info",
            "cj_handle_regs", "cj_handle_wait_timeouts", "cj_group_plan_create", "cj_group_plan_launch",
-           "cj_group_plan_autotune", "cj_group_plan_wait", "cj_group_plan_dispatcher", "cj_group_plan_info",
+           "cj_group_plan_autotune", "cj_group_plan_wait", "cj_group_plan_dispatcher", "cj_group_plan_use_dispatcher",
+           "cj_group_plan_info",
            "cj_group_plan_destroy", "cj_measure_fma_peak", "cj_update_chain_uneven_noalloc", "cj_candidates",
            "cj_autotune", "cj_featurize", "cj_mlp_create", "cj_mlp_set_params", "cj_mlp_get_params",
            "cj_mlp_forward", "cj_mlp_grad", "cj_mlp_train_step", "cj_mlp_destroy", "cj_cost_model_use", "cj_cost_model_use_ensemble",
@@ -86,6 +87,7 @@ def load():
         L.cj_group_plan_wait.argtypes = [P, ctypes.c_int]
         L.cj_group_plan_dispatcher.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                                ctypes.POINTER(i32)]
+        L.cj_group_plan_use_dispatcher.argtypes = [P, i32, ctypes.POINTER(i32)]
         L.cj_group_plan_info.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i64)]
         L.cj_group_plan_destroy.argtypes = [P]
         L.cj_measure_fma_peak.argtypes = [i32, i32, P, ctypes.POINTER(ctypes.c_double)]
@@ -331,6 +333,12 @@ class GroupPlan:
                                                ctypes.byref(bp)), "cj_group_plan_dispatcher")
         return {"state": ("none", "compiling", "ready", "failed", "not used")[st.value], "tickets": nt.value,
                 "threads": th.value, "blocks_per_sm": bp.value}
+
+    def use_dispatcher(self, variant: int = -1) -> int:
+        """Pin the dispatcher to `variant` (compiled if needed); returns the number of variants."""
+        n = ctypes.c_int32(0)
+        _check(load().cj_group_plan_use_dispatcher(self.ptr, variant, ctypes.byref(n)), "cj_group_plan_use_dispatcher")
+        return n.value
 
     def autotune(self, A_pool, X_pool, stream=None, max_groups: int = 0, reps: int = 3) -> int:
         """Time every candidate tile per group (most expensive first) and keep the fastest; returns groups changed."""

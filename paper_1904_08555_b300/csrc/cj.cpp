@@ -214,6 +214,17 @@ int lt_axis_host(int lay, int s) {
     return order[lay][s];
 }
 bool is_lt(int k) { return k == CJ_K_LTIMES || k == CJ_K_LPLUSTIMES; }
+// Shared-memory operand stages of the mode-4 twin that a TMA-fed tcgen05
+// LTimes tile (mode 5 or 6) runs where `in` admits no tensor map: mode 5's
+// own stage count; two for mode 6, whose stages are in tensor memory.
+int lt_twin_stages(const cj_template_args &a) {
+    return ((a.tile[3] >> 16) & 0xf) == 6 ? 2 : (a.tile[3] >> 8) & 0xff;
+}
+// Its producer warps: mode 5's converter count (at most 8: register producers
+// split a stage's 8 direction quads over warps); 8 for mode 6.
+int lt_twin_producers(const cj_template_args &a) {
+    return ((a.tile[3] >> 16) & 0xf) == 6 ? 8 : std::min(a.tile[3] & 0xff, 8);
+}
 bool is_eig(int k) { return k == CJ_K_EIGEN_RECURRENCE; }
 bool is_mass(int k) { return k == CJ_K_MASS; }
 // Mass operator default: elements per block filling about 256 threads, both
@@ -278,11 +289,21 @@ void default_tile(int k, cj_template_args &a) {
     a.tile[0] = tg;
     a.tile[1] = ct / tg;
     if (a.dtype == CJ_F32 && v.m <= 128) {
-        // tcgen05 3xTF32, 128 columns, 2 operand stages, 8 converter/producer
-        // warps: fed by TMA with the deepest box ring (4, 3 or 2) that fits in
-        // shared memory (mode 5), else register producers (mode 4).  The box
-        // shape rule above keeps in's innermost box extent a multiple of 4.
+        // tcgen05 3xTF32, 128 columns, fed by TMA with the deepest box ring
+        // (6 .. 2) that fits in shared memory: operands in tensor memory (mode
+        // 6: 4 TMEM stages, 4 converter warps), else in shared memory (mode 5:
+        // 2 stages, 8 converter warps); else register producers (mode 4).
+        // The box shape rule above keeps in's innermost box extent a multiple
+        // of 4.
         a.tile[1] = 128 / tg;
+        const int npa = (cjg::lt_tc_np(v.m) + 31) / 32 * 32;
+        if (2 * npa + 64 * 4 <= 512 && cjg::lt_tc_smem(v.m, v.d, 2, tg, 128 / tg, v.lout) <= 220 * 1024)
+            for (int boxes = 6; boxes >= 2; --boxes)
+                if (cjg::lt_tc_smem(v.m, v.d, 0, tg, 128 / tg, v.lout, boxes) <= 220 * 1024) {
+                    a.tile[2] = 32 * (6 + 4);
+                    a.tile[3] = (boxes << 20) | (6 << 16) | (4 << 8) | 4;
+                    return;
+                }
         for (int boxes = 4; boxes >= 2; --boxes)
             if (cjg::lt_tc_smem(v.m, v.d, 2, tg, 128 / tg, v.lout, boxes) <= 220 * 1024) {
                 a.tile[2] = 32 * (6 + 8);
@@ -407,11 +428,11 @@ cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_
     }
     if (!is_lt(k)) {
         const int map = a.tile[0], ipb = a.tile[1];
-        if (map < 1 || map > 7) return fail(CJ_ERR_INVALID_ARG, "update chain mapping %d must be 1..7", map);
+        if (map < 1 || map > 8) return fail(CJ_ERR_INVALID_ARG, "update chain mapping %d must be 1..8", map);
         if (map == 6 && a.dtype != CJ_F32)
             return fail(CJ_ERR_INVALID_ARG, "mapping 6 (two rows per thread) needs f32");
-        if (map == 5 && (a.dtype != CJ_F32 || a.n < 8))
-            return fail(CJ_ERR_INVALID_ARG, "mapping 5 (register blocks) needs f32 and n >= 8");
+        if ((map == 5 || map == 8) && (a.dtype != CJ_F32 || a.n < 8))
+            return fail(CJ_ERR_INVALID_ARG, "mappings 5 and 8 (register blocks) need f32 and n >= 8");
         if ((map == 3 || map == 7) != (a.dtype == CJ_BF16))
             return fail(CJ_ERR_INVALID_ARG, "mappings 3 and 7 (bf16 tensor cores) are the mappings of dtype bf16");
         if (map == 7 && (ipb != 1 || (a.flags & CJ_FLAG_INJECT_WAIT_TIMEOUT)))
@@ -429,8 +450,8 @@ cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_
         const LtView v = lt_view(k, a);
         const int pipe = (a.tile[3] >> 20) & 0xf, mode = (a.tile[3] >> 16) & 0xf;
         const int r = (a.tile[3] >> 8) & 0xff, s = a.tile[3] & 0xff;
-        // modes 4 and 5 reuse the pipe field: producers' prefetch depth (0 = automatic) / TMA ring depth
-        if ((mode == 4 || mode == 5 ? pipe > 8 : pipe > 1) || (a.tile[3] >> 24))
+        // modes 4-6 reuse the pipe field: producers' prefetch depth (0 = automatic) / TMA ring depth
+        if ((mode >= 4 && mode <= 6 ? pipe > 8 : pipe > 1) || (a.tile[3] >> 24))
             return fail(CJ_ERR_INVALID_ARG, "LTimes tile flags 0x%x unknown", a.tile[3]);
         if (mode == 1 && (a.dtype != CJ_F64 || s != 8 || v.d % 4 || r < 1 || (tg * tz) % (8 * r) ||
                           (tg * tz / (8 * r)) * 32 != nt || nt > 1024))
@@ -461,14 +482,29 @@ cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_
                             "2 <= TMA boxes <= 8, in's innermost box extent a multiple of 4, m <= 128)",
                             a.tile[0], a.tile[1], a.tile[2], a.tile[3]);
         }
-        if (mode > 5) return fail(CJ_ERR_INVALID_ARG, "LTimes compute mode %d unknown", mode);
-        if ((a.flags & CJ_FLAG_INJECT_WAIT_TIMEOUT) && mode != 4 && mode != 5)
-            return fail(CJ_ERR_INVALID_ARG, "the wait-timeout hook applies to tile modes 4 and 5 only");
+        if (mode == 6) {
+            // TMEM operand stages of 64 columns after two accumulators, at most 512 columns in all
+            const int inner = lt_axis_host(v.lin, 2);
+            const int ib = inner == 0 ? 32 : inner == 1 ? tg : tz;
+            const int npa = (cjg::lt_tc_np(v.m) + 31) / 32 * 32;
+            if (a.dtype != CJ_F32 || tg * tz != 128 || r < 2 || 2 * npa + 64 * r > 512 || (s != 4 && s != 8) ||
+                nt != 32 * (6 + s) || v.m > 128 || pipe < 2 || ib % 4 ||
+                cjg::lt_tc_smem(v.m, v.d, 2, tg, tz, v.lout) > 220 * 1024)   // and its mode-4 twin fits
+                return fail(CJ_ERR_INVALID_ARG, "LTimes tcgen05 TMEM-operand tile {%d,%d,%d,0x%x} invalid (f32, TG * "
+                            "TZ = 128, converter warps 4/8, threads = 32 * (6 + converter warps), 2 <= TMA boxes "
+                            "<= 8, in's innermost box extent a multiple of 4, m <= 128, 2 <= stages and "
+                            "2 * ceil32(ceil16(m)) + 64 * stages <= 512 TMEM columns)",
+                            a.tile[0], a.tile[1], a.tile[2], a.tile[3]);
+        }
+        if (mode > 6) return fail(CJ_ERR_INVALID_ARG, "LTimes compute mode %d unknown", mode);
+        if ((a.flags & CJ_FLAG_INJECT_WAIT_TIMEOUT) && mode < 4)
+            return fail(CJ_ERR_INVALID_ARG, "the wait-timeout hook applies to tile modes 4-6 only");
         if (mode == 0 && (tg < 1 || tz < 1 || r < 1 || s < 1 || nt < 32 || nt > 1024 || (tg * tz) % r ||
                           (tg * tz / r) * ((v.m + s - 1) / s) != nt))
             return fail(CJ_ERR_INVALID_ARG, "LTimes tile {%d,%d,%d,%d} does not cover its block", a.tile[0],
                         a.tile[1], a.tile[2], a.tile[3]);
-        if ((mode == 5   ? cjg::lt_tc_smem(v.m, v.d, r, tg, tz, v.lout, pipe)
+        if ((mode == 6   ? cjg::lt_tc_smem(v.m, v.d, 0, tg, tz, v.lout, pipe)
+             : mode == 5 ? cjg::lt_tc_smem(v.m, v.d, r, tg, tz, v.lout, pipe)
              : mode == 4 ? cjg::lt_tc_smem(v.m, v.d, r, tg, tz, v.lout)
              : mode == 3 ? cjg::lt_direct_smem(v.m, v.d, tg * tz, esize(a.dtype), s)
                          : cjg::lt_smem(v.m, s, v.d, tg * tz, esize(a.dtype), pipe, mode)) > 220 * 1024)
@@ -536,11 +572,12 @@ void spec_geometry(const cj_handle_s *h, Impl &s) {
         const LtView v = lt_view(h->kernel, a);
         const int mode = (a.tile[3] >> 16) & 0xf;
         s.threads = a.tile[2];
-        if (mode == 5) {   // and its mode-4 twin
-            s.threads2 = 32 * (5 + std::min(a.tile[3] & 0xff, 8));
-            s.smem2 = (size_t)cjg::lt_tc_smem(v.m, v.d, (a.tile[3] >> 8) & 0xff, a.tile[0], a.tile[1], v.lout);
+        if (mode == 5 || mode == 6) {   // and its mode-4 twin
+            s.threads2 = 32 * (5 + lt_twin_producers(a));
+            s.smem2 = (size_t)cjg::lt_tc_smem(v.m, v.d, lt_twin_stages(a), a.tile[0], a.tile[1], v.lout);
         }
-        s.smem = mode == 5   ? (size_t)cjg::lt_tc_smem(v.m, v.d, (a.tile[3] >> 8) & 0xff, a.tile[0], a.tile[1], v.lout,
+        s.smem = mode == 6   ? (size_t)cjg::lt_tc_smem(v.m, v.d, 0, a.tile[0], a.tile[1], v.lout, (a.tile[3] >> 20) & 0xf)
+                 : mode == 5 ? (size_t)cjg::lt_tc_smem(v.m, v.d, (a.tile[3] >> 8) & 0xff, a.tile[0], a.tile[1], v.lout,
                                                        (a.tile[3] >> 20) & 0xf)
                  : mode == 4 ? (size_t)cjg::lt_tc_smem(v.m, v.d, (a.tile[3] >> 8) & 0xff, a.tile[0], a.tile[1], v.lout)
                  : mode == 3 ? (size_t)cjg::lt_direct_smem(v.m, v.d, a.tile[0] * a.tile[1], es, a.tile[3] & 0xff)
@@ -553,15 +590,16 @@ void spec_geometry(const cj_handle_s *h, Impl &s) {
     }
 }
 
-// Mode 5 also compiles its mode-4 twin (register producers) into the module.
+// Modes 5 and 6 also compile their mode-4 twin (register producers) into the
+// module.
 std::string fallback_name_expression(const cj_handle_s *h) {
     const cj_template_args &a = h->a;
-    if (!is_lt(h->kernel) || ((a.tile[3] >> 16) & 0xf) != 5) return "";
+    const int mode = (a.tile[3] >> 16) & 0xf;
+    if (!is_lt(h->kernel) || (mode != 5 && mode != 6)) return "";
     const LtView v = lt_view(h->kernel, a);
     char buf[256];
-    // register producers split a stage's 8 direction quads over warps: at most 8 of them
     snprintf(buf, sizeof buf, "cj::ltimes_tc<%d, %d, %d, %d, %d, %d, %d, %d, 0, 0, %d, %d>", v.m, v.d, v.lin, v.lout,
-             a.tile[0], a.tile[1], (a.tile[3] >> 8) & 0xff, std::min(a.tile[3] & 0xff, 8), v.acc,
+             a.tile[0], a.tile[1], lt_twin_stages(a), lt_twin_producers(a), v.acc,
              (a.flags & CJ_FLAG_INJECT_WAIT_TIMEOUT) ? 1 : 0);
     return buf;
 }
@@ -592,6 +630,10 @@ std::string name_expression(const cj_handle_s *h) {
                      v.lin, v.lout, a.tile[0], a.tile[1], (a.tile[3] >> 8) & 0xff, a.tile[3] & 0xff,
                      mode == 4 ? (a.tile[3] >> 20) & 0xf : 0, mode == 5 ? (a.tile[3] >> 20) & 0xf : 0, v.acc,
                      (a.flags & CJ_FLAG_INJECT_WAIT_TIMEOUT) ? 1 : 0);
+        else if (mode == 6)   // TMA ring depth in the pipe field, operand stages in TMEM
+            snprintf(buf, sizeof buf, "cj::ltimes_tc<%d, %d, %d, %d, %d, %d, %d, %d, 0, %d, %d, %d, 1>", v.m, v.d,
+                     v.lin, v.lout, a.tile[0], a.tile[1], (a.tile[3] >> 8) & 0xff, a.tile[3] & 0xff,
+                     (a.tile[3] >> 20) & 0xf, v.acc, (a.flags & CJ_FLAG_INJECT_WAIT_TIMEOUT) ? 1 : 0);
         else if (((a.tile[3] >> 16) & 0xf) == 3)
             snprintf(buf, sizeof buf, "cj::ltimes_direct<%s, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d>", ctype(a.dtype),
                      v.m, v.d, v.lin, v.lout, a.tile[0], a.tile[1], a.tile[2], (a.tile[3] >> 8) & 0xff,
@@ -849,17 +891,19 @@ void plan_free(cj_group_plan_s *p) {
 // f32 for the n < 16 groups of a bf16 plan), for blocks of `block` threads:
 // bf16 tensor-core panels (mapping 3); f32 n >= 8 register blocks (mapping
 // 5); n <= 4 one instance per thread (mapping 2); otherwise one row per
-// thread (mapping 1).  `rule` selects among tile rules (one so far).  As many instances per chunk as fill the block (at
-// most 256), fewer where shared memory would exceed 160 KiB.
-std::array<int, 2> dispatch_tile(int dtype, int n, int block, int rule = 0) {
+// thread (mapping 1).  Rule 1 differs for f32 n >= 16: 4 x 8 register
+// blocks (mapping 8).  As many instances per chunk as fill the block (at
+// most 256), fewer where shared memory would exceed `smem_cap` bytes.
+std::array<int, 2> dispatch_tile(int dtype, int n, int block, int rule, long smem_cap) {
     const int es = esize(dtype);
     int map, tpi;
     if (dtype == CJ_BF16) map = 3, tpi = ((n + 15) / 16) * 32;
+    else if (dtype == CJ_F32 && n >= 16 && rule == 1) map = 8, tpi = ((n + 3) / 4) * ((n + 7) / 8);
     else if (dtype == CJ_F32 && n >= 8) map = 5, tpi = ((n + 3) / 4) * ((n + 3) / 4);
     else if (n <= 4) map = 2, tpi = 1;
     else map = 1, tpi = n;
     int ipb = std::max(1, std::min(256, block / tpi));
-    while (ipb > 1 && (cjg::chain_threads(n, map, ipb) > block || cjg::chain_smem(n, map, ipb, es) > 160 * 1024))
+    while (ipb > 1 && (cjg::chain_threads(n, map, ipb) > block || cjg::chain_smem(n, map, ipb, es) > smem_cap))
         --ipb;
     return {map, ipb};
 }
@@ -923,6 +967,13 @@ struct DispVariant {
     int minb, rule;
 };
 
+// Shared memory a chunk of variant v may take: what minb blocks can hold
+// together on one SM (228 KiB, less 1 KiB reserved per block and a
+// margin for the kernel's static shared memory), at most 160 KiB.
+long dispatch_smem_cap(DispVariant v) {
+    return std::min<long>(160 * 1024, 233472 / v.minb - 2048);
+}
+
 std::string dispatcher_source(const cj_group_plan_s *p, DispVariant v, long *smem_out) {
     const int minb = v.minb;
     constexpr int kBlock = kDispatchBlock;
@@ -939,7 +990,7 @@ std::string dispatcher_source(const cj_group_plan_s *p, DispVariant v, long *sme
     for (size_t g = 0; g < p->groups.size(); ++g) {
         const auto &gr = p->groups[g];
         const int gdt = (p->dtype == CJ_BF16 && gr.n < 16) ? CJ_F32 : p->dtype;
-        const auto t = dispatch_tile(gdt, gr.n, kBlock, v.rule);
+        const auto t = dispatch_tile(gdt, gr.n, kBlock, v.rule, dispatch_smem_cap(v));
         smem = std::max(smem, cjg::chain_smem(gr.n, t[0], t[1], esize(gdt)));
         src += "        case " + std::to_string(g) + ": grouped_chunk_call<" + ct + ", " + std::to_string(gr.n) +
                ", " + std::to_string(t[0]) + ", " + std::to_string(t[1]) + ", " + std::to_string(kBlock) +
@@ -982,9 +1033,12 @@ cj_handle_s *request_dispatcher(const cj_group_plan_s *p, DispVariant v) {
 // by the plan's autotuner.  FP32 bodies fit 128 registers (two blocks of 256
 // threads) without spilling and 80 (three) with small spills in the n < 8
 // bodies; BF16 tensor-core bodies want more; FP64 rows of X need up to 255.
+// FP32 starts with tile rule 1 (4 x 8 register blocks for n >= 16: 1.18 ms
+// against 1.39 ms for rule 0 on the 10,000-instance batch) and also tries
+// rule 0.
 std::vector<DispVariant> dispatcher_variants(int dtype) {
     if (dtype == CJ_F64) return {{1, 0}};
-    if (dtype == CJ_F32) return {{2, 0}, {3, 0}};
+    if (dtype == CJ_F32) return {{2, 1}, {3, 1}, {2, 0}, {3, 0}};
     return {{2, 0}, {1, 0}};
 }
 
@@ -1001,7 +1055,7 @@ cj_status make_dispatch_form(cj_group_plan_s *p, DispVariant v, cj_group_plan_s:
     for (size_t g = 0; g < p->groups.size(); ++g) {
         const auto &gr = p->groups[g];
         const int gdt = (p->dtype == CJ_BF16 && gr.n < 16) ? CJ_F32 : p->dtype;
-        const auto t = dispatch_tile(gdt, gr.n, kDispatchBlock, v.rule);
+        const auto t = dispatch_tile(gdt, gr.n, kDispatchBlock, v.rule, dispatch_smem_cap(v));
         const double per = 2.0 * gr.n * gr.n * gr.n + 2.0 * gr.n * gr.n;
         for (int64_t c = 0; c < gr.n_items; c += t[1]) {
             Tk k{0.0, gr.first_item + c, (int)g, (int)std::min<int64_t>(t[1], gr.n_items - c)};
@@ -1241,11 +1295,11 @@ CJ_API cj_status cj_launch(cj_handle h, void *const *args, int64_t batch, void *
     for (int i = 0; i < (is_lt(h->kernel) ? 5 : h->kernel == CJ_K_UPDATE_CHAIN ? 3 : 4); ++i)   // Eigen: 4
         if (!args[i]) return fail(CJ_ERR_INVALID_ARG, "argument %d is null", i);
     if (is_lt(h->kernel) && !(h->a.flags & CJ_FLAG_GENERIC) && ((h->a.tile[3] >> 16) & 0xf) >= 3) {
-        // tile modes 3-5 move `in` and `out` in 16-byte vectors
+        // tile modes 3-6 move `in` and `out` in 16-byte vectors
         const uintptr_t in = reinterpret_cast<uintptr_t>(*reinterpret_cast<void *const *>(args[1]));
         const uintptr_t out = reinterpret_cast<uintptr_t>(*reinterpret_cast<void *const *>(args[2]));
         if ((in | out) & 15)
-            return fail(CJ_ERR_INVALID_ARG, "tile modes 3-5 need 16-byte aligned in and out tensors");
+            return fail(CJ_ERR_INVALID_ARG, "tile modes 3-6 need 16-byte aligned in and out tensors");
     }
     if (G.compile_only) return fail(CJ_ERR_NO_DEVICE, "library initialised in compile-only mode");
     const Impl *im = h->impl.load(std::memory_order_acquire);
@@ -1339,22 +1393,22 @@ CJ_API cj_status cj_launch(cj_handle h, void *const *args, int64_t batch, void *
         } else {
             const long long ntiles = ((Gx + a.tile[0] - 1) / a.tile[0]) * ((Zx + a.tile[1] - 1) / a.tile[1]);
             const int mode = (a.tile[3] >> 16) & 0xf;
-            if (mode == 4 || mode == 5) {
-                // tcgen05 kernels take a TMA tensor map of `in` (unused in mode 4); mode 5
-                // falls back to its mode-4 twin when `in` admits none
+            if (mode >= 4 && mode <= 6) {
+                // tcgen05 kernels take a TMA tensor map of `in` (unused in mode 4); modes 5
+                // and 6 fall back to their mode-4 twin when `in` admits none
                 CUtensorMap map;
                 memset(&map, 0, sizeof map);
                 CUfunction fn = im->fn;
                 int threads = im->threads, bps = im->blocks_per_sm;
                 size_t smem = im->smem;
-                const bool tma = mode == 5 && lt_tensor_map(&map, in, v.lin, v.d, Gx, Zx, a.tile[0], a.tile[1]);
-                if (mode == 5 && !tma) {
+                const bool tma = mode >= 5 && lt_tensor_map(&map, in, v.lin, v.d, Gx, Zx, a.tile[0], a.tile[1]);
+                if (mode >= 5 && !tma) {
                     fn = im->fn2;
                     threads = im->threads2;
                     smem = im->smem2;
                     bps = im->blocks2;
                 }
-                if (mode == 5) (tma ? G.l_tma : G.l_tma_fb)++;
+                if (mode >= 5) (tma ? G.l_tma : G.l_tma_fb)++;
                 const unsigned grid = (unsigned)std::min(ntiles, (long long)G.num_sms * bps);
                 void *p[] = {&L, &in, &out, &Gx, &Zx, &map};
                 r = drv.LaunchKernel(fn, grid, 1, 1, threads, 1, 1, (unsigned)smem, st, p, nullptr);
@@ -1788,6 +1842,31 @@ CJ_API cj_status cj_group_plan_dispatcher(cj_group_plan p, int32_t *state, int32
     if (n_tickets) *n_tickets = p->n_tickets;
     if (threads) *threads = p->disp ? p->disp->a.tile[0] : 0;
     if (blocks_per_sm) *blocks_per_sm = dispatcher_ready(p) ? p->disp->spec.blocks_per_sm : 0;
+    return CJ_OK;
+}
+
+CJ_API cj_status cj_group_plan_use_dispatcher(cj_group_plan p, int32_t variant, int32_t *variants) {
+    if (!p) return fail(CJ_ERR_INVALID_ARG, "null plan");
+    const std::vector<DispVariant> vs = dispatcher_variants(p->dtype);
+    if (variants) *variants = p->disp ? (int32_t)vs.size() : 0;
+    if (variant < 0) return CJ_OK;
+    if (!p->disp) return fail(CJ_ERR_INVALID_ARG, "plan has no dispatcher (CJ_FLAG_GENERIC)");
+    if (variant >= (int32_t)vs.size()) return fail(CJ_ERR_INVALID_ARG, "dispatcher variant %d out of range", variant);
+    if (G.compile_only) return fail(CJ_ERR_NO_DEVICE, "compile-only mode");
+    // forms are kept in the order of dispatcher_variants: create the missing ones up to `variant`
+    for (size_t i = p->disp_forms.size(); i <= (size_t)variant; ++i) {
+        cj_group_plan_s::DispForm f;
+        const cj_status rf = make_dispatch_form(p, vs[i], &f);
+        if (rf != CJ_OK) {
+            if (f.d_tickets) cudaFree(f.d_tickets);
+            return rf;
+        }
+        p->disp_forms.push_back(f);
+    }
+    const cj_group_plan_s::DispForm f = p->disp_forms[(size_t)variant];
+    if (cj_specialize_wait(f.h, -1) != CJ_OK) return fail(CJ_ERR_COMPILE, "dispatcher variant %d failed to compile", variant);
+    use_dispatch_form(p, f);
+    p->use_dispatcher = true;
     return CJ_OK;
 }
 

@@ -17,12 +17,17 @@ enum { D_F64 = 0, D_F32 = 1, D_BF16 = 2 };
 // issues on the same FP64 pipe as DFMA and is not faster (measured).
 constexpr bool chain_dmma_ok(int n, int dtype) { return dtype == D_F64 && n % 8 == 0 && n <= 32; }
 // FP32 n >= 9: two rows per thread (mapping 6), 128 / ceil(n / 2) instances.
+// f32 n >= 32: 4 x 8 register blocks (mapping 8), about 128 threads per
+// block (t = ceil(n / 4) ceil(n / 8) threads per instance).
 constexpr int chain_default_map(int n, int dtype) {
-    return dtype == D_BF16 ? 3 : n <= 4 ? 2 : (dtype == D_F32 && n >= 9) ? 6 : 1;
+    return dtype == D_BF16 ? 3 : n <= 4 ? 2 : (dtype == D_F32 && n >= 32) ? 8 : (dtype == D_F32 && n >= 9) ? 6 : 1;
 }
+constexpr int chain_m8_tpi(int n) { return (n + 3) / 4 * ((n + 7) / 8); }
 constexpr int chain_default_ipb(int n, int dtype) {
     return dtype == D_BF16 ? (128 / ((n + 15) / 16 * 16) > 1 ? 128 / ((n + 15) / 16 * 16) : 1)
          : n <= 4 ? 128
+         : (dtype == D_F32 && n >= 32) ? ((128 + chain_m8_tpi(n) / 2) / chain_m8_tpi(n) > 1
+                                              ? (128 + chain_m8_tpi(n) / 2) / chain_m8_tpi(n) : 1)
          : (dtype == D_F32 && n >= 9) ? (128 / ((n + 1) / 2) > 1 ? 128 / ((n + 1) / 2) : 1)
          : n <= 32 ? 256 / n : (128 / n > 1 ? 128 / n : 1);
 }

@@ -27,10 +27,12 @@ CJ_HD constexpr int inst_pitch(int nn) { return nn | 1; }
 
 // Threads per block of the update chain kernels: mapping 2 one thread per
 // instance, mapping 4 one warp per 8 rows, mapping 3 one warp per 16 rows
-// (padded), mapping 5 one thread per 4x4 block, mapping 6 one thread per two
-// rows, mapping 1 one thread per row.
+// (padded), mapping 5 one thread per 4x4 block, mapping 8 one thread per 4x8
+// block (rows padded to 4, columns to 8), mapping 6 one thread per two rows,
+// mapping 1 one thread per row.
 CJ_HD constexpr int chain_threads(int n, int mapping, int ipb) {
     return mapping == 7   ? 128
+           : mapping == 8 ? ((ipb * ((n + 3) / 4) * ((n + 7) / 8) + 31) / 32) * 32
            : mapping == 2 ? ipb
            : mapping == 6 ? ((ipb * ((n + 1) / 2) + 31) / 32) * 32
            : mapping == 5 ? ((ipb * ((n + 3) / 4) * ((n + 3) / 4) + 31) / 32) * 32
@@ -42,12 +44,15 @@ CJ_HD constexpr int chain_threads(int n, int mapping, int ipb) {
 // Rows of X kept in shared memory (instead of registers) above this size.
 CJ_HD constexpr int chain_reg_rows_max(int esize) { return esize == 8 ? 32 : 48; }
 
-// Row length of A_b in shared memory: mappings 1 and 6 in FP32 pad each row
-// to a multiple of 4 so a thread reads A with 16-byte vectors (one
+// Row length of A_b in shared memory: mappings 1, 5 and 6 in FP32 pad each
+// row to a multiple of 4 so a thread reads A with 16-byte vectors (one
 // shared-memory load per four fused multiply-adds per row of X the thread
-// owns); every other mapping keeps rows of n.
+// owns), mapping 8 to a multiple of 8 (its column blocks); every other
+// mapping keeps rows of n.
 CJ_HD constexpr int chain_arow(int n, int mapping, int esize) {
-    return ((mapping == 1 || mapping == 5 || mapping == 6) && esize == 4) ? (n + 3) / 4 * 4 : n;
+    return (mapping == 8 && esize == 4)                                           ? (n + 7) / 8 * 8
+           : ((mapping == 1 || mapping == 5 || mapping == 6) && esize == 4) ? (n + 3) / 4 * 4
+                                                                            : n;
 }
 
 // Elements between consecutive staged instances of the specialized kernels.
@@ -66,6 +71,8 @@ CJ_HD constexpr long chain_smem(int n, int mapping, int ipb, int esize) {
         ? (long)ipb * inst_pitch(n * n) * esize
         : mapping == 5
         ? (long)ipb * chain_pitch(n, 5, esize) * esize + (long)ipb * ((n + 3) / 4 * 4) * ((n + 3) / 4 * 4 + 4) * esize
+        : mapping == 8   // A, then X^T: (n padded to 8) rows of (n padded to 4) + 4
+        ? (long)ipb * chain_pitch(n, 8, esize) * esize + (long)ipb * ((n + 7) / 8 * 8) * ((n + 3) / 4 * 4 + 4) * esize
         : (long)ipb * chain_pitch(n, mapping, esize) * esize +
               (mapping == 1 && n > chain_reg_rows_max(esize)
                    ? (long)chain_threads(n, 1, ipb) * xrow_pitch(n) * esize

@@ -481,7 +481,17 @@ ltimes_direct(const T* __restrict__ L, const T* __restrict__ in, T* __restrict__
 // groups SBO = 1168 B apart; the 16-byte pads make both write patterns
 // conflict-free).  L's hi/lo parts are laid out once per block with LBO =
 // 128 B and SBO = DP*32 B.  Two accumulators of NPA
-// columns let the epilogue of one tile overlap the MMAs of the next.  Every
+// columns let the epilogue of one tile overlap the MMAs of the next.
+//
+// AT = 1 (mode 6) keeps the A operand in tensor memory instead: converter
+// warp w reads its tile rows (TMEM lanes 32 (w % 4) ..) from the TMA box,
+// splits them and writes tf32 hi and lo with tcgen05.st into a STAGES-deep
+// ring of TMEM stages (32 hi + 32 lo columns each, after the accumulators);
+// the MMAs read A from tensor memory and only B (L) from shared memory.  Per
+// 4-byte element of `in` shared memory then carries the TMA write and one
+// converter read (8 bytes) instead of those plus the operand writes and the
+// three MMAs' A reads (28 bytes), the traffic that bounds the shared-memory
+// form.  Every
 // wait is bounded (about a second): on expiry the block raises its abort
 // flag, counts the event in cj_wait_timeouts, drains its MMAs, frees TMEM
 // and returns.
@@ -541,6 +551,16 @@ __device__ __forceinline__ void lt_tc_mma_tf32(unsigned d_tmem, unsigned long lo
         "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
         : "memory");
 }
+// The same with A read from tensor memory (a_tmem: lane 0, the first of the
+// 8 columns that hold this K step's tf32 elements); B from shared memory.
+__device__ __forceinline__ void lt_tc_mma_tf32_ts(unsigned d_tmem, unsigned a_tmem, unsigned long long b,
+                                                  unsigned idesc, unsigned accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
 // A TMA tensor map (the driver's 128-byte CUtensorMap), passed by value as a
 // __grid_constant__ kernel parameter.
 struct alignas(64) cj_tmap {
@@ -577,6 +597,17 @@ __device__ __forceinline__ void lt_tmem_ld16(unsigned taddr, float (&v)[16]) {
                  : "memory");
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Columns c..c+15 of this thread's TMEM lane from registers (warp w writes
+// lanes 32(w%4)..); complete once tcgen05.wait::st returns.
+__device__ __forceinline__ void lt_tmem_st16(unsigned taddr, const unsigned (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
 }
 
 // Store the staged out box of one tile (see ltimes_tc): units of V
@@ -637,14 +668,16 @@ __device__ __forceinline__ void lt_tc_store_mbox(float* __restrict__ out, const 
 }
 
 template <int M, int D, int LIN, int LOUT, int TG, int TZ, int STAGES, int NPROD, int PF_ = 0, int RAWST = 0,
-          int ACC = 0, int INJECT_TIMEOUT = 0>
+          int ACC = 0, int INJECT_TIMEOUT = 0, int AT = 0>
 __global__ void __maxnreg__(cjg::lt_tc_maxreg(NPROD + (RAWST > 0)))
 ltimes_tc(const float* __restrict__ L, const float* __restrict__ in, float* __restrict__ out, long long G, long long Z,
           const __grid_constant__ cj_tmap tmap) {
     constexpr int BM = 128, KB = 32;                 // tile columns, directions per stage
     constexpr int NP = cjg::lt_tc_np(M), DP = cjg::lt_tc_dp(D), NKB = DP / KB;
     constexpr int NPA = (NP + 31) / 32 * 32;         // TMEM columns per accumulator
-    constexpr int TCOLS = 2 * NPA <= 32 ? 32 : 2 * NPA <= 64 ? 64 : 2 * NPA <= 128 ? 128 : 2 * NPA <= 256 ? 256 : 512;
+    constexpr int ACOLS = AT ? STAGES * 2 * KB : 0;   // TMEM operand stages (AT): hi and lo, after the accumulators
+    constexpr int TUSE = 2 * NPA + ACOLS;
+    constexpr int TCOLS = TUSE <= 32 ? 32 : TUSE <= 64 ? 64 : TUSE <= 128 ? 128 : TUSE <= 256 ? 256 : 512;
     constexpr int PT = 32 * NPROD;                   // producer (converter) threads
     constexpr int PW0 = RAWST > 0 ? 6 : 5;           // first producer warp (warp 5 issues TMA in mode 5)
     constexpr unsigned RAW_BYTES = BM * KB * 4u;     // one TMA box of `in`
@@ -658,6 +691,9 @@ ltimes_tc(const float* __restrict__ L, const float* __restrict__ in, float* __re
     // register producers split the 8 direction quads of a stage over warps; converters only need whole chunks
     static_assert(TG * TZ == BM && NP <= 256 && CH * PT * 4 == BM * KB && (RAWST > 0 ? 32 : 8) % NPROD == 0,
                   "tcgen05 LTimes tile");
+    // TMEM operands: fed by TMA, each lane quarter's warps split a stage's directions, all stages fit TMEM
+    static_assert(!AT || (RAWST > 0 && NPROD % 4 == 0 && KB % (NPROD / 4 * 8) == 0 && TUSE <= 512),
+                  "tcgen05 LTimes tile with tensor-memory operands");
     // a TMA box starts on a 16-byte boundary: its innermost extent (and so
     // every innermost coordinate, a multiple of it) is a multiple of 4 floats
     static_assert(RAWST == 0 || (lt_axis(LIN, 2) == 0 ? KB : lt_axis(LIN, 2) == 1 ? TG : TZ) % 4 == 0,
@@ -692,9 +728,10 @@ ltimes_tc(const float* __restrict__ L, const float* __restrict__ in, float* __re
     unsigned char* base = cj_smem + ((1024u - (lt_smem_u32(cj_smem) & 1023u)) & 1023u);
     unsigned char* raw = base;                                    // RAWST TMA boxes (mode 5)
     unsigned char* ring = base + RAWST * RAW_BYTES;               // STAGES x [A_hi | A_lo]
-    float* sLhi = reinterpret_cast<float*>(ring + STAGES * STAGE_BYTES);
-    float* sLlo = reinterpret_cast<float*>(ring + STAGES * STAGE_BYTES + LBYTES);
-    float* sO = reinterpret_cast<float*>(ring + STAGES * STAGE_BYTES + 2 * LBYTES);
+    constexpr unsigned RING_BYTES = AT ? 0u : STAGES * STAGE_BYTES;   // the operand ring is in TMEM when AT
+    float* sLhi = reinterpret_cast<float*>(ring + RING_BYTES);
+    float* sLlo = reinterpret_cast<float*>(ring + RING_BYTES + LBYTES);
+    float* sO = reinterpret_cast<float*>(ring + RING_BYTES + 2 * LBYTES);
     const unsigned ring_u = lt_smem_u32(ring), lhi_u = lt_smem_u32(sLhi), llo_u = lt_smem_u32(sLlo);
     const unsigned bar_u = lt_smem_u32(bars);
     auto full_bar = [&](int s) { return bar_u + 8u * s; };
@@ -770,7 +807,69 @@ ltimes_tc(const float* __restrict__ L, const float* __restrict__ in, float* __re
     auto row_z = [&](int r) { return G_FASTER ? r / TG : r % TZ; };
 
     const long long n_it = (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x * NKB;   // this block's stages
-    if (RAWST > 0 && warp >= PW0) {
+    if (AT && warp >= PW0) {
+        if constexpr (AT) {
+            // ---------------- converters, TMEM operands (mode 6) ----------------
+            // Warp w owns tile rows (TMEM lanes) 32 (w % 4) + lane; the NPROD / 4
+            // warps of one lane quarter take KP consecutive directions of each
+            // raw box.  d fastest: 16-byte chunks of the row's 128-byte swizzled
+            // run; otherwise one float per direction, consecutive rows across the
+            // warp.  Each value is split into tf32 hi/lo and both go to TMEM
+            // stage s with tcgen05.st (hi in its first KB columns, lo in the next).
+            constexpr int KP = KB / (NPROD / 4);
+            constexpr int AI = lt_axis(LIN, 2), AM = lt_axis(LIN, 1);
+            constexpr int BI = AI == 0 ? KB : AI == 1 ? TG : TZ, BMID = AM == 0 ? KB : AM == 1 ? TG : TZ;
+            constexpr int SB0 = AI == 0 ? 1 : AM == 0 ? BI : BI * BMID;   // raw element strides of d, g, z
+            constexpr int SB1 = AI == 1 ? 1 : AM == 1 ? BI : BI * BMID;
+            constexpr int SB2 = AI == 2 ? 1 : AM == 2 ? BI : BI * BMID;
+            const int quarter = warp & 3, part = (warp - PW0) >> 2;
+            const int r = 32 * quarter + lane;
+            const unsigned trow = tmem + ((unsigned)(32 * quarter) << 16) + 2 * NPA + part * KP;
+            const int roff = D_FAST ? 0 : row_g(r) * SB1 + row_z(r) * SB2;
+            for (long long i = 0; i < n_it; ++i) {
+                const int rs = (int)(i % RAWST), s = (int)(i % STAGES);
+                if (!lt_mbar_wait(rawf_bar(rs), (unsigned)((i / RAWST) & 1), abort_v) ||
+                    !lt_mbar_wait(empty_bar(s), (unsigned)((i / STAGES) & 1) ^ 1u, abort_v)) {
+                    give_up();
+                    break;
+                }
+                lt_tc_fence_after();
+                const unsigned char* rb = raw + rs * RAW_BYTES;
+                float x[KP];
+                if constexpr (D_FAST) {
+#pragma unroll
+                    for (int c = 0; c < KP / 4; ++c) {
+                        const int kq = part * (KP / 4) + c;
+                        const float4 v = *reinterpret_cast<const float4*>(rb + r * 128 + ((kq ^ (r & 7)) << 4));
+                        x[4 * c] = v.x;
+                        x[4 * c + 1] = v.y;
+                        x[4 * c + 2] = v.z;
+                        x[4 * c + 3] = v.w;
+                    }
+                } else {
+                    const float* rf = reinterpret_cast<const float*>(rb) + roff;
+#pragma unroll
+                    for (int j = 0; j < KP; ++j) x[j] = rf[(part * KP + j) * SB0];
+                }
+                lt_mbar_arrive(rawe_bar(rs));   // the box is read: the TMA lane may refill it
+                const unsigned ts = trow + (unsigned)(s * 2 * KB);
+#pragma unroll
+                for (int h = 0; h < KP; h += 16) {
+                    unsigned vh[16], vl[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        vh[j] = to_tf32(x[h + j]);
+                        vl[j] = to_tf32(x[h + j] - __uint_as_float(vh[j]));
+                    }
+                    lt_tmem_st16(ts + h, vh);
+                    lt_tmem_st16(ts + KB + h, vl);
+                }
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                lt_tc_fence_before();
+                if (!INJECT_TIMEOUT) lt_mbar_arrive(full_bar(s));   // the hook: never signal a filled stage
+            }
+        }
+    } else if (RAWST > 0 && warp >= PW0) {
         // ---------------- converters (mode 5) ----------------
         // Raw box i (in's storage order; 128-byte swizzled rows when d is
         // fastest) -> tf32 hi/lo K-major operand stage.  d fastest: chunk q is
@@ -988,6 +1087,20 @@ ltimes_tc(const float* __restrict__ L, const float* __restrict__ in, float* __re
                         break;
                     }
                     lt_tc_fence_after();
+                    if constexpr (AT) {
+                        const unsigned acol = tmem + 2 * NPA + (unsigned)(s * 2 * KB);   // hi; lo KB columns on
+#pragma unroll
+                        for (int j = 0; j < KB / 8; ++j) {
+                            const unsigned bo = (kb * (KB / 4) + 2 * j) * 128u;
+                            const unsigned long long dbh = lt_tc_desc(lhi_u + bo, 128u, B_SBO);
+                            const unsigned long long dbl = lt_tc_desc(llo_u + bo, 128u, B_SBO);
+                            lt_tc_mma_tf32_ts(dt, acol + KB + 8 * j, dbh, IDESC, (kb | j) != 0);
+                            lt_tc_mma_tf32_ts(dt, acol + 8 * j, dbl, IDESC, 1u);
+                            lt_tc_mma_tf32_ts(dt, acol + 8 * j, dbh, IDESC, 1u);
+                        }
+                        lt_tc_commit(empty_bar(s));   // the TMEM stage is free once these MMAs have read it
+                        continue;
+                    }
                     const unsigned ahi = ring_u + s * STAGE_BYTES, alo = ahi + HALF;
 #pragma unroll
                     for (int j = 0; j < KB / 8; ++j) {

@@ -422,6 +422,84 @@ __device__ __forceinline__ void chain_block(T* sA, int ninst, int tid, StepsOf s
                 const int i = e / N, j = e - i * N;
                 sA[inst * P + (LAYOUT == 0 ? i * N + j : j * N + i)] = xt[j * XTP + i];
             }
+    } else if constexpr (MAP == 8) {
+        // FP32 register blocks of 4 rows x 8 columns of P = X A: thread
+        // (inst, rb, cb) owns rows 4rb..4rb+3 and columns 8cb..8cb+7, so each
+        // k step of the product is one 16-byte read of X^T and two of A for
+        // 32 fused multiply-adds (mapping 5: two reads for 16).  Rows are
+        // padded to NR (a multiple of 4), columns to NC (a multiple of 8); X^T
+        // is kept in shared memory as xt[l][r] with NC rows of pitch NR + 4.
+        // A's padded columns are zeroed here, so P's padded columns, and with
+        // them X's padded rows and columns, stay exactly zero; the product
+        // runs over the N real k only.  All threads of the block run the
+        // longest instance's step count so every barrier is uniform.
+        static_assert(sizeof(T) == 4 && N >= 8, "mapping 8 is FP32 with N >= 8");
+        constexpr int NR = (N + 3) / 4 * 4, NC = (N + 7) / 8 * 8;
+        constexpr int P = cjg::chain_pitch(N, 8, 4), AR = cjg::chain_arow(N, 8, 4);
+        constexpr int B4 = NR / 4, B8 = NC / 8, TPI = B4 * B8, XTP = NR + 4;
+        static_assert(AR == NC, "mapping 8 stages A with rows of NC");
+        T* xt_all = sA + IPB * P;
+        const int inst = tid / TPI, w = tid - inst * TPI;
+        const int rb = w % B4, cb = w / B4;
+        const bool active = inst < ninst;
+        int kmax = 0;
+        for (int q = 0; q < ninst; ++q) kmax = max(kmax, steps_of(q));
+        const int steps = active ? steps_of(inst) : 0;
+        const T cc = active ? c_of(inst) : T(0);
+        T* xt = xt_all + (active ? inst : 0) * NC * XTP;
+        T* a_w = sA + (active ? inst : 0) * P;
+        const T* a = a_w;
+        if (active) {
+            for (int e = w; e < NC * NR; e += TPI) {
+                const int l = e / NR, r = e - l * NR;
+                xt[l * XTP + r] = (l == r && l < N) ? T(1) : T(0);
+            }
+            if constexpr (NC != N)
+                for (int e = w; e < N * (NC - N); e += TPI) {
+                    const int l = e / (NC - N), j = N + (e - l * (NC - N));
+                    a_w[l * NC + j] = T(0);
+                }
+        }
+        __syncthreads();
+        for (int k = 0; k < kmax; ++k) {
+            float acc[4][8] = {};
+            const bool run = k < steps;
+            if (run) {
+#pragma unroll 4
+                for (int l = 0; l < N; ++l) {
+                    const float4 xv = *reinterpret_cast<const float4*>(xt + l * XTP + 4 * rb);
+                    const float4 a0 = *reinterpret_cast<const float4*>(a + l * NC + 8 * cb);
+                    const float4 a1 = *reinterpret_cast<const float4*>(a + l * NC + 8 * cb + 4);
+                    const float xr[4] = {xv.x, xv.y, xv.z, xv.w};
+                    const float ar[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) acc[i][j] = fmaT(xr[i], ar[j], acc[i][j]);
+                }
+            }
+            __syncthreads();   // every read of X_k is done
+            if (run) {
+                // column 8cb + j of X^T, rows 4rb..4rb+3: one 16-byte read and write each
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    float4* xp = reinterpret_cast<float4*>(xt + (8 * cb + j) * XTP + 4 * rb);
+                    float4 v = *xp;
+                    v.x = fmaT(cc, acc[0][j], v.x);
+                    v.y = fmaT(cc, acc[1][j], v.y);
+                    v.z = fmaT(cc, acc[2][j], v.z);
+                    v.w = fmaT(cc, acc[3][j], v.w);
+                    *xp = v;
+                }
+            }
+            __syncthreads();   // X_{k+1} complete
+        }
+        // X_T into the staging area in storage order (A is no longer needed)
+        if (active)
+            for (int e = w; e < NN; e += TPI) {
+                const int i = e / N, j = e - i * N;
+                sA[inst * P + (LAYOUT == 0 ? i * N + j : j * N + i)] = xt[j * XTP + i];
+            }
     } else if constexpr (MAP == 6) {
         static_assert(sizeof(T) == 4, "mapping 6 is FP32");
         constexpr int P = cjg::chain_pitch(N, 6, 4), AR = cjg::chain_arow(N, 6, 4), H = (N + 1) / 2;

@@ -58,6 +58,10 @@ void chain_candidates(const cj_template_args &a, std::vector<std::array<int, 4>>
     if (a.dtype == CJ_F64 && n % 8 == 0 && n <= 32)
         for (int ipb : {1, 2, 4, 8})
             if (ok(4, ipb)) out.push_back({4, ipb, 0, 0});
+    if (a.dtype == CJ_F32 && n >= 16)   // 4 x 8 register blocks: blocks of 128 to 512 threads
+        for (int ipb : {1, 2, 4, 8, 16, 32, 64})
+            if (ok(8, ipb) && cjg::chain_threads(n, 8, ipb) >= 128 && cjg::chain_threads(n, 8, ipb) <= 512)
+                out.push_back({8, ipb, 0, 0});
     if (a.dtype == CJ_F32 && n >= 8)
         for (int ipb : {1, 2, 4, 8, 16, 32})
             if (ok(5, ipb) && cjg::chain_threads(n, 5, ipb) >= 64) out.push_back({5, ipb, 0, 0});
@@ -94,6 +98,16 @@ void ltimes_candidates(const cj_template_args &a, std::vector<std::array<int, 4>
             if (cjg::lt_tc_smem(a.m, a.d, r, tg, ct / tg, a.layout_b, pipe) > 220 * 1024) return;
             out.push_back({tg, ct / tg, 32 * (6 + s), (pipe << 20) | (5 << 16) | (r << 8) | s});
             return;
+        } else if (mode == 6) {   // tcgen05 + TMA, operands in TMEM: r = TMEM stages, s = converter warps, pipe = boxes
+            static const int order[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+            const int inner = order[a.layout_a][2];
+            const int npa = (cjg::lt_tc_np(a.m) + 31) / 32 * 32;
+            if (ct != 128 || a.dtype != CJ_F32 || a.m > 128 || (inner == 0 ? 32 : inner == 1 ? tg : ct / tg) % 4) return;
+            if (2 * npa + 64 * r > 512 || cjg::lt_tc_smem(a.m, a.d, 0, tg, ct / tg, a.layout_b, pipe) > 220 * 1024 ||
+                cjg::lt_tc_smem(a.m, a.d, 2, tg, ct / tg, a.layout_b) > 220 * 1024)
+                return;
+            out.push_back({tg, ct / tg, 32 * (6 + s), (pipe << 20) | (6 << 16) | (r << 8) | s});
+            return;
         } else if (mode == 4) {   // tcgen05: r = stages, s = producer warps
             if (ct != 128 || a.dtype != CJ_F32 || a.m > 128) return;
             if (cjg::lt_tc_smem(a.m, a.d, r, tg, ct / tg, a.layout_b) > 220 * 1024) return;
@@ -122,9 +136,10 @@ void ltimes_candidates(const cj_template_args &a, std::vector<std::array<int, 4>
             push(tg, 64, 0, 1, 9);
             push(tg, 64, 0, 1, 12);
         } else {
+            push(tg, 128, 6, 4, 4, 6);          // tcgen05 3xTF32, TMA, operands in TMEM: 6 boxes, 4 stages, 4 converters
+            push(tg, 128, 6, 4, 8, 6);          //                                        8 converters
             push(tg, 128, 5, 2, 8, 4);          // tcgen05 3xTF32 fed by TMA: 4 boxes, 2 operand stages
             push(tg, 128, 4, 2, 8);             // tcgen05 3xTF32, register producers: 2 operand stages
-            push(tg, 128, 4, 3, 8);             //                                     3 operand stages
             push(tg, 64, 2, 1, 8, 1);           // mma.sync 3xTF32
             push(tg, 64, 0, 2, 12, 1);          // FMA, cp.async double buffer
             push(tg, 256, 3, 2, 0, 0);          // direct loads, all moments per thread
@@ -180,9 +195,10 @@ void featurize(int k, const cj_template_args &a0, int64_t batch, int32_t steps, 
         f[17 + lt_axis(a.layout_b, 1)] = 1.f;
         const int mode = (tile[3] >> 16) & 0xf, r = (tile[3] >> 8) & 0xff, s = tile[3] & 0xff;
         // f[2] and f[5] (grouped kernel, bf16) are always 0 for LTimes; here they
-        // flag the tcgen05 tiles (modes 4 and 5) and the TMA-fed one (mode 5)
-        f[2] = mode == 4 || mode == 5;
-        f[5] = mode == 5;
+        // flag the tcgen05 tiles (modes 4-6) and the TMA-fed ones (modes 5, 6;
+        // f[25] tells 6, the tensor-memory operands, apart)
+        f[2] = mode >= 4 && mode <= 6;
+        f[5] = mode == 5 || mode == 6;
         f[26] = ((tile[3] >> 20) & 0xf) / 8.f;   // cp.async flag, prefetch depth or TMA boxes
         f[20] = lg2(tile[0]) / 5;
         f[21] = lg2(tile[1]) / 7;
@@ -202,8 +218,8 @@ void featurize(int k, const cj_template_args &a0, int64_t batch, int32_t steps, 
         const int map = k == CJ_K_EIGEN_RECURRENCE ? (tile[0] == 2 ? 6 : 1) : tile[0];
         f[20] = map == 1 || map == 6;
         f[21] = map == 2;
-        f[22] = map == 4 || map == 5;   // register/tensor blocked panels
-        f[19] = map == 5 ? 1.f : map == 6 ? 0.5f : 0.f;
+        f[22] = map == 4 || map == 5 || map == 8;   // register/tensor blocked panels
+        f[19] = map == 5 ? 1.f : map == 8 ? 1.5f : map == 6 ? 0.5f : 0.f;
         f[16] = map == 7;   // tcgen05 tensor cores
         f[23] = lg2(tile[1]) / 8;
         const int threads = cjg::chain_threads(a.n, map, tile[1]);
@@ -217,7 +233,9 @@ void featurize(int k, const cj_template_args &a0, int64_t batch, int32_t steps, 
         f[10] = (map == 1 || map == 6) && a_regs;
         f[11] = (map == 1 && a.n > cjg::chain_reg_rows_max(es)) || (map == 6 && a.n > 32);
         const double np = map == 5 ? (a.n + 3) / 4 * 4 : (map == 3 || map == 7) ? (a.n + 15) / 16 * 16 : a.n;
-        f[12] = (float)(np * np * np / ((double)a.n * a.n * a.n) - 1.0);
+        // mapping 8 pads rows to 4 and columns to 8 and sums over the n real k
+        const double work = map == 8 ? (double)((a.n + 3) / 4 * 4) * ((a.n + 7) / 8 * 8) * a.n : np * np * np;
+        f[12] = (float)(work / ((double)a.n * a.n * a.n) - 1.0);
         const long smem = k == CJ_K_EIGEN_RECURRENCE ? cjg::eig_smem(a.n, tile[1], es, tile[0])
                                                        : cjg::chain_smem(a.n, map, tile[1], es);
         const double per_sm = std::max(1.0, std::min(2048.0 / threads, 228.0 * 1024 / std::max(smem, 1L)));

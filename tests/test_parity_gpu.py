@@ -124,6 +124,21 @@ def test_update_chain_f32_register_blocks(n, ipb, layout):
     assert relF_per_instance(run_chain(h, A, steps, cj.F32), ref) <= TOL32
 
 
+@pytest.mark.parametrize("n,ipb", [(8, 4), (16, 4), (17, 2), (24, 3), (30, 2), (32, 5), (33, 2), (45, 1),
+                                   (48, 2), (61, 1), (63, 2), (64, 1), (64, 3)])
+@pytest.mark.parametrize("layout", [0, 1])
+def test_update_chain_f32_register_blocks_4x8(n, ipb, layout):
+    """Mapping 8 (4 x 8 register blocks: rows padded to 4, columns to 8 with
+    zeros, X transposed in shared memory), ragged last block."""
+    steps = 64
+    h = cj.specialize(cj.K_UPDATE_CHAIN, cj.F32, n=n, layout_a=layout, tile=(8, ipb, 0, 0))
+    assert h.variant == "jit"
+    batch = oracle_batch(n, steps) + 2
+    A = synth.chain_inputs_np(synth.SEED_CHAIN_SWEEP, batch, n, layout=layout)
+    ref = oracle.update_chain(A, steps, layout=layout, nthreads=8)
+    assert relF_per_instance(run_chain(h, A, steps, cj.F32), ref) <= TOL32
+
+
 @pytest.mark.parametrize("n,ipb", [(2, 32), (5, 16), (7, 9), (8, 8), (12, 4), (15, 5), (16, 3), (31, 2), (32, 8)])
 @pytest.mark.parametrize("layout", [0, 1])
 def test_update_chain_f32_two_rows_per_thread(n, ipb, layout):
@@ -544,11 +559,49 @@ def test_grouped_plan_dispatcher(dt):
         plan.destroy()
 
 
+@pytest.mark.parametrize("dt", [cj.F64, cj.F32, cj.BF16])
+def test_grouped_plan_every_dispatcher_variant(dt):
+    """Each dispatcher variant the plan's autotuner may keep (register caps;
+    for f32 also the 4 x 8 register-block rule for n >= 16), pinned in turn
+    and launched as a graph and directly, against the oracle per instance."""
+    n, t = synth.uneven_sizes(synth.SEED_UNEVEN + 2, 400)
+    n[:6] = (1, 2, 15, 16, 63, 64)
+    pool, off = synth.uneven_inputs_np(synth.SEED_UNEVEN + 2, n)
+    A = torch.from_numpy(pool).to("cuda", tdtype(dt))
+    ref = oracle.update_chain_uneven(n, t, off, A.double().cpu().numpy(), nthreads=8)
+    tol = {cj.F64: TOL64, cj.F32: TOL32, cj.BF16: 2e-2}[dt]
+    plan = cj.GroupPlan(dt, n, t)
+    try:
+        plan.wait()
+        count = plan.use_dispatcher()
+        assert count == {cj.F64: 1, cj.F32: 4, cj.BF16: 2}[dt]
+        for v in range(count):
+            plan.use_dispatcher(v)
+            d = plan.dispatcher()
+            assert d["state"] == "ready" and d["blocks_per_sm"] >= 1, (v, d)
+            for use_graph in (True, False):
+                X = torch.full_like(A, float("nan"))
+                plan.launch(A, X, use_graph=use_graph)
+                torch.cuda.synchronize()
+                Xh = X.double().cpu().numpy()
+                assert np.all(np.isfinite(Xh)), (v, use_graph)
+                worst = max(relF(Xh[off[k]:off[k] + n[k] * n[k]], ref[off[k]:off[k] + n[k] * n[k]])
+                            for k in range(len(n)))
+                assert worst <= tol, (v, use_graph, worst)
+        with pytest.raises(cj.CJError):
+            plan.use_dispatcher(count)
+    finally:
+        plan.destroy()
+
+
 def test_generic_plan_has_no_dispatcher():
     n, t = synth.uneven_sizes(synth.SEED_UNEVEN, 50)
     plan = cj.GroupPlan(cj.F64, n, t, flags=cj.FLAG_GENERIC)
     try:
         assert plan.dispatcher()["state"] == "none"
+        assert plan.use_dispatcher() == 0
+        with pytest.raises(cj.CJError):
+            plan.use_dispatcher(0)
     finally:
         plan.destroy()
 
@@ -593,6 +646,7 @@ def test_grouped_handle_direct_launch():
     items[:, 1] = steps
     for dt, tile, flags in ((cj.F64, (0, 0, 0, 0), 0), (cj.F64, (0, 0, 0, 0), cj.FLAG_GENERIC),
                             (cj.F32, (5, 2, 0, 0), 0), (cj.F32, (1, 3, 0, 0), 0), (cj.F32, (6, 3, 0, 0), 0),
+                            (cj.F32, (8, 2, 0, 0), 0),
                             (cj.BF16, (7, 1, 0, 0), 0), (cj.BF16, (3, 2, 0, 0), 0)):
         h = cj.specialize(cj.K_UPDATE_CHAIN_GROUPED, dt, n=nn, tile=tile, flags=flags)
         it = torch.from_numpy(items).cuda()

@@ -1,6 +1,6 @@
 """Failure detection of the tensor-core LTimes kernels without a GPU fault.
 
-Every barrier wait in the tcgen05 kernels (tile modes 4 and 5) is bounded:
+Every barrier wait in the tcgen05 kernels (tile modes 4-6) is bounded:
 after about a second a block raises its abort flag, waits for its own
 tensor-core work and TMA copies, frees its tensor memory, counts the event
 and returns.  CJ_FLAG_INJECT_WAIT_TIMEOUT compiles the kernel with
@@ -31,6 +31,7 @@ def lib():
 
 @pytest.mark.parametrize("tile", [
     (1, 128, 32 * 14, (2 << 20) | (5 << 16) | (2 << 8) | 8),   # mode 5: TMA boxes in flight at the stop
+    (1, 128, 32 * 14, (2 << 20) | (6 << 16) | (2 << 8) | 8),   # mode 6: operands in tensor memory
     (1, 128, 32 * 13, (4 << 16) | (2 << 8) | 8),               # mode 4: register producers
 ])
 def test_expired_waits_are_reported_and_the_context_survives(tile):
