@@ -368,9 +368,10 @@ cj_status cj_group_plan_launch(cj_group_plan p, const void *A_pool, void *X_pool
 cj_status cj_group_plan_dispatcher(cj_group_plan p, int32_t *state, int32_t *n_tickets, int32_t *threads,
                                    int32_t *blocks_per_sm);
 /* Pin the plan's dispatcher to variant `variant` (0 .. *variants - 1; the
- * variants differ in the register cap of the launch bounds and, for f32, in
- * the tile rule of the n >= 16 groups: rule 0 = 4 x 4 register blocks
- * (mapping 5), rule 1 = 4 x 8 (mapping 8)).  Compiles it if needed (waits),
+ * variants differ in the register cap of the launch bounds, for f32 in the
+ * tile rule of the n >= 16 groups (rule 0 = 4 x 4 register blocks, mapping
+ * 5; rule 1 = 4 x 8, mapping 8), and for bf16 in the block size (256 or 128
+ * threads)).  Compiles it if needed (waits),
  * and makes later launches (and graph captures) use it, as the plan's
  * autotuner does with the fastest.  variant < 0 only reports *variants (may
  * be NULL; 0 for a plan without a dispatcher).  CJ_ERR_INVALID_ARG: null
@@ -391,8 +392,10 @@ cj_status cj_group_plan_wait(cj_group_plan p, int timeout_ms);
  * launches after one warm-up, CUDA events); the fastest replaces the group's
  * tile, and the next graph launch re-captures.  Then, once the plan's
  * dispatcher is compiled (this waits for it), the whole launch is timed in
- * both forms -- the dispatcher, and one kernel per group -- and later
- * launches use the faster.  X_pool is written: every timed
+ * both forms -- every dispatcher variant (cj_group_plan_use_dispatcher), and
+ * one kernel per group; each as a graph and issued directly, the mean of
+ * max(reps, 10) launches issued back to back after a warm-up -- and later
+ * launches use the fastest.  X_pool is written: every timed
  * launch computes its group's instances.  *changed (may be NULL) receives the
  * number of groups whose tile changed.  Synchronous; compiles run on the
  * background threads in async mode.  Not to be called while another thread

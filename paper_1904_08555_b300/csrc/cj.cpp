@@ -408,11 +408,12 @@ cj_status validate_and_normalise(int k, const cj_template_args &in, cj_template_
     }
     // explicit tiles: check the kernel can be instantiated and launched
     if (is_mass(k)) {
-        if (a.tile[0] < 1 || a.tile[1] || a.tile[2] || a.tile[3] ||
+        if (a.tile[0] < 1 || (a.tile[1] != 0 && a.tile[1] != 1) || a.tile[2] || a.tile[3] ||
             cjg::mass_threads(a.n, a.m, a.tile[0]) > 1024 ||
-            cjg::mass_smem(a.d, a.n, a.m, a.tile[0], esize(a.dtype)) > 220 * 1024)
-            return fail(CJ_ERR_INVALID_ARG, "mass operator tile {%d,%d,%d,%d} invalid ({elements per block, 0, 0, 0}, "
-                        "at most 1024 threads and 220 KiB of shared memory)", a.tile[0], a.tile[1], a.tile[2], a.tile[3]);
+            cjg::mass_smem(a.d, a.n, a.m, a.tile[0], esize(a.dtype), a.tile[1]) > 220 * 1024)
+            return fail(CJ_ERR_INVALID_ARG, "mass operator tile {%d,%d,%d,%d} invalid ({elements per block, 0 or 1 "
+                        "(persistent, staged loads), 0, 0}, at most 1024 threads and 220 KiB of shared memory)",
+                        a.tile[0], a.tile[1], a.tile[2], a.tile[3]);
         return CJ_OK;
     }
     if (is_eig(k)) {
@@ -563,7 +564,7 @@ void spec_geometry(const cj_handle_s *h, Impl &s) {
     } else if (is_mass(h->kernel)) {
         s.ipb = a.tile[0];
         s.threads = cjg::mass_threads(a.n, a.m, a.tile[0]);
-        s.smem = (size_t)cjg::mass_smem(a.d, a.n, a.m, a.tile[0], es);
+        s.smem = (size_t)cjg::mass_smem(a.d, a.n, a.m, a.tile[0], es, a.tile[1]);
     } else if (is_eig(h->kernel)) {
         s.ipb = a.tile[1];
         s.threads = cjg::chain_threads(a.n, a.tile[0] == 2 ? 6 : 1, a.tile[1]);
@@ -615,7 +616,8 @@ std::string name_expression(const cj_handle_s *h) {
         snprintf(buf, sizeof buf, "cj::update_chain<%s, %d, %d, %d, %d>", ctype(a.dtype), a.n, a.layout_a,
                  a.tile[0], a.tile[1]);
     else if (is_mass(h->kernel))
-        snprintf(buf, sizeof buf, "cj::mass_apply<%s, %d, %d, %d, %d>", ctype(a.dtype), a.d, a.n, a.m, a.tile[0]);
+        snprintf(buf, sizeof buf, "cj::mass_apply%s<%s, %d, %d, %d, %d>", a.tile[1] ? "_pipe" : "", ctype(a.dtype),
+                 a.d, a.n, a.m, a.tile[0]);
     else if (is_eig(h->kernel))
         snprintf(buf, sizeof buf, "cj::eigen_recurrence%s<%s, %d, %d>", a.tile[0] == 2 ? "2" : "", ctype(a.dtype),
                  a.n, a.tile[1]);
@@ -962,21 +964,22 @@ constexpr int kDispatchBlock = 256;
 // The dispatcher's source for `minb` resident blocks per SM (the launch
 // bounds' register cap), and its shared-memory need.
 // A dispatcher variant: resident blocks per SM the launch bounds must allow
-// (the register cap) and the tile rule.
+// (the register cap), the tile rule and the block size.
 struct DispVariant {
-    int minb, rule;
+    int minb, rule, block = kDispatchBlock;
 };
 
 // Shared memory a chunk of variant v may take: what minb blocks can hold
-// together on one SM (228 KiB, less 1 KiB reserved per block and a
-// margin for the kernel's static shared memory), at most 160 KiB.
+// together on one SM (228 KiB, less per block the 1 KiB the hardware
+// reserves and 4 KiB for the dispatcher's static shared memory: 3,088
+// bytes of chunk bookkeeping), at most 160 KiB.
 long dispatch_smem_cap(DispVariant v) {
-    return std::min<long>(160 * 1024, 233472 / v.minb - 2048);
+    return std::min<long>(160 * 1024, 233472 / v.minb - 5120);
 }
 
 std::string dispatcher_source(const cj_group_plan_s *p, DispVariant v, long *smem_out) {
     const int minb = v.minb;
-    constexpr int kBlock = kDispatchBlock;
+    const int kBlock = v.block;
     const char *ct = p->dtype == CJ_F64 ? "double" : "float";
     std::string src = "#include \"update_chain.cuh\"\nnamespace cj {\n__global__ void __launch_bounds__(" +
                       std::to_string(kBlock) + ", " + std::to_string(minb) +
@@ -1013,7 +1016,7 @@ cj_handle_s *request_dispatcher(const cj_group_plan_s *p, DispVariant v) {
     auto *h = new cj_handle_s();
     h->kernel = kDispatchKernel;
     h->a.dtype = p->dtype;
-    h->a.tile[0] = kDispatchBlock;
+    h->a.tile[0] = v.block;
     h->a.tile[1] = (int)smem;
     h->a.tile[2] = v.minb;
     h->a.tile[3] = v.rule;
@@ -1036,10 +1039,12 @@ cj_handle_s *request_dispatcher(const cj_group_plan_s *p, DispVariant v) {
 // FP32 starts with tile rule 1 (4 x 8 register blocks for n >= 16: 1.18 ms
 // against 1.39 ms for rule 0 on the 10,000-instance batch) and also tries
 // rule 0.
+// BF16 also tries blocks of 128 threads, three per SM (170 registers: the
+// n = 64 panel bodies fit without spilling, 12 warps per SM).
 std::vector<DispVariant> dispatcher_variants(int dtype) {
     if (dtype == CJ_F64) return {{1, 0}};
     if (dtype == CJ_F32) return {{2, 1}, {3, 1}, {2, 0}, {3, 0}};
-    return {{2, 0}, {1, 0}};
+    return {{2, 0}, {1, 0}, {3, 0, 128}};
 }
 
 // Ticket the plan's work for variant v (each ticket one chunk of one group,
@@ -1055,7 +1060,7 @@ cj_status make_dispatch_form(cj_group_plan_s *p, DispVariant v, cj_group_plan_s:
     for (size_t g = 0; g < p->groups.size(); ++g) {
         const auto &gr = p->groups[g];
         const int gdt = (p->dtype == CJ_BF16 && gr.n < 16) ? CJ_F32 : p->dtype;
-        const auto t = dispatch_tile(gdt, gr.n, kDispatchBlock, v.rule, dispatch_smem_cap(v));
+        const auto t = dispatch_tile(gdt, gr.n, v.block, v.rule, dispatch_smem_cap(v));
         const double per = 2.0 * gr.n * gr.n * gr.n + 2.0 * gr.n * gr.n;
         for (int64_t c = 0; c < gr.n_items; c += t[1]) {
             Tk k{0.0, gr.first_item + c, (int)g, (int)std::min<int64_t>(t[1], gr.n_items - c)};
@@ -1337,7 +1342,11 @@ CJ_API cj_status cj_launch(cj_handle h, void *const *args, int64_t batch, void *
         if (!B1 || !op || !xv || !yv) return fail(CJ_ERR_INVALID_ARG, "null B1/op/x/y");
         if (batch == 0) return CJ_OK;
         long long ne = batch;
-        const unsigned grid = (unsigned)((batch + im->ipb - 1) / im->ipb);
+        const long long groups = (batch + im->ipb - 1) / im->ipb;
+        // the persistent kernel (tile[1] = 1): at most its resident blocks
+        const unsigned grid = (unsigned)(im->variant != V_GENERIC && a.tile[1]
+                                             ? std::min(groups, (long long)G.num_sms * im->blocks_per_sm)
+                                             : groups);
         if (im->variant == V_GENERIC) {
             int dim = a.d, D = a.n, Q = a.m, epb = im->ipb;
             void *p[] = {&B1, &op, &xv, &yv, &ne, &dim, &D, &Q, &epb};
@@ -1758,24 +1767,29 @@ CJ_API cj_status cj_group_plan_autotune(cj_group_plan p, const void *A_pool, voi
     // 3. the launch form: every compiled dispatcher variant against one
     //    kernel per group with the tiles just chosen, each timed as a whole
     //    launch, as a CUDA graph and issued directly (a form's time is the
-    //    faster of the two); the fastest is kept
+    //    faster of the two); the fastest is kept.
+    //    A form's time is that of launches issued back to back, as a caller
+    //    issues them in steady state: one warm-up launch (it captures the
+    //    graph), then max(reps, 10) launches between two events.  Timing each
+    //    launch with a host wait in between would add the host's submission
+    //    of the launch to it, which is far larger for one kernel per group
+    //    (tens of graph nodes or launches) than for the dispatcher.
+    const int form_reps = std::max(reps, 10);
     auto time_form = [&](int flags, float *out) {
-        std::vector<float> ms;
-        for (int r = 0; r <= reps && rc == CJ_OK; ++r) {
-            float t = 0;
-            if (cudaEventRecord(e0, st) != cudaSuccess)
-                rc = fail(CJ_ERR_CUDA, "grouped autotune: event failed");
-            else if ((rc = plan_launch(p, A_pool, X_pool, st, flags)) == CJ_OK &&
-                     (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                      cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
-                rc = fail(CJ_ERR_CUDA, "grouped autotune: timing failed");
-            else if (r > 0)
-                ms.push_back(t);
+        float t = 0;
+        if ((rc = plan_launch(p, A_pool, X_pool, st, flags)) != CJ_OK) return;
+        if (cudaStreamSynchronize(st) != cudaSuccess || cudaEventRecord(e0, st) != cudaSuccess) {
+            rc = fail(CJ_ERR_CUDA, "grouped autotune: event failed");
+            return;
         }
-        if (rc == CJ_OK) {
-            std::sort(ms.begin(), ms.end());
-            *out = std::min(*out, ms[ms.size() / 2]);
+        for (int r = 0; r < form_reps && rc == CJ_OK; ++r) rc = plan_launch(p, A_pool, X_pool, st, flags);
+        if (rc != CJ_OK) return;
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+            rc = fail(CJ_ERR_CUDA, "grouped autotune: timing failed");
+            return;
         }
+        *out = std::min(*out, t / form_reps);
     };
     if (rc == CJ_OK && !p->disp_forms.empty()) {
         float best_disp = INFINITY, best_group = INFINITY;

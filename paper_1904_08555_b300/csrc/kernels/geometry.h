@@ -55,6 +55,15 @@ CJ_HD constexpr int chain_arow(int n, int mapping, int esize) {
                                                                             : n;
 }
 
+// Mapping 8 (FP32): one copy of an instance's X^T (it keeps two), (n padded
+// to 8) rows of pitch (n padded to 4) + 4, then padded to an odd number of
+// 16-byte units, so that the copies a warp reads start in different bank
+// groups.
+CJ_HD constexpr int chain_m8_xti(int n) {
+    return ((n + 7) / 8 * 8) * ((n + 3) / 4 * 4 + 4) / 4 % 2 ? ((n + 7) / 8 * 8) * ((n + 3) / 4 * 4 + 4)
+                                                             : ((n + 7) / 8 * 8) * ((n + 3) / 4 * 4 + 4) + 4;
+}
+
 // Elements between consecutive staged instances of the specialized kernels.
 CJ_HD constexpr int chain_pitch(int n, int mapping, int esize) {
     return mapping == 2 ? inst_pitch(n * n) : row_pitch(n * chain_arow(n, mapping, esize), esize);
@@ -71,8 +80,8 @@ CJ_HD constexpr long chain_smem(int n, int mapping, int ipb, int esize) {
         ? (long)ipb * inst_pitch(n * n) * esize
         : mapping == 5
         ? (long)ipb * chain_pitch(n, 5, esize) * esize + (long)ipb * ((n + 3) / 4 * 4) * ((n + 3) / 4 * 4 + 4) * esize
-        : mapping == 8   // A, then X^T: (n padded to 8) rows of (n padded to 4) + 4
-        ? (long)ipb * chain_pitch(n, 8, esize) * esize + (long)ipb * ((n + 7) / 8 * 8) * ((n + 3) / 4 * 4 + 4) * esize
+        : mapping == 8   // A, then two copies of X^T (chain_m8_xti elements each) per instance
+        ? (long)ipb * chain_pitch(n, 8, esize) * esize + 2L * ipb * chain_m8_xti(n) * esize
         : (long)ipb * chain_pitch(n, mapping, esize) * esize +
               (mapping == 1 && n > chain_reg_rows_max(esize)
                    ? (long)chain_threads(n, 1, ipb) * xrow_pitch(n) * esize
@@ -182,9 +191,12 @@ CJ_HD constexpr long lt_generic_smem(int m, int d, int cols, int esize) {
 CJ_HD constexpr int mass_m(int D, int Q) { return D > Q ? D : Q; }
 CJ_HD constexpr int mass_threads(int D, int Q, int epb) { return ((epb * mass_m(D, Q) * mass_m(D, Q) + 31) / 32) * 32; }
 CJ_HD constexpr int mass_b_elems(int D, int Q) { return Q * D; }
-CJ_HD constexpr long mass_smem(int dim, int D, int Q, int epb, int esize) {
+// pipe = 1 (the persistent kernel): two stages of every element's x (D^dim)
+// and op (Q^dim) values besides.
+CJ_HD constexpr long mass_smem(int dim, int D, int Q, int epb, int esize, int pipe = 0) {
     return ((long)mass_b_elems(D, Q) +
-            2L * epb * (dim == 2 ? mass_m(D, Q) * mass_m(D, Q) : mass_m(D, Q) * mass_m(D, Q) * mass_m(D, Q))) *
+            2L * epb * (dim == 2 ? mass_m(D, Q) * mass_m(D, Q) : mass_m(D, Q) * mass_m(D, Q) * mass_m(D, Q)) +
+            (pipe ? 2L * epb * (dim == 2 ? D * D + Q * Q : D * D * D + Q * Q * Q) : 0L)) *
            esize;
 }
 

@@ -156,6 +156,69 @@ mass_apply(const T* __restrict__ B1, const T* __restrict__ op, const T* __restri
                          DIM, D, Q, M, r % M, r / M, active);
 }
 
+// One element (T = 4 or 8 bytes) from global to shared memory without
+// registers: completes at the next cp.async.wait_group that covers it.
+template <class T>
+__device__ __forceinline__ void mass_cp_async(T* dst, const T* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(T) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+
+// Specialized and persistent (tile {EPB, 1, 0, 0}): block b takes element
+// groups b, b + grid, ... (EPB consecutive elements each).  While one group
+// is computed, the x and op values of the block's next group are copied into
+// the other of two shared-memory stages with cp.async, so that each SM keeps
+// loads in flight through the compute stages.  Shared memory: B1, the two
+// work buffers per element, then stage s at [x: EPB D^dim | op: EPB Q^dim].
+template <class T, int DIM, int D, int Q, int EPB>
+__global__ void __launch_bounds__(cjg::mass_threads(D, Q, EPB))
+mass_apply_pipe(const T* __restrict__ B1, const T* __restrict__ op, const T* __restrict__ x, T* __restrict__ y,
+                long long ne) {
+    constexpr int M = D > Q ? D : Q;
+    constexpr int ND = DIM == 2 ? D * D : D * D * D, NQ = DIM == 2 ? Q * Q : Q * Q * Q;
+    constexpr int MD = DIM == 2 ? M * M : M * M * M;
+    constexpr int NT = cjg::mass_threads(D, Q, EPB);
+    constexpr int SX = EPB * ND, SO = EPB * NQ;   // stage extents
+    extern __shared__ __align__(16) unsigned char cj_smem[];
+    T* b = reinterpret_cast<T*>(cj_smem);
+    T* bufs = b + cjg::mass_b_elems(D, Q);
+    T* stage = bufs + 2 * EPB * MD;
+    const int t = threadIdx.x, le = t / (M * M), r = t - le * M * M;
+    for (int i = t; i < Q * D; i += NT) b[i] = B1[i];
+    const long long ngroups = (ne + EPB - 1) / EPB;
+    // the x and op values of group g (cnt elements, contiguous in both) into stage s
+    auto issue = [&](long long g, int s) {
+        const long long e0 = g * EPB;
+        const int cnt = ne - e0 < EPB ? (int)(ne - e0) : EPB;
+        T* sx = stage + s * (SX + SO);
+        T* so = sx + SX;
+        for (int i = t; i < cnt * ND; i += NT) mass_cp_async(sx + i, x + e0 * ND + i);
+        for (int i = t; i < cnt * NQ; i += NT) mass_cp_async(so + i, op + e0 * NQ + i);
+    };
+    if ((long long)blockIdx.x < ngroups) issue(blockIdx.x, 0);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    int s = 0;
+    for (long long g = blockIdx.x; g < ngroups; g += gridDim.x, s ^= 1) {
+        // the next group's copies start before this group's wait
+        if (g + gridDim.x < ngroups) issue(g + gridDim.x, s ^ 1);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 1;" ::: "memory");   // this group's stage has landed
+        __syncthreads();
+        const long long e = g * EPB + le;
+        const bool active = le < EPB && e < ne;
+        const int lb = le < EPB ? le : 0;
+        const T* sx = stage + s * (SX + SO) + lb * ND;
+        const T* so = stage + s * (SX + SO) + SX + lb * NQ;
+        mass_element<T, int>(sx, so, y + (active ? e : 0) * ND, b, bufs + (2 * lb) * MD, bufs + (2 * lb + 1) * MD,
+                             DIM, D, Q, M, r % M, r / M, active);
+        __syncthreads();   // stage s is read: the next iteration's copies may overwrite it
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 // Generic: run-time dimension, D, Q and elements per block (the same stages
 // with run-time loop bounds).
 template <class T>

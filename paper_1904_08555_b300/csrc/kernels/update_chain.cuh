@@ -428,15 +428,19 @@ __device__ __forceinline__ void chain_block(T* sA, int ninst, int tid, StepsOf s
         // k step of the product is one 16-byte read of X^T and two of A for
         // 32 fused multiply-adds (mapping 5: two reads for 16).  Rows are
         // padded to NR (a multiple of 4), columns to NC (a multiple of 8); X^T
-        // is kept in shared memory as xt[l][r] with NC rows of pitch NR + 4.
-        // A's padded columns are zeroed here, so P's padded columns, and with
-        // them X's padded rows and columns, stay exactly zero; the product
-        // runs over the N real k only.  All threads of the block run the
-        // longest instance's step count so every barrier is uniform.
+        // is kept in shared memory as xt[l][r] with NC rows of pitch NR + 4,
+        // twice: step k reads X_k from one copy and writes X_{k+1} into the
+        // other, so a step needs one barrier (mapping 5: two).  A's padded
+        // columns are zeroed here, so P's padded columns, and with them X's
+        // padded rows and columns, stay exactly zero; the product runs over
+        // the N real k only.  Each copy is chain_m8_xti(N) elements (an odd
+        // number of 16-byte units).  All threads of the block run the longest
+        // instance's step count so every barrier is uniform; an instance's
+        // X_T is in copy T % 2.
         static_assert(sizeof(T) == 4 && N >= 8, "mapping 8 is FP32 with N >= 8");
         constexpr int NR = (N + 3) / 4 * 4, NC = (N + 7) / 8 * 8;
         constexpr int P = cjg::chain_pitch(N, 8, 4), AR = cjg::chain_arow(N, 8, 4);
-        constexpr int B4 = NR / 4, B8 = NC / 8, TPI = B4 * B8, XTP = NR + 4;
+        constexpr int B4 = NR / 4, B8 = NC / 8, TPI = B4 * B8, XTP = NR + 4, XTI = cjg::chain_m8_xti(N);
         static_assert(AR == NC, "mapping 8 stages A with rows of NC");
         T* xt_all = sA + IPB * P;
         const int inst = tid / TPI, w = tid - inst * TPI;
@@ -446,13 +450,15 @@ __device__ __forceinline__ void chain_block(T* sA, int ninst, int tid, StepsOf s
         for (int q = 0; q < ninst; ++q) kmax = max(kmax, steps_of(q));
         const int steps = active ? steps_of(inst) : 0;
         const T cc = active ? c_of(inst) : T(0);
-        T* xt = xt_all + (active ? inst : 0) * NC * XTP;
+        T* xt0 = xt_all + (active ? inst : 0) * 2 * XTI;   // X_k for even k
+        T* xt1 = xt0 + XTI;                                // odd k
         T* a_w = sA + (active ? inst : 0) * P;
         const T* a = a_w;
         if (active) {
+            // X_0 = I; every entry of the other copy is written by the first step
             for (int e = w; e < NC * NR; e += TPI) {
                 const int l = e / NR, r = e - l * NR;
-                xt[l * XTP + r] = (l == r && l < N) ? T(1) : T(0);
+                xt0[l * XTP + r] = (l == r && l < N) ? T(1) : T(0);
             }
             if constexpr (NC != N)
                 for (int e = w; e < N * (NC - N); e += TPI) {
@@ -462,12 +468,13 @@ __device__ __forceinline__ void chain_block(T* sA, int ninst, int tid, StepsOf s
         }
         __syncthreads();
         for (int k = 0; k < kmax; ++k) {
-            float acc[4][8] = {};
-            const bool run = k < steps;
-            if (run) {
+            const T* cur = (k & 1) ? xt1 : xt0;
+            T* nxt = (k & 1) ? xt0 : xt1;
+            if (k < steps) {
+                float acc[4][8] = {};
 #pragma unroll 4
                 for (int l = 0; l < N; ++l) {
-                    const float4 xv = *reinterpret_cast<const float4*>(xt + l * XTP + 4 * rb);
+                    const float4 xv = *reinterpret_cast<const float4*>(cur + l * XTP + 4 * rb);
                     const float4 a0 = *reinterpret_cast<const float4*>(a + l * NC + 8 * cb);
                     const float4 a1 = *reinterpret_cast<const float4*>(a + l * NC + 8 * cb + 4);
                     const float xr[4] = {xv.x, xv.y, xv.z, xv.w};
@@ -477,28 +484,25 @@ __device__ __forceinline__ void chain_block(T* sA, int ninst, int tid, StepsOf s
 #pragma unroll
                         for (int j = 0; j < 8; ++j) acc[i][j] = fmaT(xr[i], ar[j], acc[i][j]);
                 }
-            }
-            __syncthreads();   // every read of X_k is done
-            if (run) {
-                // column 8cb + j of X^T, rows 4rb..4rb+3: one 16-byte read and write each
+                // column 8cb + j of X_{k+1}^T, rows 4rb..4rb+3: one 16-byte read of X_k and one write
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    float4* xp = reinterpret_cast<float4*>(xt + (8 * cb + j) * XTP + 4 * rb);
-                    float4 v = *xp;
+                    float4 v = *reinterpret_cast<const float4*>(cur + (8 * cb + j) * XTP + 4 * rb);
                     v.x = fmaT(cc, acc[0][j], v.x);
                     v.y = fmaT(cc, acc[1][j], v.y);
                     v.z = fmaT(cc, acc[2][j], v.z);
                     v.w = fmaT(cc, acc[3][j], v.w);
-                    *xp = v;
+                    *reinterpret_cast<float4*>(nxt + (8 * cb + j) * XTP + 4 * rb) = v;
                 }
             }
-            __syncthreads();   // X_{k+1} complete
+            __syncthreads();   // X_{k+1} complete, and every read of X_k done before it is overwritten
         }
         // X_T into the staging area in storage order (A is no longer needed)
+        const T* xf = (steps & 1) ? xt1 : xt0;
         if (active)
             for (int e = w; e < NN; e += TPI) {
                 const int i = e / N, j = e - i * N;
-                sA[inst * P + (LAYOUT == 0 ? i * N + j : j * N + i)] = xt[j * XTP + i];
+                sA[inst * P + (LAYOUT == 0 ? i * N + j : j * N + i)] = xf[j * XTP + i];
             }
     } else if constexpr (MAP == 6) {
         static_assert(sizeof(T) == 4, "mapping 6 is FP32");

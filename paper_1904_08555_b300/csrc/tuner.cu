@@ -260,9 +260,11 @@ cj_status candidates(int k, const cj_template_args &a, std::vector<std::array<in
     out.clear();
     if (k == CJ_K_LTIMES || k == CJ_K_LPLUSTIMES) ltimes_candidates(lt_swapped(k, a), out);
     else if (k == CJ_K_MASS) {
-        for (int epb : {1, 2, 4, 8, 16, 32, 64})
-            if (cjg::mass_threads(a.n, a.m, epb) <= 1024 && cjg::mass_smem(a.d, a.n, a.m, epb, esize(a.dtype)) <= 200 * 1024)
-                out.push_back({epb, 0, 0, 0});
+        for (int pipe : {0, 1})   // one group per block; persistent with staged loads
+            for (int epb : {1, 2, 4, 8, 16, 32, 64})
+                if (cjg::mass_threads(a.n, a.m, epb) <= 1024 &&
+                    cjg::mass_smem(a.d, a.n, a.m, epb, esize(a.dtype), pipe) <= 200 * 1024)
+                    out.push_back({epb, pipe, 0, 0});
     } else if (k == CJ_K_EIGEN_RECURRENCE) {
         for (int map : {1, 2}) {
             if (map == 2 && a.dtype != CJ_F32) continue;

@@ -180,3 +180,37 @@ def test_tensor_core_register_cap_fits_the_sub_partitions(tmp_path):
         # maximal: 255, or a multiple of 8 whose next multiple no longer fits
         assert regs == 255 or (regs % 8 == 0 and busiest * 32 * (regs + 8) > 16384)
         assert (5 + w) * 32 * regs <= 65536      # the whole block fits the SM's register file
+
+
+M8_PROG = r"""
+#include <cstdio>
+#include "geometry.h"
+int main() {
+    for (int n = 8; n <= 64; ++n)
+        std::printf("%d %d %d %d %d %ld\n", n, cjg::chain_m8_xti(n), cjg::chain_arow(n, 8, 4),
+                    cjg::chain_threads(n, 8, 3), cjg::chain_pitch(n, 8, 4), cjg::chain_smem(n, 8, 3, 4));
+    return 0;
+}
+"""
+
+
+def test_four_by_eight_register_blocks_layout(tmp_path):
+    """Mapping 8 (FP32, 4 x 8 register blocks): A rows padded to a multiple of
+    8 columns; one instance's X^T holds (n padded to 8) rows of (n padded to
+    4) + 4 floats and is padded to an odd number of 16-byte units (the copies
+    a warp reads then start in different bank groups); threads are
+    ceil(n/4) * ceil(n/8) per instance, rounded up to whole warps; shared
+    memory is A's staging plus two copies of X^T (read one, write the
+    other), per instance."""
+    src, exe = tmp_path / "m8.cpp", tmp_path / "m8"
+    src.write_text(M8_PROG)
+    subprocess.run(["g++", "-std=c++17", "-O1", "-I", CSRC, "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    for line in (l for l in out if l.strip()):
+        n, xti, arow, threads, pitch, smem = (int(v) for v in line.split())
+        nr, nc = -(-n // 4) * 4, -(-n // 8) * 8
+        assert arow == nc
+        assert xti in (nc * (nr + 4), nc * (nr + 4) + 4) and xti % 4 == 0 and (xti // 4) % 2 == 1
+        assert threads == -(-(3 * (nr // 4) * (nc // 8)) // 32) * 32
+        assert pitch >= n * nc and pitch % 4 == 0 and (pitch // 4) % 2 == 1
+        assert smem == 3 * (pitch + 2 * xti) * 4

@@ -17,6 +17,14 @@ pytestmark = pytest.mark.gpu
 TOL64, TOL32 = 1e-12, 1e-5
 
 
+def tol32(dim, D, Q):
+    """FP32 bound: each of the 2 dim stages is a dot product of length at most
+    max(D, Q), whose rounding error is at most that length times the unit
+    roundoff 2^-24 relative to the sum of |terms|; a factor 4 allows for the
+    cancellation between terms.  At least 1e-5, the library's FP32 tolerance."""
+    return max(TOL32, 4 * 2 * dim * max(D, Q) * 2.0 ** -24)
+
+
 @pytest.fixture(scope="module", autouse=True)
 def lib():
     if not torch.cuda.is_available():
@@ -59,7 +67,7 @@ def test_mass_against_oracle(dim, D, Q, dt, generic):
     ref = oracle.mass(B1, op, x, dim, nthreads=4)
     y = run_mass(h, B1, op, x, dt)
     assert np.all(np.isfinite(y))
-    assert max_rel_err(y, ref) <= (TOL64 if dt == cj.F64 else TOL32)
+    assert max_rel_err(y, ref) <= (TOL64 if dt == cj.F64 else tol32(dim, D, Q))
 
 
 @pytest.mark.parametrize("dim,D,Q,epb", [(2, 3, 4, 1), (2, 4, 6, 3), (2, 4, 6, 16), (3, 3, 4, 2), (3, 5, 8, 1),
@@ -106,3 +114,40 @@ def test_mass_full_size_sampled(dim, D, Q, dt):
     it = torch.from_numpy(idx).cuda()
     ref = oracle.mass(Bt.double().cpu().numpy(), op[it].double().cpu().numpy(), x[it].double().cpu().numpy(), dim)
     assert max_rel_err(y[it].double().cpu().numpy(), ref) <= (TOL64 if dt == cj.F64 else TOL32)
+
+
+PIPE_SHAPES = [(2, 2, 3), (2, 3, 4), (2, 5, 8), (2, 16, 16), (3, 2, 3), (3, 4, 6), (3, 5, 8), (3, 8, 8)]
+
+
+@pytest.mark.parametrize("dim,D,Q", PIPE_SHAPES)
+@pytest.mark.parametrize("dt", [cj.F64, cj.F32])
+def test_mass_persistent_staged(dim, D, Q, dt):
+    """Tile {epb, 1}: a persistent grid whose blocks stage the next group's x and
+    op with cp.async while computing the current one.  Enough elements that every
+    block runs several groups (the grid is at most 148 SMs x 8 blocks), with a
+    ragged last group."""
+    epb = max(1, 256 // max(D, Q) ** 2)
+    h = cj.specialize(cj.K_MASS, dt, n=D, m=Q, d=dim, tile=(epb, 1, 0, 0))
+    assert h.variant == "jit"
+    ne = 3 * 148 * 8 * epb + 5
+    B1, op, x = synth.mass_inputs_np(synth.SEED_MASS, dim, D, Q, ne)
+    if dt == cj.F32:
+        B1, op, x = (a.astype(np.float32).astype(np.float64) for a in (B1, op, x))
+    ref = oracle.mass(B1, op, x, dim, nthreads=8)
+    y = run_mass(h, B1, op, x, dt)
+    assert np.all(np.isfinite(y))
+    assert max_rel_err(y, ref) <= (TOL64 if dt == cj.F64 else tol32(dim, D, Q))
+
+
+@pytest.mark.parametrize("ne", [1, 2, 5, 37])
+def test_mass_persistent_small_batches(ne):
+    """Fewer elements than one group, and fewer groups than blocks."""
+    h = cj.specialize(cj.K_MASS, cj.F64, n=4, m=6, d=3, tile=(7, 1, 0, 0))
+    B1, op, x = synth.mass_inputs_np(synth.SEED_MASS, 3, 4, 6, ne)
+    ref = oracle.mass(B1, op, x, 3)
+    assert max_rel_err(run_mass(h, B1, op, x, cj.F64), ref) <= TOL64
+
+
+def test_mass_persistent_tile_is_validated():
+    with pytest.raises(cj.CJError):
+        cj.specialize(cj.K_MASS, cj.F64, n=4, m=6, d=3, tile=(7, 2, 0, 0))
