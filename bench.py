@@ -693,9 +693,14 @@ def _mass_case(torch, cj, stream, oracle, dt, tdt, es, dim, D, Q, ne, K, W, samp
     f = mass_flops(dim, D, Q) * ne
     row = {"dim": dim, "D": D, "Q": Q, "elements": ne, "laghos_key": hex((dim << 16) | ((D - 1) << 8) | (Q >> 1))}
     worst = 0.0
-    for name, fl in (("spec", 0), ("generic", cj.FLAG_GENERIC), ("staged", 0)):
-        # staged: the default tile's elements per block on the persistent kernel with staged loads
-        tile = (row["tile"][0], 1, 0, 0) if name == "staged" else (0, 0, 0, 0)
+    forms = [("spec", 0), ("generic", cj.FLAG_GENERIC), ("staged", 0)]
+    if dim == 2 and D * Q + D * D <= 80:
+        forms.append(("thread", 0))
+    for name, fl in forms:
+        # staged: the default tile's elements per block on the persistent kernel with staged loads;
+        # thread: 2-D, one thread per element (128 per block)
+        tile = ((row["tile"][0], 1, 0, 0) if name == "staged" else (128, 2, 0, 0) if name == "thread"
+                else (0, 0, 0, 0))
         h = cj.specialize(cj.K_MASS, dt, n=D, m=Q, d=dim, flags=fl, tile=tile)
         h.wait()
         fn = lambda h=h: cj.launch_mass(h, Bt, op, x, y, ne, stream=stream)
@@ -714,6 +719,8 @@ def _mass_case(torch, cj, stream, oracle, dt, tdt, es, dim, D, Q, ne, K, W, samp
             row["tile"] = _key_tile(h)
     row["speedup_vs_generic"] = row["generic_us"] / row["spec_us"]
     row["staged_speedup"] = row["spec_us"] / row["staged_us"]
+    if "thread_us" in row:
+        row["thread_speedup"] = row["spec_us"] / row["thread_us"]
     return row, f, worst
 
 

@@ -151,10 +151,15 @@ typedef struct {
  *     else {1, max(1, 128 / n)}; bf16 -> {3, max(1, 128 / n16)} with n16 = n
  *     rounded up to a multiple of 16 (mapping 3: one warp per 16 rows,
  *     bf16 operands, fp32 accumulate and state).
- *   mass operator: {elements per block, 0, 0, 0}; an element owns
- *     max(D, Q)^2 threads and two shared-memory buffers of max(D, Q)^d values.
- *     Default: max(1, 256 / max(D, Q)^2) elements, fewer if the buffers of a
- *     block would exceed 96 KiB.
+ *   mass operator: {elements per block, form, 0, 0}; form 0: an element owns
+ *     max(D, Q)^2 threads and two shared-memory buffers of max(D, Q)^d values;
+ *     form 1: the same on a persistent grid whose blocks stage the next
+ *     group's x and op with cp.async while computing the current one (two
+ *     stages of x and op in shared memory besides); form 2 (2-D with
+ *     D Q + D^2 <= 80): one thread per element, every stage in registers.
+ *     Default: form 2 with 128 elements where it applies, else form 0 with
+ *     max(1, 256 / max(D, Q)^2) elements, fewer if the buffers of a block
+ *     would exceed 96 KiB.
  *   Eigen recurrence: {mapping, instances per block, 0, 0}; M_k of every
  *     instance in shared memory, two buffers; mapping 1 = one thread per row
  *     of M, 2 = two rows per thread (rows h and h + ceil(n / 2); f32 only;

@@ -189,16 +189,23 @@ CJ_HD constexpr long lt_generic_smem(int m, int d, int cols, int esize) {
 // Mass operator (mass.cuh): an element owns M x M threads, M = max(D, Q);
 // shared memory holds B1 (Q x D) and two buffers of M^dim values per element.
 CJ_HD constexpr int mass_m(int D, int Q) { return D > Q ? D : Q; }
-CJ_HD constexpr int mass_threads(int D, int Q, int epb) { return ((epb * mass_m(D, Q) * mass_m(D, Q) + 31) / 32) * 32; }
-CJ_HD constexpr int mass_b_elems(int D, int Q) { return Q * D; }
-// pipe = 1 (the persistent kernel): two stages of every element's x (D^dim)
-// and op (Q^dim) values besides.
-CJ_HD constexpr long mass_smem(int dim, int D, int Q, int epb, int esize, int pipe = 0) {
-    return ((long)mass_b_elems(D, Q) +
-            2L * epb * (dim == 2 ? mass_m(D, Q) * mass_m(D, Q) : mass_m(D, Q) * mass_m(D, Q) * mass_m(D, Q)) +
-            (pipe ? 2L * epb * (dim == 2 ? D * D + Q * Q : D * D * D + Q * Q * Q) : 0L)) *
-           esize;
+// form 2 (2-D, one thread per element, every stage in registers): epb threads.
+CJ_HD constexpr int mass_threads(int D, int Q, int epb, int form = 0) {
+    return form == 2 ? (epb + 31) / 32 * 32 : ((epb * mass_m(D, Q) * mass_m(D, Q) + 31) / 32) * 32;
 }
+CJ_HD constexpr int mass_b_elems(int D, int Q) { return Q * D; }
+// form 1 (the persistent kernel): two stages of every element's x (D^dim)
+// and op (Q^dim) values besides; form 2: B1 only.
+CJ_HD constexpr long mass_smem(int dim, int D, int Q, int epb, int esize, int form = 0) {
+    return form == 2 ? (long)mass_b_elems(D, Q) * esize
+                     : ((long)mass_b_elems(D, Q) +
+                        2L * epb * (dim == 2 ? mass_m(D, Q) * mass_m(D, Q) : mass_m(D, Q) * mass_m(D, Q) * mass_m(D, Q)) +
+                        (form ? 2L * epb * (dim == 2 ? D * D + Q * Q : D * D * D + Q * Q * Q) : 0L)) *
+                           esize;
+}
+// Form 2 keeps an element's D x Q first-stage values and its D x D result in
+// registers: allowed while D Q + D^2 <= 80.
+CJ_HD constexpr bool mass_thread_ok(int dim, int D, int Q) { return dim == 2 && D * Q + D * D <= 80; }
 
 }  // namespace cjg
 

@@ -219,6 +219,72 @@ mass_apply_pipe(const T* __restrict__ B1, const T* __restrict__ op, const T* __r
     asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
+// 2-D, one thread per element (tile {EPB, 2, 0, 0}): the same four
+// contractions and the scaling, every value in the thread's registers and
+// no barrier after B1 is staged.  The x stage T1[jy][qx] = sum_jx
+// B1[qx][jx] X[jy][jx] is kept whole (D x Q); the rest goes one quadrature
+// row qy at a time: T2[qx] = op[qy][qx] sum_jy B1[qy][jy] T1[jy][qx],
+// T3[jx] = sum_qx B1[qx][jx] T2[qx], and Y[jy][jx] += B1[qy][jy] T3[jx].
+// Each thread reads its element's x and op rows through L1 (a warp's
+// elements are contiguous, so every line it touches is used whole).
+template <class T, int D, int Q, int EPB>
+__global__ void __launch_bounds__(cjg::mass_threads(D, Q, EPB, 2))
+mass_apply_thread(const T* __restrict__ B1, const T* __restrict__ op, const T* __restrict__ x, T* __restrict__ y,
+                  long long ne) {
+    static_assert(cjg::mass_thread_ok(2, D, Q), "one thread per element keeps D Q + D^2 <= 80 values");
+    extern __shared__ __align__(16) unsigned char cj_smem[];
+    T* b = reinterpret_cast<T*>(cj_smem);   // B1, Q x D (cjg::mass_smem, form 2)
+    for (int i = threadIdx.x; i < Q * D; i += blockDim.x) b[i] = B1[i];
+    __syncthreads();
+    const long long e = (long long)blockIdx.x * EPB + threadIdx.x;
+    if (threadIdx.x >= EPB || e >= ne) return;
+    const T* xe = x + e * (D * D);
+    const T* oe = op + e * (Q * Q);
+    T t1[D][Q];
+#pragma unroll
+    for (int jy = 0; jy < D; ++jy) {
+        T xr[D];
+#pragma unroll
+        for (int jx = 0; jx < D; ++jx) xr[jx] = __ldg(xe + jy * D + jx);
+#pragma unroll
+        for (int qx = 0; qx < Q; ++qx) {
+            T s = T(0);
+#pragma unroll
+            for (int jx = 0; jx < D; ++jx) s = mass_fma(b[qx * D + jx], xr[jx], s);
+            t1[jy][qx] = s;
+        }
+    }
+    T yv[D][D];
+#pragma unroll
+    for (int jy = 0; jy < D; ++jy)
+#pragma unroll
+        for (int jx = 0; jx < D; ++jx) yv[jy][jx] = T(0);
+#pragma unroll
+    for (int qy = 0; qy < Q; ++qy) {
+        T t2[Q];
+#pragma unroll
+        for (int qx = 0; qx < Q; ++qx) {
+            T s = T(0);
+#pragma unroll
+            for (int jy = 0; jy < D; ++jy) s = mass_fma(b[qy * D + jy], t1[jy][qx], s);
+            t2[qx] = __ldg(oe + qy * Q + qx) * s;
+        }
+#pragma unroll
+        for (int jx = 0; jx < D; ++jx) {
+            T s = T(0);
+#pragma unroll
+            for (int qx = 0; qx < Q; ++qx) s = mass_fma(b[qx * D + jx], t2[qx], s);
+#pragma unroll
+            for (int jy = 0; jy < D; ++jy) yv[jy][jx] = mass_fma(b[qy * D + jy], s, yv[jy][jx]);
+        }
+    }
+    T* ye = y + e * (D * D);
+#pragma unroll
+    for (int jy = 0; jy < D; ++jy)
+#pragma unroll
+        for (int jx = 0; jx < D; ++jx) ye[jy * D + jx] = yv[jy][jx];
+}
+
 // Generic: run-time dimension, D, Q and elements per block (the same stages
 // with run-time loop bounds).
 template <class T>

@@ -265,6 +265,8 @@ cj_status candidates(int k, const cj_template_args &a, std::vector<std::array<in
                 if (cjg::mass_threads(a.n, a.m, epb) <= 1024 &&
                     cjg::mass_smem(a.d, a.n, a.m, epb, esize(a.dtype), pipe) <= 200 * 1024)
                     out.push_back({epb, pipe, 0, 0});
+        if (cjg::mass_thread_ok(a.d, a.n, a.m))   // 2-D, one thread per element
+            for (int epb : {64, 128, 256}) out.push_back({epb, 2, 0, 0});
     } else if (k == CJ_K_EIGEN_RECURRENCE) {
         for (int map : {1, 2}) {
             if (map == 2 && a.dtype != CJ_F32) continue;

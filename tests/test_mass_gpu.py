@@ -151,3 +151,31 @@ def test_mass_persistent_small_batches(ne):
 def test_mass_persistent_tile_is_validated():
     with pytest.raises(cj.CJError):
         cj.specialize(cj.K_MASS, cj.F64, n=4, m=6, d=3, tile=(7, 2, 0, 0))
+
+
+THREAD_SHAPES = [(1, 1), (2, 2), (2, 3), (3, 4), (4, 6), (4, 8), (5, 8), (6, 3), (8, 2)]
+
+
+@pytest.mark.parametrize("D,Q", THREAD_SHAPES)
+@pytest.mark.parametrize("dt", [cj.F64, cj.F32])
+@pytest.mark.parametrize("epb", [64, 128])
+def test_mass_thread_per_element(D, Q, dt, epb):
+    """Tile {epb, 2}: 2-D elements, one thread each, every stage in registers;
+    several blocks and a ragged last one."""
+    h = cj.specialize(cj.K_MASS, dt, n=D, m=Q, d=2, tile=(epb, 2, 0, 0))
+    assert h.variant == "jit"
+    ne = 5 * epb + 3
+    B1, op, x = synth.mass_inputs_np(synth.SEED_MASS, 2, D, Q, ne)
+    if dt == cj.F32:
+        B1, op, x = (a.astype(np.float32).astype(np.float64) for a in (B1, op, x))
+    ref = oracle.mass(B1, op, x, 2, nthreads=4)
+    y = run_mass(h, B1, op, x, dt)
+    assert np.all(np.isfinite(y))
+    assert max_rel_err(y, ref) <= (TOL64 if dt == cj.F64 else tol32(2, D, Q))
+
+
+def test_mass_thread_per_element_is_validated():
+    with pytest.raises(cj.CJError):   # 3-D
+        cj.specialize(cj.K_MASS, cj.F64, n=3, m=4, d=3, tile=(128, 2, 0, 0))
+    with pytest.raises(cj.CJError):   # D Q + D^2 = 96 values per thread
+        cj.specialize(cj.K_MASS, cj.F64, n=6, m=10, d=2, tile=(128, 2, 0, 0))
