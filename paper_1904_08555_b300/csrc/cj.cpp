@@ -24,6 +24,7 @@
 #include <condition_variable>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <mutex>
@@ -805,6 +806,23 @@ cj_status compile_handle(cj_handle_s *h) {
     return CJ_OK;
 }
 
+// At process exit without cj_shutdown: stop the compile threads (a compile
+// in flight finishes first).  Registered with atexit by cj_init, after the
+// statically linked NVRTC and runtime have built their own static state, so
+// it runs before their destructors; a thread still inside NVRTC while they
+// ran would crash the process on its way out.
+void stop_workers_at_exit() {
+    {
+        std::lock_guard<std::mutex> lk(G.mu);
+        G.stop = true;
+        G.queue.clear();
+    }
+    G.qcv.notify_all();
+    for (auto &t : G.workers)
+        if (t.joinable()) t.join();
+    G.workers.clear();
+}
+
 void worker_loop() {
     if (!G.compile_only) cudaSetDevice(G.device);
     for (;;) {
@@ -1196,6 +1214,8 @@ CJ_API cj_status cj_init(const cj_config *cfg, int device) {
         G.lookup_ns.clear();
         G.lookup_pos = 0;
     }
+    static std::once_flag exit_hook;
+    std::call_once(exit_hook, [] { std::atexit(stop_workers_at_exit); });
     for (uint32_t i = 0; i < c.compile_threads; ++i) G.workers.emplace_back(worker_loop);
     G.inited = true;
     t_err.clear();

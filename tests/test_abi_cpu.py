@@ -389,3 +389,20 @@ def test_eigen_recurrence_requests(compile_only_sync):
             assert key[3:5] == bytes(2) and key[8:12] == bytes(4) and h.variant == "jit"
             for tile in cj.candidates(cj.K_EIGEN_RECURRENCE, dt, n=n):
                 cj.specialize(cj.K_EIGEN_RECURRENCE, dt, n=n, tile=tile)
+
+
+def test_exit_without_shutdown_while_compiling():
+    """A process that exits with a run-time compile still in flight and never
+    calls cj_shutdown exits cleanly: the library stops its compile threads at
+    exit, before the statically linked compiler's own state is torn down."""
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_1904_08555_b300 import cj\n"
+            "cj.init(compile_only=True, compile_threads=2)\n"
+            "cj.specialize(cj.K_LTIMES, cj.F32, layout_a=0, layout_b=1, m=64, d=128)\n"
+            "cj.specialize(cj.K_UPDATE_CHAIN, cj.F32, n=61)\n"
+            "print('exiting')\n") % ROOT
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, (r.returncode, r.stderr[-2000:])
+    assert "exiting" in r.stdout
