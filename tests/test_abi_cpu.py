@@ -406,3 +406,50 @@ def test_exit_without_shutdown_while_compiling():
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, (r.returncode, r.stderr[-2000:])
     assert "exiting" in r.stdout
+
+
+def test_concurrent_requests_share_one_cache_entry():
+    """The cache is program-global: eight host threads requesting the same
+    instantiations at once (ctypes drops the GIL for the call) get one handle
+    per distinct request, each key equal to the request's canonical key, and
+    each distinct request compiled once."""
+    import threading
+    from oracle import keys as K
+    cj.init(compile_only=True, compile_threads=4)
+    try:
+        reqs = [(cj.K_UPDATE_CHAIN, cj.F64, n, 0, 0, 0, 0) for n in (3, 5, 7, 9, 12, 17, 24)] + \
+               [(cj.K_UPDATE_CHAIN, cj.F32, n, 1, 0, 0, 0) for n in (6, 10, 40)] + \
+               [(cj.K_LTIMES, cj.F64, 0, la, lb, 36, 96) for la, lb in ((0, 0), (2, 5), (4, 1))]
+        got = [dict() for _ in range(8)]
+        errors = []
+        start = threading.Barrier(8)
+
+        def worker(t):
+            try:
+                start.wait()
+                order = reqs[t % len(reqs):] + reqs[:t % len(reqs)]   # every thread in its own order
+                for r in order:
+                    got[t][r] = cj.specialize(*r)
+            except Exception as e:   # reported below
+                errors.append(e)
+
+        threads = [threading.Thread(target=worker, args=(t,)) for t in range(8)]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join()
+        assert not errors, errors
+        for r in reqs:
+            hs = {got[t][r].ptr for t in range(8)}
+            assert len(hs) == 1, r
+            h = got[0][r]
+            assert h.wait() == cj.CJ_OK
+            tile = K.parse_key(bytes.fromhex(h.key_hex))["tile"]
+            k, dt, n, la, lb, m, d = r
+            assert h.key_hex == K.canonical_key(k, dt, n, la, lb, m, d, tile, 0).hex(), r
+        s = cj.stats()
+        assert s["requests"] == 8 * len(reqs)
+        assert s["compiles_ok"] + s["compiles_failed"] == len(reqs)
+        assert s["cache_hits"] == 8 * len(reqs) - len(reqs)
+    finally:
+        cj.shutdown()
