@@ -453,3 +453,39 @@ def test_concurrent_requests_share_one_cache_entry():
         assert s["cache_hits"] == 8 * len(reqs) - len(reqs)
     finally:
         cj.shutdown()
+
+
+NEW_TILE_CASES = [
+    # (kernel, dtype, n, la, lb, m, d, tile, valid)
+    (cj.K_LTIMES, cj.F32, 0, 0, 0, 36, 96, (1, 128, 320, (6 << 20) | (6 << 16) | (4 << 8) | 4), True),
+    (cj.K_LTIMES, cj.F32, 0, 3, 5, 64, 64, (1, 128, 448, (4 << 20) | (6 << 16) | (6 << 8) | 8), True),
+    (cj.K_LTIMES, cj.F32, 0, 0, 0, 64, 64, (1, 128, 448, (4 << 20) | (6 << 16) | (7 << 8) | 8), False),  # 576 TMEM cols
+    (cj.K_LTIMES, cj.F32, 0, 0, 0, 36, 96, (1, 128, 256, (4 << 20) | (6 << 16) | (2 << 8) | 2), False),  # 2 converters
+    (cj.K_LTIMES, cj.F64, 0, 0, 0, 36, 96, (1, 128, 320, (6 << 20) | (6 << 16) | (4 << 8) | 4), False),  # f64
+    (cj.K_LTIMES, cj.F32, 0, 0, 0, 36, 96, (1, 128, 320, (1 << 20) | (6 << 16) | (4 << 8) | 4), False),  # 1 box
+    (cj.K_UPDATE_CHAIN, cj.F32, 33, 0, 0, 0, 0, (8, 3, 0, 0), True),
+    (cj.K_UPDATE_CHAIN_GROUPED, cj.F32, 64, 0, 0, 0, 0, (8, 2, 0, 0), True),
+    (cj.K_UPDATE_CHAIN, cj.F64, 33, 0, 0, 0, 0, (8, 3, 0, 0), False),   # mapping 8 is f32
+    (cj.K_UPDATE_CHAIN, cj.F32, 7, 0, 0, 0, 0, (8, 3, 0, 0), False),    # n >= 8
+    (cj.K_UPDATE_CHAIN, cj.F32, 33, 0, 0, 0, 0, (9, 3, 0, 0), False),   # no mapping 9
+    (cj.K_MASS, cj.F32, 4, 0, 0, 6, 2, (128, 2, 0, 0), True),
+    (cj.K_MASS, cj.F64, 5, 0, 0, 8, 3, (4, 1, 0, 0), True),
+    (cj.K_MASS, cj.F64, 4, 0, 0, 6, 3, (128, 2, 0, 0), False),          # form 2 is 2-D
+    (cj.K_MASS, cj.F64, 6, 0, 0, 10, 2, (128, 2, 0, 0), False),         # D Q + D^2 = 96 > 80
+    (cj.K_MASS, cj.F64, 4, 0, 0, 6, 2, (128, 3, 0, 0), False),          # no form 3
+]
+
+
+@pytest.mark.parametrize("case", NEW_TILE_CASES)
+def test_tensor_memory_register_block_and_mass_form_tiles(compile_only_sync, case):
+    """LTimes mode 6 (operands in tensor memory), chain mapping 8 (4 x 8 register
+    blocks) and the mass operator's forms 1 and 2: valid tiles compile (run-time
+    instantiations), invalid ones are refused before any compile."""
+    k, dt, n, la, lb, m, d, tile, valid = case
+    if valid:
+        h = cj.specialize(k, dt, n, la, lb, m, d, tile)
+        assert h.variant == "jit"
+    else:
+        with pytest.raises(cj.CJError) as e:
+            cj.specialize(k, dt, n, la, lb, m, d, tile)
+        assert e.value.status == cj.CJ_ERR_INVALID_ARG
