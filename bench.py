@@ -334,27 +334,51 @@ def cj_arm(args):
     traffic = TRAFFIC_PER_INSTANCE.get(dom_name)
     traffic = traffic * batch[dom] if traffic is not None else None
 
-    # end to end through the C ABI with host buffers: H2D of A, launch, D2H of X, every size
+    # end to end through the C ABI with host buffers: every step copies each
+    # size's A in from pinned host memory, launches, and copies its X out.
+    # The copies run on two copy streams, so that size n's copy-in and size
+    # n-1's copy-out overlap size n-1's and n's compute, as a pipelined
+    # caller runs them; events order each buffer's reuse across steps (A[n]
+    # is rewritten once the previous launch read it, X[n] once the previous
+    # copy-out read it).  Every copy of every step is inside the timed region.
     h2d = sum(chain_bytes(batch[n], n, 8) / 2 for n in SWEEP_N)
     host_A = {n: A[n].cpu().pin_memory() for n in SWEEP_N}
     host_X = {n: torch.empty(A[n].shape, dtype=torch.float64).pin_memory() for n in SWEEP_N}
+    copy_in, copy_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    ev_in = {n: torch.cuda.Event() for n in SWEEP_N}     # A[n] copied in
+    ev_run = {n: torch.cuda.Event() for n in SWEEP_N}    # X[n] computed; A[n] read
+    ev_out = {n: torch.cuda.Event() for n in SWEEP_N}    # X[n] copied out
 
-    def e2e_step():
+    def e2e_step(first):
         for n in SWEEP_N:
-            A[n].copy_(host_A[n], non_blocking=True)
+            if not first:
+                copy_in.wait_event(ev_run[n])
+            with torch.cuda.stream(copy_in):
+                A[n].copy_(host_A[n], non_blocking=True)
+            ev_in[n].record(copy_in)
+            stream.wait_event(ev_in[n])
+            if not first:
+                stream.wait_event(ev_out[n])
             h = cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=n, flags=cj.FLAG_NO_AOT)
             cj.launch_update_chain(h, A[n], X[n], T_STEPS, stream=stream)
-            host_X[n].copy_(X[n], non_blocking=True)
+            ev_run[n].record(stream)
+            copy_out.wait_event(ev_run[n])
+            with torch.cuda.stream(copy_out):
+                host_X[n].copy_(X[n], non_blocking=True)
+            ev_out[n].record(copy_out)
 
     with torch.cuda.stream(stream):
-        e2e_step()
-        stream.synchronize()
+        e2e_step(True)
+        torch.cuda.synchronize(dev)
         barrier(world)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
+        copy_in.wait_event(e0)      # no copy starts before the timed region
+        copy_out.wait_event(e0)
         for _ in range(args.steps):
-            e2e_step()
+            e2e_step(False)
+        stream.wait_event(ev_out[SWEEP_N[-1]])   # the last copy-out ends the region
         e1.record(stream)
         e1.synchronize()
     ms_e2e = max_over_ranks(world, e0.elapsed_time(e1))
