@@ -62,9 +62,10 @@ void chain_candidates(const cj_template_args &a, std::vector<std::array<int, 4>>
         for (int ipb : {1, 2, 4, 8, 16, 32, 64})
             if (ok(8, ipb) && cjg::chain_threads(n, 8, ipb) >= 128 && cjg::chain_threads(n, 8, ipb) <= 512)
                 out.push_back({8, ipb, 0, 0});
-    if (a.dtype == CJ_F32 && n >= 8)
+    if (a.dtype == CJ_F32 && n >= 8)   // 4 x 4 blocks: from n = 16 on, mapping 8's space covers the large blocks
         for (int ipb : {1, 2, 4, 8, 16, 32})
-            if (ok(5, ipb) && cjg::chain_threads(n, 5, ipb) >= 64) out.push_back({5, ipb, 0, 0});
+            if (ok(5, ipb) && cjg::chain_threads(n, 5, ipb) >= 64 && (n < 16 || cjg::chain_threads(n, 5, ipb) <= 256))
+                out.push_back({5, ipb, 0, 0});
     if (a.dtype == CJ_F32)
         for (int ipb : {1, 2, 4, 8, 16, 32})
             if (ok(6, ipb) && cjg::chain_threads(n, 6, ipb) >= 64) out.push_back({6, ipb, 0, 0});
@@ -144,7 +145,6 @@ void ltimes_candidates(const cj_template_args &a, std::vector<std::array<int, 4>
             push(tg, 64, 0, 2, 12, 1);          // FMA, cp.async double buffer
             push(tg, 256, 3, 2, 0, 0);          // direct loads, all moments per thread
             if (a.m > 12) push(tg, 128, 3, 2, 12, 0);   // direct loads, 12 moments per thread
-            push(tg, 128, 0, 4, 12, 0);         // unpipelined baseline
         }
     }
 }
@@ -260,9 +260,9 @@ cj_status candidates(int k, const cj_template_args &a, std::vector<std::array<in
     out.clear();
     if (k == CJ_K_LTIMES || k == CJ_K_LPLUSTIMES) ltimes_candidates(lt_swapped(k, a), out);
     else if (k == CJ_K_MASS) {
-        for (int pipe : {0, 1})   // one group per block; persistent with staged loads
+        for (int pipe : {0, 1})   // one group per block (7 sizes); persistent with staged loads (3)
             for (int epb : {1, 2, 4, 8, 16, 32, 64})
-                if (cjg::mass_threads(a.n, a.m, epb) <= 1024 &&
+                if ((pipe == 0 || epb == 4 || epb == 16 || epb == 64) && cjg::mass_threads(a.n, a.m, epb) <= 1024 &&
                     cjg::mass_smem(a.d, a.n, a.m, epb, esize(a.dtype), pipe) <= 200 * 1024)
                     out.push_back({epb, pipe, 0, 0});
         if (cjg::mass_thread_ok(a.d, a.n, a.m))   // 2-D, one thread per element

@@ -290,7 +290,7 @@ def test_compiles_open_no_file_when_pwd_is_set(tmp_path):
 def test_every_candidate_tile_is_a_valid_request(compile_only_sync, req):
     k = req.pop("kernel")
     cands = cj.candidates(k, **req)
-    assert 2 <= len(cands) <= 20
+    assert 2 <= len(cands) <= 16
     assert len(set(cands)) == len(cands)
     for tile in cands[:3]:
         h = cj.specialize(k, tile=tile, **req)      # compiles in compile-only mode
@@ -489,3 +489,27 @@ def test_tensor_memory_register_block_and_mass_form_tiles(compile_only_sync, cas
         with pytest.raises(cj.CJError) as e:
             cj.specialize(k, dt, n, la, lb, m, d, tile)
         assert e.value.status == cj.CJ_ERR_INVALID_ARG
+
+
+def test_every_candidate_space_has_at_most_16_tiles(compile_only_sync):
+    """The autotuner's variant space V(kernel, dtype) holds at most 16 tiles for
+    every request shape: the chains at every n and dtype, LTimes and
+    LPlusTimes at every pair of storage orders, the mass operator at every
+    dimension, D and Q up to 8."""
+    sizes = []
+    for dt in (cj.F64, cj.F32, cj.BF16):
+        for n in range(16 if dt == cj.BF16 else 1, 65):
+            for k in (cj.K_UPDATE_CHAIN, cj.K_UPDATE_CHAIN_GROUPED):
+                sizes.append(((k, dt, n), len(cj.candidates(k, dt, n=n))))
+    for dt in (cj.F64, cj.F32):
+        for la in range(6):
+            for lb in range(6):
+                for k in (cj.K_LTIMES, cj.K_LPLUSTIMES):
+                    sizes.append(((k, dt, la, lb), len(cj.candidates(k, dt, layout_a=la, layout_b=lb, m=36, d=96))))
+    for dt in (cj.F64, cj.F32):
+        for dim in (2, 3):
+            for D in range(1, 9):
+                for Q in range(1, 9):
+                    sizes.append(((cj.K_MASS, dt, dim, D, Q), len(cj.candidates(cj.K_MASS, dt, n=D, m=Q, d=dim))))
+    bad = [(req, c) for req, c in sizes if not 1 <= c <= 16]
+    assert not bad, bad[:10]
