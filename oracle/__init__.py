@@ -50,33 +50,38 @@ def _load():
     global _lib
     if _lib is None:
         build()
-        lib = ctypes.CDLL(_LIB)
-        P = ctypes.c_void_p
-        i32, i64, f64 = ctypes.c_int, ctypes.c_int64, ctypes.c_double
-        lib.oracle_update_chain.argtypes = [i32, i32, i32, i64, P, P, i32]
-        lib.oracle_update_chain.restype = i32
-        lib.oracle_update_chain_uneven.argtypes = [i64, P, P, P, P, P]
-        lib.oracle_update_chain_uneven.restype = i32
-        lib.oracle_ltimes.argtypes = [i32, i32, i64, i64, i32, i32, P, P, P, i32]
-        lib.oracle_ltimes.restype = i32
-        lib.oracle_ltimes_sample.argtypes = [i32, i32, i64, i64, i32, P, P, i64, P, P]
-        lib.oracle_lplustimes.argtypes = [i32, i32, i64, i64, i32, i32, P, P, P]
-        lib.oracle_lplustimes.restype = i32
-        lib.oracle_ltimes_sample.restype = i32
-        lib.oracle_mlp_forward.argtypes = [i32, i32, i64] + [P] * 10
-        lib.oracle_mlp_forward.restype = None
-        lib.oracle_mlp_loss_grad.argtypes = [i32, i32, i64] + [P] * 14
-        lib.oracle_mlp_loss_grad.restype = f64
-        lib.oracle_adam.argtypes = [i64, P, P, P, P, i64, f64, f64, f64, f64]
-        lib.oracle_adam.restype = None
-        lib.oracle_eigen_bench.argtypes = [i32, i32, P]
-        lib.oracle_eigen_bench.restype = None
-        lib.oracle_eigen_recurrence.argtypes = [ctypes.c_longlong, i32, i32, ctypes.c_double, P, P]
-        lib.oracle_eigen_recurrence.restype = None
-        lib.oracle_mass.argtypes = [i32, i32, i32, i64, P, P, P, P, i32]
-        lib.oracle_mass.restype = i32
-        _lib = lib
+        _lib = _bind(ctypes.CDLL(_LIB))
     return _lib
+
+
+def _bind(lib):
+    """Argument and result types of the oracle's C functions on a loaded library
+    (the tests also bind copies of oracle.c built with a planted mistake)."""
+    P = ctypes.c_void_p
+    i32, i64, f64 = ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    lib.oracle_update_chain.argtypes = [i32, i32, i32, i64, P, P, i32]
+    lib.oracle_update_chain.restype = i32
+    lib.oracle_update_chain_uneven.argtypes = [i64, P, P, P, P, P]
+    lib.oracle_update_chain_uneven.restype = i32
+    lib.oracle_ltimes.argtypes = [i32, i32, i64, i64, i32, i32, P, P, P, i32]
+    lib.oracle_ltimes.restype = i32
+    lib.oracle_ltimes_sample.argtypes = [i32, i32, i64, i64, i32, P, P, i64, P, P]
+    lib.oracle_lplustimes.argtypes = [i32, i32, i64, i64, i32, i32, P, P, P]
+    lib.oracle_lplustimes.restype = i32
+    lib.oracle_ltimes_sample.restype = i32
+    lib.oracle_mlp_forward.argtypes = [i32, i32, i64] + [P] * 10
+    lib.oracle_mlp_forward.restype = None
+    lib.oracle_mlp_loss_grad.argtypes = [i32, i32, i64] + [P] * 14
+    lib.oracle_mlp_loss_grad.restype = f64
+    lib.oracle_adam.argtypes = [i64, P, P, P, P, i64, f64, f64, f64, f64]
+    lib.oracle_adam.restype = None
+    lib.oracle_eigen_bench.argtypes = [i32, i32, P]
+    lib.oracle_eigen_bench.restype = None
+    lib.oracle_eigen_recurrence.argtypes = [ctypes.c_longlong, i32, i32, ctypes.c_double, P, P]
+    lib.oracle_eigen_recurrence.restype = None
+    lib.oracle_mass.argtypes = [i32, i32, i32, i64, P, P, P, P, i32]
+    lib.oracle_mass.restype = i32
+    return lib
 
 
 def _p(a: np.ndarray):
