@@ -216,3 +216,67 @@ def test_planted_mistake_fails_a_pin(tmp_path, name, group, old, new):
         pins = GROUPS[group]()
     failed = [k for k, v in pins.items() if not v]
     assert failed, f"no pin of group {group} catches {name}"
+
+
+# ---------------------------------------------------------------------------
+# The key contract (oracle/keys.py): hand-assembled bytes and the variant rule
+# ---------------------------------------------------------------------------
+
+def keys_pins(K):
+    u16 = lambda v: int(v).to_bytes(2, "little")
+    u32 = lambda v: int(v).to_bytes(4, "little")
+    pins = {}
+    want = (u16(1) + bytes([0, 1, 0, 0]) + u16(12) + u16(0) + u16(0) +
+            u32(1) + u32(21) + u32(0) + u32(0) + u32(2))
+    pins["chain key, column-major, NO_AOT"] = K.canonical_key(1, 0, n=12, layout_a=1, tile=(1, 21, 0, 0),
+                                                              flags=2) == want
+    want = (u16(2) + bytes([1, 3, 5, 0]) + u16(0) + u16(36) + u16(96) +
+            u32(1) + u32(128) + u32(320) + u32(6685700) + u32(0))
+    pins["LTimes key ignores n, keeps both orders"] = K.canonical_key(2, 1, n=7, layout_a=3, layout_b=5, m=36, d=96,
+                                                                      tile=(1, 128, 320, 6685700)) == want
+    want = u16(3) + bytes([1, 0, 0, 0]) + u16(40) + u16(0) + u16(0) + u32(8) + u32(2) + u32(0) + u32(0) + u32(0)
+    pins["grouped key zeroes the layout"] = K.canonical_key(3, 1, n=40, layout_a=1, tile=(8, 2, 0, 0)) == want
+    want = u16(1) + bytes([0, 0, 0, 0]) + u16(5) + u16(0) * 2 + u32(0) * 4 + u32(1)
+    pins["GENERIC drops the tile"] = K.canonical_key(1, 0, n=5, tile=(1, 32, 0, 0), flags=1) == want
+    pins["unknown flag bits are dropped"] = (K.canonical_key(1, 0, n=5, tile=(1, 32, 0, 0), flags=0x4) ==
+                                             K.canonical_key(1, 0, n=5, tile=(1, 32, 0, 0)))
+    pins["variant rule"] = (K.expected_variant(1, 1, 32, True) == 1 and K.expected_variant(1, 0, 16, True) == 1 and
+                            K.expected_variant(1, 0, 16, False) == 2 and K.expected_variant(1, 0, 5, True) == 2 and
+                            K.expected_variant(1, 0, 8, True, flags=2) == 2 and
+                            K.expected_variant(1, 0, 8, True, flags=1) == 0 and
+                            K.expected_variant(1, 2, 16, True) == 2 and K.expected_variant(3, 0, 8, True) == 2)
+    return pins
+
+
+KEY_MUTANTS = [
+    ("keys_swapped_orders", "layout_a, layout_b, 0, n, m, d, *tile", "layout_b, layout_a, 0, n, m, d, *tile"),
+    ("keys_grouped_keeps_layout", "            layout_a = 0\n", "            pass\n"),
+    ("keys_generic_keeps_tile", "        tile = (0, 0, 0, 0)\n", "        pass\n"),
+    ("keys_all_flags_kept", "*tile, flags & KEY_FLAGS)", "*tile, flags)"),
+    ("keys_aot_set_without_32", "AOT_SIZES = (4, 8, 16, 32)", "AOT_SIZES = (4, 8, 16)"),
+    ("keys_aot_for_explicit_tiles", "\n            and tile_left_to_library and", "\n            and"),
+    ("keys_ltimes_keeps_n", "    elif kernel in (K_LTIMES, K_LPLUSTIMES):\n        n = 0\n",
+     "    elif kernel in (K_LTIMES, K_LPLUSTIMES):\n        pass\n"),
+]
+
+
+def keys_module(text):
+    import types
+    mod = types.ModuleType("keys_copy")
+    exec(compile(text, "keys_copy.py", "exec"), mod.__dict__)
+    return mod
+
+
+def test_unmodified_keys_pass_every_pin():
+    from oracle import keys as K
+    pins = keys_pins(K)
+    assert all(pins.values()), {k: v for k, v in pins.items() if not v}
+
+
+@pytest.mark.parametrize("name,old,new", KEY_MUTANTS, ids=[m[0] for m in KEY_MUTANTS])
+def test_planted_key_mistake_fails_a_pin(name, old, new):
+    from oracle import keys as K
+    text = open(K.__file__).read()
+    assert text.count(old) == 1, name
+    pins = keys_pins(keys_module(text.replace(old, new)))
+    assert [k for k, v in pins.items() if not v], f"no key pin catches {name}"
