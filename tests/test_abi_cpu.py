@@ -513,3 +513,24 @@ def test_every_candidate_space_has_at_most_16_tiles(compile_only_sync):
                     sizes.append(((cj.K_MASS, dt, dim, D, Q), len(cj.candidates(cj.K_MASS, dt, n=D, m=Q, d=dim))))
     bad = [(req, c) for req, c in sizes if not 1 <= c <= 16]
     assert not bad, bad[:10]
+
+
+def test_features_tell_the_new_forms_apart(compile_only_sync):
+    """The cost model sees which form a tile is: LTimes mode 6 (operands in
+    tensor memory) against mode 5 (the same TMA-fed tile, operands in shared
+    memory), and chain mapping 8 (4 x 8 register blocks, columns padded to
+    8) against mapping 5 (4 x 4)."""
+    import numpy as np
+    t5 = (1, 128, 448, (4 << 20) | (5 << 16) | (2 << 8) | 8)
+    t6 = (1, 128, 448, (4 << 20) | (6 << 16) | (2 << 8) | 8)
+    f5 = cj.featurize(cj.K_LTIMES, cj.F32, 1 << 23, 1, t5, m=36, d=96)
+    f6 = cj.featurize(cj.K_LTIMES, cj.F32, 1 << 23, 1, t6, m=36, d=96)
+    assert f5[2] == f6[2] == 1.0            # both tensor-core tiles
+    assert f5[5] == f6[5] == 1.0            # both fed by TMA
+    assert f5[25] != f6[25]                 # the mode itself
+    assert np.count_nonzero(f5 != f6) >= 1
+    g5 = cj.featurize(cj.K_UPDATE_CHAIN, cj.F32, 1 << 14, 64, (5, 1, 0, 0), n=60)
+    g8 = cj.featurize(cj.K_UPDATE_CHAIN, cj.F32, 1 << 14, 64, (8, 1, 0, 0), n=60)
+    assert g5[22] == g8[22] == 1.0          # register-blocked panels
+    assert g5[19] != g8[19]                 # 4 x 4 against 4 x 8
+    assert g8[12] > g5[12] >= 0.0           # padding: n = 60 is a multiple of 4, not of 8
