@@ -162,6 +162,7 @@ class Handle:
         self.kernel = kernel
         self.dtype = args.dtype
         self.n = args.n
+        self.m, self.d = args.m, args.d
 
     def info(self):
         buf = ctypes.create_string_buffer(65)
@@ -212,15 +213,27 @@ def _launch(h: Handle, vals, batch: int, stream: int) -> None:
     _check(load().cj_launch(h.ptr, arr, batch, stream), "cj_launch")
 
 
+def _check_sizes(h: Handle, where: str, batch: int, *pairs) -> None:
+    """Each (tensor, elements) pair: a contiguous CUDA tensor of the handle's
+    element type holding at least that many elements (skipped for raw device
+    addresses and for an empty batch, which reads and writes nothing)."""
+    if batch > 0:
+        for t, elems in pairs:
+            _check_pool(t, h.dtype, elems, where)
+
+
 def launch_update_chain(h: Handle, A, X, steps: int, batch: int | None = None, stream=None) -> None:
     """X_T for every instance: A, X hold batch*n*n elements (tensors or device pointers)."""
     if batch is None:
         batch = A.numel() // (h.n * h.n)
+    _check_sizes(h, "cj_launch", batch, (A, batch * h.n * h.n), (X, batch * h.n * h.n))
     vals = [ctypes.c_void_p(_ptr(A)), ctypes.c_void_p(_ptr(X)), ctypes.c_int32(steps)]
     _launch(h, vals, batch, _stream(stream, A, X))
 
 
 def launch_ltimes(h: Handle, L, x, out, G: int, Z: int, stream=None) -> None:
+    """out = L . in: L [m][d], x (d*G*Z, layout_a), out (m*G*Z, layout_b)."""
+    _check_sizes(h, "cj_launch", G * Z, (L, h.m * h.d), (x, h.d * G * Z), (out, h.m * G * Z))
     vals = [ctypes.c_void_p(_ptr(L)), ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(out)),
             ctypes.c_int64(G), ctypes.c_int64(Z)]
     _launch(h, vals, Z, _stream(stream, L, x, out))
@@ -228,6 +241,7 @@ def launch_ltimes(h: Handle, L, x, out, G: int, Z: int, stream=None) -> None:
 
 def launch_lplustimes(h: Handle, Lp, out, x, G: int, Z: int, stream=None) -> None:
     """x += Lp . out (LPlusTimes): Lp [d][m], out (m*G*Z, layout_b), x (d*G*Z, layout_a)."""
+    _check_sizes(h, "cj_launch", G * Z, (Lp, h.m * h.d), (out, h.m * G * Z), (x, h.d * G * Z))
     vals = [ctypes.c_void_p(_ptr(Lp)), ctypes.c_void_p(_ptr(out)), ctypes.c_void_p(_ptr(x)),
             ctypes.c_int64(G), ctypes.c_int64(Z)]
     _launch(h, vals, Z, _stream(stream, Lp, out, x))
@@ -237,12 +251,15 @@ def launch_eigen(h: Handle, M0, M, repeat: int, c: float = 5e-5, batch=None, str
     """M_{k+1} = Ones + c (M_k + M_k M_k), repeat times, from M0 (batch*n*n, row-major) into M."""
     if batch is None:
         batch = M0.numel() // (h.n * h.n) if hasattr(M0, "numel") else 0
+    _check_sizes(h, "cj_launch", batch, (M0, batch * h.n * h.n), (M, batch * h.n * h.n))
     vals = [ctypes.c_void_p(_ptr(M0)), ctypes.c_void_p(_ptr(M)), ctypes.c_int32(repeat), ctypes.c_double(c)]
     _launch(h, vals, batch, _stream(stream, M0, M))
 
 
 def launch_mass(h: Handle, B1, op, x, y, ne: int, stream=None) -> None:
     """y_e = B^T diag(op_e) B x_e for ne elements (B1: [Q][D]; op: ne*Q^d; x, y: ne*D^d)."""
+    D, Q, dim = h.n, h.m, h.d
+    _check_sizes(h, "cj_launch", ne, (B1, Q * D), (op, ne * Q ** dim), (x, ne * D ** dim), (y, ne * D ** dim))
     vals = [ctypes.c_void_p(_ptr(B1)), ctypes.c_void_p(_ptr(op)), ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(y))]
     _launch(h, vals, ne, _stream(stream, B1, op, x, y))
 

@@ -534,3 +534,28 @@ def test_features_tell_the_new_forms_apart(compile_only_sync):
     assert g5[22] == g8[22] == 1.0          # register-blocked panels
     assert g5[19] != g8[19]                 # 4 x 4 against 4 x 8
     assert g8[12] > g5[12] >= 0.0           # padding: n = 60 is a multiple of 4, not of 8
+
+
+def test_binding_refuses_tensors_that_do_not_fit(compile_only_sync):
+    """The launch wrappers check each tensor against the request before calling
+    into libcj: a contiguous CUDA tensor of the handle's element type holding
+    enough elements.  Here (no GPU) every tensor is a host tensor, so each call
+    is refused with CJ_ERR_INVALID_ARG and never reaches the launch."""
+    torch = pytest.importorskip("torch")
+    h = cj.specialize(cj.K_UPDATE_CHAIN, cj.F64, n=4)
+    A = torch.zeros(3, 4, 4, dtype=torch.float64)
+    with pytest.raises(cj.CJError) as e:
+        cj.launch_update_chain(h, A, A, 8)
+    assert e.value.status == cj.CJ_ERR_INVALID_ARG and "CUDA" in str(e.value)
+    hl = cj.specialize(cj.K_LTIMES, cj.F32, m=36, d=96)
+    small = torch.zeros(10, dtype=torch.float32)
+    with pytest.raises(cj.CJError) as e:
+        cj.launch_ltimes(hl, small, small, small, 8, 64)
+    assert e.value.status == cj.CJ_ERR_INVALID_ARG
+    hm = cj.specialize(cj.K_MASS, cj.F64, n=3, m=4, d=2)
+    with pytest.raises(cj.CJError):
+        cj.launch_mass(hm, small, small, small, small, 5)
+    # an empty batch reads and writes nothing: no check, and libcj answers (no device here)
+    with pytest.raises(cj.CJError) as e:
+        cj.launch_mass(hm, small, small, small, small, 0)
+    assert e.value.status == cj.CJ_ERR_NO_DEVICE
