@@ -379,9 +379,10 @@ cj_status cj_group_plan_dispatcher(cj_group_plan p, int32_t *state, int32_t *n_t
  * threads)).  Compiles it if needed (waits),
  * and makes later launches (and graph captures) use it, as the plan's
  * autotuner does with the fastest.  variant < 0 only reports *variants (may
- * be NULL; 0 for a plan without a dispatcher).  CJ_ERR_INVALID_ARG: null
- * plan, no dispatcher or variant out of range; CJ_ERR_COMPILE: it failed to
- * compile; CJ_ERR_NO_DEVICE in compile-only mode. */
+ * be NULL; 0 for a plan without a dispatcher).  Not to be called while
+ * another thread launches or destroys the same plan.  CJ_ERR_INVALID_ARG:
+ * null plan, no dispatcher or variant out of range; CJ_ERR_COMPILE: it failed
+ * to compile; CJ_ERR_NO_DEVICE in compile-only mode. */
 cj_status cj_group_plan_use_dispatcher(cj_group_plan p, int32_t variant, int32_t *variants);
 /* Wait up to timeout_ms (negative: forever) for the instantiations of every
  * group of p to finish compiling.  CJ_OK: every group launches its
